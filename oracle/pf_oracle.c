@@ -1,0 +1,554 @@
+/*
+ * pf_oracle.c -- plain, slow FP64 CPU oracle for an ensemble of M independent
+ * bootstrap particle filters (Crisan, Miguez & Rios, "A simple scheme for the
+ * parallelisation of particle filters ...", arXiv:1407.8071).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker, not the product: only
+ * the test-suite, the smoke check and the CPU-baseline leg of the benchmark
+ * may load it.  It shares no code, header, table or constant generator with
+ * the CUDA path; the counter-based generator below is written separately on
+ * each side from its published definition.
+ *
+ * Everything is computed in double precision, in the order the paper states:
+ *   - Algorithm 1 (bootstrap filter): initialisation (step 1), propagation and
+ *     normalised weights (step 2a), resampling (step 2b).
+ *   - eq. (eqGtN): the running normalising-constant estimate G_t^N.
+ *   - Definition 1: the ensemble average of the M per-filter estimates.
+ *   - Sec. 4.1 eqs. (eqDiscreteLorenz-1..3): Euler-Maruyama Lorenz 63.
+ *   - Sec. 5.1: a diffusively coupled stochastic FitzHugh-Nagumo lattice,
+ *     here in the Rogers-McCulloch form with zero-flux boundaries.
+ * Resampling is systematic (allowed by the remark after Algorithm 1, which
+ * admits schemes other than multinomial); multinomial resampling, the form
+ * Algorithm 1 step 2b states literally, is kept for the rate tests.
+ *
+ * Compile with -ffp-contract=off: the resampling arithmetic must round every
+ * product and sum separately so that it is reproducible bit for bit.
+ *
+ * Parity status per function is stated in the Python wrapper's header.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_LG 0
+#define ORC_LORENZ63 1
+#define ORC_FHN 2
+
+#define ORC_STREAM_TRUTH 0u
+#define ORC_STREAM_OBS 1u
+#define ORC_STREAM_INIT 2u
+#define ORC_STREAM_DYN 3u
+#define ORC_STREAM_RESAMPLE 4u
+#define ORC_STREAM_PROPOSAL 5u
+#define ORC_STREAM_MISC 6u
+
+/* Model description, filled from Python (ctypes mirror in oracle/__init__.py). */
+typedef struct {
+    int32_t kind;      /* ORC_LG, ORC_LORENZ63, ORC_FHN                         */
+    int32_t dx;        /* state dimension                                        */
+    int32_t J;         /* FHN lattice side (dx = 2 J^2), else 0                  */
+    int32_t K;         /* Euler-Maruyama sub-steps between observations          */
+    double dt;         /* Euler-Maruyama step                                    */
+    double sigma_dyn;  /* dynamical noise scale: increment sigma*sqrt(dt)*z      */
+    double sigma0;     /* prior std around x0_mean                               */
+    double sigma_obs;  /* observation noise std                                  */
+    int32_t dy;        /* number of observed components                          */
+    int32_t n_params;  /* length of params                                       */
+    const double *params;   /* LG: A (dx*dx, drift -A x); L63: s,r,b; FHN: below */
+    const double *x0_mean;  /* dx                                               */
+    const int32_t *obs_idx; /* dy indices into the state vector                  */
+} orc_model;
+
+/* FHN parameter layout: a, b, c1, c2, d, D, stim_amp, stim_steps, stim_block */
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10: Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11.  Ten rounds of the 4x32 Philox bijection; the key */
+/* is bumped by the Weyl constants (golden ratio and sqrt(3)-1 in 0.32 fixed  */
+/* point) between rounds.                                                     */
+/* ------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Batch form for the tests: ctr is n x 4, out is n x 4. */
+void orc_philox_batch(int64_t n, const uint32_t *ctr, uint32_t key0, uint32_t key1, uint32_t *out)
+{
+    uint32_t key[2] = {key0, key1};
+    for (int64_t i = 0; i < n; ++i) orc_philox4x32_10(ctr + 4 * i, key, out + 4 * i);
+}
+
+/* Box & Muller (1958): two independent N(0,1) from two uniforms.
+ * u1 = (top 24 bits of a + 1) * 2^-24 lies in (0, 1]; u2 = (top 24 bits of b) * 2^-24
+ * lies in [0, 1).  Both are exact in binary32 and binary64. */
+static void box_muller(uint32_t a, uint32_t b, double *z0, double *z1)
+{
+    double u1 = ((double)(a >> 8) + 1.0) * 0x1p-24;
+    double u2 = (double)(b >> 8) * 0x1p-24;
+    double R = sqrt(-2.0 * log(u1));
+    double th = 2.0 * M_PI * u2;
+    *z0 = R * cos(th);
+    *z1 = R * sin(th);
+}
+
+/* Four normals for one Philox block: lanes (0,1) from words (0,1), lanes (2,3) from (2,3). */
+static void normals4(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, double z[4])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    box_muller(r[0], r[1], &z[0], &z[1]);
+    box_muller(r[2], r[3], &z[2], &z[3]);
+}
+
+/* Box-Muller on raw word pairs (ab: n x 2) -> z: n x 2. */
+void orc_box_muller_batch(int64_t n, const uint32_t *ab, double *z)
+{
+    for (int64_t i = 0; i < n; ++i) box_muller(ab[2 * i], ab[2 * i + 1], &z[2 * i], &z[2 * i + 1]);
+}
+
+void orc_normals_batch(int64_t n, const uint32_t *ctr, uint64_t seed, double *z)
+{
+    for (int64_t i = 0; i < n; ++i)
+        normals4(seed, ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], z + 4 * i);
+}
+
+/* Normal number nu of the stream addressed by (c0, c1, c2, stream):
+ * block nu/4 of the counter's last word, lane nu%4.  A one-block cache keeps
+ * the oracle from recomputing Philox four times per block. */
+typedef struct {
+    uint64_t seed;
+    uint32_t c0, c1, c2, stream;
+    int64_t block;
+    double z[4];
+} nstream;
+
+static void ns_init(nstream *s, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t stream)
+{
+    s->seed = seed; s->c0 = c0; s->c1 = c1; s->c2 = c2; s->stream = stream; s->block = -1;
+}
+
+static double ns_get(nstream *s, int64_t nu)
+{
+    int64_t b = nu >> 2;
+    if (b != s->block) {
+        normals4(s->seed, s->c0, s->c1, s->c2, (s->stream << 24) | (uint32_t)b, s->z);
+        s->block = b;
+    }
+    return s->z[nu & 3];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Models.                                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Position of variable v's normal within one sub-step's block of dx normals.
+ * LG and Lorenz: identity.  FHN (variable = plane*J^2 + node, plane 0 = v,
+ * plane 1 = w): 2*node + plane, so the (v, w) pair of a node is adjacent. */
+static int64_t noise_slot(const orc_model *md, int64_t v)
+{
+    if (md->kind == ORC_FHN) {
+        int64_t nn = (int64_t)md->J * md->J;
+        int64_t plane = v / nn, node = v % nn;
+        return 2 * node + plane;
+    }
+    return v;
+}
+
+/* Drift f(x) at sub-step n (the step from x_{n-1} to x_n, n >= 1). */
+static void drift(const orc_model *md, int64_t n, const double *x, double *f)
+{
+    const double *p = md->params;
+    if (md->kind == ORC_LG) {
+        int d = md->dx;
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) s += p[i * d + j] * x[j];
+            f[i] = -s;
+        }
+    } else if (md->kind == ORC_LORENZ63) {
+        /* Sec. 4.1; the continuous form's first equation reads -s(X1 - X2) as in
+         * eq. (eqDiscreteLorenz-1). */
+        double s = p[0], r = p[1], b = p[2];
+        f[0] = -s * (x[0] - x[1]);
+        f[1] = r * x[0] - x[1] - x[0] * x[2];
+        f[2] = x[0] * x[1] - b * x[2];
+    } else { /* ORC_FHN */
+        double a = p[0], bb = p[1], c1 = p[2], c2 = p[3], dd = p[4], D = p[5];
+        double amp = p[6];
+        int64_t stim_steps = (int64_t)p[7];
+        int blk = (int)p[8];
+        int J = md->J, nn = J * J;
+        const double *vv = x, *ww = x + nn;
+        for (int i = 0; i < J; ++i) {
+            for (int j = 0; j < J; ++j) {
+                int k = i * J + j;
+                double v = vv[k], w = ww[k];
+                /* zero-flux 5-point Laplacian: existing 4-neighbours minus count * v */
+                double lap = 0.0;
+                int cnt = 0;
+                if (i > 0) { lap += vv[k - J]; cnt++; }
+                if (i < J - 1) { lap += vv[k + J]; cnt++; }
+                if (j > 0) { lap += vv[k - 1]; cnt++; }
+                if (j < J - 1) { lap += vv[k + 1]; cnt++; }
+                lap -= (double)cnt * v;
+                double I = (i < blk && j < blk && (n - 1) < stim_steps) ? amp : 0.0;
+                f[k] = c1 * v * (v - a) * (1.0 - v) - c2 * v * w + D * lap + I;
+                f[nn + k] = bb * (v - dd * w);
+            }
+        }
+    }
+}
+
+/* One Euler-Maruyama step x <- x + dt f(x) + sigma sqrt(dt) z, z[v] = normal of
+ * variable v.  f must have room for dx doubles. */
+static void em_step(const orc_model *md, int64_t n, double *x, const double *z, double *f)
+{
+    drift(md, n, x, f);
+    double sq = md->sigma_dyn * sqrt(md->dt);
+    for (int v = 0; v < md->dx; ++v) x[v] = x[v] + md->dt * f[v] + sq * z[v];
+}
+
+/* Propagate one particle (filter-local index i of filter m, or the truth with
+ * c0 = 0, c2 = record) over the K sub-steps from observation t-1 to t.
+ * Normal number nu = k*dx + slot(v) for sub-step k = 0..K-1, counter
+ * (c0, t, c2, stream<<24 | nu/4). */
+static void propagate_one(const orc_model *md, uint64_t seed, uint32_t stream, uint32_t c0, uint32_t c2,
+                          int32_t t, double *x, double *z, double *f)
+{
+    nstream ns;
+    ns_init(&ns, seed, c0, (uint32_t)t, c2, stream);
+    for (int k = 0; k < md->K; ++k) {
+        for (int v = 0; v < md->dx; ++v) z[v] = ns_get(&ns, (int64_t)k * md->dx + noise_slot(md, v));
+        int64_t n = (int64_t)(t - 1) * md->K + k + 1;
+        em_step(md, n, x, z, f);
+    }
+}
+
+/* Prior draw x0 = x0_mean + sigma0 z, z from (c0, 0, c2, stream<<24 | slot/4). */
+static void prior_one(const orc_model *md, uint64_t seed, uint32_t stream, uint32_t c0, uint32_t c2, double *x)
+{
+    nstream ns;
+    ns_init(&ns, seed, c0, 0u, c2, stream);
+    for (int v = 0; v < md->dx; ++v) x[v] = md->x0_mean[v] + md->sigma0 * ns_get(&ns, noise_slot(md, v));
+}
+
+/* log g without its constant: -1/2 sum_j (y_j - x[idx_j])^2 / sigma_obs^2. */
+static double loglik(const orc_model *md, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int j = 0; j < md->dy; ++j) {
+        double e = y[j] - x[md->obs_idx[j]];
+        s += e * e;
+    }
+    return -0.5 * s / (md->sigma_obs * md->sigma_obs);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Component entry points (particle-major x: n x dx).                        */
+/* ------------------------------------------------------------------------- */
+
+void orc_prior(const orc_model *md, int64_t n, const int32_t *pid, const int32_t *fid, uint64_t seed, double *x)
+{
+    for (int64_t q = 0; q < n; ++q)
+        prior_one(md, seed, ORC_STREAM_INIT, (uint32_t)pid[q], (uint32_t)fid[q], x + q * md->dx);
+}
+
+void orc_propagate(const orc_model *md, int64_t n, const int32_t *pid, const int32_t *fid, int32_t t,
+                   uint64_t seed, int32_t stream, double *x)
+{
+    double *z = (double *)malloc(sizeof(double) * md->dx);
+    double *f = (double *)malloc(sizeof(double) * md->dx);
+    for (int64_t q = 0; q < n; ++q)
+        propagate_one(md, seed, (uint32_t)stream, (uint32_t)pid[q], (uint32_t)fid[q], t, x + q * md->dx, z, f);
+    free(z);
+    free(f);
+}
+
+/* One Euler-Maruyama step with explicit normals (z: n x dx), for the
+ * closed-form single-step pins. */
+void orc_em_step(const orc_model *md, int64_t n, int64_t step, double *x, const double *z)
+{
+    double *f = (double *)malloc(sizeof(double) * md->dx);
+    for (int64_t q = 0; q < n; ++q) em_step(md, step, x + q * md->dx, z + q * md->dx, f);
+    free(f);
+}
+
+void orc_drift(const orc_model *md, int64_t step, const double *x, double *f) { drift(md, step, x, f); }
+
+void orc_loglik(const orc_model *md, int64_t n, const double *x, const double *y, double *l)
+{
+    for (int64_t q = 0; q < n; ++q) l[q] = loglik(md, x + q * md->dx, y);
+}
+
+/* Per-filter normaliser (Algorithm 1 step 2a in the log domain):
+ * out[0] = max l, out[1] = log sum exp(l), out[2] = sum w, out[3] = sum w^2,
+ * out[4] = ESS = (sum w)^2 / sum w^2, with w = exp(l - max) and Neumaier-
+ * compensated sums. */
+void orc_normalise(int64_t n, const double *l, double *out)
+{
+    double mx = -INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+        if (l[i] > mx) mx = l[i];
+    double s = 0.0, cs = 0.0, s2 = 0.0, cs2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double w = exp(l[i] - mx);
+        double t = s + w;
+        if (fabs(s) >= fabs(w)) cs += (s - t) + w; else cs += (w - t) + s;
+        s = t;
+        double w2 = w * w;
+        double t2 = s2 + w2;
+        if (fabs(s2) >= fabs(w2)) cs2 += (s2 - t2) + w2; else cs2 += (w2 - t2) + s2;
+        s2 = t2;
+    }
+    s += cs;
+    s2 += cs2;
+    out[0] = mx;
+    out[1] = mx + log(s);
+    out[2] = s;
+    out[3] = s2;
+    out[4] = s * s / s2;
+}
+
+/* Systematic resampling, exact-integer form.
+ * L = ceil(log2 N), sh = 52 - L; q_i = floor(w_i 2^sh) for unnormalised weights
+ * w_i in [0, 1]; C_k = q_0 + ... + q_k (exact: every partial sum is an integer
+ * below 2^53); c = C_{N-1} / N; t_i = (i + u) * c, each operation rounded to
+ * nearest; a_i = min{k : C_k > t_i}, or, when no C_k exceeds t_i, the last k
+ * with q_k > 0.  The plain two-pointer merge below is that definition. */
+static int ceil_log2(int64_t n)
+{
+    int L = 0;
+    while (((int64_t)1 << L) < n) ++L;
+    return L;
+}
+
+void orc_quantise(int64_t N, const double *w, double *q)
+{
+    int sh = 52 - ceil_log2(N);
+    double scale = ldexp(1.0, sh);
+    for (int64_t i = 0; i < N; ++i) q[i] = floor(w[i] * scale);
+}
+
+void orc_systematic(int64_t N, const double *w, double u, int32_t *anc)
+{
+    double *C = (double *)malloc(sizeof(double) * N);
+    orc_quantise(N, w, C);
+    double run = 0.0;
+    int64_t last_pos = 0;
+    for (int64_t k = 0; k < N; ++k) {
+        run = run + C[k];
+        if (C[k] > 0.0) last_pos = k;
+        C[k] = run;
+    }
+    double c = C[N - 1] / (double)N;
+    int64_t k = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        volatile double a = (double)i + u; /* two separately rounded operations */
+        double t = a * c;
+        while (k < N && !(C[k] > t)) ++k;
+        anc[i] = (int32_t)(k < N ? k : last_pos);
+    }
+    free(C);
+}
+
+/* Multinomial resampling (Algorithm 1 step 2b as stated): a_i = min{k : C_k > U_i C_N}
+ * with the same exact prefix and independent uniforms U_i. */
+void orc_multinomial(int64_t N, const double *w, const double *U, int32_t *anc)
+{
+    double *C = (double *)malloc(sizeof(double) * N);
+    orc_quantise(N, w, C);
+    double run = 0.0;
+    int64_t last_pos = 0;
+    for (int64_t k = 0; k < N; ++k) {
+        run = run + C[k];
+        if (C[k] > 0.0) last_pos = k;
+        C[k] = run;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        double t = U[i] * C[N - 1];
+        int64_t lo = 0, hi = N; /* first k with C_k > t */
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (C[mid] > t) hi = mid; else lo = mid + 1;
+        }
+        anc[i] = (int32_t)(lo < N ? lo : last_pos);
+    }
+    free(C);
+}
+
+/* Resampling uniform for filter m at observation t: word 0 of Philox at
+ * (0, t, m, RESAMPLE<<24) times 2^-32. */
+double orc_resample_u(uint64_t seed, int32_t m, int32_t t)
+{
+    uint32_t ctr[4] = {0u, (uint32_t)t, (uint32_t)m, ORC_STREAM_RESAMPLE << 24};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    return (double)r[0] * 0x1p-32;
+}
+
+static double multinomial_u(uint64_t seed, int32_t m, int32_t t, int64_t i)
+{
+    uint32_t ctr[4] = {(uint32_t)i, (uint32_t)t, (uint32_t)m, (ORC_STREAM_RESAMPLE << 24) | 1u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    return (double)r[0] * 0x1p-32;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Synthetic truth and observation record (Sec. 4.2: one record, generated    */
+/* once and shared by every filter).                                          */
+/* init_mode 0: X_0 = x0_mean; 1: X_0 = x0_mean + sigma0 z (stream MISC).     */
+/* Truth dynamics use stream TRUTH with c0 = 0, c2 = record; observation     */
+/* noise uses stream OBS at (0, t, record, OBS<<24 | j/4), lane j%4.          */
+/* x_out: (T+1) x dx, y_out: T x dy.                                          */
+/* ------------------------------------------------------------------------- */
+void orc_simulate(const orc_model *md, int32_t T, uint64_t seed, int32_t record, int32_t init_mode,
+                  double *x_out, double *y_out)
+{
+    int dx = md->dx;
+    double *x = (double *)malloc(sizeof(double) * dx);
+    double *z = (double *)malloc(sizeof(double) * dx);
+    double *f = (double *)malloc(sizeof(double) * dx);
+    if (init_mode == 1) prior_one(md, seed, ORC_STREAM_MISC, 0u, (uint32_t)record, x);
+    else memcpy(x, md->x0_mean, sizeof(double) * dx);
+    memcpy(x_out, x, sizeof(double) * dx);
+    for (int32_t t = 1; t <= T; ++t) {
+        propagate_one(md, seed, ORC_STREAM_TRUTH, 0u, (uint32_t)record, t, x, z, f);
+        memcpy(x_out + (int64_t)t * dx, x, sizeof(double) * dx);
+        nstream ns;
+        ns_init(&ns, seed, 0u, (uint32_t)t, (uint32_t)record, ORC_STREAM_OBS);
+        for (int j = 0; j < md->dy; ++j)
+            y_out[(int64_t)(t - 1) * md->dy + j] = x[md->obs_idx[j]] + md->sigma_obs * ns_get(&ns, j);
+    }
+    free(x);
+    free(z);
+    free(f);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The ensemble: M independent runs of Algorithm 1 and the average of          */
+/* Definition 1.                                                              */
+/*                                                                            */
+/* obs: T x dy (obs_per_filter = 0) or T x M x dy (obs_per_filter = 1).       */
+/* resampler: 0 systematic, 1 multinomial.                                    */
+/* Outputs (any may be NULL), row-major over (t-1, m, e):                     */
+/*   est_post[T][M][n_est]  (f, pi_t^{m,N}), post-resampling mean             */
+/*   est_pre [T][M][n_est]  weighted pre-resampling mean                       */
+/*   log_G   [T][M]         log G_t^N, eq. (eqGtN), with the Gaussian constant */
+/*   ess     [T][M]         (sum w)^2 / sum w^2 before resampling              */
+/*   ens     [T][n_est]     Definition 1: mean over m of est_post               */
+/* x_final: sum_m N_m x dx particle-major filter-after-filter (or NULL).       */
+/* ------------------------------------------------------------------------- */
+int orc_bf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, const double *obs,
+               int32_t obs_per_filter, uint64_t seed, int32_t resampler, int32_t n_est, const int32_t *est_idx,
+               double *est_post, double *est_pre, double *log_G, double *ess, double *ens, double *x_final,
+               int32_t n_threads)
+{
+    int dx = md->dx;
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (M + 1));
+    off[0] = 0;
+    for (int m = 0; m < M; ++m) off[m + 1] = off[m] + N[m];
+    const double log_const = -0.5 * md->dy * log(2.0 * M_PI * md->sigma_obs * md->sigma_obs);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int m = 0; m < M; ++m) {
+        int64_t Nm = N[m];
+        double *x = (double *)malloc(sizeof(double) * Nm * dx);
+        double *xn = (double *)malloc(sizeof(double) * Nm * dx);
+        double *l = (double *)malloc(sizeof(double) * Nm);
+        double *w = (double *)malloc(sizeof(double) * Nm);
+        double *U = (double *)malloc(sizeof(double) * Nm);
+        int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * Nm);
+        double *z = (double *)malloc(sizeof(double) * dx);
+        double *f = (double *)malloc(sizeof(double) * dx);
+        double lg = 0.0;
+        /* Algorithm 1, step 1 */
+        for (int64_t i = 0; i < Nm; ++i) prior_one(md, seed, ORC_STREAM_INIT, (uint32_t)i, (uint32_t)m, x + i * dx);
+        for (int32_t t = 1; t <= T; ++t) {
+            const double *y = obs_per_filter ? obs + ((int64_t)(t - 1) * M + m) * md->dy
+                                             : obs + (int64_t)(t - 1) * md->dy;
+            /* step 2a: propagate and weight */
+            for (int64_t i = 0; i < Nm; ++i) {
+                propagate_one(md, seed, ORC_STREAM_DYN, (uint32_t)i, (uint32_t)m, t, x + i * dx, z, f);
+                l[i] = loglik(md, x + i * dx, y);
+            }
+            double nrm[5];
+            orc_normalise(Nm, l, nrm);
+            for (int64_t i = 0; i < Nm; ++i) w[i] = exp(l[i] - nrm[0]);
+            /* eq. (eqGtN): log G_t = log G_{t-1} + log((1/N) sum_j g_t(x_j)) */
+            lg += nrm[1] - log((double)Nm) + log_const;
+            int64_t row = (int64_t)(t - 1) * M + m;
+            if (log_G) log_G[row] = lg;
+            if (ess) ess[row] = nrm[4];
+            if (est_pre) {
+                for (int e = 0; e < n_est; ++e) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < Nm; ++i) s += w[i] * x[i * dx + est_idx[e]];
+                    est_pre[row * n_est + e] = s / nrm[2];
+                }
+            }
+            /* step 2b: resample */
+            if (resampler == 1) {
+                for (int64_t i = 0; i < Nm; ++i) U[i] = multinomial_u(seed, m, t, i);
+                orc_multinomial(Nm, w, U, anc);
+            } else {
+                orc_systematic(Nm, w, orc_resample_u(seed, m, t), anc);
+            }
+            for (int64_t i = 0; i < Nm; ++i) memcpy(xn + i * dx, x + (int64_t)anc[i] * dx, sizeof(double) * dx);
+            double *tmp = x; x = xn; xn = tmp;
+            if (est_post) {
+                for (int e = 0; e < n_est; ++e) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < Nm; ++i) s += x[i * dx + est_idx[e]];
+                    est_post[row * n_est + e] = s / (double)Nm;
+                }
+            }
+        }
+        if (x_final) memcpy(x_final + off[m] * dx, x, sizeof(double) * Nm * dx);
+        free(x); free(xn); free(l); free(w); free(U); free(anc); free(z); free(f);
+    }
+    /* Definition 1: the ensemble average over the M filters, in filter order */
+    if (ens && est_post) {
+        for (int32_t t = 0; t < T; ++t)
+            for (int e = 0; e < n_est; ++e) {
+                double s = 0.0;
+                for (int m = 0; m < M; ++m) s += est_post[((int64_t)t * M + m) * n_est + e];
+                ens[(int64_t)t * n_est + e] = s / (double)M;
+            }
+    }
+    free(off);
+    return 0;
+}

@@ -1,0 +1,146 @@
+"""Pins for the oracle's counter-based generator and Box-Muller normals.
+
+Philox4x32-10 (Salmon et al., SC'11) has no closed form, so it is pinned by
+(1) inverting it with an independent inverse built from the published round
+structure, the published multipliers and the Weyl key increments derived here
+from their definitions (golden ratio and sqrt(3) - 1), which catches a wrong
+constant, word order or key schedule, and (2) statistical properties that
+any correct 10-round Philox meets.  Box-Muller is pinned by closed-form
+special values and by distribution tests.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1407_8071_gb300 import workloads as W
+
+MASK = (1 << 32) - 1
+M0, M1 = 0xD2511F53, 0xCD9E8D57  # published Philox-4x32 multipliers
+
+
+def weyl_constants():
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    # 0.32 fixed point of (phi - 1) and (sqrt(3) - 1), via exact integer arithmetic
+    w0 = math.isqrt(5 << 64) + (1 << 32)  # floor(2^32 * sqrt5) + 2^32 = floor(2^32 (sqrt5 + 1))
+    w0 = (w0 // 2) - (1 << 32)            # floor(2^32 * (phi - 1)) = floor(2^32 (sqrt5 - 1) / 2)
+    w1 = math.isqrt(3 << 64) - (1 << 32)  # floor(2^32 * (sqrt3 - 1))
+    assert abs(w0 / 2 ** 32 - (phi - 1.0)) < 1e-9
+    return w0, w1
+
+
+def philox_inverse(out, key):
+    """Undo 10 Philox rounds: lo words give the multiplied inputs back through the
+    multipliers' inverses mod 2^32, the hi words then undo the XORs."""
+    w0, w1 = weyl_constants()
+    inv0, inv1 = pow(M0, -1, 1 << 32), pow(M1, -1, 1 << 32)
+    keys = []
+    k0, k1 = key
+    for r in range(10):
+        if r:
+            k0, k1 = (k0 + w0) & MASK, (k1 + w1) & MASK
+        keys.append((k0, k1))
+    n0, n1, n2, n3 = out
+    for k0, k1 in reversed(keys):
+        c0 = (n3 * inv0) & MASK
+        c2 = (n1 * inv1) & MASK
+        hi0 = (M0 * c0) >> 32
+        hi1 = (M1 * c2) >> 32
+        c1 = n0 ^ hi1 ^ k0
+        c3 = n2 ^ hi0 ^ k1
+        n0, n1, n2, n3 = c0, c1, c2, c3
+    return n0, n1, n2, n3
+
+
+def test_weyl_constants_match_definitions():
+    w0, w1 = weyl_constants()
+    assert w0 == 0x9E3779B9
+    assert w1 == 0xBB67AE85
+
+
+def test_philox_inverts_to_counter():
+    ctr = W.random_counters(200, seed=11)
+    keys = W.random_counters(200, seed=12)[:, :2]
+    for c, k in zip(ctr, keys):
+        out = oracle.philox(c[None, :], int(k[0]), int(k[1]))[0]
+        back = philox_inverse(tuple(int(v) for v in out), (int(k[0]), int(k[1])))
+        assert back == tuple(int(v) for v in c)
+
+
+def test_philox_uniform_chi2():
+    n = 1 << 16
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n)
+    ctr[:, 1] = 7
+    ctr[:, 3] = 3 << 24
+    out = oracle.philox(ctr, 0x1234, 0x5678)
+    for word in range(4):
+        counts = np.bincount((out[:, word] >> 24).astype(np.int64), minlength=256)
+        p = stats.chisquare(counts).pvalue
+        assert p > 1e-4, (word, p)
+
+
+def test_philox_avalanche():
+    rng = np.random.default_rng(5)
+    base = W.random_counters(256, seed=13)
+    flips = []
+    for c in base:
+        bit = int(rng.integers(0, 128))
+        c2 = c.copy()
+        c2[bit // 32] ^= np.uint32(1 << (bit % 32))
+        a = oracle.philox(c[None], 1, 2)[0]
+        b = oracle.philox(c2[None], 1, 2)[0]
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)))
+    # 128 output bits, each flipping with probability 1/2
+    assert abs(np.mean(flips) - 64.0) < 1.5
+    assert 4.0 < np.std(flips) < 8.0
+
+
+def test_box_muller_closed_forms():
+    # u1 = 1 (a's top 24 bits all ones) gives R = 0.
+    z = oracle.box_muller(np.array([[0xFFFFFFFF, 12345 << 8]], dtype=np.uint32))
+    assert np.all(z == 0.0)
+    # u1 = 2^-24, u2 = 0: z0 = sqrt(48 ln 2), z1 = 0
+    z = oracle.box_muller(np.array([[0x000000FF, 0x000000FF]], dtype=np.uint32))
+    assert z[0, 0] == pytest.approx(math.sqrt(48.0 * math.log(2.0)), rel=1e-15)
+    assert abs(z[0, 1]) < 1e-15
+    # u1 = 1/2, u2 = 1/4: R = sqrt(2 ln 2), angle pi/2 -> (0, R)
+    z = oracle.box_muller(np.array([[(1 << 31) - 256, 1 << 30]], dtype=np.uint32))
+    R = math.sqrt(2.0 * math.log(2.0))
+    assert abs(z[0, 0]) < 1e-15 and z[0, 1] == pytest.approx(R, rel=1e-15)
+
+
+def test_normals_distribution():
+    n = 1 << 15
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n)
+    ctr[:, 2] = 9
+    ctr[:, 3] = W.STREAM_DYN << 24
+    z = oracle.normals(ctr, seed=0xABCDEF0123)
+    flat = z.ravel()
+    assert abs(flat.mean()) < 4.0 / math.sqrt(flat.size)
+    assert abs(flat.var() - 1.0) < 4.0 * math.sqrt(2.0 / flat.size)
+    assert stats.kstest(flat, "norm").pvalue > 1e-4
+    # the two members of a pair and the two pairs are uncorrelated
+    for a, b in [(0, 1), (2, 3), (0, 2), (1, 3)]:
+        r = np.corrcoef(z[:, a], z[:, b])[0, 1]
+        assert abs(r) < 4.0 / math.sqrt(n), (a, b, r)
+
+
+def test_normals_are_philox_then_box_muller():
+    ctr = W.random_counters(64, seed=21)
+    seed = 0x0123456789ABCDEF
+    r = oracle.philox(ctr, seed & MASK, seed >> 32)
+    z = oracle.normals(ctr, seed)
+    zp = oracle.box_muller(r.reshape(-1, 2)).reshape(-1, 4)
+    assert np.array_equal(z, zp)
+
+
+def test_resample_uniform_grid_and_streams():
+    us = np.array([oracle.resample_u(77, m, t) for m in range(64) for t in range(1, 17)])
+    assert np.all((us >= 0.0) & (us < 1.0))
+    assert np.all(us * 2 ** 32 == np.floor(us * 2 ** 32))
+    assert len(np.unique(us)) == us.size
+    assert stats.kstest(us, "uniform").pvalue > 1e-4
