@@ -1,0 +1,403 @@
+"""Throughput benchmark of the GPU ensemble particle filter.
+
+Workload (default): the Lorenz 63 ensemble with a total budget of M * N = 2^20
+particles swept over M in {1, 4, 16, 64, 256, 1024, 4096}, N = 2^20 / M, all
+seven configurations resident on the GPU.  One bench step is one observation
+time of all seven: for each configuration K = 40 Euler-Maruyama sub-steps of
+every particle, Gaussian weights, FP64 normalisation, systematic resampling
+with the gather, and the per-filter and ensemble means.  The metric is
+particle-steps/s (one Euler-Maruyama sub-step of one particle).
+
+`--workload fhn` runs the 40 x 40 FitzHugh-Nagumo lattice at M = 32, N = 1024.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the plain restatement of the method this project checks against) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1407_8071_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+# Algorithmic ALU operations per Lorenz particle-step (one Euler-Maruyama
+# sub-step of one particle); the derivation is in the design doc:
+#   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs) = 40,
+#                  0.75 calls per sub-step (3 blocks per 4 sub-steps)       -> 30
+#   Box-Muller pair: 4 (uniforms) + 8 (log) + 2 (sqrt) + 12 (sincospi)
+#                  + 3 (scalings) = 29, 1.5 pairs per sub-step               -> 43.5
+#   drift 7 + Euler-Maruyama update 6                                      -> 13
+LORENZ_OPS_PER_PARTICLE_STEP = 86.5
+# Algorithmic bytes of one FHN particle per observation interval: read and
+# write the 40 x 40 x 2 FP32 state once (the K sub-steps stay on chip) + logw.
+FHN_BYTES_PER_PARTICLE_OBS = 2 * 3200 * 4 + 4
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1407_8071_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel sources have not changed since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = source_digest()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+class Workload:
+    def __init__(self, name, seed_base):
+        import torch
+        from paper_1407_8071_gb300 import pf
+        self.name = name
+        self.filters = []
+        if name == "lorenz-sweep":
+            self.spec = W.lorenz63()
+            self.rows = W.lorenz_sweep()
+            rec_seed = W.SEED_LORENZ_OBS
+        elif name == "fhn":
+            self.spec = W.fhn_lattice()
+            self.rows = [(W.FHN_FULL["M"], W.FHN_FULL["N"])]
+            rec_seed = W.SEED_FHN_OBS
+        else:
+            raise ValueError(name)
+        T = 200 if name == "lorenz-sweep" else W.FHN_FULL["T"]
+        _, y = pf.pf_simulate(self.spec, T, rec_seed)
+        self.T = T
+        self.y_host = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
+        self.y_dev = self.y_host.cuda()
+        self.stream = torch.cuda.Stream()
+        for i, (M, N) in enumerate(self.rows):
+            f = pf.EnsembleFilter(self.spec, M, N, seed=seed_base + i)
+            f.set_stream(self.stream.cuda_stream)
+            self.filters.append(f)
+        self.particles = sum(M * N for M, N in self.rows)
+        self.particle_steps_per_step = self.particles * self.spec.K
+        # kernels one pf_step launches (propagate, tile max, weights, scan, ancestors, means, ensemble
+        # for the small models; lattice: propagate, tile max, weights, scan, ancestors, gather, means, ensemble)
+        self.kernels_per_filter_step = 8 if self.spec.kind == W.FHN else 7
+        self.t = 0
+
+    def step_device(self):
+        row = self.y_dev[self.t % self.T]
+        for f in self.filters:
+            f.step_device(row)
+        self.t += 1
+
+    def step_host(self):
+        """Through the public API with host buffers: H2D of y_t, D2H of each ensemble estimate."""
+        from paper_1407_8071_gb300 import pf
+        y = self.y_host[self.t % self.T].numpy()
+        for f in self.filters:
+            f.step(y)
+        var = 1 if self.spec.kind == W.LORENZ63 else 0
+        for f in self.filters:
+            f.estimate(pf.PF_STAT_MEAN, var=var)
+        self.t += 1
+
+    def close(self):
+        for f in self.filters:
+            f.close()
+
+
+def time_region(torch, stream, fn, K, barrier=None):
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(K):
+        fn()
+    end.record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    return start.elapsed_time(end) / 1e3
+
+
+def phase_times(torch, wl, reps=5):
+    """Average device time of the propagate+weight kernel and of the resampling
+    chain, per launch, with CUDA events on the filters' stream."""
+    prop, res = [], []
+    for f in wl.filters:
+        for _ in range(reps):
+            row = wl.y_dev[wl.t % wl.T]
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(wl.stream)
+            f.propagate_device(row)
+            e1.record(wl.stream)
+            f.resample()
+            e2.record(wl.stream)
+            torch.cuda.synchronize()
+            prop.append(e0.elapsed_time(e1) / 1e3)
+            res.append(e1.elapsed_time(e2) / 1e3)
+            wl.t += 1
+    return float(np.mean(prop)), float(np.mean(res)), prop
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(workload: str, target_s: float):
+    """Times the FP64 oracle on a bounded sample of the workload; returns
+    (particle-steps/s, threads, sample description)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    if workload == "fhn":
+        spec = W.fhn_lattice()
+        M, N = min(32, 2 * cores), 4
+        _, y = oracle.simulate(spec, 4, W.SEED_FHN_OBS)
+    else:
+        spec = W.lorenz63()
+        M, N = min(64, 2 * cores), 1 << 14  # filters of the M = 64, N = 16384 row of the sweep
+        _, y = oracle.simulate(spec, 200, W.SEED_LORENZ_OBS)
+    threads = min(M, cores)
+    t0 = time.perf_counter()
+    oracle.bf_run(spec, M, N, 1, y, seed=1, est_idx=[1], threads=threads)
+    dt1 = time.perf_counter() - t0
+    T = int(max(1, min(len(y), round(target_s / max(dt1, 1e-3)))))
+    t0 = time.perf_counter()
+    oracle.bf_run(spec, M, N, T, y, seed=2, est_idx=[1], threads=threads)
+    dt = time.perf_counter() - t0
+    ps = M * N * T * spec.K
+    desc = (f"{W.KIND_NAMES[spec.kind]}: {M} filters x {N} particles x {T} observations x K={spec.K} "
+            f"(= {ps:.3g} particle-steps) of the {workload} workload, FP64, OpenMP over filters")
+    return ps / dt, threads, desc
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import oracle
+    cores = os.cpu_count() or 1
+    if args.workload == "fhn":
+        spec = W.fhn_lattice()
+        M, N = min(32, 2 * cores), 2
+        _, y = oracle.simulate(spec, 2, W.SEED_FHN_OBS)
+    else:
+        spec = W.lorenz63()
+        M, N = min(32, 2 * cores), 1 << 12
+        _, y = oracle.simulate(spec, 2, W.SEED_LORENZ_OBS)
+    threads = min(M, cores)
+    work = M * N * spec.K
+    for _ in range(args.warmup):
+        oracle.bf_run(spec, M, N, 1, y, seed=3, est_idx=[1], threads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.bf_run(spec, M, N, 1, y, seed=4 + k, est_idx=[1], threads=threads)
+    dt = time.perf_counter() - t0
+    value = work * args.steps / dt
+    sample = (f"each step: one observation interval (K={spec.K}) of {M} filters x {N} particles of the "
+              f"{args.workload} workload in the FP64 C oracle (prior draw included)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="lorenz-sweep", choices=["lorenz-sweep", "fhn"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1407_8071_gb300 import pf
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    barrier = None
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+    pf.lib()
+
+    wl = Workload(args.workload, seed_base=1000 * rank + 1)
+    for _ in range(args.warmup):
+        wl.step_device()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    elapsed = time_region(torch, wl.stream, wl.step_device, args.steps, barrier)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * wl.particle_steps_per_step * args.steps / elapsed
+
+    # end to end through the public API with host buffers
+    for _ in range(2):
+        wl.step_host()
+    e2e_elapsed = time_region(torch, wl.stream, wl.step_host, args.steps, barrier)
+    if world > 1:
+        t = torch.tensor([e2e_elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_elapsed = float(t.item())
+    e2e_value = world * wl.particle_steps_per_step * args.steps / e2e_elapsed
+    nf = len(wl.filters)
+
+    # the dominant kernel, timed live per launch
+    t_prop, t_res, _ = phase_times(torch, wl)
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if wl.spec.kind == W.LORENZ63:
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # T ops/s
+        per_launch_ops = (wl.particles / nf) * wl.spec.K * LORENZ_OPS_PER_PARTICLE_STEP
+        achieved = per_launch_ops / t_prop / 1e12
+        roofline = {"bound": "alu", "kernel": "k_propagate_small<3>", "achieved": achieved, "peak": alu_peak,
+                    "unit": "Tops/s", "frac": achieved / alu_peak,
+                    "traffic": recorded_traffic("k_propagate_small<3>"),
+                    "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
+                    "ops_per_particle_step": LORENZ_OPS_PER_PARTICLE_STEP, "avg_launch_s": t_prop}
+    else:
+        hbm = float(peaks["hbm_gbs"])
+        per_launch_bytes = wl.particles * FHN_BYTES_PER_PARTICLE_OBS
+        achieved = per_launch_bytes / t_prop / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_propagate_fhn<float>", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm, "traffic": recorded_traffic("k_propagate_fhn<float>"),
+                    "peak_source": f"{peak_src} copy bandwidth", "avg_launch_s": t_prop}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": ("lorenz63 ensemble, M*N = 2^20 swept over M in {1,4,16,64,256,1024,4096}, all seven "
+                         "resident; one step = one observation (K=40 Euler-Maruyama sub-steps) of each")
+            if args.workload == "lorenz-sweep" else "fhn 40x40 lattice, M=32 x N=1024, K=20",
+            "rows": [{"M": M, "N": N} for M, N in wl.rows], "K": wl.spec.K, "dt": wl.spec.dt,
+            "precision": "FP32 state and propagation; FP64 normaliser, prefix sum and M-average",
+            "l2": ("working set of the seven contexts (~340 MB) exceeds the 129 MB L2; each context's data "
+                   "is evicted by the other six between its steps") if args.workload == "lorenz-sweep"
+            else "state 839 MB per buffer, larger than L2",
+        },
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": nf * wl.spec.dy * 4,
+                "d2h_bytes_per_step": nf * 8},
+        "gpu_launches": args.steps * nf * wl.kernels_per_filter_step,
+        "roofline": roofline,
+        "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res},
+    }
+    wl.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc = oracle_sample(args.workload, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

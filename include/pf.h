@@ -1,0 +1,268 @@
+/*
+ * pf.h -- C ABI of the GB300 ensemble particle filter.
+ *
+ * The library runs the parallelisation scheme of Crisan, Miguez & Rios
+ * (arXiv:1407.8071): M fully independent bootstrap particle filters
+ * (Algorithm 1) with N_m particles each, on one GPU, and the average of their
+ * estimates (Definition 1).  Every step of the filter runs in this library's
+ * own sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: a pf_status.  Nothing aborts or prints; pf_last_error()
+ *   gives a one-line description of the last failure on a context.
+ * - Ownership: the caller owns every pointer it passes in.  Inputs are read
+ *   (or copied) during the call, or, for asynchronous device work, before the
+ *   work the call enqueues completes on the context's stream; no pointer is
+ *   retained after a call returns unless stated.
+ * - Host/device: an argument named h_* is host memory, d_* is device memory
+ *   of the current CUDA device.  Unprefixed pointers are host memory.
+ * - Streams: device work is enqueued on the context's stream (pf_set_stream;
+ *   default: a stream the context creates).  Calls are asynchronous unless
+ *   they return host data (pf_estimate, pf_get_*), which synchronise.
+ * - Threads: a context is used by one host thread at a time.
+ * - Errors are sticky per context: after PF_ECUDA or PF_ENUMERIC every further
+ *   step returns PF_ESTATE until pf_destroy.
+ * - Sizes: 1 <= M, 1 <= N_m <= 2^24, sum_m N_m * dx * 4 bytes must fit in
+ *   device memory (else PF_ENOMEM).
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit
+ * seed, counter (particle i, observation t, filter m, stream<<24 | block),
+ * and Box-Muller normals from 24-bit uniforms; the stream ids are
+ * 0 truth dynamics, 1 observation noise, 2 prior, 3 particle dynamics,
+ * 4 resampling uniforms, 5 proposal noise, 6 other.
+ */
+#ifndef PF_GB300_PF_H
+#define PF_GB300_PF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__) || defined(__clang__)
+#define PF_API __attribute__((visibility("default")))
+#else
+#define PF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pf_ctx pf_ctx; /* opaque; owns all of its device memory */
+
+typedef enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,       /* invalid argument (NULL where required, size out of range, bad model) */
+    PF_ENOMEM = 2,       /* device or host allocation failed                                      */
+    PF_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed                           */
+    PF_ENUMERIC = 4,     /* a filter's weights were all zero or not finite (pf_last_error names it) */
+    PF_ETIMEOUT = 5,     /* a bounded device-side wait gave up                                    */
+    PF_ESTATE = 6,       /* the context is in an error state, or the call is out of order         */
+    PF_EUNSUPPORTED = 7  /* the model or option is not available in this build                    */
+} pf_status;
+
+typedef enum {
+    PF_MODEL_LINEAR_GAUSSIAN = 0, /* dx in [1,4]; drift -A x; params = A (dx*dx, row-major)           */
+    PF_MODEL_LORENZ63 = 1,        /* dx = 3; Sec. 4.1 eqs. eqDiscreteLorenz-1..3; params = (s, r, b)  */
+    PF_MODEL_FHN_LATTICE = 2      /* dx = 2 J^2, J even in [2,44]; Sec. 5.1 lattice, Rogers-McCulloch
+                                     form; params = (a, b, c1, c2, d, D, stim_amp, stim_steps,
+                                     stim_block); state = v-plane then w-plane, node = row*J + col   */
+} pf_model_kind;
+
+/* The Markov kernel tau_t (Sec. 2.2, eq. eqKernel): steps_per_obs Euler-
+ * Maruyama sub-steps x <- x + dt f(x) + sigma_dyn sqrt(dt) z between two
+ * observations.  params is copied. */
+typedef struct {
+    int32_t kind;          /* pf_model_kind                      */
+    int32_t dx;            /* state dimension                    */
+    int32_t J;             /* lattice side (FHN), else 0         */
+    int32_t steps_per_obs; /* K >= 1                             */
+    const double *params;  /* model constants, see pf_model_kind */
+    int32_t n_params;
+} pf_model;
+
+/* The likelihood g_t^y (Sec. 2.2): y = x[idx] + sigma_obs * noise,
+ * 1 <= dy <= 4096; idx is copied. */
+typedef struct {
+    int32_t dy;
+    const int32_t *idx;
+    double sigma_obs;
+} pf_obs_op;
+
+/* Prior tau_0 = N(x0_mean, sigma0^2 I) (Alg. 1 step 1) and the seed. x0_mean
+ * (dx doubles) is copied. */
+typedef struct {
+    double sigma_dyn;
+    const double *x0_mean;
+    double sigma0;
+    uint64_t seed;
+} pf_noise;
+
+typedef enum {
+    PF_STAT_MEAN = 0,         /* (f, pi_t^N) with f = x[var]: post-resampling particle mean        */
+    PF_STAT_LOG_EVIDENCE = 1, /* log G_t^N, eq. eqGtN (Gaussian constant included)                  */
+    PF_STAT_ESS = 2,          /* (sum w)^2 / sum w^2 before resampling                               */
+    PF_STAT_LOG_Z = 3         /* log sum_i exp(l_i) of this step's log-weights (no constant)         */
+} pf_stat_kind;
+
+/* A statistic request.  kind = PF_STAT_MEAN uses var (0 <= var < dx, or -1 for
+ * all dx variables).  per_filter = 0 asks for the ensemble average over the M
+ * filters (Definition 1; for ESS / LOG_EVIDENCE / LOG_Z the plain average);
+ * per_filter = 1 asks for the M per-filter values. */
+typedef struct {
+    int32_t kind;
+    int32_t var;
+    int32_t per_filter;
+} pf_stat;
+
+/* Optional allocator for context memory.  alloc returns NULL on failure;
+ * free receives the pointer and size alloc returned.  stream is the
+ * context's cudaStream_t. */
+typedef void *(*pf_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*pf_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* --------------------------------------------------------------------- */
+/* Context life cycle                                                    */
+/* --------------------------------------------------------------------- */
+
+/* Sets the allocator used by contexts created afterwards on this process
+ * (NULL, NULL restores cudaMalloc / cudaFree).  Not thread-safe with
+ * concurrent pf_create. */
+PF_API pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *user);
+
+/* Creates M independent bootstrap filters with N[m] particles each for the
+ * model, observation operator and noise given (Sec. 3.1: M independent
+ * instances of Algorithm 1 on one observation record).  Draws the initial
+ * particles (Alg. 1 step 1) on the device.  N has M entries.  On success *out
+ * is a new context (destroy with pf_destroy); on failure *out is NULL.
+ * Errors: PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_EUNSUPPORTED. */
+PF_API pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double dt, const pf_obs_op *obs,
+                    const pf_noise *noise, pf_ctx **out);
+
+/* Frees the context and its device memory.  NULL-safe.  Synchronises the
+ * context's stream first. */
+PF_API void pf_destroy(pf_ctx *ctx);
+
+/* Last error text of a context (or of the last failed pf_create when ctx is
+ * NULL).  Valid until the next call on that context. */
+PF_API const char *pf_last_error(const pf_ctx *ctx);
+
+/* Uses the caller's cudaStream_t for all later work of this context (NULL:
+ * back to the context's own stream).  The stream must outlive its use. */
+PF_API pf_status pf_set_stream(pf_ctx *ctx, void *stream);
+
+/* --------------------------------------------------------------------- */
+/* The hot path: one observation time of all M filters                   */
+/* --------------------------------------------------------------------- */
+
+/* One recursive step of Algorithm 1 for every particle of every filter:
+ * propagation through tau_t and the weights w_t (step 2a), per-filter
+ * normalisation in FP64 with the running G_t^N (eq. eqGtN), systematic
+ * resampling (step 2b), and the per-filter and ensemble means (Definition 1).
+ * h_obs: host FP32 observation y_t, dy values when obs_stride = 0 (one record
+ * shared by every filter, Sec. 4.2), or M rows of obs_stride >= dy floats
+ * (one record per filter).  Asynchronous; h_obs may be reused on return.
+ * Errors: PF_EINVAL, PF_ECUDA, PF_ESTATE. */
+PF_API pf_status pf_step(pf_ctx *ctx, const float *h_obs, int32_t obs_stride);
+
+/* pf_step with the observation already in device memory (d_obs, same layout
+ * as h_obs); d_obs must stay valid until the step completes on the stream. */
+PF_API pf_status pf_step_device(pf_ctx *ctx, const float *d_obs, int32_t obs_stride);
+
+/* The two halves of pf_step, for callers that inspect the weighted particles
+ * between them: pf_propagate is step 2a (propagate + log-weights);
+ * pf_resample is the normalisation, step 2b and the estimates.  A pf_step is
+ * exactly pf_propagate followed by pf_resample.  pf_propagate_device takes the
+ * observation from device memory like pf_step_device.  Out-of-order calls return
+ * PF_ESTATE. */
+PF_API pf_status pf_propagate(pf_ctx *ctx, const float *h_obs, int32_t obs_stride);
+PF_API pf_status pf_propagate_device(pf_ctx *ctx, const float *d_obs, int32_t obs_stride);
+PF_API pf_status pf_resample(pf_ctx *ctx);
+
+/* Reads a statistic of the last completed step (synchronises).  out receives
+ * 1 value (ensemble), dx values (MEAN with var = -1), M values (per_filter),
+ * or M*dx values (MEAN, var = -1, per_filter; row-major [m][var]).
+ * Errors: PF_EINVAL, PF_ECUDA, PF_ENUMERIC (a filter degenerated), PF_ESTATE
+ * (no step completed yet). */
+PF_API pf_status pf_estimate(pf_ctx *ctx, const pf_stat *stat, double *out);
+
+/* --------------------------------------------------------------------- */
+/* Inspection and state transfer (synchronous; for tests and checkpoints) */
+/* --------------------------------------------------------------------- */
+
+/* Number of completed observation steps t (0 after pf_create). */
+PF_API pf_status pf_get_time(const pf_ctx *ctx, int32_t *t);
+
+/* Copies the current particles to/from host FP32 memory laid out as
+ * [sum_m N_m][dx], filter after filter, particle-major.  After pf_propagate
+ * they are the weighted particles x-bar_t; after pf_resample / pf_step the
+ * resampled x_t.  pf_set_state also sets the step counter to t (so the next
+ * step draws the random numbers of observation t + 1): a checkpoint resumes
+ * bit-identically. */
+PF_API pf_status pf_get_state(pf_ctx *ctx, float *h_x);
+PF_API pf_status pf_set_state(pf_ctx *ctx, const float *h_x, int32_t t);
+
+/* FP32 log-weights l_i = log g_t(x-bar_i) without the Gaussian constant, after
+ * pf_propagate (sum N_m values).  pf_set_logw replaces them (before
+ * pf_resample). */
+PF_API pf_status pf_get_logw(pf_ctx *ctx, float *h_l);
+PF_API pf_status pf_set_logw(pf_ctx *ctx, const float *h_l);
+
+/* Filter-local ancestor indices a_i of the last resampling (sum N_m int32). */
+PF_API pf_status pf_get_ancestors(pf_ctx *ctx, int32_t *h_a);
+
+/* --------------------------------------------------------------------- */
+/* Stateless building blocks (device pointers; enqueued on `stream`)      */
+/* --------------------------------------------------------------------- */
+
+/* Philox4x32-10 of n counters: d_ctr and d_out are n x 4 uint32. */
+PF_API pf_status pf_rng_philox(int64_t n, const uint32_t *d_ctr, uint32_t key0, uint32_t key1, uint32_t *d_out,
+                        void *stream);
+
+/* Four FP32 Box-Muller normals per counter (key = seed): d_z is n x 4. */
+PF_API pf_status pf_rng_normals(int64_t n, const uint32_t *d_ctr, uint64_t seed, float *d_z, void *stream);
+
+/* Bytes of device scratch pf_systematic_resample needs for M filters with
+ * `total` particles in all. */
+PF_API size_t pf_systematic_scratch_bytes(int32_t M, int64_t total);
+
+/* Systematic resampling of M filters (Algorithm 1 step 2b, systematic form)
+ * from unnormalised FP64 weights w in [0, 1] with at least one weight > 0
+ * per filter and one uniform u_m in [0, 1) per filter.  Definition (exact,
+ * reproducible bit for bit): L = ceil(log2 N_m), q_k = floor(w_k 2^(52-L)),
+ * C_k = q_0 + ... + q_k, t_i = (i + u_m) * (C_{N-1} / N_m) with each
+ * operation rounded to nearest, a_i = min{k : C_k > t_i}, or the last k with
+ * q_k > 0 when no C_k exceeds t_i.
+ * h_N: the M particle counts (host); the filters' weights sit contiguously in
+ * d_w, filter after filter (sum N_m doubles), and each filter's largest
+ * weight should be 1 so that its quantised total is positive.
+ * d_u: M doubles.  d_anc receives sum N_m filter-local indices.
+ * d_scratch: caller-owned device scratch of at least
+ * pf_systematic_scratch_bytes(M, sum N_m) bytes, 256-byte aligned; it may be
+ * reused once the call's work completes on `stream`.  The call synchronises
+ * `stream` once to upload its launch plan, then enqueues three kernels.
+ * Errors: PF_EINVAL, PF_ECUDA. */
+PF_API pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_w, const double *d_u,
+                                 int32_t *d_anc, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* --------------------------------------------------------------------- */
+/* Synthetic records                                                      */
+/* --------------------------------------------------------------------- */
+
+/* Simulates the hidden state and a T-step observation record on the device
+ * in FP64 with the stream-0 (dynamics) and stream-1 (observation noise)
+ * random numbers of `record` (counter word 2).  init_random = 0 starts at
+ * x0_mean, 1 draws X_0 from the prior with stream 6.  h_x: (T+1) x dx
+ * doubles (X_0 .. X_T at observation times); h_y: T x dy floats (may be
+ * NULL).  Synchronous.  Errors: PF_EINVAL, PF_ENOMEM, PF_ECUDA. */
+PF_API pf_status pf_simulate(const pf_model *model, double dt, const pf_obs_op *obs, const pf_noise *noise, int32_t T,
+                      int32_t record, int32_t init_random, double *h_x, float *h_y);
+
+/* Library version string. */
+PF_API const char *pf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PF_GB300_PF_H */

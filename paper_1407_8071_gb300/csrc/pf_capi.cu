@@ -1,0 +1,732 @@
+// pf_capi.cu -- the C ABI of include/pf.h: context life cycle, the per-step
+// launch sequence (captured once per buffer parity into a CUDA graph), and
+// the stateless building blocks.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pf.h"
+#include "pf_internal.h"
+
+using namespace pf;
+
+struct pf_ctx {
+    Ctx c;
+};
+
+namespace {
+
+std::mutex g_mu;
+pf_alloc_fn g_alloc = nullptr;
+pf_free_fn g_free = nullptr;
+void *g_alloc_user = nullptr;
+thread_local std::string g_create_error;
+
+pf_status fail(Ctx &c, pf_status st, const std::string &msg)
+{
+    c.last_error = msg;
+    return st;
+}
+
+pf_status cuda_fail(Ctx &c, cudaError_t e, const char *where)
+{
+    c.last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    c.fatal = PF_ECUDA;
+    return PF_ECUDA;
+}
+
+void *ctx_alloc(Ctx &c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c.alloc) {
+        p = c.alloc(bytes, (void *)c.stream, c.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c.allocations.emplace_back(p, bytes);
+    return p;
+}
+
+void ctx_free_all(Ctx &c)
+{
+    for (auto &a : c.allocations) {
+        if (c.free_fn) c.free_fn(a.first, a.second, (void *)c.stream, c.alloc_user);
+        else cudaFree(a.first);
+    }
+    c.allocations.clear();
+}
+
+template <typename T>
+bool alloc_n(Ctx &c, T *&p, size_t n)
+{
+    p = static_cast<T *>(ctx_alloc(c, n * sizeof(T)));
+    return p != nullptr;
+}
+
+// obs layout: 0 = one shared row of dy floats; 1 = M rows of dy floats.
+int obs_mode(int32_t stride) { return stride == 0 ? 0 : 1; }
+
+pf_status validate_step(Ctx &c, const float *obs, int32_t stride)
+{
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (!obs) return fail(c, PF_EINVAL, "obs is NULL");
+    if (stride != 0 && stride < c.mp.dy) return fail(c, PF_EINVAL, "obs_stride must be 0 or >= dy");
+    return PF_OK;
+}
+
+// Copies y_t into the context's observation buffer.  Host observations go
+// through one of two pinned staging slots (so the caller's buffer is free on
+// return even when it is itself pinned); a slot is refilled only after its
+// previous copy has completed.
+cudaError_t stage_obs(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind)
+{
+    const size_t row = (size_t)c.mp.dy * sizeof(float);
+    const size_t rows = stride == 0 ? 1 : (size_t)c.M;
+    if (kind == cudaMemcpyDeviceToDevice) {
+        if (stride == 0) return cudaMemcpyAsync(c.d_obs, obs, row, kind, c.stream);
+        return cudaMemcpy2DAsync(c.d_obs, row, obs, (size_t)stride * sizeof(float), row, rows, kind, c.stream);
+    }
+    const int s = c.stage_slot;
+    cudaError_t e = cudaSuccess;
+    if (c.stage_used[s]) e = cudaEventSynchronize(c.stage_ev[s]);
+    if (e != cudaSuccess) return e;
+    for (size_t r = 0; r < rows; ++r)
+        std::memcpy(c.h_stage[s] + r * c.mp.dy, obs + r * (size_t)(stride ? stride : 0), row);
+    e = cudaMemcpyAsync(c.d_obs, c.h_stage[s], rows * row, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c.stage_ev[s], c.stream);
+    c.stage_used[s] = true;
+    c.stage_slot ^= 1;
+    return e;
+}
+
+int32_t kernel_stride(const Ctx &c, int mode) { return mode == 0 ? 0 : c.mp.dy; }
+
+cudaError_t enqueue_step(Ctx &c, int mode)
+{
+    const int nxt = c.cur ^ 1;
+    cudaError_t e = launch_propagate(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[c.cur], c.stream);
+    if (e != cudaSuccess) return e;
+    return launch_resample(c, c.x[c.cur], c.x[nxt], c.stream);
+}
+
+pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind)
+{
+    pf_status st = validate_step(c, obs, stride);
+    if (st != PF_OK) return st;
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_step called between pf_propagate and pf_resample");
+    cudaSetDevice(c.device);
+    cudaError_t e = stage_obs(c, obs, stride, kind);
+    if (e != cudaSuccess) return cuda_fail(c, e, "observation copy");
+    const int mode = obs_mode(stride);
+    const int par = c.cur;
+    if (!c.graph[par] || c.graph_mode[par] != mode) {
+        if (c.graph[par]) {
+            cudaGraphExecDestroy(c.graph[par]);
+            c.graph[par] = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph capture begin");
+        const cudaError_t le = enqueue_step(c, mode);
+        e = cudaStreamEndCapture(c.stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(c, le, "step launch (capture)");
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
+        e = cudaGraphInstantiate(&c.graph[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        c.graph_mode[par] = mode;
+    }
+    e = cudaGraphLaunch(c.graph[par], c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c.cur ^= 1;
+    c.t += 1;
+    c.steps_done = true;
+    return PF_OK;
+}
+
+pf_status sync(Ctx &c, const char *where)
+{
+    cudaSetDevice(c.device);
+    const cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return PF_OK;
+}
+
+pf_status check_device_flags(Ctx &c)
+{
+    int32_t err[2];
+    const cudaError_t e = cudaMemcpy(err, c.err, sizeof(err), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "error word read");
+    if (err[0] & kErrDegenerate) {
+        c.fatal = PF_ENUMERIC;
+        return fail(c, PF_ENUMERIC, "filter " + std::to_string(err[1]) +
+                                        " had no finite positive weight (all log-weights -inf or NaN)");
+    }
+    return PF_OK;
+}
+
+bool model_ok(const pf_model *m, std::string &why)
+{
+    if (!m) { why = "model is NULL"; return false; }
+    if (m->steps_per_obs < 1) { why = "steps_per_obs must be >= 1"; return false; }
+    switch (m->kind) {
+    case PF_MODEL_LINEAR_GAUSSIAN:
+        if (m->dx < 1 || m->dx > kMaxLgDim) { why = "linear-Gaussian dx must be in [1, 4]"; return false; }
+        if (!m->params || m->n_params != m->dx * m->dx) { why = "linear-Gaussian params must hold dx*dx values"; return false; }
+        return true;
+    case PF_MODEL_LORENZ63:
+        if (m->dx != 3) { why = "Lorenz 63 has dx = 3"; return false; }
+        if (!m->params || m->n_params != 3) { why = "Lorenz 63 params are (s, r, b)"; return false; }
+        return true;
+    case PF_MODEL_FHN_LATTICE:
+        if (m->J < 2 || m->J > 44 || (m->J & 1)) { why = "lattice side J must be even, 2..44"; return false; }
+        if (m->dx != 2 * m->J * m->J) { why = "lattice dx must be 2 J^2"; return false; }
+        if (!m->params || m->n_params != 9) { why = "lattice params are (a, b, c1, c2, d, D, amp, steps, block)"; return false; }
+        return true;
+    default:
+        why = "unknown model kind";
+        return false;
+    }
+}
+
+bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const pf_noise *noise, ModelParams &mp,
+                 std::string &why)
+{
+    if (!model_ok(model, why)) return false;
+    if (!(dt > 0.0) || !std::isfinite(dt)) { why = "dt must be positive"; return false; }
+    if (!obs || obs->dy < 1 || obs->dy > 4096 || !obs->idx) { why = "obs op needs 1 <= dy <= 4096 and idx"; return false; }
+    if (!(obs->sigma_obs > 0.0)) { why = "sigma_obs must be positive"; return false; }
+    if (!noise || !noise->x0_mean) { why = "noise needs x0_mean"; return false; }
+    if (!(noise->sigma_dyn >= 0.0) || !(noise->sigma0 >= 0.0)) { why = "noise scales must be >= 0"; return false; }
+    if (model->kind != PF_MODEL_FHN_LATTICE && obs->dy > kMaxObsSmall) { why = "small models observe at most 8 components"; return false; }
+    for (int j = 0; j < obs->dy; ++j) {
+        const int32_t i = obs->idx[j];
+        const int32_t lim = model->kind == PF_MODEL_FHN_LATTICE ? model->J * model->J : model->dx;
+        if (i < 0 || i >= lim) { why = "observation index out of range (lattice: v-plane nodes only)"; return false; }
+    }
+    mp = ModelParams{};
+    mp.kind = model->kind;
+    mp.dx = model->dx;
+    mp.J = model->J;
+    mp.K = model->steps_per_obs;
+    mp.dt = dt;
+    mp.sigma_dyn = noise->sigma_dyn;
+    mp.sigma0 = noise->sigma0;
+    mp.sigma_obs = obs->sigma_obs;
+    for (int i = 0; i < model->n_params && i < 16; ++i) mp.p[i] = model->params[i];
+    mp.dy = obs->dy;
+    for (int j = 0; j < obs->dy && j < kMaxObsSmall; ++j) mp.obs_small[j] = obs->idx[j];
+    if (model->kind != PF_MODEL_FHN_LATTICE)
+        for (int v = 0; v < model->dx; ++v) mp.x0_small[v] = noise->x0_mean[v];
+    return true;
+}
+
+// Tiles of at most kTile particles, never spanning two filters.
+void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std::vector<FilterDesc> &filt,
+                std::vector<int64_t> &off)
+{
+    const int32_t M = (int32_t)N.size();
+    off.assign(M + 1, 0);
+    for (int m = 0; m < M; ++m) off[m + 1] = off[m] + N[m];
+    tiles.clear();
+    filt.resize(M);
+    for (int m = 0; m < M; ++m) {
+        FilterDesc fd{};
+        fd.off = off[m];
+        fd.N = N[m];
+        fd.tile_begin = (int32_t)tiles.size();
+        fd.shift = 52 - ceil_log2_host(N[m]);
+        for (int32_t s = 0; s < N[m]; s += kTile) {
+            TileDesc td{};
+            td.m = m;
+            td.lstart = s;
+            td.len = std::min(kTile, N[m] - s);
+            td.gstart = off[m] + s;
+            tiles.push_back(td);
+        }
+        fd.tile_count = (int32_t)tiles.size() - fd.tile_begin;
+        filt[m] = fd;
+    }
+}
+
+}  // namespace
+
+namespace pf {
+int ceil_log2_host(int64_t n)
+{
+    int L = 0;
+    while (((int64_t)1 << L) < n) ++L;
+    return L;
+}
+}  // namespace pf
+
+extern "C" {
+
+const char *pf_version(void) { return "paper_1407_8071_gb300 0.1 (sm_103a)"; }
+
+pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return PF_EINVAL;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = user;
+    return PF_OK;
+}
+
+pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double dt, const pf_obs_op *obs,
+                    const pf_noise *noise, pf_ctx **out)
+{
+    if (!out) return PF_EINVAL;
+    *out = nullptr;
+    std::string why;
+    ModelParams mp;
+    if (!fill_params(model, dt, obs, noise, mp, why)) {
+        g_create_error = why;
+        return PF_EINVAL;
+    }
+    if (M < 1 || !N) {
+        g_create_error = "M must be >= 1 and N non-NULL";
+        return PF_EINVAL;
+    }
+    for (int m = 0; m < M; ++m)
+        if (N[m] < 1 || N[m] > (1 << 24)) {
+            g_create_error = "every N[m] must be in [1, 2^24]";
+            return PF_EINVAL;
+        }
+    pf_ctx *h = new (std::nothrow) pf_ctx();
+    if (!h) return PF_ENOMEM;
+    Ctx &c = h->c;
+    c.mp = mp;
+    c.key = make_key(noise->seed);
+    c.M = M;
+    c.N.assign(N, N + M);
+    cudaGetDevice(&c.device);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        c.alloc = g_alloc;
+        c.free_fn = g_free;
+        c.alloc_user = g_alloc_user;
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("stream create: ") + cudaGetErrorString(e);
+        delete h;
+        return PF_ECUDA;
+    }
+    c.stream = c.own_stream;
+
+    std::vector<TileDesc> tiles;
+    std::vector<FilterDesc> filt;
+    make_tiles(c.N, tiles, filt, c.off);
+    c.P = c.off[M];
+    c.n_tiles = (int32_t)tiles.size();
+    const int dx = mp.dx;
+    const int64_t P = c.P;
+    bool ok = alloc_n(c, c.tiles, tiles.size()) && alloc_n(c, c.filt, filt.size()) &&
+              alloc_n(c, c.x[0], (size_t)P * dx) && alloc_n(c, c.x[1], (size_t)P * dx) && alloc_n(c, c.logw, P) &&
+              alloc_n(c, c.tile_max, c.n_tiles) && alloc_n(c, c.tile_sums, (size_t)c.n_tiles * kTsCount) &&
+              alloc_n(c, c.fstats, (size_t)M * kFsCount) && alloc_n(c, c.C, P) && alloc_n(c, c.B, P) &&
+              alloc_n(c, c.anc, P) && alloc_n(c, c.est, (size_t)M * dx) && alloc_n(c, c.ens, dx) &&
+              alloc_n(c, c.d_obs, (size_t)M * mp.dy) && alloc_n(c, c.d_t, 1) && alloc_n(c, c.err, 2) &&
+              alloc_n(c, c.obs_idx, mp.dy) && alloc_n(c, c.x0, dx);
+    if (ok && mp.kind == PF_MODEL_FHN_LATTICE) ok = alloc_n(c, c.pfilt, P) && alloc_n(c, c.obs_slot, mp.J * mp.J);
+    else if (ok) ok = alloc_n(c, c.tile_est, (size_t)c.n_tiles * dx);
+    if (!ok) {
+        g_create_error = "device allocation failed";
+        ctx_free_all(c);
+        cudaStreamDestroy(c.own_stream);
+        delete h;
+        return PF_ENOMEM;
+    }
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok = cudaMallocHost(&c.h_stage[k], (size_t)M * mp.dy * sizeof(float)) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c.stage_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        g_create_error = "pinned staging allocation failed";
+        for (int k = 0; k < 2; ++k) {
+            if (c.h_stage[k]) cudaFreeHost(c.h_stage[k]);
+            if (c.stage_ev[k]) cudaEventDestroy(c.stage_ev[k]);
+        }
+        ctx_free_all(c);
+        cudaStreamDestroy(c.own_stream);
+        delete h;
+        return PF_ENOMEM;
+    }
+    std::vector<int32_t> pf_host;
+    std::vector<int32_t> slot;
+    const int32_t zero = 0, err_init[2] = {0, -1};
+    e = cudaMemcpyAsync(c.tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.filt, filt.data(), filt.size() * sizeof(FilterDesc), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.obs_idx, obs->idx, mp.dy * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.x0, noise->x0_mean, dx * sizeof(double), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_t, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.fstats, 0, (size_t)M * kFsCount * sizeof(double), c.stream);
+    if (e == cudaSuccess && mp.kind == PF_MODEL_FHN_LATTICE) {
+        pf_host.resize(P);
+        for (int m = 0; m < M; ++m) std::fill(pf_host.begin() + c.off[m], pf_host.begin() + c.off[m + 1], m);
+        slot.assign(mp.J * mp.J, -1);
+        for (int j = 0; j < mp.dy; ++j) slot[obs->idx[j]] = j;
+        e = cudaMemcpyAsync(c.pfilt, pf_host.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c.obs_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+    }
+    if (e == cudaSuccess) e = launch_init(c, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);  // host staging vectors go out of scope
+    if (e != cudaSuccess) {
+        g_create_error = std::string("create: ") + cudaGetErrorString(e);
+        for (int k = 0; k < 2; ++k) {
+            cudaFreeHost(c.h_stage[k]);
+            cudaEventDestroy(c.stage_ev[k]);
+        }
+        ctx_free_all(c);
+        cudaStreamDestroy(c.own_stream);
+        delete h;
+        return PF_ECUDA;
+    }
+    *out = h;
+    return PF_OK;
+}
+
+void pf_destroy(pf_ctx *h)
+{
+    if (!h) return;
+    Ctx &c = h->c;
+    cudaSetDevice(c.device);
+    cudaStreamSynchronize(c.stream);
+    for (auto &g : c.graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (int k = 0; k < 2; ++k) {
+        if (c.h_stage[k]) cudaFreeHost(c.h_stage[k]);
+        if (c.stage_ev[k]) cudaEventDestroy(c.stage_ev[k]);
+    }
+    ctx_free_all(c);
+    if (c.own_stream) cudaStreamDestroy(c.own_stream);
+    delete h;
+}
+
+const char *pf_last_error(const pf_ctx *h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->c.last_error.c_str();
+}
+
+pf_status pf_set_stream(pf_ctx *h, void *stream)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c.own_stream;
+    if (s != c.stream) {
+        cudaStreamSynchronize(c.stream);
+        c.stream = s;
+    }
+    return PF_OK;
+}
+
+pf_status pf_step(pf_ctx *h, const float *h_obs, int32_t obs_stride)
+{
+    if (!h) return PF_EINVAL;
+    return run_step(h->c, h_obs, obs_stride, cudaMemcpyHostToDevice);
+}
+
+pf_status pf_step_device(pf_ctx *h, const float *d_obs, int32_t obs_stride)
+{
+    if (!h) return PF_EINVAL;
+    return run_step(h->c, d_obs, obs_stride, cudaMemcpyDeviceToDevice);
+}
+
+static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride, cudaMemcpyKind kind)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    pf_status st = validate_step(c, obs, obs_stride);
+    if (st != PF_OK) return st;
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_propagate called twice without pf_resample");
+    cudaSetDevice(c.device);
+    cudaError_t e = stage_obs(c, obs, obs_stride, kind);
+    if (e == cudaSuccess)
+        e = launch_propagate(c, c.d_obs, kernel_stride(c, obs_mode(obs_stride)), c.x[c.cur], c.x[c.cur], c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "propagate");
+    c.phase = 1;
+    return PF_OK;
+}
+
+pf_status pf_propagate(pf_ctx *h, const float *h_obs, int32_t obs_stride)
+{
+    return propagate_impl(h, h_obs, obs_stride, cudaMemcpyHostToDevice);
+}
+
+pf_status pf_propagate_device(pf_ctx *h, const float *d_obs, int32_t obs_stride)
+{
+    return propagate_impl(h, d_obs, obs_stride, cudaMemcpyDeviceToDevice);
+}
+
+pf_status pf_resample(pf_ctx *h)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 1) return fail(c, PF_ESTATE, "pf_resample needs a preceding pf_propagate");
+    cudaSetDevice(c.device);
+    const cudaError_t e = launch_resample(c, c.x[c.cur], c.x[c.cur ^ 1], c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resample");
+    c.cur ^= 1;
+    c.t += 1;
+    c.phase = 0;
+    c.steps_done = true;
+    return PF_OK;
+}
+
+pf_status pf_estimate(pf_ctx *h, const pf_stat *stat, double *out)
+{
+    if (!h || !stat || !out) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal == PF_ECUDA) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (!c.steps_done) return fail(c, PF_ESTATE, "no step has completed");
+    pf_status st = sync(c, "estimate");
+    if (st != PF_OK) return st;
+    st = check_device_flags(c);
+    if (st != PF_OK) return st;
+    const int dx = c.mp.dx, M = c.M;
+    cudaError_t e = cudaSuccess;
+    if (stat->kind == PF_STAT_MEAN) {
+        if (stat->var < -1 || stat->var >= dx) return fail(c, PF_EINVAL, "var out of range");
+        if (stat->per_filter) {
+            std::vector<double> est((size_t)M * dx);
+            e = cudaMemcpy(est.data(), c.est, est.size() * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(c, e, "estimate copy");
+            if (stat->var < 0) std::memcpy(out, est.data(), est.size() * sizeof(double));
+            else for (int m = 0; m < M; ++m) out[m] = est[(size_t)m * dx + stat->var];
+        } else if (stat->var < 0) {
+            e = cudaMemcpy(out, c.ens, dx * sizeof(double), cudaMemcpyDeviceToHost);
+        } else {
+            e = cudaMemcpy(out, c.ens + stat->var, sizeof(double), cudaMemcpyDeviceToHost);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "estimate copy");
+        return PF_OK;
+    }
+    int slot;
+    switch (stat->kind) {
+    case PF_STAT_LOG_EVIDENCE: slot = kFsLogG; break;
+    case PF_STAT_ESS: slot = kFsEss; break;
+    case PF_STAT_LOG_Z: slot = kFsLogZ; break;
+    default: return fail(c, PF_EINVAL, "unknown statistic");
+    }
+    std::vector<double> fs((size_t)M * kFsCount);
+    e = cudaMemcpy(fs.data(), c.fstats, fs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "statistic copy");
+    if (stat->per_filter) {
+        for (int m = 0; m < M; ++m) out[m] = fs[(size_t)m * kFsCount + slot];
+    } else {
+        double s = 0.0;
+        for (int m = 0; m < M; ++m) s += fs[(size_t)m * kFsCount + slot];
+        out[0] = s / M;
+    }
+    return PF_OK;
+}
+
+pf_status pf_get_time(const pf_ctx *h, int32_t *t)
+{
+    if (!h || !t) return PF_EINVAL;
+    *t = h->c.t;
+    return PF_OK;
+}
+
+pf_status pf_get_state(pf_ctx *h, float *h_x)
+{
+    if (!h || !h_x) return PF_EINVAL;
+    Ctx &c = h->c;
+    pf_status st = sync(c, "get_state");
+    if (st != PF_OK) return st;
+    const int dx = c.mp.dx;
+    const size_t n = (size_t)c.P * dx;
+    if (c.mp.kind == PF_MODEL_FHN_LATTICE) {
+        const cudaError_t e = cudaMemcpy(h_x, c.x[c.cur], n * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
+        return PF_OK;
+    }
+    std::vector<float> soa(n);
+    const cudaError_t e = cudaMemcpy(soa.data(), c.x[c.cur], n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
+    for (int64_t p = 0; p < c.P; ++p)
+        for (int v = 0; v < dx; ++v) h_x[p * dx + v] = soa[(size_t)v * c.P + p];
+    return PF_OK;
+}
+
+pf_status pf_set_state(pf_ctx *h, const float *h_x, int32_t t)
+{
+    if (!h || !h_x || t < 0) return PF_EINVAL;
+    Ctx &c = h->c;
+    pf_status st = sync(c, "set_state");
+    if (st != PF_OK) return st;
+    const int dx = c.mp.dx;
+    const size_t n = (size_t)c.P * dx;
+    cudaError_t e;
+    if (c.mp.kind == PF_MODEL_FHN_LATTICE) {
+        e = cudaMemcpy(c.x[c.cur], h_x, n * sizeof(float), cudaMemcpyHostToDevice);
+    } else {
+        std::vector<float> soa(n);
+        for (int64_t p = 0; p < c.P; ++p)
+            for (int v = 0; v < dx; ++v) soa[(size_t)v * c.P + p] = h_x[p * dx + v];
+        e = cudaMemcpy(c.x[c.cur], soa.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_t, &t, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state copy");
+    c.t = t;
+    c.phase = 0;
+    return PF_OK;
+}
+
+pf_status pf_get_logw(pf_ctx *h, float *h_l)
+{
+    if (!h || !h_l) return PF_EINVAL;
+    Ctx &c = h->c;
+    pf_status st = sync(c, "get_logw");
+    if (st != PF_OK) return st;
+    const cudaError_t e = cudaMemcpy(h_l, c.logw, c.P * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "get_logw copy");
+}
+
+pf_status pf_set_logw(pf_ctx *h, const float *h_l)
+{
+    if (!h || !h_l) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.phase != 1) return fail(c, PF_ESTATE, "pf_set_logw needs a preceding pf_propagate");
+    pf_status st = sync(c, "set_logw");
+    if (st != PF_OK) return st;
+    const cudaError_t e = cudaMemcpy(c.logw, h_l, c.P * sizeof(float), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "set_logw copy");
+}
+
+pf_status pf_get_ancestors(pf_ctx *h, int32_t *h_a)
+{
+    if (!h || !h_a) return PF_EINVAL;
+    Ctx &c = h->c;
+    pf_status st = sync(c, "get_ancestors");
+    if (st != PF_OK) return st;
+    const cudaError_t e = cudaMemcpy(h_a, c.anc, c.P * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "get_ancestors copy");
+}
+
+pf_status pf_rng_philox(int64_t n, const uint32_t *d_ctr, uint32_t key0, uint32_t key1, uint32_t *d_out, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return PF_EINVAL;
+    return launch_rng_philox(n, d_ctr, key0, key1, d_out, (cudaStream_t)stream) == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+pf_status pf_rng_normals(int64_t n, const uint32_t *d_ctr, uint64_t seed, float *d_z, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_ctr || !d_z))) return PF_EINVAL;
+    return launch_rng_normals(n, d_ctr, seed, d_z, (cudaStream_t)stream) == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+// Scratch layout of the stateless resampler (each piece 256-byte aligned).
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int64_t max_tiles(int32_t M, int64_t total) { return (int64_t)M + total / kTile + 1; }
+
+size_t pf_systematic_scratch_bytes(int32_t M, int64_t total)
+{
+    if (M < 1 || total < 0) return 0;
+    const int64_t nt = max_tiles(M, total);
+    return align256(nt * sizeof(TileDesc)) + align256((size_t)M * sizeof(FilterDesc)) +
+           align256(nt * sizeof(float)) + align256(nt * kTsCount * sizeof(double)) +
+           align256((size_t)M * kFsCount * sizeof(double)) + align256(total * sizeof(double)) +
+           align256(total * sizeof(int32_t)) + align256(2 * sizeof(int32_t));
+}
+
+pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_w, const double *d_u, int32_t *d_anc,
+                                 void *d_scratch, size_t scratch_bytes, void *stream)
+{
+    if (M < 1 || !h_N || !d_w || !d_u || !d_anc || !d_scratch) return PF_EINVAL;
+    if (((uintptr_t)d_scratch & 255) != 0) return PF_EINVAL;
+    std::vector<int32_t> N(h_N, h_N + M);
+    for (int m = 0; m < M; ++m)
+        if (N[m] < 1 || N[m] > (1 << 24)) return PF_EINVAL;
+    std::vector<TileDesc> tiles;
+    std::vector<FilterDesc> filt;
+    std::vector<int64_t> off;
+    make_tiles(N, tiles, filt, off);
+    const int64_t total = off[M];
+    if (scratch_bytes < pf_systematic_scratch_bytes(M, total)) return PF_EINVAL;
+    const int64_t nt = max_tiles(M, total);
+    char *p = static_cast<char *>(d_scratch);
+    auto take = [&p](size_t b) { char *r = p; p += align256(b); return r; };
+    ResampleArgs a{};
+    TileDesc *d_tiles = reinterpret_cast<TileDesc *>(take(nt * sizeof(TileDesc)));
+    FilterDesc *d_filt = reinterpret_cast<FilterDesc *>(take((size_t)M * sizeof(FilterDesc)));
+    a.tiles = d_tiles;
+    a.filt = d_filt;
+    a.tile_max = reinterpret_cast<float *>(take(nt * sizeof(float)));
+    a.tile_sums = reinterpret_cast<double *>(take(nt * kTsCount * sizeof(double)));
+    a.fstats = reinterpret_cast<double *>(take((size_t)M * kFsCount * sizeof(double)));
+    a.C = reinterpret_cast<double *>(take(total * sizeof(double)));
+    a.B = reinterpret_cast<int32_t *>(take(total * sizeof(int32_t)));
+    a.err = reinterpret_cast<int32_t *>(take(2 * sizeof(int32_t)));
+    a.w_direct = d_w;
+    a.u_direct = d_u;
+    a.anc = d_anc;
+    a.d_t = nullptr;
+    a.logw = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_filt, filt.data(), filt.size() * sizeof(FilterDesc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 2 * sizeof(int32_t), s);
+    // pageable copies are staged before the call returns, but keep the host
+    // vectors alive until the stream has consumed them
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = launch_systematic(M, (int32_t)tiles.size(), a, s);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+pf_status pf_simulate(const pf_model *model, double dt, const pf_obs_op *obs, const pf_noise *noise, int32_t T,
+                      int32_t record, int32_t init_random, double *h_x, float *h_y)
+{
+    std::string why;
+    ModelParams mp;
+    if (!fill_params(model, dt, obs, noise, mp, why)) {
+        g_create_error = why;
+        return PF_EINVAL;
+    }
+    if (T < 0 || !h_x) return PF_EINVAL;
+    const size_t nx = (size_t)(T + 1) * mp.dx, ny = (size_t)T * mp.dy;
+    double *d_x = nullptr, *d_x0 = nullptr;
+    float *d_y = nullptr;
+    int32_t *d_idx = nullptr;
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&d_x, nx * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d_x0, mp.dx * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&d_y, (ny ? ny : 1) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d_idx, mp.dy * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_x0, noise->x0_mean, mp.dx * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_idx, obs->idx, mp.dy * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_simulate(mp, d_x0, d_idx, make_key(noise->seed), T, record, init_random, d_x, d_y, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_x, d_x, nx * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && h_y && ny) e = cudaMemcpyAsync(h_y, d_y, ny * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_x);
+    cudaFree(d_x0);
+    cudaFree(d_y);
+    cudaFree(d_idx);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("simulate: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA;
+    }
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// pf_device.cuh -- device building blocks of the GB300 ensemble particle filter:
+// the counter-based generator, Box-Muller normals, and the state-space models
+// of arXiv:1407.8071 (Sec. 4.1 Lorenz 63; Sec. 5.1 FitzHugh-Nagumo lattice in
+// the Rogers-McCulloch form; a linear-Gaussian model whose exact filter is the
+// Kalman filter).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pf {
+
+enum : uint32_t {
+    kStreamTruth = 0u,
+    kStreamObs = 1u,
+    kStreamInit = 2u,
+    kStreamDyn = 3u,
+    kStreamResample = 4u,
+    kStreamProposal = 5u,
+    kStreamMisc = 6u,
+};
+
+enum ModelKind : int32_t { kLinearGaussian = 0, kLorenz63 = 1, kFhnLattice = 2 };
+
+constexpr int kMaxLgDim = 4;
+constexpr int kMaxObsSmall = 8;  // observation indices passed by value for the small models
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the 4x32
+// Philox bijection with the published multipliers; the key advances by the
+// Weyl increments (0.32 fixed point of the golden ratio's fraction and of
+// sqrt(3) - 1) before every round but the first.  One 32x32->64 multiply per
+// product (mul.lo + mul.hi fold into one wide IMAD).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+#else
+        const uint64_t p0 = (uint64_t)M0 * c.x, p1 = (uint64_t)M1 * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += W0;
+        k1 += W1;
+    }
+    return c;
+}
+
+struct Key {
+    uint32_t k0, k1;
+};
+
+__host__ __device__ __forceinline__ Key make_key(uint64_t seed)
+{
+    return Key{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+}
+
+// Box & Muller (1958) on two 32-bit words.  u1 = ((a >> 8) + 1) 2^-24 in (0, 1]
+// and u2 = (b >> 8) 2^-24 in [0, 1) are exact in binary32, so the only
+// rounding is that of log, sqrt and sin/cos (sincospi takes 2 u2 exactly).
+template <typename Real>
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, Real &z0, Real &z1);
+
+template <>
+__device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1)
+{
+    const float u1 = __uint2float_rn((a >> 8) + 1u) * 0x1p-24f;
+    const float u2 = __uint2float_rn(b >> 8) * 0x1p-24f;
+    const float R = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = R * c;
+    z1 = R * s;
+}
+
+template <>
+__device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, double &z0, double &z1)
+{
+    const double u1 = ((double)(a >> 8) + 1.0) * 0x1p-24;
+    const double u2 = (double)(b >> 8) * 0x1p-24;
+    const double R = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    z0 = R * c;
+    z1 = R * s;
+}
+
+// Normals (4 per block) of counter (c0, c1, c2, stream<<24 | block).
+template <typename Real>
+__device__ __forceinline__ void normals4(Key key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t stream,
+                                         uint32_t block, Real z[4])
+{
+    const uint4 r = philox4x32_10(make_uint4(c0, c1, c2, (stream << 24) | block), key.k0, key.k1);
+    box_muller<Real>(r.x, r.y, z[0], z[1]);
+    box_muller<Real>(r.z, r.w, z[2], z[3]);
+}
+
+// Resampling uniform of filter m at observation t: word 0 of Philox at
+// (0, t, m, RESAMPLE<<24) times 2^-32 (exact in binary64).
+__device__ __forceinline__ double resample_uniform(Key key, int32_t m, int32_t t)
+{
+    const uint4 r = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)m, kStreamResample << 24), key.k0, key.k1);
+    return (double)r.x * 0x1p-32;
+}
+
+// ---------------------------------------------------------------------------
+// Model parameters passed by value to the kernels.
+// ---------------------------------------------------------------------------
+struct ModelParams {
+    int32_t kind;
+    int32_t dx;
+    int32_t J;
+    int32_t K;             // Euler-Maruyama sub-steps per observation
+    double dt;
+    double sigma_dyn;
+    double sigma0;
+    double sigma_obs;
+    double p[16];          // LG: A row-major (dx <= 4); L63: s, r, b; FHN: a, b, c1, c2, d, D, amp, steps, block
+    int32_t dy;
+    int32_t obs_small[kMaxObsSmall];  // observation indices when dy <= kMaxObsSmall
+    double x0_small[kMaxLgDim];       // prior mean for the small models
+};
+
+// Drift of the small models (thread per particle), in the state's precision.
+template <int D, typename Real>
+struct SmallModel {
+    // f(x) for LG (drift -A x) or Lorenz 63 (Sec. 4.1; first component
+    // -s (x1 - x2) as in eq. eqDiscreteLorenz-1).
+    __device__ __forceinline__ static void drift(const ModelParams &mp, const Real x[D], Real f[D])
+    {
+        if (mp.kind == kLorenz63) {
+            const Real s = (Real)mp.p[0], r = (Real)mp.p[1], b = (Real)mp.p[2];
+            f[0] = s * (x[1] - x[0]);
+            f[1] = r * x[0] - x[1] - x[0] * x[2];
+            f[2] = x[0] * x[1] - b * x[2];
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                Real s = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) s += (Real)mp.p[i * D + j] * x[j];
+                f[i] = -s;
+            }
+        }
+    }
+};
+
+// lcm(D, 4) / D sub-steps share lcm(D, 4) / 4 Philox blocks: normal number
+// nu = k * D + v of an observation interval sits in block nu / 4, lane nu % 4.
+template <int D>
+struct NoisePacking {
+    static constexpr int lcm = (D % 4 == 0) ? D : (D % 2 == 0) ? 2 * D : 4 * D;
+    static constexpr int steps = lcm / D;   // sub-steps per group
+    static constexpr int blocks = lcm / 4;  // Philox calls per group
+};
+
+// Propagates one particle of a small model over the K sub-steps of
+// observation t (Alg. 1 step 2a; Euler-Maruyama), stream `stream`,
+// counter words (c0, t, c2).
+template <int D, typename Real>
+__device__ __forceinline__ void propagate_small(const ModelParams &mp, Key key, uint32_t stream, uint32_t c0,
+                                                uint32_t t, uint32_t c2, Real x[D])
+{
+    using NP = NoisePacking<D>;
+    const Real dt = (Real)mp.dt;
+    const Real sq = (Real)(mp.sigma_dyn * sqrt(mp.dt));
+    const int K = mp.K;
+    uint32_t block = 0;
+    for (int k0 = 0; k0 < K; k0 += NP::steps) {
+        Real z[4 * NP::blocks];
+#pragma unroll
+        for (int b = 0; b < NP::blocks; ++b) normals4<Real>(key, c0, t, c2, stream, block + b, z + 4 * b);
+        block += NP::blocks;
+#pragma unroll
+        for (int s = 0; s < NP::steps; ++s) {
+            if (k0 + s < K) {
+                Real f[D];
+                SmallModel<D, Real>::drift(mp, x, f);
+#pragma unroll
+                for (int v = 0; v < D; ++v) x[v] = x[v] + dt * f[v] + sq * z[s * D + v];
+            }
+        }
+    }
+}
+
+// log g without its constant: -1/2 sum_j (y_j - x[idx_j])^2 / sigma_obs^2.
+template <int D, typename Real>
+__device__ __forceinline__ Real loglik_small(const ModelParams &mp, const float *y, const Real x[D])
+{
+    Real s = 0;
+    for (int j = 0; j < mp.dy; ++j) {
+        const int idx = mp.obs_small[j];
+        Real xv = 0;
+#pragma unroll
+        for (int v = 0; v < D; ++v)
+            if (v == idx) xv = x[v];
+        const Real e = (Real)y[j] - xv;
+        s += e * e;
+    }
+    return (Real)(-0.5 / (mp.sigma_obs * mp.sigma_obs)) * s;
+}
+
+}  // namespace pf

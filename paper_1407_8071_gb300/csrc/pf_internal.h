@@ -1,0 +1,143 @@
+// pf_internal.h -- host-side layout of a filter context and the kernel
+// launchers shared by the translation units of the library.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pf.h"
+#include "pf_device.cuh"
+
+namespace pf {
+
+// Particles of all filters sit contiguously, filter after filter.  Each filter
+// is cut into tiles of at most kTile particles; a tile never spans two filters,
+// so every per-filter reduction is a reduction over that filter's tiles.
+constexpr int kTile = 1024;
+constexpr int kResampleThreads = 256;
+constexpr int kItems = kTile / kResampleThreads;  // particles per thread in the tile kernels
+
+struct TileDesc {
+    int32_t m;       // filter
+    int32_t lstart;  // filter-local index of the tile's first particle
+    int32_t len;     // particles in the tile
+    int32_t pad;
+    int64_t gstart;  // global index of the tile's first particle
+};
+
+struct FilterDesc {
+    int64_t off;         // global index of particle 0
+    int32_t N;           // particles
+    int32_t tile_begin;  // first tile
+    int32_t tile_count;  // tiles
+    int32_t shift;       // 52 - ceil(log2 N): weight quantisation exponent
+};
+
+// Per-filter scalars kept in FP64 on the device.
+enum FStat : int {
+    kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsCtot = 4, kFsU = 5, kFsC = 6, kFsDegenerate = 7, kFsCount = 8
+};
+// Per-tile FP64 partial sums.
+enum TSum : int { kTsW = 0, kTsW2 = 1, kTsQ = 2, kTsCount = 4 };
+
+// Device error word: bit flags plus the first offending filter.
+enum : int32_t { kErrDegenerate = 1 };
+
+// Everything the resampling kernels need, by value.
+struct ResampleArgs {
+    const TileDesc *tiles;
+    const FilterDesc *filt;
+    const float *logw;       // FP32 log-weights (null when w_direct is used)
+    const double *w_direct;  // FP64 weights in [0, 1] (stateless entry point)
+    const double *u_direct;  // per-filter uniforms (stateless entry point), else drawn from Philox
+    Key key;
+    const int32_t *d_t;      // completed steps; the step being resampled is *d_t + 1
+    float *tile_max;         // [tiles]
+    double *tile_sums;       // [tiles][kTsCount]
+    double *fstats;          // [M][kFsCount]
+    double *C;               // [P] inclusive prefix of the quantised weights
+    int32_t *B;              // [P] ancestor start markers
+    int32_t *anc;            // [P] filter-local ancestors
+    int32_t *err;            // [2]
+    double log_const;        // -dy/2 log(2 pi sigma_obs^2), added to log G only
+};
+
+struct Ctx;
+
+// Launchers (k_filter.cu).  All enqueue on `s` and return cudaGetLastError().
+cudaError_t launch_init(const Ctx &c, cudaStream_t s);
+cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t obs_stride, const float *x_in, float *x_out,
+                             cudaStream_t s);
+cudaError_t launch_resample(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s);
+cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s);
+cudaError_t launch_rng_philox(int64_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                              cudaStream_t s);
+cudaError_t launch_rng_normals(int64_t n, const uint32_t *ctr, uint64_t seed, float *z, cudaStream_t s);
+cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int32_t *d_obs_idx, Key key,
+                            int32_t T, int32_t record, int32_t init_random, double *d_x, float *d_y,
+                            cudaStream_t s);
+
+// Host helpers (pf_capi.cu) used by the launchers.
+int ceil_log2_host(int64_t n);
+
+struct Ctx {
+    ModelParams mp{};
+    Key key{};
+    int32_t M = 0;
+    int64_t P = 0;  // total particles
+    int32_t n_tiles = 0;
+    std::vector<int32_t> N;
+    std::vector<int64_t> off;
+
+    // device memory
+    TileDesc *tiles = nullptr;
+    FilterDesc *filt = nullptr;
+    int32_t *pfilt = nullptr;     // [P] filter of each particle (lattice kernels)
+    float *x[2] = {nullptr, nullptr};
+    float *logw = nullptr;
+    float *tile_max = nullptr;
+    double *tile_sums = nullptr;
+    double *fstats = nullptr;
+    double *C = nullptr;
+    int32_t *B = nullptr;
+    int32_t *anc = nullptr;
+    double *tile_est = nullptr;   // [tiles][dx] (small models)
+    double *est = nullptr;        // [M][dx]
+    double *ens = nullptr;        // [dx]
+    float *d_obs = nullptr;       // [M * dy] the current observation on the device
+    float *h_stage[2] = {nullptr, nullptr};        // pinned host staging, [M * dy] each
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};  // copy-out of each staging slot done
+    bool stage_used[2] = {false, false};
+    int stage_slot = 0;
+    int32_t *d_t = nullptr;       // completed steps
+    int32_t *err = nullptr;       // [2]
+    int32_t *obs_idx = nullptr;   // [dy]
+    int32_t *obs_slot = nullptr;  // [J*J] lattice node -> observation index or -1
+    double *x0 = nullptr;         // [dx]
+
+    int cur = 0;  // x[cur] holds the current particles
+    int32_t t = 0;
+    int phase = 0;  // 0: ready to propagate; 1: propagated, ready to resample
+    bool steps_done = false;
+    int32_t graph_mode[2] = {-1, -1};  // obs layout each captured graph was built for
+
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+
+    pf_alloc_fn alloc = nullptr;
+    pf_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<std::pair<void *, size_t>> allocations;
+
+    int device = 0;
+    int32_t fatal = 0;  // sticky pf_status
+    std::string last_error;
+
+    size_t dyn_obs() const { return (size_t)mp.dy; }
+};
+
+}  // namespace pf

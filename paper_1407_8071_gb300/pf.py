@@ -1,0 +1,299 @@
+"""ctypes binding of include/pf.h (same names as the C ABI) and a small wrapper.
+
+Argument marshalling only: every step of the filter runs in libpf_gb300.so's
+CUDA kernels.  The library is built in-tree on first use if it is missing or
+stale; if it cannot be built or loaded the import of any entry point raises,
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_size_t, c_uint32, c_uint64, c_void_p
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+from . import workloads as W
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENUMERIC, PF_ETIMEOUT, PF_ESTATE, PF_EUNSUPPORTED = range(8)
+STATUS_NAMES = ["PF_OK", "PF_EINVAL", "PF_ENOMEM", "PF_ECUDA", "PF_ENUMERIC", "PF_ETIMEOUT", "PF_ESTATE",
+                "PF_EUNSUPPORTED"]
+PF_STAT_MEAN, PF_STAT_LOG_EVIDENCE, PF_STAT_ESS, PF_STAT_LOG_Z = range(4)
+
+
+class pf_model(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("dx", c_int32), ("J", c_int32), ("steps_per_obs", c_int32),
+                ("params", POINTER(c_double)), ("n_params", c_int32)]
+
+
+class pf_obs_op(ctypes.Structure):
+    _fields_ = [("dy", c_int32), ("idx", POINTER(c_int32)), ("sigma_obs", c_double)]
+
+
+class pf_noise(ctypes.Structure):
+    _fields_ = [("sigma_dyn", c_double), ("x0_mean", POINTER(c_double)), ("sigma0", c_double), ("seed", c_uint64)]
+
+
+class pf_stat(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("var", c_int32), ("per_filter", c_int32)]
+
+
+PF_ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+PF_FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+_SIGS = {
+    "pf_version": (c_char_p, []),
+    "pf_set_allocator": (c_int32, [PF_ALLOC_FN, PF_FREE_FN, c_void_p]),
+    "pf_create": (c_int32, [POINTER(pf_model), c_int32, POINTER(c_int32), c_double, POINTER(pf_obs_op),
+                            POINTER(pf_noise), POINTER(c_void_p)]),
+    "pf_destroy": (None, [c_void_p]),
+    "pf_last_error": (c_char_p, [c_void_p]),
+    "pf_set_stream": (c_int32, [c_void_p, c_void_p]),
+    "pf_step": (c_int32, [c_void_p, POINTER(c_float), c_int32]),
+    "pf_step_device": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "pf_propagate": (c_int32, [c_void_p, POINTER(c_float), c_int32]),
+    "pf_propagate_device": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "pf_resample": (c_int32, [c_void_p]),
+    "pf_estimate": (c_int32, [c_void_p, POINTER(pf_stat), POINTER(c_double)]),
+    "pf_get_time": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "pf_get_state": (c_int32, [c_void_p, POINTER(c_float)]),
+    "pf_set_state": (c_int32, [c_void_p, POINTER(c_float), c_int32]),
+    "pf_get_logw": (c_int32, [c_void_p, POINTER(c_float)]),
+    "pf_set_logw": (c_int32, [c_void_p, POINTER(c_float)]),
+    "pf_get_ancestors": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "pf_rng_philox": (c_int32, [c_int64, c_void_p, c_uint32, c_uint32, c_void_p, c_void_p]),
+    "pf_rng_normals": (c_int32, [c_int64, c_void_p, c_uint64, c_void_p, c_void_p]),
+    "pf_systematic_scratch_bytes": (c_size_t, [c_int32, c_int64]),
+    "pf_systematic_resample": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p, c_void_p,
+                                         c_size_t, c_void_p]),
+    "pf_simulate": (c_int32, [POINTER(pf_model), c_double, POINTER(pf_obs_op), POINTER(pf_noise), c_int32, c_int32,
+                              c_int32, POINTER(c_double), POINTER(c_float)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libpf_gb300.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols() -> list:
+    return sorted(_SIGS)
+
+
+class PFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _check(st: int, ctx=None):
+    if st != PF_OK:
+        raise PFError(st, (lib().pf_last_error(ctx) or b"").decode())
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_float))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_int32))
+
+
+# ---------------------------------------------------------------------------
+# Thin wrappers with the C names
+# ---------------------------------------------------------------------------
+class _Structs:
+    """Builds the pf_model / pf_obs_op / pf_noise structs of a ModelSpec and keeps their arrays alive."""
+
+    def __init__(self, spec: W.ModelSpec, seed: int):
+        self.params = np.ascontiguousarray(spec.params, dtype=np.float64)
+        self.idx = np.ascontiguousarray(spec.obs_idx, dtype=np.int32)
+        self.x0 = np.ascontiguousarray(spec.x0_mean, dtype=np.float64)
+        self.model = pf_model(spec.kind, spec.dx, spec.J, spec.K, _dp(self.params), len(self.params))
+        self.obs = pf_obs_op(len(self.idx), _ip(self.idx), spec.sigma_obs)
+        self.noise = pf_noise(spec.sigma_dyn, _dp(self.x0), spec.sigma0, seed)
+
+
+def pf_simulate(spec: W.ModelSpec, T: int, seed: int, record: int = 0):
+    """Truth X_0..X_T (FP64) and observations (FP32) simulated on the GPU."""
+    s = _Structs(spec, seed)
+    x = np.empty((T + 1, spec.dx), dtype=np.float64)
+    y = np.empty((T, spec.dy), dtype=np.float32)
+    _check(lib().pf_simulate(ctypes.byref(s.model), spec.dt, ctypes.byref(s.obs), ctypes.byref(s.noise), T, record,
+                             1 if spec.truth_init_random else 0, _dp(x), _fp(y)))
+    return x, y
+
+
+def pf_rng_philox(d_ctr, key0: int, key1: int, d_out, stream=None):
+    n = d_ctr.shape[0]
+    _check(lib().pf_rng_philox(n, d_ctr.data_ptr(), key0, key1, d_out.data_ptr(), stream))
+
+
+def pf_rng_normals(d_ctr, seed: int, d_z, stream=None):
+    n = d_ctr.shape[0]
+    _check(lib().pf_rng_normals(n, d_ctr.data_ptr(), seed, d_z.data_ptr(), stream))
+
+
+def pf_systematic_scratch_bytes(M: int, total: int) -> int:
+    return int(lib().pf_systematic_scratch_bytes(M, total))
+
+
+def pf_systematic_resample(N: Sequence[int], d_w, d_u, d_anc, d_scratch, stream=None):
+    """Stateless systematic resampling of len(N) filters (device tensors)."""
+    Nh = np.ascontiguousarray(N, dtype=np.int32)
+    _check(lib().pf_systematic_resample(len(Nh), _ip(Nh), d_w.data_ptr(), d_u.data_ptr(), d_anc.data_ptr(),
+                                        d_scratch.data_ptr(), d_scratch.numel() * d_scratch.element_size(), stream))
+
+
+# ---------------------------------------------------------------------------
+# torch caching allocator as the context allocator
+# ---------------------------------------------------------------------------
+_torch_hooks = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route context device memory through torch's caching allocator."""
+    global _torch_hooks
+    if not enable:
+        _check(lib().pf_set_allocator(PF_ALLOC_FN(), PF_FREE_FN(), None))
+        _torch_hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (PF_ALLOC_FN(_alloc), PF_FREE_FN(_free))
+    _check(lib().pf_set_allocator(hooks[0], hooks[1], None))
+    _torch_hooks = hooks
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+class EnsembleFilter:
+    """M independent bootstrap filters on the GPU (Sec. 3.1) behind the C ABI."""
+
+    def __init__(self, spec: W.ModelSpec, M: int, N, seed: int):
+        self.spec = spec
+        self.M = int(M)
+        self.N = np.ascontiguousarray(np.broadcast_to(np.asarray(N, dtype=np.int32), (self.M,)), dtype=np.int32)
+        self.P = int(self.N.sum())
+        self._s = _Structs(spec, seed)
+        h = c_void_p()
+        st = lib().pf_create(ctypes.byref(self._s.model), self.M, _ip(self.N), spec.dt, ctypes.byref(self._s.obs),
+                             ctypes.byref(self._s.noise), ctypes.byref(h))
+        _check(st)
+        self.h = h
+
+    # -- life cycle
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream_handle: Optional[int]):
+        _check(lib().pf_set_stream(self.h, stream_handle), self.h)
+
+    # -- hot path
+    @staticmethod
+    def _obs(y):
+        return np.ascontiguousarray(y, dtype=np.float32)
+
+    def step(self, y, per_filter: bool = False):
+        y = self._obs(y)
+        _check(lib().pf_step(self.h, _fp(y), self.spec.dy if per_filter else 0), self.h)
+
+    def step_device(self, d_y, per_filter: bool = False):
+        _check(lib().pf_step_device(self.h, d_y.data_ptr(), self.spec.dy if per_filter else 0), self.h)
+
+    def propagate(self, y, per_filter: bool = False):
+        y = self._obs(y)
+        _check(lib().pf_propagate(self.h, _fp(y), self.spec.dy if per_filter else 0), self.h)
+
+    def propagate_device(self, d_y, per_filter: bool = False):
+        _check(lib().pf_propagate_device(self.h, d_y.data_ptr(), self.spec.dy if per_filter else 0), self.h)
+
+    def resample(self):
+        _check(lib().pf_resample(self.h), self.h)
+
+    def estimate(self, kind: int = PF_STAT_MEAN, var: int = -1, per_filter: bool = False) -> np.ndarray:
+        n = 1
+        if kind == PF_STAT_MEAN and var < 0:
+            n = self.spec.dx
+        if per_filter:
+            n *= self.M
+        out = np.empty(n, dtype=np.float64)
+        st = pf_stat(kind, var, 1 if per_filter else 0)
+        _check(lib().pf_estimate(self.h, ctypes.byref(st), _dp(out)), self.h)
+        if per_filter and kind == PF_STAT_MEAN and var < 0:
+            return out.reshape(self.M, self.spec.dx)
+        return out
+
+    # -- inspection
+    @property
+    def t(self) -> int:
+        v = c_int32()
+        _check(lib().pf_get_time(self.h, ctypes.byref(v)), self.h)
+        return v.value
+
+    def get_state(self) -> np.ndarray:
+        x = np.empty((self.P, self.spec.dx), dtype=np.float32)
+        _check(lib().pf_get_state(self.h, _fp(x)), self.h)
+        return x
+
+    def set_state(self, x, t: int):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(self.P, self.spec.dx)
+        _check(lib().pf_set_state(self.h, _fp(x), int(t)), self.h)
+
+    def get_logw(self) -> np.ndarray:
+        l = np.empty(self.P, dtype=np.float32)
+        _check(lib().pf_get_logw(self.h, _fp(l)), self.h)
+        return l
+
+    def set_logw(self, l):
+        l = np.ascontiguousarray(l, dtype=np.float32)
+        _check(lib().pf_set_logw(self.h, _fp(l)), self.h)
+
+    def get_ancestors(self) -> np.ndarray:
+        a = np.empty(self.P, dtype=np.int32)
+        _check(lib().pf_get_ancestors(self.h, _ip(a)), self.h)
+        return a
+
+    def offsets(self) -> np.ndarray:
+        return np.concatenate([[0], np.cumsum(self.N)]).astype(np.int64)

@@ -1,0 +1,182 @@
+"""GPU parity of the filter's building blocks against the FP64 oracle (through the C ABI).
+
+Tolerances (FP32 state on the GPU vs FP64 in the oracle):
+* Philox words: bit-exact.
+* Box-Muller normals: |z_gpu - z| <= 4e-6 (|z| + 1) -- logf/sqrtf/sincospif
+  rounding on exact 24-bit uniforms.
+* Propagated states after a full observation interval from identical inputs:
+  |x_gpu - x| <= 1e-5 max(|x|, rms of the component over the batch).
+* Log-weights: |l_gpu - l| <= 1e-5 max(|l|, 1).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_8071_gb300 import pf, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+STATE_RTOL = 1e-5
+
+
+def assert_state_close(xg, xo, rtol=STATE_RTOL):
+    xg = np.asarray(xg, dtype=np.float64)
+    rms = np.sqrt(np.mean(xo ** 2, axis=0, keepdims=True))
+    scale = np.maximum(np.abs(xo), rms)
+    err = np.abs(xg - xo) / np.maximum(scale, 1e-30)
+    assert np.max(err) <= rtol, f"max scaled error {np.max(err):.3e} at {np.unravel_index(np.argmax(err), err.shape)}"
+
+
+def ids(N, M):
+    pid = np.concatenate([np.arange(n) for n in np.broadcast_to(N, (M,))]).astype(np.int32)
+    fid = np.repeat(np.arange(M), np.broadcast_to(N, (M,))).astype(np.int32)
+    return pid, fid
+
+
+# ------------------------------------------------------------------ generator
+def test_philox_bit_exact():
+    ctr = W.random_counters(1 << 16, seed=1)
+    ctr[:64] = 0
+    ctr[64:128] = 0xFFFFFFFF
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.empty_like(d_ctr)
+    for key in [(0, 0), (0xDEADBEEF, 0x12345678), (0xFFFFFFFF, 0xFFFFFFFF)]:
+        pf.pf_rng_philox(d_ctr, key[0], key[1], d_out)
+        torch.cuda.synchronize()
+        got = d_out.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, oracle.philox(ctr, *key))
+
+
+def test_normals_match_oracle():
+    ctr = W.random_counters(1 << 15, seed=2)
+    seed = 0x0123456789ABCDEF
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_z = torch.empty((len(ctr), 4), dtype=torch.float32, device="cuda")
+    pf.pf_rng_normals(d_ctr, seed, d_z)
+    torch.cuda.synchronize()
+    z = oracle.normals(ctr, seed)
+    err = np.abs(d_z.cpu().numpy() - z) / (np.abs(z) + 1.0)
+    assert err.max() <= 4e-6, err.max()
+
+
+# ------------------------------------------------------------------ prior and propagation
+SMALL_SPECS = {
+    "lorenz63": lambda: W.lorenz63(),
+    "lg1": lambda: W.linear_gaussian(A=[[0.3]], obs_idx=[0]),
+    "lg2": lambda: W.linear_gaussian(A=[[0.5, -1.0], [1.0, 0.5]], obs_idx=[1]),
+    "lg3": lambda: W.linear_gaussian(),
+    "lg4": lambda: W.linear_gaussian(A=np.diag([0.1, 0.2, 0.3, 0.4]).tolist(), obs_idx=[0, 3]),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL_SPECS))
+def test_prior_matches_oracle(name):
+    spec = SMALL_SPECS[name]()
+    M, N, seed = 3, 777, 0xC0FFEE
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        xg = f.get_state()
+    pid, fid = ids(N, M)
+    xo = oracle.prior(spec, pid, fid, seed)
+    assert_state_close(xg, xo, rtol=1e-6)
+
+
+@pytest.mark.parametrize("name", list(SMALL_SPECS))
+@pytest.mark.parametrize("t", [1, 7])
+def test_propagate_and_weights_match_oracle(name, t):
+    spec = SMALL_SPECS[name]()
+    M, N, seed = 3, 1500, 77  # ragged tail: 1500 = 1024 + 476
+    x0 = W.random_states(spec, M * N, seed=5).astype(np.float32)
+    y = np.linspace(-2.0, 3.0, spec.dy).astype(np.float32)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.set_state(x0, t - 1)
+        f.propagate(y)
+        xg = f.get_state()
+        lg = f.get_logw()
+    pid, fid = ids(N, M)
+    xo = oracle.propagate(spec, x0.astype(np.float64), pid, fid, t, seed)
+    assert_state_close(xg, xo)
+    lo = oracle.loglik(spec, xo, y.astype(np.float64))
+    assert np.max(np.abs(lg - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+
+
+def test_lorenz_full_size_sampled():
+    """Lorenz at M * N = 2^20 (the bench launch), sampled particles vs the oracle one by one."""
+    spec = W.lorenz63()
+    M, N, seed = 64, 1 << 14, 2024
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        x0 = f.get_state()
+        f.propagate(np.array([1.0, 20.0], dtype=np.float32))
+        xg = f.get_state()
+    rng = np.random.default_rng(0)
+    sample = rng.choice(M * N, size=3000, replace=False)
+    pid, fid = (sample % N).astype(np.int32), (sample // N).astype(np.int32)
+    xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid, fid, 1, seed)
+    assert_state_close(xg[sample], xo)
+
+
+# ------------------------------------------------------------------ lattice
+def fhn_spec(J, **kw):
+    return W.fhn_lattice(J=J, **kw)
+
+
+@pytest.mark.parametrize("J,M,N", [(2, 2, 5), (8, 3, 40), (20, 2, 9), (40, 1, 3)])
+def test_fhn_prior_and_propagate_match_oracle(J, M, N):
+    spec = fhn_spec(J)
+    seed = 99
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        x_init = f.get_state()
+        pid, fid = ids(N, M)
+        assert_state_close(x_init, oracle.prior(spec, pid, fid, seed), rtol=1e-6)
+        x0 = W.random_states(spec, M * N, seed=J).astype(np.float32)
+        y = np.random.default_rng(J).uniform(0.0, 1.0, spec.dy).astype(np.float32)
+        for t in (1, 9):  # t = 9 crosses the end of the stimulus (200 sub-steps)
+            f.set_state(x0, t - 1)
+            f.propagate(y)
+            xg = f.get_state()
+            lg = f.get_logw()
+            xo = oracle.propagate(spec, x0.astype(np.float64), pid, fid, t, seed)
+            assert_state_close(xg, xo)
+            lo = oracle.loglik(spec, xo, y.astype(np.float64))
+            assert np.max(np.abs(lg - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+            f.resample()
+
+
+def test_fhn_full_size_sampled():
+    """The 40 x 40 lattice at M = 32, N = 1024 (the full workload), sampled particles."""
+    spec = fhn_spec(40)
+    M, N, seed = 32, 1024, 31
+    _, y = oracle.simulate(spec, 1, W.SEED_FHN_OBS)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        x0 = f.get_state()
+        f.propagate(y[0].astype(np.float32))
+        xg = f.get_state()
+        lg = f.get_logw()
+    rng = np.random.default_rng(1)
+    sample = rng.choice(M * N, size=24, replace=False)
+    pid, fid = (sample % N).astype(np.int32), (sample // N).astype(np.int32)
+    xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid, fid, 1, seed)
+    assert_state_close(xg[sample], xo)
+    lo = oracle.loglik(spec, xo, y[0].astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(lg[sample] - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+
+
+# ------------------------------------------------------------------ record simulator
+@pytest.mark.parametrize("name", ["lorenz63", "lg3"])
+def test_simulate_matches_oracle_small(name):
+    spec = SMALL_SPECS[name]()
+    T, seed = 200, W.SEED_LORENZ_OBS
+    xg, yg = pf.pf_simulate(spec, T, seed, record=3)
+    xo, yo = oracle.simulate(spec, T, seed, record=3)
+    # FP64 on both sides; Lorenz amplifies rounding differences chaotically
+    assert np.max(np.abs(xg - xo) / (np.abs(xo) + 1.0)) <= 1e-7
+    assert np.max(np.abs(yg - yo.astype(np.float32)) / (np.abs(yo) + 1.0)) <= 1e-6
+
+
+def test_simulate_matches_oracle_lattice():
+    spec = fhn_spec(12)
+    T, seed = 12, W.SEED_FHN_OBS
+    xg, yg = pf.pf_simulate(spec, T, seed)
+    xo, yo = oracle.simulate(spec, T, seed)
+    assert np.max(np.abs(xg - xo)) <= 1e-10
+    assert np.max(np.abs(yg - yo.astype(np.float32)) / (np.abs(yo) + 1.0)) <= 1e-6

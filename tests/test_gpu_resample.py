@@ -1,0 +1,151 @@
+"""GPU resampling and normalisation against the FP64 oracle (through the C ABI).
+
+* Stateless systematic resampling: ancestors bit-exact against the oracle
+  given identical FP64 weights and uniforms, for ragged filters spanning
+  several tiles (1024 particles), ties, zeros, spikes and N = 1.
+* In-context resampling from FP32 log-weights: the GPU computes the weights
+  with FP32 exp, so ancestors are compared with the oracle's (FP64 exp)
+  allowing the rare boundary moved by one FP32 rounding; offspring counts obey
+  the floor/ceil invariant; log Z, ESS and log G match within 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_8071_gb300 import pf, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+KINDS = ["lognormal", "spike", "ties", "sparse", "uniform"]
+
+
+def run_stateless(N_list, kind_of, seed):
+    N_list = np.asarray(N_list, dtype=np.int32)
+    ws = [W.random_weights(int(n), seed=seed + i, kind=kind_of(i)) for i, n in enumerate(N_list)]
+    us = W.random_uniforms(len(N_list), seed=seed)
+    w = np.concatenate(ws)
+    d_w = torch.from_numpy(w).cuda()
+    d_u = torch.from_numpy(us).cuda()
+    d_anc = torch.empty(len(w), dtype=torch.int32, device="cuda")
+    nbytes = pf.pf_systematic_scratch_bytes(len(N_list), len(w))
+    d_scr = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    pf.pf_systematic_resample(N_list, d_w, d_u, d_anc, d_scr)
+    torch.cuda.synchronize()
+    got = d_anc.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(N_list)])
+    for i, n in enumerate(N_list):
+        exp = oracle.systematic(ws[i], float(us[i]))
+        assert np.array_equal(got[off[i]:off[i + 1]], exp), (i, n, kind_of(i))
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_systematic_bit_exact_ragged(kind):
+    run_stateless([1, 2, 3, 1023, 1024, 1025, 3000, 4096, 17, 64], lambda i: kind, seed=10 + len(kind))
+
+
+def test_systematic_bit_exact_mixed_many_filters():
+    N = W.ragged_counts(256, 64, 4096)
+    run_stateless(N, lambda i: KINDS[i % len(KINDS)], seed=500)
+
+
+def test_systematic_bit_exact_one_big_filter():
+    run_stateless([1 << 20], lambda i: "lognormal", seed=7)
+    run_stateless([(1 << 20) - 3], lambda i: "sparse", seed=8)
+
+
+def test_systematic_golden_worked_examples():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "systematic_worked.txt")
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        n, w, u, a = [f.split() for f in line.split("|")]
+        w = np.array(w, dtype=np.float64)
+        d_w = torch.from_numpy(w).cuda()
+        d_u = torch.tensor([float(u[0])], dtype=torch.float64, device="cuda")
+        d_anc = torch.empty(len(w), dtype=torch.int32, device="cuda")
+        d_scr = torch.empty(pf.pf_systematic_scratch_bytes(1, len(w)), dtype=torch.uint8, device="cuda")
+        pf.pf_systematic_resample([len(w)], d_w, d_u, d_anc, d_scr)
+        torch.cuda.synchronize()
+        assert d_anc.cpu().tolist() == [int(v) for v in a]
+
+
+def _filter_with_logw(spec, M, N, seed, logw):
+    f = pf.EnsembleFilter(spec, M, N, seed)
+    f.propagate(np.zeros(spec.dy, dtype=np.float32))
+    f.set_logw(logw)
+    f.resample()
+    return f
+
+
+@pytest.mark.parametrize("N", [1, 100, 512, 1024, 2500])
+def test_context_resampling_and_normaliser(N):
+    spec = W.lorenz63()
+    M, seed = 5, 4242
+    rng = np.random.default_rng(N)
+    logw = rng.normal(-30.0, 4.0, size=M * N).astype(np.float32)
+    f = _filter_with_logw(spec, M, N, seed, logw)
+    anc = f.get_ancestors()
+    logZ = f.estimate(pf.PF_STAT_LOG_Z, per_filter=True)
+    ess = f.estimate(pf.PF_STAT_ESS, per_filter=True)
+    logG = f.estimate(pf.PF_STAT_LOG_EVIDENCE, per_filter=True)
+    f.close()
+    const = -0.5 * spec.dy * math.log(2 * math.pi * spec.sigma_obs ** 2)
+    mismatched = 0
+    for m in range(M):
+        l = logw[m * N:(m + 1) * N].astype(np.float64)
+        nrm = oracle.normalise(l)
+        assert logZ[m] == pytest.approx(nrm["logZ"], rel=1e-6)
+        assert ess[m] == pytest.approx(nrm["ess"], rel=1e-5)
+        assert logG[m] == pytest.approx(nrm["logZ"] - math.log(N) + const, rel=1e-6)
+        w = np.exp(l - nrm["max"])
+        exp = oracle.systematic(w, oracle.resample_u(seed, m, 1))
+        a = anc[m * N:(m + 1) * N]
+        mismatched += int(np.sum(a != exp))
+        assert np.all(np.diff(a) >= 0)
+        o = np.bincount(a, minlength=N)
+        q = oracle.quantise(w)
+        what = q / q.sum()
+        assert np.all(o >= np.floor(N * what) - 1) and np.all(o <= np.ceil(N * what) + 1)
+    # FP32 exp moves a systematic boundary only when a t_i falls within ~1e-7 of a C_k
+    assert mismatched <= max(2, M * N // 1000)
+
+
+def test_context_gather_and_estimate_are_exact():
+    spec = W.lorenz63()
+    M, N, seed = 3, 2000, 5
+    rng = np.random.default_rng(3)
+    f = pf.EnsembleFilter(spec, M, N, seed)
+    f.propagate(np.zeros(2, dtype=np.float32))
+    xbar = f.get_state()
+    f.set_logw(rng.normal(0.0, 2.0, M * N).astype(np.float32))
+    f.resample()
+    anc = f.get_ancestors()
+    x = f.get_state()
+    est = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)
+    ens = f.estimate(pf.PF_STAT_MEAN, var=-1)
+    f.close()
+    for m in range(M):
+        src = xbar[m * N + anc[m * N:(m + 1) * N]]
+        assert np.array_equal(x[m * N:(m + 1) * N], src)
+        ref = src.astype(np.float64).mean(axis=0)
+        assert np.allclose(est[m], ref, rtol=1e-12, atol=1e-12)
+    assert np.allclose(ens, est.mean(axis=0), rtol=1e-13, atol=1e-13)
+
+
+def test_degenerate_filter_is_reported():
+    spec = W.lorenz63()
+    M, N = 2, 64
+    logw = np.zeros(M * N, dtype=np.float32)
+    logw[N:] = -np.inf
+    f = _filter_with_logw(spec, M, N, 1, logw)
+    with pytest.raises(pf.PFError) as e:
+        f.estimate(pf.PF_STAT_MEAN, var=1)
+    assert e.value.status == pf.PF_ENUMERIC and "filter 1" in str(e.value)
+    with pytest.raises(pf.PFError) as e:
+        f.step(np.zeros(2))
+    assert e.value.status == pf.PF_ESTATE
+    f.close()
