@@ -21,8 +21,8 @@
  * admits schemes other than multinomial); multinomial resampling, the form
  * Algorithm 1 step 2b states literally, is kept for the rate tests.
  *
- * Compile with -ffp-contract=off: the resampling arithmetic must round every
- * product and sum separately so that it is reproducible bit for bit.
+ * Compile with -ffp-contract=off so that every product and sum is rounded
+ * separately, as written.
  *
  * Parity status per function is stated in the Python wrapper's header.
  */
@@ -338,12 +338,14 @@ void orc_normalise(int64_t n, const double *l, double *out)
     out[4] = s * s / s2;
 }
 
-/* Systematic resampling, exact-integer form.
- * L = ceil(log2 N), sh = 52 - L; q_i = floor(w_i 2^sh) for unnormalised weights
- * w_i in [0, 1]; C_k = q_0 + ... + q_k (exact: every partial sum is an integer
- * below 2^53); c = C_{N-1} / N; t_i = (i + u) * c, each operation rounded to
- * nearest; a_i = min{k : C_k > t_i}, or, when no C_k exceeds t_i, the last k
- * with q_k > 0.  The plain two-pointer merge below is that definition. */
+/* Systematic resampling in exact arithmetic.
+ * L = ceil(log2 N), sh = 52 - L; q_k = floor(w_k 2^sh) for unnormalised weights
+ * w_k in [0, 1] (an exact integer below 2^53); C_k = q_0 + ... + q_k (exact);
+ * u = U 2^-32 with U = floor(u 2^32); a_i = min{k : C_k > (i + u) C_{N-1} / N},
+ * the comparison made exactly as C_k N 2^32 > (i 2^32 + U) C_{N-1} in 128-bit
+ * integers.  Since (i + u) / N < 1 every i has an ancestor; the last positive
+ * q is the fallback only if every weight quantises to zero.  The plain
+ * two-pointer merge below is that definition. */
 static int ceil_log2(int64_t n)
 {
     int L = 0;
@@ -358,47 +360,53 @@ void orc_quantise(int64_t N, const double *w, double *q)
     for (int64_t i = 0; i < N; ++i) q[i] = floor(w[i] * scale);
 }
 
-void orc_systematic(int64_t N, const double *w, double u, int32_t *anc)
+typedef unsigned __int128 u128;
+
+/* cumulative quantised weights; returns the last k with q_k > 0 */
+static int64_t cumulative(int64_t N, const double *w, uint64_t *C)
 {
-    double *C = (double *)malloc(sizeof(double) * N);
-    orc_quantise(N, w, C);
-    double run = 0.0;
+    double *q = (double *)malloc(sizeof(double) * N);
+    orc_quantise(N, w, q);
+    uint64_t run = 0;
     int64_t last_pos = 0;
     for (int64_t k = 0; k < N; ++k) {
-        run = run + C[k];
-        if (C[k] > 0.0) last_pos = k;
+        run += (uint64_t)q[k];
+        if (q[k] > 0.0) last_pos = k;
         C[k] = run;
     }
-    double c = C[N - 1] / (double)N;
+    free(q);
+    return last_pos;
+}
+
+void orc_systematic(int64_t N, const double *w, double u, int32_t *anc)
+{
+    uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    int64_t last_pos = cumulative(N, w, C);
+    const uint64_t U = (uint64_t)floor(u * 4294967296.0);
+    const u128 total = C[N - 1];
     int64_t k = 0;
     for (int64_t i = 0; i < N; ++i) {
-        volatile double a = (double)i + u; /* two separately rounded operations */
-        double t = a * c;
-        while (k < N && !(C[k] > t)) ++k;
+        const u128 t = ((((u128)i) << 32) | U) * total; /* (i + u) C_{N-1} 2^32 */
+        while (k < N && !(((u128)C[k] * (u128)N) << 32 > t)) ++k;
         anc[i] = (int32_t)(k < N ? k : last_pos);
     }
     free(C);
 }
 
-/* Multinomial resampling (Algorithm 1 step 2b as stated): a_i = min{k : C_k > U_i C_N}
- * with the same exact prefix and independent uniforms U_i. */
+/* Multinomial resampling (Algorithm 1 step 2b as stated): a_i = min{k : C_k > U_i C_{N-1}}
+ * with the same exact prefix and independent uniforms U_i (compared exactly on the
+ * 2^-32 grid). */
 void orc_multinomial(int64_t N, const double *w, const double *U, int32_t *anc)
 {
-    double *C = (double *)malloc(sizeof(double) * N);
-    orc_quantise(N, w, C);
-    double run = 0.0;
-    int64_t last_pos = 0;
-    for (int64_t k = 0; k < N; ++k) {
-        run = run + C[k];
-        if (C[k] > 0.0) last_pos = k;
-        C[k] = run;
-    }
+    uint64_t *C = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    int64_t last_pos = cumulative(N, w, C);
+    const u128 total = C[N - 1];
     for (int64_t i = 0; i < N; ++i) {
-        double t = U[i] * C[N - 1];
-        int64_t lo = 0, hi = N; /* first k with C_k > t */
+        const u128 t = (u128)(uint64_t)floor(U[i] * 4294967296.0) * total;
+        int64_t lo = 0, hi = N; /* first k with C_k 2^32 > t */
         while (lo < hi) {
             int64_t mid = (lo + hi) / 2;
-            if (C[mid] > t) hi = mid; else lo = mid + 1;
+            if (((u128)C[mid] << 32) > t) hi = mid; else lo = mid + 1;
         }
         anc[i] = (int32_t)(lo < N ? lo : last_pos);
     }
