@@ -154,11 +154,17 @@ class Workload:
         self.T = T
         self.y_host = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
         self.y_dev = self.y_host.cuda()
+        torch.cuda.synchronize()
+        # one stream per context: the configurations are independent, so their
+        # kernels may overlap; `stream` is where the timed region starts and ends
         self.stream = torch.cuda.Stream()
+        self.streams = []
         for i, (M, N) in enumerate(self.rows):
             f = pf.EnsembleFilter(self.spec, M, N, seed=seed_base + i)
-            f.set_stream(self.stream.cuda_stream)
+            st = torch.cuda.Stream()
+            f.set_stream(st.cuda_stream)
             self.filters.append(f)
+            self.streams.append(st)
         self.particles = sum(M * N for M, N in self.rows)
         self.particle_steps_per_step = self.particles * self.spec.K
         # kernels one pf_step launches (propagate, tile max, weights, scan, ancestors, means, ensemble
@@ -188,16 +194,20 @@ class Workload:
             f.close()
 
 
-def time_region(torch, stream, fn, K, barrier=None):
+def time_region(torch, wl, fn, K, barrier=None):
     torch.cuda.synchronize()
     if barrier:
         barrier()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
-    start.record(stream)
+    start.record(wl.stream)
+    for st in wl.streams:
+        st.wait_stream(wl.stream)
     for _ in range(K):
         fn()
-    end.record(stream)
+    for st in wl.streams:
+        wl.stream.wait_stream(st)
+    end.record(wl.stream)
     torch.cuda.synchronize()
     if barrier:
         barrier()
@@ -208,15 +218,15 @@ def phase_times(torch, wl, reps=5):
     """Average device time of the propagate+weight kernel and of the resampling
     chain, per launch, with CUDA events on the filters' stream."""
     prop, res = [], []
-    for f in wl.filters:
+    for f, st in zip(wl.filters, wl.streams):
         for _ in range(reps):
             row = wl.y_dev[wl.t % wl.T]
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(wl.stream)
+            e0.record(st)
             f.propagate_device(row)
-            e1.record(wl.stream)
+            e1.record(st)
             f.resample()
-            e2.record(wl.stream)
+            e2.record(st)
             torch.cuda.synchronize()
             prop.append(e0.elapsed_time(e1) / 1e3)
             res.append(e1.elapsed_time(e2) / 1e3)
@@ -326,7 +336,7 @@ def main():
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    elapsed = time_region(torch, wl.stream, wl.step_device, args.steps, barrier)
+    elapsed = time_region(torch, wl, wl.step_device, args.steps, barrier)
     clocks = sampler.stop()
     if world > 1:
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
@@ -337,7 +347,7 @@ def main():
     # end to end through the public API with host buffers
     for _ in range(2):
         wl.step_host()
-    e2e_elapsed = time_region(torch, wl.stream, wl.step_host, args.steps, barrier)
+    e2e_elapsed = time_region(torch, wl, wl.step_host, args.steps, barrier)
     if world > 1:
         t = torch.tensor([e2e_elapsed], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

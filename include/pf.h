@@ -143,8 +143,9 @@ PF_API pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, d
  * context's stream first. */
 PF_API void pf_destroy(pf_ctx *ctx);
 
-/* Last error text of a context (or of the last failed pf_create when ctx is
- * NULL).  Valid until the next call on that context. */
+/* Last error text of a context (or, when ctx is NULL, of the last failed
+ * pf_create or context-free call on this thread).  Valid until the next call
+ * on that context. */
 PF_API const char *pf_last_error(const pf_ctx *ctx);
 
 /* Uses the caller's cudaStream_t for all later work of this context (NULL:
@@ -227,12 +228,12 @@ PF_API pf_status pf_rng_normals(int64_t n, const uint32_t *d_ctr, uint64_t seed,
 PF_API size_t pf_systematic_scratch_bytes(int32_t M, int64_t total);
 
 /* Systematic resampling of M filters (Algorithm 1 step 2b, systematic form)
- * from unnormalised FP64 weights w in [0, 1] with at least one weight > 0
- * per filter and one uniform u_m in [0, 1) per filter.  Definition (exact,
- * reproducible bit for bit): L = ceil(log2 N_m), q_k = floor(w_k 2^(52-L)),
- * C_k = q_0 + ... + q_k, t_i = (i + u_m) * (C_{N-1} / N_m) with each
- * operation rounded to nearest, a_i = min{k : C_k > t_i}, or the last k with
- * q_k > 0 when no C_k exceeds t_i.
+ * from unnormalised FP64 weights w in [0, 1] and one uniform u_m in [0, 1)
+ * per filter.  Definition (exact, reproducible bit for bit):
+ * L = ceil(log2 N_m), q_k = floor(w_k 2^(52-L)) (an integer below 2^53),
+ * C_k = q_0 + ... + q_k (exact), U = floor(u_m 2^32), and
+ * a_i = min{k : C_k > (i + U 2^-32) C_{N-1} / N_m} in exact arithmetic (the
+ * device compares C_k N 2^32 with (i 2^32 + U) C_{N-1} in 128-bit integers).
  * h_N: the M particle counts (host); the filters' weights sit contiguously in
  * d_w, filter after filter (sum N_m doubles), and each filter's largest
  * weight should be 1 so that its quantised total is positive.

@@ -11,6 +11,13 @@
 // Particles of all filters are contiguous; tiles of <= kTile particles never
 // span two filters, so per-filter reductions read only that filter's tiles
 // and no kernel waits on another block.
+//
+// FP64 is a narrow pipe on this GPU (about 1/64 of the FP32 rate), so it is
+// used only where the precision contract needs it -- the per-filter sums of
+// the normaliser and of the estimates, and the average over filters -- and
+// there only above the thread level: each thread sums its few particles in
+// FP32 and the block combines the thread sums in FP64.  Systematic resampling
+// is exact integer arithmetic (64-bit prefix, 128-bit comparisons).
 #include <cfloat>
 #include <cmath>
 
@@ -31,13 +38,6 @@ __device__ __forceinline__ float warp_max_f(float v)
     return v;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Max over the block, returned to every thread.
 __device__ float block_max_f(float v, float *sh)
 {
@@ -51,47 +51,74 @@ __device__ float block_max_f(float v, float *sh)
     return r;
 }
 
-// Sums of NV doubles over the block in a fixed order (deterministic), to every thread.
-template <int NV>
-__device__ void block_sum_d(double (&v)[NV], double *sh)
+__device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) v[j] = warp_sum_d(v[j]);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0)
-#pragma unroll
-        for (int j = 0; j < NV; ++j) sh[w * NV + j] = v[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        double r = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i * NV + j];
-        v[j] = r;
-    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// Exclusive prefix sum of one double per thread (exact for integer-valued
-// doubles below 2^53, the only use); returns the exclusive prefix.
-__device__ double block_exscan_d(double v, double *sh)
+// FP64 sums over the block of NV per-thread values, in a fixed order
+// (deterministic): warp j < NV sums column j.  `sh` holds blockDim.x * NV + NV
+// doubles.  Every thread receives the sums.
+template <int NV>
+__device__ void block_sum_dd(double (&v)[NV], double *sh)
+{
+    const int n = blockDim.x, tid = threadIdx.x;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sh[j * n + tid] = v[j];
+    __syncthreads();
+    const int w = tid >> 5, l = tid & 31;
+    if (w < NV) {
+        double acc = 0.0;
+        for (int i = l; i < n; i += 32) acc += sh[w * n + i];
+        acc = warp_sum_d(acc);
+        if (l == 0) sh[NV * n + w] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[j] = sh[NV * n + j];
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ uint64_t block_sum_u64(uint64_t v, uint64_t *sh)
+{
+    v = warp_sum_u64(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    uint64_t r = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    return r;
+}
+
+// Exclusive prefix sum of one uint64 per thread.
+__device__ uint64_t block_exscan_u64(uint64_t v, uint64_t *sh)
 {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    double inc = v;
+    uint64_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const double n = __shfl_up_sync(0xffffffffu, inc, o);
+        const uint64_t n = __shfl_up_sync(0xffffffffu, inc, o);
         if (l >= o) inc += n;
     }
     __syncthreads();
     if (l == 31) sh[w] = inc;
     __syncthreads();
-    double base = 0.0;
+    uint64_t base = 0;
     for (int i = 0; i < w; ++i) base += sh[i];
     return base + inc - v;
 }
 
-// Exclusive prefix max of one int per thread; returns the exclusive prefix
-// (identity -1).
+// Exclusive prefix max of one int per thread (identity -1).
 __device__ int block_exscan_max_i(int v, int *sh)
 {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -111,53 +138,117 @@ __device__ int block_exscan_max_i(int v, int *sh)
     return max(base, ex);
 }
 
-// ------------------------------------------------------------------ systematic resampling arithmetic
-// t_i = RN(RN(i + u) * c), each operation rounded to nearest (no contraction).
-__device__ __forceinline__ double t_of(int64_t i, double u, double c) { return __dmul_rn(__dadd_rn((double)i, u), c); }
-
-// #{i in [0, N) : t_i < x}.  t_i is non-decreasing in i, so the set is a prefix;
-// a real-valued estimate is corrected by a short walk, with bisection as the
-// exact fallback.
-__device__ int64_t count_below(double x, double u, double c, double inv_c, int64_t N)
+// ------------------------------------------------------------------ exact systematic resampling
+// q = floor(w 2^shift) of a weight in [0, 1], exactly, from the float's bits
+// (weights of 1 or more count as 1; NaN and non-positive weights as 0).
+__device__ __forceinline__ uint64_t quant_f32(float w, int shift)
 {
-    if (!(x > 0.0)) return 0;
-    double est = ceil(x * inv_c - u);
-    int64_t i = est <= 0.0 ? 0 : (est >= (double)N ? N : (int64_t)est);
+    if (!(w > 0.0f)) return 0;
+    if (w >= 1.0f) return 1ull << shift;
+    const uint32_t b = __float_as_uint(w);
+    int e = (int)((b >> 23) & 0xFF);
+    uint64_t m = b & 0x7FFFFFu;
+    if (e == 0) e = 1; else m |= 0x800000u;  // w = m 2^(e - 150)
+    const int sh = e - 150 + shift;
+    if (sh >= 0) return m << sh;
+    return (-sh) >= 64 ? 0 : (m >> (-sh));
+}
+
+__device__ __forceinline__ uint64_t quant_f64(double w, int shift)
+{
+    if (!(w > 0.0)) return 0;
+    if (w >= 1.0) return 1ull << shift;
+    const uint64_t b = (uint64_t)__double_as_longlong(w);
+    int e = (int)((b >> 52) & 0x7FF);
+    uint64_t m = b & ((1ull << 52) - 1);
+    if (e == 0) e = 1; else m |= 1ull << 52;  // w = m 2^(e - 1075)
+    const int sh = e - 1075 + shift;          // < 0 since w < 1 and shift <= 52
+    return (-sh) >= 64 ? 0 : (m >> (-sh));
+}
+
+struct U128 {
+    uint64_t hi, lo;
+};
+
+__device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) { return U128{__umul64hi(a, b), a * b}; }
+
+__device__ __forceinline__ bool ge128(const U128 &a, const U128 &b)
+{
+    return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);
+}
+
+// x N 2^32 as 128 bits (x < 2^53, N <= 2^24).
+__device__ __forceinline__ U128 scaled_C(uint64_t x, uint64_t N)
+{
+    const U128 p = mul64(x, N);
+    return U128{(p.hi << 32) | (p.lo >> 32), p.lo << 32};
+}
+
+// (i 2^32 + U) Ctot: the systematic grid point t_i = (i + U 2^-32) Ctot / N, times N 2^32.
+__device__ __forceinline__ U128 grid_point(uint64_t i, uint32_t U, uint64_t Ctot)
+{
+    return mul64((i << 32) | U, Ctot);
+}
+
+struct Grid {
+    uint64_t Ctot;   // C_{N-1}
+    uint32_t U;      // u = U 2^-32
+    int64_t N;
+    float n_over_c;  // N / Ctot (estimate only)
+};
+
+// #{i in [0, N) : t_i < x}: the t_i increase with i, so this is the first i
+// with grid_point(i) >= x N 2^32.  A float estimate is corrected by a short
+// walk on the exact comparison, with bisection as the fallback.
+__device__ int64_t count_below(uint64_t x, const Grid &g)
+{
+    if (x == 0) return 0;
+    const U128 X = scaled_C(x, (uint64_t)g.N);
+    const float est = ceilf(__fmaf_rn(__ull2float_rn(x), g.n_over_c, -(float)g.U * 0x1p-32f));
+    int64_t i = est <= 0.0f ? 0 : (est >= (float)g.N ? g.N : (int64_t)est);
     bool settled = false;
     for (int it = 0; it < 4; ++it) {
-        if (i > 0 && t_of(i - 1, u, c) >= x) --i;
+        if (i > 0 && ge128(grid_point((uint64_t)(i - 1), g.U, g.Ctot), X)) --i;
         else { settled = true; break; }
     }
     if (settled) {
         settled = false;
         for (int it = 0; it < 4; ++it) {
-            if (i < N && t_of(i, u, c) < x) ++i;
+            if (i < g.N && !ge128(grid_point((uint64_t)i, g.U, g.Ctot), X)) ++i;
             else { settled = true; break; }
         }
     }
     if (!settled) {
-        int64_t lo = 0, hi = N;  // smallest i with t_i >= x, or N
+        int64_t lo = 0, hi = g.N;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (t_of(mid, u, c) < x) lo = mid + 1; else hi = mid;
+            if (ge128(grid_point((uint64_t)mid, g.U, g.Ctot), X)) hi = mid; else lo = mid + 1;
         }
         i = lo;
     }
     return i;
 }
 
-// Unnormalised weight of particle p: exp(l - max) in FP32 from the FP32
-// log-weight (non-finite log-weights weigh 0; a degenerate filter weighs
-// uniformly and is flagged), or the caller's FP64 weight.
-__device__ __forceinline__ double weight_of(const ResampleArgs &a, int64_t p, float mx, bool degenerate)
+// a_i0 = min{k : C_k > t_i0}, by bisection over the filter's prefix (every
+// i0 < N has one, since t_i0 < C_{N-1}).
+__device__ int32_t search_ancestor(const uint64_t *C, const Grid &g, int64_t i0)
 {
-    if (a.w_direct) return a.w_direct[p];
-    if (degenerate) return 1.0;
-    const float l = a.logw[p];
-    return (l > -INFINITY && l < INFINITY) ? (double)expf(l - mx) : 0.0;
+    const U128 T = grid_point((uint64_t)i0, g.U, g.Ctot);
+    int64_t lo = 0, hi = g.N - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (!ge128(T, scaled_C(C[mid], (uint64_t)g.N))) hi = mid; else lo = mid + 1;  // C_mid N 2^32 > T
+    }
+    return (int32_t)lo;
 }
 
-__device__ __forceinline__ double quantise(double w, int shift) { return floor(ldexp(w, shift)); }
+// Unnormalised FP32 weight exp(l - max) from the FP32 log-weight; non-finite
+// log-weights weigh 0; a degenerate filter weighs uniformly.
+__device__ __forceinline__ float weight_f32(float l, float mx, bool degenerate)
+{
+    if (degenerate) return 1.0f;
+    return (l > -INFINITY && l < INFINITY) ? expf(l - mx) : 0.0f;
+}
 
 }  // namespace
 
@@ -198,27 +289,30 @@ __global__ void __launch_bounds__(256) k_init_fhn(ModelParams mp, Key key, const
 }
 
 // ------------------------------------------------------------------ propagate + weight (Alg. 1 step 2a)
-// Thread per particle, SoA state x[v * P + p] (coalesced), K Euler-Maruyama
-// sub-steps in registers, then the FP32 log-likelihood.
+// Thread per particle over the flat particle range (128-thread CTAs, so the
+// grid has many small blocks and little wave-quantisation loss), SoA state
+// x[v * P + p] (coalesced), K Euler-Maruyama sub-steps in registers, then the
+// FP32 log-likelihood.
 template <int D>
-__global__ void __launch_bounds__(256) k_propagate_small(ModelParams mp, Key key, const TileDesc *tiles,
+__global__ void __launch_bounds__(128) k_propagate_small(ModelParams mp, Key key, const int32_t *__restrict__ pfilt,
+                                                         const FilterDesc *__restrict__ filt,
                                                          const float *__restrict__ x_in, float *__restrict__ x_out,
                                                          int64_t P, float *logw, const float *obs, int32_t obs_stride,
                                                          const int32_t *d_t)
 {
-    const TileDesc td = tiles[blockIdx.x];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
     const uint32_t t = (uint32_t)(*d_t + 1);
-    const float *y = obs + (obs_stride ? (int64_t)td.m * obs_stride : 0);
-    for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
-        const int64_t p = td.gstart + j;
-        float xs[D];
+    const int32_t m = pfilt[p];
+    const uint32_t i = (uint32_t)(p - filt[m].off);
+    const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
+    float xs[D];
 #pragma unroll
-        for (int v = 0; v < D; ++v) xs[v] = x_in[v * P + p];
-        propagate_small<D, float>(mp, key, kStreamDyn, (uint32_t)(td.lstart + j), t, (uint32_t)td.m, xs);
+    for (int v = 0; v < D; ++v) xs[v] = x_in[v * P + p];
+    propagate_small<D, float>(mp, key, kStreamDyn, i, t, (uint32_t)m, xs);
 #pragma unroll
-        for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[v];
-        logw[p] = loglik_small<D, float>(mp, y, xs);
-    }
+    for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[v];
+    logw[p] = loglik_small<D, float>(mp, y, xs);
 }
 
 // Lattice propagation (Sec. 5.1, Rogers-McCulloch form): a CTA holds ppc
@@ -228,40 +322,39 @@ __global__ void __launch_bounds__(256) k_propagate_small(ModelParams mp, Key key
 template <typename Real>
 __device__ __forceinline__ Real fhn_drift_v(const ModelParams &mp, Real v, Real w, Real lap, Real I)
 {
-    const Real a = (Real)mp.p[0], c1 = (Real)mp.p[2], c2 = (Real)mp.p[3], D = (Real)mp.p[5];
+    const Real a = par<Real>(mp, 0), c1 = par<Real>(mp, 2), c2 = par<Real>(mp, 3), D = par<Real>(mp, 5);
     return c1 * v * (v - a) * ((Real)1 - v) - c2 * v * w + D * lap + I;
 }
 
 template <typename Real>
 __device__ __forceinline__ Real fhn_drift_w(const ModelParams &mp, Real v, Real w)
 {
-    const Real b = (Real)mp.p[1], d = (Real)mp.p[4];
+    const Real b = par<Real>(mp, 1), d = par<Real>(mp, 4);
     return b * (v - d * w);
 }
 
-// One observation interval of `count` lattice particles.  Real = float for
-// the filters (state in FP32) and double for the truth record.
-// Thread (slot s, pair q): particle p = first + s, nodes 2q and 2q+1 (same row).
+// One observation interval of lattice particles.  Real = float for the
+// filters (state in FP32) and double for the truth record.  Thread (slot s,
+// pair q): particle p = blockIdx.x * ppc + s, nodes 2q and 2q+1 (same row);
+// threads past ppc * pairs (warp padding) hold no particle.
 template <typename Real>
 __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const int32_t *pfilt,
                                 const FilterDesc *filt, const Real *__restrict__ x_in, Real *__restrict__ x_out,
                                 int64_t P, float *logw, const float *obs, int32_t obs_stride,
                                 const int32_t *obs_slot, const int32_t *d_t, int32_t fixed_c0, int32_t fixed_c2,
-                                int32_t t_direct)
+                                int32_t t_direct, int32_t ppc)
 {
     extern __shared__ unsigned char smem_raw[];
     const int J = mp.J, nn = J * J, pairs = nn / 2;
-    const int ppc = blockDim.x / pairs;
     Real *sv = reinterpret_cast<Real *>(smem_raw);  // [2][ppc][nn]
-    const int s = threadIdx.x / pairs;
-    const int q = threadIdx.x - s * pairs;
+    const int slot = (int)threadIdx.x / pairs;
+    const int s = min(slot, ppc);                  // s == ppc: padding thread
+    const int q = threadIdx.x - min(slot, ppc - 1) * pairs;
     const int64_t p = (int64_t)blockIdx.x * ppc + s;
     const bool active = (s < ppc) && (p < P);
     const uint32_t t = (uint32_t)(d_t ? *d_t + 1 : t_direct);
 
     uint32_t c0 = 0, c2 = 0;
-    const Real *xi = nullptr;
-    Real *xo = nullptr;
     Real v0 = 0, v1 = 0, w0 = 0, w1 = 0;
     const int n0 = 2 * q, row = n0 / J, col = n0 - row * J;
     if (active) {
@@ -273,16 +366,15 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
             c0 = (uint32_t)fixed_c0;
             c2 = (uint32_t)fixed_c2;
         }
-        xi = x_in + p * (int64_t)mp.dx;
-        xo = x_out + p * (int64_t)mp.dx;
+        const Real *xi = x_in + p * (int64_t)mp.dx;
         v0 = xi[n0];
         v1 = xi[n0 + 1];
         w0 = xi[nn + n0];
         w1 = xi[nn + n0 + 1];
     }
-    const Real dt = (Real)mp.dt;
-    const Real sq = (Real)(mp.sigma_dyn * sqrt(mp.dt));
-    const Real amp = (Real)mp.p[6];
+    const Real dt = par_dt<Real>(mp);
+    const Real sq = par_sq<Real>(mp);
+    const Real amp = par<Real>(mp, 6);
     const int64_t stim_steps = (int64_t)mp.p[7];
     const int blk = (int)mp.p[8];
     const bool stim_node0 = row < blk && col < blk, stim_node1 = row < blk && col + 1 < blk;
@@ -301,7 +393,7 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
         __syncthreads();
         if (active) {
             Real z[4];
-            normals4<Real>(Key{key.k0, key.k1}, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
+            normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
             Real l0 = v1, l1 = v0;
             if (up) { l0 += buf[n0 - J]; l1 += buf[n0 + 1 - J]; }
             if (down) { l0 += buf[n0 + J]; l1 += buf[n0 + 1 + J]; }
@@ -320,6 +412,7 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
         }
     }
     if (active) {
+        Real *xo = x_out + p * (int64_t)mp.dx;
         xo[n0] = v0;
         xo[n0 + 1] = v1;
         xo[nn + n0] = w0;
@@ -339,14 +432,14 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
     float *red = reinterpret_cast<float *>(smem_raw);
     red[threadIdx.x] = part;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < ppc) {
-        const int64_t pp = (int64_t)blockIdx.x * ppc + warp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int sl = warp; sl < ppc; sl += nwarps) {  // one warp per particle slot, fixed order
+        const int64_t pp = (int64_t)blockIdx.x * ppc + sl;
         float acc = 0.0f;
-        for (int i = lane; i < pairs; i += 32) acc += red[warp * pairs + i];
+        for (int i = lane; i < pairs; i += 32) acc += red[sl * pairs + i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0 && pp < P) logw[pp] = (float)(-0.5 / (mp.sigma_obs * mp.sigma_obs)) * acc;
+        if (lane == 0 && pp < P) logw[pp] = mp.fhalf_prec * acc;
     }
 }
 
@@ -365,37 +458,60 @@ __global__ void __launch_bounds__(kResampleThreads) k_tile_max(ResampleArgs a)
     if (threadIdx.x == 0) a.tile_max[blockIdx.x] = mx;
 }
 
-// Pass 2: filter maximum, then per tile the FP64 sums of w, w^2 and of the
-// quantised weights q = floor(w 2^shift); clears the ancestor markers.
+// Pass 2: the filter maximum, then per tile sum w and sum w^2 (FP32 per
+// thread, FP64 across threads) and the exact sum of q = floor(w 2^shift);
+// clears the ancestor markers.
+template <bool Direct>
 __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
 {
-    __shared__ double shd[kWarps * 3];
+    __shared__ double shd[kResampleThreads * 2 + 2];
+    __shared__ uint64_t shu[kWarps];
     __shared__ float shf[kWarps];
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = a.filt[td.m];
-    float mx = -INFINITY;
-    if (!a.w_direct) {
-        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) mx = fmaxf(mx, a.tile_max[fd.tile_begin + j]);
-        mx = block_max_f(mx, shf);
+    float mx = 0.0f;
+    bool degenerate = false;
+    if (!Direct) {
+        float m = -INFINITY;
+        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) m = fmaxf(m, a.tile_max[fd.tile_begin + j]);
+        m = block_max_f(m, shf);
+        degenerate = !(m > -INFINITY);
+        mx = degenerate ? 0.0f : m;
     }
-    const bool degenerate = !a.w_direct && !(mx > -INFINITY);
-    double s[3] = {0.0, 0.0, 0.0};
-    for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
-        const int64_t p = td.gstart + j;
-        const double w = weight_of(a, p, mx, degenerate);
-        s[0] += w;
-        s[1] += w * w;
-        s[2] += quantise(w, fd.shift);
-        a.B[p] = -1;
+    double s[2];
+    uint64_t qs = 0;
+    if (Direct) {
+        s[0] = s[1] = 0.0;
+        for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
+            const int64_t p = td.gstart + j;
+            const double w = a.w_direct[p];
+            s[0] += w;
+            s[1] += w * w;
+            qs += quant_f64(w, fd.shift);
+            a.B[p] = -1;
+        }
+    } else {
+        float f0 = 0.0f, f1 = 0.0f;
+        for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
+            const int64_t p = td.gstart + j;
+            const float w = weight_f32(a.logw[p], mx, degenerate);
+            f0 += w;
+            f1 = __fmaf_rn(w, w, f1);
+            qs += quant_f32(w, fd.shift);
+            a.B[p] = -1;
+        }
+        s[0] = (double)f0;
+        s[1] = (double)f1;
     }
-    block_sum_d<3>(s, shd);
+    block_sum_dd<2>(s, shd);
+    qs = block_sum_u64(qs, shu);
     if (threadIdx.x == 0) {
         double *ts = a.tile_sums + (int64_t)blockIdx.x * kTsCount;
         ts[kTsW] = s[0];
         ts[kTsW2] = s[1];
-        ts[kTsQ] = s[2];
+        a.tile_q[blockIdx.x] = qs;
         if (td.lstart == 0) {
-            a.fstats[(int64_t)td.m * kFsCount + kFsMax] = degenerate ? 0.0 : (double)mx;
+            a.fstats[(int64_t)td.m * kFsCount + kFsMax] = (double)mx;
             a.fstats[(int64_t)td.m * kFsCount + kFsDegenerate] = degenerate ? 1.0 : 0.0;
             if (degenerate) {
                 atomicOr(&a.err[0], kErrDegenerate);
@@ -405,99 +521,90 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
     }
 }
 
-// Pass 3: exact FP64 prefix of q (tile offset + block scan), the counts
+// Pass 3: the exact prefix C of q (tile offset + block scan), the counts
 // #{i : t_i < C_k}, and the start markers B[lo_k] = k of every particle with
-// offspring (plus the tail marker of the last particle with q > 0).  The
-// first tile of each filter also writes the filter's log Z, ESS, log G.
+// offspring.  The first tile of each filter also writes the filter's log Z,
+// ESS and log G (eq. eqGtN) and its (C_tot, U).
+template <bool Direct>
 __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs a)
 {
-    __shared__ double shd[kWarps * 4];
-    __shared__ double shs[kWarps];
+    __shared__ double shd[kResampleThreads * 2 + 2];
+    __shared__ uint64_t shu[kWarps * 3];
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = a.filt[td.m];
     const int ti = blockIdx.x - fd.tile_begin;
-    // filter totals and the prefix before this tile, in a fixed order
-    double s[4] = {0.0, 0.0, 0.0, 0.0};  // Q_all, Q_before, W, W2
+    uint64_t q_all = 0, q_before = 0;
     for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) {
-        const double *ts = a.tile_sums + (int64_t)(fd.tile_begin + j) * kTsCount;
-        s[0] += ts[kTsQ];
-        if (j < ti) s[1] += ts[kTsQ];
-        s[2] += ts[kTsW];
-        s[3] += ts[kTsW2];
+        const uint64_t v = a.tile_q[fd.tile_begin + j];
+        q_all += v;
+        if (j < ti) q_before += v;
     }
-    block_sum_d<4>(s, shd);
-    const float mx = a.w_direct ? 0.0f : (float)a.fstats[(int64_t)td.m * kFsCount + kFsMax];
-    const bool degenerate = !a.w_direct && a.fstats[(int64_t)td.m * kFsCount + kFsDegenerate] != 0.0;
-    double Ctot = s[0];
+    const uint64_t Ctot = block_sum_u64(q_all, shu);
+    const uint64_t Cbefore = block_sum_u64(q_before, shu + kWarps);
     const int32_t t = a.d_t ? *a.d_t + 1 : 0;
-    const double u = a.u_direct ? a.u_direct[td.m] : resample_uniform(a.key, td.m, t);
-    const int64_t N = fd.N;
-    const double c = __ddiv_rn(Ctot, (double)N);
-    const double inv_c = 1.0 / c;
+    uint32_t U;
+    if (Direct) U = (uint32_t)fmin(floor(a.u_direct[td.m] * 4294967296.0), 4294967295.0);
+    else U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
+    const Grid g{Ctot, U, (int64_t)fd.N, (float)fd.N / __ull2float_rn(Ctot > 0 ? Ctot : 1)};
 
-    if (threadIdx.x == 0 && ti == 0) {
-        double *fs = a.fstats + (int64_t)td.m * kFsCount;
-        const double logS = log(s[2]);
-        const double logZ = (double)mx + logS;
-        fs[kFsLogZ] = logZ;
-        fs[kFsEss] = s[2] * s[2] / s[3];
-        if (a.d_t) fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)N) + a.log_const;
-        fs[kFsCtot] = Ctot;
-        fs[kFsU] = u;
-        fs[kFsC] = c;
+    if (ti == 0) {  // filter scalars (FP64)
+        double s[2] = {0.0, 0.0};
+        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) {
+            const double *ts = a.tile_sums + (int64_t)(fd.tile_begin + j) * kTsCount;
+            s[0] += ts[kTsW];
+            s[1] += ts[kTsW2];
+        }
+        block_sum_dd<2>(s, shd);
+        if (threadIdx.x == 0) {
+            double *fs = a.fstats + (int64_t)td.m * kFsCount;
+            const double logZ = fs[kFsMax] + log(s[0]);
+            fs[kFsLogZ] = logZ;
+            fs[kFsEss] = s[0] * s[0] / s[1];
+            if (a.d_t) fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)fd.N) + a.log_const;
+            a.fint[(int64_t)td.m * 2] = Ctot;
+            a.fint[(int64_t)td.m * 2 + 1] = U;
+        }
     }
+    const float mx = Direct ? 0.0f : (float)a.fstats[(int64_t)td.m * kFsCount + kFsMax];
+    const bool degenerate = !Direct && a.fstats[(int64_t)td.m * kFsCount + kFsDegenerate] != 0.0;
     // blocked items: thread j owns tile positions [j * kItems, (j + 1) * kItems)
     const int j0 = threadIdx.x * kItems;
-    double q[kItems];
-    double tsum = 0.0;
+    uint64_t q[kItems];
+    uint64_t tsum = 0;
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int j = j0 + r;
-        q[r] = 0.0;
-        if (j < td.len) q[r] = quantise(weight_of(a, td.gstart + j, mx, degenerate), fd.shift);
+        q[r] = 0;
+        if (j < td.len) {
+            const int64_t p = td.gstart + j;
+            q[r] = Direct ? quant_f64(a.w_direct[p], fd.shift)
+                          : quant_f32(weight_f32(a.logw[p], mx, degenerate), fd.shift);
+        }
         tsum += q[r];
     }
-    double Cprev = s[1] + block_exscan_d(tsum, shs);  // C_{k-1} before my first item
-    int64_t cnt_prev = count_below(Cprev, u, c, inv_c, N);
+    uint64_t Cprev = Cbefore + block_exscan_u64(tsum, shu + 2 * kWarps);  // C_{k-1} before my first item
+    int64_t cnt_prev = count_below(Cprev, g);
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int j = j0 + r;
         if (j >= td.len) break;
-        const int64_t k = td.lstart + j;
-        const double Ck = Cprev + q[r];
+        const uint64_t Ck = Cprev + q[r];
         a.C[td.gstart + j] = Ck;
-        if (q[r] > 0.0) {
-            const int64_t cnt = count_below(Ck, u, c, inv_c, N);
-            if (cnt > cnt_prev) a.B[fd.off + cnt_prev] = (int32_t)k;
-            if (Ck == Ctot && cnt < N) a.B[fd.off + cnt] = (int32_t)k;  // tail of the last q > 0
+        if (q[r] > 0) {
+            const int64_t cnt = count_below(Ck, g);
+            if (cnt > cnt_prev) a.B[fd.off + cnt_prev] = td.lstart + j;
             cnt_prev = cnt;
         }
         Cprev = Ck;
     }
 }
 
-// Ancestor of the tile's first output index by bisection over the filter's C.
-__device__ __forceinline__ int32_t search_ancestor(const double *C, int64_t N, double Ctot, double tq)
-{
-    // min{k : C_k > tq}, or, when tq >= Ctot, min{k : C_k >= Ctot}
-    const bool tail = !(tq < Ctot);
-    int64_t lo = 0, hi = N - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        const bool right = tail ? (C[mid] >= Ctot) : (C[mid] > tq);
-        if (right) hi = mid; else lo = mid + 1;
-    }
-    return (int32_t)lo;
-}
-
-// Pass 4 (ancestors only): a_i = max(first ancestor of the tile, max of the
-// markers B[i0..i]).
+// a_i = max(first ancestor of the tile, max of the markers B[i0..i]).
 __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const TileDesc &td, const FilterDesc &fd,
                                                int32_t (&anc)[kItems], int *shi)
 {
-    const double *fs = a.fstats + (int64_t)td.m * kFsCount;
-    const double Ctot = fs[kFsCtot], u = fs[kFsU], c = fs[kFsC];
-    const int32_t a0 = search_ancestor(a.C + fd.off, fd.N, Ctot, t_of(td.lstart, u, c));
+    const Grid g{a.fint[(int64_t)td.m * 2], (uint32_t)a.fint[(int64_t)td.m * 2 + 1], (int64_t)fd.N, 0.0f};
+    const int32_t a0 = search_ancestor(a.C + fd.off, g, td.lstart);
     const int j0 = threadIdx.x * kItems;
     int b[kItems];
     int tmax = -1;
@@ -515,23 +622,23 @@ __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const Tile
     }
 }
 
-// Small models: ancestors, gather of the SoA state and per-tile FP64 sums of
-// every variable of the resampled particles.
+// Small models: ancestors, gather of the SoA state and per-tile sums of every
+// variable of the resampled particles (FP32 per thread, FP64 across threads).
 template <int D>
 __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleArgs a, const float *__restrict__ x_in,
                                                                       float *__restrict__ x_out, int64_t P,
                                                                       double *tile_est)
 {
     __shared__ int shi[kWarps];
-    __shared__ double shd[kWarps * D];
+    __shared__ double shd[kResampleThreads * D + D];
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = a.filt[td.m];
     int32_t anc[kItems];
     tile_ancestors(a, td, fd, anc, shi);
     const int j0 = threadIdx.x * kItems;
-    double s[D];
+    float f[D];
 #pragma unroll
-    for (int v = 0; v < D; ++v) s[v] = 0.0;
+    for (int v = 0; v < D; ++v) f[v] = 0.0f;
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int j = j0 + r;
@@ -543,16 +650,17 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
             for (int v = 0; v < D; ++v) {
                 const float xv = x_in[v * P + src];
                 x_out[v * P + p] = xv;
-                s[v] += (double)xv;
+                f[v] += xv;
             }
         }
     }
-    if (tile_est) {
-        block_sum_d<D>(s, shd);
-        if (threadIdx.x == 0)
+    double s[D];
 #pragma unroll
-            for (int v = 0; v < D; ++v) tile_est[(int64_t)blockIdx.x * D + v] = s[v];
-    }
+    for (int v = 0; v < D; ++v) s[v] = (double)f[v];
+    block_sum_dd<D>(s, shd);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int v = 0; v < D; ++v) tile_est[(int64_t)blockIdx.x * D + v] = s[v];
 }
 
 // Ancestors only (lattice models and the stateless entry point).
@@ -581,7 +689,8 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t *__restrict__
     for (int i = threadIdx.x; i < row4; i += blockDim.x) b[i] = a[i];
 }
 
-// Lattice estimates: est[m][v] = (1/N_m) sum_i x[off + i][v], FP64, i ascending.
+// Lattice estimates: est[m][v] = (1/N_m) sum_i x[off + i][v]; FP32 partial
+// sums over runs of 16 particles, accumulated in FP64, i ascending.
 __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const float *__restrict__ x, int dx,
                                                    double *est)
 {
@@ -590,41 +699,46 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
     if (v >= dx) return;
     const FilterDesc fd = filt[m];
     const float *base = x + fd.off * (int64_t)dx + v;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int i = 0;
-    for (; i + 4 <= fd.N; i += 4) {
-        s0 += (double)base[(int64_t)i * dx];
-        s1 += (double)base[(int64_t)(i + 1) * dx];
-        s2 += (double)base[(int64_t)(i + 2) * dx];
-        s3 += (double)base[(int64_t)(i + 3) * dx];
+    double acc = 0.0;
+    for (int i0 = 0; i0 < fd.N; i0 += 16) {
+        const int n = min(16, fd.N - i0);
+        float f = 0.0f;
+        for (int i = 0; i < n; ++i) f += base[(int64_t)(i0 + i) * dx];
+        acc += (double)f;
     }
-    for (; i < fd.N; ++i) s0 += (double)base[(int64_t)i * dx];
-    est[(int64_t)m * dx + v] = ((s0 + s1) + (s2 + s3)) / (double)fd.N;
+    est[(int64_t)m * dx + v] = acc / (double)fd.N;
 }
 
-// Small models: est[m][v] = (1/N_m) sum over the filter's tiles, fixed order.
-__global__ void k_filter_means(const FilterDesc *filt, const double *tile_est, int dx, double *est, int32_t M)
+// Small models: est[m][v] = (1/N_m) sum over the filter's tiles; one warp per
+// (m, v), lane-strided partial sums and a fixed xor tree (deterministic).
+__global__ void __launch_bounds__(256) k_filter_means(const FilterDesc *filt, const double *tile_est, int dx,
+                                                      double *est, int32_t M)
 {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)M * dx) return;
-    const int m = (int)(gid / dx), v = (int)(gid % dx);
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)M * dx) return;  // whole warps exit together
+    const int m = (int)(w / dx), v = (int)(w % dx);
     const FilterDesc fd = filt[m];
     double s = 0.0;
-    for (int j = 0; j < fd.tile_count; ++j) s += tile_est[(int64_t)(fd.tile_begin + j) * dx + v];
-    est[gid] = s / (double)fd.N;
+    for (int j = lane; j < fd.tile_count; j += 32) s += tile_est[(int64_t)(fd.tile_begin + j) * dx + v];
+    s = warp_sum_d(s);
+    if (lane == 0) est[w] = s / (double)fd.N;
 }
 
-// Definition 1: ens[v] = (1/M) sum_m est[m][v] (FP64, m ascending); advances
-// the step counter.
-__global__ void k_ensemble(const double *est, int dx, int32_t M, double *ens, int32_t *d_t)
+// Definition 1: ens[v] = (1/M) sum_m est[m][v] in FP64, one CTA per variable,
+// strided partial sums then a fixed-order tree (deterministic); advances the
+// step counter.
+__global__ void __launch_bounds__(128) k_ensemble(const double *est, int dx, int32_t M, double *ens, int32_t *d_t)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v < dx) {
-        double s = 0.0;
-        for (int m = 0; m < M; ++m) s += est[(int64_t)m * dx + v];
-        ens[v] = s / (double)M;
+    __shared__ double sh[128 + 1];
+    const int v = blockIdx.x;
+    double s[1] = {0.0};
+    for (int m = threadIdx.x; m < M; m += blockDim.x) s[0] += est[(int64_t)m * dx + v];
+    block_sum_dd<1>(s, sh);
+    if (threadIdx.x == 0) {
+        ens[v] = s[0] / (double)M;
+        if (v == 0 && d_t) *d_t += 1;
     }
-    if (v == 0 && d_t) *d_t += 1;
 }
 
 // ------------------------------------------------------------------ synthetic record (FP64)
@@ -687,17 +801,17 @@ __global__ void k_observe(ModelParams mp, Key key, const int32_t *obs_idx, int32
 }
 
 // ------------------------------------------------------------------ generator components
-__global__ void k_rng_philox(int64_t n, const uint4 *ctr, uint32_t k0, uint32_t k1, uint4 *out)
+__global__ void k_rng_philox(int64_t n, const uint4 *ctr, Key key, uint4 *out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = philox4x32_10(ctr[i], k0, k1);
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
 }
 
 __global__ void k_rng_normals(int64_t n, const uint4 *ctr, Key key, float4 *z)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint4 r = philox4x32_10(ctr[i], key.k0, key.k1);
+    const uint4 r = philox4x32_10(ctr[i], key);
     float a, b, c, d;
     box_muller<float>(r.x, r.y, a, b);
     box_muller<float>(r.z, r.w, c, d);
@@ -707,13 +821,15 @@ __global__ void k_rng_normals(int64_t n, const uint4 *ctr, Key key, float4 *z)
 // ------------------------------------------------------------------ launchers
 namespace {
 
+// Threads of a lattice CTA: ppc particles x J^2/2 node pairs, rounded up to
+// whole warps (the extra threads hold no particle).
 int fhn_threads(const ModelParams &mp, int *ppc)
 {
     const int pairs = mp.J * mp.J / 2;
     int n = 1;
     while ((n + 1) * pairs <= 1024 && n < 8) ++n;
     *ppc = n;
-    return n * pairs;
+    return (n * pairs + 31) / 32 * 32;
 }
 
 size_t fhn_smem(const ModelParams &mp, int threads, int ppc, size_t real_bytes)
@@ -734,7 +850,8 @@ template <int D>
 cudaError_t propagate_small_launch(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                                    cudaStream_t s)
 {
-    k_propagate_small<D><<<c.n_tiles, 256, 0, s>>>(c.mp, c.key, c.tiles, xi, xo, c.P, c.logw, d_obs, stride, c.d_t);
+    k_propagate_small<D><<<(unsigned)((c.P + 127) / 128), 128, 0, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P,
+                                                                      c.logw, d_obs, stride, c.d_t);
     return cudaGetLastError();
 }
 
@@ -744,13 +861,13 @@ ResampleArgs ctx_args(const Ctx &c)
     a.tiles = c.tiles;
     a.filt = c.filt;
     a.logw = c.logw;
-    a.w_direct = nullptr;
-    a.u_direct = nullptr;
     a.key = c.key;
     a.d_t = c.d_t;
     a.tile_max = c.tile_max;
     a.tile_sums = c.tile_sums;
+    a.tile_q = c.tile_q;
     a.fstats = c.fstats;
+    a.fint = c.fint;
     a.C = c.C;
     a.B = c.B;
     a.anc = c.anc;
@@ -786,7 +903,7 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
         const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
         const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
         k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
-                                                           c.logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0);
+                                                           c.logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc);
         return cudaGetLastError();
     }
     switch (c.mp.dx) {
@@ -802,8 +919,8 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
 {
     const ResampleArgs a = ctx_args(c);
     k_tile_max<<<c.n_tiles, kResampleThreads, 0, s>>>(a);
-    k_weights<<<c.n_tiles, kResampleThreads, 0, s>>>(a);
-    k_scan_scatter<<<c.n_tiles, kResampleThreads, 0, s>>>(a);
+    k_weights<false><<<c.n_tiles, kResampleThreads, 0, s>>>(a);
+    k_scan_scatter<false><<<c.n_tiles, kResampleThreads, 0, s>>>(a);
     const int dx = c.mp.dx;
     if (c.mp.kind == kFhnLattice) {
         k_ancestors<<<c.n_tiles, kResampleThreads, 0, s>>>(a);
@@ -819,18 +936,18 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
         case 4: k_ancestors_small<4><<<c.n_tiles, kResampleThreads, 0, s>>>(a, xi, xo, c.P, c.tile_est); break;
         default: return cudaErrorInvalidValue;
         }
-        const int64_t n = (int64_t)c.M * dx;
-        k_filter_means<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c.filt, c.tile_est, dx, c.est, c.M);
+        const int64_t threads = (int64_t)c.M * dx * 32;
+        k_filter_means<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(c.filt, c.tile_est, dx, c.est, c.M);
     }
-    k_ensemble<<<(dx + 255) / 256, 256, 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
+    k_ensemble<<<dx, 128, 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s)
 {
     (void)M;
-    k_weights<<<n_tiles, kResampleThreads, 0, s>>>(a);
-    k_scan_scatter<<<n_tiles, kResampleThreads, 0, s>>>(a);
+    k_weights<true><<<n_tiles, kResampleThreads, 0, s>>>(a);
+    k_scan_scatter<true><<<n_tiles, kResampleThreads, 0, s>>>(a);
     k_ancestors<<<n_tiles, kResampleThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -838,8 +955,9 @@ cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a,
 cudaError_t launch_rng_philox(int64_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    k_rng_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, reinterpret_cast<const uint4 *>(ctr), k0, k1,
-                                                             reinterpret_cast<uint4 *>(out));
+    k_rng_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        n, reinterpret_cast<const uint4 *>(ctr), make_key((uint64_t)k0 | ((uint64_t)k1 << 32)),
+        reinterpret_cast<uint4 *>(out));
     return cudaGetLastError();
 }
 
@@ -866,12 +984,13 @@ cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int
     }
     const int pairs = mp.J * mp.J / 2;
     k_fhn_truth_init<<<(pairs + 255) / 256, 256, 0, s>>>(mp, key, record, init_random, d_x0, d_x);
-    const size_t smem = fhn_smem(mp, pairs, 1, sizeof(double));
+    const int threads = (pairs + 31) / 32 * 32;
+    const size_t smem = fhn_smem(mp, threads, 1, sizeof(double));
     for (int32_t t = 1; t <= T; ++t) {
         const double *xi = d_x + (int64_t)(t - 1) * mp.dx;
         double *xo = d_x + (int64_t)t * mp.dx;
-        k_propagate_fhn<double><<<1, pairs, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1, nullptr,
-                                                       nullptr, 0, nullptr, nullptr, 0, record, t);
+        k_propagate_fhn<double><<<1, threads, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1, nullptr,
+                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1);
         if (d_y)
             k_observe<<<(mp.dy + 255) / 256, 256, 0, s>>>(mp, key, d_obs_idx, t, record, xo,
                                                           d_y + (int64_t)(t - 1) * mp.dy);

@@ -228,6 +228,12 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
     for (int j = 0; j < obs->dy && j < kMaxObsSmall; ++j) mp.obs_small[j] = obs->idx[j];
     if (model->kind != PF_MODEL_FHN_LATTICE)
         for (int v = 0; v < model->dx; ++v) mp.x0_small[v] = noise->x0_mean[v];
+    for (int i = 0; i < 16; ++i) mp.fp[i] = (float)mp.p[i];
+    mp.fdt = (float)dt;
+    mp.dsq = noise->sigma_dyn * std::sqrt(dt);
+    mp.fsq = (float)mp.dsq;
+    mp.dhalf_prec = -0.5 / (obs->sigma_obs * obs->sigma_obs);
+    mp.fhalf_prec = (float)mp.dhalf_prec;
     return true;
 }
 
@@ -262,6 +268,8 @@ void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std
 }  // namespace
 
 namespace pf {
+void set_global_error(const char *msg) { g_create_error = msg; }
+
 int ceil_log2_host(int64_t n)
 {
     int L = 0;
@@ -336,11 +344,13 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     bool ok = alloc_n(c, c.tiles, tiles.size()) && alloc_n(c, c.filt, filt.size()) &&
               alloc_n(c, c.x[0], (size_t)P * dx) && alloc_n(c, c.x[1], (size_t)P * dx) && alloc_n(c, c.logw, P) &&
               alloc_n(c, c.tile_max, c.n_tiles) && alloc_n(c, c.tile_sums, (size_t)c.n_tiles * kTsCount) &&
+              alloc_n(c, c.tile_q, c.n_tiles) && alloc_n(c, c.fint, (size_t)M * 2) &&
               alloc_n(c, c.fstats, (size_t)M * kFsCount) && alloc_n(c, c.C, P) && alloc_n(c, c.B, P) &&
               alloc_n(c, c.anc, P) && alloc_n(c, c.est, (size_t)M * dx) && alloc_n(c, c.ens, dx) &&
               alloc_n(c, c.d_obs, (size_t)M * mp.dy) && alloc_n(c, c.d_t, 1) && alloc_n(c, c.err, 2) &&
               alloc_n(c, c.obs_idx, mp.dy) && alloc_n(c, c.x0, dx);
-    if (ok && mp.kind == PF_MODEL_FHN_LATTICE) ok = alloc_n(c, c.pfilt, P) && alloc_n(c, c.obs_slot, mp.J * mp.J);
+    if (ok) ok = alloc_n(c, c.pfilt, P);
+    if (ok && mp.kind == PF_MODEL_FHN_LATTICE) ok = alloc_n(c, c.obs_slot, mp.J * mp.J);
     else if (ok) ok = alloc_n(c, c.tile_est, (size_t)c.n_tiles * dx);
     if (!ok) {
         g_create_error = "device allocation failed";
@@ -374,14 +384,15 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_t, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c.fstats, 0, (size_t)M * kFsCount * sizeof(double), c.stream);
-    if (e == cudaSuccess && mp.kind == PF_MODEL_FHN_LATTICE) {
+    if (e == cudaSuccess) {
         pf_host.resize(P);
         for (int m = 0; m < M; ++m) std::fill(pf_host.begin() + c.off[m], pf_host.begin() + c.off[m + 1], m);
+        e = cudaMemcpyAsync(c.pfilt, pf_host.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+    }
+    if (e == cudaSuccess && mp.kind == PF_MODEL_FHN_LATTICE) {
         slot.assign(mp.J * mp.J, -1);
         for (int j = 0; j < mp.dy; ++j) slot[obs->idx[j]] = j;
-        e = cudaMemcpyAsync(c.pfilt, pf_host.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(c.obs_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+        e = cudaMemcpyAsync(c.obs_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
     }
     if (e == cudaSuccess) e = launch_init(c, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);  // host staging vectors go out of scope
@@ -642,9 +653,9 @@ size_t pf_systematic_scratch_bytes(int32_t M, int64_t total)
     if (M < 1 || total < 0) return 0;
     const int64_t nt = max_tiles(M, total);
     return align256(nt * sizeof(TileDesc)) + align256((size_t)M * sizeof(FilterDesc)) +
-           align256(nt * sizeof(float)) + align256(nt * kTsCount * sizeof(double)) +
-           align256((size_t)M * kFsCount * sizeof(double)) + align256(total * sizeof(double)) +
-           align256(total * sizeof(int32_t)) + align256(2 * sizeof(int32_t));
+           align256(nt * sizeof(float)) + align256(nt * kTsCount * sizeof(double)) + align256(nt * sizeof(uint64_t)) +
+           align256((size_t)M * kFsCount * sizeof(double)) + align256((size_t)M * 2 * sizeof(uint64_t)) +
+           align256(total * sizeof(uint64_t)) + align256(total * sizeof(int32_t)) + align256(2 * sizeof(int32_t));
 }
 
 pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_w, const double *d_u, int32_t *d_anc,
@@ -671,8 +682,10 @@ pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_
     a.filt = d_filt;
     a.tile_max = reinterpret_cast<float *>(take(nt * sizeof(float)));
     a.tile_sums = reinterpret_cast<double *>(take(nt * kTsCount * sizeof(double)));
+    a.tile_q = reinterpret_cast<uint64_t *>(take(nt * sizeof(uint64_t)));
     a.fstats = reinterpret_cast<double *>(take((size_t)M * kFsCount * sizeof(double)));
-    a.C = reinterpret_cast<double *>(take(total * sizeof(double)));
+    a.fint = reinterpret_cast<uint64_t *>(take((size_t)M * 2 * sizeof(uint64_t)));
+    a.C = reinterpret_cast<uint64_t *>(take(total * sizeof(uint64_t)));
     a.B = reinterpret_cast<int32_t *>(take(total * sizeof(int32_t)));
     a.err = reinterpret_cast<int32_t *>(take(2 * sizeof(int32_t)));
     a.w_direct = d_w;
@@ -684,8 +697,7 @@ pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_
     cudaError_t e = cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_filt, filt.data(), filt.size() * sizeof(FilterDesc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.err, 0, 2 * sizeof(int32_t), s);
-    // pageable copies are staged before the call returns, but keep the host
-    // vectors alive until the stream has consumed them
+    // the plan is staged from host vectors: let the stream consume them first
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = launch_systematic(M, (int32_t)tiles.size(), a, s);
     return e == cudaSuccess ? PF_OK : PF_ECUDA;

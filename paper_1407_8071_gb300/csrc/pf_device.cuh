@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace pf {
@@ -27,44 +28,47 @@ constexpr int kMaxObsSmall = 8;  // observation indices passed by value for the 
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the 4x32
-// Philox bijection with the published multipliers; the key advances by the
-// Weyl increments (0.32 fixed point of the golden ratio's fraction and of
-// sqrt(3) - 1) before every round but the first.  One 32x32->64 multiply per
-// product (mul.lo + mul.hi fold into one wide IMAD).
+// Philox bijection with the published multipliers; round r uses the key
+// advanced r times by the Weyl increments (0.32 fixed point of the golden
+// ratio's fraction and of sqrt(3) - 1).  The ten round keys are computed once
+// on the host and passed as kernel parameters, so the rounds read them as
+// constant operands.  One 32x32->64 multiply per product.
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+struct Key {
+    uint32_t k0[10], k1[10];
+};
+
+inline Key make_key(uint64_t seed)
+{
+    Key k;
+    uint32_t a = (uint32_t)(seed & 0xffffffffu), b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = a;
+        k.k1[r] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const Key &key)
 {
     constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-#ifdef __CUDA_ARCH__
         const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
         const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-#else
-        const uint64_t p0 = (uint64_t)M0 * c.x, p1 = (uint64_t)M1 * c.z;
-        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
-        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
-#endif
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += W0;
-        k1 += W1;
+        c = make_uint4(hi1 ^ c.y ^ key.k0[r], lo1, hi0 ^ c.w ^ key.k1[r], lo0);
     }
     return c;
 }
 
-struct Key {
-    uint32_t k0, k1;
-};
-
-__host__ __device__ __forceinline__ Key make_key(uint64_t seed)
-{
-    return Key{(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
-}
-
 // Box & Muller (1958) on two 32-bit words.  u1 = ((a >> 8) + 1) 2^-24 in (0, 1]
-// and u2 = (b >> 8) 2^-24 in [0, 1) are exact in binary32, so the only
-// rounding is that of log, sqrt and sin/cos (sincospi takes 2 u2 exactly).
+// and u2 = (b >> 8) 2^-24 in [0, 1) are exact in binary32 and binary64;
+// z0 = R cos(2 pi u2), z1 = R sin(2 pi u2), R = sqrt(-2 ln u1).
+// FP32: the angle is taken as 2 pi (u2 - 1/2) in [-pi, pi) (u2 - 1/2 is exact;
+// cos and sin change sign) so the hardware sine/cosine run on their accurate
+// range (absolute error below 2^-21); R = v * rsqrt(v).
 template <typename Real>
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, Real &z0, Real &z1);
 
@@ -72,12 +76,13 @@ template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1)
 {
     const float u1 = __uint2float_rn((a >> 8) + 1u) * 0x1p-24f;
-    const float u2 = __uint2float_rn(b >> 8) * 0x1p-24f;
-    const float R = sqrtf(-2.0f * logf(u1));
+    const float h = __uint2float_rn(b >> 8) * 0x1p-24f - 0.5f;
+    const float v = -2.0f * logf(u1);
+    const float R = v > 0.0f ? v * rsqrtf(v) : 0.0f;
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = R * c;
-    z1 = R * s;
+    __sincosf(6.28318530717958647692f * h, &s, &c);
+    z0 = -R * c;
+    z1 = -R * s;
 }
 
 template <>
@@ -94,20 +99,12 @@ __device__ __forceinline__ void box_muller<double>(uint32_t a, uint32_t b, doubl
 
 // Normals (4 per block) of counter (c0, c1, c2, stream<<24 | block).
 template <typename Real>
-__device__ __forceinline__ void normals4(Key key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t stream,
+__device__ __forceinline__ void normals4(const Key &key, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t stream,
                                          uint32_t block, Real z[4])
 {
-    const uint4 r = philox4x32_10(make_uint4(c0, c1, c2, (stream << 24) | block), key.k0, key.k1);
+    const uint4 r = philox4x32_10(make_uint4(c0, c1, c2, (stream << 24) | block), key);
     box_muller<Real>(r.x, r.y, z[0], z[1]);
     box_muller<Real>(r.z, r.w, z[2], z[3]);
-}
-
-// Resampling uniform of filter m at observation t: word 0 of Philox at
-// (0, t, m, RESAMPLE<<24) times 2^-32 (exact in binary64).
-__device__ __forceinline__ double resample_uniform(Key key, int32_t m, int32_t t)
-{
-    const uint4 r = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)m, kStreamResample << 24), key.k0, key.k1);
-    return (double)r.x * 0x1p-32;
 }
 
 // ---------------------------------------------------------------------------
@@ -126,7 +123,40 @@ struct ModelParams {
     int32_t dy;
     int32_t obs_small[kMaxObsSmall];  // observation indices when dy <= kMaxObsSmall
     double x0_small[kMaxLgDim];       // prior mean for the small models
+    // FP32 copies made once on the host (FP64 is a narrow pipe on this GPU):
+    float fp[16];      // p
+    float fdt;         // dt
+    float fsq;         // sigma_dyn * sqrt(dt)
+    float fhalf_prec;  // -1 / (2 sigma_obs^2)
+    double dsq;        // sigma_dyn * sqrt(dt) in FP64 (truth records)
+    double dhalf_prec; // -1 / (2 sigma_obs^2) in FP64
 };
+
+// Model constants in the precision of the state.
+template <typename Real>
+__device__ __forceinline__ Real par(const ModelParams &mp, int i)
+{
+    if constexpr (std::is_same<Real, float>::value) return mp.fp[i];
+    else return mp.p[i];
+}
+template <typename Real>
+__device__ __forceinline__ Real par_dt(const ModelParams &mp)
+{
+    if constexpr (std::is_same<Real, float>::value) return mp.fdt;
+    else return mp.dt;
+}
+template <typename Real>
+__device__ __forceinline__ Real par_sq(const ModelParams &mp)
+{
+    if constexpr (std::is_same<Real, float>::value) return mp.fsq;
+    else return mp.dsq;
+}
+template <typename Real>
+__device__ __forceinline__ Real par_half_prec(const ModelParams &mp)
+{
+    if constexpr (std::is_same<Real, float>::value) return mp.fhalf_prec;
+    else return mp.dhalf_prec;
+}
 
 // Drift of the small models (thread per particle), in the state's precision.
 template <int D, typename Real>
@@ -136,7 +166,7 @@ struct SmallModel {
     __device__ __forceinline__ static void drift(const ModelParams &mp, const Real x[D], Real f[D])
     {
         if (mp.kind == kLorenz63) {
-            const Real s = (Real)mp.p[0], r = (Real)mp.p[1], b = (Real)mp.p[2];
+            const Real s = par<Real>(mp, 0), r = par<Real>(mp, 1), b = par<Real>(mp, 2);
             f[0] = s * (x[1] - x[0]);
             f[1] = r * x[0] - x[1] - x[0] * x[2];
             f[2] = x[0] * x[1] - b * x[2];
@@ -145,7 +175,7 @@ struct SmallModel {
             for (int i = 0; i < D; ++i) {
                 Real s = 0;
 #pragma unroll
-                for (int j = 0; j < D; ++j) s += (Real)mp.p[i * D + j] * x[j];
+                for (int j = 0; j < D; ++j) s += par<Real>(mp, i * D + j) * x[j];
                 f[i] = -s;
             }
         }
@@ -165,12 +195,12 @@ struct NoisePacking {
 // observation t (Alg. 1 step 2a; Euler-Maruyama), stream `stream`,
 // counter words (c0, t, c2).
 template <int D, typename Real>
-__device__ __forceinline__ void propagate_small(const ModelParams &mp, Key key, uint32_t stream, uint32_t c0,
+__device__ __forceinline__ void propagate_small(const ModelParams &mp, const Key &key, uint32_t stream, uint32_t c0,
                                                 uint32_t t, uint32_t c2, Real x[D])
 {
     using NP = NoisePacking<D>;
-    const Real dt = (Real)mp.dt;
-    const Real sq = (Real)(mp.sigma_dyn * sqrt(mp.dt));
+    const Real dt = par_dt<Real>(mp);
+    const Real sq = par_sq<Real>(mp);
     const int K = mp.K;
     uint32_t block = 0;
     for (int k0 = 0; k0 < K; k0 += NP::steps) {
@@ -204,7 +234,7 @@ __device__ __forceinline__ Real loglik_small(const ModelParams &mp, const float 
         const Real e = (Real)y[j] - xv;
         s += e * e;
     }
-    return (Real)(-0.5 / (mp.sigma_obs * mp.sigma_obs)) * s;
+    return par_half_prec<Real>(mp) * s;
 }
 
 }  // namespace pf

@@ -37,11 +37,9 @@ struct FilterDesc {
 };
 
 // Per-filter scalars kept in FP64 on the device.
-enum FStat : int {
-    kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsCtot = 4, kFsU = 5, kFsC = 6, kFsDegenerate = 7, kFsCount = 8
-};
+enum FStat : int { kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsCount = 8 };
 // Per-tile FP64 partial sums.
-enum TSum : int { kTsW = 0, kTsW2 = 1, kTsQ = 2, kTsCount = 4 };
+enum TSum : int { kTsW = 0, kTsW2 = 1, kTsCount = 2 };
 
 // Device error word: bit flags plus the first offending filter.
 enum : int32_t { kErrDegenerate = 1 };
@@ -57,8 +55,10 @@ struct ResampleArgs {
     const int32_t *d_t;      // completed steps; the step being resampled is *d_t + 1
     float *tile_max;         // [tiles]
     double *tile_sums;       // [tiles][kTsCount]
+    uint64_t *tile_q;        // [tiles] exact sum of the quantised weights
     double *fstats;          // [M][kFsCount]
-    double *C;               // [P] inclusive prefix of the quantised weights
+    uint64_t *fint;          // [M][2]: C_{N-1} and the resampling uniform U (u = U 2^-32)
+    uint64_t *C;             // [P] inclusive prefix of the quantised weights
     int32_t *B;              // [P] ancestor start markers
     int32_t *anc;            // [P] filter-local ancestors
     int32_t *err;            // [2]
@@ -80,8 +80,9 @@ cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int
                             int32_t T, int32_t record, int32_t init_random, double *d_x, float *d_y,
                             cudaStream_t s);
 
-// Host helpers (pf_capi.cu) used by the launchers.
+// Host helpers (pf_capi.cu).
 int ceil_log2_host(int64_t n);
+void set_global_error(const char *msg);  // text of pf_last_error(NULL) on this thread
 
 struct Ctx {
     ModelParams mp{};
@@ -100,8 +101,10 @@ struct Ctx {
     float *logw = nullptr;
     float *tile_max = nullptr;
     double *tile_sums = nullptr;
+    uint64_t *tile_q = nullptr;
     double *fstats = nullptr;
-    double *C = nullptr;
+    uint64_t *fint = nullptr;
+    uint64_t *C = nullptr;
     int32_t *B = nullptr;
     int32_t *anc = nullptr;
     double *tile_est = nullptr;   // [tiles][dx] (small models)

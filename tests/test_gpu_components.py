@@ -2,11 +2,15 @@
 
 Tolerances (FP32 state on the GPU vs FP64 in the oracle):
 * Philox words: bit-exact.
-* Box-Muller normals: |z_gpu - z| <= 4e-6 (|z| + 1) -- logf/sqrtf/sincospif
-  rounding on exact 24-bit uniforms.
+* Box-Muller normals: |z_gpu - z| <= 1e-5 (|z| + 1): the uniforms are exact;
+  FP32 log (about 1 ulp), v rsqrt(v) (about 2 ulp) and the hardware sine/cosine
+  on [-pi, pi) (absolute error below 2^-21, plus pi 2^-24 from rounding the
+  angle) times R <= sqrt(48 ln 2) = 5.77 bound the error by ~4e-6 + 1e-6 |z|.
 * Propagated states after a full observation interval from identical inputs:
   |x_gpu - x| <= 1e-5 max(|x|, rms of the component over the batch).
-* Log-weights: |l_gpu - l| <= 1e-5 max(|l|, 1).
+* Log-weights: |l_gpu - l| <= 1e-5 max(|l|, 1), with l the oracle's likelihood
+  at the GPU's propagated states (so the check isolates the weight step; the
+  states are checked on their own above).
 """
 import numpy as np
 import pytest
@@ -57,7 +61,7 @@ def test_normals_match_oracle():
     torch.cuda.synchronize()
     z = oracle.normals(ctr, seed)
     err = np.abs(d_z.cpu().numpy() - z) / (np.abs(z) + 1.0)
-    assert err.max() <= 4e-6, err.max()
+    assert err.max() <= 1e-5, err.max()
 
 
 # ------------------------------------------------------------------ prior and propagation
@@ -78,7 +82,8 @@ def test_prior_matches_oracle(name):
         xg = f.get_state()
     pid, fid = ids(N, M)
     xo = oracle.prior(spec, pid, fid, seed)
-    assert_state_close(xg, xo, rtol=1e-6)
+    # x0 = mean + sigma0 z: the normals' error bound 1e-5 (|z| + 1) carries over
+    assert_state_close(xg, xo, rtol=1e-5)
 
 
 @pytest.mark.parametrize("name", list(SMALL_SPECS))
@@ -96,7 +101,8 @@ def test_propagate_and_weights_match_oracle(name, t):
     pid, fid = ids(N, M)
     xo = oracle.propagate(spec, x0.astype(np.float64), pid, fid, t, seed)
     assert_state_close(xg, xo)
-    lo = oracle.loglik(spec, xo, y.astype(np.float64))
+    # a3 on its own: the oracle's likelihood at the GPU's propagated states
+    lo = oracle.loglik(spec, xg.astype(np.float64), y.astype(np.float64))
     assert np.max(np.abs(lg - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
 
 
@@ -120,14 +126,14 @@ def fhn_spec(J, **kw):
     return W.fhn_lattice(J=J, **kw)
 
 
-@pytest.mark.parametrize("J,M,N", [(2, 2, 5), (8, 3, 40), (20, 2, 9), (40, 1, 3)])
+@pytest.mark.parametrize("J,M,N", [(2, 2, 5), (2, 3, 17), (8, 3, 40), (20, 2, 9), (40, 1, 3)])
 def test_fhn_prior_and_propagate_match_oracle(J, M, N):
     spec = fhn_spec(J)
     seed = 99
     with pf.EnsembleFilter(spec, M, N, seed) as f:
         x_init = f.get_state()
         pid, fid = ids(N, M)
-        assert_state_close(x_init, oracle.prior(spec, pid, fid, seed), rtol=1e-6)
+        assert_state_close(x_init, oracle.prior(spec, pid, fid, seed), rtol=1e-5)
         x0 = W.random_states(spec, M * N, seed=J).astype(np.float32)
         y = np.random.default_rng(J).uniform(0.0, 1.0, spec.dy).astype(np.float32)
         for t in (1, 9):  # t = 9 crosses the end of the stimulus (200 sub-steps)
@@ -137,7 +143,7 @@ def test_fhn_prior_and_propagate_match_oracle(J, M, N):
             lg = f.get_logw()
             xo = oracle.propagate(spec, x0.astype(np.float64), pid, fid, t, seed)
             assert_state_close(xg, xo)
-            lo = oracle.loglik(spec, xo, y.astype(np.float64))
+            lo = oracle.loglik(spec, xg.astype(np.float64), y.astype(np.float64))
             assert np.max(np.abs(lg - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
             f.resample()
 
@@ -157,7 +163,7 @@ def test_fhn_full_size_sampled():
     pid, fid = (sample % N).astype(np.int32), (sample // N).astype(np.int32)
     xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid, fid, 1, seed)
     assert_state_close(xg[sample], xo)
-    lo = oracle.loglik(spec, xo, y[0].astype(np.float32).astype(np.float64))
+    lo = oracle.loglik(spec, xg[sample].astype(np.float64), y[0].astype(np.float32).astype(np.float64))
     assert np.max(np.abs(lg[sample] - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
 
 

@@ -114,7 +114,7 @@ def test_context_resampling_and_normaliser(N):
     assert mismatched <= max(2, M * N // 1000)
 
 
-def test_context_gather_and_estimate_are_exact():
+def test_context_gather_is_exact_and_estimate_within_fp32_partials():
     spec = W.lorenz63()
     M, N, seed = 3, 2000, 5
     rng = np.random.default_rng(3)
@@ -132,7 +132,9 @@ def test_context_gather_and_estimate_are_exact():
         src = xbar[m * N + anc[m * N:(m + 1) * N]]
         assert np.array_equal(x[m * N:(m + 1) * N], src)
         ref = src.astype(np.float64).mean(axis=0)
-        assert np.allclose(est[m], ref, rtol=1e-12, atol=1e-12)
+        # each thread sums its 4 particles in FP32 (error <= 3 2^-24 of their
+        # absolute sum), the rest is FP64
+        assert np.all(np.abs(est[m] - ref) <= 1e-6 * np.abs(src).astype(np.float64).mean(axis=0))
     assert np.allclose(ens, est.mean(axis=0), rtol=1e-13, atol=1e-13)
 
 
