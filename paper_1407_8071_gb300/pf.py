@@ -68,6 +68,8 @@ _SIGS = {
     "pf_systematic_scratch_bytes": (c_size_t, [c_int32, c_int64]),
     "pf_systematic_resample": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p, c_void_p,
                                          c_size_t, c_void_p]),
+    "pf_systematic_resample_noalloc": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p,
+                                                 c_void_p]),
     "pf_simulate": (c_int32, [POINTER(pf_model), c_double, POINTER(pf_obs_op), POINTER(pf_noise), c_int32, c_int32,
                               c_int32, POINTER(c_double), POINTER(c_float)]),
 }
@@ -160,6 +162,13 @@ def pf_systematic_resample(N: Sequence[int], d_w, d_u, d_anc, d_scratch, stream=
     Nh = np.ascontiguousarray(N, dtype=np.int32)
     _check(lib().pf_systematic_resample(len(Nh), _ip(Nh), d_w.data_ptr(), d_u.data_ptr(), d_anc.data_ptr(),
                                         d_scratch.data_ptr(), d_scratch.numel() * d_scratch.element_size(), stream))
+
+
+def pf_systematic_resample_noalloc(N: Sequence[int], d_w, d_u, d_anc, stream=None):
+    """Systematic resampling with the library's built-in scratch (no allocation)."""
+    Nh = np.ascontiguousarray(N, dtype=np.int32)
+    _check(lib().pf_systematic_resample_noalloc(len(Nh), _ip(Nh), d_w.data_ptr(), d_u.data_ptr(), d_anc.data_ptr(),
+                                                stream))
 
 
 # ---------------------------------------------------------------------------
