@@ -167,9 +167,10 @@ class Workload:
             self.streams.append(st)
         self.particles = sum(M * N for M, N in self.rows)
         self.particle_steps_per_step = self.particles * self.spec.K
-        # kernels one pf_step launches (propagate, tile max, weights, scan, ancestors, means, ensemble
-        # for the small models; lattice: propagate, tile max, weights, scan, ancestors, gather, means, ensemble)
-        self.kernels_per_filter_step = 8 if self.spec.kind == W.FHN else 7
+        # kernels one pf_step launches: small models -- propagate (+ sub-tile maxima), weights, scan,
+        # ancestors (+ gather, means, ensemble); lattice -- propagate, tile maxima, weights, scan,
+        # ancestors, gather, means, ensemble
+        self.kernels_per_filter_step = 8 if self.spec.kind == W.FHN else 4
         self.t = 0
 
     def step_device(self):

@@ -243,6 +243,52 @@ def bf_run(spec, M: int, N, T: int, obs: np.ndarray, seed: int, resampler: str =
     return dict(est=post, est_pre=pre, log_G=logG, ess=ess, ens=ens, x_final=xf)
 
 
+class _OrcProposal(ctypes.Structure):
+    _fields_ = [("theta", ctypes.POINTER(ctypes.c_float)), ("bf16", ctypes.c_int32), ("ess_frac", ctypes.c_double)]
+
+
+def mlp_forward_c(theta: np.ndarray, rows: np.ndarray, bf16: bool = True) -> np.ndarray:
+    """The C oracle's network forward (the one its filter uses)."""
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    rows = np.ascontiguousarray(rows, dtype=np.float64).reshape(-1, 51)
+    out = np.empty((len(rows), 4))
+    pr = _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, 0.1)
+    lib().orc_mlp_forward(ctypes.byref(pr), ctypes.c_int64(len(rows)), _p(rows, ctypes.c_double),
+                          _p(out, ctypes.c_double))
+    return out
+
+
+def patch_row_c(spec, x: np.ndarray, node: int, y: float) -> np.ndarray:
+    md = _Model(spec)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    row = np.empty(51)
+    lib().orc_patch_row(md.ref, _p(x, ctypes.c_double), ctypes.c_int32(node), ctypes.c_double(y),
+                        _p(row, ctypes.c_double))
+    return row
+
+
+def bf_run_proposal(spec, theta, M: int, N, T: int, obs: np.ndarray, seed: int, est_idx=None, bf16: bool = True,
+                    ess_frac: float = 0.1, obs_per_filter: bool = False, threads: int = 0) -> dict:
+    """M filters with the learned proposal (lattice); theta None = bootstrap."""
+    md = _Model(spec)
+    N = np.ascontiguousarray(np.broadcast_to(np.asarray(N, dtype=np.int32), (M,)), dtype=np.int32)
+    est_idx = np.ascontiguousarray(range(spec.dx) if est_idx is None else est_idx, dtype=np.int32)
+    ne = len(est_idx)
+    obs = np.ascontiguousarray(obs, dtype=np.float64)
+    post, logG, ess = np.empty((T, M, ne)), np.empty((T, M)), np.empty((T, M))
+    ens, fb = np.empty((T, ne)), np.empty((T, M))
+    th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+    pr = None if th is None else _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, ess_frac)
+    nullp = ctypes.POINTER(ctypes.c_double)()
+    lib().orc_bf_run_proposal(md.ref, ctypes.byref(pr) if pr is not None else None, ctypes.c_int32(M),
+                              _p(N, ctypes.c_int32), ctypes.c_int32(T), _p(obs, ctypes.c_double),
+                              ctypes.c_int32(1 if obs_per_filter else 0), ctypes.c_uint64(seed), ctypes.c_int32(0),
+                              ctypes.c_int32(ne), _p(est_idx, ctypes.c_int32), _p(post, ctypes.c_double), nullp,
+                              _p(logG, ctypes.c_double), _p(ess, ctypes.c_double), _p(ens, ctypes.c_double), nullp,
+                              _p(fb, ctypes.c_double), ctypes.c_int32(threads))
+    return dict(est=post, log_G=logG, ess=ess, ens=ens, fallback=fb)
+
+
 # --------------------------------------------------------------------------
 # Kalman filter: the exact filter of the linear-Gaussian case (Sec. 2.2)
 # --------------------------------------------------------------------------

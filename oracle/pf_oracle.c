@@ -273,6 +273,124 @@ static double loglik(const orc_model *md, const double *x, const double *y)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Learned proposal (growth direction; the paper admits tailored importance   */
+/* functions, Sec. 6 footnote).  At the observed lattice nodes, the last      */
+/* Euler-Maruyama sub-step before an observation is drawn from               */
+/*   q = N(m + h o_mu, (h exp(clip(o_s, -3, 3)))^2),  h = sigma sqrt(dt),      */
+/* with the same normals the transition would use, and the weight gains      */
+/* log p - log q.  o = MLP(5x5 patch of v, 5x5 patch of w, y at the node).    */
+/* ------------------------------------------------------------------------- */
+#define MLP_IN 51
+#define MLP_HID 128
+#define MLP_OUT 4
+#define MLP_CLAMP 3.0
+
+typedef struct {
+    const float *theta; /* W1 (128x51), b1, W2 (128x128), b2, W3 (4x128), b3 */
+    int32_t bf16;       /* round weights and layer inputs to bfloat16          */
+    double ess_frac;    /* fall back to the transition when ESS < ess_frac N    */
+} orc_proposal;
+
+static double bf16r(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return x; /* inf / nan */
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+
+void orc_mlp_forward(const orc_proposal *pr, int64_t rows, const double *in, double *out)
+{
+    const float *W1 = pr->theta, *b1 = W1 + MLP_HID * MLP_IN, *W2 = b1 + MLP_HID, *b2 = W2 + MLP_HID * MLP_HID;
+    const float *W3 = b2 + MLP_HID, *b3 = W3 + MLP_OUT * MLP_HID;
+    double a0[MLP_IN], a1[MLP_HID], a2[MLP_HID];
+    for (int64_t r = 0; r < rows; ++r) {
+        for (int i = 0; i < MLP_IN; ++i) a0[i] = pr->bf16 ? bf16r(in[r * MLP_IN + i]) : in[r * MLP_IN + i];
+        for (int o = 0; o < MLP_HID; ++o) {
+            double z = b1[o];
+            for (int i = 0; i < MLP_IN; ++i) z += (pr->bf16 ? bf16r(W1[o * MLP_IN + i]) : W1[o * MLP_IN + i]) * a0[i];
+            a1[o] = pr->bf16 ? bf16r(gelu(z)) : gelu(z);
+        }
+        for (int o = 0; o < MLP_HID; ++o) {
+            double z = b2[o];
+            for (int i = 0; i < MLP_HID; ++i) z += (pr->bf16 ? bf16r(W2[o * MLP_HID + i]) : W2[o * MLP_HID + i]) * a1[i];
+            a2[o] = pr->bf16 ? bf16r(gelu(z)) : gelu(z);
+        }
+        for (int o = 0; o < MLP_OUT; ++o) {
+            double z = b3[o];
+            for (int i = 0; i < MLP_HID; ++i) z += (pr->bf16 ? bf16r(W3[o * MLP_HID + i]) : W3[o * MLP_HID + i]) * a2[i];
+            out[r * MLP_OUT + o] = z;
+        }
+    }
+}
+
+/* The network input of lattice node `node`: 5x5 patches of v and w (row-major,
+ * mirrored at the edges: index -1 -> 0, -2 -> 1, J -> J-1, J+1 -> J-2) and y. */
+static int mirror(int k, int J) { return k < 0 ? -k - 1 : (k >= J ? 2 * J - k - 1 : k); }
+
+void orc_patch_row(const orc_model *md, const double *x, int32_t node, double y, double *row)
+{
+    int J = md->J, nn = J * J, i = node / J, j = node % J, r = 0;
+    for (int di = -2; di <= 2; ++di)
+        for (int dj = -2; dj <= 2; ++dj, ++r) {
+            int k = mirror(i + di, J) * J + mirror(j + dj, J);
+            row[r] = x[k];
+            row[25 + r] = x[nn + k];
+        }
+    row[50] = y;
+}
+
+/* K - 1 ordinary sub-steps, then the last one with the proposal at the
+ * observed nodes.  On return x holds the proposed state, xb (dx) the state
+ * the transition alone would have produced, and *lw = sum (log p - log q). */
+static void propagate_proposal(const orc_model *md, const orc_proposal *pr, uint64_t seed, uint32_t c0,
+                               uint32_t c2, int32_t t, const double *y, double *x, double *xb, double *lw,
+                               double *z, double *f)
+{
+    nstream ns;
+    ns_init(&ns, seed, c0, (uint32_t)t, c2, ORC_STREAM_DYN);
+    const int K = md->K, dx = md->dx, nn = md->J * md->J;
+    for (int k = 0; k < K - 1; ++k) {
+        for (int v = 0; v < dx; ++v) z[v] = ns_get(&ns, (int64_t)k * dx + noise_slot(md, v));
+        em_step(md, (int64_t)(t - 1) * K + k + 1, x, z, f);
+    }
+    const int k = K - 1;
+    for (int v = 0; v < dx; ++v) z[v] = ns_get(&ns, (int64_t)k * dx + noise_slot(md, v));
+    drift(md, (int64_t)(t - 1) * K + k + 1, x, f);
+    const double h = md->sigma_dyn * sqrt(md->dt);
+    double row[MLP_IN], o[MLP_OUT];
+    *lw = 0.0;
+    /* observed nodes first, from the pre-step state */
+    double *prop = (double *)malloc(sizeof(double) * 2 * md->dy);
+    for (int j = 0; j < md->dy; ++j) {
+        const int nd = md->obs_idx[j];
+        orc_patch_row(md, x, nd, y[j], row);
+        orc_mlp_forward(pr, 1, row, o);
+        for (int c = 0; c < 2; ++c) {
+            const int var = c * nn + nd;
+            const double m = x[var] + md->dt * f[var];
+            const double oc = o[2 + c] < -MLP_CLAMP ? -MLP_CLAMP : (o[2 + c] > MLP_CLAMP ? MLP_CLAMP : o[2 + c]);
+            const double mu = m + h * o[c], sd = h * exp(oc);
+            const double xv = mu + sd * z[var];
+            prop[2 * j + c] = xv;
+            *lw += (-(xv - m) * (xv - m) / (2.0 * h * h) - log(h)) - (-(xv - mu) * (xv - mu) / (2.0 * sd * sd) - log(sd));
+        }
+    }
+    for (int v = 0; v < dx; ++v) {
+        x[v] = x[v] + md->dt * f[v] + h * z[v];
+        xb[v] = x[v];
+    }
+    for (int j = 0; j < md->dy; ++j)
+        for (int c = 0; c < 2; ++c) x[c * nn + md->obs_idx[j]] = prop[2 * j + c];
+    free(prop);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Component entry points (particle-major x: n x dx).                        */
 /* ------------------------------------------------------------------------- */
 
@@ -478,10 +596,27 @@ void orc_simulate(const orc_model *md, int32_t T, uint64_t seed, int32_t record,
 /*   ens     [T][n_est]     Definition 1: mean over m of est_post               */
 /* x_final: sum_m N_m x dx particle-major filter-after-filter (or NULL).       */
 /* ------------------------------------------------------------------------- */
+int orc_bf_run_proposal(const orc_model *md, const orc_proposal *pr, int32_t M, const int32_t *N, int32_t T,
+                        const double *obs, int32_t obs_per_filter, uint64_t seed, int32_t resampler, int32_t n_est,
+                        const int32_t *est_idx, double *est_post, double *est_pre, double *log_G, double *ess,
+                        double *ens, double *x_final, double *fallback, int32_t n_threads);
+
 int orc_bf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, const double *obs,
                int32_t obs_per_filter, uint64_t seed, int32_t resampler, int32_t n_est, const int32_t *est_idx,
                double *est_post, double *est_pre, double *log_G, double *ess, double *ens, double *x_final,
                int32_t n_threads)
+{
+    return orc_bf_run_proposal(md, NULL, M, N, T, obs, obs_per_filter, seed, resampler, n_est, est_idx, est_post,
+                               est_pre, log_G, ess, ens, x_final, NULL, n_threads);
+}
+
+/* Algorithm 1 x M with an optional learned proposal (pr != NULL, lattice only):
+ * fallback[T][M] = 1 where a filter's ESS under the proposal fell below
+ * ess_frac N and the step used the transition instead. */
+int orc_bf_run_proposal(const orc_model *md, const orc_proposal *pr, int32_t M, const int32_t *N, int32_t T,
+                        const double *obs, int32_t obs_per_filter, uint64_t seed, int32_t resampler, int32_t n_est,
+                        const int32_t *est_idx, double *est_post, double *est_pre, double *log_G, double *ess,
+                        double *ens, double *x_final, double *fallback, int32_t n_threads)
 {
     int dx = md->dx;
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (M + 1));
@@ -502,6 +637,8 @@ int orc_bf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, cons
         int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * Nm);
         double *z = (double *)malloc(sizeof(double) * dx);
         double *f = (double *)malloc(sizeof(double) * dx);
+        double *xb = pr ? (double *)malloc(sizeof(double) * Nm * dx) : NULL;
+        double *lb = pr ? (double *)malloc(sizeof(double) * Nm) : NULL;
         double lg = 0.0;
         /* Algorithm 1, step 1 */
         for (int64_t i = 0; i < Nm; ++i) prior_one(md, seed, ORC_STREAM_INIT, (uint32_t)i, (uint32_t)m, x + i * dx);
@@ -509,9 +646,27 @@ int orc_bf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, cons
             const double *y = obs_per_filter ? obs + ((int64_t)(t - 1) * M + m) * md->dy
                                              : obs + (int64_t)(t - 1) * md->dy;
             /* step 2a: propagate and weight */
-            for (int64_t i = 0; i < Nm; ++i) {
-                propagate_one(md, seed, ORC_STREAM_DYN, (uint32_t)i, (uint32_t)m, t, x + i * dx, z, f);
-                l[i] = loglik(md, x + i * dx, y);
+            int used_fallback = 0;
+            if (pr) {
+                for (int64_t i = 0; i < Nm; ++i) {
+                    double lw;
+                    propagate_proposal(md, pr, seed, (uint32_t)i, (uint32_t)m, t, y, x + i * dx, xb + i * dx, &lw, z,
+                                       f);
+                    l[i] = loglik(md, x + i * dx, y) + lw;
+                    lb[i] = loglik(md, xb + i * dx, y);
+                }
+                double np_[5];
+                orc_normalise(Nm, l, np_);
+                if (np_[4] < pr->ess_frac * (double)Nm) { /* the bootstrap proposal instead */
+                    used_fallback = 1;
+                    memcpy(x, xb, sizeof(double) * Nm * dx);
+                    memcpy(l, lb, sizeof(double) * Nm);
+                }
+            } else {
+                for (int64_t i = 0; i < Nm; ++i) {
+                    propagate_one(md, seed, ORC_STREAM_DYN, (uint32_t)i, (uint32_t)m, t, x + i * dx, z, f);
+                    l[i] = loglik(md, x + i * dx, y);
+                }
             }
             double nrm[5];
             orc_normalise(Nm, l, nrm);
@@ -519,6 +674,7 @@ int orc_bf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, cons
             /* eq. (eqGtN): log G_t = log G_{t-1} + log((1/N) sum_j g_t(x_j)) */
             lg += nrm[1] - log((double)Nm) + log_const;
             int64_t row = (int64_t)(t - 1) * M + m;
+            if (fallback) fallback[row] = used_fallback;
             if (log_G) log_G[row] = lg;
             if (ess) ess[row] = nrm[4];
             if (est_pre) {
@@ -547,6 +703,7 @@ int orc_bf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, cons
         }
         if (x_final) memcpy(x_final + off[m] * dx, x, sizeof(double) * Nm * dx);
         free(x); free(xn); free(l); free(w); free(U); free(anc); free(z); free(f);
+        free(xb); free(lb);
     }
     /* Definition 1: the ensemble average over the M filters, in filter order */
     if (ens && est_post) {

@@ -2,12 +2,11 @@
 // filters (arXiv:1407.8071, Algorithm 1 run M times, Definition 1 average).
 //
 // One observation step is
-//   propagate+weight  (Alg. 1 step 2a)      k_propagate_small / k_propagate_fhn
-//   tile maxima       (log-sum-exp, pass 1)  k_tile_max
+//   propagate+weight  (Alg. 1 step 2a)      k_propagate_small / k_propagate_fhn (+ per-filter max log-weight)
 //   weights           (FP64 sums, eq. eqGtN) k_weights
 //   prefix + scatter  (step 2b, systematic)  k_scan_scatter
-//   ancestors+gather  (step 2b)              k_ancestors_small / k_ancestors + k_gather_rows
-//   estimates         (Def. 1)               k_filter_means / k_mean_rows, k_ensemble
+//   ancestors+gather  (step 2b)              k_ancestors_small (+ per-filter means) / k_ancestors + k_gather_rows
+//   estimates         (Def. 1)               (fused above) / k_mean_rows; then k_ensemble
 // Particles of all filters are contiguous; tiles of <= kTile particles never
 // span two filters, so per-filter reductions read only that filter's tiles
 // and no kernel waits on another block.
@@ -15,9 +14,12 @@
 // FP64 is a narrow pipe on this GPU (about 1/64 of the FP32 rate), so it is
 // used only where the precision contract needs it -- the per-filter sums of
 // the normaliser and of the estimates, and the average over filters -- and
-// there only above the thread level: each thread sums its few particles in
-// FP32 and the block combines the thread sums in FP64.  Systematic resampling
-// is exact integer arithmetic (64-bit prefix, 128-bit comparisons).
+// there only above the tile level: inside a tile, sums are compensated FP32
+// pairs (Knuth's two-sum, about 48 significant bits), converted to FP64 once
+// per tile.  Systematic resampling is exact integer arithmetic (64-bit
+// prefix, 128-bit comparisons).  The per-filter means of the small models are
+// finished by the last tile of each filter (completion counter, no waiting), in
+// a fixed order.
 #include <cfloat>
 #include <cmath>
 
@@ -58,6 +60,64 @@ __device__ __forceinline__ double warp_sum_d(double v)
     return v;
 }
 
+// Compensated FP32 pair (hi + lo) and Knuth's two-sum: the pair holds a sum
+// to about 2^-48 relative accuracy with FP32 instructions only.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, float b)
+{
+    const float s = __fadd_rn(a.hi, b);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return FF{s, __fadd_rn(a.lo, e)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    FF r = ff_add(a, b.hi);
+    r.lo = __fadd_rn(r.lo, b.lo);
+    return r;
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Sums of NV compensated pairs over the block in a fixed order (xor tree in
+// each warp, then warps in order); every thread receives the FP64 results.
+// `sh` holds 2 * NV * (blockDim.x / 32) floats + NV doubles.
+template <int NV>
+__device__ void block_sum_ff(FF (&v)[NV], double (&out)[NV], void *shm)
+{
+    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    float *sf = reinterpret_cast<float *>(shm);
+    double *sd = reinterpret_cast<double *>(sf + 2 * NV * 32);
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            FF other{__shfl_xor_sync(0xffffffffu, v[j].hi, o), __shfl_xor_sync(0xffffffffu, v[j].lo, o)};
+            v[j] = ff_add(v[j], other);
+        }
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            sf[2 * (j * 32 + w)] = v[j].hi;
+            sf[2 * (j * 32 + w) + 1] = v[j].lo;
+        }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int j = threadIdx.x;
+        FF acc{0.0f, 0.0f};
+        for (int i = 0; i < nw; ++i) acc = ff_add(acc, FF{sf[2 * (j * 32 + i)], sf[2 * (j * 32 + i) + 1]});
+        sd[j] = ff_to_double(acc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) out[j] = sd[j];
+}
+
 // FP64 sums over the block of NV per-thread values, in a fixed order
 // (deterministic): warp j < NV sums column j.  `sh` holds blockDim.x * NV + NV
 // doubles.  Every thread receives the sums.
@@ -70,11 +130,11 @@ __device__ void block_sum_dd(double (&v)[NV], double *sh)
     for (int j = 0; j < NV; ++j) sh[j * n + tid] = v[j];
     __syncthreads();
     const int w = tid >> 5, l = tid & 31;
-    if (w < NV) {
+    for (int j = w; j < NV; j += (n >> 5)) {
         double acc = 0.0;
-        for (int i = l; i < n; i += 32) acc += sh[w * n + i];
+        for (int i = l; i < n; i += 32) acc += sh[j * n + i];
         acc = warp_sum_d(acc);
-        if (l == 0) sh[NV * n + w] = acc;
+        if (l == 0) sh[NV * n + j] = acc;
     }
     __syncthreads();
 #pragma unroll
@@ -191,11 +251,26 @@ __device__ __forceinline__ U128 grid_point(uint64_t i, uint32_t U, uint64_t Ctot
 }
 
 struct Grid {
-    uint64_t Ctot;   // C_{N-1}
-    uint32_t U;      // u = U 2^-32
+    uint64_t Ctot;  // C_{N-1}
+    uint32_t U;     // u = U 2^-32
     int64_t N;
-    float n_over_c;  // N / Ctot (estimate only)
+    int est_shift;  // the estimate uses x >> est_shift (< 2^24, exact in FP32)
+    float est_scale;  // N 2^est_shift / Ctot
+    float u;        // U 2^-32
 };
+
+__device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
+{
+    Grid g;
+    g.Ctot = Ctot;
+    g.U = U;
+    g.N = N;
+    const int bits = 64 - __clzll((long long)(Ctot | 1));
+    g.est_shift = bits > 24 ? bits - 24 : 0;
+    g.est_scale = (float)((double)N * (double)(1ull << g.est_shift) / (double)(Ctot ? Ctot : 1));
+    g.u = __uint2float_rn(U) * 0x1p-32f;
+    return g;
+}
 
 // #{i in [0, N) : t_i < x}: the t_i increase with i, so this is the first i
 // with grid_point(i) >= x N 2^32.  A float estimate is corrected by a short
@@ -204,8 +279,9 @@ __device__ int64_t count_below(uint64_t x, const Grid &g)
 {
     if (x == 0) return 0;
     const U128 X = scaled_C(x, (uint64_t)g.N);
-    const float est = ceilf(__fmaf_rn(__ull2float_rn(x), g.n_over_c, -(float)g.U * 0x1p-32f));
-    int64_t i = est <= 0.0f ? 0 : (est >= (float)g.N ? g.N : (int64_t)est);
+    const float xf = __uint2float_rn((uint32_t)(x >> g.est_shift));
+    const float est = ceilf(__fmaf_rn(xf, g.est_scale, -g.u));
+    int64_t i = est <= 0.0f ? 0 : (est >= (float)g.N ? g.N : (int64_t)__float2int_rz(est));
     bool settled = false;
     for (int it = 0; it < 4; ++it) {
         if (i > 0 && ge128(grid_point((uint64_t)(i - 1), g.U, g.Ctot), X)) --i;
@@ -289,30 +365,35 @@ __global__ void __launch_bounds__(256) k_init_fhn(ModelParams mp, Key key, const
 }
 
 // ------------------------------------------------------------------ propagate + weight (Alg. 1 step 2a)
-// Thread per particle over the flat particle range (128-thread CTAs, so the
-// grid has many small blocks and little wave-quantisation loss), SoA state
-// x[v * P + p] (coalesced), K Euler-Maruyama sub-steps in registers, then the
-// FP32 log-likelihood.
+// Thread per particle, one CTA per sub-tile of <= kSubTile particles (filter
+// aligned, so the grid has many small blocks and little wave-quantisation
+// loss), SoA state x[v * P + p] (coalesced), K Euler-Maruyama sub-steps in
+// registers, then the FP32 log-likelihood; the sub-tile's maximum of it joins
+// the filter's maximum by one atomicMax (the first pass of the log-sum-exp).
 template <int D>
-__global__ void __launch_bounds__(128) k_propagate_small(ModelParams mp, Key key, const int32_t *__restrict__ pfilt,
-                                                         const FilterDesc *__restrict__ filt,
-                                                         const float *__restrict__ x_in, float *__restrict__ x_out,
-                                                         int64_t P, float *logw, const float *obs, int32_t obs_stride,
-                                                         const int32_t *d_t)
+__global__ void __launch_bounds__(kSubTile, 16) k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs,
+                                                              const float *__restrict__ x_in, float *__restrict__ x_out,
+                                                              int64_t P, float *logw, int32_t *fmax_key, const float *obs,
+                                                              int32_t obs_stride, const int32_t *d_t)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
+    __shared__ float sh[kSubTile / 32];
+    const TileDesc st = subs[blockIdx.x];
     const uint32_t t = (uint32_t)(*d_t + 1);
-    const int32_t m = pfilt[p];
-    const uint32_t i = (uint32_t)(p - filt[m].off);
-    const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
-    float xs[D];
+    const float *y = obs + (obs_stride ? (int64_t)st.m * obs_stride : 0);
+    float l = -INFINITY;
+    if ((int)threadIdx.x < st.len) {
+        const int64_t p = st.gstart + threadIdx.x;
+        float xs[D];
 #pragma unroll
-    for (int v = 0; v < D; ++v) xs[v] = x_in[v * P + p];
-    propagate_small<D, float>(mp, key, kStreamDyn, i, t, (uint32_t)m, xs);
+        for (int v = 0; v < D; ++v) xs[v] = x_in[v * P + p];
+        propagate_small<D, float>(mp, key, kStreamDyn, (uint32_t)(st.lstart + threadIdx.x), t, (uint32_t)st.m, xs);
 #pragma unroll
-    for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[v];
-    logw[p] = loglik_small<D, float>(mp, y, xs);
+        for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[v];
+        l = loglik_small<D, float>(mp, y, xs);
+        logw[p] = l;
+    }
+    const float mx = block_max_f(l < INFINITY ? l : -INFINITY, sh);  // NaN never wins
+    if (threadIdx.x == 0 && mx > -INFINITY) atomicMax(&fmax_key[st.m], float_order_key(mx));
 }
 
 // Lattice propagation (Sec. 5.1, Rogers-McCulloch form): a CTA holds ppc
@@ -342,7 +423,7 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
                                 const FilterDesc *filt, const Real *__restrict__ x_in, Real *__restrict__ x_out,
                                 int64_t P, float *logw, const float *obs, int32_t obs_stride,
                                 const int32_t *obs_slot, const int32_t *d_t, int32_t fixed_c0, int32_t fixed_c2,
-                                int32_t t_direct, int32_t ppc)
+                                int32_t t_direct, int32_t ppc, int32_t *fmax_key)
 {
     extern __shared__ unsigned char smem_raw[];
     const int J = mp.J, nn = J * J, pairs = nn / 2;
@@ -439,23 +520,35 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
         for (int i = lane; i < pairs; i += 32) acc += red[sl * pairs + i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0 && pp < P) logw[pp] = mp.fhalf_prec * acc;
+        if (lane == 0 && pp < P) {
+            const float l = mp.fhalf_prec * acc;
+            logw[pp] = l;
+            if (l > -INFINITY && l < INFINITY) atomicMax(&fmax_key[pfilt[pp]], float_order_key(l));
+        }
     }
 }
 
 // ------------------------------------------------------------------ resampling chain
-// Pass 1: maximum log-weight of each tile.
-__global__ void __launch_bounds__(kResampleThreads) k_tile_max(ResampleArgs a)
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t value)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = value;
+}
+
+// The per-filter maximum log-weight from scratch (after pf_set_logw): one
+// atomicMax per tile, into keys the caller reset to -inf.
+__global__ void __launch_bounds__(kResampleThreads) k_refresh_max(const TileDesc *tiles, const float *logw,
+                                                                  int32_t *fmax_key)
 {
     __shared__ float sh[kWarps];
-    const TileDesc td = a.tiles[blockIdx.x];
+    const TileDesc td = tiles[blockIdx.x];
     float mx = -INFINITY;
     for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
-        const float l = a.logw[td.gstart + j];
+        const float l = logw[td.gstart + j];
         if (l < INFINITY) mx = fmaxf(mx, l);  // NaN and +inf never win
     }
     mx = block_max_f(mx, sh);
-    if (threadIdx.x == 0) a.tile_max[blockIdx.x] = mx;
+    if (threadIdx.x == 0 && mx > -INFINITY) atomicMax(&fmax_key[td.m], float_order_key(mx));
 }
 
 // Pass 2: the filter maximum, then per tile sum w and sum w^2 (FP32 per
@@ -471,10 +564,9 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
     const FilterDesc fd = a.filt[td.m];
     float mx = 0.0f;
     bool degenerate = false;
+    (void)shf;
     if (!Direct) {
-        float m = -INFINITY;
-        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) m = fmaxf(m, a.tile_max[fd.tile_begin + j]);
-        m = block_max_f(m, shf);
+        const float m = float_from_order_key(a.fmax_key[td.m]);
         degenerate = !(m > -INFINITY);
         mx = degenerate ? 0.0f : m;
     }
@@ -490,20 +582,19 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
             qs += quant_f64(w, fd.shift);
             a.B[p] = -1;
         }
+        block_sum_dd<2>(s, shd);
     } else {
-        float f0 = 0.0f, f1 = 0.0f;
+        FF f[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
         for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
             const int64_t p = td.gstart + j;
             const float w = weight_f32(a.logw[p], mx, degenerate);
-            f0 += w;
-            f1 = __fmaf_rn(w, w, f1);
+            f[0] = ff_add(f[0], w);
+            f[1] = ff_add(f[1], __fmul_rn(w, w));
             qs += quant_f32(w, fd.shift);
             a.B[p] = -1;
         }
-        s[0] = (double)f0;
-        s[1] = (double)f1;
+        block_sum_ff<2>(f, s, shd);
     }
-    block_sum_dd<2>(s, shd);
     qs = block_sum_u64(qs, shu);
     if (threadIdx.x == 0) {
         double *ts = a.tile_sums + (int64_t)blockIdx.x * kTsCount;
@@ -545,7 +636,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
     uint32_t U;
     if (Direct) U = (uint32_t)fmin(floor(a.u_direct[td.m] * 4294967296.0), 4294967295.0);
     else U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
-    const Grid g{Ctot, U, (int64_t)fd.N, (float)fd.N / __ull2float_rn(Ctot > 0 ? Ctot : 1)};
+    const Grid g = make_grid(Ctot, U, (int64_t)fd.N);
 
     if (ti == 0) {  // filter scalars (FP64)
         double s[2] = {0.0, 0.0};
@@ -563,6 +654,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
             if (a.d_t) fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)fd.N) + a.log_const;
             a.fint[(int64_t)td.m * 2] = Ctot;
             a.fint[(int64_t)td.m * 2 + 1] = U;
+            if (!Direct) a.fmax_key[td.m] = kNegInfKey;  // k_weights has consumed it
         }
     }
     const float mx = Direct ? 0.0f : (float)a.fstats[(int64_t)td.m * kFsCount + kFsMax];
@@ -603,7 +695,10 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
 __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const TileDesc &td, const FilterDesc &fd,
                                                int32_t (&anc)[kItems], int *shi)
 {
-    const Grid g{a.fint[(int64_t)td.m * 2], (uint32_t)a.fint[(int64_t)td.m * 2 + 1], (int64_t)fd.N, 0.0f};
+    Grid g;
+    g.Ctot = a.fint[(int64_t)td.m * 2];
+    g.U = (uint32_t)a.fint[(int64_t)td.m * 2 + 1];
+    g.N = fd.N;
     const int32_t a0 = search_ancestor(a.C + fd.off, g, td.lstart);
     const int j0 = threadIdx.x * kItems;
     int b[kItems];
@@ -623,22 +718,26 @@ __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const Tile
 }
 
 // Small models: ancestors, gather of the SoA state and per-tile sums of every
-// variable of the resampled particles (FP32 per thread, FP64 across threads).
+// variable of the resampled particles (compensated FP32 pairs, FP64 per tile).
+// The last tile of a filter to finish (atomic completion counter after a
+// memory fence; nothing waits) turns the filter's tile sums into est[m], the
+// per-filter estimates of Definition 1, in a fixed order.
 template <int D>
 __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleArgs a, const float *__restrict__ x_in,
                                                                       float *__restrict__ x_out, int64_t P,
-                                                                      double *tile_est)
+                                                                      double *tile_est, double *est)
 {
     __shared__ int shi[kWarps];
-    __shared__ double shd[kResampleThreads * D + D];
+    __shared__ double shd[kResampleThreads * D + 2 * D * 32];
+    __shared__ int last;
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = a.filt[td.m];
     int32_t anc[kItems];
     tile_ancestors(a, td, fd, anc, shi);
     const int j0 = threadIdx.x * kItems;
-    float f[D];
+    FF f[D];
 #pragma unroll
-    for (int v = 0; v < D; ++v) f[v] = 0.0f;
+    for (int v = 0; v < D; ++v) f[v] = FF{0.0f, 0.0f};
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         const int j = j0 + r;
@@ -650,17 +749,34 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
             for (int v = 0; v < D; ++v) {
                 const float xv = x_in[v * P + src];
                 x_out[v * P + p] = xv;
-                f[v] += xv;
+                f[v] = ff_add(f[v], xv);
             }
         }
     }
     double s[D];
-#pragma unroll
-    for (int v = 0; v < D; ++v) s[v] = (double)f[v];
-    block_sum_dd<D>(s, shd);
-    if (threadIdx.x == 0)
+    block_sum_ff<D>(f, s, shd);
+    if (fd.tile_count == 1) {  // the tile is the filter
+        if (threadIdx.x < D) est[(int64_t)td.m * D + threadIdx.x] = s[threadIdx.x] / (double)fd.N;
+        return;
+    }
+    if (threadIdx.x == 0) {
 #pragma unroll
         for (int v = 0; v < D; ++v) tile_est[(int64_t)blockIdx.x * D + v] = s[v];
+        __threadfence();
+        last = (atomicAdd(&a.done[td.m], 1) == fd.tile_count - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // the filter's estimate: tiles strided over the threads, then a fixed tree
+    double part[D];
+#pragma unroll
+    for (int v = 0; v < D; ++v) part[v] = 0.0;
+    for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x)
+#pragma unroll
+        for (int v = 0; v < D; ++v) part[v] += __ldcg(&tile_est[(int64_t)(fd.tile_begin + j) * D + v]);
+    block_sum_dd<D>(part, shd);
+    if (threadIdx.x < D) est[(int64_t)td.m * D + threadIdx.x] = part[threadIdx.x] / (double)fd.N;
+    if (threadIdx.x == 0) a.done[td.m] = 0;
 }
 
 // Ancestors only (lattice models and the stateless entry point).
@@ -689,8 +805,8 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t *__restrict__
     for (int i = threadIdx.x; i < row4; i += blockDim.x) b[i] = a[i];
 }
 
-// Lattice estimates: est[m][v] = (1/N_m) sum_i x[off + i][v]; FP32 partial
-// sums over runs of 16 particles, accumulated in FP64, i ascending.
+// Lattice estimates: est[m][v] = (1/N_m) sum_i x[off + i][v], i ascending, in
+// a compensated FP32 pair converted to FP64 at the end.
 __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const float *__restrict__ x, int dx,
                                                    double *est)
 {
@@ -699,30 +815,17 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
     if (v >= dx) return;
     const FilterDesc fd = filt[m];
     const float *base = x + fd.off * (int64_t)dx + v;
-    double acc = 0.0;
-    for (int i0 = 0; i0 < fd.N; i0 += 16) {
-        const int n = min(16, fd.N - i0);
-        float f = 0.0f;
-        for (int i = 0; i < n; ++i) f += base[(int64_t)(i0 + i) * dx];
-        acc += (double)f;
+    FF acc{0.0f, 0.0f};
+    int i = 0;
+    for (; i + 8 <= fd.N; i += 8) {  // eight loads in flight, then the ordered adds
+        float r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = base[(int64_t)(i + k) * dx];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = ff_add(acc, r[k]);
     }
-    est[(int64_t)m * dx + v] = acc / (double)fd.N;
-}
-
-// Small models: est[m][v] = (1/N_m) sum over the filter's tiles; one warp per
-// (m, v), lane-strided partial sums and a fixed xor tree (deterministic).
-__global__ void __launch_bounds__(256) k_filter_means(const FilterDesc *filt, const double *tile_est, int dx,
-                                                      double *est, int32_t M)
-{
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= (int64_t)M * dx) return;  // whole warps exit together
-    const int m = (int)(w / dx), v = (int)(w % dx);
-    const FilterDesc fd = filt[m];
-    double s = 0.0;
-    for (int j = lane; j < fd.tile_count; j += 32) s += tile_est[(int64_t)(fd.tile_begin + j) * dx + v];
-    s = warp_sum_d(s);
-    if (lane == 0) est[w] = s / (double)fd.N;
+    for (; i < fd.N; ++i) acc = ff_add(acc, base[(int64_t)i * dx]);
+    est[(int64_t)m * dx + v] = ff_to_double(acc) / (double)fd.N;
 }
 
 // Definition 1: ens[v] = (1/M) sum_m est[m][v] in FP64, one CTA per variable,
@@ -850,8 +953,8 @@ template <int D>
 cudaError_t propagate_small_launch(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                                    cudaStream_t s)
 {
-    k_propagate_small<D><<<(unsigned)((c.P + 127) / 128), 128, 0, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P,
-                                                                      c.logw, d_obs, stride, c.d_t);
+    k_propagate_small<D><<<c.n_subs, kSubTile, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs,
+                                                       stride, c.d_t);
     return cudaGetLastError();
 }
 
@@ -863,7 +966,7 @@ ResampleArgs ctx_args(const Ctx &c)
     a.logw = c.logw;
     a.key = c.key;
     a.d_t = c.d_t;
-    a.tile_max = c.tile_max;
+    a.fmax_key = c.fmax_key;
     a.tile_sums = c.tile_sums;
     a.tile_q = c.tile_q;
     a.fstats = c.fstats;
@@ -872,6 +975,7 @@ ResampleArgs ctx_args(const Ctx &c)
     a.B = c.B;
     a.anc = c.anc;
     a.err = c.err;
+    a.done = c.done;
     a.log_const = -0.5 * c.mp.dy * log(2.0 * M_PI * c.mp.sigma_obs * c.mp.sigma_obs);
     return a;
 }
@@ -903,7 +1007,8 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
         const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
         const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
         k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
-                                                           c.logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc);
+                                                           c.logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc,
+                                                           c.fmax_key);
         return cudaGetLastError();
     }
     switch (c.mp.dx) {
@@ -915,29 +1020,33 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
     }
 }
 
+cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)
+{
+    k_fill_i32<<<(c.M + 255) / 256, 256, 0, s>>>(c.fmax_key, c.M, kNegInfKey);
+    k_refresh_max<<<c.n_tiles, kResampleThreads, 0, s>>>(c.tiles, c.logw, c.fmax_key);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream_t s)
 {
     const ResampleArgs a = ctx_args(c);
-    k_tile_max<<<c.n_tiles, kResampleThreads, 0, s>>>(a);
-    k_weights<false><<<c.n_tiles, kResampleThreads, 0, s>>>(a);
-    k_scan_scatter<false><<<c.n_tiles, kResampleThreads, 0, s>>>(a);
-    const int dx = c.mp.dx;
+    const int dx = c.mp.dx, th = c.resample_threads;
+    k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
+    k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
     if (c.mp.kind == kFhnLattice) {
-        k_ancestors<<<c.n_tiles, kResampleThreads, 0, s>>>(a);
+        k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
                                                    reinterpret_cast<float4 *>(xo), dx / 4);
         dim3 g((dx + 255) / 256, c.M);
         k_mean_rows<<<g, 256, 0, s>>>(c.filt, xo, dx, c.est);
     } else {
         switch (dx) {
-        case 1: k_ancestors_small<1><<<c.n_tiles, kResampleThreads, 0, s>>>(a, xi, xo, c.P, c.tile_est); break;
-        case 2: k_ancestors_small<2><<<c.n_tiles, kResampleThreads, 0, s>>>(a, xi, xo, c.P, c.tile_est); break;
-        case 3: k_ancestors_small<3><<<c.n_tiles, kResampleThreads, 0, s>>>(a, xi, xo, c.P, c.tile_est); break;
-        case 4: k_ancestors_small<4><<<c.n_tiles, kResampleThreads, 0, s>>>(a, xi, xo, c.P, c.tile_est); break;
+        case 1: k_ancestors_small<1><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
+        case 2: k_ancestors_small<2><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
+        case 3: k_ancestors_small<3><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
+        case 4: k_ancestors_small<4><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
         default: return cudaErrorInvalidValue;
         }
-        const int64_t threads = (int64_t)c.M * dx * 32;
-        k_filter_means<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(c.filt, c.tile_est, dx, c.est, c.M);
     }
     k_ensemble<<<dx, 128, 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
     return cudaGetLastError();
@@ -990,7 +1099,7 @@ cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int
         const double *xi = d_x + (int64_t)(t - 1) * mp.dx;
         double *xo = d_x + (int64_t)t * mp.dx;
         k_propagate_fhn<double><<<1, threads, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1, nullptr,
-                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1);
+                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1, nullptr);
         if (d_y)
             k_observe<<<(mp.dy + 255) / 256, 256, 0, s>>>(mp, key, d_obs_idx, t, record, xo,
                                                           d_y + (int64_t)(t - 1) * mp.dy);

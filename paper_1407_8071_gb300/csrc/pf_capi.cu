@@ -237,9 +237,11 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
     return true;
 }
 
-// Tiles of at most kTile particles, never spanning two filters.
+// Tiles of at most kTile particles, never spanning two filters; sub-tiles of
+// at most kSubTile particles inside them.  Per-filter partial maxima come from
+// the sub-tiles (small models) or the tiles (lattice, stateless resampling).
 void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std::vector<FilterDesc> &filt,
-                std::vector<int64_t> &off)
+                std::vector<int64_t> &off, std::vector<TileDesc> *subs = nullptr)
 {
     const int32_t M = (int32_t)N.size();
     off.assign(M + 1, 0);
@@ -261,6 +263,16 @@ void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std
             tiles.push_back(td);
         }
         fd.tile_count = (int32_t)tiles.size() - fd.tile_begin;
+        if (subs) {
+            for (int32_t s = 0; s < N[m]; s += kSubTile) {
+                TileDesc st{};
+                st.m = m;
+                st.lstart = s;
+                st.len = std::min(kSubTile, N[m] - s);
+                st.gstart = off[m] + s;
+                subs->push_back(st);
+            }
+        }
         filt[m] = fd;
     }
 }
@@ -334,16 +346,27 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     }
     c.stream = c.own_stream;
 
-    std::vector<TileDesc> tiles;
+    std::vector<TileDesc> tiles, subs;
     std::vector<FilterDesc> filt;
-    make_tiles(c.N, tiles, filt, c.off);
+    const bool small = mp.kind != PF_MODEL_FHN_LATTICE;
+    make_tiles(c.N, tiles, filt, c.off, small ? &subs : nullptr);
     c.P = c.off[M];
     c.n_tiles = (int32_t)tiles.size();
+    c.n_subs = (int32_t)subs.size();
+    {
+        int max_len = 1;
+        for (const TileDesc &td : tiles) max_len = std::max(max_len, td.len);
+        int th = 64;  // threads per tile CTA: enough for kItems particles each, whole warps, 64..256
+        while (th < kResampleThreads && th * kItems < max_len) th *= 2;
+        c.resample_threads = th;
+    }
     const int dx = mp.dx;
     const int64_t P = c.P;
     bool ok = alloc_n(c, c.tiles, tiles.size()) && alloc_n(c, c.filt, filt.size()) &&
+              alloc_n(c, c.done, (size_t)M) && alloc_n(c, c.fmax_key, (size_t)M) &&
+              (!small || alloc_n(c, c.subs, subs.size())) &&
               alloc_n(c, c.x[0], (size_t)P * dx) && alloc_n(c, c.x[1], (size_t)P * dx) && alloc_n(c, c.logw, P) &&
-              alloc_n(c, c.tile_max, c.n_tiles) && alloc_n(c, c.tile_sums, (size_t)c.n_tiles * kTsCount) &&
+              alloc_n(c, c.tile_sums, (size_t)c.n_tiles * kTsCount) &&
               alloc_n(c, c.tile_q, c.n_tiles) && alloc_n(c, c.fint, (size_t)M * 2) &&
               alloc_n(c, c.fstats, (size_t)M * kFsCount) && alloc_n(c, c.C, P) && alloc_n(c, c.B, P) &&
               alloc_n(c, c.anc, P) && alloc_n(c, c.est, (size_t)M * dx) && alloc_n(c, c.ens, dx) &&
@@ -384,6 +407,12 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_t, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.err, err_init, sizeof(err_init), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c.fstats, 0, (size_t)M * kFsCount * sizeof(double), c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.done, 0, (size_t)M * sizeof(int32_t), c.stream);
+    std::vector<int32_t> neg_inf((size_t)M, kNegInfKey);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.fmax_key, neg_inf.data(), (size_t)M * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess && small)
+        e = cudaMemcpyAsync(c.subs, subs.data(), subs.size() * sizeof(TileDesc), cudaMemcpyHostToDevice, c.stream);
     if (e == cudaSuccess) {
         pf_host.resize(P);
         for (int m = 0; m < M; ++m) std::fill(pf_host.begin() + c.off[m], pf_host.begin() + c.off[m + 1], m);
@@ -617,7 +646,8 @@ pf_status pf_set_logw(pf_ctx *h, const float *h_l)
     if (c.phase != 1) return fail(c, PF_ESTATE, "pf_set_logw needs a preceding pf_propagate");
     pf_status st = sync(c, "set_logw");
     if (st != PF_OK) return st;
-    const cudaError_t e = cudaMemcpy(c.logw, h_l, c.P * sizeof(float), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(c.logw, h_l, c.P * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_refresh_max(c, c.stream);
     return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "set_logw copy");
 }
 
@@ -653,7 +683,7 @@ size_t pf_systematic_scratch_bytes(int32_t M, int64_t total)
     if (M < 1 || total < 0) return 0;
     const int64_t nt = max_tiles(M, total);
     return align256(nt * sizeof(TileDesc)) + align256((size_t)M * sizeof(FilterDesc)) +
-           align256(nt * sizeof(float)) + align256(nt * kTsCount * sizeof(double)) + align256(nt * sizeof(uint64_t)) +
+           align256(nt * kTsCount * sizeof(double)) + align256(nt * sizeof(uint64_t)) +
            align256((size_t)M * kFsCount * sizeof(double)) + align256((size_t)M * 2 * sizeof(uint64_t)) +
            align256(total * sizeof(uint64_t)) + align256(total * sizeof(int32_t)) + align256(2 * sizeof(int32_t));
 }
@@ -680,7 +710,6 @@ pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_
     FilterDesc *d_filt = reinterpret_cast<FilterDesc *>(take((size_t)M * sizeof(FilterDesc)));
     a.tiles = d_tiles;
     a.filt = d_filt;
-    a.tile_max = reinterpret_cast<float *>(take(nt * sizeof(float)));
     a.tile_sums = reinterpret_cast<double *>(take(nt * kTsCount * sizeof(double)));
     a.tile_q = reinterpret_cast<uint64_t *>(take(nt * sizeof(uint64_t)));
     a.fstats = reinterpret_cast<double *>(take((size_t)M * kFsCount * sizeof(double)));

@@ -19,6 +19,7 @@ namespace pf {
 constexpr int kTile = 1024;
 constexpr int kResampleThreads = 256;
 constexpr int kItems = kTile / kResampleThreads;  // particles per thread in the tile kernels
+constexpr int kSubTile = 128;                     // propagation block of the thread-per-particle models
 
 struct TileDesc {
     int32_t m;       // filter
@@ -35,6 +36,20 @@ struct FilterDesc {
     int32_t tile_count;  // tiles
     int32_t shift;       // 52 - ceil(log2 N): weight quantisation exponent
 };
+
+// Order-preserving int image of a float (signed-int max = float max), so the
+// per-filter maximum log-weight can be taken with atomicMax.
+__host__ __device__ __forceinline__ int32_t float_order_key(float f)
+{
+    union { float f; int32_t i; } u{f};
+    return u.i >= 0 ? u.i : (u.i ^ 0x7FFFFFFF);
+}
+__host__ __device__ __forceinline__ float float_from_order_key(int32_t k)
+{
+    union { int32_t i; float f; } u{k >= 0 ? k : (k ^ 0x7FFFFFFF)};
+    return u.f;
+}
+constexpr int32_t kNegInfKey = (int32_t)0x807FFFFF;  // float_order_key(-inf)
 
 // Per-filter scalars kept in FP64 on the device.
 enum FStat : int { kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsCount = 8 };
@@ -53,7 +68,7 @@ struct ResampleArgs {
     const double *u_direct;  // per-filter uniforms (stateless entry point), else drawn from Philox
     Key key;
     const int32_t *d_t;      // completed steps; the step being resampled is *d_t + 1
-    float *tile_max;         // [tiles]
+    int32_t *fmax_key;       // [M] order key of each filter's maximum log-weight (atomicMax; -inf between steps)
     double *tile_sums;       // [tiles][kTsCount]
     uint64_t *tile_q;        // [tiles] exact sum of the quantised weights
     double *fstats;          // [M][kFsCount]
@@ -63,6 +78,7 @@ struct ResampleArgs {
     int32_t *anc;            // [P] filter-local ancestors
     int32_t *err;            // [2]
     double log_const;        // -dy/2 log(2 pi sigma_obs^2), added to log G only
+    int32_t *done;           // [M] per-filter completion counters, kept at 0 between steps
 };
 
 struct Ctx;
@@ -72,6 +88,7 @@ cudaError_t launch_init(const Ctx &c, cudaStream_t s);
 cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t obs_stride, const float *x_in, float *x_out,
                              cudaStream_t s);
 cudaError_t launch_resample(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s);
+cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s);  // after the log-weights were replaced
 cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_rng_philox(int64_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                               cudaStream_t s);
@@ -95,11 +112,14 @@ struct Ctx {
 
     // device memory
     TileDesc *tiles = nullptr;
+    TileDesc *subs = nullptr;     // sub-tiles of kSubTile particles (small models)
+    int32_t n_subs = 0;
     FilterDesc *filt = nullptr;
     int32_t *pfilt = nullptr;     // [P] filter of each particle (lattice kernels)
     float *x[2] = {nullptr, nullptr};
     float *logw = nullptr;
-    float *tile_max = nullptr;
+    int32_t *fmax_key = nullptr;  // [M]
+    int resample_threads = kResampleThreads;
     double *tile_sums = nullptr;
     uint64_t *tile_q = nullptr;
     double *fstats = nullptr;
@@ -117,6 +137,7 @@ struct Ctx {
     int stage_slot = 0;
     int32_t *d_t = nullptr;       // completed steps
     int32_t *err = nullptr;       // [2]
+    int32_t *done = nullptr;      // [M]
     int32_t *obs_idx = nullptr;   // [dy]
     int32_t *obs_slot = nullptr;  // [J*J] lattice node -> observation index or -1
     double *x0 = nullptr;         // [dx]

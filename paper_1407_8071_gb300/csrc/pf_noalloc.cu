@@ -25,7 +25,7 @@ constexpr size_t kTilesMax = kNoallocMaxFilters + kNoallocMaxParticles / pf::kTi
 constexpr size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kScratchBytes =
     a256(kTilesMax * sizeof(pf::TileDesc)) + a256(kNoallocMaxFilters * sizeof(pf::FilterDesc)) +
-    a256(kTilesMax * sizeof(float)) + a256(kTilesMax * pf::kTsCount * sizeof(double)) +
+    a256(kTilesMax * pf::kTsCount * sizeof(double)) +
     a256(kTilesMax * sizeof(uint64_t)) + a256(kNoallocMaxFilters * pf::kFsCount * sizeof(double)) +
     a256(kNoallocMaxFilters * 2 * sizeof(uint64_t)) + a256(kNoallocMaxParticles * sizeof(uint64_t)) +
     a256(kNoallocMaxParticles * sizeof(int32_t)) + a256(2 * sizeof(int32_t));
