@@ -102,7 +102,8 @@ typedef enum {
     PF_STAT_MEAN = 0,         /* (f, pi_t^N) with f = x[var]: post-resampling particle mean        */
     PF_STAT_LOG_EVIDENCE = 1, /* log G_t^N, eq. eqGtN (Gaussian constant included)                  */
     PF_STAT_ESS = 2,          /* (sum w)^2 / sum w^2 before resampling                               */
-    PF_STAT_LOG_Z = 3         /* log sum_i exp(l_i) of this step's log-weights (no constant)         */
+    PF_STAT_LOG_Z = 3,        /* log sum_i exp(l_i) of this step's log-weights (no constant)         */
+    PF_STAT_FALLBACK = 4      /* 1 where the learned proposal fell back to the transition this step   */
 } pf_stat_kind;
 
 /* A statistic request.  kind = PF_STAT_MEAN uses var (0 <= var < dx, or -1 for
@@ -187,6 +188,18 @@ PF_API pf_status pf_resample(pf_ctx *ctx);
  * (no step completed yet). */
 PF_API pf_status pf_estimate(pf_ctx *ctx, const pf_stat *stat, double *out);
 
+/* Picks the launch schedule of this context's hot kernels by timing the
+ * candidates on copies of its particles: for the lattice, particles per CTA
+ * (one particle per CTA up to as many as fit in 1024 threads); for every model,
+ * threads per resampling tile CTA (64, 128, 256 -- fewer threads and more CTAs
+ * for small filters).  The choice is cached per (model, lattice side, K, dx,
+ * particles, filters) for the process, and reported in h_choice[0..1] (may be
+ * NULL).  The filter's state, statistics and step counter are unchanged.
+ * Synchronises; needs about one particle buffer of temporary device memory.
+ * Errors: PF_ESTATE (between pf_propagate and pf_resample, or recording),
+ * PF_ENOMEM, PF_ECUDA. */
+PF_API pf_status pf_autotune(pf_ctx *ctx, int32_t *h_choice);
+
 /* --------------------------------------------------------------------- */
 /* Inspection and state transfer (synchronous; for tests and checkpoints) */
 /* --------------------------------------------------------------------- */
@@ -245,6 +258,69 @@ PF_API size_t pf_systematic_scratch_bytes(int32_t M, int64_t total);
  * Errors: PF_EINVAL, PF_ECUDA. */
 PF_API pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_w, const double *d_u,
                                  int32_t *d_anc, void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* --------------------------------------------------------------------- */
+/* Learned proposal network (growth direction)                            */
+/* --------------------------------------------------------------------- */
+
+/* The network of the learned proposal: 51 inputs (5x5 patches of v and w
+ * around an observed lattice node, row-major, mirrored at the lattice edge,
+ * then y at the node) -> 128 -> 128 -> 4 outputs (o_mu_v, o_mu_w, o_s_v,
+ * o_s_w), exact GELU between layers.  Parameters: PF_MLP_PARAMS FP32 values,
+ * W1 (128 x 51), b1 (128), W2 (128 x 128), b2 (128), W3 (4 x 128), b3 (4),
+ * row-major.  The kernels use bfloat16 operands on the tensor cores and FP32
+ * accumulation.  At the observed nodes the last Euler-Maruyama sub-step before
+ * an observation is then drawn from q = N(m + h o_mu, (h exp(clip(o_s,-3,3)))^2)
+ * with h = sigma_dyn sqrt(dt) and m the transition mean; the weights carry
+ * p g / q (the paper's analysis covers such importance functions, Sec. 6
+ * footnote). */
+#define PF_MLP_PARAMS 23684
+
+/* Forward pass of `rows` FP32 input rows (rows x 51, device) -> d_out
+ * (rows x 4, device).  d_theta: PF_MLP_PARAMS FP32 values on the device. */
+PF_API pf_status pf_mlp_forward(int64_t rows, const float *d_in, const float *d_theta, float *d_out, void *stream);
+
+/* Training state on the device: FP32 master parameters and Adam moments
+ * (beta1 0.9, beta2 0.999, eps 1e-8), workspace for batches up to max_batch
+ * rows.  h_theta: initial parameters (copied). */
+typedef struct pf_mlp_trainer pf_mlp_trainer;
+PF_API pf_status pf_mlp_trainer_create(const float *h_theta, int32_t n_params, int64_t max_batch,
+                                       pf_mlp_trainer **out);
+/* One step on a batch: d_X (batch x 51 inputs) and d_R (batch x 2 standardised
+ * residuals r = (x'_target - m) / h) on the device.  Loss: the mean over rows
+ * of sum_c (r_c - o_mu_c)^2 / (2 e^{2 s_c}) + s_c, s_c = clip(o_s_c, -3, 3).
+ * lr > 0 takes an Adam step; lr = 0 only computes the gradient.  h_grad
+ * (PF_MLP_PARAMS floats) and h_loss may be NULL; when either is given the
+ * call synchronises `stream`.  Deterministic (fixed-order reductions). */
+PF_API pf_status pf_mlp_train_step(pf_mlp_trainer *tr, int64_t batch, const float *d_X, const float *d_R, float lr,
+                                   float *h_grad, double *h_loss, void *stream);
+/* Copies the current parameters to host memory (synchronous). */
+PF_API pf_status pf_mlp_trainer_get(pf_mlp_trainer *tr, float *h_theta);
+/* NULL-safe. */
+PF_API void pf_mlp_trainer_destroy(pf_mlp_trainer *tr);
+
+/* Turns the learned proposal on for a lattice context (h_theta: PF_MLP_PARAMS
+ * FP32 network parameters, copied) or off (h_theta = NULL).  Each step then
+ * draws the last sub-step at the observed nodes from q (see above) with the
+ * transition's own normals, weights by g p / q, and falls back to the
+ * transition for a filter whose ESS under q is below ess_frac N (the
+ * PF_STAT_FALLBACK statistic reports it).  A zero output layer reproduces the
+ * bootstrap filter exactly.  Synchronises.  Errors: PF_EINVAL,
+ * PF_EUNSUPPORTED (not a lattice), PF_ENOMEM, PF_ESTATE. */
+PF_API pf_status pf_set_proposal(pf_ctx *ctx, const float *h_theta, int32_t n_params, double ess_frac);
+
+/* Records training tuples for the proposal network during the following
+ * steps (lattice contexts): for every resampled particle whose filter-local
+ * index is a multiple of `stride` and every observed node, the 51 network
+ * inputs of its ancestor before the last sub-step (d_X, rows of 51 floats) and
+ * the standardised residual (x_t - m) / h of its node (d_R, rows of 2 floats).
+ * d_X and d_R are caller-owned device buffers of `capacity` rows that must
+ * stay valid while recording is on; tuples past capacity are dropped.  Steps
+ * taken while recording are launched without a CUDA graph.  d_X = NULL stops
+ * recording.  Synchronises. */
+PF_API pf_status pf_record_tuples(pf_ctx *ctx, float *d_X, float *d_R, int64_t capacity, int32_t stride);
+/* Rows written so far by the current recording (at most its capacity). */
+PF_API pf_status pf_recorded_tuples(const pf_ctx *ctx, int64_t *count);
 
 /* Systematic resampling that allocates nothing.  Some callers cannot call
  * cudaMalloc when they resample -- code running while its stream is captured

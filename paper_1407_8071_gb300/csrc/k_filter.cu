@@ -22,9 +22,11 @@
 // a fixed order.
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "pf.h"
 #include "pf_internal.h"
+#include "lattice.cuh"
 
 namespace pf {
 
@@ -396,38 +398,25 @@ __global__ void __launch_bounds__(kSubTile, 16) k_propagate_small(ModelParams mp
     if (threadIdx.x == 0 && mx > -INFINITY) atomicMax(&fmax_key[st.m], float_order_key(mx));
 }
 
-// Lattice propagation (Sec. 5.1, Rogers-McCulloch form): a CTA holds ppc
-// particles; each thread owns two adjacent nodes (v, w in registers).  The
-// v-plane goes through shared memory once per sub-step (double-buffered, one
-// barrier per sub-step) for the zero-flux 5-point Laplacian.
-template <typename Real>
-__device__ __forceinline__ Real fhn_drift_v(const ModelParams &mp, Real v, Real w, Real lap, Real I)
-{
-    const Real a = par<Real>(mp, 0), c1 = par<Real>(mp, 2), c2 = par<Real>(mp, 3), D = par<Real>(mp, 5);
-    return c1 * v * (v - a) * ((Real)1 - v) - c2 * v * w + D * lap + I;
-}
-
-template <typename Real>
-__device__ __forceinline__ Real fhn_drift_w(const ModelParams &mp, Real v, Real w)
-{
-    const Real b = par<Real>(mp, 1), d = par<Real>(mp, 4);
-    return b * (v - d * w);
-}
-
 // One observation interval of lattice particles.  Real = float for the
 // filters (state in FP32) and double for the truth record.  Thread (slot s,
 // pair q): particle p = blockIdx.x * ppc + s, nodes 2q and 2q+1 (same row);
-// threads past ppc * pairs (warp padding) hold no particle.
+// threads past ppc * pairs (warp padding) hold no particle.  The v-plane sits
+// in shared memory as one (v[2q], v[2q+1]) pair per thread, so every
+// neighbour read is a conflict-free 2-word load; a missing neighbour (zero
+// flux) reads the node itself, which turns sum_existing(v_n) - count v into
+// sum_4(v_n) - 4 v.
 template <typename Real>
-__global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const int32_t *pfilt,
-                                const FilterDesc *filt, const Real *__restrict__ x_in, Real *__restrict__ x_out,
-                                int64_t P, float *logw, const float *obs, int32_t obs_stride,
-                                const int32_t *obs_slot, const int32_t *d_t, int32_t fixed_c0, int32_t fixed_c2,
-                                int32_t t_direct, int32_t ppc, int32_t *fmax_key)
+__global__ void __launch_bounds__(1024, 2)
+    k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const int32_t *pfilt, const FilterDesc *filt,
+                    const Real *__restrict__ x_in, Real *__restrict__ x_out, int64_t P, float *logw, const float *obs,
+                    int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t fixed_c0,
+                    int32_t fixed_c2, int32_t t_direct, int32_t ppc, int32_t *fmax_key, int32_t n_steps)
 {
+    using Pair = typename std::conditional<std::is_same<Real, float>::value, float2, double2>::type;
     extern __shared__ unsigned char smem_raw[];
-    const int J = mp.J, nn = J * J, pairs = nn / 2;
-    Real *sv = reinterpret_cast<Real *>(smem_raw);  // [2][ppc][nn]
+    const int J = mp.J, nn = J * J, pairs = nn / 2, half = J / 2;
+    Pair *sv = reinterpret_cast<Pair *>(smem_raw);  // [2][ppc][pairs]
     const int slot = (int)threadIdx.x / pairs;
     const int s = min(slot, ppc);                  // s == ppc: padding thread
     const int q = threadIdx.x - min(slot, ppc - 1) * pairs;
@@ -461,35 +450,35 @@ __global__ void k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const 
     const bool stim_node0 = row < blk && col < blk, stim_node1 = row < blk && col + 1 < blk;
     const int64_t n_base = (int64_t)(t - 1) * mp.K;  // (n - 1) of sub-step k is n_base + k
     const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
-    const bool up = row > 0, down = row < J - 1, left = col > 0, right = col + 2 < J;
-    const Real cnt0 = (Real)((int)up + (int)down + (int)left + 1);
-    const Real cnt1 = (Real)((int)up + (int)down + (int)right + 1);
+    // neighbour pairs (the own pair where the lattice ends)
+    const int qu = row > 0 ? q - half : q, qd = row < J - 1 ? q + half : q;
+    const int ql = col > 0 ? q - 1 : q, qr = col + 2 < J ? q + 1 : q;
+    const bool has_left = col > 0, has_right = col + 2 < J;
 
-    for (int k = 0; k < mp.K; ++k) {
-        Real *buf = sv + ((k & 1) * ppc + (active ? s : 0)) * nn;
+    for (int k = 0; k < n_steps; ++k) {
+        Pair *buf = sv + ((k & 1) * ppc + (active ? s : 0)) * pairs;
         if (active) {
-            buf[n0] = v0;
-            buf[n0 + 1] = v1;
+            Pair mine;
+            mine.x = v0;
+            mine.y = v1;
+            buf[q] = mine;
         }
         __syncthreads();
         if (active) {
             Real z[4];
             normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
-            Real l0 = v1, l1 = v0;
-            if (up) { l0 += buf[n0 - J]; l1 += buf[n0 + 1 - J]; }
-            if (down) { l0 += buf[n0 + J]; l1 += buf[n0 + 1 + J]; }
-            if (left) l0 += buf[n0 - 1];
-            if (right) l1 += buf[n0 + 2];
-            l0 -= cnt0 * v0;
-            l1 -= cnt1 * v1;
+            const Pair up = buf[qu], dn = buf[qd], lf = buf[ql], rt = buf[qr];
+            const Real left = has_left ? lf.y : v0, right = has_right ? rt.x : v1;
+            Real l0, l1;
+            pair_laplacian<Real>(v0, v1, up.x, up.y, dn.x, dn.y, left, right, l0, l1);
             const bool on = (n_base + k) < stim_steps;
             const Real I0 = (on && stim_node0) ? amp : (Real)0, I1 = (on && stim_node1) ? amp : (Real)0;
             const Real fv0 = fhn_drift_v<Real>(mp, v0, w0, l0, I0), fv1 = fhn_drift_v<Real>(mp, v1, w1, l1, I1);
             const Real fw0 = fhn_drift_w<Real>(mp, v0, w0), fw1 = fhn_drift_w<Real>(mp, v1, w1);
-            v0 = v0 + dt * fv0 + sq * z[0];
-            w0 = w0 + dt * fw0 + sq * z[1];
-            v1 = v1 + dt * fv1 + sq * z[2];
-            w1 = w1 + dt * fw1 + sq * z[3];
+            v0 = em_update(v0, fv0, z[0], dt, sq);
+            w0 = em_update(w0, fw0, z[1], dt, sq);
+            v1 = em_update(v1, fv1, z[2], dt, sq);
+            w1 = em_update(w1, fw1, z[3], dt, sq);
         }
     }
     if (active) {
@@ -925,19 +914,21 @@ __global__ void k_rng_normals(int64_t n, const uint4 *ctr, Key key, float4 *z)
 namespace {
 
 // Threads of a lattice CTA: ppc particles x J^2/2 node pairs, rounded up to
-// whole warps (the extra threads hold no particle).
-int fhn_threads(const ModelParams &mp, int *ppc)
+// whole warps (the extra threads hold no particle).  want = 0 picks as many
+// particles as fit in 1024 threads (at most 8).
+int fhn_threads(const ModelParams &mp, int *ppc, int want = 0)
 {
     const int pairs = mp.J * mp.J / 2;
     int n = 1;
     while ((n + 1) * pairs <= 1024 && n < 8) ++n;
+    if (want > 0 && want < n) n = want;
     *ppc = n;
     return (n * pairs + 31) / 32 * 32;
 }
 
 size_t fhn_smem(const ModelParams &mp, int threads, int ppc, size_t real_bytes)
 {
-    const size_t planes = 2 * (size_t)ppc * mp.J * mp.J * real_bytes;
+    const size_t planes = 2 * (size_t)ppc * mp.J * mp.J * real_bytes;  // two buffers of ppc v-planes
     const size_t red = (size_t)threads * sizeof(float);
     return planes > red ? planes : red;
 }
@@ -1003,12 +994,18 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
 {
     if (c.mp.kind == kFhnLattice) {
         int ppc;
-        const int threads = fhn_threads(c.mp, &ppc);
+        const int threads = fhn_threads(c.mp, &ppc, c.fhn_ppc);
         const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
         const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
+        static bool carveout_set = false;  // prefer shared memory so two CTAs fit per SM
+        if (!carveout_set) {
+            cudaFuncSetAttribute(k_propagate_fhn<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+            carveout_set = true;
+        }
         k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
                                                            c.logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc,
-                                                           c.fmax_key);
+                                                           c.fmax_key, c.mp.K);
         return cudaGetLastError();
     }
     switch (c.mp.dx) {
@@ -1018,6 +1015,19 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
     case 4: return propagate_small_launch<4>(c, d_obs, stride, xi, xo, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, float *x, int32_t n_steps,
+                                cudaStream_t s)
+{
+    int ppc;
+    const int threads = fhn_threads(c.mp, &ppc, c.fhn_ppc);
+    const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
+    const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
+    k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, x, x, c.P, nullptr,
+                                                       d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc, nullptr,
+                                                       n_steps);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)
@@ -1099,7 +1109,7 @@ cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int
         const double *xi = d_x + (int64_t)(t - 1) * mp.dx;
         double *xo = d_x + (int64_t)t * mp.dx;
         k_propagate_fhn<double><<<1, threads, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1, nullptr,
-                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1, nullptr);
+                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1, nullptr, mp.K);
         if (d_y)
             k_observe<<<(mp.dy + 255) / 256, 256, 0, s>>>(mp, key, d_obs_idx, t, record, xo,
                                                           d_y + (int64_t)(t - 1) * mp.dy);

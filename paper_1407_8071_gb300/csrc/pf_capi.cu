@@ -3,6 +3,8 @@
 // the stateless building blocks.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -108,12 +110,28 @@ cudaError_t stage_obs(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind k
 
 int32_t kernel_stride(const Ctx &c, int mode) { return mode == 0 ? 0 : c.mp.dy; }
 
-cudaError_t enqueue_step(Ctx &c, int mode)
+cudaError_t enqueue_propagate(Ctx &c, int mode)
+{
+    if (c.split_path()) return launch_propagate_split(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.stream);
+    return launch_propagate(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[c.cur], c.stream);
+}
+
+cudaError_t enqueue_resample(Ctx &c)
 {
     const int nxt = c.cur ^ 1;
-    cudaError_t e = launch_propagate(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[c.cur], c.stream);
+    cudaError_t e = launch_resample(c, c.x[c.cur], c.x[nxt], c.stream);
+    if (e == cudaSuccess && c.rec_X && c.rec_count < c.rec_cap) {
+        e = launch_gather_tuples(c, c.x[nxt], c.stream);
+        c.rec_count += c.rec_sel_total * c.mp.dy;
+    }
+    return e;
+}
+
+cudaError_t enqueue_step(Ctx &c, int mode)
+{
+    cudaError_t e = enqueue_propagate(c, mode);
     if (e != cudaSuccess) return e;
-    return launch_resample(c, c.x[c.cur], c.x[nxt], c.stream);
+    return enqueue_resample(c);
 }
 
 pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind)
@@ -126,6 +144,14 @@ pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind
     if (e != cudaSuccess) return cuda_fail(c, e, "observation copy");
     const int mode = obs_mode(stride);
     const int par = c.cur;
+    if (c.rec_X) {  // recording steps carry a moving output offset: launched directly
+        e = enqueue_step(c, mode);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        c.cur ^= 1;
+        c.t += 1;
+        c.steps_done = true;
+        return PF_OK;
+    }
     if (!c.graph[par] || c.graph_mode[par] != mode) {
         if (c.graph[par]) {
             cudaGraphExecDestroy(c.graph[par]);
@@ -289,6 +315,33 @@ int ceil_log2_host(int64_t n)
     return L;
 }
 }  // namespace pf
+
+// Schedules chosen by pf_autotune, per (model, J, K, dx, particles, filters).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int64_t, int32_t>, std::pair<int, int>> g_tune_cache;
+
+// Median time of `reps` launches of fn on the context's stream (ms).
+template <typename F>
+static float time_ms(Ctx &c, int reps, F fn)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    std::vector<float> ts;
+    for (int r = 0; r < reps; ++r) {
+        cudaEventRecord(a, c.stream);
+        fn();
+        cudaEventRecord(b, c.stream);
+        cudaEventSynchronize(b);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        ts.push_back(ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
+}
 
 extern "C" {
 
@@ -496,8 +549,7 @@ static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride,
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_propagate called twice without pf_resample");
     cudaSetDevice(c.device);
     cudaError_t e = stage_obs(c, obs, obs_stride, kind);
-    if (e == cudaSuccess)
-        e = launch_propagate(c, c.d_obs, kernel_stride(c, obs_mode(obs_stride)), c.x[c.cur], c.x[c.cur], c.stream);
+    if (e == cudaSuccess) e = enqueue_propagate(c, obs_mode(obs_stride));
     if (e != cudaSuccess) return cuda_fail(c, e, "propagate");
     c.phase = 1;
     return PF_OK;
@@ -520,7 +572,7 @@ pf_status pf_resample(pf_ctx *h)
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
     if (c.phase != 1) return fail(c, PF_ESTATE, "pf_resample needs a preceding pf_propagate");
     cudaSetDevice(c.device);
-    const cudaError_t e = launch_resample(c, c.x[c.cur], c.x[c.cur ^ 1], c.stream);
+    const cudaError_t e = enqueue_resample(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "resample");
     c.cur ^= 1;
     c.t += 1;
@@ -562,6 +614,7 @@ pf_status pf_estimate(pf_ctx *h, const pf_stat *stat, double *out)
     case PF_STAT_LOG_EVIDENCE: slot = kFsLogG; break;
     case PF_STAT_ESS: slot = kFsEss; break;
     case PF_STAT_LOG_Z: slot = kFsLogZ; break;
+    case PF_STAT_FALLBACK: slot = kFsFallback; break;
     default: return fail(c, PF_EINVAL, "unknown statistic");
     }
     std::vector<double> fs((size_t)M * kFsCount);
@@ -573,6 +626,199 @@ pf_status pf_estimate(pf_ctx *h, const pf_stat *stat, double *out)
         double s = 0.0;
         for (int m = 0; m < M; ++m) s += fs[(size_t)m * kFsCount + slot];
         out[0] = s / M;
+    }
+    return PF_OK;
+}
+
+static void drop_graphs(Ctx &c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c.graph[k]) cudaGraphExecDestroy(c.graph[k]);
+        c.graph[k] = nullptr;
+        c.graph_mode[k] = -1;
+    }
+}
+
+// Buffers shared by the learned proposal and the tuple recording.
+static pf_status ensure_proposal_buffers(Ctx &c)
+{
+    if (c.rows) return PF_OK;
+    const size_t R = (size_t)c.P * c.mp.dy;
+    const bool ok = alloc_n(c, c.theta, (size_t)PF_MLP_PARAMS) &&
+                    alloc_n(c, c.wpack, (size_t)(128 * 64 + 128 * 128 + 8 * 128) + 128 * 128) &&
+                    alloc_n(c, c.rows, R * 64) && alloc_n(c, c.mlp_out, R * 4) && alloc_n(c, c.xboot, R * 2) &&
+                    alloc_n(c, c.mp_obs, R * 2) && alloc_n(c, c.logw_boot, (size_t)c.P) &&
+                    alloc_n(c, c.rec_sel_off, (size_t)c.M);
+    return ok ? PF_OK : fail(c, PF_ENOMEM, "proposal buffers: device allocation failed");
+}
+
+pf_status pf_set_proposal(pf_ctx *h, const float *h_theta, int32_t n_params, double ess_frac)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_proposal between pf_propagate and pf_resample");
+    if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "the learned proposal is for the lattice");
+    if (h_theta && (n_params != PF_MLP_PARAMS || !(ess_frac >= 0.0 && ess_frac <= 1.0)))
+        return fail(c, PF_EINVAL, "n_params must be PF_MLP_PARAMS and ess_frac in [0, 1]");
+    pf_status st = sync(c, "set_proposal");
+    if (st != PF_OK) return st;
+    drop_graphs(c);
+    if (!h_theta) {
+        c.prop_on = false;
+        return PF_OK;
+    }
+    st = ensure_proposal_buffers(c);
+    if (st != PF_OK) return st;
+    cudaError_t e = cudaMemcpy(c.theta, h_theta, PF_MLP_PARAMS * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_mlp_pack(c.theta, c.wpack, c.wpack + (128 * 64 + 128 * 128 + 8 * 128), c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_proposal");
+    c.prop_on = true;
+    c.prop_ess_frac = (float)ess_frac;
+    return PF_OK;
+}
+
+pf_status pf_record_tuples(pf_ctx *h, float *d_X, float *d_R, int64_t capacity, int32_t stride)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the lattice");
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_record_tuples between pf_propagate and pf_resample");
+    pf_status st = sync(c, "record_tuples");
+    if (st != PF_OK) return st;
+    drop_graphs(c);
+    if (!d_X) {
+        c.rec_X = c.rec_R = nullptr;
+        return PF_OK;
+    }
+    if (!d_R || capacity < 1 || stride < 1) return fail(c, PF_EINVAL, "d_R, capacity >= 1 and stride >= 1 needed");
+    st = ensure_proposal_buffers(c);
+    if (st != PF_OK) return st;
+    std::vector<int64_t> sel(c.M);
+    int64_t acc = 0;
+    for (int m = 0; m < c.M; ++m) {
+        sel[m] = acc;
+        acc += (c.N[m] + stride - 1) / stride;
+    }
+    const cudaError_t e = cudaMemcpy(c.rec_sel_off, sel.data(), c.M * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "record_tuples");
+    c.rec_X = d_X;
+    c.rec_R = d_R;
+    c.rec_cap = capacity;
+    c.rec_count = 0;
+    c.rec_stride = stride;
+    c.rec_sel_total = acc;
+    return PF_OK;
+}
+
+pf_status pf_recorded_tuples(const pf_ctx *h, int64_t *count)
+{
+    if (!h || !count) return PF_EINVAL;
+    *count = std::min(h->c.rec_count, h->c.rec_cap);
+    return PF_OK;
+}
+
+pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 0 || c.rec_X) return fail(c, PF_ESTATE, "pf_autotune needs a context between steps, not recording");
+    pf_status st = sync(c, "autotune");
+    if (st != PF_OK) return st;
+    const auto key = std::make_tuple((int)c.mp.kind, (int)c.mp.J, (int)c.mp.K, (int)c.mp.dx, (int64_t)c.P, c.M);
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c.fhn_ppc = it->second.first;
+            c.resample_threads = it->second.second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        // Trials run on copies: the current particles are copied into the other
+        // buffer and propagated there; resampling writes into a temporary
+        // buffer.  Everything a caller can read afterwards -- log-weights,
+        // ancestors, per-filter scalars, estimates, the step counter -- is saved
+        // before and restored after.
+        const size_t P = (size_t)c.P, dx = (size_t)c.mp.dx, M = (size_t)c.M;
+        const size_t xb = P * dx * sizeof(float);
+        const size_t save_bytes = P * 4 + P * 4 + M * kFsCount * 8 + M * dx * 8 + dx * 8 + M * 4;
+        char *tmp = nullptr, *save = nullptr;
+        cudaError_t e = cudaMalloc(&tmp, xb);
+        if (e == cudaSuccess) e = cudaMalloc(&save, save_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (tmp) cudaFree(tmp);
+            return fail(c, PF_ENOMEM, "autotune: no room for its trial buffers");
+        }
+        struct Span { void *dev; size_t bytes; };
+        const Span spans[] = {{c.logw, P * 4}, {c.anc, P * 4}, {c.fstats, M * kFsCount * 8}, {c.est, M * dx * 8},
+                              {c.ens, dx * 8}, {c.fmax_key, M * 4}};
+        size_t o = 0;
+        for (const Span &sp : spans) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(save + o, sp.dev, sp.bytes, cudaMemcpyDeviceToDevice, c.stream);
+            o += sp.bytes;
+        }
+        float *scratch = c.x[c.cur ^ 1];
+        float *dest = reinterpret_cast<float *>(tmp);
+        std::vector<float> zeros(M * c.mp.dy, 0.0f);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_obs, zeros.data(), zeros.size() * 4, cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        int best_ppc = c.fhn_ppc, best_rt = c.resample_threads;
+        auto trial_step = [&] {
+            cudaMemcpyAsync(scratch, c.x[c.cur], xb, cudaMemcpyDeviceToDevice, c.stream);
+            launch_propagate(c, c.d_obs, 0, scratch, scratch, c.stream);
+        };
+        if (e == cudaSuccess && c.mp.kind == PF_MODEL_FHN_LATTICE) {  // particles per lattice CTA
+            const int pairs = c.mp.J * c.mp.J / 2;
+            int maxp = 1;
+            while ((maxp + 1) * pairs <= 1024 && maxp < 8) ++maxp;
+            float best = 1e30f;
+            for (int ppc = 1; ppc <= maxp; ++ppc) {
+                c.fhn_ppc = ppc;
+                const float ms = time_ms(c, 3, trial_step);
+                if (ms < best) { best = ms; best_ppc = ppc; }
+            }
+            c.fhn_ppc = best_ppc;
+        }
+        if (e == cudaSuccess) {  // threads per resampling tile CTA
+            int max_len = 1;
+            for (int32_t n : c.N) max_len = std::max(max_len, std::min(n, kTile));
+            std::vector<int> cands;
+            for (int th = 64; th <= kResampleThreads; th *= 2)
+                if (th * kItems >= max_len) cands.push_back(th);
+            float best = 1e30f;
+            for (int th : cands) {
+                c.resample_threads = th;
+                trial_step();
+                const float ms = time_ms(c, 3, [&] { launch_resample(c, scratch, dest, c.stream); });
+                if (ms < best) { best = ms; best_rt = th; }
+            }
+            c.resample_threads = best_rt;
+        }
+        o = 0;
+        for (const Span &sp : spans) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(sp.dev, save + o, sp.bytes, cudaMemcpyDeviceToDevice, c.stream);
+            o += sp.bytes;
+        }
+        const int32_t t_now = c.t;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_t, &t_now, sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        cudaFree(tmp);
+        cudaFree(save);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {c.fhn_ppc, c.resample_threads};
+    }
+    drop_graphs(c);
+    if (h_choice) {
+        h_choice[0] = c.fhn_ppc;
+        h_choice[1] = c.resample_threads;
     }
     return PF_OK;
 }

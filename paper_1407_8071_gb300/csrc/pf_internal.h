@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "pf.h"
@@ -52,7 +53,9 @@ __host__ __device__ __forceinline__ float float_from_order_key(int32_t k)
 constexpr int32_t kNegInfKey = (int32_t)0x807FFFFF;  // float_order_key(-inf)
 
 // Per-filter scalars kept in FP64 on the device.
-enum FStat : int { kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsCount = 8 };
+enum FStat : int {
+    kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsFallback = 5, kFsCount = 8
+};
 // Per-tile FP64 partial sums.
 enum TSum : int { kTsW = 0, kTsW2 = 1, kTsCount = 2 };
 
@@ -89,6 +92,14 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t obs_strid
                              cudaStream_t s);
 cudaError_t launch_resample(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s);
 cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s);  // after the log-weights were replaced
+// Learned proposal (k_filter.cu, k_proposal.cu, k_mlp.cu).
+cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, float *x, int32_t n_steps,
+                                cudaStream_t s);
+cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t stride, float *x, cudaStream_t s);
+cudaError_t launch_gather_tuples(const Ctx &c, const float *x_new, cudaStream_t s);
+cudaError_t launch_mlp_pack(const float *theta, __nv_bfloat16 *wp, __nv_bfloat16 *w2t, cudaStream_t s);
+cudaError_t launch_mlp_forward_bf16(const __nv_bfloat16 *rows, int64_t R, const __nv_bfloat16 *wp, const float *theta,
+                                    float *out, cudaStream_t s);
 cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_rng_philox(int64_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                               cudaStream_t s);
@@ -120,6 +131,7 @@ struct Ctx {
     float *logw = nullptr;
     int32_t *fmax_key = nullptr;  // [M]
     int resample_threads = kResampleThreads;
+    int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
     double *tile_sums = nullptr;
     uint64_t *tile_q = nullptr;
     double *fstats = nullptr;
@@ -141,6 +153,22 @@ struct Ctx {
     int32_t *obs_idx = nullptr;   // [dy]
     int32_t *obs_slot = nullptr;  // [J*J] lattice node -> observation index or -1
     double *x0 = nullptr;         // [dx]
+
+    // learned proposal (lattice) and training-tuple recording
+    bool prop_on = false;
+    float prop_ess_frac = 0.1f;
+    float *theta = nullptr;           // [PF_MLP_PARAMS] FP32
+    __nv_bfloat16 *wpack = nullptr;   // packed BF16 weights (+ W2^T)
+    __nv_bfloat16 *rows = nullptr;    // [P * dy][64] network inputs
+    float *mlp_out = nullptr;         // [P * dy][4]
+    float *xboot = nullptr;           // [P][dy][2] the transition's candidates at the observed nodes
+    float *mp_obs = nullptr;          // [P][dy][2] transition means at the observed nodes
+    float *logw_boot = nullptr;       // [P]
+    float *rec_X = nullptr, *rec_R = nullptr;  // caller's tuple buffers (recording armed when non-null)
+    int64_t rec_cap = 0, rec_count = 0, rec_sel_total = 0;
+    int32_t rec_stride = 1;
+    int64_t *rec_sel_off = nullptr;   // [M] kept particles before each filter
+    bool split_path() const { return prop_on || rec_X != nullptr; }
 
     int cur = 0;  // x[cur] holds the current particles
     int32_t t = 0;

@@ -20,7 +20,7 @@ from . import workloads as W
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ENUMERIC, PF_ETIMEOUT, PF_ESTATE, PF_EUNSUPPORTED = range(8)
 STATUS_NAMES = ["PF_OK", "PF_EINVAL", "PF_ENOMEM", "PF_ECUDA", "PF_ENUMERIC", "PF_ETIMEOUT", "PF_ESTATE",
                 "PF_EUNSUPPORTED"]
-PF_STAT_MEAN, PF_STAT_LOG_EVIDENCE, PF_STAT_ESS, PF_STAT_LOG_Z = range(4)
+PF_STAT_MEAN, PF_STAT_LOG_EVIDENCE, PF_STAT_ESS, PF_STAT_LOG_Z, PF_STAT_FALLBACK = range(5)
 
 
 class pf_model(ctypes.Structure):
@@ -70,6 +70,16 @@ _SIGS = {
                                          c_size_t, c_void_p]),
     "pf_systematic_resample_noalloc": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p,
                                                  c_void_p]),
+    "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
+    "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
+    "pf_record_tuples": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
+    "pf_recorded_tuples": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "pf_mlp_forward": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pf_mlp_trainer_create": (c_int32, [POINTER(c_float), c_int32, c_int64, POINTER(c_void_p)]),
+    "pf_mlp_train_step": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_float, POINTER(c_float),
+                                    POINTER(c_double), c_void_p]),
+    "pf_mlp_trainer_get": (c_int32, [c_void_p, POINTER(c_float)]),
+    "pf_mlp_trainer_destroy": (None, [c_void_p]),
     "pf_simulate": (c_int32, [POINTER(pf_model), c_double, POINTER(pf_obs_op), POINTER(pf_noise), c_int32, c_int32,
                               c_int32, POINTER(c_double), POINTER(c_float)]),
 }
@@ -169,6 +179,50 @@ def pf_systematic_resample_noalloc(N: Sequence[int], d_w, d_u, d_anc, stream=Non
     Nh = np.ascontiguousarray(N, dtype=np.int32)
     _check(lib().pf_systematic_resample_noalloc(len(Nh), _ip(Nh), d_w.data_ptr(), d_u.data_ptr(), d_anc.data_ptr(),
                                                 stream))
+
+
+MLP_PARAMS = 23684
+
+
+def pf_mlp_forward(d_in, d_theta, d_out, stream=None):
+    """Network forward of d_in (rows x 51 FP32, device) into d_out (rows x 4)."""
+    _check(lib().pf_mlp_forward(d_in.shape[0], d_in.data_ptr(), d_theta.data_ptr(), d_out.data_ptr(), stream))
+
+
+class MLPTrainer:
+    """Adam training of the proposal network on the GPU (pf_mlp_trainer_*)."""
+
+    def __init__(self, theta, max_batch: int):
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        assert th.size == MLP_PARAMS
+        h = c_void_p()
+        _check(lib().pf_mlp_trainer_create(_fp(th), MLP_PARAMS, int(max_batch), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, d_X, d_R, lr: float, want_grad: bool = False, want_loss: bool = True, stream=None):
+        g = np.empty(MLP_PARAMS, dtype=np.float32) if want_grad else None
+        loss = c_double(0.0)
+        _check(lib().pf_mlp_train_step(self.h, d_X.shape[0], d_X.data_ptr(), d_R.data_ptr(), float(lr),
+                                       _fp(g) if g is not None else POINTER(c_float)(),
+                                       ctypes.byref(loss) if (want_loss or want_grad) else POINTER(c_double)(),
+                                       stream))
+        return loss.value, g
+
+    def theta(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(lib().pf_mlp_trainer_get(self.h, _fp(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pf_mlp_trainer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------
@@ -303,6 +357,32 @@ class EnsembleFilter:
         a = np.empty(self.P, dtype=np.int32)
         _check(lib().pf_get_ancestors(self.h, _ip(a)), self.h)
         return a
+
+    def autotune(self):
+        """Pick the launch schedule by timing (cached per shape); returns (particles per lattice CTA, resample threads)."""
+        ch = (c_int32 * 2)()
+        _check(lib().pf_autotune(self.h, ch), self.h)
+        return int(ch[0]), int(ch[1])
+
+    def set_proposal(self, theta, ess_frac: float = 0.1):
+        """Learned proposal on (theta: PF_MLP_PARAMS values) or off (None)."""
+        if theta is None:
+            _check(lib().pf_set_proposal(self.h, POINTER(c_float)(), 0, 0.0), self.h)
+            return
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().pf_set_proposal(self.h, _fp(th), th.size, float(ess_frac)), self.h)
+
+    def record_tuples(self, d_X, d_R, stride: int = 1):
+        """Record (inputs, standardised residual) training tuples into device tensors (None stops)."""
+        if d_X is None:
+            _check(lib().pf_record_tuples(self.h, None, None, 0, 1), self.h)
+            return
+        _check(lib().pf_record_tuples(self.h, d_X.data_ptr(), d_R.data_ptr(), d_X.shape[0], int(stride)), self.h)
+
+    def recorded_tuples(self) -> int:
+        n = c_int64()
+        _check(lib().pf_recorded_tuples(self.h, ctypes.byref(n)), self.h)
+        return n.value
 
     def offsets(self) -> np.ndarray:
         return np.concatenate([[0], np.cumsum(self.N)]).astype(np.int64)

@@ -1,0 +1,70 @@
+"""Training the learned proposal from tuples the filter itself generates.
+
+The plain (bootstrap) lattice filter records, at each observation, for its
+resampled particles and each observed node, the network input of the
+ancestor before the last sub-step and the standardised residual of the
+node's new value, r = (x_t - m) / h (pf_record_tuples).  The network is then
+fitted to those tuples by minimising the Gaussian negative log-likelihood on
+the GPU (pf_mlp_train_step): it learns where, given the local state and the
+observation, the resampled (posterior) particles moved in their last
+sub-step.  All arithmetic runs in libpf_gb300.so; this module only orders the
+calls.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import pf
+from . import workloads as W
+
+
+def collect_tuples(spec: W.ModelSpec, M: int, N: int, record: np.ndarray, seed: int, capacity: int,
+                   stride: int = 1, steps: int | None = None):
+    """Runs the bootstrap filter over the record and returns (X, R) device tensors
+    (capacity x 51 and capacity x 2) holding the first `count` tuples, and count."""
+    import torch
+    X = torch.empty((capacity, 51), dtype=torch.float32, device="cuda")
+    R = torch.empty((capacity, 2), dtype=torch.float32, device="cuda")
+    steps = len(record) if steps is None else steps
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.record_tuples(X, R, stride=stride)
+        for t in range(steps):
+            f.step(record[t])
+            if f.recorded_tuples() >= capacity:
+                break
+        n = f.recorded_tuples()
+        f.record_tuples(None, None)
+    return X[:n], R[:n], n
+
+
+def train(theta0: np.ndarray, X, R, epochs: int = 4, batch: int = 8192, lr: float = 1e-3, seed: int = 0,
+          log=None) -> tuple[np.ndarray, list]:
+    """Adam on the tuples in shuffled mini-batches; returns the parameters and the loss history."""
+    import torch
+    n = X.shape[0]
+    tr = pf.MLPTrainer(theta0, max_batch=batch)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    losses = []
+    try:
+        for ep in range(epochs):
+            perm = torch.randperm(n, device="cuda", generator=g)
+            for b0 in range(0, n - batch + 1, batch):
+                idx = perm[b0:b0 + batch]
+                loss, _ = tr.step(X[idx].contiguous(), R[idx].contiguous(), lr=lr)
+                losses.append(loss)
+            if log:
+                log(f"epoch {ep}: loss {np.mean(losses[-max(1, n // batch):]):.5f}")
+        return tr.theta(), losses
+    finally:
+        tr.close()
+
+
+def mean_nll(theta: np.ndarray, X, R) -> float:
+    """Held-out loss of a parameter vector (one gradient-free trainer step)."""
+    tr = pf.MLPTrainer(theta, max_batch=X.shape[0])
+    try:
+        loss, _ = tr.step(X, R, lr=0.0)
+        return loss
+    finally:
+        tr.close()

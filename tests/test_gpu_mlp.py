@@ -1,0 +1,101 @@
+"""The learned proposal's network on the GPU against the FP64 oracle (oracle/mlp.py).
+
+Tolerances (BF16 operands and activations on both sides; the GPU accumulates
+in FP32 and stores backward intermediates in BF16, the oracle works in FP64):
+* forward: |o_gpu - o| <= 2e-2 (|o| + rms(o)),
+* gradient: cosine >= 0.999 and ||g_gpu - g|| <= 5e-2 ||g|| overall and per
+  parameter block; loss within 1e-3 relative,
+* Adam's first step: theta moves by lr sign(g) wherever |g| is not tiny,
+* training steps are bit-for-bit repeatable.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1407_8071_gb300 import pf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _theta(seed, out_scale=0.5):
+    p = mlp.unpack(mlp.init_params(seed, out_scale=out_scale))
+    rng = np.random.default_rng(seed + 100)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(0.0, 0.1, p[k].shape)
+    return mlp.pack(p).astype(np.float32).astype(np.float64)
+
+
+def _rows(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0.0, 1.0, (n, mlp.IN))
+    R = rng.normal(0.0, 1.0, (n, 2)) + 0.3 * X[:, :2]
+    return X.astype(np.float32).astype(np.float64), R.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("n", [1, 17, 64, 1000, 70001])
+def test_forward_matches_oracle(n):
+    th = _theta(1)
+    X, _ = _rows(n, 2)
+    d_out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    pf.pf_mlp_forward(torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(th.astype(np.float32)).cuda(),
+                      d_out)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().astype(np.float64)
+    ref, _ = mlp.forward(th, X, bf16_emulation=True)
+    scale = np.sqrt(np.mean(ref ** 2, axis=0, keepdims=True))
+    assert np.all(np.abs(got - ref) <= 2e-2 * (np.abs(ref) + scale)), np.max(np.abs(got - ref) / (np.abs(ref) + scale))
+
+
+def _blocks():
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in mlp._SHAPES])
+    return [(name, offs[i], offs[i + 1]) for i, (name, _) in enumerate(mlp._SHAPES)]
+
+
+@pytest.mark.parametrize("B", [64, 300, 4096])
+def test_gradient_matches_oracle(B):
+    th = _theta(3)
+    X, R = _rows(B, 4)
+    tr = pf.MLPTrainer(th, max_batch=B)
+    loss, g = tr.step(torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(R.astype(np.float32)).cuda(),
+                      lr=0.0, want_grad=True)
+    tr.close()
+    lo, go = mlp.loss_and_grad(th, X, R, bf16_emulation=True)
+    assert loss == pytest.approx(lo, rel=1e-3)
+    g = g.astype(np.float64)
+    cos = g @ go / (np.linalg.norm(g) * np.linalg.norm(go))
+    assert cos >= 0.999, cos
+    assert np.linalg.norm(g - go) <= 5e-2 * np.linalg.norm(go)
+    for name, a, b in _blocks():
+        assert np.linalg.norm(g[a:b] - go[a:b]) <= 5e-2 * np.linalg.norm(go[a:b]) + 1e-7, name
+
+
+def test_adam_first_step_and_determinism():
+    th = _theta(5)
+    X, R = _rows(2048, 6)
+    dX, dR = torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(R.astype(np.float32)).cuda()
+    lr = 1e-3
+    t1 = pf.MLPTrainer(th, max_batch=2048)
+    t1.step(dX, dR, lr=lr)
+    th1 = t1.theta().astype(np.float64)
+    t2 = pf.MLPTrainer(th, max_batch=2048)
+    t2.step(dX, dR, lr=lr)
+    assert np.array_equal(t1.theta(), t2.theta())
+    t1.close()
+    t2.close()
+    _, go = mlp.loss_and_grad(th, X, R, bf16_emulation=True)
+    big = np.abs(go) > 1e-2 * np.abs(go).max()
+    step = th1 - th
+    assert np.all(np.abs(step) <= lr * 1.0001 + 1e-7)
+    assert np.mean(np.sign(step[big]) == -np.sign(go[big])) >= 0.99
+
+
+def test_training_reduces_the_loss():
+    th = mlp.init_params(7, out_scale=0.0)
+    X, R = _rows(8192, 8)
+    dX, dR = torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(R.astype(np.float32)).cuda()
+    tr = pf.MLPTrainer(th, max_batch=8192)
+    losses = [tr.step(dX, dR, lr=3e-3)[0] for _ in range(60)]
+    tr.close()
+    # R = noise + 0.3 X[:, :2]: a good fit removes part of the variance
+    assert losses[-1] < losses[0] - 0.05, (losses[0], losses[-1])
