@@ -8,7 +8,12 @@ every particle, Gaussian weights, FP64 normalisation, systematic resampling
 with the gather, and the per-filter and ensemble means.  The metric is
 particle-steps/s (one Euler-Maruyama sub-step of one particle).
 
-`--workload fhn` runs the 40 x 40 FitzHugh-Nagumo lattice at M = 32, N = 1024.
+`--workload fhn` runs the 40 x 40 FitzHugh-Nagumo lattice at M = 32, N = 1024;
+`--workload fhn-learned` the same with the learned proposal (network trained,
+untimed, on tuples the plain filter records); `--workload ragged` 256 lattice
+filters of 20 x 20 nodes with N log-uniform in [64, 4096], independent records
+and the learned proposal, in one autotuned context -- and, beside it, the same
+batch as 256 separate contexts.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 (the plain restatement of the method this project checks against) on a bounded
@@ -47,9 +52,12 @@ FP32_LANES_PER_SM = 128
 #                  + 3 (scalings) = 29, 1.5 pairs per sub-step               -> 43.5
 #   drift 7 + Euler-Maruyama update 6                                      -> 13
 LORENZ_OPS_PER_PARTICLE_STEP = 86.5
-# Algorithmic bytes of one FHN particle per observation interval: read and
-# write the 40 x 40 x 2 FP32 state once (the K sub-steps stay on chip) + logw.
-FHN_BYTES_PER_PARTICLE_OBS = 2 * 3200 * 4 + 4
+# Algorithmic ALU operations per lattice node-step (one Euler-Maruyama
+# sub-step of one node, both planes): Philox4x32-10 40 per 4 normals -> 20,
+# one Box-Muller pair 29, Laplacian 4 (three adds, one fused -4v), drift of
+# v 9 (cubic, coupling, D times the Laplacian), of w 2, two Euler-Maruyama
+# updates 4 -> 68.
+FHN_OPS_PER_NODE_STEP = 68
 
 
 def env_int(name, default):
@@ -133,66 +141,140 @@ def recorded_traffic(kernel: str):
 # ---------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------
+WORKLOAD_TEXT = {
+    "lorenz-sweep": ("lorenz63 ensemble, M*N = 2^20 swept over M in {1,4,16,64,256,1024,4096}, all seven "
+                     "resident; one step = one observation (K=40 Euler-Maruyama sub-steps) of each"),
+    "fhn": "fhn 40x40 lattice (3200 variables), M=32 x N=1024, K=20, bootstrap proposal",
+    "fhn-learned": "fhn 40x40 lattice, M=32 x N=1024, K=20, learned proposal (network trained untimed)",
+    "ragged": ("256 fhn 20x20 lattices, N log-uniform in [64, 4096], independent records, learned proposal, "
+               "one autotuned context (all filters in each launch, CUDA graph)"),
+}
+
+
 class Workload:
     def __init__(self, name, seed_base):
         import torch
-        from paper_1407_8071_gb300 import pf
+        from paper_1407_8071_gb300 import pf, proposal
         self.name = name
-        self.filters = []
+        self.filters, self.streams = [], []
+        self.per_filter_obs = False
+        self.choice = None
+        self.N_list = None
         if name == "lorenz-sweep":
             self.spec = W.lorenz63()
             self.rows = W.lorenz_sweep()
-            rec_seed = W.SEED_LORENZ_OBS
-        elif name == "fhn":
+            rec_seed, T = W.SEED_LORENZ_OBS, 200
+        elif name in ("fhn", "fhn-learned"):
             self.spec = W.fhn_lattice()
             self.rows = [(W.FHN_FULL["M"], W.FHN_FULL["N"])]
-            rec_seed = W.SEED_FHN_OBS
+            rec_seed, T = W.SEED_FHN_OBS, W.FHN_FULL["T"]
+        elif name == "ragged":
+            self.spec = W.fhn_lattice(J=W.RAGGED["J"])
+            self.N_list = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
+            self.rows = [(len(self.N_list), self.N_list)]
+            rec_seed, T = W.SEED_RAGGED, 50
+            self.per_filter_obs = True
         else:
             raise ValueError(name)
-        T = 200 if name == "lorenz-sweep" else W.FHN_FULL["T"]
-        _, y = pf.pf_simulate(self.spec, T, rec_seed)
         self.T = T
+        if self.per_filter_obs:  # an independent record per filter: T x M x dy
+            y = np.stack([pf.pf_simulate(self.spec, T, rec_seed, record=m)[1] for m in range(len(self.N_list))],
+                         axis=1)
+            train_record = pf.pf_simulate(self.spec, 20, rec_seed, record=1 << 20)[1]
+        else:
+            y = pf.pf_simulate(self.spec, T, rec_seed)[1]
+            train_record = y
         self.y_host = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
         self.y_dev = self.y_host.cuda()
         torch.cuda.synchronize()
+        self.theta = None
+        if name in ("fhn-learned", "ragged"):
+            self.theta = proposal.trained_theta(self.spec, train_record[:20], seed=seed_base + 77)
         # one stream per context: the configurations are independent, so their
         # kernels may overlap; `stream` is where the timed region starts and ends
         self.stream = torch.cuda.Stream()
-        self.streams = []
         for i, (M, N) in enumerate(self.rows):
             f = pf.EnsembleFilter(self.spec, M, N, seed=seed_base + i)
             st = torch.cuda.Stream()
             f.set_stream(st.cuda_stream)
+            if self.theta is not None:
+                f.set_proposal(self.theta, 0.1)
+            if self.spec.kind == W.FHN:
+                self.choice = f.autotune()
             self.filters.append(f)
             self.streams.append(st)
-        self.particles = sum(M * N for M, N in self.rows)
+        self.particles = int(sum(int(np.sum(N)) if np.ndim(N) else M * N for M, N in self.rows))
         self.particle_steps_per_step = self.particles * self.spec.K
-        # kernels one pf_step launches: small models -- propagate (+ sub-tile maxima), weights, scan,
-        # ancestors (+ gather, means, ensemble); lattice -- propagate, tile maxima, weights, scan,
-        # ancestors, gather, means, ensemble
-        self.kernels_per_filter_step = 8 if self.spec.kind == W.FHN else 4
+        # kernels one pf_step launches: small models -- propagate, weights, scan, ancestors, ensemble;
+        # lattice -- propagate, weights, scan, ancestors, gather, means, ensemble; the learned proposal
+        # replaces the propagate by sub-steps, network rows, network forward, last step and select
+        if self.spec.kind == W.FHN:
+            self.kernels_per_filter_step = 7 + (4 if self.theta is not None else 0)
+        else:
+            self.kernels_per_filter_step = 5
         self.t = 0
 
+    def row(self, src):
+        return src[self.t % self.T]
+
     def step_device(self):
-        row = self.y_dev[self.t % self.T]
+        r = self.row(self.y_dev)
         for f in self.filters:
-            f.step_device(row)
+            f.step_device(r, per_filter=self.per_filter_obs)
         self.t += 1
 
     def step_host(self):
         """Through the public API with host buffers: H2D of y_t, D2H of each ensemble estimate."""
         from paper_1407_8071_gb300 import pf
-        y = self.y_host[self.t % self.T].numpy()
+        y = self.row(self.y_host).numpy()
         for f in self.filters:
-            f.step(y)
+            f.step(y, per_filter=self.per_filter_obs)
         var = 1 if self.spec.kind == W.LORENZ63 else 0
         for f in self.filters:
             f.estimate(pf.PF_STAT_MEAN, var=var)
         self.t += 1
 
+    def obs_bytes(self):
+        """Observation bytes one step copies host to device."""
+        per = int(np.prod(self.y_host.shape[1:])) * 4
+        return per * len(self.filters)
+
     def close(self):
         for f in self.filters:
             f.close()
+
+
+def separate_contexts(torch, wl, steps):
+    """The ragged batch as one context per filter, stepped one after another on
+    one stream (the alternative to batching all filters in each launch)."""
+    from paper_1407_8071_gb300 import pf
+    st = torch.cuda.Stream()
+    ctxs = []
+    for m, n in enumerate(wl.N_list):
+        f = pf.EnsembleFilter(wl.spec, 1, int(n), seed=7000 + m)
+        f.set_stream(st.cuda_stream)
+        if wl.theta is not None:
+            f.set_proposal(wl.theta, 0.1)
+        ctxs.append(f)
+
+    def step(t):
+        for m, f in enumerate(ctxs):
+            f.step_device(wl.y_dev[t % wl.T, m])
+
+    for t in range(3):
+        step(t)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for t in range(steps):
+        step(t)
+    b.record(st)
+    torch.cuda.synchronize()
+    el = a.elapsed_time(b) / 1e3
+    for f in ctxs:
+        f.close()
+    return {"value": wl.particle_steps_per_step * steps / el, "unit": METRIC, "ms_per_step": el / steps * 1e3,
+            "contexts": len(ctxs), "gpu_launches": steps * len(ctxs) * wl.kernels_per_filter_step}
 
 
 def time_region(torch, wl, fn, K, barrier=None):
@@ -224,7 +306,7 @@ def phase_times(torch, wl, reps=5):
             row = wl.y_dev[wl.t % wl.T]
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(st)
-            f.propagate_device(row)
+            f.propagate_device(row, per_filter=wl.per_filter_obs)
             e1.record(st)
             f.resample()
             e2.record(st)
@@ -238,30 +320,60 @@ def phase_times(torch, wl, reps=5):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(workload: str, target_s: float):
+def oracle_case(workload: str, M: int, n_scale: int, T: int, theta=None):
+    """A bounded sample of `workload` for the FP64 oracle: (spec, M, N, y, per-filter obs, theta)."""
+    import oracle
+    if workload == "lorenz-sweep":  # filters of the M = 64, N = 16384 row of the sweep
+        spec = W.lorenz63()
+        return spec, M, (1 << 14) // n_scale, oracle.simulate(spec, T, W.SEED_LORENZ_OBS)[1], False, None
+    if workload in ("fhn", "fhn-learned"):
+        spec = W.fhn_lattice()
+        y = oracle.simulate(spec, T, W.SEED_FHN_OBS)[1]
+        if workload == "fhn-learned" and theta is None:
+            from paper_1407_8071_gb300 import proposal
+            theta = proposal.initial_theta(1)
+        return spec, M, max(2, 8 // n_scale), y, False, theta
+    spec = W.fhn_lattice(J=W.RAGGED["J"])
+    counts = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
+    N = np.maximum(1, counts[:M] // (16 * n_scale))  # the first M filters' counts, scaled down
+    y = np.stack([oracle.simulate(spec, T, W.SEED_RAGGED, record=m)[1] for m in range(M)], axis=1)
+    if theta is None:
+        from paper_1407_8071_gb300 import proposal
+        theta = proposal.initial_theta(1)
+    return spec, M, N, y, True, theta
+
+
+def oracle_run(case, T, seed, threads):
+    import oracle
+    spec, M, N, y, per_filter, theta = case
+    if spec.kind == W.FHN:
+        oracle.bf_run_proposal(spec, theta, M, N, T, y[:T], seed=seed, est_idx=[1], obs_per_filter=per_filter,
+                               threads=threads)
+    else:
+        oracle.bf_run(spec, M, N, T, y[:T], seed=seed, est_idx=[1], threads=threads)
+    return int(np.sum(np.broadcast_to(N, (M,)))) * T * spec.K
+
+
+def oracle_sample(workload: str, target_s: float, theta=None):
     """Times the FP64 oracle on a bounded sample of the workload; returns
     (particle-steps/s, threads, sample description)."""
-    import oracle
     cores = os.cpu_count() or 1
-    if workload == "fhn":
-        spec = W.fhn_lattice()
-        M, N = min(32, 2 * cores), 4
-        _, y = oracle.simulate(spec, 4, W.SEED_FHN_OBS)
-    else:
-        spec = W.lorenz63()
-        M, N = min(64, 2 * cores), 1 << 14  # filters of the M = 64, N = 16384 row of the sweep
-        _, y = oracle.simulate(spec, 200, W.SEED_LORENZ_OBS)
+    M = min(64 if workload == "lorenz-sweep" else 32, 2 * cores)
+    Tmax = 200 if workload == "lorenz-sweep" else 6
+    case = oracle_case(workload, M, 1, Tmax, theta)
     threads = min(M, cores)
     t0 = time.perf_counter()
-    oracle.bf_run(spec, M, N, 1, y, seed=1, est_idx=[1], threads=threads)
+    oracle_run(case, 1, 1, threads)
     dt1 = time.perf_counter() - t0
-    T = int(max(1, min(len(y), round(target_s / max(dt1, 1e-3)))))
+    T = int(max(1, min(Tmax, round(target_s / max(dt1, 1e-3)))))
     t0 = time.perf_counter()
-    oracle.bf_run(spec, M, N, T, y, seed=2, est_idx=[1], threads=threads)
+    ps = oracle_run(case, T, 2, threads)
     dt = time.perf_counter() - t0
-    ps = M * N * T * spec.K
-    desc = (f"{W.KIND_NAMES[spec.kind]}: {M} filters x {N} particles x {T} observations x K={spec.K} "
-            f"(= {ps:.3g} particle-steps) of the {workload} workload, FP64, OpenMP over filters")
+    spec, _, N, _, _, th = case
+    ntxt = f"{N} particles" if np.ndim(N) == 0 else f"{int(np.sum(N))} particles in all (ragged)"
+    desc = (f"{W.KIND_NAMES[spec.kind]}: {M} filters, {ntxt}, {T} observations x K={spec.K} "
+            f"(= {ps:.3g} particle-steps) of the {workload} workload, FP64, OpenMP over filters"
+            + (", learned proposal" if th is not None else ""))
     return ps / dt, threads, desc
 
 
@@ -269,32 +381,28 @@ def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
-    import oracle
     cores = os.cpu_count() or 1
-    if args.workload == "fhn":
-        spec = W.fhn_lattice()
-        M, N = min(32, 2 * cores), 2
-        _, y = oracle.simulate(spec, 2, W.SEED_FHN_OBS)
-    else:
-        spec = W.lorenz63()
-        M, N = min(32, 2 * cores), 1 << 12
-        _, y = oracle.simulate(spec, 2, W.SEED_LORENZ_OBS)
+    M = min(32, 2 * cores)
+    case = oracle_case(args.workload, M, 4, 2)
     threads = min(M, cores)
-    work = M * N * spec.K
-    for _ in range(args.warmup):
-        oracle.bf_run(spec, M, N, 1, y, seed=3, est_idx=[1], threads=threads)
+    for k in range(args.warmup):
+        oracle_run(case, 1, 3 + k, threads)
     t0 = time.perf_counter()
+    work = 0
     for k in range(args.steps):
-        oracle.bf_run(spec, M, N, 1, y, seed=4 + k, est_idx=[1], threads=threads)
+        work += oracle_run(case, 1, 100 + k, threads)
     dt = time.perf_counter() - t0
-    value = work * args.steps / dt
-    sample = (f"each step: one observation interval (K={spec.K}) of {M} filters x {N} particles of the "
-              f"{args.workload} workload in the FP64 C oracle (prior draw included)")
+    value = work / dt
+    spec, _, N, _, _, th = case
+    ntxt = f"{N} particles each" if np.ndim(N) == 0 else f"{int(np.sum(N))} particles in all (ragged)"
+    sample = (f"each step: one observation interval (K={spec.K}) of {M} filters, {ntxt}, of the "
+              f"{args.workload} workload in the FP64 C oracle (prior draw included)"
+              + (", learned proposal" if th is not None else ""))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "sample": sample},
+        "config": {"workload": WORKLOAD_TEXT[args.workload], "sample": sample},
         "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -310,7 +418,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="lorenz-sweep", choices=["lorenz-sweep", "fhn"])
+    ap.add_argument("--workload", default="lorenz-sweep", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -370,37 +478,46 @@ def main():
                     "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
                     "ops_per_particle_step": LORENZ_OPS_PER_PARTICLE_STEP, "avg_launch_s": t_prop}
     else:
-        hbm = float(peaks["hbm_gbs"])
-        per_launch_bytes = wl.particles * FHN_BYTES_PER_PARTICLE_OBS
-        achieved = per_launch_bytes / t_prop / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_propagate_fhn<float>", "achieved": achieved, "peak": hbm,
-                    "unit": "GB/s", "frac": achieved / hbm, "traffic": recorded_traffic("k_propagate_fhn<float>"),
-                    "peak_source": f"{peak_src} copy bandwidth", "avg_launch_s": t_prop}
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+        per_launch_ops = (wl.particles / nf) * wl.spec.K * wl.spec.J * wl.spec.J * FHN_OPS_PER_NODE_STEP
+        achieved = per_launch_ops / t_prop / 1e12
+        kern = "k_propagate_fhn<float>" if wl.theta is None else "proposal propagate (5 kernels)"
+        roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                    "frac": achieved / alu_peak,
+                    "traffic": recorded_traffic("k_propagate_fhn<float>") if wl.theta is None else None,
+                    "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
+                    "ops_per_node_step": FHN_OPS_PER_NODE_STEP, "avg_launch_s": t_prop}
 
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
-            "workload": ("lorenz63 ensemble, M*N = 2^20 swept over M in {1,4,16,64,256,1024,4096}, all seven "
-                         "resident; one step = one observation (K=40 Euler-Maruyama sub-steps) of each")
-            if args.workload == "lorenz-sweep" else "fhn 40x40 lattice, M=32 x N=1024, K=20",
-            "rows": [{"M": M, "N": N} for M, N in wl.rows], "K": wl.spec.K, "dt": wl.spec.dt,
+            "workload": WORKLOAD_TEXT[args.workload],
+            "rows": ([{"M": M, "N": N} for M, N in wl.rows] if wl.N_list is None else
+                     [{"M": len(wl.N_list), "N_min": int(wl.N_list.min()), "N_max": int(wl.N_list.max()),
+                       "N_total": int(wl.N_list.sum())}]),
+            "K": wl.spec.K, "dt": wl.spec.dt,
+            "autotuned": None if wl.choice is None else {"particles_per_cta": wl.choice[0],
+                                                         "resample_threads": wl.choice[1]},
             "precision": "FP32 state and propagation; FP64 normaliser, prefix sum and M-average",
             "l2": ("working set of the seven contexts (~340 MB) exceeds the 129 MB L2; each context's data "
                    "is evicted by the other six between its steps") if args.workload == "lorenz-sweep"
-            else "state 839 MB per buffer, larger than L2",
+            else f"state {wl.particles * wl.spec.dx * 4 / 1e6:.0f} MB per buffer, larger than L2",
         },
         "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": nf * wl.spec.dy * 4,
+        "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": wl.obs_bytes(),
                 "d2h_bytes_per_step": nf * 8},
         "gpu_launches": args.steps * nf * wl.kernels_per_filter_step,
         "roofline": roofline,
         "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res},
     }
+    theta = wl.theta
+    if wl.N_list is not None:
+        line["separate_contexts"] = separate_contexts(torch, wl, max(1, args.steps // 4))
     wl.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample(args.workload, args.cpu_seconds)
+        v, cores, desc = oracle_sample(args.workload, args.cpu_seconds, theta)
         line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": desc}
     if rank == 0:

@@ -193,8 +193,9 @@ PF_API pf_status pf_estimate(pf_ctx *ctx, const pf_stat *stat, double *out);
  * (one particle per CTA up to as many as fit in 1024 threads); for every model,
  * threads per resampling tile CTA (64, 128, 256 -- fewer threads and more CTAs
  * for small filters).  The choice is cached per (model, lattice side, K, dx,
- * particles, filters) for the process, and reported in h_choice[0..1] (may be
- * NULL).  The filter's state, statistics and step counter are unchanged.
+ * particle counts) for the process, and reported in h_choice[0..1] (may be
+ * NULL): h_choice[0] particles per lattice CTA (0 for the small models, which
+ * run one particle per thread), h_choice[1] resampling threads.  The filter's state, statistics and step counter are unchanged.
  * Synchronises; needs about one particle buffer of temporary device memory.
  * Errors: PF_ESTATE (between pf_propagate and pf_resample, or recording),
  * PF_ENOMEM, PF_ECUDA. */

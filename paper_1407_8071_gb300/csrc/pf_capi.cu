@@ -318,7 +318,20 @@ int ceil_log2_host(int64_t n)
 
 // Schedules chosen by pf_autotune, per (model, J, K, dx, particles, filters).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, int, int64_t, int32_t>, std::pair<int, int>> g_tune_cache;
+// keyed by model kind, lattice side, K, dx, total particles, filters and a
+// hash (FNV-1a) of the particle counts, so ragged batches of the same total
+// are told apart
+static std::map<std::tuple<int, int, int, int, int64_t, int32_t, uint64_t>, std::pair<int, int>> g_tune_cache;
+
+static uint64_t counts_hash(const std::vector<int32_t> &N)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (int32_t n : N) {
+        h ^= (uint32_t)n;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 
 // Median time of `reps` launches of fn on the context's stream (ms).
 template <typename F>
@@ -727,7 +740,8 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
     if (c.phase != 0 || c.rec_X) return fail(c, PF_ESTATE, "pf_autotune needs a context between steps, not recording");
     pf_status st = sync(c, "autotune");
     if (st != PF_OK) return st;
-    const auto key = std::make_tuple((int)c.mp.kind, (int)c.mp.J, (int)c.mp.K, (int)c.mp.dx, (int64_t)c.P, c.M);
+    const auto key = std::make_tuple((int)c.mp.kind, (int)c.mp.J, (int)c.mp.K, (int)c.mp.dx, (int64_t)c.P, c.M,
+                                     counts_hash(c.N));
     bool cached = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -746,7 +760,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         // before and restored after.
         const size_t P = (size_t)c.P, dx = (size_t)c.mp.dx, M = (size_t)c.M;
         const size_t xb = P * dx * sizeof(float);
-        const size_t save_bytes = P * 4 + P * 4 + M * kFsCount * 8 + M * dx * 8 + dx * 8 + M * 4;
+        const size_t save_bytes = P * 4 + P * 4 + M * kFsCount * 8 + M * dx * 8 + dx * 8 + M * 4 + M * 16 + 8;
         char *tmp = nullptr, *save = nullptr;
         cudaError_t e = cudaMalloc(&tmp, xb);
         if (e == cudaSuccess) e = cudaMalloc(&save, save_bytes);
@@ -757,7 +771,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         }
         struct Span { void *dev; size_t bytes; };
         const Span spans[] = {{c.logw, P * 4}, {c.anc, P * 4}, {c.fstats, M * kFsCount * 8}, {c.est, M * dx * 8},
-                              {c.ens, dx * 8}, {c.fmax_key, M * 4}};
+                              {c.ens, dx * 8}, {c.fmax_key, M * 4}, {c.fint, M * 16}, {c.err, 8}};
         size_t o = 0;
         for (const Span &sp : spans) {
             if (e == cudaSuccess) e = cudaMemcpyAsync(save + o, sp.dev, sp.bytes, cudaMemcpyDeviceToDevice, c.stream);
@@ -795,7 +809,12 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
             for (int th : cands) {
                 c.resample_threads = th;
                 trial_step();
-                const float ms = time_ms(c, 3, [&] { launch_resample(c, scratch, dest, c.stream); });
+                // each resampling consumes the per-filter maxima the propagation
+                // left (and resets them), so every trial recomputes them first
+                const float ms = time_ms(c, 3, [&] {
+                    launch_refresh_max(c, c.stream);
+                    launch_resample(c, scratch, dest, c.stream);
+                });
                 if (ms < best) { best = ms; best_rt = th; }
             }
             c.resample_threads = best_rt;

@@ -68,3 +68,25 @@ def mean_nll(theta: np.ndarray, X, R) -> float:
         return loss
     finally:
         tr.close()
+
+
+def initial_theta(seed: int) -> np.ndarray:
+    """Starting parameters: He-normal hidden layers, zero output layer (the
+    zero network makes q equal the transition, so training starts from the
+    bootstrap filter).  Layout: W1 (128 x 51), b1, W2 (128 x 128), b2,
+    W3 (4 x 128), b3, row-major, PF_MLP_PARAMS values."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, np.sqrt(2.0 / 51), 128 * 51), np.zeros(128),
+             rng.normal(0.0, np.sqrt(2.0 / 128), 128 * 128), np.zeros(128),
+             np.zeros(4 * 128), np.zeros(4)]
+    theta = np.concatenate(parts).astype(np.float32)
+    assert theta.size == pf.MLP_PARAMS
+    return theta
+
+
+def trained_theta(spec: W.ModelSpec, record: np.ndarray, seed: int, tuples: int = 300_000, epochs: int = 2,
+                  M: int = 16, N: int = 256, stride: int = 4) -> np.ndarray:
+    """Collect tuples with the plain filter on `record`, then train from initial_theta."""
+    X, R, n = collect_tuples(spec, M, N, record, seed=seed, capacity=tuples, stride=stride)
+    theta, _ = train(initial_theta(seed), X, R, epochs=epochs, batch=8192, lr=1e-3)
+    return theta
