@@ -367,34 +367,51 @@ __global__ void __launch_bounds__(256) k_init_fhn(ModelParams mp, Key key, const
 }
 
 // ------------------------------------------------------------------ propagate + weight (Alg. 1 step 2a)
-// Thread per particle, one CTA per sub-tile of <= kSubTile particles (filter
-// aligned, so the grid has many small blocks and little wave-quantisation
-// loss), SoA state x[v * P + p] (coalesced), K Euler-Maruyama sub-steps in
-// registers, then the FP32 log-likelihood; the sub-tile's maximum of it joins
-// the filter's maximum by one atomicMax (the first pass of the log-sum-exp).
+// One CTA of kSubTile / 2 threads per sub-tile of <= kSubTile particles
+// (filter aligned, so the grid has many small blocks and little
+// wave-quantisation loss); thread i carries particles i and i + kSubTile / 2
+// of its sub-tile (two independent generator chains to interleave).  SoA
+// state x[v * P + p] (coalesced), K Euler-Maruyama sub-steps in registers,
+// then the FP32 log-likelihood; the sub-tile's maximum of it joins the
+// filter's maximum by one atomicMax (the first pass of the log-sum-exp).  A
+// thread past the sub-tile's end repeats its last particle and stores nothing.
+constexpr int kPropThreads = kSubTile / 2;
+
 template <int D>
-__global__ void __launch_bounds__(kSubTile, 16) k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs,
-                                                              const float *__restrict__ x_in, float *__restrict__ x_out,
-                                                              int64_t P, float *logw, int32_t *fmax_key, const float *obs,
-                                                              int32_t obs_stride, const int32_t *d_t)
+__global__ void __launch_bounds__(kPropThreads, 16)
+    k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *__restrict__ x_in,
+                      float *__restrict__ x_out, int64_t P, float *logw, int32_t *fmax_key, const float *obs,
+                      int32_t obs_stride, const int32_t *d_t)
 {
-    __shared__ float sh[kSubTile / 32];
+    __shared__ float sh[kPropThreads / 32];
     const TileDesc st = subs[blockIdx.x];
     const uint32_t t = (uint32_t)(*d_t + 1);
     const float *y = obs + (obs_stride ? (int64_t)st.m * obs_stride : 0);
-    float l = -INFINITY;
-    if ((int)threadIdx.x < st.len) {
-        const int64_t p = st.gstart + threadIdx.x;
-        float xs[D];
+    int j[2];
+    uint32_t c0[2];
+    float xs[2][D];
 #pragma unroll
-        for (int v = 0; v < D; ++v) xs[v] = x_in[v * P + p];
-        propagate_small<D, float>(mp, key, kStreamDyn, (uint32_t)(st.lstart + threadIdx.x), t, (uint32_t)st.m, xs);
+    for (int r = 0; r < 2; ++r) {
+        j[r] = min((int)threadIdx.x + r * kPropThreads, st.len - 1);
+        c0[r] = (uint32_t)(st.lstart + j[r]);
+        const int64_t p = st.gstart + j[r];
 #pragma unroll
-        for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[v];
-        l = loglik_small<D, float>(mp, y, xs);
-        logw[p] = l;
+        for (int v = 0; v < D; ++v) xs[r][v] = x_in[v * P + p];
     }
-    const float mx = block_max_f(l < INFINITY ? l : -INFINITY, sh);  // NaN never wins
+    propagate_small_n<D, 2, float>(mp, key, kStreamDyn, c0, t, (uint32_t)st.m, xs);
+    float l = -INFINITY;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if ((int)threadIdx.x + r * kPropThreads < st.len) {
+            const int64_t p = st.gstart + j[r];
+#pragma unroll
+            for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[r][v];
+            const float lr = loglik_small<D, float>(mp, y, xs[r]);
+            logw[p] = lr;
+            l = fmaxf(l, lr < INFINITY ? lr : -INFINITY);  // NaN never wins
+        }
+    }
+    const float mx = block_max_f(l, sh);
     if (threadIdx.x == 0 && mx > -INFINITY) atomicMax(&fmax_key[st.m], float_order_key(mx));
 }
 
@@ -944,7 +961,7 @@ template <int D>
 cudaError_t propagate_small_launch(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                                    cudaStream_t s)
 {
-    k_propagate_small<D><<<c.n_subs, kSubTile, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs,
+    k_propagate_small<D><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs,
                                                        stride, c.d_t);
     return cudaGetLastError();
 }

@@ -68,16 +68,45 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const Key &key)
 // z0 = R cos(2 pi u2), z1 = R sin(2 pi u2), R = sqrt(-2 ln u1).
 // FP32: the angle is taken as 2 pi (u2 - 1/2) in [-pi, pi) (u2 - 1/2 is exact;
 // cos and sin change sign) so the hardware sine/cosine run on their accurate
-// range (absolute error below 2^-21); R = v * rsqrt(v).
+// range (absolute error below 2^-21); R = v * rsqrt(v); v = -2 ln u1 from
+// neg2_ln_u24 below.
 template <typename Real>
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, Real &z0, Real &z1);
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// -2 ln(n 2^-24) for an integer n in [1, 2^24], in FP32 with a relative error
+// of a few ulp everywhere (also as n -> 2^24, where v -> 0).  Range reduction:
+// n = f 2^k with f in [sqrt(1/2), sqrt(2)) (k from the exponent of the exact
+// binary32 n, moved by one when the significand is at or above sqrt(2)), then
+// ln f = 2 artanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + ...), s = (f - 1)/(f + 1),
+// |s| <= 3 - 2 sqrt(2) = 0.1716 (Abramowitz & Stegun 4.1.27); the first
+// omitted term, 2 s^9 / 9, is below 3e-8 of ln f.  f - 1 is exact (Sterbenz),
+// so s keeps its relative accuracy as f -> 1.  -2 ln u1 = -2 (k - 24) ln 2 - 2 ln f.
+__device__ __forceinline__ float neg2_ln_u24(uint32_t n)
+{
+    const uint32_t bits = __float_as_uint(__uint2float_rn(n));
+    const uint32_t k = (bits - 0x3F3504F3u) >> 23;  // 0x3F3504F3: binary32 sqrt(1/2)
+    const float f = __uint_as_float(bits - (k << 23));
+    const float s = (f - 1.0f) * rcp_approx(f + 1.0f);
+    const float s2 = s * s;
+    float c = -4.0f / 7.0f;  // -2 x the series' coefficients 2 / (2j + 1)
+    c = fmaf(c, s2, -4.0f / 5.0f);
+    c = fmaf(c, s2, -4.0f / 3.0f);
+    const float m2lnf = fmaf(s * s2, c, -4.0f * s);
+    return fmaf((float)((int32_t)k - 24), -1.38629436111989061883f, m2lnf);  // -2 ln 2
+}
 
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1)
 {
-    const float u1 = __uint2float_rn((a >> 8) + 1u) * 0x1p-24f;
+    const float v = neg2_ln_u24((a >> 8) + 1u);
     const float h = __uint2float_rn(b >> 8) * 0x1p-24f - 0.5f;
-    const float v = -2.0f * logf(u1);
     const float R = v > 0.0f ? v * rsqrtf(v) : 0.0f;
     float s, c;
     __sincosf(6.28318530717958647692f * h, &s, &c);
@@ -191,12 +220,13 @@ struct NoisePacking {
     static constexpr int blocks = lcm / 4;  // Philox calls per group
 };
 
-// Propagates one particle of a small model over the K sub-steps of
-// observation t (Alg. 1 step 2a; Euler-Maruyama), stream `stream`,
-// counter words (c0, t, c2).
-template <int D, typename Real>
-__device__ __forceinline__ void propagate_small(const ModelParams &mp, const Key &key, uint32_t stream, uint32_t c0,
-                                                uint32_t t, uint32_t c2, Real x[D])
+// Propagates R particles of a small model over the K sub-steps of
+// observation t (Alg. 1 step 2a; Euler-Maruyama), stream `stream`, counter
+// words (c0[r], t, c2).  Several particles per thread give the scheduler
+// independent generator chains to interleave.
+template <int D, int R, typename Real>
+__device__ __forceinline__ void propagate_small_n(const ModelParams &mp, const Key &key, uint32_t stream,
+                                                  const uint32_t c0[R], uint32_t t, uint32_t c2, Real x[R][D])
 {
     using NP = NoisePacking<D>;
     const Real dt = par_dt<Real>(mp);
@@ -204,20 +234,38 @@ __device__ __forceinline__ void propagate_small(const ModelParams &mp, const Key
     const int K = mp.K;
     uint32_t block = 0;
     for (int k0 = 0; k0 < K; k0 += NP::steps) {
-        Real z[4 * NP::blocks];
+        Real z[R][4 * NP::blocks];
 #pragma unroll
-        for (int b = 0; b < NP::blocks; ++b) normals4<Real>(key, c0, t, c2, stream, block + b, z + 4 * b);
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int b = 0; b < NP::blocks; ++b) normals4<Real>(key, c0[r], t, c2, stream, block + b, z[r] + 4 * b);
         block += NP::blocks;
 #pragma unroll
         for (int s = 0; s < NP::steps; ++s) {
             if (k0 + s < K) {
-                Real f[D];
-                SmallModel<D, Real>::drift(mp, x, f);
 #pragma unroll
-                for (int v = 0; v < D; ++v) x[v] = x[v] + dt * f[v] + sq * z[s * D + v];
+                for (int r = 0; r < R; ++r) {
+                    Real f[D];
+                    SmallModel<D, Real>::drift(mp, x[r], f);
+#pragma unroll
+                    for (int v = 0; v < D; ++v) x[r][v] = x[r][v] + dt * f[v] + sq * z[r][s * D + v];
+                }
             }
         }
     }
+}
+
+template <int D, typename Real>
+__device__ __forceinline__ void propagate_small(const ModelParams &mp, const Key &key, uint32_t stream, uint32_t c0,
+                                                uint32_t t, uint32_t c2, Real x[D])
+{
+    Real xr[1][D];
+#pragma unroll
+    for (int v = 0; v < D; ++v) xr[0][v] = x[v];
+    const uint32_t c[1] = {c0};
+    propagate_small_n<D, 1, Real>(mp, key, stream, c, t, c2, xr);
+#pragma unroll
+    for (int v = 0; v < D; ++v) x[v] = xr[0][v];
 }
 
 // log g without its constant: -1/2 sum_j (y_j - x[idx_j])^2 / sigma_obs^2.
