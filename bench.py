@@ -411,6 +411,27 @@ def run_reference(args):
     return 0
 
 
+def run_study(args):
+    """MSE of the averaged estimator against a reference posterior: the Lorenz
+    2^20 sweep over 64 seeds, and plain vs learned proposal on the lattice at
+    equal MSE (wall time to reach the plain filter's MSE at N = 1024)."""
+    import torch
+    from paper_1407_8071_gb300 import pf, proposal, study
+    torch.cuda.set_device(env_int("LOCAL_RANK", 0))
+    pf.lib()
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    t0 = time.perf_counter()
+    lor = study.lorenz_sweep_mse(log=log)
+    spec = W.fhn_lattice()
+    train_record = pf.pf_simulate(spec, 20, W.SEED_FHN_OBS, record=1)[1]  # not the scored record
+    theta = proposal.trained_theta(spec, train_record, seed=77)
+    lat = study.lattice_time_to_mse(theta, log=log)
+    line = {"study": "mse", "data": "synthetic", "lorenz_sweep": lor, "lattice": lat,
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line))
+    return 0
+
+
 # ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
@@ -421,10 +442,14 @@ def main():
     ap.add_argument("--workload", default="lorenz-sweep", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--study", choices=["mse"], default=None,
+                    help="accuracy study instead of the throughput bench (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.study:
+        return run_study(args)
 
     import torch
     import torch.distributed as dist
