@@ -281,6 +281,19 @@ PF_API pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const dou
  * (rows x 4, device).  d_theta: PF_MLP_PARAMS FP32 values on the device. */
 PF_API pf_status pf_mlp_forward(int64_t rows, const float *d_in, const float *d_theta, float *d_out, void *stream);
 
+/* The same network evaluated on lattice states, its input rows built on the
+ * device from the states inside the kernel (the form the filter runs: the
+ * fifth-generation tensor cores, tcgen05 with accumulators in tensor memory,
+ * and an erf approximation with |error| <= 1.5e-7 in the GELU).  J: lattice
+ * side (2..44); d_x: P particles of 2 J^2 FP32 (v-plane, then w-plane);
+ * h_obs_idx: dy node indices in [0, J^2) (host, copied); d_y: dy FP32
+ * observations shared by all particles; d_theta: PF_MLP_PARAMS FP32 values;
+ * d_out: (P dy) x 4 FP32, row p dy + j for particle p and observed node j.
+ * All device pointers; enqueued on `stream` with stream-ordered temporaries.
+ * Errors: PF_EINVAL, PF_ENOMEM, PF_ECUDA. */
+PF_API pf_status pf_proposal_forward(int32_t J, int64_t P, const float *d_x, int32_t dy, const int32_t *h_obs_idx,
+                                     const float *d_y, const float *d_theta, float *d_out, void *stream);
+
 /* Training state on the device: FP32 master parameters and Adam moments
  * (beta1 0.9, beta2 0.999, eps 1e-8), workspace for batches up to max_batch
  * rows.  h_theta: initial parameters (copied). */

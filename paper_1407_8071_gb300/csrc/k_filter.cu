@@ -811,27 +811,56 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t *__restrict__
     for (int i = threadIdx.x; i < row4; i += blockDim.x) b[i] = a[i];
 }
 
-// Lattice estimates: est[m][v] = (1/N_m) sum_i x[off + i][v], i ascending, in
-// a compensated FP32 pair converted to FP64 at the end.
-__global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const float *__restrict__ x, int dx,
+// Per-filter means of every variable of the resampled lattice particles
+// (estimator after eq. eqGtN): CTA (chunk of <= kMeanChunk particles of one
+// filter, variable block).  Each thread sums its variable over the chunk in
+// a compensated FP32 pair (coalesced over the block's variables), writes the
+// FP64 partial, and the last CTA of the filter's chunks (completion counter,
+// reset by that CTA) adds the partials in chunk order in FP64: deterministic,
+// and parallel over particles, so one filter of many particles is as fast as
+// many small ones.
+__global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const TileDesc *__restrict__ chunks,
+                                                   const float *__restrict__ x, int dx, double *part, int32_t *cnt,
                                                    double *est)
 {
-    const int m = blockIdx.y;
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= dx) return;
-    const FilterDesc fd = filt[m];
-    const float *base = x + fd.off * (int64_t)dx + v;
-    FF acc{0.0f, 0.0f};
-    int i = 0;
-    for (; i + 8 <= fd.N; i += 8) {  // eight loads in flight, then the ordered adds
-        float r[8];
+    __shared__ int last;
+    const TileDesc ch = chunks[blockIdx.x];
+    const FilterDesc fd = filt[ch.m];
+    const int v = blockIdx.y * blockDim.x + threadIdx.x;
+    double mine = 0.0;
+    if (v < dx) {
+        const float *base = x + ch.gstart * (int64_t)dx + v;
+        FF acc{0.0f, 0.0f};
+        int i = 0;
+        for (; i + 8 <= ch.len; i += 8) {  // eight loads in flight, then the ordered adds
+            float r[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) r[k] = base[(int64_t)(i + k) * dx];
+            for (int k = 0; k < 8; ++k) r[k] = base[(int64_t)(i + k) * dx];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc = ff_add(acc, r[k]);
+            for (int k = 0; k < 8; ++k) acc = ff_add(acc, r[k]);
+        }
+        for (; i < ch.len; ++i) acc = ff_add(acc, base[(int64_t)i * dx]);
+        mine = ff_to_double(acc);
     }
-    for (; i < fd.N; ++i) acc = ff_add(acc, base[(int64_t)i * dx]);
-    est[(int64_t)m * dx + v] = ff_to_double(acc) / (double)fd.N;
+    if (fd.mc_count == 1) {  // the whole filter in this chunk (uniform over the CTA)
+        if (v < dx) est[(int64_t)ch.m * dx + v] = mine / (double)fd.N;
+        return;
+    }
+    if (v < dx) part[(int64_t)blockIdx.x * dx + v] = mine;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *c = cnt + (int64_t)ch.m * gridDim.y + blockIdx.y;
+        last = (atomicAdd(c, 1) == fd.mc_count - 1);
+        if (last) *c = 0;  // every other chunk of this filter and block has counted
+    }
+    __syncthreads();
+    if (last && v < dx) {
+        __threadfence();
+        double s = 0.0;
+        for (int k = 0; k < fd.mc_count; ++k) s += __ldcg(&part[(int64_t)(fd.mc_begin + k) * dx + v]);
+        est[(int64_t)ch.m * dx + v] = s / (double)fd.N;
+    }
 }
 
 // Definition 1: ens[v] = (1/M) sum_m est[m][v] in FP64, one CTA per variable,
@@ -1064,8 +1093,8 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
         k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
                                                    reinterpret_cast<float4 *>(xo), dx / 4);
-        dim3 g((dx + 255) / 256, c.M);
-        k_mean_rows<<<g, 256, 0, s>>>(c.filt, xo, dx, c.est);
+        dim3 g(c.n_mchunks, (dx + 255) / 256);
+        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xo, dx, c.mean_part, c.mean_cnt, c.est);
     } else {
         switch (dx) {
         case 1: k_ancestors_small<1><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;

@@ -23,12 +23,6 @@
 
 namespace pf {
 
-namespace {
-
-__device__ __forceinline__ int mirror(int k, int J) { return k < 0 ? -k - 1 : (k >= J ? 2 * J - k - 1 : k); }
-
-}  // namespace
-
 // Network input rows (BF16, 64 wide, zero-padded) for every (particle, observed
 // node): the 5x5 patches of v and w around the node, mirrored at the edges,
 // then y at the node.
@@ -48,7 +42,7 @@ __global__ void k_build_rows(ModelParams mp, const float *__restrict__ x, int64_
     int r = 0;
     for (int di = -2; di <= 2; ++di)
         for (int dj = -2; dj <= 2; ++dj, ++r) {
-            const int k = mirror(ri + di, J) * J + mirror(ci + dj, J);
+            const int k = mirror_index(ri + di, J) * J + mirror_index(ci + dj, J);
             out[r] = __float2bfloat16_rn(xp[k]);
             out[25 + r] = __float2bfloat16_rn(xp[nn + k]);
         }
@@ -319,17 +313,16 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
         if (e != cudaSuccess) return e;
     }
     const float *mo = nullptr;
-    if (c.prop_on) {
+    if (c.rec_X) {  // the recorded tuples need the rows themselves
         const int64_t R = c.P * c.mp.dy;
         k_build_rows<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(c.mp, x, c.P, c.pfilt, c.obs_idx, d_obs, stride,
                                                                  c.rows);
-        cudaError_t e = launch_mlp_forward_bf16(c.rows, R, c.wpack, c.theta, c.mlp_out, s);
+    }
+    if (c.prop_on) {  // rows built inside the tensor-core forward
+        cudaError_t e = launch_proposal_forward_tc(c.mp.J, c.mp.dx, c.mp.dy, x, c.P, c.pfilt, c.obs_idx, d_obs, stride,
+                                                   c.wpack, c.theta, c.mlp_out, c.err, s);
         if (e != cudaSuccess) return e;
         mo = c.mlp_out;
-    } else if (c.rec_X) {
-        const int64_t R = c.P * c.mp.dy;
-        k_build_rows<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(c.mp, x, c.P, c.pfilt, c.obs_idx, d_obs, stride,
-                                                                 c.rows);
     }
     const size_t smem_last = std::max((size_t)ppc * pairs * sizeof(float2), (size_t)3 * threads * sizeof(float));
     k_last_step_fhn<<<grid, threads, smem_last, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride, c.obs_slot,

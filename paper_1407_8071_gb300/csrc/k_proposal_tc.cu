@@ -1,0 +1,413 @@
+// k_proposal_tc.cu -- the learned proposal's network forward on the
+// fifth-generation tensor cores, fused with the construction of its input
+// rows from the lattice state.
+//
+// One CTA of 128 threads, persistent over tiles of 128 network rows (one row
+// per (particle, observed node)); two CTAs per SM (shared memory bounds it).
+// Per tile:
+//   rows     every thread gathers its row (5x5 patches of v and w, mirrored at
+//            the edges, then y at the node) from the particle's state, rounds
+//            it to BF16 and stores it as the A operand in shared memory;
+//   layer 1  one thread issues 4 tcgen05.mma (M 128, N 128, K 16) into tensor
+//            memory (TMEM columns 0..127), commit -> mbarrier;
+//   GELU     every thread loads its row of the accumulator (tcgen05.ld, warp w
+//            owns TMEM lanes 32w..32w+31), adds the bias, applies GELU and
+//            stores BF16 as the next A operand;
+//   layer 2  8 MMAs into TMEM columns 128..255, GELU again;
+//   layer 3  8 MMAs with N 16 (W3 zero-padded from 4 to 16 rows) into
+//            columns 0..15; each thread writes its 4 outputs + bias (FP32).
+// Operands are K-major without swizzle: element (r, k) of a tile with K
+// columns sits at (r / 8) (K / 8) 128 + (k / 8) 128 + (r % 8) 16 + (k % 8) 2
+// bytes (8 x 16-byte core matrices; K-direction stride 128 B, row-group
+// stride K * 16 B).  The weights are staged once per CTA.  Every wait on the
+// tensor cores is bounded (2 s by the global timer); on expiry the kernel
+// flags kErrTimeout in the context's error word, stops, and frees its TMEM.
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lattice.cuh"
+#include "mlp_device.cuh"
+#include "pf.h"
+#include "pf_internal.h"
+
+namespace pf {
+namespace tc {
+
+constexpr int kRows = 128;
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kOffW1 = 0;                            // 128 x 64
+constexpr uint32_t kOffW2 = kOffW1 + 128 * 64 * 2;        // 128 x 128
+constexpr uint32_t kOffW3 = kOffW2 + 128 * 128 * 2;       // 16 x 128
+constexpr uint32_t kOffA = kOffW3 + 16 * 128 * 2;         // 128 x 64
+constexpr uint32_t kOffH = kOffA + 128 * 64 * 2;          // 128 x 128
+constexpr uint32_t kOffBias = kOffH + 128 * 128 * 2;      // b1[128], b2[128], b3[4]
+constexpr uint32_t kOffBar = kOffBias + (128 + 128 + 4) * 4;
+constexpr uint32_t kOffTmem = kOffBar + 8;
+constexpr uint32_t kSmemBytes = kOffTmem + 8;
+static_assert(kOffBar % 8 == 0, "mbarrier alignment");
+static_assert(kSmemBytes <= 110 * 1024, "two CTAs per SM");
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
+// (K-direction) byte offset >> 4 (16-29), stride (8-row group) byte offset
+// >> 4 (32-45), descriptor version 1 (bits 46-47), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t cm_off(int r, int kgroup, int kdim)
+{
+    return (uint32_t)((r >> 3) * (kdim * 16) + kgroup * 128 + (r & 7) * 16);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for one completion of the barrier's phase `parity`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
+}
+
+// Bias + GELU on 32 accumulator columns [c0, c0 + 32) of row r, stored as BF16
+// into the 128-wide A operand at `h`.
+__device__ __forceinline__ void gelu_store(const uint32_t (&v)[32], const float *bias, int c0, int r, unsigned char *h)
+{
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = g * 8 + 2 * i;
+            w[i] = mlp::pack_bf16(mlp::gelu_fast(__uint_as_float(v[c]) + bias[c0 + c]),
+                                  mlp::gelu_fast(__uint_as_float(v[c + 1]) + bias[c0 + c + 1]));
+        }
+        *reinterpret_cast<uint4 *>(h + cm_off(r, (c0 >> 3) + g, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const float *__restrict__ x, int64_t P,
+                          const int32_t *__restrict__ pfilt, const int32_t *__restrict__ obs_idx,
+                          const float *__restrict__ obs, int32_t obs_stride, const __nv_bfloat16 *__restrict__ wp,
+                          const float *__restrict__ theta, float *__restrict__ out, int32_t *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t R = P * dy;
+    const int64_t n_tiles = (R + kRows - 1) / kRows;
+    float *bias = reinterpret_cast<float *>(smem + kOffBias);
+    const uint32_t bar = smem_u32(smem + kOffBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffTmem);
+
+    // weights (core-matrix layout) and biases, once per CTA
+    const uint4 *w1g = reinterpret_cast<const uint4 *>(wp);
+    const uint4 *w2g = reinterpret_cast<const uint4 *>(wp + mlp::kPackW1);
+    const uint4 *w3g = reinterpret_cast<const uint4 *>(wp + mlp::kPackW1 + mlp::kPackW2);
+    for (int i = tid; i < 128 * 8; i += kThreads) {  // W1: 128 rows x 8 groups of 8
+        const int n = i >> 3, g = i & 7;
+        *reinterpret_cast<uint4 *>(smem + kOffW1 + cm_off(n, g, 64)) = w1g[n * 8 + g];
+    }
+    for (int i = tid; i < 128 * 16; i += kThreads) {  // W2: 128 rows x 16 groups
+        const int n = i >> 4, g = i & 15;
+        *reinterpret_cast<uint4 *>(smem + kOffW2 + cm_off(n, g, 128)) = w2g[n * 16 + g];
+    }
+    for (int i = tid; i < 16 * 16; i += kThreads) {  // W3: 8 packed rows, rows 8..15 zero
+        const int n = i >> 4, g = i & 15;
+        *reinterpret_cast<uint4 *>(smem + kOffW3 + cm_off(n, g, 128)) =
+            n < mlp::kOutPad ? w3g[n * 16 + g] : make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int i = tid; i < 128; i += kThreads) {
+        bias[i] = theta[mlp::kOffB1 + i];
+        bias[128 + i] = theta[mlp::kOffB2 + i];
+    }
+    if (tid < 4) bias[256 + tid] = theta[mlp::kOffB3 + tid];
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t id128 = idesc_bf16(128, 128), id16 = idesc_bf16(128, 16);
+    uint32_t phase = 0;
+    bool expired = false;
+    const int nn = J * J;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // ---- input rows -> A
+        {
+            const int64_t g = tile * kRows + tid;
+            uint32_t w[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) w[i] = 0u;
+            if (g < R) {
+                const int64_t p = g / dy;
+                const int j = (int)(g - p * dy);
+                const int nd = obs_idx[j], ri = nd / J, ci = nd - ri * J;
+                const float *xp = x + p * (int64_t)dx;
+                float vals[51];
+                int q = 0;
+#pragma unroll
+                for (int di = -2; di <= 2; ++di)
+#pragma unroll
+                    for (int dj = -2; dj <= 2; ++dj, ++q) {
+                        const int k = mirror_index(ri + di, J) * J + mirror_index(ci + dj, J);
+                        vals[q] = xp[k];
+                        vals[25 + q] = xp[nn + k];
+                    }
+                vals[50] = obs[(obs_stride ? (int64_t)pfilt[p] * obs_stride : 0) + j];
+#pragma unroll
+                for (int i = 0; i < 25; ++i) w[i] = mlp::pack_bf16(vals[2 * i], vals[2 * i + 1]);
+                w[25] = mlp::pack_bf16(vals[50], 0.0f);
+            }
+#pragma unroll
+            for (int kg = 0; kg < 8; ++kg)
+                *reinterpret_cast<uint4 *>(smem + kOffA + cm_off(tid, kg, 64)) =
+                    make_uint4(w[4 * kg], w[4 * kg + 1], w[4 * kg + 2], w[4 * kg + 3]);
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        // ---- layer 1
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                umma(tmem, sdesc(sbase + kOffA + 256 * k, 128, 1024), sdesc(sbase + kOffW1 + 256 * k, 128, 1024),
+                     id128, k > 0);
+            umma_commit(bar);
+        }
+        bool ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) { expired = true; break; }
+        tc_fence_after();
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(lane_base + c0, v);
+            tc_wait_ld();
+            gelu_store(v, bias, c0, tid, smem + kOffH);
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        // ---- layer 2
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                umma(tmem + 128, sdesc(sbase + kOffH + 256 * k, 128, 2048), sdesc(sbase + kOffW2 + 256 * k, 128, 2048),
+                     id128, k > 0);
+            umma_commit(bar);
+        }
+        ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) { expired = true; break; }
+        tc_fence_after();
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(lane_base + 128 + c0, v);
+            tc_wait_ld();
+            gelu_store(v, bias + 128, c0, tid, smem + kOffH);
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        // ---- layer 3 (N = 16; rows 4..15 of W3 are zero)
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                umma(tmem, sdesc(sbase + kOffH + 256 * k, 128, 2048), sdesc(sbase + kOffW3 + 256 * k, 128, 2048), id16,
+                     k > 0);
+            umma_commit(bar);
+        }
+        ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) { expired = true; break; }
+        tc_fence_after();
+        {
+            uint32_t v[4];
+            tmem_ld4(lane_base, v);
+            tc_wait_ld();
+            const int64_t g = tile * kRows + tid;
+            if (g < R)
+                reinterpret_cast<float4 *>(out)[g] =
+                    make_float4(__uint_as_float(v[0]) + bias[256], __uint_as_float(v[1]) + bias[257],
+                                __uint_as_float(v[2]) + bias[258], __uint_as_float(v[3]) + bias[259]);
+        }
+        tc_fence_before();
+    }
+    // a wait that expired: report it (every thread left the loop together)
+    if (expired && tid == 0 && err) atomicOr(&err[0], kErrTimeout);
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+}  // namespace tc
+
+cudaError_t launch_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const float *x, int64_t P,
+                                       const int32_t *pfilt, const int32_t *obs_idx, const float *obs,
+                                       int32_t obs_stride, const __nv_bfloat16 *wp, const float *theta, float *out,
+                                       int32_t *err, cudaStream_t s)
+{
+    const int64_t R = P * dy;
+    if (R <= 0) return cudaSuccess;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(tc::k_proposal_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)tc::kSmemBytes);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
+    const int64_t grid = std::min<int64_t>(n_tiles, 2 * (int64_t)tc::sm_count());
+    tc::k_proposal_forward_tc<<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
+        J, dx, dy, x, P, pfilt, obs_idx, obs, obs_stride, wp, theta, out, err);
+    return cudaGetLastError();
+}
+
+}  // namespace pf
+
+extern "C" {
+
+pf_status pf_proposal_forward(int32_t J, int64_t P, const float *d_x, int32_t dy, const int32_t *h_obs_idx,
+                              const float *d_y, const float *d_theta, float *d_out, void *stream)
+{
+    if (J < 2 || J > 44 || P < 0 || dy < 1 || !h_obs_idx) return PF_EINVAL;
+    if (P > 0 && (!d_x || !d_y || !d_theta || !d_out)) return PF_EINVAL;
+    if (((uintptr_t)d_out & 15u) != 0) return PF_EINVAL;  // float4 rows
+    for (int j = 0; j < dy; ++j)
+        if (h_obs_idx[j] < 0 || h_obs_idx[j] >= J * J) return PF_EINVAL;
+    if (P == 0) return PF_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    __nv_bfloat16 *wp = nullptr;
+    int32_t *idx = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&wp, (pf::mlp::kPackTotal + pf::mlp::kHid * pf::mlp::kHid) * 2, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&idx, (size_t)dy * sizeof(int32_t), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (wp) cudaFreeAsync(wp, s);
+        return PF_ENOMEM;
+    }
+    e = cudaMemcpyAsync(idx, h_obs_idx, (size_t)dy * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = pf::launch_mlp_pack(d_theta, wp, wp + pf::mlp::kPackTotal, s);
+    if (e == cudaSuccess)
+        e = pf::launch_proposal_forward_tc(J, 2 * J * J, dy, d_x, P, nullptr, idx, d_y, 0, wp, d_theta, d_out,
+                                           nullptr, s);
+    cudaFreeAsync(idx, s);
+    cudaFreeAsync(wp, s);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+}  // extern "C"

@@ -23,6 +23,10 @@ __device__ __forceinline__ Real fhn_drift_w(const ModelParams &mp, Real v, Real 
     return b * (v - d * w);
 }
 
+// Mirror reflection of a lattice coordinate k in [-2, J + 1] (zero flux at the
+// edges): -1 -> 0, -2 -> 1, J -> J - 1, J + 1 -> J - 2.
+__device__ __forceinline__ int mirror_index(int k, int J) { return k < 0 ? -k - 1 : (k >= J ? 2 * J - k - 1 : k); }
+
 // Euler-Maruyama update written with explicit fused multiply-adds, so that
 // every kernel that takes a lattice sub-step rounds it identically.
 __device__ __forceinline__ float em_update(float x, float f, float z, float dt, float sq)

@@ -31,6 +31,27 @@ constexpr int kLdHid = kHid + 8;     // ... of 128
 constexpr int kPackW1 = kHid * kInPad, kPackW2 = kHid * kHid, kPackW3 = kOutPad * kHid;
 constexpr int kPackTotal = kPackW1 + kPackW2 + kPackW3;
 
+// GELU for the inference kernel: x Phi(x) with Phi(x) = (1 + erf(x / sqrt 2)) / 2
+// and erf from Abramowitz & Stegun 7.1.26 (Hastings' rational form,
+// |error| <= 1.5e-7): 1 - erf(u) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-u^2},
+// t = 1 / (1 + p u), u = |x| / sqrt 2; Phi(x) = 1 - tail / 2 for x >= 0 and
+// tail / 2 below.  Far below the BF16 rounding of the activations it feeds.
+__device__ __forceinline__ float gelu_fast(float x)
+{
+    const float u = fabsf(x) * 0.70710678118654752f;
+    float t;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(fmaf(0.3275911f, u, 1.0f)));
+    float q = fmaf(t, 1.061405429f, -1.453152027f);
+    q = fmaf(t, q, 1.421413741f);
+    q = fmaf(t, q, -0.284496736f);
+    q = fmaf(t, q, 0.254829592f);
+    q *= t;
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-u * u * 1.44269504088896341f));
+    const float tail = q * e;  // 1 - erf(|x| / sqrt 2) = 2 Phi(-|x|), without cancellation
+    return 0.5f * x * (x >= 0.0f ? 2.0f - tail : tail);
+}
+
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
 __device__ __forceinline__ float gelu_grad(float x)

@@ -198,6 +198,10 @@ pf_status check_device_flags(Ctx &c)
         return fail(c, PF_ENUMERIC, "filter " + std::to_string(err[1]) +
                                         " had no finite positive weight (all log-weights -inf or NaN)");
     }
+    if (err[0] & kErrTimeout) {
+        c.fatal = PF_ETIMEOUT;
+        return fail(c, PF_ETIMEOUT, "a tensor-core wait in the proposal network expired");
+    }
     return PF_OK;
 }
 
@@ -267,7 +271,8 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
 // at most kSubTile particles inside them.  Per-filter partial maxima come from
 // the sub-tiles (small models) or the tiles (lattice, stateless resampling).
 void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std::vector<FilterDesc> &filt,
-                std::vector<int64_t> &off, std::vector<TileDesc> *subs = nullptr)
+                std::vector<int64_t> &off, std::vector<TileDesc> *subs = nullptr,
+                std::vector<TileDesc> *mchunks = nullptr)
 {
     const int32_t M = (int32_t)N.size();
     off.assign(M + 1, 0);
@@ -289,6 +294,18 @@ void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std
             tiles.push_back(td);
         }
         fd.tile_count = (int32_t)tiles.size() - fd.tile_begin;
+        if (mchunks) {
+            fd.mc_begin = (int32_t)mchunks->size();
+            for (int32_t s = 0; s < N[m]; s += kMeanChunk) {
+                TileDesc mc{};
+                mc.m = m;
+                mc.lstart = s;
+                mc.len = std::min(kMeanChunk, N[m] - s);
+                mc.gstart = off[m] + s;
+                mchunks->push_back(mc);
+            }
+            fd.mc_count = (int32_t)mchunks->size() - fd.mc_begin;
+        }
         if (subs) {
             for (int32_t s = 0; s < N[m]; s += kSubTile) {
                 TileDesc st{};
@@ -412,13 +429,14 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     }
     c.stream = c.own_stream;
 
-    std::vector<TileDesc> tiles, subs;
+    std::vector<TileDesc> tiles, subs, mchunks;
     std::vector<FilterDesc> filt;
     const bool small = mp.kind != PF_MODEL_FHN_LATTICE;
-    make_tiles(c.N, tiles, filt, c.off, small ? &subs : nullptr);
+    make_tiles(c.N, tiles, filt, c.off, small ? &subs : nullptr, small ? nullptr : &mchunks);
     c.P = c.off[M];
     c.n_tiles = (int32_t)tiles.size();
     c.n_subs = (int32_t)subs.size();
+    c.n_mchunks = (int32_t)mchunks.size();
     {
         int max_len = 1;
         for (const TileDesc &td : tiles) max_len = std::max(max_len, td.len);
@@ -439,7 +457,10 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
               alloc_n(c, c.d_obs, (size_t)M * mp.dy) && alloc_n(c, c.d_t, 1) && alloc_n(c, c.err, 2) &&
               alloc_n(c, c.obs_idx, mp.dy) && alloc_n(c, c.x0, dx);
     if (ok) ok = alloc_n(c, c.pfilt, P);
-    if (ok && mp.kind == PF_MODEL_FHN_LATTICE) ok = alloc_n(c, c.obs_slot, mp.J * mp.J);
+    if (ok && mp.kind == PF_MODEL_FHN_LATTICE)
+        ok = alloc_n(c, c.obs_slot, mp.J * mp.J) && alloc_n(c, c.mchunks, mchunks.size()) &&
+             alloc_n(c, c.mean_part, mchunks.size() * (size_t)dx) &&
+             alloc_n(c, c.mean_cnt, (size_t)M * ((dx + 255) / 256));
     else if (ok) ok = alloc_n(c, c.tile_est, (size_t)c.n_tiles * dx);
     if (!ok) {
         g_create_error = "device allocation failed";
@@ -488,6 +509,11 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
         slot.assign(mp.J * mp.J, -1);
         for (int j = 0; j < mp.dy; ++j) slot[obs->idx[j]] = j;
         e = cudaMemcpyAsync(c.obs_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c.mchunks, mchunks.data(), mchunks.size() * sizeof(TileDesc), cudaMemcpyHostToDevice,
+                                c.stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c.mean_cnt, 0, (size_t)M * ((dx + 255) / 256) * sizeof(int32_t), c.stream);
     }
     if (e == cudaSuccess) e = launch_init(c, c.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);  // host staging vectors go out of scope

@@ -21,6 +21,7 @@ constexpr int kTile = 1024;
 constexpr int kResampleThreads = 256;
 constexpr int kItems = kTile / kResampleThreads;  // particles per thread in the tile kernels
 constexpr int kSubTile = 128;                     // propagation block of the thread-per-particle models
+constexpr int kMeanChunk = 256;                   // particles per partial sum of the lattice means
 
 struct TileDesc {
     int32_t m;       // filter
@@ -36,6 +37,9 @@ struct FilterDesc {
     int32_t tile_begin;  // first tile
     int32_t tile_count;  // tiles
     int32_t shift;       // 52 - ceil(log2 N): weight quantisation exponent
+    int32_t mc_begin;    // first chunk of kMeanChunk particles (lattice means)
+    int32_t mc_count;    // chunks
+    int32_t pad;
 };
 
 // Order-preserving int image of a float (signed-int max = float max), so the
@@ -60,7 +64,7 @@ enum FStat : int {
 enum TSum : int { kTsW = 0, kTsW2 = 1, kTsCount = 2 };
 
 // Device error word: bit flags plus the first offending filter.
-enum : int32_t { kErrDegenerate = 1 };
+enum : int32_t { kErrDegenerate = 1, kErrTimeout = 2 };
 
 // Everything the resampling kernels need, by value.
 struct ResampleArgs {
@@ -98,6 +102,13 @@ cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride
 cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t stride, float *x, cudaStream_t s);
 cudaError_t launch_gather_tuples(const Ctx &c, const float *x_new, cudaStream_t s);
 cudaError_t launch_mlp_pack(const float *theta, __nv_bfloat16 *wp, __nv_bfloat16 *w2t, cudaStream_t s);
+// Network forward on the tcgen05 tensor cores fused with its input rows
+// (k_proposal_tc.cu): out[(p dy + j)][4] for every particle p and observed
+// node j; pfilt may be null when obs_stride is 0; err may be null.
+cudaError_t launch_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const float *x, int64_t P,
+                                       const int32_t *pfilt, const int32_t *obs_idx, const float *obs,
+                                       int32_t obs_stride, const __nv_bfloat16 *wp, const float *theta, float *out,
+                                       int32_t *err, cudaStream_t s);
 cudaError_t launch_mlp_forward_bf16(const __nv_bfloat16 *rows, int64_t R, const __nv_bfloat16 *wp, const float *theta,
                                     float *out, cudaStream_t s);
 cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s);
@@ -124,6 +135,10 @@ struct Ctx {
     // device memory
     TileDesc *tiles = nullptr;
     TileDesc *subs = nullptr;     // sub-tiles of kSubTile particles (small models)
+    TileDesc *mchunks = nullptr;  // chunks of kMeanChunk particles (lattice means)
+    int32_t n_mchunks = 0;
+    double *mean_part = nullptr;  // [n_mchunks][dx] FP64 partial sums (lattice)
+    int32_t *mean_cnt = nullptr;  // [M][ceil(dx / 256)] chunk completion counters, zero between launches
     int32_t n_subs = 0;
     FilterDesc *filt = nullptr;
     int32_t *pfilt = nullptr;     // [P] filter of each particle (lattice kernels)

@@ -74,6 +74,8 @@ _SIGS = {
     "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
     "pf_record_tuples": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
     "pf_recorded_tuples": (c_int32, [c_void_p, POINTER(c_int64)]),
+    "pf_proposal_forward": (c_int32, [c_int32, c_int64, c_void_p, c_int32, POINTER(c_int32), c_void_p, c_void_p,
+                                      c_void_p, c_void_p]),
     "pf_mlp_forward": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_mlp_trainer_create": (c_int32, [POINTER(c_float), c_int32, c_int64, POINTER(c_void_p)]),
     "pf_mlp_train_step": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_float, POINTER(c_float),
@@ -182,6 +184,14 @@ def pf_systematic_resample_noalloc(N: Sequence[int], d_w, d_u, d_anc, stream=Non
 
 
 MLP_PARAMS = 23684
+
+
+def pf_proposal_forward(J: int, d_x, obs_idx, d_y, d_theta, d_out, stream=None):
+    """Network outputs for every (particle, observed node) of lattice states d_x
+    (P x 2 J^2, device), rows built on the device; d_out: (P dy) x 4 FP32."""
+    idx = np.ascontiguousarray(obs_idx, dtype=np.int32)
+    _check(lib().pf_proposal_forward(int(J), d_x.shape[0], d_x.data_ptr(), len(idx), _ip(idx), d_y.data_ptr(),
+                                     d_theta.data_ptr(), d_out.data_ptr(), stream))
 
 
 def pf_mlp_forward(d_in, d_theta, d_out, stream=None):

@@ -99,3 +99,29 @@ def test_training_reduces_the_loss():
     tr.close()
     # R = noise + 0.3 X[:, :2]: a good fit removes part of the variance
     assert losses[-1] < losses[0] - 0.05, (losses[0], losses[-1])
+
+
+@pytest.mark.parametrize("J,P", [(8, 300), (40, 37), (2, 5)])
+def test_lattice_forward_on_tcgen05_matches_oracle(J, P):
+    """The filter's fused form: input rows gathered from lattice states on the
+    device, the network on tcgen05 with TMEM accumulators (a ragged last tile
+    of 128 rows), against the FP64 oracle's rows (oracle/mlp.patch_rows) and
+    BF16-emulating forward; tolerance as for the forward above (the GELU's erf
+    approximation, |error| <= 1.5e-7, is far below the BF16 rounding)."""
+    from paper_1407_8071_gb300 import workloads as W
+    th = _theta(9)
+    nodes = W.fhn_obs_nodes(J, 4 if J > 2 else 1)
+    rng = np.random.default_rng(J * 1000 + P)
+    x = rng.normal(0.0, 0.3, (P, 2 * J * J)).astype(np.float32)
+    y = rng.normal(0.0, 0.5, len(nodes)).astype(np.float32)
+    d_out = torch.full((P * len(nodes), 4), float("nan"), dtype=torch.float32, device="cuda")
+    pf.pf_proposal_forward(J, torch.from_numpy(x).cuda(), nodes, torch.from_numpy(y).cuda(),
+                           torch.from_numpy(th.astype(np.float32)).cuda(), d_out)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().astype(np.float64)
+    rows = np.concatenate([mlp.patch_rows(x[p].astype(np.float64), J, nodes, y.astype(np.float64)) for p in range(P)])
+    ref, _ = mlp.forward(th, rows, bf16_emulation=True)
+    scale = np.sqrt(np.mean(ref ** 2, axis=0, keepdims=True))
+    err = np.abs(got - ref) / (np.abs(ref) + scale)
+    assert np.all(np.isfinite(got))
+    assert err.max() <= 2e-2, (err.max(), np.unravel_index(np.argmax(err), err.shape))
