@@ -58,7 +58,7 @@ __global__ void k_build_rows(ModelParams mp, const float *__restrict__ x, int64_
 // where z is the transition's own normal; elsewhere x' = m + h z.  Writes x',
 // the transition's candidate and m at the observed nodes, log g + sum(log p -
 // log q) and the transition's log g.
-__global__ void __launch_bounds__(1024) k_last_step_fhn(ModelParams mp, Key key, const int32_t *pfilt,
+__global__ void __launch_bounds__(1024, 2) k_last_step_fhn(ModelParams mp, Key key, const int32_t *pfilt,
                                                            const FilterDesc *filt, float *x, int64_t P,
                                                            const float *obs, int32_t obs_stride,
                                                            const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(1024) k_last_step_fhn(ModelParams mp, Key key,
         normals4<float>(key, c0, t, c2, kStreamDyn, (uint32_t)k * (uint32_t)(mp.dx / 4) + (uint32_t)q, z);
         const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
         float *xo = x + p * (int64_t)mp.dx;
-#pragma unroll
+        const float inv_h = 1.0f / h;
+#pragma unroll 1
         for (int e = 0; e < 2; ++e) {
             const int node = n0 + e;
             const bool stim = on && row < blk && col + e < blk;
@@ -131,9 +132,12 @@ __global__ void __launch_bounds__(1024) k_last_step_fhn(ModelParams mp, Key key,
                 for (int cc = 0; cc < 2; ++cc) {
                     const float os = fminf(fmaxf(o[2 + cc], -mlp::kClamp), mlp::kClamp);
                     const float mu = __fmaf_rn(h, o[cc], mc[cc]);
-                    const float sd = h * __expf(os);
+                    const float es = __expf(os);  // exactly 1 at os = 0
+                    const float sd = h * es;
                     xn[cc] = __fmaf_rn(sd, zc[cc], mu);
-                    const float t1 = (xn[cc] - mc[cc]) / h, t2 = (xn[cc] - mu) / sd;
+                    // standardised residuals under p and q (the same products when o = 0,
+                    // so a zero network adds exactly nothing)
+                    const float t1 = (xn[cc] - mc[cc]) * inv_h, t2 = (xn[cc] - mu) * (inv_h / es);
                     lw += os + 0.5f * (t2 * t2 - t1 * t1);
                 }
                 nv = xn[0];
@@ -248,23 +252,31 @@ __global__ void __launch_bounds__(256) k_proposal_select(const FilterDesc *filt,
         fallback = 1;  // recording without a network: the transition's step
     }
     __syncthreads();
-    const int nn = mp.J * mp.J, dy = mp.dy;
-    if (fallback) {
+    if (fallback)  // the observed nodes follow in k_proposal_fixup
         for (int i = tid; i < fd.N; i += blockDim.x) logw[fd.off + i] = logw_boot[fd.off + i];
-        for (int64_t e = tid; e < (int64_t)fd.N * dy; e += blockDim.x) {
-            const int64_t i = e / dy;
-            const int j = (int)(e - i * dy);
-            const int64_t p = fd.off + i;
-            const int nd = obs_idx[j];
-            x[p * mp.dx + nd] = xboot[(p * dy + j) * 2];
-            x[p * mp.dx + nn + nd] = xboot[(p * dy + j) * 2 + 1];
-        }
-    }
     if (tid == 0) {
         const float mx = fallback ? mb : mp_;
         fmax_key[blockIdx.x] = mx > -INFINITY ? float_order_key(mx) : kNegInfKey;
         fstats[(int64_t)blockIdx.x * kFsCount + kFsFallback] = (use_proposal && fallback) ? 1.0 : 0.0;
     }
+}
+
+// The fallback's state: for particles of filters that took the transition's
+// step, the observed nodes get the transition's candidates (grid-wide, one
+// thread per (particle, observed node), so the copy is as parallel as the data).
+__global__ void __launch_bounds__(256) k_proposal_fixup(const int32_t *__restrict__ pfilt, ModelParams mp, int64_t P,
+                                                        const double *__restrict__ fstats, float *x,
+                                                        const float *__restrict__ xboot,
+                                                        const int32_t *__restrict__ obs_idx)
+{
+    const int dy = mp.dy;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= P * dy) return;
+    const int64_t p = e / dy;
+    if (fstats[(int64_t)pfilt[p] * kFsCount + kFsFallback] == 0.0) return;
+    const int j = (int)(e - p * dy), nd = obs_idx[j], nn = mp.J * mp.J;
+    x[p * mp.dx + nd] = xboot[e * 2];
+    x[p * mp.dx + nn + nd] = xboot[e * 2 + 1];
 }
 
 // Training tuples from the resampled particles: for every kept particle i
@@ -329,6 +341,9 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
                                                      c.d_t, ppc, mo, c.xboot, c.mp_obs, c.logw, c.logw_boot);
     k_proposal_select<<<c.M, 256, 0, s>>>(c.filt, c.mp, c.prop_ess_frac, c.prop_on ? 1 : 0, c.logw, c.logw_boot, x,
                                           c.xboot, c.obs_idx, c.fmax_key, c.fstats);
+    const int64_t rows = c.P * c.mp.dy;
+    k_proposal_fixup<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(c.pfilt, c.mp, c.P, c.fstats, x, c.xboot,
+                                                                  c.obs_idx);
     return cudaGetLastError();
 }
 
