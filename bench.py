@@ -524,7 +524,8 @@ def main():
                        "N_total": int(wl.N_list.sum())}]),
             "K": wl.spec.K, "dt": wl.spec.dt,
             "autotuned": None if wl.choice is None else {"particles_per_cta": wl.choice[0],
-                                                         "resample_threads": wl.choice[1]},
+                                                         "resample_threads": wl.choice[1],
+                                                         "nodes_per_thread": wl.choice[2]},
             "precision": "FP32 state and propagation; FP64 normaliser, prefix sum and M-average",
             "l2": ("working set of the seven contexts (~340 MB) exceeds the 129 MB L2; each context's data "
                    "is evicted by the other six between its steps") if args.workload == "lorenz-sweep"

@@ -193,13 +193,24 @@ PF_API pf_status pf_estimate(pf_ctx *ctx, const pf_stat *stat, double *out);
  * (one particle per CTA up to as many as fit in 1024 threads); for every model,
  * threads per resampling tile CTA (64, 128, 256 -- fewer threads and more CTAs
  * for small filters).  The choice is cached per (model, lattice side, K, dx,
- * particle counts) for the process, and reported in h_choice[0..1] (may be
+ * particle counts) for the process, and reported in h_choice[0..2] (may be
  * NULL): h_choice[0] particles per lattice CTA (0 for the small models, which
- * run one particle per thread), h_choice[1] resampling threads.  The filter's state, statistics and step counter are unchanged.
+ * run one particle per thread), h_choice[1] resampling threads, h_choice[2]
+ * lattice nodes per thread (2 or 4; 1 for the small models).  The filter's state, statistics and step counter are unchanged.
  * Synchronises; needs about one particle buffer of temporary device memory.
  * Errors: PF_ESTATE (between pf_propagate and pf_resample, or recording),
  * PF_ENOMEM, PF_ECUDA. */
 PF_API pf_status pf_autotune(pf_ctx *ctx, int32_t *h_choice);
+
+/* Sets the launch schedule explicitly (0 in any field: the default):
+ * nodes_per_thread 2 or 4 for the lattice kernels (4 needs J % 4 == 0),
+ * particles_per_cta >= 1 for the lattice (clamped to what fits in 1024
+ * threads), resample_threads 64, 128 or 256 (at least a quarter of the
+ * largest tile, min(N_m, 1024)).  Results do not depend on the schedule
+ * (particles and ancestors bit for bit; FP64 estimates to summation order).
+ * Synchronises.  Errors: PF_EINVAL, PF_ESTATE. */
+PF_API pf_status pf_set_schedule(pf_ctx *ctx, int32_t nodes_per_thread, int32_t particles_per_cta,
+                                 int32_t resample_threads);
 
 /* --------------------------------------------------------------------- */
 /* Inspection and state transfer (synchronous; for tests and checkpoints) */

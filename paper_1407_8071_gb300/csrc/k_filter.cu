@@ -534,6 +534,118 @@ __global__ void __launch_bounds__(1024, 2)
     }
 }
 
+// The same interval with four nodes per thread (lattice sides divisible by
+// 4): thread (slot s, quad q) carries nodes 4q..4q+3 of one row, i.e. the two
+// pairs 2q and 2q+1 of k_propagate_fhn, with their Philox blocks, the same
+// per-node arithmetic (two pair_laplacian calls, the same drift and update
+// calls) and the same per-particle reduction over pairs, so its results are
+// bit-identical to the pair kernel's.  One barrier and four shared-memory
+// loads serve four nodes (up/down as float4, left/right as scalars), and the
+// two generator chains interleave.
+constexpr int kFhn4MaxThreads = 512;  // three CTAs per SM at <= 42 registers
+
+__global__ void __launch_bounds__(kFhn4MaxThreads, 3)
+    k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
+                     const float *__restrict__ x_in, float *__restrict__ x_out, int64_t P, float *logw,
+                     const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
+                     int32_t *fmax_key, int32_t n_steps)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int J = mp.J, nn = J * J, quads = nn / 4, pairs = nn / 2, qrow = J / 4;
+    float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [2][ppc][quads]
+    const int slot = (int)threadIdx.x / quads;
+    const int s = min(slot, ppc);                   // s == ppc: padding thread
+    const int q = threadIdx.x - min(slot, ppc - 1) * quads;
+    const int64_t p = (int64_t)blockIdx.x * ppc + s;
+    const bool active = (s < ppc) && (p < P);
+    const uint32_t t = (uint32_t)(*d_t + 1);
+
+    uint32_t c0 = 0, c2 = 0;
+    float v[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
+    const int n0 = 4 * q, row = n0 / J, col = n0 - row * J;
+    if (active) {
+        const int32_t m = pfilt[p];
+        c0 = (uint32_t)(p - filt[m].off);
+        c2 = (uint32_t)m;
+        const float4 a = *reinterpret_cast<const float4 *>(x_in + p * (int64_t)mp.dx + n0);
+        const float4 b = *reinterpret_cast<const float4 *>(x_in + p * (int64_t)mp.dx + nn + n0);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
+    }
+    const float dt = mp.fdt, sq = mp.fsq, amp = mp.fp[6];
+    const int64_t stim_steps = (int64_t)mp.p[7];
+    const int blk = (int)mp.p[8];
+    const int64_t n_base = (int64_t)(t - 1) * mp.K;
+    const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
+    const int qu = row > 0 ? q - qrow : q, qd = row < J - 1 ? q + qrow : q;
+    const bool has_left = col > 0, has_right = col + 4 < J;
+    const int ql = has_left ? q - 1 : q, qr = has_right ? q + 1 : q;
+
+    for (int k = 0; k < n_steps; ++k) {
+        float4 *buf = sv + ((k & 1) * ppc + (active ? s : 0)) * quads;
+        if (active) buf[q] = make_float4(v[0], v[1], v[2], v[3]);
+        __syncthreads();
+        if (active) {
+            float z[8];
+            const uint32_t bk = (uint32_t)k * blocks_per_step + 2u * (uint32_t)q;
+            normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
+            normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+            const float4 up = buf[qu], dn = buf[qd];
+            const float left = has_left ? buf[ql].w : v[0], right = has_right ? buf[qr].x : v[3];
+            float l[4];
+            pair_laplacian<float>(v[0], v[1], up.x, up.y, dn.x, dn.y, left, v[2], l[0], l[1]);
+            pair_laplacian<float>(v[2], v[3], up.z, up.w, dn.z, dn.w, v[1], right, l[2], l[3]);
+            const bool on = (n_base + k) < stim_steps;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float I = (on && row < blk && col + e < blk) ? amp : 0.0f;
+                const float fv = fhn_drift_v<float>(mp, v[e], w[e], l[e], I), fw = fhn_drift_w<float>(mp, v[e], w[e]);
+                v[e] = em_update(v[e], fv, z[2 * e], dt, sq);
+                w[e] = em_update(w[e], fw, z[2 * e + 1], dt, sq);
+            }
+        }
+    }
+    if (active) {
+        *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + n0) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + nn + n0) = make_float4(w[0], w[1], w[2], w[3]);
+    }
+    if (!logw) return;
+    // per pair, as the pair kernel forms it, then its fixed-order sum over pairs
+    float part[2] = {0.0f, 0.0f};
+    if (active) {
+        const int32_t m = pfilt[p];
+        const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = obs_slot[n0 + e];
+            if (j >= 0) {
+                const float d = y[j] - v[e];
+                part[e >> 1] += d * d;
+            }
+        }
+    }
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(smem_raw);  // [ppc][pairs]
+    if (active) {
+        red[s * pairs + 2 * q] = part[0];
+        red[s * pairs + 2 * q + 1] = part[1];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int sl = warp; sl < ppc; sl += nwarps) {
+        const int64_t pp = (int64_t)blockIdx.x * ppc + sl;
+        float acc = 0.0f;
+        for (int i = lane; i < pairs; i += 32) acc += red[sl * pairs + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && pp < P) {
+            const float lv = mp.fhalf_prec * acc;
+            logw[pp] = lv;
+            if (lv > -INFINITY && lv < INFINITY) atomicMax(&fmax_key[pfilt[pp]], float_order_key(lv));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ resampling chain
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t value)
 {
@@ -962,15 +1074,22 @@ namespace {
 // Threads of a lattice CTA: ppc particles x J^2/2 node pairs, rounded up to
 // whole warps (the extra threads hold no particle).  want = 0 picks as many
 // particles as fit in 1024 threads (at most 8).
-int fhn_threads(const ModelParams &mp, int *ppc, int want = 0)
+// Threads of a lattice CTA carrying up to `want` particles (0: as many as fit
+// in 1024 threads -- 512 for the four-node kernel --, at most 8) with `nodes`
+// (2 or 4) nodes per thread.
+int fhn_threads(const ModelParams &mp, int *ppc, int want = 0, int nodes = 2)
 {
-    const int pairs = mp.J * mp.J / 2;
+    const int per = mp.J * mp.J / nodes, cap = nodes == 4 ? kFhn4MaxThreads : 1024;
     int n = 1;
-    while ((n + 1) * pairs <= 1024 && n < 8) ++n;
+    while ((n + 1) * per <= cap && n < 8) ++n;
     if (want > 0 && want < n) n = want;
     *ppc = n;
-    return (n * pairs + 31) / 32 * 32;
+    return (n * per + 31) / 32 * 32;
 }
+
+// Nodes per thread of the lattice kernels: 4 where the side allows it, unless
+// the schedule asks for 2.
+int fhn_nodes(const Ctx &c) { return (c.fhn_nodes == 2 || c.mp.J % 4 != 0) ? 2 : 4; }
 
 size_t fhn_smem(const ModelParams &mp, int threads, int ppc, size_t real_bytes)
 {
@@ -1035,24 +1154,41 @@ cudaError_t launch_init(const Ctx &c, cudaStream_t s)
     }
 }
 
+// n_steps lattice sub-steps of every particle, xi -> xo, with the weights and
+// per-filter maxima when `weigh` (the pair or the four-node kernel).
+cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
+                                int32_t n_steps, bool weigh, cudaStream_t s)
+{
+    const int nodes = fhn_nodes(c);
+    int ppc;
+    const int threads = fhn_threads(c.mp, &ppc, c.fhn_ppc, nodes);
+    const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
+    const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
+    static bool carveout_set = false;  // prefer shared memory so that several CTAs fit per SM
+    if (!carveout_set) {
+        cudaFuncSetAttribute(k_propagate_fhn<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        carveout_set = true;
+    }
+    if (nodes == 4)
+        k_propagate_fhn4<<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, weigh ? c.logw : nullptr,
+                                                     d_obs, stride, c.obs_slot, c.d_t, ppc,
+                                                     weigh ? c.fmax_key : nullptr, n_steps);
+    else
+        k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
+                                                           weigh ? c.logw : nullptr, d_obs, stride, c.obs_slot, c.d_t,
+                                                           0, 0, 0, ppc, weigh ? c.fmax_key : nullptr, n_steps);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                              cudaStream_t s)
 {
     if (c.mp.kind == kFhnLattice) {
         int ppc;
-        const int threads = fhn_threads(c.mp, &ppc, c.fhn_ppc);
-        const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
-        const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
-        static bool carveout_set = false;  // prefer shared memory so two CTAs fit per SM
-        if (!carveout_set) {
-            cudaFuncSetAttribute(k_propagate_fhn<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
-            carveout_set = true;
-        }
-        k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
-                                                           c.logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc,
-                                                           c.fmax_key, c.mp.K);
-        return cudaGetLastError();
+        return launch_fhn_interval(c, d_obs, stride, xi, xo, c.mp.K, true, s);
     }
     switch (c.mp.dx) {
     case 1: return propagate_small_launch<1>(c, d_obs, stride, xi, xo, s);
@@ -1066,14 +1202,7 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
 cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, float *x, int32_t n_steps,
                                 cudaStream_t s)
 {
-    int ppc;
-    const int threads = fhn_threads(c.mp, &ppc, c.fhn_ppc);
-    const size_t smem = fhn_smem(c.mp, threads, ppc, sizeof(float));
-    const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
-    k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, x, x, c.P, nullptr,
-                                                       d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc, nullptr,
-                                                       n_steps);
-    return cudaGetLastError();
+    return launch_fhn_interval(c, d_obs, stride, x, x, n_steps, false, s);
 }
 
 cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)

@@ -338,7 +338,7 @@ static std::mutex g_tune_mu;
 // keyed by model kind, lattice side, K, dx, total particles, filters and a
 // hash (FNV-1a) of the particle counts, so ragged batches of the same total
 // are told apart
-static std::map<std::tuple<int, int, int, int, int64_t, int32_t, uint64_t>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int64_t, int32_t, uint64_t>, std::tuple<int, int, int>> g_tune_cache;
 
 static uint64_t counts_hash(const std::vector<int32_t> &N)
 {
@@ -773,8 +773,9 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            c.fhn_ppc = it->second.first;
-            c.resample_threads = it->second.second;
+            c.fhn_ppc = std::get<0>(it->second);
+            c.resample_threads = std::get<1>(it->second);
+            c.fhn_nodes = std::get<2>(it->second);
             cached = true;
         }
     }
@@ -808,22 +809,27 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         std::vector<float> zeros(M * c.mp.dy, 0.0f);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_obs, zeros.data(), zeros.size() * 4, cudaMemcpyHostToDevice, c.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-        int best_ppc = c.fhn_ppc, best_rt = c.resample_threads;
+        int best_ppc = c.fhn_ppc, best_rt = c.resample_threads, best_nodes = c.fhn_nodes;
         auto trial_step = [&] {
             cudaMemcpyAsync(scratch, c.x[c.cur], xb, cudaMemcpyDeviceToDevice, c.stream);
             launch_propagate(c, c.d_obs, 0, scratch, scratch, c.stream);
         };
-        if (e == cudaSuccess && c.mp.kind == PF_MODEL_FHN_LATTICE) {  // particles per lattice CTA
-            const int pairs = c.mp.J * c.mp.J / 2;
-            int maxp = 1;
-            while ((maxp + 1) * pairs <= 1024 && maxp < 8) ++maxp;
+        if (e == cudaSuccess && c.mp.kind == PF_MODEL_FHN_LATTICE) {  // nodes per thread, particles per CTA
             float best = 1e30f;
-            for (int ppc = 1; ppc <= maxp; ++ppc) {
-                c.fhn_ppc = ppc;
-                const float ms = time_ms(c, 3, trial_step);
-                if (ms < best) { best = ms; best_ppc = ppc; }
+            for (int nodes = 2; nodes <= 4; nodes += 2) {
+                if (nodes == 4 && c.mp.J % 4 != 0) continue;
+                const int per = c.mp.J * c.mp.J / nodes, cap = nodes == 4 ? 512 : 1024;
+                int maxp = 1;
+                while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
+                for (int ppc = 1; ppc <= maxp; ++ppc) {
+                    c.fhn_nodes = nodes;
+                    c.fhn_ppc = ppc;
+                    const float ms = time_ms(c, 3, trial_step);
+                    if (ms < best) { best = ms; best_ppc = ppc; best_nodes = nodes; }
+                }
             }
             c.fhn_ppc = best_ppc;
+            c.fhn_nodes = best_nodes;
         }
         if (e == cudaSuccess) {  // threads per resampling tile CTA
             int max_len = 1;
@@ -858,13 +864,39 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {c.fhn_ppc, c.resample_threads};
+        g_tune_cache[key] = std::make_tuple(c.fhn_ppc, c.resample_threads, c.fhn_nodes);
     }
     drop_graphs(c);
     if (h_choice) {
         h_choice[0] = c.fhn_ppc;
         h_choice[1] = c.resample_threads;
+        h_choice[2] = c.mp.kind == PF_MODEL_FHN_LATTICE ? (c.fhn_nodes ? c.fhn_nodes : (c.mp.J % 4 ? 2 : 4)) : 1;
     }
+    return PF_OK;
+}
+
+pf_status pf_set_schedule(pf_ctx *h, int32_t nodes_per_thread, int32_t particles_per_cta, int32_t resample_threads)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_schedule between pf_propagate and pf_resample");
+    const bool lattice = c.mp.kind == PF_MODEL_FHN_LATTICE;
+    if (nodes_per_thread != 0 && !(lattice && (nodes_per_thread == 2 || (nodes_per_thread == 4 && c.mp.J % 4 == 0))))
+        return fail(c, PF_EINVAL, "nodes_per_thread: 0, 2, or 4 (lattice sides divisible by 4)");
+    if (particles_per_cta < 0 || (particles_per_cta > 0 && !lattice))
+        return fail(c, PF_EINVAL, "particles_per_cta: 0, or >= 1 for the lattice");
+    int max_len = 1;
+    for (int32_t n : c.N) max_len = std::max(max_len, std::min(n, kTile));
+    if (resample_threads != 0 && !((resample_threads == 64 || resample_threads == 128 || resample_threads == 256) &&
+                                   resample_threads * kItems >= max_len))
+        return fail(c, PF_EINVAL, "resample_threads: 0, or 64/128/256 with 4 threads' worth covering a tile");
+    pf_status st = sync(c, "set_schedule");
+    if (st != PF_OK) return st;
+    c.fhn_nodes = nodes_per_thread;
+    c.fhn_ppc = particles_per_cta;
+    if (resample_threads) c.resample_threads = resample_threads;
+    drop_graphs(c);
     return PF_OK;
 }
 

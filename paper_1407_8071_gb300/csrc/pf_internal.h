@@ -147,6 +147,7 @@ struct Ctx {
     int32_t *fmax_key = nullptr;  // [M]
     int resample_threads = kResampleThreads;
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
+    int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, or 0 (4 where J % 4 == 0)
     double *tile_sums = nullptr;
     uint64_t *tile_q = nullptr;
     double *fstats = nullptr;

@@ -70,6 +70,7 @@ _SIGS = {
                                          c_size_t, c_void_p]),
     "pf_systematic_resample_noalloc": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p,
                                                  c_void_p]),
+    "pf_set_schedule": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
     "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
     "pf_record_tuples": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
@@ -369,10 +370,15 @@ class EnsembleFilter:
         return a
 
     def autotune(self):
-        """Pick the launch schedule by timing (cached per shape); returns (particles per lattice CTA, resample threads)."""
-        ch = (c_int32 * 2)()
+        """Pick the launch schedule by timing (cached per shape); returns (particles per lattice CTA,
+        resample threads, lattice nodes per thread)."""
+        ch = (c_int32 * 3)()
         _check(lib().pf_autotune(self.h, ch), self.h)
-        return int(ch[0]), int(ch[1])
+        return int(ch[0]), int(ch[1]), int(ch[2])
+
+    def set_schedule(self, nodes_per_thread: int = 0, particles_per_cta: int = 0, resample_threads: int = 0):
+        """Set the launch schedule explicitly (0: default)."""
+        _check(lib().pf_set_schedule(self.h, nodes_per_thread, particles_per_cta, resample_threads), self.h)
 
     def set_proposal(self, theta, ess_frac: float = 0.1):
         """Learned proposal on (theta: PF_MLP_PARAMS values) or off (None)."""

@@ -46,13 +46,14 @@ def test_autotune_preserves_the_filter(spec_name):
             if tune:
                 x0, l0, e0 = f.get_state(), f.get_logw(), f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)
                 z0 = f.estimate(pf.PF_STAT_LOG_Z, per_filter=True)
-                ppc, threads = f.autotune()
+                ppc, threads, nodes = f.autotune()
                 assert (ppc >= 1 if spec.kind == W.FHN else ppc == 0) and threads in (64, 128, 256)
+                assert nodes in ((2, 4) if spec.kind == W.FHN else (1,))
                 assert f.t == 2
                 assert np.array_equal(f.get_state(), x0) and np.array_equal(f.get_logw(), l0)
                 assert np.array_equal(f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True), e0)
                 assert np.array_equal(f.estimate(pf.PF_STAT_LOG_Z, per_filter=True), z0)
-                assert f.autotune() == (ppc, threads)  # cached per shape
+                assert f.autotune() == (ppc, threads, nodes)  # cached per shape
             for t in range(2, T):
                 f.step(y[t])
             outs.append((f.get_state(), f.get_ancestors(), f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True),
@@ -61,6 +62,33 @@ def test_autotune_preserves_the_filter(spec_name):
     assert np.array_equal(xa, xb) and np.array_equal(aa, ab)
     assert np.allclose(ea, eb, rtol=1e-9, atol=1e-12)
     assert np.allclose(za, zb, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("J", [8, 20, 6])
+def test_lattice_schedules_give_identical_filters(J):
+    """Two or four nodes per thread and any number of particles per CTA: the
+    same particles, log-weights and ancestors bit for bit (the four-node
+    kernel keeps the pair kernel's arithmetic and reduction order)."""
+    spec = W.fhn_lattice(J=J)
+    T = 3
+    _, y = oracle.simulate(spec, T, W.SEED_FHN_OBS)
+    y = y.astype(np.float32)
+    N = W.ragged_counts(4, 30, 300, seed=J)
+    scheds = [(2, 1, 0), (2, 0, 0), (0, 0, 0)] + ([(4, 1, 0), (4, 0, 128)] if J % 4 == 0 else [])
+    outs = []
+    for nodes, ppc, rt in scheds:
+        with pf.EnsembleFilter(spec, len(N), N, 23) as f:
+            f.set_schedule(nodes, ppc, rt)
+            for t in range(T):
+                f.step(y[t])
+            outs.append((f.get_state(), f.get_logw(), f.get_ancestors(),
+                         f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)))
+    for x, l, a, e in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(l, outs[0][1]) and np.array_equal(a, outs[0][2])
+        assert np.allclose(e, outs[0][3], rtol=1e-12, atol=1e-15)
+    if J % 4 != 0:
+        with pf.EnsembleFilter(spec, 1, 10, 1) as f, pytest.raises(pf.PFError):
+            f.set_schedule(4, 0, 0)
 
 
 @pytest.mark.parametrize("proposal", [False, True])
