@@ -52,6 +52,13 @@ FP32_LANES_PER_SM = 128
 #                  + 3 (scalings) = 29, 1.5 pairs per sub-step               -> 43.5
 #   drift 7 + Euler-Maruyama update 6                                      -> 13
 LORENZ_OPS_PER_PARTICLE_STEP = 86.5
+# Algorithmic HBM bytes of the resampling chain per particle (weights: logw;
+# scan: logw again, the 64-bit prefix and the start markers; ancestors: prefix
+# and markers, ancestor index), plus, per state variable, the gather (read and
+# write) and the per-filter means (read).
+RESAMPLE_BYTES_PER_PARTICLE = 4 + (4 + 8 + 4) + (12 + 4)
+RESAMPLE_BYTES_PER_VARIABLE = 4 + 4 + 4
+
 # Algorithmic ALU operations per lattice node-step (one Euler-Maruyama
 # sub-step of one node, both planes): Philox4x32-10 40 per 4 normals -> 20,
 # one Box-Muller pair 29, Laplacian 4 (three adds, one fused -4v), drift of
@@ -320,6 +327,19 @@ def phase_times(torch, wl, reps=5):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
+def resample_roofline(wl, t_res, peaks, peak_src):
+    """HBM roofline of the resampling chain (normaliser, systematic resampling,
+    gather, per-filter means), per context step, on algorithmic bytes."""
+    nf = len(wl.filters)
+    per_ctx = wl.particles / nf
+    bytes_ = per_ctx * (RESAMPLE_BYTES_PER_PARTICLE + wl.spec.dx * RESAMPLE_BYTES_PER_VARIABLE)
+    hbm = float(peaks["hbm_gbs"])
+    achieved = bytes_ / t_res / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "bytes_per_launch": bytes_, "avg_chain_s": t_res, "peak_source": f"{peak_src} copy bandwidth",
+            "note": ("working set below the 129 MB L2 per context" if bytes_ < 129e6 else "larger than L2")}
+
+
 def oracle_case(workload: str, M: int, n_scale: int, T: int, theta=None):
     """A bounded sample of `workload` for the FP64 oracle: (spec, M, N, y, per-filter obs, theta)."""
     import oracle
@@ -537,6 +557,7 @@ def main():
         "gpu_launches": args.steps * nf * wl.kernels_per_filter_step,
         "roofline": roofline,
         "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res},
+        "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src),
     }
     theta = wl.theta
     if wl.N_list is not None:

@@ -26,6 +26,13 @@ multinomial            Alg. 1 step 2b                                 offspring 
 bf_run                 Alg. 1 x M, Def. 1, eq. eqGtN                  LG: converges to the Kalman mean; Lemma 2
                                                                       (E G = Kalman evidence); Thm. 1 bias
                                                                       ~ 1/N; Cor. 2 variance ~ 1/(MN)
+apf_run                auxiliary particle filters (Pitt & Shephard),  LG: converges to the Kalman mean; E G =
+                       the filter of Sec. 5.3; remark after Cor. 2    Kalman evidence (unbiased, as Lemma 2);
+                                                                      Lorenz: same posterior as bf_run
+bf_run_proposal        Alg. 1 step 2a with an importance function     zero network = bf_run bit for bit; p g / q
+                       (remark after Alg. 1; Sec. 6 footnote)         weights keep the bootstrap posterior
+mlp (oracle/mlp.py)    the proposal's network                         finite-difference gradients; BF16 rounding
+                                                                      against its definition
 kalman                 exact filter of the LG case (Sec. 2.2)         joint-Gaussian conditioning of the whole
                                                                       record (a different method)
 simulate               record generator (Sec. 4.2)                    same model code as propagate; obs noise
@@ -265,6 +272,24 @@ def patch_row_c(spec, x: np.ndarray, node: int, y: float) -> np.ndarray:
     lib().orc_patch_row(md.ref, _p(x, ctypes.c_double), ctypes.c_int32(node), ctypes.c_double(y),
                         _p(row, ctypes.c_double))
     return row
+
+
+def apf_run(spec, M: int, N, T: int, obs: np.ndarray, seed: int, est_idx: Optional[Sequence[int]] = None,
+            obs_per_filter: bool = False, threads: int = 0) -> dict:
+    """M independent auxiliary particle filters (Pitt & Shephard) and their average (Def. 1):
+    look-ahead by the noise-free Euler prediction, first-stage systematic resampling,
+    second-stage weights g(y | x) / g(y | mu), weighted estimates."""
+    md = _Model(spec)
+    N = np.ascontiguousarray(np.broadcast_to(np.asarray(N, dtype=np.int32), (M,)), dtype=np.int32)
+    est_idx = np.ascontiguousarray(range(spec.dx) if est_idx is None else est_idx, dtype=np.int32)
+    ne = len(est_idx)
+    obs = np.ascontiguousarray(obs, dtype=np.float64)
+    est, logG, ess, ens = np.empty((T, M, ne)), np.empty((T, M)), np.empty((T, M)), np.empty((T, ne))
+    lib().orc_apf_run(md.ref, ctypes.c_int32(M), _p(N, ctypes.c_int32), ctypes.c_int32(T), _p(obs, ctypes.c_double),
+                      ctypes.c_int32(1 if obs_per_filter else 0), ctypes.c_uint64(seed), ctypes.c_int32(ne),
+                      _p(est_idx, ctypes.c_int32), _p(est, ctypes.c_double), _p(logG, ctypes.c_double),
+                      _p(ess, ctypes.c_double), _p(ens, ctypes.c_double), ctypes.c_int32(threads))
+    return dict(est=est, log_G=logG, ess=ess, ens=ens)
 
 
 def bf_run_proposal(spec, theta, M: int, N, T: int, obs: np.ndarray, seed: int, est_idx=None, bf16: bool = True,

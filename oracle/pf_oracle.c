@@ -717,3 +717,105 @@ int orc_bf_run_proposal(const orc_model *md, const orc_proposal *pr, int32_t M, 
     free(off);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Ensemble of auxiliary particle filters (Pitt & Shephard 1999), the filter  */
+/* the paper runs on its lattice (Sec. 5.3; the remark after Corollary 2      */
+/* extends the analysis to it).  Per filter and observation t:                */
+/*   mu_i  = the noise-free Euler prediction of particle i over interval t;  */
+/*   first stage: a = systematic resampling with weights                      */
+/*          lambda_i = W_{t-1,i} g_t(mu_i)  (W: second-stage weights of t-1); */
+/*   x_i   = the transition from x_{t-1,a_i} (the filter's own noise, the same*/
+/*           counters as the bootstrap filter's particle i at step t);        */
+/*   second stage: w_i = g_t(x_i) / g_t(mu_{a_i});                            */
+/*   estimate (f, pi_t) = sum_i w_i f(x_i) / sum_i w_i;                       */
+/*   likelihood factor (unbiased): [sum_i W_{t-1,i} lambda_i]                 */
+/*                      x [(1/N) sum_i w_i]  with W_{t-1} normalised, W_0 = 1/N.*/
+/* est[T][M][n_est], log_G[T][M] (running), ess[T][M] (second stage),        */
+/* ens[T][n_est] (Definition 1).                                              */
+/* ------------------------------------------------------------------------- */
+static void predict_one(const orc_model *md, int32_t t, double *x, double *f)
+{
+    for (int k = 0; k < md->K; ++k) {
+        int64_t n = (int64_t)(t - 1) * md->K + k + 1;
+        drift(md, n, x, f);
+        for (int v = 0; v < md->dx; ++v) x[v] = x[v] + md->dt * f[v];
+    }
+}
+
+int orc_apf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, const double *obs,
+                int32_t obs_per_filter, uint64_t seed, int32_t n_est, const int32_t *est_idx, double *est,
+                double *log_G, double *ess, double *ens, int32_t n_threads)
+{
+    int dx = md->dx;
+    const double log_const = -0.5 * md->dy * log(2.0 * M_PI * md->sigma_obs * md->sigma_obs);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int m = 0; m < M; ++m) {
+        int64_t Nm = N[m];
+        double *x = (double *)malloc(sizeof(double) * Nm * dx);
+        double *xn = (double *)malloc(sizeof(double) * Nm * dx);
+        double *mu = (double *)malloc(sizeof(double) * dx);
+        double *la = (double *)malloc(sizeof(double) * Nm);
+        double *l1 = (double *)malloc(sizeof(double) * Nm);
+        double *lw2 = (double *)malloc(sizeof(double) * Nm);
+        double *w = (double *)malloc(sizeof(double) * Nm);
+        int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * Nm);
+        double *z = (double *)malloc(sizeof(double) * dx);
+        double *f = (double *)malloc(sizeof(double) * dx);
+        double lg = 0.0, lse2_prev = log((double)Nm);
+        for (int64_t i = 0; i < Nm; ++i) {
+            prior_one(md, seed, ORC_STREAM_INIT, (uint32_t)i, (uint32_t)m, x + i * dx);
+            lw2[i] = 0.0;
+        }
+        for (int32_t t = 1; t <= T; ++t) {
+            const double *y = obs_per_filter ? obs + ((int64_t)(t - 1) * M + m) * md->dy
+                                             : obs + (int64_t)(t - 1) * md->dy;
+            /* first stage: look-ahead weights and resampling */
+            for (int64_t i = 0; i < Nm; ++i) {
+                memcpy(mu, x + i * dx, sizeof(double) * dx);
+                predict_one(md, t, mu, f);
+                la[i] = loglik(md, mu, y);
+                l1[i] = lw2[i] + la[i];
+            }
+            double n1[5];
+            orc_normalise(Nm, l1, n1);
+            for (int64_t i = 0; i < Nm; ++i) w[i] = exp(l1[i] - n1[0]);
+            orc_systematic(Nm, w, orc_resample_u(seed, m, t), anc);
+            /* second stage: propagate the selected particles, weight */
+            for (int64_t i = 0; i < Nm; ++i) {
+                memcpy(xn + i * dx, x + (int64_t)anc[i] * dx, sizeof(double) * dx);
+                propagate_one(md, seed, ORC_STREAM_DYN, (uint32_t)i, (uint32_t)m, t, xn + i * dx, z, f);
+            }
+            for (int64_t i = 0; i < Nm; ++i) l1[i] = loglik(md, xn + i * dx, y) - la[anc[i]];
+            memcpy(lw2, l1, sizeof(double) * Nm);
+            double *tmp = x; x = xn; xn = tmp;
+            double n2[5];
+            orc_normalise(Nm, lw2, n2);
+            lg += (n1[1] - lse2_prev) + (n2[1] - log((double)Nm)) + log_const;
+            lse2_prev = n2[1];
+            int64_t row = (int64_t)(t - 1) * M + m;
+            if (log_G) log_G[row] = lg;
+            if (ess) ess[row] = n2[4];
+            if (est) {
+                for (int e = 0; e < n_est; ++e) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < Nm; ++i) s += exp(lw2[i] - n2[0]) * x[i * dx + est_idx[e]];
+                    est[row * n_est + e] = s / n2[2];
+                }
+            }
+        }
+        free(x); free(xn); free(mu); free(la); free(l1); free(lw2); free(w); free(anc); free(z); free(f);
+    }
+    if (ens && est) {
+        for (int32_t t = 0; t < T; ++t)
+            for (int e = 0; e < n_est; ++e) {
+                double s = 0.0;
+                for (int m = 0; m < M; ++m) s += est[((int64_t)t * M + m) * n_est + e];
+                ens[(int64_t)t * n_est + e] = s / (double)M;
+            }
+    }
+    return 0;
+}

@@ -2,20 +2,22 @@
 // fifth-generation tensor cores, fused with the construction of its input
 // rows from the lattice state.
 //
-// One CTA of 128 threads, persistent over tiles of 128 network rows (one row
-// per (particle, observed node)); two CTAs per SM (shared memory bounds it).
+// One CTA of 256 threads (two warpgroups), persistent over tiles of 128
+// network rows (one row per (particle, observed node)); two CTAs per SM
+// (shared memory bounds it).  Thread t works on row t % 128, half t / 128.
 // Per tile:
-//   rows     every thread gathers its row (5x5 patches of v and w, mirrored at
-//            the edges, then y at the node) from the particle's state, rounds
-//            it to BF16 and stores it as the A operand in shared memory;
+//   rows     every thread gathers its half of its row (columns 0..31: the v
+//            patch and the first w values; 32..63: the rest of the w patch and
+//            y; 5x5 patches mirrored at the edges) from the particle's state,
+//            rounds it to BF16 and stores it as the A operand in shared memory;
 //   layer 1  one thread issues 4 tcgen05.mma (M 128, N 128, K 16) into tensor
 //            memory (TMEM columns 0..127), commit -> mbarrier;
-//   GELU     every thread loads its row of the accumulator (tcgen05.ld, warp w
-//            owns TMEM lanes 32w..32w+31), adds the bias, applies GELU and
-//            stores BF16 as the next A operand;
+//   GELU     every thread loads its half of its row of the accumulator
+//            (tcgen05.ld; warp w reaches TMEM lanes 32 (w % 4) .. + 31), adds
+//            the bias, applies GELU and stores BF16 as the next A operand;
 //   layer 2  8 MMAs into TMEM columns 128..255, GELU again;
 //   layer 3  8 MMAs with N 16 (W3 zero-padded from 4 to 16 rows) into
-//            columns 0..15; each thread writes its 4 outputs + bias (FP32).
+//            columns 0..15; the first warpgroup writes the 4 outputs + bias.
 // Operands are K-major without swizzle: element (r, k) of a tile with K
 // columns sits at (r / 8) (K / 8) 128 + (k / 8) 128 + (r % 8) 16 + (k % 8) 2
 // bytes (8 x 16-byte core matrices; K-direction stride 128 B, row-group
@@ -37,7 +39,7 @@ namespace pf {
 namespace tc {
 
 constexpr int kRows = 128;
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kOffW1 = 0;                            // 128 x 64
 constexpr uint32_t kOffW2 = kOffW1 + 128 * 64 * 2;        // 128 x 128
@@ -218,7 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const int row = tid & (kRows - 1), half = tid >> 7;
 
     const uint32_t sbase = smem_u32(smem);
     const uint32_t id128 = idesc_bf16(128, 128), id16 = idesc_bf16(128, 16);
@@ -226,35 +229,42 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool expired = false;
     const int nn = J * J;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // ---- input rows -> A
+        // ---- input rows -> A (half 0: columns 0..31, half 1: columns 32..63)
         {
-            const int64_t g = tile * kRows + tid;
-            uint32_t w[32];
+            const int64_t g = tile * kRows + row;
+            uint32_t w[16];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) w[i] = 0u;
+            for (int i = 0; i < 16; ++i) w[i] = 0u;
             if (g < R) {
                 const int64_t p = g / dy;
                 const int j = (int)(g - p * dy);
                 const int nd = obs_idx[j], ri = nd / J, ci = nd - ri * J;
                 const float *xp = x + p * (int64_t)dx;
-                float vals[51];
-                int q = 0;
+                float vals[32];
+                if (half == 0) {  // v patch (25) and w patch elements 0..6
 #pragma unroll
-                for (int di = -2; di <= 2; ++di)
-#pragma unroll
-                    for (int dj = -2; dj <= 2; ++dj, ++q) {
-                        const int k = mirror_index(ri + di, J) * J + mirror_index(ci + dj, J);
-                        vals[q] = xp[k];
-                        vals[25 + q] = xp[nn + k];
+                    for (int q = 0; q < 32; ++q) {
+                        const int e = q < 25 ? q : q - 25;
+                        const int k = mirror_index(ri + e / 5 - 2, J) * J + mirror_index(ci + e % 5 - 2, J);
+                        vals[q] = xp[(q < 25 ? 0 : nn) + k];
                     }
-                vals[50] = obs[(obs_stride ? (int64_t)pfilt[p] * obs_stride : 0) + j];
+                } else {  // w patch elements 7..24, y, zeros
 #pragma unroll
-                for (int i = 0; i < 25; ++i) w[i] = mlp::pack_bf16(vals[2 * i], vals[2 * i + 1]);
-                w[25] = mlp::pack_bf16(vals[50], 0.0f);
+                    for (int q = 0; q < 18; ++q) {
+                        const int e = q + 7;
+                        const int k = mirror_index(ri + e / 5 - 2, J) * J + mirror_index(ci + e % 5 - 2, J);
+                        vals[q] = xp[nn + k];
+                    }
+                    vals[18] = obs[(obs_stride ? (int64_t)pfilt[p] * obs_stride : 0) + j];
+#pragma unroll
+                    for (int q = 19; q < 32; ++q) vals[q] = 0.0f;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) w[i] = mlp::pack_bf16(vals[2 * i], vals[2 * i + 1]);
             }
 #pragma unroll
-            for (int kg = 0; kg < 8; ++kg)
-                *reinterpret_cast<uint4 *>(smem + kOffA + cm_off(tid, kg, 64)) =
+            for (int kg = 0; kg < 4; ++kg)
+                *reinterpret_cast<uint4 *>(smem + kOffA + cm_off(row, 4 * half + kg, 64)) =
                     make_uint4(w[4 * kg], w[4 * kg + 1], w[4 * kg + 2], w[4 * kg + 3]);
         }
         fence_proxy_async();
@@ -274,11 +284,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (__syncthreads_or(!ok)) { expired = true; break; }
         tc_fence_after();
 #pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 32) {
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             uint32_t v[32];
             tmem_ld32(lane_base + c0, v);
             tc_wait_ld();
-            gelu_store(v, bias, c0, tid, smem + kOffH);
+            gelu_store(v, bias, c0, row, smem + kOffH);
         }
         fence_proxy_async();
         tc_fence_before();
@@ -297,11 +307,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (__syncthreads_or(!ok)) { expired = true; break; }
         tc_fence_after();
 #pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 32) {
+        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             uint32_t v[32];
             tmem_ld32(lane_base + 128 + c0, v);
             tc_wait_ld();
-            gelu_store(v, bias + 128, c0, tid, smem + kOffH);
+            gelu_store(v, bias + 128, c0, row, smem + kOffH);
         }
         fence_proxy_async();
         tc_fence_before();
@@ -319,11 +329,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         phase ^= 1u;
         if (__syncthreads_or(!ok)) { expired = true; break; }
         tc_fence_after();
-        {
+        if (half == 0) {
             uint32_t v[4];
             tmem_ld4(lane_base, v);
             tc_wait_ld();
-            const int64_t g = tile * kRows + tid;
+            const int64_t g = tile * kRows + row;
             if (g < R)
                 reinterpret_cast<float4 *>(out)[g] =
                     make_float4(__uint_as_float(v[0]) + bias[256], __uint_as_float(v[1]) + bias[257],

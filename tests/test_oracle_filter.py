@@ -219,3 +219,48 @@ def test_theorem1_bias_rate_and_corollary_variance_rates():
     # Corollary 1: Var ~ c / N
     slope_v = np.polyfit(np.log(Ns), np.log(var), 1)[0]
     assert -1.1 < slope_v < -0.9, slope_v
+
+
+# ------------------------------------------------------------ auxiliary particle filters
+def test_apf_ensemble_converges_to_kalman_mean():
+    """The ensemble of auxiliary particle filters estimates the same posterior
+    (linear-Gaussian model: the Kalman filter)."""
+    spec = W.linear_gaussian()
+    T = 10
+    _, y = oracle.simulate(spec, T, seed=W.SEED_LORENZ_OBS)
+    m, _, _ = oracle.kalman(spec, y)
+    M, N = 64, 1024
+    r = oracle.apf_run(spec, M, N, T, y, seed=6)
+    est = r["est"]
+    se = est.std(axis=1, ddof=1) / math.sqrt(M)
+    assert np.all(np.abs(r["ens"] - m) < 4.5 * se + 2e-3)
+    assert np.allclose(r["ens"], est.mean(axis=1), rtol=0, atol=1e-13)
+
+
+def test_apf_unbiased_evidence():
+    """The auxiliary filter's likelihood estimate (first-stage sum times the
+    mean second-stage weight) is unbiased, like the bootstrap filter's (the
+    remark after Corollary 2 extends Lemma 2 to it): E exp(log G) equals the
+    Kalman evidence at every t."""
+    spec = W.linear_gaussian(**SCALAR)
+    _, _, ll = oracle.kalman(spec, Y_SCALAR)
+    M = 1 << 16
+    for N in (4, 32):
+        r = oracle.apf_run(spec, M, N, 2, Y_SCALAR, seed=200 + N)
+        for t in range(2):
+            ratio = np.exp(r["log_G"][t] - ll[t])
+            assert abs(ratio.mean() - 1.0) < 4.5 * ratio.std() / math.sqrt(M), (N, t)
+
+
+def test_apf_and_bootstrap_agree_on_lorenz():
+    """Both filters target the same posterior: on Lorenz 63 the ensemble means
+    of x2 agree within the statistical tolerance."""
+    spec = W.lorenz63()
+    T = 20
+    _, y = oracle.simulate(spec, T, W.SEED_LORENZ_OBS)
+    M, N = 64, 512
+    a = oracle.apf_run(spec, M, N, T, y, seed=31, est_idx=[1])["est"][:, :, 0]
+    b = oracle.bf_run(spec, M, N, T, y, seed=32, est_idx=[1])["est"][:, :, 0]
+    for t in (4, 9, 19):
+        se = math.sqrt(a[t].var(ddof=1) / M + b[t].var(ddof=1) / M)
+        assert abs(a[t].mean() - b[t].mean()) < 4.5 * se, (t, a[t].mean(), b[t].mean(), se)
