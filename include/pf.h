@@ -202,6 +202,23 @@ PF_API pf_status pf_estimate(pf_ctx *ctx, const pf_stat *stat, double *out);
  * PF_ENOMEM, PF_ECUDA. */
 PF_API pf_status pf_autotune(pf_ctx *ctx, int32_t *h_choice);
 
+/* Switches the context between the bootstrap filter (on = 0, the default) and
+ * the auxiliary particle filter of Pitt & Shephard (on = 1), the filter the
+ * paper runs on its lattice (Sec. 5.3; the remark after Corollary 2 extends
+ * the analysis to it).  Per observation t each filter then: predicts every
+ * particle without noise over the K sub-steps (mu); resamples (systematic,
+ * exact) with weights W_{t-1} g_t(mu); propagates the selected particles with
+ * the transition; weights them by g_t(x) / g_t(mu_ancestor).  PF_STAT_MEAN is
+ * then the weighted mean, PF_STAT_ESS the ESS of the second-stage weights, and
+ * PF_STAT_LOG_EVIDENCE accumulates the unbiased estimate [sum W g(mu)] x
+ * [(1/N) sum w].  pf_get_logw returns the second-stage log-weights; switching
+ * on or pf_set_state makes them uniform.  Steps go through pf_step /
+ * pf_step_device only (pf_propagate, pf_resample and pf_set_logw return
+ * PF_EUNSUPPORTED), and the mode is not combined with the learned proposal
+ * or tuple recording.  Synchronises.
+ * Errors: PF_ESTATE, PF_EUNSUPPORTED, PF_ENOMEM. */
+PF_API pf_status pf_set_auxiliary(pf_ctx *ctx, int32_t on);
+
 /* Sets the launch schedule explicitly (0 in any field: the default):
  * nodes_per_thread 2 or 4 for the lattice kernels (4 needs J % 4 == 0),
  * particles_per_cta >= 1 for the lattice (clamped to what fits in 1024

@@ -377,11 +377,15 @@ __global__ void __launch_bounds__(256) k_init_fhn(ModelParams mp, Key key, const
 // thread past the sub-tile's end repeats its last particle and stores nothing.
 constexpr int kPropThreads = kSubTile / 2;
 
-template <int D>
+// Mode 0: the bootstrap filter.  Mode 1: the auxiliary filter's look-ahead
+// (noise-free Euler prediction mu, nothing stored but la_out = log g(y | mu)
+// and logw = lw_prev + la_out).  Mode 2: its second stage (logw = log g(y | x)
+// - la_src[off + anc]).
+template <int D, int Mode>
 __global__ void __launch_bounds__(kPropThreads, 16)
     k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *__restrict__ x_in,
                       float *__restrict__ x_out, int64_t P, float *logw, int32_t *fmax_key, const float *obs,
-                      int32_t obs_stride, const int32_t *d_t)
+                      int32_t obs_stride, const int32_t *d_t, AuxPtrs aux)
 {
     __shared__ float sh[kPropThreads / 32];
     const TileDesc st = subs[blockIdx.x];
@@ -398,15 +402,23 @@ __global__ void __launch_bounds__(kPropThreads, 16)
 #pragma unroll
         for (int v = 0; v < D; ++v) xs[r][v] = x_in[v * P + p];
     }
-    propagate_small_n<D, 2, float>(mp, key, kStreamDyn, c0, t, (uint32_t)st.m, xs);
+    propagate_small_n<D, 2, float, Mode != 1>(mp, key, kStreamDyn, c0, t, (uint32_t)st.m, xs);
     float l = -INFINITY;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         if ((int)threadIdx.x + r * kPropThreads < st.len) {
             const int64_t p = st.gstart + j[r];
+            if (Mode != 1) {
 #pragma unroll
-            for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[r][v];
-            const float lr = loglik_small<D, float>(mp, y, xs[r]);
+                for (int v = 0; v < D; ++v) x_out[v * P + p] = xs[r][v];
+            }
+            float lr = loglik_small<D, float>(mp, y, xs[r]);
+            if (Mode == 1) {
+                aux.la_out[p] = lr;
+                lr = aux.lw_prev[p] + lr;
+            } else if (Mode == 2) {
+                lr -= aux.la_src[(st.gstart - st.lstart) + aux.anc[p]];
+            }
             logw[p] = lr;
             l = fmaxf(l, lr < INFINITY ? lr : -INFINITY);  // NaN never wins
         }
@@ -428,7 +440,8 @@ __global__ void __launch_bounds__(1024, 2)
     k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const int32_t *pfilt, const FilterDesc *filt,
                     const Real *__restrict__ x_in, Real *__restrict__ x_out, int64_t P, float *logw, const float *obs,
                     int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t fixed_c0,
-                    int32_t fixed_c2, int32_t t_direct, int32_t ppc, int32_t *fmax_key, int32_t n_steps)
+                    int32_t fixed_c2, int32_t t_direct, int32_t ppc, int32_t *fmax_key, int32_t n_steps,
+                    AuxPtrs aux, int32_t noise)
 {
     using Pair = typename std::conditional<std::is_same<Real, float>::value, float2, double2>::type;
     extern __shared__ unsigned char smem_raw[];
@@ -482,8 +495,8 @@ __global__ void __launch_bounds__(1024, 2)
         }
         __syncthreads();
         if (active) {
-            Real z[4];
-            normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
+            Real z[4] = {(Real)0, (Real)0, (Real)0, (Real)0};
+            if (noise) normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
             const Pair up = buf[qu], dn = buf[qd], lf = buf[ql], rt = buf[qr];
             const Real left = has_left ? lf.y : v0, right = has_right ? rt.x : v1;
             Real l0, l1;
@@ -498,7 +511,7 @@ __global__ void __launch_bounds__(1024, 2)
             w1 = em_update(w1, fw1, z[3], dt, sq);
         }
     }
-    if (active) {
+    if (active && x_out) {
         Real *xo = x_out + p * (int64_t)mp.dx;
         xo[n0] = v0;
         xo[n0 + 1] = v1;
@@ -527,7 +540,13 @@ __global__ void __launch_bounds__(1024, 2)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0 && pp < P) {
-            const float l = mp.fhalf_prec * acc;
+            float l = mp.fhalf_prec * acc;
+            if (aux.la_out) {  // auxiliary look-ahead
+                aux.la_out[pp] = l;
+                l = aux.lw_prev[pp] + l;
+            } else if (aux.la_src) {  // auxiliary second stage
+                l -= aux.la_src[filt[pfilt[pp]].off + aux.anc[pp]];
+            }
             logw[pp] = l;
             if (l > -INFINITY && l < INFINITY) atomicMax(&fmax_key[pfilt[pp]], float_order_key(l));
         }
@@ -548,7 +567,7 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
     k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
                      const float *__restrict__ x_in, float *__restrict__ x_out, int64_t P, float *logw,
                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
-                     int32_t *fmax_key, int32_t n_steps)
+                     int32_t *fmax_key, int32_t n_steps, AuxPtrs aux, int32_t noise)
 {
     extern __shared__ unsigned char smem_raw[];
     const int J = mp.J, nn = J * J, quads = nn / 4, pairs = nn / 2, qrow = J / 4;
@@ -586,10 +605,12 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
         if (active) buf[q] = make_float4(v[0], v[1], v[2], v[3]);
         __syncthreads();
         if (active) {
-            float z[8];
+            float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const uint32_t bk = (uint32_t)k * blocks_per_step + 2u * (uint32_t)q;
-            normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
-            normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+            if (noise) {
+                normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
+                normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+            }
             const float4 up = buf[qu], dn = buf[qd];
             const float left = has_left ? buf[ql].w : v[0], right = has_right ? buf[qr].x : v[3];
             float l[4];
@@ -605,7 +626,7 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
             }
         }
     }
-    if (active) {
+    if (active && x_out) {
         *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + n0) = make_float4(v[0], v[1], v[2], v[3]);
         *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + nn + n0) = make_float4(w[0], w[1], w[2], w[3]);
     }
@@ -639,7 +660,13 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0 && pp < P) {
-            const float lv = mp.fhalf_prec * acc;
+            float lv = mp.fhalf_prec * acc;
+            if (aux.la_out) {
+                aux.la_out[pp] = lv;
+                lv = aux.lw_prev[pp] + lv;
+            } else if (aux.la_src) {
+                lv -= aux.la_src[filt[pfilt[pp]].off + aux.anc[pp]];
+            }
             logw[pp] = lv;
             if (lv > -INFINITY && lv < INFINITY) atomicMax(&fmax_key[pfilt[pp]], float_order_key(lv));
         }
@@ -931,14 +958,23 @@ __global__ void __launch_bounds__(256) k_gather_rows(const int32_t *__restrict__
 // reset by that CTA) adds the partials in chunk order in FP64: deterministic,
 // and parallel over particles, so one filter of many particles is as fast as
 // many small ones.
+__device__ __forceinline__ float aux_weight(float l, float mx)
+{
+    return (mx > -INFINITY && l > -INFINITY && l < INFINITY) ? expf(l - mx) : 0.0f;  // NaN weighs nothing
+}
+
 __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const TileDesc *__restrict__ chunks,
                                                    const float *__restrict__ x, int dx, double *part, int32_t *cnt,
-                                                   double *est)
+                                                   double *est, const float *__restrict__ lw2,
+                                                   const int32_t *__restrict__ fmax2, const double *fstats)
 {
     __shared__ int last;
     const TileDesc ch = chunks[blockIdx.x];
     const FilterDesc fd = filt[ch.m];
     const int v = blockIdx.y * blockDim.x + threadIdx.x;
+    // auxiliary filter: weighted by exp(lw2 - max), divided by the filter's sum of those weights
+    const float mx = lw2 ? float_from_order_key(fmax2[ch.m]) : 0.0f;
+    const double denom = lw2 ? fstats[(int64_t)ch.m * kFsCount + kFsSumW] : (double)fd.N;
     double mine = 0.0;
     if (v < dx) {
         const float *base = x + ch.gstart * (int64_t)dx + v;
@@ -948,14 +984,19 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
             float r[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) r[k] = base[(int64_t)(i + k) * dx];
+            if (lw2) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) r[k] *= aux_weight(lw2[ch.gstart + i + k], mx);
+            }
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc = ff_add(acc, r[k]);
         }
-        for (; i < ch.len; ++i) acc = ff_add(acc, base[(int64_t)i * dx]);
+        for (; i < ch.len; ++i)
+            acc = ff_add(acc, base[(int64_t)i * dx] * (lw2 ? aux_weight(lw2[ch.gstart + i], mx) : 1.0f));
         mine = ff_to_double(acc);
     }
     if (fd.mc_count == 1) {  // the whole filter in this chunk (uniform over the CTA)
-        if (v < dx) est[(int64_t)ch.m * dx + v] = mine / (double)fd.N;
+        if (v < dx) est[(int64_t)ch.m * dx + v] = mine / denom;
         return;
     }
     if (v < dx) part[(int64_t)blockIdx.x * dx + v] = mine;
@@ -971,7 +1012,82 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
         __threadfence();
         double s = 0.0;
         for (int k = 0; k < fd.mc_count; ++k) s += __ldcg(&part[(int64_t)(fd.mc_begin + k) * dx + v]);
-        est[(int64_t)ch.m * dx + v] = s / (double)fd.N;
+        est[(int64_t)ch.m * dx + v] = s / denom;
+    }
+}
+
+// Second stage of the auxiliary particle filter, per filter: from the
+// second-stage log-weights lw2 and their maximum (order keys), sum w and
+// sum w^2 (ESS), log sum w (log G_t gains lse2_t - lse2_{t-1}: the first-stage
+// factor sum W lambda with W normalised, times the mean second-stage weight),
+// and for the small models the weighted means of the D variables.  Tile
+// partials in compensated FP32 pairs, FP64 across tiles, combined in tile order
+// by the filter's last tile (completion counter kept at 0 between steps).
+template <int D>
+__global__ void __launch_bounds__(kResampleThreads)
+    k_weight_stats(const TileDesc *tiles, const FilterDesc *filt, const float *__restrict__ lw2,
+                   const int32_t *__restrict__ fmax2, const float *__restrict__ x, int64_t P, double *tile_sums,
+                   double *tile_est, int32_t *done, double *fstats, double *est, int32_t *err)
+{
+    constexpr int NV = D + 2;  // w, w^2, w x_v
+    __shared__ double shd[kResampleThreads * NV + 2 * NV * 32];
+    __shared__ int last;
+    const TileDesc td = tiles[blockIdx.x];
+    const FilterDesc fd = filt[td.m];
+    const float mx = float_from_order_key(fmax2[td.m]);
+    FF f[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) f[i] = FF{0.0f, 0.0f};
+    for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
+        const int64_t p = td.gstart + j;
+        const float w = aux_weight(lw2[p], mx);
+        f[0] = ff_add(f[0], w);
+        f[1] = ff_add(f[1], w * w);
+#pragma unroll
+        for (int v = 0; v < D; ++v) f[2 + v] = ff_add(f[2 + v], w * x[v * P + p]);
+    }
+    double s[NV];
+    block_sum_ff<NV>(f, s, shd);
+    if (fd.tile_count > 1) {
+        if (threadIdx.x == 0) {
+            tile_sums[(int64_t)blockIdx.x * kTsCount + kTsW] = s[0];
+            tile_sums[(int64_t)blockIdx.x * kTsCount + kTsW2] = s[1];
+#pragma unroll
+            for (int v = 0; v < D; ++v) tile_est[(int64_t)blockIdx.x * D + v] = s[2 + v];
+            __threadfence();
+            last = (atomicAdd(&done[td.m], 1) == fd.tile_count - 1);
+        }
+        __syncthreads();
+        if (!last) return;
+        double part[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) part[i] = 0.0;
+        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) {
+            const int64_t b = fd.tile_begin + j;
+            part[0] += __ldcg(&tile_sums[b * kTsCount + kTsW]);
+            part[1] += __ldcg(&tile_sums[b * kTsCount + kTsW2]);
+#pragma unroll
+            for (int v = 0; v < D; ++v) part[2 + v] += __ldcg(&tile_est[b * D + v]);
+        }
+        block_sum_dd<NV>(part, shd);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) s[i] = part[i];
+        if (threadIdx.x == 0) done[td.m] = 0;
+    }
+    if (threadIdx.x == 0) {
+        double *fs = fstats + (int64_t)td.m * kFsCount;
+        const double sw = s[0];
+        if (!(sw > 0.0)) {
+            atomicOr(&err[0], kErrDegenerate);
+            atomicCAS(&err[1], -1, td.m);
+        }
+        const double lse2 = (double)mx + log(sw);
+        fs[kFsEss] = sw * sw / s[1];
+        fs[kFsLogG] += lse2 - fs[kFsLse2];
+        fs[kFsLse2] = lse2;
+        fs[kFsSumW] = sw;
+#pragma unroll
+        for (int v = 0; v < D; ++v) est[(int64_t)td.m * D + v] = s[2 + v] / sw;
     }
 }
 
@@ -1109,8 +1225,8 @@ template <int D>
 cudaError_t propagate_small_launch(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                                    cudaStream_t s)
 {
-    k_propagate_small<D><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs,
-                                                       stride, c.d_t);
+    k_propagate_small<D, 0><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key,
+                                                              d_obs, stride, c.d_t, AuxPtrs{});
     return cudaGetLastError();
 }
 
@@ -1157,8 +1273,11 @@ cudaError_t launch_init(const Ctx &c, cudaStream_t s)
 // n_steps lattice sub-steps of every particle, xi -> xo, with the weights and
 // per-filter maxima when `weigh` (the pair or the four-node kernel).
 cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
-                                int32_t n_steps, bool weigh, cudaStream_t s)
+                                int32_t n_steps, bool weigh, cudaStream_t s, float *logw = nullptr,
+                                int32_t *fmax = nullptr, AuxPtrs aux = AuxPtrs{}, int32_t noise = 1)
 {
+    if (!logw) logw = c.logw;
+    if (!fmax) fmax = c.fmax_key;
     const int nodes = fhn_nodes(c);
     int ppc;
     const int threads = fhn_threads(c.mp, &ppc, c.fhn_ppc, nodes);
@@ -1173,13 +1292,13 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
         carveout_set = true;
     }
     if (nodes == 4)
-        k_propagate_fhn4<<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, weigh ? c.logw : nullptr,
-                                                     d_obs, stride, c.obs_slot, c.d_t, ppc,
-                                                     weigh ? c.fmax_key : nullptr, n_steps);
+        k_propagate_fhn4<<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, weigh ? logw : nullptr,
+                                                     d_obs, stride, c.obs_slot, c.d_t, ppc, weigh ? fmax : nullptr,
+                                                     n_steps, aux, noise);
     else
         k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
-                                                           weigh ? c.logw : nullptr, d_obs, stride, c.obs_slot, c.d_t,
-                                                           0, 0, 0, ppc, weigh ? c.fmax_key : nullptr, n_steps);
+                                                           weigh ? logw : nullptr, d_obs, stride, c.obs_slot, c.d_t,
+                                                           0, 0, 0, ppc, weigh ? fmax : nullptr, n_steps, aux, noise);
     return cudaGetLastError();
 }
 
@@ -1212,6 +1331,66 @@ cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// One step of the ensemble of auxiliary particle filters: look-ahead weights
+// (noise-free prediction), first-stage systematic resampling and gather, the
+// second-stage propagation and weights, weighted estimates, the M-average.
+template <int D>
+cudaError_t apf_small(const Ctx &c, const ResampleArgs &a, const float *d_obs, int32_t stride, const float *x, float *xn,
+                      cudaStream_t s)
+{
+    const int th = c.resample_threads;
+    k_propagate_small<D, 1><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, x, nullptr, c.P, c.logw,
+                                                              c.fmax_key, d_obs, stride, c.d_t,
+                                                              AuxPtrs{c.lw2, c.la, nullptr, nullptr});
+    k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
+    k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
+    k_ancestors_small<D><<<c.n_tiles, th, 0, s>>>(a, x, xn, c.P, c.tile_est, c.est);
+    k_propagate_small<D, 2><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xn, xn, c.P, c.lw2, c.fmax2, d_obs,
+                                                              stride, c.d_t, AuxPtrs{nullptr, nullptr, c.la, c.anc});
+    k_weight_stats<D><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, xn, c.P, c.tile_sums, c.tile_est,
+                                               c.done, c.fstats, c.est, c.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cudaStream_t s)
+{
+    const ResampleArgs a = ctx_args(c);
+    const int dx = c.mp.dx, th = c.resample_threads;
+    const float *x = c.x[c.cur];
+    float *xn = c.x[c.cur ^ 1];
+    k_fill_i32<<<(c.M + 255) / 256, 256, 0, s>>>(c.fmax2, c.M, kNegInfKey);
+    cudaError_t e = cudaSuccess;
+    if (c.mp.kind == kFhnLattice) {
+        e = launch_fhn_interval(c, d_obs, stride, x, nullptr, c.mp.K, true, s, c.logw, c.fmax_key,
+                                AuxPtrs{c.lw2, c.la, nullptr, nullptr}, 0);
+        if (e != cudaSuccess) return e;
+        k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
+        k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
+        k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
+        k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(x),
+                                                   reinterpret_cast<float4 *>(xn), dx / 4);
+        e = launch_fhn_interval(c, d_obs, stride, xn, xn, c.mp.K, true, s, c.lw2, c.fmax2,
+                                AuxPtrs{nullptr, nullptr, c.la, c.anc}, 1);
+        if (e != cudaSuccess) return e;
+        k_weight_stats<0><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, nullptr, c.P, c.tile_sums, nullptr,
+                                                   c.done, c.fstats, c.est, c.err);
+        dim3 g(c.n_mchunks, (dx + 255) / 256);
+        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, c.lw2, c.fmax2,
+                                      c.fstats);
+    } else {
+        switch (dx) {
+        case 1: e = apf_small<1>(c, a, d_obs, stride, x, xn, s); break;
+        case 2: e = apf_small<2>(c, a, d_obs, stride, x, xn, s); break;
+        case 3: e = apf_small<3>(c, a, d_obs, stride, x, xn, s); break;
+        case 4: e = apf_small<4>(c, a, d_obs, stride, x, xn, s); break;
+        default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    k_ensemble<<<dx, 128, 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream_t s)
 {
     const ResampleArgs a = ctx_args(c);
@@ -1223,7 +1402,8 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
                                                    reinterpret_cast<float4 *>(xo), dx / 4);
         dim3 g(c.n_mchunks, (dx + 255) / 256);
-        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xo, dx, c.mean_part, c.mean_cnt, c.est);
+        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xo, dx, c.mean_part, c.mean_cnt, c.est, nullptr, nullptr,
+                                      nullptr);
     } else {
         switch (dx) {
         case 1: k_ancestors_small<1><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
@@ -1284,7 +1464,8 @@ cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int
         const double *xi = d_x + (int64_t)(t - 1) * mp.dx;
         double *xo = d_x + (int64_t)t * mp.dx;
         k_propagate_fhn<double><<<1, threads, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1, nullptr,
-                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1, nullptr, mp.K);
+                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1, nullptr, mp.K,
+                                                         AuxPtrs{}, 1);
         if (d_y)
             k_observe<<<(mp.dy + 255) / 256, 256, 0, s>>>(mp, key, d_obs_idx, t, record, xo,
                                                           d_y + (int64_t)(t - 1) * mp.dy);

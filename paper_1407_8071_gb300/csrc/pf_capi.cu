@@ -129,9 +129,25 @@ cudaError_t enqueue_resample(Ctx &c)
 
 cudaError_t enqueue_step(Ctx &c, int mode)
 {
+    if (c.aux) return launch_apf_step(c, c.d_obs, kernel_stride(c, mode), c.stream);
     cudaError_t e = enqueue_propagate(c, mode);
     if (e != cudaSuccess) return e;
     return enqueue_resample(c);
+}
+
+// Second-stage weights of the auxiliary filter back to uniform (lw2 = 0, and the
+// running log sum of them = log N_m), e.g. when it is switched on or the state
+// is replaced.
+pf_status reset_aux_weights(Ctx &c)
+{
+    std::vector<double> fs((size_t)c.M * kFsCount);
+    cudaError_t e = cudaMemsetAsync(c.lw2, 0, (size_t)c.P * sizeof(float), c.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fs.data(), c.fstats, fs.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "auxiliary weights reset");
+    for (int m = 0; m < c.M; ++m) fs[(size_t)m * kFsCount + kFsLse2] = std::log((double)c.N[m]);
+    e = cudaMemcpy(c.fstats, fs.data(), fs.size() * sizeof(double), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "auxiliary weights reset");
 }
 
 pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind)
@@ -586,6 +602,7 @@ static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride,
     pf_status st = validate_step(c, obs, obs_stride);
     if (st != PF_OK) return st;
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_propagate called twice without pf_resample");
+    if (c.aux) return fail(c, PF_EUNSUPPORTED, "the auxiliary filter steps as a whole: use pf_step");
     cudaSetDevice(c.device);
     cudaError_t e = stage_obs(c, obs, obs_stride, kind);
     if (e == cudaSuccess) e = enqueue_propagate(c, obs_mode(obs_stride));
@@ -698,6 +715,7 @@ pf_status pf_set_proposal(pf_ctx *h, const float *h_theta, int32_t n_params, dou
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_proposal between pf_propagate and pf_resample");
     if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "the learned proposal is for the lattice");
+    if (c.aux && h_theta) return fail(c, PF_EUNSUPPORTED, "the learned proposal is not combined with the auxiliary filter");
     if (h_theta && (n_params != PF_MLP_PARAMS || !(ess_frac >= 0.0 && ess_frac <= 1.0)))
         return fail(c, PF_EINVAL, "n_params must be PF_MLP_PARAMS and ess_frac in [0, 1]");
     pf_status st = sync(c, "set_proposal");
@@ -723,6 +741,7 @@ pf_status pf_record_tuples(pf_ctx *h, float *d_X, float *d_R, int64_t capacity, 
     if (!h) return PF_EINVAL;
     Ctx &c = h->c;
     if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the lattice");
+    if (c.aux && d_X) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the bootstrap filter");
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_record_tuples between pf_propagate and pf_resample");
     pf_status st = sync(c, "record_tuples");
     if (st != PF_OK) return st;
@@ -875,6 +894,29 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
     return PF_OK;
 }
 
+pf_status pf_set_auxiliary(pf_ctx *h, int32_t on)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_auxiliary between pf_propagate and pf_resample");
+    if (on && (c.prop_on || c.rec_X))
+        return fail(c, PF_EUNSUPPORTED, "the auxiliary filter is not combined with the learned proposal or recording");
+    pf_status st = sync(c, "set_auxiliary");
+    if (st != PF_OK) return st;
+    drop_graphs(c);
+    if (!on) {
+        c.aux = false;
+        return PF_OK;
+    }
+    if (!c.la) {
+        const bool ok = alloc_n(c, c.la, (size_t)c.P) && alloc_n(c, c.lw2, (size_t)c.P) && alloc_n(c, c.fmax2, (size_t)c.M);
+        if (!ok) return fail(c, PF_ENOMEM, "auxiliary filter buffers: device allocation failed");
+    }
+    c.aux = true;
+    return reset_aux_weights(c);
+}
+
 pf_status pf_set_schedule(pf_ctx *h, int32_t nodes_per_thread, int32_t particles_per_cta, int32_t resample_threads)
 {
     if (!h) return PF_EINVAL;
@@ -949,6 +991,7 @@ pf_status pf_set_state(pf_ctx *h, const float *h_x, int32_t t)
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state copy");
     c.t = t;
     c.phase = 0;
+    if (c.aux) return reset_aux_weights(c);
     return PF_OK;
 }
 
@@ -958,7 +1001,7 @@ pf_status pf_get_logw(pf_ctx *h, float *h_l)
     Ctx &c = h->c;
     pf_status st = sync(c, "get_logw");
     if (st != PF_OK) return st;
-    const cudaError_t e = cudaMemcpy(h_l, c.logw, c.P * sizeof(float), cudaMemcpyDeviceToHost);
+    const cudaError_t e = cudaMemcpy(h_l, c.aux ? c.lw2 : c.logw, c.P * sizeof(float), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "get_logw copy");
 }
 
@@ -966,6 +1009,7 @@ pf_status pf_set_logw(pf_ctx *h, const float *h_l)
 {
     if (!h || !h_l) return PF_EINVAL;
     Ctx &c = h->c;
+    if (c.aux) return fail(c, PF_EUNSUPPORTED, "pf_set_logw: not with the auxiliary filter");
     if (c.phase != 1) return fail(c, PF_ESTATE, "pf_set_logw needs a preceding pf_propagate");
     pf_status st = sync(c, "set_logw");
     if (st != PF_OK) return st;

@@ -223,8 +223,9 @@ struct NoisePacking {
 // Propagates R particles of a small model over the K sub-steps of
 // observation t (Alg. 1 step 2a; Euler-Maruyama), stream `stream`, counter
 // words (c0[r], t, c2).  Several particles per thread give the scheduler
-// independent generator chains to interleave.
-template <int D, int R, typename Real>
+// independent generator chains to interleave.  Noise = false takes the
+// noise-free Euler steps (z = 0) without drawing normals.
+template <int D, int R, typename Real, bool Noise = true>
 __device__ __forceinline__ void propagate_small_n(const ModelParams &mp, const Key &key, uint32_t stream,
                                                   const uint32_t c0[R], uint32_t t, uint32_t c2, Real x[R][D])
 {
@@ -238,7 +239,14 @@ __device__ __forceinline__ void propagate_small_n(const ModelParams &mp, const K
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int b = 0; b < NP::blocks; ++b) normals4<Real>(key, c0[r], t, c2, stream, block + b, z[r] + 4 * b);
+            for (int b = 0; b < NP::blocks; ++b) {
+                if (Noise) {
+                    normals4<Real>(key, c0[r], t, c2, stream, block + b, z[r] + 4 * b);
+                } else {  // the noise-free Euler prediction (auxiliary filter's look-ahead)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) z[r][4 * b + i] = (Real)0;
+                }
+            }
         block += NP::blocks;
 #pragma unroll
         for (int s = 0; s < NP::steps; ++s) {

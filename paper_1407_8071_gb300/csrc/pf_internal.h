@@ -58,7 +58,10 @@ constexpr int32_t kNegInfKey = (int32_t)0x807FFFFF;  // float_order_key(-inf)
 
 // Per-filter scalars kept in FP64 on the device.
 enum FStat : int {
-    kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsFallback = 5, kFsCount = 8
+    kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsFallback = 5,
+    kFsLse2 = 6,  // auxiliary filter: log sum of the second-stage weights (log N before the first step)
+    kFsSumW = 7,  // auxiliary filter: sum of exp(lw2 - max) behind the weighted means
+    kFsCount = 8
 };
 // Per-tile FP64 partial sums.
 enum TSum : int { kTsW = 0, kTsW2 = 1, kTsCount = 2 };
@@ -88,6 +91,17 @@ struct ResampleArgs {
     int32_t *done;           // [M] per-filter completion counters, kept at 0 between steps
 };
 
+// Extra pointers of the auxiliary particle filter's two propagations (all
+// null for the bootstrap filter):
+//   look-ahead (noise off): la_out[p] = log g(y | mu_p), logw[p] = lw_prev[p] + la_out[p];
+//   second stage:           logw[p] = log g(y | x_p) - la_src[off_m + anc[p]].
+struct AuxPtrs {
+    const float *lw_prev;
+    float *la_out;
+    const float *la_src;
+    const int32_t *anc;
+};
+
 struct Ctx;
 
 // Launchers (k_filter.cu).  All enqueue on `s` and return cudaGetLastError().
@@ -96,6 +110,8 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t obs_strid
                              cudaStream_t s);
 cudaError_t launch_resample(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s);
 cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s);  // after the log-weights were replaced
+// One observation step of the ensemble of auxiliary particle filters (k_filter.cu).
+cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t obs_stride, cudaStream_t s);
 // Learned proposal (k_filter.cu, k_proposal.cu, k_mlp.cu).
 cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, float *x, int32_t n_steps,
                                 cudaStream_t s);
@@ -148,6 +164,11 @@ struct Ctx {
     int resample_threads = kResampleThreads;
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
     int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, or 0 (4 where J % 4 == 0)
+    // auxiliary particle filters (pf_set_auxiliary)
+    bool aux = false;
+    float *la = nullptr;           // [P] look-ahead log-likelihoods log g(y | mu)
+    float *lw2 = nullptr;          // [P] second-stage log-weights
+    int32_t *fmax2 = nullptr;      // [M] order keys of the second-stage maxima
     double *tile_sums = nullptr;
     uint64_t *tile_q = nullptr;
     double *fstats = nullptr;

@@ -71,6 +71,7 @@ _SIGS = {
     "pf_systematic_resample_noalloc": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p,
                                                  c_void_p]),
     "pf_set_schedule": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
+    "pf_set_auxiliary": (c_int32, [c_void_p, c_int32]),
     "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
     "pf_record_tuples": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
@@ -375,6 +376,10 @@ class EnsembleFilter:
         ch = (c_int32 * 3)()
         _check(lib().pf_autotune(self.h, ch), self.h)
         return int(ch[0]), int(ch[1]), int(ch[2])
+
+    def set_auxiliary(self, on: bool = True):
+        """Auxiliary particle filters (Pitt & Shephard) instead of bootstrap filters."""
+        _check(lib().pf_set_auxiliary(self.h, 1 if on else 0), self.h)
 
     def set_schedule(self, nodes_per_thread: int = 0, particles_per_cta: int = 0, resample_threads: int = 0):
         """Set the launch schedule explicitly (0: default)."""
