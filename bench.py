@@ -65,6 +65,9 @@ RESAMPLE_BYTES_PER_VARIABLE = 4 + 4 + 4
 # v 9 (cubic, coupling, D times the Laplacian), of w 2, two Euler-Maruyama
 # updates 4 -> 68.
 FHN_OPS_PER_NODE_STEP = 68
+# The auxiliary filter's noise-free look-ahead: Laplacian 4, drift 9 + 2,
+# two Euler updates 2 -> 17 per node-step.
+FHN_LOOKAHEAD_OPS_PER_NODE_STEP = 17
 
 
 def env_int(name, default):
@@ -153,6 +156,7 @@ WORKLOAD_TEXT = {
                      "resident; one step = one observation (K=40 Euler-Maruyama sub-steps) of each"),
     "fhn": "fhn 40x40 lattice (3200 variables), M=32 x N=1024, K=20, bootstrap proposal",
     "fhn-learned": "fhn 40x40 lattice, M=32 x N=1024, K=20, learned proposal (network trained untimed)",
+    "fhn-apf": "fhn 40x40 lattice, M=32 x N=1024, K=20, auxiliary particle filters (the paper's Sec. 5.3 filter)",
     "ragged": ("256 fhn 20x20 lattices, N log-uniform in [64, 4096], independent records, learned proposal, "
                "one autotuned context (all filters in each launch, CUDA graph)"),
 }
@@ -171,7 +175,7 @@ class Workload:
             self.spec = W.lorenz63()
             self.rows = W.lorenz_sweep()
             rec_seed, T = W.SEED_LORENZ_OBS, 200
-        elif name in ("fhn", "fhn-learned"):
+        elif name in ("fhn", "fhn-learned", "fhn-apf"):
             self.spec = W.fhn_lattice()
             self.rows = [(W.FHN_FULL["M"], W.FHN_FULL["N"])]
             rec_seed, T = W.SEED_FHN_OBS, W.FHN_FULL["T"]
@@ -195,6 +199,7 @@ class Workload:
         self.y_dev = self.y_host.cuda()
         torch.cuda.synchronize()
         self.theta = None
+        self.aux = name == "fhn-apf"
         if name in ("fhn-learned", "ragged"):
             self.theta = proposal.trained_theta(self.spec, train_record[:20], seed=seed_base + 77)
         # one stream per context: the configurations are independent, so their
@@ -208,6 +213,8 @@ class Workload:
                 f.set_proposal(self.theta, 0.1)
             if self.spec.kind == W.FHN:
                 self.choice = f.autotune()
+            if self.aux:
+                f.set_auxiliary(True)
             self.filters.append(f)
             self.streams.append(st)
         self.particles = int(sum(int(np.sum(N)) if np.ndim(N) else M * N for M, N in self.rows))
@@ -215,7 +222,9 @@ class Workload:
         # kernels one pf_step launches: small models -- propagate, weights, scan, ancestors, ensemble;
         # lattice -- propagate, weights, scan, ancestors, gather, means, ensemble; the learned proposal
         # replaces the propagate by sub-steps, network rows, network forward, last step and select
-        if self.spec.kind == W.FHN:
+        if self.aux:  # fill, look-ahead, weights, scan, ancestors, gather, propagate, stats, means, ensemble
+            self.kernels_per_filter_step = 10
+        elif self.spec.kind == W.FHN:
             self.kernels_per_filter_step = 7 + (4 if self.theta is not None else 0)
         else:
             self.kernels_per_filter_step = 5
@@ -306,8 +315,20 @@ def time_region(torch, wl, fn, K, barrier=None):
 
 def phase_times(torch, wl, reps=5):
     """Average device time of the propagate+weight kernel and of the resampling
-    chain, per launch, with CUDA events on the filters' stream."""
+    chain, per launch, with CUDA events on the filters' stream (the auxiliary
+    filter steps as one unit: its whole step is the first figure)."""
     prop, res = [], []
+    if wl.aux:
+        for f, st in zip(wl.filters, wl.streams):
+            for _ in range(reps):
+                e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                e0.record(st)
+                f.step_device(wl.y_dev[wl.t % wl.T])
+                e1.record(st)
+                torch.cuda.synchronize()
+                prop.append(e0.elapsed_time(e1) / 1e3)
+                wl.t += 1
+        return float(np.mean(prop)), 0.0, prop
     for f, st in zip(wl.filters, wl.streams):
         for _ in range(reps):
             row = wl.y_dev[wl.t % wl.T]
@@ -346,7 +367,7 @@ def oracle_case(workload: str, M: int, n_scale: int, T: int, theta=None):
     if workload == "lorenz-sweep":  # filters of the M = 64, N = 16384 row of the sweep
         spec = W.lorenz63()
         return spec, M, (1 << 14) // n_scale, oracle.simulate(spec, T, W.SEED_LORENZ_OBS)[1], False, None
-    if workload in ("fhn", "fhn-learned"):
+    if workload in ("fhn", "fhn-learned", "fhn-apf"):
         spec = W.fhn_lattice()
         y = oracle.simulate(spec, T, W.SEED_FHN_OBS)[1]
         if workload == "fhn-learned" and theta is None:
@@ -363,10 +384,12 @@ def oracle_case(workload: str, M: int, n_scale: int, T: int, theta=None):
     return spec, M, N, y, True, theta
 
 
-def oracle_run(case, T, seed, threads):
+def oracle_run(case, T, seed, threads, aux=False):
     import oracle
     spec, M, N, y, per_filter, theta = case
-    if spec.kind == W.FHN:
+    if aux:
+        oracle.apf_run(spec, M, N, T, y[:T], seed=seed, est_idx=[1], obs_per_filter=per_filter, threads=threads)
+    elif spec.kind == W.FHN:
         oracle.bf_run_proposal(spec, theta, M, N, T, y[:T], seed=seed, est_idx=[1], obs_per_filter=per_filter,
                                threads=threads)
     else:
@@ -383,17 +406,18 @@ def oracle_sample(workload: str, target_s: float, theta=None):
     case = oracle_case(workload, M, 1, Tmax, theta)
     threads = min(M, cores)
     t0 = time.perf_counter()
-    oracle_run(case, 1, 1, threads)
+    aux = workload == "fhn-apf"
+    oracle_run(case, 1, 1, threads, aux)
     dt1 = time.perf_counter() - t0
     T = int(max(1, min(Tmax, round(target_s / max(dt1, 1e-3)))))
     t0 = time.perf_counter()
-    ps = oracle_run(case, T, 2, threads)
+    ps = oracle_run(case, T, 2, threads, aux)
     dt = time.perf_counter() - t0
     spec, _, N, _, _, th = case
     ntxt = f"{N} particles" if np.ndim(N) == 0 else f"{int(np.sum(N))} particles in all (ragged)"
     desc = (f"{W.KIND_NAMES[spec.kind]}: {M} filters, {ntxt}, {T} observations x K={spec.K} "
             f"(= {ps:.3g} particle-steps) of the {workload} workload, FP64, OpenMP over filters"
-            + (", learned proposal" if th is not None else ""))
+            + (", learned proposal" if th is not None else "") + (", auxiliary filters" if aux else ""))
     return ps / dt, threads, desc
 
 
@@ -406,11 +430,11 @@ def run_reference(args):
     case = oracle_case(args.workload, M, 4, 2)
     threads = min(M, cores)
     for k in range(args.warmup):
-        oracle_run(case, 1, 3 + k, threads)
+        oracle_run(case, 1, 3 + k, threads, args.workload == "fhn-apf")
     t0 = time.perf_counter()
     work = 0
     for k in range(args.steps):
-        work += oracle_run(case, 1, 100 + k, threads)
+        work += oracle_run(case, 1, 100 + k, threads, args.workload == "fhn-apf")
     dt = time.perf_counter() - t0
     value = work / dt
     spec, _, N, _, _, th = case
@@ -524,9 +548,11 @@ def main():
                     "ops_per_particle_step": LORENZ_OPS_PER_PARTICLE_STEP, "avg_launch_s": t_prop}
     else:
         alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-        per_launch_ops = (wl.particles / nf) * wl.spec.K * wl.spec.J * wl.spec.J * FHN_OPS_PER_NODE_STEP
+        ops_node = FHN_OPS_PER_NODE_STEP + (FHN_LOOKAHEAD_OPS_PER_NODE_STEP if wl.aux else 0)
+        per_launch_ops = (wl.particles / nf) * wl.spec.K * wl.spec.J * wl.spec.J * ops_node
         achieved = per_launch_ops / t_prop / 1e12
-        kern = "k_propagate_fhn<float>" if wl.theta is None else "proposal propagate (5 kernels)"
+        kern = ("k_propagate_fhn<float>" if wl.theta is None else "proposal propagate (5 kernels)") if not wl.aux \
+            else "auxiliary step (look-ahead + second-stage propagate + resampling)"
         roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                     "frac": achieved / alu_peak,
                     "traffic": recorded_traffic("k_propagate_fhn<float>") if wl.theta is None else None,
@@ -557,7 +583,7 @@ def main():
         "gpu_launches": args.steps * nf * wl.kernels_per_filter_step,
         "roofline": roofline,
         "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res},
-        "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src),
+        "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src) if t_res > 0 else None,
     }
     theta = wl.theta
     if wl.N_list is not None:

@@ -7,8 +7,8 @@ reference posterior, and the wall time needed to reach a given MSE.
   side by side in one context (R M filters; ensemble r = filters
   [r M, (r + 1) M)), so one launch per step serves all of them.
 * The lattice: MSE of the averaged v-estimates against a reference posterior,
-  plain bootstrap vs learned proposal vs the centralised filter at several
-  sizes, and the time-error index of Sec. 3.4 (wall time x MSE), so they can
+  plain bootstrap vs learned proposal vs auxiliary filters vs the centralised
+  filter at several sizes, and the time-error index of Sec. 3.4 (wall time x MSE), so they can
   be compared at equal MSE.
 
 The Lorenz reference posterior is a bootstrap filter with many more particles
@@ -35,7 +35,7 @@ def _var_index(spec: W.ModelSpec):
 
 
 def filter_estimates(spec: W.ModelSpec, M: int, N, seed: int, d_y, theta=None, ess_frac: float = 0.1,
-                     want_ess: bool = False):
+                     want_ess: bool = False, aux: bool = False):
     """Per-filter posterior means of the scored statistics at every observation
     time: array (T, M, n_stat); optionally the per-filter ESS (T, M)."""
     idx = _var_index(spec)
@@ -45,6 +45,8 @@ def filter_estimates(spec: W.ModelSpec, M: int, N, seed: int, d_y, theta=None, e
     with pf.EnsembleFilter(spec, M, N, seed) as f:
         if theta is not None:
             f.set_proposal(theta, ess_frac)
+        if aux:
+            f.set_auxiliary(True)
         for t in range(T):
             f.step_device(d_y[t])
             if len(idx) == 1:
@@ -66,7 +68,8 @@ def reference_posterior(spec: W.ModelSpec, N_ref: int, seeds, d_y):
     return acc / len(seeds)
 
 
-def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, warmup: int = 3) -> float:
+def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, warmup: int = 3,
+              aux: bool = False) -> float:
     """Device seconds per observation step of one M-filter context (CUDA events)."""
     import torch
     st = torch.cuda.Stream()
@@ -74,6 +77,8 @@ def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, wa
         f.set_stream(st.cuda_stream)
         if theta is not None:
             f.set_proposal(theta, 0.1)
+        if aux:
+            f.set_auxiliary(True)
         for t in range(warmup):
             f.step_device(d_y[t % d_y.shape[0]])
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -157,13 +162,15 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
     d_y = torch.from_numpy(np.ascontiguousarray(y)).cuda()
     ref = ensemble_reference(spec, M_ref, N_ref, ref_seeds, d_y)
     out = {}
-    for name, th, m_run in (("plain", None, M), ("learned", theta, M), ("centralised", None, 1)):
+    for name, th, m_run, aux in (("plain", None, M, False), ("learned", theta, M, False),
+                                 ("auxiliary", None, M, True), ("centralised", None, 1, False)):
         rows = []
         for N in Ns:
             n_run = N * M // m_run
-            est, ess = filter_estimates(spec, R * m_run, n_run, 2000 + N + 7 * m_run, d_y, theta=th, want_ess=True)
+            est, ess = filter_estimates(spec, R * m_run, n_run, 2000 + N + 7 * m_run, d_y, theta=th, want_ess=True,
+                                        aux=aux)
             mse, var, bias2, _ = ensemble_mse(est, m_run, ref, skip=skip)
-            dt = step_time(spec, m_run, n_run, d_y, theta=th)
+            dt = step_time(spec, m_run, n_run, d_y, theta=th, aux=aux)
             rows.append({"M": m_run, "N": n_run, "mse": mse, "var": var, "bias2": bias2, "s_per_step": dt,
                          "s_per_run": dt * T, "mean_ess_frac": float(np.mean(ess[skip:]) / n_run),
                          "time_error_index": dt * T * mse})
@@ -185,4 +192,5 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
             "ref_seeds": len(ref_seeds), "skip": skip, "rows": out, "target_mse": target,
             "plain_s_at_target": out["plain"][-1]["s_per_run"],
             "learned_s_at_target": time_at(out["learned"], target),
+            "auxiliary_s_at_target": time_at(out["auxiliary"], target),
             "centralised_s_at_target": time_at(out["centralised"], target)}
