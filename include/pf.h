@@ -64,9 +64,18 @@ typedef enum {
 typedef enum {
     PF_MODEL_LINEAR_GAUSSIAN = 0, /* dx in [1,4]; drift -A x; params = A (dx*dx, row-major)           */
     PF_MODEL_LORENZ63 = 1,        /* dx = 3; Sec. 4.1 eqs. eqDiscreteLorenz-1..3; params = (s, r, b)  */
-    PF_MODEL_FHN_LATTICE = 2      /* dx = 2 J^2, J even in [2,44]; Sec. 5.1 lattice, Rogers-McCulloch
+    PF_MODEL_FHN_LATTICE = 2,     /* dx = 2 J^2, J even in [2,44]; Sec. 5.1 lattice, Rogers-McCulloch
                                      form; params = (a, b, c1, c2, d, D, stim_amp, stim_steps,
                                      stim_block); state = v-plane then w-plane, node = row*J + col   */
+    PF_MODEL_FHN_PAPER = 3        /* dx = 3 J^2, J even in [2,44]; the paper's own lattice, eqs. eqUd,
+                                     eqVd with the random stimulus of eqs. eqStimulusRegion-
+                                     eqPsi_ijt; state = U-plane, V-plane, S-plane (sub-steps since
+                                     the node's last stimulus event, capped at l0); 17 params:
+                                     alpha_3..alpha_0 of p3, beta_0..beta_2, 1/D, forcing amplitude,
+                                     forcing period and pulse width (sub-steps), forced columns,
+                                     u-, u+, round(eps 2^24), stimulus amplitude, l0.  Noise only
+                                     on U; the stimulus draws use Philox stream 6 (particles) / 7
+                                     (pf_simulate's truth), block = sub-step index.               */
 } pf_model_kind;
 
 /* The Markov kernel tau_t (Sec. 2.2, eq. eqKernel): steps_per_obs Euler-

@@ -37,6 +37,7 @@
 #define ORC_LG 0
 #define ORC_LORENZ63 1
 #define ORC_FHN 2
+#define ORC_FHNP 3 /* the paper's own lattice variant, Sec. 5.1-5.2 */
 
 #define ORC_STREAM_TRUTH 0u
 #define ORC_STREAM_OBS 1u
@@ -44,7 +45,8 @@
 #define ORC_STREAM_DYN 3u
 #define ORC_STREAM_RESAMPLE 4u
 #define ORC_STREAM_PROPOSAL 5u
-#define ORC_STREAM_MISC 6u
+#define ORC_STREAM_MISC 6u        /* also the particles' random stimulus (lattice variant of Sec. 5.1) */
+#define ORC_STREAM_STIM_TRUTH 7u  /* the truth's random stimulus */
 
 /* Model description, filled from Python (ctypes mirror in oracle/__init__.py). */
 typedef struct {
@@ -64,6 +66,17 @@ typedef struct {
 } orc_model;
 
 /* FHN parameter layout: a, b, c1, c2, d, D, stim_amp, stim_steps, stim_block */
+/* FHNP (the paper's variant) parameter layout:
+ *   0..3  alpha_3, alpha_2, alpha_1, alpha_0   (p3(u) = sum alpha_r u^r)
+ *   4..6  beta_0, beta_1, beta_2               (eq. eqVd)
+ *   7     coupling 1/D                          (eq. eqUd: (1/D) sum of the neighbours' U)
+ *   8     F~, forcing amplitude;  9 forcing period (sub-steps);  10 pulse width (sub-steps)
+ *   11    forced columns (m_ij = 1 for j < this)
+ *   12, 13  u-, u+ thresholds of the stimulus region (eq. eqStimulusRegion)
+ *   14    epsilon (Bernoulli), as an integer threshold on 24-bit uniforms: round(eps 2^24)
+ *   15    stimulus amplitude;  16  l0 (steps a stimulus is held)
+ * State: planes U, V and S = sub-steps since the node's last stimulus event, capped at l0
+ * (Psi = amplitude while S < l0). */
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10: Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   */
@@ -175,7 +188,7 @@ static double ns_get(nstream *s, int64_t nu)
  * plane 1 = w): 2*node + plane, so the (v, w) pair of a node is adjacent. */
 static int64_t noise_slot(const orc_model *md, int64_t v)
 {
-    if (md->kind == ORC_FHN) {
+    if (md->kind == ORC_FHN || md->kind == ORC_FHNP) {
         int64_t nn = (int64_t)md->J * md->J;
         int64_t plane = v / nn, node = v % nn;
         return 2 * node + plane;
@@ -201,6 +214,31 @@ static void drift(const orc_model *md, int64_t n, const double *x, double *f)
         f[0] = -s * (x[0] - x[1]);
         f[1] = r * x[0] - x[1] - x[0] * x[2];
         f[2] = x[0] * x[1] - b * x[2];
+    } else if (md->kind == ORC_FHNP) {
+        /* eqs. eqUd, eqVd: f_U = p3(U) - V + (1/D) sum_nbr U + m F_n + Psi, f_V = b0 U + b1 V + b2;
+         * the neighbour sets are the von Neumann ones of Sec. 5.2 (edges and corners have fewer) */
+        int J = md->J, nn = J * J;
+        double per = p[9], wid = p[10];
+        int fcols = (int)p[11];
+        double l0 = p[16];
+        int on = fmod((double)(n - 1), per) < wid;
+        const double *U = x, *V = x + nn, *S = x + 2 * nn;
+        for (int i = 0; i < J; ++i)
+            for (int j = 0; j < J; ++j) {
+                int k = i * J + j;
+                double u = U[k];
+                double nb = 0.0;
+                if (i > 0) nb += U[k - J];
+                if (i < J - 1) nb += U[k + J];
+                if (j > 0) nb += U[k - 1];
+                if (j < J - 1) nb += U[k + 1];
+                double p3 = ((p[0] * u + p[1]) * u + p[2]) * u + p[3];
+                double force = (on && j < fcols) ? p[8] : 0.0;
+                double psi = S[k] < l0 ? p[15] : 0.0;
+                f[k] = p3 - V[k] + p[7] * nb + force + psi;
+                f[nn + k] = p[4] * u + p[5] * V[k] + p[6];
+                f[2 * nn + k] = 0.0;
+            }
     } else { /* ORC_FHN */
         double a = p[0], bb = p[1], c1 = p[2], c2 = p[3], dd = p[4], D = p[5];
         double amp = p[6];
@@ -241,13 +279,67 @@ static void em_step(const orc_model *md, int64_t n, double *x, const double *z, 
  * c0 = 0, c2 = record) over the K sub-steps from observation t-1 to t.
  * Normal number nu = k*dx + slot(v) for sub-step k = 0..K-1, counter
  * (c0, t, c2, stream<<24 | nu/4). */
+/* The lattice variant's random stimulus before sub-step k of interval t
+ * (eqs. eqStimulusRegion-eqPsi_ijt): one Philox block (c0, t, c2, stream<<24 | k)
+ * gives r0, r1; an event happens when (r0 >> 8) < round(eps 2^24) and the
+ * stimulus region S (nodes whose U, or a neighbour's U, lies in (u-, u+)) is
+ * not empty; it hits the node of rank floor((r1 >> 8) |S| / 2^24) in S
+ * (row-major order) and its neighbours.  Every node's counter S ages by one
+ * (capped at l0) or restarts at 0 where the event hits.  events = 0 ages only
+ * (the auxiliary filter's noise-free look-ahead). */
+static void fhnp_stimulus(const orc_model *md, uint64_t seed, uint32_t stream, uint32_t c0, uint32_t t, uint32_t c2,
+                          int k, int events, double *x)
+{
+    const double *p = md->params;
+    int J = md->J, nn = J * J;
+    double *U = x, *S = x + 2 * nn;
+    double l0 = p[16];
+    int target = -1;
+    if (events) {
+        uint32_t ctr[4] = {c0, t, c2, (stream << 24) | (uint32_t)k}, key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        if ((r[0] >> 8) < (uint32_t)p[14]) {
+            int64_t cnt = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                int64_t rank = pass ? (int64_t)(((uint64_t)(r[1] >> 8) * (uint64_t)cnt) >> 24) : -1, seen = 0;
+                for (int i = 0; i < J && target < 0; ++i)
+                    for (int j = 0; j < J; ++j) {
+                        int q = i * J + j, in = 0;
+                        int nb[5] = {q, i > 0 ? q - J : -1, i < J - 1 ? q + J : -1, j > 0 ? q - 1 : -1, j < J - 1 ? q + 1 : -1};
+                        for (int e = 0; e < 5; ++e)
+                            if (nb[e] >= 0 && U[nb[e]] > p[12] && U[nb[e]] < p[13]) in = 1;
+                        if (!in) continue;
+                        if (pass == 1 && seen == rank) { target = q; break; }
+                        ++seen;
+                    }
+                if (pass == 0) cnt = seen;
+                if (cnt == 0) break;
+            }
+        }
+    }
+    int ti = target >= 0 ? target / J : -10, tj = target >= 0 ? target % J : -10;
+    for (int i = 0; i < J; ++i)
+        for (int j = 0; j < J; ++j) {
+            int q = i * J + j;
+            int hit = (i == ti && j == tj) || (i == ti && (j == tj - 1 || j == tj + 1)) ||
+                      (j == tj && (i == ti - 1 || i == ti + 1));
+            S[q] = hit ? 0.0 : (S[q] + 1.0 < l0 ? S[q] + 1.0 : l0);
+        }
+}
+
 static void propagate_one(const orc_model *md, uint64_t seed, uint32_t stream, uint32_t c0, uint32_t c2,
                           int32_t t, double *x, double *z, double *f)
 {
     nstream ns;
     ns_init(&ns, seed, c0, (uint32_t)t, c2, stream);
+    const int64_t nn = (int64_t)md->J * md->J;
     for (int k = 0; k < md->K; ++k) {
-        for (int v = 0; v < md->dx; ++v) z[v] = ns_get(&ns, (int64_t)k * md->dx + noise_slot(md, v));
+        if (md->kind == ORC_FHNP)
+            fhnp_stimulus(md, seed, stream == ORC_STREAM_TRUTH ? ORC_STREAM_STIM_TRUTH : ORC_STREAM_MISC, c0,
+                          (uint32_t)t, c2, k, 1, x);
+        for (int v = 0; v < md->dx; ++v)
+            z[v] = (md->kind == ORC_FHNP && v >= nn) ? 0.0 : ns_get(&ns, (int64_t)k * md->dx + noise_slot(md, v));
         int64_t n = (int64_t)(t - 1) * md->K + k + 1;
         em_step(md, n, x, z, f);
     }
@@ -258,7 +350,9 @@ static void prior_one(const orc_model *md, uint64_t seed, uint32_t stream, uint3
 {
     nstream ns;
     ns_init(&ns, seed, c0, 0u, c2, stream);
-    for (int v = 0; v < md->dx; ++v) x[v] = md->x0_mean[v] + md->sigma0 * ns_get(&ns, noise_slot(md, v));
+    const int64_t s_plane = md->kind == ORC_FHNP ? 2 * (int64_t)md->J * md->J : md->dx;  /* S starts exact */
+    for (int v = 0; v < md->dx; ++v)
+        x[v] = md->x0_mean[v] + (v < s_plane ? md->sigma0 * ns_get(&ns, noise_slot(md, v)) : 0.0);
 }
 
 /* log g without its constant: -1/2 sum_j (y_j - x[idx_j])^2 / sigma_obs^2. */
@@ -737,6 +831,7 @@ int orc_bf_run_proposal(const orc_model *md, const orc_proposal *pr, int32_t M, 
 static void predict_one(const orc_model *md, int32_t t, double *x, double *f)
 {
     for (int k = 0; k < md->K; ++k) {
+        if (md->kind == ORC_FHNP) fhnp_stimulus(md, 0, 0, 0, 0, 0, k, 0, x);  /* no new events: ageing only */
         int64_t n = (int64_t)(t - 1) * md->K + k + 1;
         drift(md, n, x, f);
         for (int v = 0; v < md->dx; ++v) x[v] = x[v] + md->dt * f[v];

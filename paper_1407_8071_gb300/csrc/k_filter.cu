@@ -364,6 +364,10 @@ __global__ void __launch_bounds__(256) k_init_fhn(ModelParams mp, Key key, const
     xp[nn + n0] = (float)(x0[nn + n0] + mp.sigma0 * (double)z[1]);
     xp[n1] = (float)(x0[n1] + mp.sigma0 * (double)z[2]);
     xp[nn + n1] = (float)(x0[nn + n1] + mp.sigma0 * (double)z[3]);
+    if (mp.kind == kFhnPaper) {  // the stimulus counters start exact
+        xp[2 * nn + n0] = (float)x0[2 * nn + n0];
+        xp[2 * nn + n1] = (float)x0[2 * nn + n1];
+    }
 }
 
 // ------------------------------------------------------------------ propagate + weight (Alg. 1 step 2a)
@@ -1154,6 +1158,10 @@ __global__ void k_fhn_truth_init(ModelParams mp, Key key, int32_t record, int32_
     x[nn + n0] = x0[nn + n0] + mp.sigma0 * z[1];
     x[n1] = x0[n1] + mp.sigma0 * z[2];
     x[nn + n1] = x0[nn + n1] + mp.sigma0 * z[3];
+    if (mp.kind == kFhnPaper) {
+        x[2 * nn + n0] = x0[2 * nn + n0];
+        x[2 * nn + n1] = x0[2 * nn + n1];
+    }
 }
 
 __global__ void k_observe(ModelParams mp, Key key, const int32_t *obs_idx, int32_t t, int32_t record,
@@ -1256,7 +1264,7 @@ ResampleArgs ctx_args(const Ctx &c)
 
 cudaError_t launch_init(const Ctx &c, cudaStream_t s)
 {
-    if (c.mp.kind == kFhnLattice) {
+    if (is_lattice(c.mp.kind)) {
         const int64_t work = c.P * (c.mp.J * c.mp.J / 2);
         k_init_fhn<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(c.mp, c.key, c.pfilt, c.filt, c.x0, c.x[c.cur], c.P);
         return cudaGetLastError();
@@ -1305,8 +1313,10 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
 cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                              cudaStream_t s)
 {
-    if (c.mp.kind == kFhnLattice) {
+    if (is_lattice(c.mp.kind)) {
         int ppc;
+        if (c.mp.kind == kFhnPaper)
+            return launch_fhnp_interval(c, d_obs, stride, xi, xo, c.mp.K, c.logw, c.fmax_key, AuxPtrs{}, 1, s);
         return launch_fhn_interval(c, d_obs, stride, xi, xo, c.mp.K, true, s);
     }
     switch (c.mp.dx) {
@@ -1360,17 +1370,25 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
     float *xn = c.x[c.cur ^ 1];
     k_fill_i32<<<(c.M + 255) / 256, 256, 0, s>>>(c.fmax2, c.M, kNegInfKey);
     cudaError_t e = cudaSuccess;
-    if (c.mp.kind == kFhnLattice) {
-        e = launch_fhn_interval(c, d_obs, stride, x, nullptr, c.mp.K, true, s, c.logw, c.fmax_key,
-                                AuxPtrs{c.lw2, c.la, nullptr, nullptr}, 0);
+    if (is_lattice(c.mp.kind)) {
+        if (c.mp.kind == kFhnPaper)
+            e = launch_fhnp_interval(c, d_obs, stride, x, nullptr, c.mp.K, c.logw, c.fmax_key,
+                                     AuxPtrs{c.lw2, c.la, nullptr, nullptr}, 0, s);
+        else
+            e = launch_fhn_interval(c, d_obs, stride, x, nullptr, c.mp.K, true, s, c.logw, c.fmax_key,
+                                    AuxPtrs{c.lw2, c.la, nullptr, nullptr}, 0);
         if (e != cudaSuccess) return e;
         k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
         k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
         k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(x),
                                                    reinterpret_cast<float4 *>(xn), dx / 4);
-        e = launch_fhn_interval(c, d_obs, stride, xn, xn, c.mp.K, true, s, c.lw2, c.fmax2,
-                                AuxPtrs{nullptr, nullptr, c.la, c.anc}, 1);
+        if (c.mp.kind == kFhnPaper)
+            e = launch_fhnp_interval(c, d_obs, stride, xn, xn, c.mp.K, c.lw2, c.fmax2,
+                                     AuxPtrs{nullptr, nullptr, c.la, c.anc}, 1, s);
+        else
+            e = launch_fhn_interval(c, d_obs, stride, xn, xn, c.mp.K, true, s, c.lw2, c.fmax2,
+                                    AuxPtrs{nullptr, nullptr, c.la, c.anc}, 1);
         if (e != cudaSuccess) return e;
         k_weight_stats<0><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, nullptr, c.P, c.tile_sums, nullptr,
                                                    c.done, c.fstats, c.est, c.err);
@@ -1397,7 +1415,7 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
     const int dx = c.mp.dx, th = c.resample_threads;
     k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
     k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
-    if (c.mp.kind == kFhnLattice) {
+    if (is_lattice(c.mp.kind)) {
         k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
                                                    reinterpret_cast<float4 *>(xo), dx / 4);
@@ -1446,7 +1464,7 @@ cudaError_t launch_rng_normals(int64_t n, const uint32_t *ctr, uint64_t seed, fl
 cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int32_t *d_obs_idx, Key key, int32_t T,
                             int32_t record, int32_t init_random, double *d_x, float *d_y, cudaStream_t s)
 {
-    if (mp.kind != kFhnLattice) {
+    if (!is_lattice(mp.kind)) {
         switch (mp.dx) {
         case 1: k_simulate_small<1><<<1, 32, 0, s>>>(mp, key, T, record, init_random, d_x, d_y); break;
         case 2: k_simulate_small<2><<<1, 32, 0, s>>>(mp, key, T, record, init_random, d_x, d_y); break;
@@ -1463,9 +1481,14 @@ cudaError_t launch_simulate(const ModelParams &mp, const double *d_x0, const int
     for (int32_t t = 1; t <= T; ++t) {
         const double *xi = d_x + (int64_t)(t - 1) * mp.dx;
         double *xo = d_x + (int64_t)t * mp.dx;
-        k_propagate_fhn<double><<<1, threads, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1, nullptr,
-                                                         nullptr, 0, nullptr, nullptr, 0, record, t, 1, nullptr, mp.K,
-                                                         AuxPtrs{}, 1);
+        if (mp.kind == kFhnPaper) {
+            const cudaError_t e = launch_fhnp_truth_step(mp, key, record, t, xi, xo, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            k_propagate_fhn<double><<<1, threads, smem, s>>>(mp, key, kStreamTruth, nullptr, nullptr, xi, xo, 1,
+                                                             nullptr, nullptr, 0, nullptr, nullptr, 0, record, t, 1,
+                                                             nullptr, mp.K, AuxPtrs{}, 1);
+        }
         if (d_y)
             k_observe<<<(mp.dy + 255) / 256, 256, 0, s>>>(mp, key, d_obs_idx, t, record, xo,
                                                           d_y + (int64_t)(t - 1) * mp.dy);

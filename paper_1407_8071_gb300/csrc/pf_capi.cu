@@ -239,6 +239,12 @@ bool model_ok(const pf_model *m, std::string &why)
         if (m->dx != 2 * m->J * m->J) { why = "lattice dx must be 2 J^2"; return false; }
         if (!m->params || m->n_params != 9) { why = "lattice params are (a, b, c1, c2, d, D, amp, steps, block)"; return false; }
         return true;
+    case PF_MODEL_FHN_PAPER:
+        if (m->J < 2 || m->J > 44 || (m->J & 1)) { why = "lattice side J must be even, 2..44"; return false; }
+        if (m->dx != 3 * m->J * m->J) { why = "the paper's lattice has dx = 3 J^2 (U, V, stimulus counters)"; return false; }
+        if (!m->params || m->n_params != 17) { why = "the paper's lattice takes 17 params (see pf.h)"; return false; }
+        if (!(m->params[9] >= 1.0) || !(m->params[16] >= 1.0)) { why = "forcing period and l0 must be >= 1"; return false; }
+        return true;
     default:
         why = "unknown model kind";
         return false;
@@ -254,10 +260,10 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
     if (!(obs->sigma_obs > 0.0)) { why = "sigma_obs must be positive"; return false; }
     if (!noise || !noise->x0_mean) { why = "noise needs x0_mean"; return false; }
     if (!(noise->sigma_dyn >= 0.0) || !(noise->sigma0 >= 0.0)) { why = "noise scales must be >= 0"; return false; }
-    if (model->kind != PF_MODEL_FHN_LATTICE && obs->dy > kMaxObsSmall) { why = "small models observe at most 8 components"; return false; }
+    if (!is_lattice(model->kind) && obs->dy > kMaxObsSmall) { why = "small models observe at most 8 components"; return false; }
     for (int j = 0; j < obs->dy; ++j) {
         const int32_t i = obs->idx[j];
-        const int32_t lim = model->kind == PF_MODEL_FHN_LATTICE ? model->J * model->J : model->dx;
+        const int32_t lim = is_lattice(model->kind) ? model->J * model->J : model->dx;
         if (i < 0 || i >= lim) { why = "observation index out of range (lattice: v-plane nodes only)"; return false; }
     }
     mp = ModelParams{};
@@ -269,12 +275,12 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
     mp.sigma_dyn = noise->sigma_dyn;
     mp.sigma0 = noise->sigma0;
     mp.sigma_obs = obs->sigma_obs;
-    for (int i = 0; i < model->n_params && i < 16; ++i) mp.p[i] = model->params[i];
+    for (int i = 0; i < model->n_params && i < 24; ++i) mp.p[i] = model->params[i];
     mp.dy = obs->dy;
     for (int j = 0; j < obs->dy && j < kMaxObsSmall; ++j) mp.obs_small[j] = obs->idx[j];
-    if (model->kind != PF_MODEL_FHN_LATTICE)
+    if (!is_lattice(model->kind))
         for (int v = 0; v < model->dx; ++v) mp.x0_small[v] = noise->x0_mean[v];
-    for (int i = 0; i < 16; ++i) mp.fp[i] = (float)mp.p[i];
+    for (int i = 0; i < 24; ++i) mp.fp[i] = (float)mp.p[i];
     mp.fdt = (float)dt;
     mp.dsq = noise->sigma_dyn * std::sqrt(dt);
     mp.fsq = (float)mp.dsq;
@@ -447,7 +453,7 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
 
     std::vector<TileDesc> tiles, subs, mchunks;
     std::vector<FilterDesc> filt;
-    const bool small = mp.kind != PF_MODEL_FHN_LATTICE;
+    const bool small = !is_lattice(mp.kind);
     make_tiles(c.N, tiles, filt, c.off, small ? &subs : nullptr, small ? nullptr : &mchunks);
     c.P = c.off[M];
     c.n_tiles = (int32_t)tiles.size();
@@ -473,7 +479,7 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
               alloc_n(c, c.d_obs, (size_t)M * mp.dy) && alloc_n(c, c.d_t, 1) && alloc_n(c, c.err, 2) &&
               alloc_n(c, c.obs_idx, mp.dy) && alloc_n(c, c.x0, dx);
     if (ok) ok = alloc_n(c, c.pfilt, P);
-    if (ok && mp.kind == PF_MODEL_FHN_LATTICE)
+    if (ok && is_lattice(mp.kind))
         ok = alloc_n(c, c.obs_slot, mp.J * mp.J) && alloc_n(c, c.mchunks, mchunks.size()) &&
              alloc_n(c, c.mean_part, mchunks.size() * (size_t)dx) &&
              alloc_n(c, c.mean_cnt, (size_t)M * ((dx + 255) / 256));
@@ -521,7 +527,7 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
         for (int m = 0; m < M; ++m) std::fill(pf_host.begin() + c.off[m], pf_host.begin() + c.off[m + 1], m);
         e = cudaMemcpyAsync(c.pfilt, pf_host.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
     }
-    if (e == cudaSuccess && mp.kind == PF_MODEL_FHN_LATTICE) {
+    if (e == cudaSuccess && is_lattice(mp.kind)) {
         slot.assign(mp.J * mp.J, -1);
         for (int j = 0; j < mp.dy; ++j) slot[obs->idx[j]] = j;
         e = cudaMemcpyAsync(c.obs_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream);
@@ -833,10 +839,10 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
             cudaMemcpyAsync(scratch, c.x[c.cur], xb, cudaMemcpyDeviceToDevice, c.stream);
             launch_propagate(c, c.d_obs, 0, scratch, scratch, c.stream);
         };
-        if (e == cudaSuccess && c.mp.kind == PF_MODEL_FHN_LATTICE) {  // nodes per thread, particles per CTA
+        if (e == cudaSuccess && is_lattice(c.mp.kind)) {  // nodes per thread, particles per CTA
             float best = 1e30f;
             for (int nodes = 2; nodes <= 4; nodes += 2) {
-                if (nodes == 4 && c.mp.J % 4 != 0) continue;
+                if (nodes == 4 && (c.mp.J % 4 != 0 || c.mp.kind == PF_MODEL_FHN_PAPER)) continue;
                 const int per = c.mp.J * c.mp.J / nodes, cap = nodes == 4 ? 512 : 1024;
                 int maxp = 1;
                 while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
@@ -889,7 +895,8 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
     if (h_choice) {
         h_choice[0] = c.fhn_ppc;
         h_choice[1] = c.resample_threads;
-        h_choice[2] = c.mp.kind == PF_MODEL_FHN_LATTICE ? (c.fhn_nodes ? c.fhn_nodes : (c.mp.J % 4 ? 2 : 4)) : 1;
+        h_choice[2] = c.mp.kind == PF_MODEL_FHN_LATTICE ? (c.fhn_nodes ? c.fhn_nodes : (c.mp.J % 4 ? 2 : 4))
+                      : (c.mp.kind == PF_MODEL_FHN_PAPER ? 2 : 1);
     }
     return PF_OK;
 }
@@ -923,9 +930,11 @@ pf_status pf_set_schedule(pf_ctx *h, int32_t nodes_per_thread, int32_t particles
     Ctx &c = h->c;
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_schedule between pf_propagate and pf_resample");
-    const bool lattice = c.mp.kind == PF_MODEL_FHN_LATTICE;
-    if (nodes_per_thread != 0 && !(lattice && (nodes_per_thread == 2 || (nodes_per_thread == 4 && c.mp.J % 4 == 0))))
-        return fail(c, PF_EINVAL, "nodes_per_thread: 0, 2, or 4 (lattice sides divisible by 4)");
+    const bool lattice = is_lattice(c.mp.kind);
+    if (nodes_per_thread != 0 &&
+        !(lattice && (nodes_per_thread == 2 ||
+                      (nodes_per_thread == 4 && c.mp.J % 4 == 0 && c.mp.kind == PF_MODEL_FHN_LATTICE))))
+        return fail(c, PF_EINVAL, "nodes_per_thread: 0, 2, or 4 (Rogers-McCulloch lattice, J divisible by 4)");
     if (particles_per_cta < 0 || (particles_per_cta > 0 && !lattice))
         return fail(c, PF_EINVAL, "particles_per_cta: 0, or >= 1 for the lattice");
     int max_len = 1;
@@ -957,7 +966,7 @@ pf_status pf_get_state(pf_ctx *h, float *h_x)
     if (st != PF_OK) return st;
     const int dx = c.mp.dx;
     const size_t n = (size_t)c.P * dx;
-    if (c.mp.kind == PF_MODEL_FHN_LATTICE) {
+    if (is_lattice(c.mp.kind)) {
         const cudaError_t e = cudaMemcpy(h_x, c.x[c.cur], n * sizeof(float), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
         return PF_OK;
@@ -979,7 +988,7 @@ pf_status pf_set_state(pf_ctx *h, const float *h_x, int32_t t)
     const int dx = c.mp.dx;
     const size_t n = (size_t)c.P * dx;
     cudaError_t e;
-    if (c.mp.kind == PF_MODEL_FHN_LATTICE) {
+    if (is_lattice(c.mp.kind)) {
         e = cudaMemcpy(c.x[c.cur], h_x, n * sizeof(float), cudaMemcpyHostToDevice);
     } else {
         std::vector<float> soa(n);

@@ -18,10 +18,14 @@ enum : uint32_t {
     kStreamDyn = 3u,
     kStreamResample = 4u,
     kStreamProposal = 5u,
-    kStreamMisc = 6u,
+    kStreamMisc = 6u,       // also the particles' random stimulus of the paper's lattice variant
+    kStreamStimTruth = 7u,  // the truth's random stimulus
 };
 
-enum ModelKind : int32_t { kLinearGaussian = 0, kLorenz63 = 1, kFhnLattice = 2 };
+enum ModelKind : int32_t { kLinearGaussian = 0, kLorenz63 = 1, kFhnLattice = 2, kFhnPaper = 3 };
+
+// Both lattices: particle-major state, node pairs, stencil kernels.
+__host__ __device__ __forceinline__ bool is_lattice(int32_t kind) { return kind == kFhnLattice || kind == kFhnPaper; }
 
 constexpr int kMaxLgDim = 4;
 constexpr int kMaxObsSmall = 8;  // observation indices passed by value for the small models
@@ -148,12 +152,13 @@ struct ModelParams {
     double sigma_dyn;
     double sigma0;
     double sigma_obs;
-    double p[16];          // LG: A row-major (dx <= 4); L63: s, r, b; FHN: a, b, c1, c2, d, D, amp, steps, block
+    double p[24];          // LG: A row-major (dx <= 4); L63: s, r, b; FHN: a, b, c1, c2, d, D, amp, steps, block;
+                           // the paper's lattice: the 17 values of pf.h
     int32_t dy;
     int32_t obs_small[kMaxObsSmall];  // observation indices when dy <= kMaxObsSmall
     double x0_small[kMaxLgDim];       // prior mean for the small models
     // FP32 copies made once on the host (FP64 is a narrow pipe on this GPU):
-    float fp[16];      // p
+    float fp[24];      // p
     float fdt;         // dt
     float fsq;         // sigma_dyn * sqrt(dt)
     float fhalf_prec;  // -1 / (2 sigma_obs^2)

@@ -110,6 +110,13 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t obs_strid
                              cudaStream_t s);
 cudaError_t launch_resample(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s);
 cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s);  // after the log-weights were replaced
+// The paper's own lattice variant (k_fhn_paper.cu): n_steps Euler steps of every
+// particle xi -> xo (xo null: not stored), weights into logw / fmax when non-null.
+cudaError_t launch_fhnp_interval(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
+                                 int32_t n_steps, float *logw, int32_t *fmax, AuxPtrs aux, int32_t noise,
+                                 cudaStream_t s);
+cudaError_t launch_fhnp_truth_step(const ModelParams &mp, Key key, int32_t record, int32_t t, const double *xi,
+                                   double *xo, cudaStream_t s);
 // One observation step of the ensemble of auxiliary particle filters (k_filter.cu).
 cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t obs_stride, cudaStream_t s);
 // Learned proposal (k_filter.cu, k_proposal.cu, k_mlp.cu).

@@ -25,8 +25,8 @@ from typing import List, Optional
 
 import numpy as np
 
-LG, LORENZ63, FHN = 0, 1, 2
-KIND_NAMES = {LG: "linear_gaussian", LORENZ63: "lorenz63", FHN: "fhn_lattice"}
+LG, LORENZ63, FHN, FHN_PAPER = 0, 1, 2, 3
+KIND_NAMES = {LG: "linear_gaussian", LORENZ63: "lorenz63", FHN: "fhn_lattice", FHN_PAPER: "fhn_paper_lattice"}
 
 # Philox stream identifiers, the last counter word's top byte (both sides use
 # these numbers; each side implements the generator itself).
@@ -106,6 +106,56 @@ def fhn_lattice(J: int = 40, K: int = 20, dt: float = 0.05, sigma: float = 0.01,
     return ModelSpec(kind=FHN, dx=dx, K=K, dt=dt, sigma_dyn=sigma, sigma0=sigma0, sigma_obs=sigma_obs,
                      params=params, x0_mean=[0.0] * dx, obs_idx=fhn_obs_nodes(J, obs_every), J=J,
                      truth_init_random=True)
+
+
+# The paper's own lattice (Sec. 5.1-5.2): p3(u) = -u (u + sqrt(18/5)) (u - sqrt(18/5)),
+# (b0, b1, b2) = (2.1, -0.6, 0.6), 1/D = 4.5e-3, T_d = 5e-3, forcing pulses of
+# amplitude 200 every 20 time units, random stimuli of amplitude 200 held for
+# l0 = 25 steps, thresholds (-1.8, -1.6), epsilon = 1e-3, noise variance 1/2 on
+# U, observation variance 1/2.  Readings where the text is silent or garbled:
+# the cubic's sign (as printed it makes U blow up), a 25-step forcing pulse on
+# the first column, the stimulus held while any event lies in the last l0 steps.
+FHNP_PARAMS = dict(a3=-1.0, a2=0.0, a1=18.0 / 5.0, a0=0.0, b0=2.1, b1=-0.6, b2=0.6, coupling=4.5e-3, F=200.0,
+                   period_steps=4000, width_steps=25, forced_cols=1, u_lo=-1.8, u_hi=-1.6, eps=1e-3,
+                   F_psi=200.0, l0=25)
+
+
+def fhnp_rest_state(p=FHNP_PARAMS):
+    """The node's resting point: p3(u) = v and b0 u + b1 v + b2 = 0 (the real root)."""
+    # p3(u) + (b0 u + b2) / b1 = 0
+    c = [p["a3"], p["a2"], p["a1"] + p["b0"] / p["b1"], p["a0"] + p["b2"] / p["b1"]]
+    roots = np.roots(c)
+    u = float(min(roots, key=lambda r: abs(r.imag)).real)
+    return u, -(p["b0"] * u + p["b2"]) / p["b1"]
+
+
+def fhnp_obs_nodes(J: int = 32, zones: int = 5, size: int = 2) -> List[int]:
+    """5 x 5 equally spaced zones of 2 x 2 nodes (Sec. 5.2, Fig. 3): zone corners at
+    offset + k * spacing, spacing = J / zones rounded down, centred."""
+    sp = J // zones
+    off = (J - sp * (zones - 1) - size) // 2
+    out = []
+    for a in range(zones):
+        for b in range(zones):
+            for di in range(size):
+                for dj in range(size):
+                    out.append((off + a * sp + di) * J + off + b * sp + dj)
+    return out
+
+
+def fhn_paper(J: int = 32, K: int = 1, dt: float = 5e-3, sigma: float = math.sqrt(0.5),
+              sigma_obs: float = math.sqrt(0.5), sigma0: float = 0.05, zones: int = 5, **over) -> ModelSpec:
+    p = dict(FHNP_PARAMS)
+    p.update(over)
+    params = [p["a3"], p["a2"], p["a1"], p["a0"], p["b0"], p["b1"], p["b2"], p["coupling"], p["F"],
+              float(p["period_steps"]), float(p["width_steps"]), float(p["forced_cols"]), p["u_lo"], p["u_hi"],
+              float(round(p["eps"] * (1 << 24))), p["F_psi"], float(p["l0"])]
+    u0, v0 = fhnp_rest_state(p)
+    nn = J * J
+    x0 = [u0] * nn + [v0] * nn + [float(p["l0"])] * nn
+    obs = fhnp_obs_nodes(J, zones) if J >= 2 * zones else list(range(nn))
+    return ModelSpec(kind=FHN_PAPER, dx=3 * nn, K=K, dt=dt, sigma_dyn=sigma, sigma0=sigma0, sigma_obs=sigma_obs,
+                     params=params, x0_mean=x0, obs_idx=obs, J=J, truth_init_random=True)
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,104 @@
+"""The paper's own stochastic FitzHugh-Nagumo lattice (Sec. 5.1-5.2) on the GPU
+against the FP64 oracle.
+
+* Prior and one observation interval from identical inputs: U and V within
+  1e-5 of max(|x|, rms); the stimulus counters S exactly (the random stimulus
+  is integer logic on the shared Philox words; with K = 1 its band test reads
+  the identical FP32 input, so even events decided at every step agree).
+* The FP64 truth records of both sides agree (stimulus events included).
+* Bootstrap and auxiliary filters: statistical parity with the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_8071_gb300 import pf, workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _ids(N, M):
+    pid = np.concatenate([np.arange(n) for n in np.broadcast_to(N, (M,))]).astype(np.int32)
+    fid = np.repeat(np.arange(M), np.broadcast_to(N, (M,))).astype(np.int32)
+    return pid, fid
+
+
+def _close(xg, xo, rtol=1e-5):
+    xg = np.asarray(xg, dtype=np.float64)
+    rms = np.sqrt(np.mean(xo ** 2, axis=0, keepdims=True))
+    err = np.abs(xg - xo) / np.maximum(np.maximum(np.abs(xo), rms), 1e-30)
+    assert err.max() <= rtol, (err.max(), np.unravel_index(np.argmax(err), err.shape))
+
+
+def _states(spec, n, seed, band_frac=0.1):
+    """Rest state plus noise; a fraction of U values inside the stimulus band, S mixed."""
+    rng = np.random.default_rng(seed)
+    nn = spec.J * spec.J
+    x = np.tile(np.asarray(spec.x0_mean), (n, 1))
+    x[:, :2 * nn] += rng.normal(0.0, 0.3, (n, 2 * nn))
+    band = rng.random((n, nn)) < band_frac
+    x[:, :nn][band] = rng.uniform(-1.79, -1.61, band.sum())
+    x[:, 2 * nn:] = rng.integers(0, 26, (n, nn))
+    return x.astype(np.float32)
+
+
+@pytest.mark.parametrize("J,M,N,eps", [(8, 3, 40, 0.0), (8, 2, 50, 1.0 - 2.0 ** -30), (32, 1, 3, 0.5), (6, 2, 7, 0.3)])
+def test_paper_lattice_prior_and_interval_match_oracle(J, M, N, eps):
+    spec = W.fhn_paper(J=J, zones=4 if J >= 8 else 1, eps=eps)
+    seed = 77
+    nn = J * J
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        pid, fid = _ids(N, M)
+        x_init = f.get_state()
+        xo0 = oracle.prior(spec, pid, fid, seed)
+        _close(x_init[:, :2 * nn], xo0[:, :2 * nn])
+        assert np.array_equal(x_init[:, 2 * nn:], xo0[:, 2 * nn:].astype(np.float32))
+        x0 = _states(spec, M * N, seed=J)
+        y = np.random.default_rng(J).normal(-1.0, 0.5, spec.dy).astype(np.float32)
+        for t in (1, 7):
+            f.set_state(x0, t - 1)
+            f.propagate(y)
+            xg = f.get_state()
+            xo = oracle.propagate(spec, x0.astype(np.float64), pid, fid, t, seed)
+            assert np.array_equal(xg[:, 2 * nn:], xo[:, 2 * nn:].astype(np.float32)), "stimulus counters differ"
+            _close(xg[:, :2 * nn], xo[:, :2 * nn])
+            lo = oracle.loglik(spec, xg.astype(np.float64), y.astype(np.float64))
+            assert np.max(np.abs(f.get_logw() - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+            f.resample()
+
+
+def test_paper_lattice_truth_record_matches_oracle():
+    spec = W.fhn_paper(J=8, zones=4, eps=0.05)
+    T, seed = 60, W.SEED_FHN_OBS
+    xg, yg = pf.pf_simulate(spec, T, seed, record=2)
+    xo, yo = oracle.simulate(spec, T, seed, record=2)
+    nn = 64
+    assert np.array_equal(xg[:, 2 * nn:], xo[:, 2 * nn:])
+    assert (xo[:, 2 * nn:] < 25).any(), "no stimulus event in the record"
+    assert np.max(np.abs(xg[:, :2 * nn] - xo[:, :2 * nn]) / (np.abs(xo[:, :2 * nn]) + 1.0)) <= 1e-9
+    assert np.max(np.abs(yg - yo.astype(np.float32)) / (np.abs(yo) + 1.0)) <= 1e-6
+
+
+@pytest.mark.parametrize("aux", [False, True])
+def test_paper_lattice_filters_match_oracle(aux):
+    spec = W.fhn_paper(J=8, zones=4, eps=0.02, K=2)
+    T = 10
+    _, y = oracle.simulate(spec, T, W.SEED_FHN_OBS)
+    y32 = y.astype(np.float32)
+    M, N, node = 96, 64, 9
+    est = np.empty((T, M))
+    with pf.EnsembleFilter(spec, M, N, 61) as f:
+        if aux:
+            f.set_auxiliary(True)
+        for t in range(T):
+            f.step(y32[t])
+            est[t] = f.estimate(pf.PF_STAT_MEAN, var=node, per_filter=True)
+    run = oracle.apf_run if aux else oracle.bf_run
+    eo = run(spec, M, N, T, y32.astype(np.float64), seed=62, est_idx=[node])["est"][:, :, 0]
+    for t in (0, 4, 9):
+        a, b = est[t], eo[t]
+        se = math.sqrt(a.var(ddof=1) / M + b.var(ddof=1) / M)
+        assert abs(a.mean() - b.mean()) <= 4.5 * se + 1e-9, (t, a.mean(), b.mean(), se)

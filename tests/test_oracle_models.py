@@ -212,3 +212,94 @@ def test_workload_constants_are_the_papers():
     assert spec.params == pytest.approx(vals["lorenz_s"] + vals["lorenz_r"] + vals["lorenz_b"], rel=1e-15)
     assert spec.x0_mean == vals["x_star"]
     assert spec.dt == vals["lorenz_dt"][0]
+
+
+# ------------------------------------------------------------ the paper's own lattice (Sec. 5.1-5.2)
+def _paper(J=4, **over):
+    base = dict(coupling=0.0, F=0.0, eps=0.0, F_psi=0.0)
+    base.update(over)
+    return W.fhn_paper(J=J, sigma=0.0, **base)
+
+
+def test_paper_lattice_rest_state_is_a_fixed_point():
+    """Uncoupled, unforced, unstimulated, noise-free: the resting point of
+    p3(u) = v, b0 u + b1 v + b2 = 0 does not move, and S stays at l0 (pins the
+    cubic's sign and the recovery equation)."""
+    spec = _paper()
+    x0 = np.array(spec.x0_mean)[None, :]
+    x = oracle.propagate(spec, x0, [0], [0], 1, seed=1)
+    for t in range(2, 40):
+        x = oracle.propagate(spec, x, [0], [0], t, seed=1)
+    assert np.allclose(x, x0, rtol=0, atol=1e-12)
+
+
+def test_paper_lattice_node_matches_the_ode():
+    """A single uncoupled node from (1, 0) follows du = p3(u) - v, dv = b0 u + b1 v + b2
+    (scipy's integrator) to first order in the step."""
+    from scipy.integrate import solve_ivp
+    p = W.FHNP_PARAMS
+    errs = []
+    for dt in (1e-3, 5e-4):
+        spec = _paper(J=2)
+        spec.dt = dt
+        nn = 4
+        x = np.array([1.0] * nn + [0.0] * nn + [25.0] * nn)[None, :]
+        steps = int(round(0.5 / dt))
+        for t in range(1, steps + 1):
+            x = oracle.propagate(spec, x, [0], [0], t, seed=1)
+
+        def rhs(_, s):
+            u, v = s
+            return [-u ** 3 + p["a1"] * u - v, p["b0"] * u + p["b1"] * v + p["b2"]]
+        ref = solve_ivp(rhs, (0.0, 0.5), [1.0, 0.0], rtol=1e-11, atol=1e-12).y[:, -1]
+        errs.append(max(abs(x[0, 0] - ref[0]), abs(x[0, nn] - ref[1])))
+    assert errs[0] < 5e-3 and 1.6 < errs[0] / errs[1] < 2.4, errs
+
+
+def test_paper_lattice_forcing_pulse_and_stimulus_hold():
+    """Forcing acts on the first column during the first `width` sub-steps of each
+    period; a stimulus counter started at 0 keeps Psi on for l0 - 1 more steps."""
+    spec = _paper(J=4, F=200.0, period_steps=30, width_steps=5, F_psi=200.0, l0=7)
+    nn = 16
+    u0, v0 = W.fhnp_rest_state()
+    x = np.array([u0] * nn + [v0] * nn + [7.0] * nn)
+    x[2 * nn + 5] = 0.0  # node (1, 1): S = 0
+    ref = np.array([u0] * nn + [v0] * nn + [7.0] * nn)
+    du_forced, du_psi = [], []
+    xs, rs = x[None, :], ref[None, :]
+    for t in range(1, 12):
+        xn = oracle.propagate(spec, xs, [0], [0], t, seed=1)
+        rn = oracle.propagate(_paper(J=4), rs, [0], [0], t, seed=1)  # nothing applied
+        du_forced.append(xn[0, 4] - xs[0, 4] - (rn[0, 4] - rs[0, 4]))   # node (1, 0): forced column
+        du_psi.append(xn[0, 5] - xs[0, 5] - (rn[0, 5] - rs[0, 5]))     # node (1, 1): stimulated
+        xs, rs = xn, rn
+    kick = 200.0 * spec.dt
+    forced = [abs(d - kick) < 0.3 * kick for d in du_forced]
+    assert forced[:5] == [True] * 5 and not any(forced[5:8])
+    held = [d > 0.5 * kick for d in du_psi]
+    assert held[:6] == [True] * 6 and not any(held[6:])
+    assert xs[0, 2 * nn + 5] == 7.0 and xs[0, 2 * nn + 0] == 7.0
+
+
+def test_paper_lattice_stimulus_picks_the_region_uniformly():
+    """One node in the band (u-, u+): the stimulus region is it and its neighbours;
+    with epsilon = 1 every step hits one of them, chosen uniformly (chi-square
+    over seeds), together with its neighbours (S restarts at 0 on a plus shape)."""
+    from scipy.stats import chisquare
+    J, nn = 8, 64
+    spec = _paper(J=J, eps=1.0 - 2.0 ** -30)
+    u0, v0 = W.fhnp_rest_state()
+    x = np.array([u0] * nn + [v0] * nn + [25.0] * nn)
+    i0, j0 = 3, 4
+    x[i0 * J + j0] = -1.7
+    region = [(i0, j0), (i0 - 1, j0), (i0 + 1, j0), (i0, j0 - 1), (i0, j0 + 1)]
+    counts = dict.fromkeys(region, 0)
+    R = 2000
+    for seed in range(R):
+        xn = oracle.propagate(spec, x[None, :], [0], [0], 1, seed=seed)[0]
+        zero = {(q // J, q % J) for q in range(nn) if xn[2 * nn + q] == 0.0}
+        centre = [c for c in region if zero == {c, (c[0] - 1, c[1]), (c[0] + 1, c[1]), (c[0], c[1] - 1),
+                                                (c[0], c[1] + 1)} & {(a, b) for a in range(J) for b in range(J)}]
+        assert len(centre) == 1, zero
+        counts[centre[0]] += 1
+    assert chisquare(list(counts.values())).pvalue > 1e-3, counts
