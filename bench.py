@@ -68,6 +68,14 @@ FHN_OPS_PER_NODE_STEP = 68
 # The auxiliary filter's noise-free look-ahead: Laplacian 4, drift 9 + 2,
 # two Euler updates 2 -> 17 per node-step.
 FHN_LOOKAHEAD_OPS_PER_NODE_STEP = 17
+# The paper's lattice per node-step: Philox 40 / 2 nodes (the U normal takes
+# half a Box-Muller pair's block) -> 20, Box-Muller pair / 2 -> 14.5,
+# neighbour sum 3 + coupling 1, cubic 3, drift of U 4 and V 2, stimulus
+# counter 2, two updates 2 -> 51.5 (look-ahead without the generator: 17).
+FHNP_OPS_PER_NODE_STEP = 51.5
+# With one Euler step per observation the auxiliary step on the paper's lattice
+# moves each particle's state six times (see the roofline below).
+FHNP_STATE_PASSES = 6
 
 
 def env_int(name, default):
@@ -157,6 +165,9 @@ WORKLOAD_TEXT = {
     "fhn": "fhn 40x40 lattice (3200 variables), M=32 x N=1024, K=20, bootstrap proposal",
     "fhn-learned": "fhn 40x40 lattice, M=32 x N=1024, K=20, learned proposal (network trained untimed)",
     "fhn-apf": "fhn 40x40 lattice, M=32 x N=1024, K=20, auxiliary particle filters (the paper's Sec. 5.3 filter)",
+    "fhn-paper": ("the paper's own 32x32 FitzHugh-Nagumo lattice with random re-entry stimuli (3072 variables), "
+                  "M=10 x N=5000 auxiliary particle filters, one Euler step per observation (the paper's Sec. 5.3 "
+                  "set-up)"),
     "ragged": ("256 fhn 20x20 lattices, N log-uniform in [64, 4096], independent records, learned proposal, "
                "one autotuned context (all filters in each launch, CUDA graph)"),
 }
@@ -179,6 +190,10 @@ class Workload:
             self.spec = W.fhn_lattice()
             self.rows = [(W.FHN_FULL["M"], W.FHN_FULL["N"])]
             rec_seed, T = W.SEED_FHN_OBS, W.FHN_FULL["T"]
+        elif name == "fhn-paper":
+            self.spec = W.fhn_paper()
+            self.rows = [(10, 5000)]
+            rec_seed, T = W.SEED_FHN_OBS, 400
         elif name == "ragged":
             self.spec = W.fhn_lattice(J=W.RAGGED["J"])
             self.N_list = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
@@ -199,7 +214,7 @@ class Workload:
         self.y_dev = self.y_host.cuda()
         torch.cuda.synchronize()
         self.theta = None
-        self.aux = name == "fhn-apf"
+        self.aux = name in ("fhn-apf", "fhn-paper")
         if name in ("fhn-learned", "ragged"):
             self.theta = proposal.trained_theta(self.spec, train_record[:20], seed=seed_base + 77)
         # one stream per context: the configurations are independent, so their
@@ -211,7 +226,7 @@ class Workload:
             f.set_stream(st.cuda_stream)
             if self.theta is not None:
                 f.set_proposal(self.theta, 0.1)
-            if self.spec.kind == W.FHN:
+            if self.spec.kind in (W.FHN, W.FHN_PAPER):
                 self.choice = f.autotune()
             if self.aux:
                 f.set_auxiliary(True)
@@ -224,7 +239,7 @@ class Workload:
         # replaces the propagate by sub-steps, network rows, network forward, last step and select
         if self.aux:  # fill, look-ahead, weights, scan, ancestors, gather, propagate, stats, means, ensemble
             self.kernels_per_filter_step = 10
-        elif self.spec.kind == W.FHN:
+        elif self.spec.kind in (W.FHN, W.FHN_PAPER):
             self.kernels_per_filter_step = 7 + (4 if self.theta is not None else 0)
         else:
             self.kernels_per_filter_step = 5
@@ -374,6 +389,9 @@ def oracle_case(workload: str, M: int, n_scale: int, T: int, theta=None):
             from paper_1407_8071_gb300 import proposal
             theta = proposal.initial_theta(1)
         return spec, M, max(2, 8 // n_scale), y, False, theta
+    if workload == "fhn-paper":
+        spec = W.fhn_paper()
+        return spec, M, max(4, 40 // n_scale), oracle.simulate(spec, T, W.SEED_FHN_OBS)[1], False, None
     spec = W.fhn_lattice(J=W.RAGGED["J"])
     counts = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
     N = np.maximum(1, counts[:M] // (16 * n_scale))  # the first M filters' counts, scaled down
@@ -401,12 +419,12 @@ def oracle_sample(workload: str, target_s: float, theta=None):
     """Times the FP64 oracle on a bounded sample of the workload; returns
     (particle-steps/s, threads, sample description)."""
     cores = os.cpu_count() or 1
-    M = min(64 if workload == "lorenz-sweep" else 32, 2 * cores)
-    Tmax = 200 if workload == "lorenz-sweep" else 6
+    M = min(64 if workload == "lorenz-sweep" else (10 if workload == "fhn-paper" else 32), 2 * cores)
+    Tmax = 200 if workload == "lorenz-sweep" else (40 if workload == "fhn-paper" else 6)
     case = oracle_case(workload, M, 1, Tmax, theta)
     threads = min(M, cores)
     t0 = time.perf_counter()
-    aux = workload == "fhn-apf"
+    aux = workload in ("fhn-apf", "fhn-paper")
     oracle_run(case, 1, 1, threads, aux)
     dt1 = time.perf_counter() - t0
     T = int(max(1, min(Tmax, round(target_s / max(dt1, 1e-3)))))
@@ -430,11 +448,11 @@ def run_reference(args):
     case = oracle_case(args.workload, M, 4, 2)
     threads = min(M, cores)
     for k in range(args.warmup):
-        oracle_run(case, 1, 3 + k, threads, args.workload == "fhn-apf")
+        oracle_run(case, 1, 3 + k, threads, args.workload in ("fhn-apf", "fhn-paper"))
     t0 = time.perf_counter()
     work = 0
     for k in range(args.steps):
-        work += oracle_run(case, 1, 100 + k, threads, args.workload == "fhn-apf")
+        work += oracle_run(case, 1, 100 + k, threads, args.workload in ("fhn-apf", "fhn-paper"))
     dt = time.perf_counter() - t0
     value = work / dt
     spec, _, N, _, _, th = case
@@ -470,7 +488,8 @@ def run_study(args):
     train_record = pf.pf_simulate(spec, 20, W.SEED_FHN_OBS, record=1)[1]  # not the scored record
     theta = proposal.trained_theta(spec, train_record, seed=77)
     lat = study.lattice_time_to_mse(theta, log=log)
-    line = {"study": "mse", "data": "synthetic", "lorenz_sweep": lor, "lattice": lat,
+    paper = study.paper_lattice_mse(log=log)
+    line = {"study": "mse", "data": "synthetic", "lorenz_sweep": lor, "lattice": lat, "paper_lattice": paper,
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line))
     return 0
@@ -546,9 +565,20 @@ def main():
                     "traffic": recorded_traffic("k_propagate_small<3>"),
                     "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
                     "ops_per_particle_step": LORENZ_OPS_PER_PARTICLE_STEP, "avg_launch_s": t_prop}
+    elif wl.spec.kind == W.FHN_PAPER:
+        # one Euler step per observation: the step streams the state six times (look-ahead read,
+        # gather read + write, second-stage read + write, weighted means read), so HBM bounds it
+        hbm = float(peaks["hbm_gbs"])
+        per_launch_bytes = (wl.particles / nf) * wl.spec.dx * 4 * FHNP_STATE_PASSES
+        achieved = per_launch_bytes / t_prop / 1e9
+        roofline = {"bound": "hbm", "kernel": "auxiliary step (look-ahead, resampling + gather, second stage, means)",
+                    "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "peak_source": f"{peak_src} copy bandwidth", "bytes_per_particle_step": wl.spec.dx * 4 *
+                    FHNP_STATE_PASSES, "avg_launch_s": t_prop}
     else:
         alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-        ops_node = FHN_OPS_PER_NODE_STEP + (FHN_LOOKAHEAD_OPS_PER_NODE_STEP if wl.aux else 0)
+        base_ops = FHN_OPS_PER_NODE_STEP
+        ops_node = base_ops + (FHN_LOOKAHEAD_OPS_PER_NODE_STEP if wl.aux else 0)
         per_launch_ops = (wl.particles / nf) * wl.spec.K * wl.spec.J * wl.spec.J * ops_node
         achieved = per_launch_ops / t_prop / 1e12
         kern = ("k_propagate_fhn<float>" if wl.theta is None else "proposal propagate (5 kernels)") if not wl.aux \

@@ -194,3 +194,36 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
             "learned_s_at_target": time_at(out["learned"], target),
             "auxiliary_s_at_target": time_at(out["auxiliary"], target),
             "centralised_s_at_target": time_at(out["centralised"], target)}
+
+
+def paper_lattice_mse(Ns=(100, 500, 1000, 2000, 5000), M: int = 10, records=(0, 1, 2, 3), T: int = 200,
+                      skip: int = 20, log=None):
+    """The paper's Sec. 5.3 experiment on its own lattice (32 x 32, random
+    re-entry stimuli), synthetic records: empirical MSE per node of the
+    posterior-mean U against the true U, for an ensemble of M auxiliary
+    filters with N particles each and for the centralised auxiliary filter
+    with K = M N particles, averaged over the records; device time per step."""
+    import torch
+    spec = W.fhn_paper()
+    nn = spec.J * spec.J
+    rows = {"ensemble": [], "centralised": []}
+    for N in Ns:
+        for name, m_run, n_run in (("ensemble", M, N), ("centralised", 1, M * N)):
+            errs = []
+            for r in records:
+                x, y = pf.pf_simulate(spec, T, W.SEED_FHN_OBS, record=r)
+                d_y = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+                with pf.EnsembleFilter(spec, m_run, n_run, 4000 + 17 * r + N) as f:
+                    f.set_auxiliary(True)
+                    for t in range(T):
+                        f.step_device(d_y[t])
+                        if t >= skip:
+                            u = f.estimate(pf.PF_STAT_MEAN, var=-1)[:nn]
+                            errs.append(np.mean((u - x[t + 1, :nn]) ** 2))
+            dt = step_time(spec, m_run, n_run, d_y, aux=True)
+            rows[name].append({"M": m_run, "N": n_run, "mse_per_node": float(np.mean(errs)), "s_per_step": dt})
+            if log:
+                log(f"paper lattice {name:11s} M={m_run:3d} N={n_run:6d}  MSE/node {np.mean(errs):.4f}  "
+                    f"{dt * 1e3:.3f} ms/step")
+    return {"workload": "paper's 32x32 lattice, auxiliary filters", "M": M, "records": len(records), "T": T,
+            "skip": skip, "rows": rows}
