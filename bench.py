@@ -162,6 +162,9 @@ def recorded_traffic(kernel: str):
 WORKLOAD_TEXT = {
     "lorenz-sweep": ("lorenz63 ensemble, M*N = 2^20 swept over M in {1,4,16,64,256,1024,4096}, all seven "
                      "resident; one step = one observation (K=40 Euler-Maruyama sub-steps) of each"),
+    "lorenz-sweep-1ctx": ("lorenz63 ensemble, the seven M*N = 2^20 configurations of the sweep (M in {1,4,16,64,256,"
+                          "1024,4096}) as one ragged batch of 5461 filters in one context: every kernel launch covers "
+                          "all of them, one CUDA graph per step (K=40 sub-steps)"),
     "fhn": "fhn 40x40 lattice (3200 variables), M=32 x N=1024, K=20, bootstrap proposal",
     "fhn-learned": "fhn 40x40 lattice, M=32 x N=1024, K=20, learned proposal (network trained untimed)",
     "fhn-apf": "fhn 40x40 lattice, M=32 x N=1024, K=20, auxiliary particle filters (the paper's Sec. 5.3 filter)",
@@ -185,6 +188,11 @@ class Workload:
         if name == "lorenz-sweep":
             self.spec = W.lorenz63()
             self.rows = W.lorenz_sweep()
+            rec_seed, T = W.SEED_LORENZ_OBS, 200
+        elif name == "lorenz-sweep-1ctx":
+            self.spec = W.lorenz63()
+            self.N_list = np.concatenate([np.full(M, N, dtype=np.int32) for M, N in W.lorenz_sweep()])
+            self.rows = [(len(self.N_list), self.N_list)]
             rec_seed, T = W.SEED_LORENZ_OBS, 200
         elif name in ("fhn", "fhn-learned", "fhn-apf"):
             self.spec = W.fhn_lattice()
@@ -226,8 +234,7 @@ class Workload:
             f.set_stream(st.cuda_stream)
             if self.theta is not None:
                 f.set_proposal(self.theta, 0.1)
-            if self.spec.kind in (W.FHN, W.FHN_PAPER):
-                self.choice = f.autotune()
+            self.choice = f.autotune()
             if self.aux:
                 f.set_auxiliary(True)
             self.filters.append(f)
@@ -379,7 +386,7 @@ def resample_roofline(wl, t_res, peaks, peak_src):
 def oracle_case(workload: str, M: int, n_scale: int, T: int, theta=None):
     """A bounded sample of `workload` for the FP64 oracle: (spec, M, N, y, per-filter obs, theta)."""
     import oracle
-    if workload == "lorenz-sweep":  # filters of the M = 64, N = 16384 row of the sweep
+    if workload.startswith("lorenz-sweep"):  # filters of the M = 64, N = 16384 row of the sweep
         spec = W.lorenz63()
         return spec, M, (1 << 14) // n_scale, oracle.simulate(spec, T, W.SEED_LORENZ_OBS)[1], False, None
     if workload in ("fhn", "fhn-learned", "fhn-apf"):
@@ -419,8 +426,8 @@ def oracle_sample(workload: str, target_s: float, theta=None):
     """Times the FP64 oracle on a bounded sample of the workload; returns
     (particle-steps/s, threads, sample description)."""
     cores = os.cpu_count() or 1
-    M = min(64 if workload == "lorenz-sweep" else (10 if workload == "fhn-paper" else 32), 2 * cores)
-    Tmax = 200 if workload == "lorenz-sweep" else (40 if workload == "fhn-paper" else 6)
+    M = min(64 if workload.startswith("lorenz-sweep") else (10 if workload == "fhn-paper" else 32), 2 * cores)
+    Tmax = 200 if workload.startswith("lorenz-sweep") else (40 if workload == "fhn-paper" else 6)
     case = oracle_case(workload, M, 1, Tmax, theta)
     threads = min(M, cores)
     t0 = time.perf_counter()
@@ -604,7 +611,7 @@ def main():
                                                          "nodes_per_thread": wl.choice[2]},
             "precision": "FP32 state and propagation; FP64 normaliser, prefix sum and M-average",
             "l2": ("working set of the seven contexts (~340 MB) exceeds the 129 MB L2; each context's data "
-                   "is evicted by the other six between its steps") if args.workload == "lorenz-sweep"
+                   "is evicted by the other six between its steps") if args.workload.startswith("lorenz-sweep")
             else f"state {wl.particles * wl.spec.dx * 4 / 1e6:.0f} MB per buffer, larger than L2",
         },
         "clocks": clocks,
@@ -616,7 +623,7 @@ def main():
         "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src) if t_res > 0 else None,
     }
     theta = wl.theta
-    if wl.N_list is not None:
+    if wl.name == "ragged":
         line["separate_contexts"] = separate_contexts(torch, wl, max(1, args.steps // 4))
     wl.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
