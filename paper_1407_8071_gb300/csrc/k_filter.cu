@@ -269,7 +269,9 @@ __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
     g.N = N;
     const int bits = 64 - __clzll((long long)(Ctot | 1));
     g.est_shift = bits > 24 ? bits - 24 : 0;
-    g.est_scale = (float)((double)N * (double)(1ull << g.est_shift) / (double)(Ctot ? Ctot : 1));
+    // only a starting point for the exact walk: FP32 is enough (and FP64 division would
+    // cost every thread of the scan a slow FP64 sequence)
+    g.est_scale = (float)N * (float)(1ull << g.est_shift) / (float)(Ctot ? Ctot : 1);
     g.u = __uint2float_rn(U) * 0x1p-32f;
     return g;
 }
@@ -305,19 +307,6 @@ __device__ int64_t count_below(uint64_t x, const Grid &g)
         i = lo;
     }
     return i;
-}
-
-// a_i0 = min{k : C_k > t_i0}, by bisection over the filter's prefix (every
-// i0 < N has one, since t_i0 < C_{N-1}).
-__device__ int32_t search_ancestor(const uint64_t *C, const Grid &g, int64_t i0)
-{
-    const U128 T = grid_point((uint64_t)i0, g.U, g.Ctot);
-    int64_t lo = 0, hi = g.N - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (!ge128(T, scaled_C(C[mid], (uint64_t)g.N))) hi = mid; else lo = mid + 1;  // C_mid N 2^32 > T
-    }
-    return (int32_t)lo;
 }
 
 // Unnormalised FP32 weight exp(l - max) from the FP32 log-weight; non-finite
@@ -833,22 +822,27 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
         a.C[td.gstart + j] = Ck;
         if (q[r] > 0) {
             const int64_t cnt = count_below(Ck, g);
-            if (cnt > cnt_prev) a.B[fd.off + cnt_prev] = td.lstart + j;
+            if (cnt > cnt_prev) {
+                a.B[fd.off + cnt_prev] = td.lstart + j;
+                // the outputs [cnt_prev, cnt) descend from this particle: it is the first
+                // ancestor of every output tile that starts in that range (one writer each)
+                for (int64_t o = (cnt_prev + kTile - 1) / kTile * kTile; o < cnt; o += kTile)
+                    a.tile_anc0[fd.tile_begin + o / kTile] = td.lstart + j;
+            }
             cnt_prev = cnt;
         }
         Cprev = Ck;
     }
 }
 
-// a_i = max(first ancestor of the tile, max of the markers B[i0..i]).
+// a_i = max(first ancestor of the tile, max of the markers B[i0..i]); the
+// first ancestor comes from the scan (the particle whose offspring range
+// holds the tile's first output).
 __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const TileDesc &td, const FilterDesc &fd,
                                                int32_t (&anc)[kItems], int *shi)
 {
-    Grid g;
-    g.Ctot = a.fint[(int64_t)td.m * 2];
-    g.U = (uint32_t)a.fint[(int64_t)td.m * 2 + 1];
-    g.N = fd.N;
-    const int32_t a0 = search_ancestor(a.C + fd.off, g, td.lstart);
+    (void)fd;
+    const int32_t a0 = a.tile_anc0[blockIdx.x];
     const int j0 = threadIdx.x * kItems;
     int b[kItems];
     int tmax = -1;
@@ -1098,9 +1092,9 @@ __global__ void __launch_bounds__(kResampleThreads)
 // Definition 1: ens[v] = (1/M) sum_m est[m][v] in FP64, one CTA per variable,
 // strided partial sums then a fixed-order tree (deterministic); advances the
 // step counter.
-__global__ void __launch_bounds__(128) k_ensemble(const double *est, int dx, int32_t M, double *ens, int32_t *d_t)
+__global__ void __launch_bounds__(1024) k_ensemble(const double *est, int dx, int32_t M, double *ens, int32_t *d_t)
 {
-    __shared__ double sh[128 + 1];
+    __shared__ double sh[1024 + 1];
     const int v = blockIdx.x;
     double s[1] = {0.0};
     for (int m = threadIdx.x; m < M; m += blockDim.x) s[0] += est[(int64_t)m * dx + v];
@@ -1238,6 +1232,14 @@ cudaError_t propagate_small_launch(const Ctx &c, const float *d_obs, int32_t str
     return cudaGetLastError();
 }
 
+// Threads of the M-average: enough to have a few filters each, 32..1024.
+int ensemble_threads(int32_t M)
+{
+    int th = 32;
+    while (th < 1024 && th * 8 < M) th *= 2;
+    return th;
+}
+
 ResampleArgs ctx_args(const Ctx &c)
 {
     ResampleArgs a{};
@@ -1254,6 +1256,7 @@ ResampleArgs ctx_args(const Ctx &c)
     a.C = c.C;
     a.B = c.B;
     a.anc = c.anc;
+    a.tile_anc0 = c.tile_anc0;
     a.err = c.err;
     a.done = c.done;
     a.log_const = -0.5 * c.mp.dy * log(2.0 * M_PI * c.mp.sigma_obs * c.mp.sigma_obs);
@@ -1405,7 +1408,7 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
         }
         if (e != cudaSuccess) return e;
     }
-    k_ensemble<<<dx, 128, 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
+    k_ensemble<<<dx, ensemble_threads(c.M), 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
     return cudaGetLastError();
 }
 
@@ -1431,7 +1434,7 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
         default: return cudaErrorInvalidValue;
         }
     }
-    k_ensemble<<<dx, 128, 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
+    k_ensemble<<<dx, ensemble_threads(c.M), 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
     return cudaGetLastError();
 }
 

@@ -475,7 +475,8 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
               alloc_n(c, c.tile_sums, (size_t)c.n_tiles * kTsCount) &&
               alloc_n(c, c.tile_q, c.n_tiles) && alloc_n(c, c.fint, (size_t)M * 2) &&
               alloc_n(c, c.fstats, (size_t)M * kFsCount) && alloc_n(c, c.C, P) && alloc_n(c, c.B, P) &&
-              alloc_n(c, c.anc, P) && alloc_n(c, c.est, (size_t)M * dx) && alloc_n(c, c.ens, dx) &&
+              alloc_n(c, c.anc, P) && alloc_n(c, c.tile_anc0, (size_t)c.n_tiles) &&
+              alloc_n(c, c.est, (size_t)M * dx) && alloc_n(c, c.ens, dx) &&
               alloc_n(c, c.d_obs, (size_t)M * mp.dy) && alloc_n(c, c.d_t, 1) && alloc_n(c, c.err, 2) &&
               alloc_n(c, c.obs_idx, mp.dy) && alloc_n(c, c.x0, dx);
     if (ok) ok = alloc_n(c, c.pfilt, P);
@@ -1061,7 +1062,8 @@ size_t pf_systematic_scratch_bytes(int32_t M, int64_t total)
     return align256(nt * sizeof(TileDesc)) + align256((size_t)M * sizeof(FilterDesc)) +
            align256(nt * kTsCount * sizeof(double)) + align256(nt * sizeof(uint64_t)) +
            align256((size_t)M * kFsCount * sizeof(double)) + align256((size_t)M * 2 * sizeof(uint64_t)) +
-           align256(total * sizeof(uint64_t)) + align256(total * sizeof(int32_t)) + align256(2 * sizeof(int32_t));
+           align256(total * sizeof(uint64_t)) + align256(total * sizeof(int32_t)) + align256(2 * sizeof(int32_t)) +
+           align256(nt * sizeof(int32_t));
 }
 
 pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_w, const double *d_u, int32_t *d_anc,
@@ -1093,6 +1095,7 @@ pf_status pf_systematic_resample(int32_t M, const int32_t *h_N, const double *d_
     a.C = reinterpret_cast<uint64_t *>(take(total * sizeof(uint64_t)));
     a.B = reinterpret_cast<int32_t *>(take(total * sizeof(int32_t)));
     a.err = reinterpret_cast<int32_t *>(take(2 * sizeof(int32_t)));
+    a.tile_anc0 = reinterpret_cast<int32_t *>(take(nt * sizeof(int32_t)));
     a.w_direct = d_w;
     a.u_direct = d_u;
     a.anc = d_anc;

@@ -86,6 +86,7 @@ struct ResampleArgs {
     uint64_t *C;             // [P] inclusive prefix of the quantised weights
     int32_t *B;              // [P] ancestor start markers
     int32_t *anc;            // [P] filter-local ancestors
+    int32_t *tile_anc0;      // [tiles] ancestor of each tile's first output (written by the scan)
     int32_t *err;            // [2]
     double log_const;        // -dy/2 log(2 pi sigma_obs^2), added to log G only
     int32_t *done;           // [M] per-filter completion counters, kept at 0 between steps
@@ -183,6 +184,7 @@ struct Ctx {
     uint64_t *C = nullptr;
     int32_t *B = nullptr;
     int32_t *anc = nullptr;
+    int32_t *tile_anc0 = nullptr; // [tiles]
     double *tile_est = nullptr;   // [tiles][dx] (small models)
     double *est = nullptr;        // [M][dx]
     double *ens = nullptr;        // [dx]

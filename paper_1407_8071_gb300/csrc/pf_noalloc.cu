@@ -19,8 +19,8 @@ constexpr int64_t kNoallocMaxParticles = PF_NOALLOC_MAX_PARTICLES;
 
 // Scratch of pf_systematic_resample for the largest problem accepted
 // (about 3.3 MB; every GPU that loads the library holds it until exit):
-// tile plan, per-tile and per-filter sums, the 64-bit prefix and the
-// ancestor markers.
+// tile plan, per-tile and per-filter sums, the 64-bit prefix, the
+// ancestor markers and each tile's first ancestor.
 constexpr size_t kTilesMax = kNoallocMaxFilters + kNoallocMaxParticles / pf::kTile + 1;
 constexpr size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kScratchBytes =
@@ -28,7 +28,7 @@ constexpr size_t kScratchBytes =
     a256(kTilesMax * pf::kTsCount * sizeof(double)) +
     a256(kTilesMax * sizeof(uint64_t)) + a256(kNoallocMaxFilters * pf::kFsCount * sizeof(double)) +
     a256(kNoallocMaxFilters * 2 * sizeof(uint64_t)) + a256(kNoallocMaxParticles * sizeof(uint64_t)) +
-    a256(kNoallocMaxParticles * sizeof(int32_t)) + a256(2 * sizeof(int32_t));
+    a256(kNoallocMaxParticles * sizeof(int32_t)) + a256(2 * sizeof(int32_t)) + a256(kTilesMax * sizeof(int32_t));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
