@@ -1,12 +1,15 @@
 """Throughput benchmark of the GPU ensemble particle filter.
 
 Workload (default): the Lorenz 63 ensemble with a total budget of M * N = 2^20
-particles swept over M in {1, 4, 16, 64, 256, 1024, 4096}, N = 2^20 / M, all
-seven configurations resident on the GPU.  One bench step is one observation
-time of all seven: for each configuration K = 40 Euler-Maruyama sub-steps of
-every particle, Gaussian weights, FP64 normalisation, systematic resampling
-with the gather, and the per-filter and ensemble means.  The metric is
-particle-steps/s (one Euler-Maruyama sub-step of one particle).
+particles swept over M in {1, 4, 16, 64, 256, 1024, 4096}, N = 2^20 / M; the
+seven configurations (5461 filters, 7 x 2^20 particles) run as one ragged batch
+in one context, so every launch covers all of them and each step is one CUDA
+graph.  One bench step is one observation time: K = 40 Euler-Maruyama
+sub-steps of every particle, Gaussian weights, FP64 normalisation, systematic
+resampling with the gather, and the per-filter and ensemble means.  The metric
+is particle-steps/s (one Euler-Maruyama sub-step of one particle).
+`--workload lorenz-sweep-7ctx` runs the seven configurations as seven contexts
+on seven streams instead.
 
 `--workload fhn` runs the 40 x 40 FitzHugh-Nagumo lattice at M = 32, N = 1024;
 `--workload fhn-learned` the same with the learned proposal (network trained,
@@ -160,11 +163,11 @@ def recorded_traffic(kernel: str):
 # Workloads
 # ---------------------------------------------------------------------------
 WORKLOAD_TEXT = {
-    "lorenz-sweep": ("lorenz63 ensemble, M*N = 2^20 swept over M in {1,4,16,64,256,1024,4096}, all seven "
-                     "resident; one step = one observation (K=40 Euler-Maruyama sub-steps) of each"),
-    "lorenz-sweep-1ctx": ("lorenz63 ensemble, the seven M*N = 2^20 configurations of the sweep (M in {1,4,16,64,256,"
-                          "1024,4096}) as one ragged batch of 5461 filters in one context: every kernel launch covers "
-                          "all of them, one CUDA graph per step (K=40 sub-steps)"),
+    "lorenz-sweep": ("lorenz63 ensemble, the seven M*N = 2^20 configurations of the sweep (M in {1,4,16,64,256,"
+                     "1024,4096}) as one ragged batch of 5461 filters in one context: every kernel launch covers "
+                     "all of them, one CUDA graph per step (one observation, K=40 Euler-Maruyama sub-steps)"),
+    "lorenz-sweep-7ctx": ("lorenz63 ensemble, M*N = 2^20 swept over M in {1,4,16,64,256,1024,4096}, the seven "
+                          "configurations as seven contexts on seven streams; one step = one observation of each"),
     "fhn": "fhn 40x40 lattice (3200 variables), M=32 x N=1024, K=20, bootstrap proposal",
     "fhn-learned": "fhn 40x40 lattice, M=32 x N=1024, K=20, learned proposal (network trained untimed)",
     "fhn-apf": "fhn 40x40 lattice, M=32 x N=1024, K=20, auxiliary particle filters (the paper's Sec. 5.3 filter)",
@@ -185,11 +188,11 @@ class Workload:
         self.per_filter_obs = False
         self.choice = None
         self.N_list = None
-        if name == "lorenz-sweep":
+        if name == "lorenz-sweep-7ctx":
             self.spec = W.lorenz63()
             self.rows = W.lorenz_sweep()
             rec_seed, T = W.SEED_LORENZ_OBS, 200
-        elif name == "lorenz-sweep-1ctx":
+        elif name == "lorenz-sweep":
             self.spec = W.lorenz63()
             self.N_list = np.concatenate([np.full(M, N, dtype=np.int32) for M, N in W.lorenz_sweep()])
             self.rows = [(len(self.N_list), self.N_list)]
@@ -610,8 +613,8 @@ def main():
                                                          "resample_threads": wl.choice[1],
                                                          "nodes_per_thread": wl.choice[2]},
             "precision": "FP32 state and propagation; FP64 normaliser, prefix sum and M-average",
-            "l2": ("working set of the seven contexts (~340 MB) exceeds the 129 MB L2; each context's data "
-                   "is evicted by the other six between its steps") if args.workload.startswith("lorenz-sweep")
+            "l2": ("working set of the seven configurations (~340 MB: state 2 x 88 MB, prefix 59 MB, ...) exceeds "
+                   "the 129 MB L2") if args.workload.startswith("lorenz-sweep")
             else f"state {wl.particles * wl.spec.dx * 4 / 1e6:.0f} MB per buffer, larger than L2",
         },
         "clocks": clocks,

@@ -259,7 +259,15 @@ struct Grid {
     int est_shift;  // the estimate uses x >> est_shift (< 2^24, exact in FP32)
     float est_scale;  // N 2^est_shift / Ctot
     float u;        // U 2^-32
+    float Nf;       // N (<= 2^24, exact)
 };
+
+// A 64-bit unsigned value as FP32 from its two 32-bit halves: 64-bit integer
+// conversions run on the narrow FP64 pipe of this GPU, 32-bit ones do not.
+__device__ __forceinline__ float u64_to_f32(uint64_t v)
+{
+    return __fmaf_rn(__uint2float_rn((uint32_t)(v >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)v));
+}
 
 __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
 {
@@ -271,7 +279,8 @@ __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
     g.est_shift = bits > 24 ? bits - 24 : 0;
     // only a starting point for the exact walk: FP32 is enough (and FP64 division would
     // cost every thread of the scan a slow FP64 sequence)
-    g.est_scale = (float)N * (float)(1ull << g.est_shift) / (float)(Ctot ? Ctot : 1);
+    g.Nf = __int2float_rn((int32_t)N);
+    g.est_scale = g.Nf * __int_as_float((127 + g.est_shift) << 23) / u64_to_f32(Ctot ? Ctot : 1);
     g.u = __uint2float_rn(U) * 0x1p-32f;
     return g;
 }
@@ -285,7 +294,7 @@ __device__ int64_t count_below(uint64_t x, const Grid &g)
     const U128 X = scaled_C(x, (uint64_t)g.N);
     const float xf = __uint2float_rn((uint32_t)(x >> g.est_shift));
     const float est = ceilf(__fmaf_rn(xf, g.est_scale, -g.u));
-    int64_t i = est <= 0.0f ? 0 : (est >= (float)g.N ? g.N : (int64_t)__float2int_rz(est));
+    int64_t i = est <= 0.0f ? 0 : (est >= g.Nf ? g.N : (int64_t)__float2int_rz(est));
     bool settled = false;
     for (int it = 0; it < 4; ++it) {
         if (i > 0 && ge128(grid_point((uint64_t)(i - 1), g.U, g.Ctot), X)) --i;
@@ -428,7 +437,7 @@ __global__ void __launch_bounds__(kPropThreads, 16)
 // neighbour read is a conflict-free 2-word load; a missing neighbour (zero
 // flux) reads the node itself, which turns sum_existing(v_n) - count v into
 // sum_4(v_n) - 4 v.
-template <typename Real>
+template <typename Real, bool Noise = true>
 __global__ void __launch_bounds__(1024, 2)
     k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const int32_t *pfilt, const FilterDesc *filt,
                     const Real *__restrict__ x_in, Real *__restrict__ x_out, int64_t P, float *logw, const float *obs,
@@ -438,6 +447,7 @@ __global__ void __launch_bounds__(1024, 2)
 {
     using Pair = typename std::conditional<std::is_same<Real, float>::value, float2, double2>::type;
     extern __shared__ unsigned char smem_raw[];
+    (void)noise;  // the template parameter Noise decides
     const int J = mp.J, nn = J * J, pairs = nn / 2, half = J / 2;
     Pair *sv = reinterpret_cast<Pair *>(smem_raw);  // [2][ppc][pairs]
     const int slot = (int)threadIdx.x / pairs;
@@ -488,8 +498,12 @@ __global__ void __launch_bounds__(1024, 2)
         }
         __syncthreads();
         if (active) {
-            Real z[4] = {(Real)0, (Real)0, (Real)0, (Real)0};
-            if (noise) normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
+            Real z[4];
+            if (Noise) {
+                normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
+            } else {
+                z[0] = z[1] = z[2] = z[3] = (Real)0;
+            }
             const Pair up = buf[qu], dn = buf[qd], lf = buf[ql], rt = buf[qr];
             const Real left = has_left ? lf.y : v0, right = has_right ? rt.x : v1;
             Real l0, l1;
@@ -556,6 +570,7 @@ __global__ void __launch_bounds__(1024, 2)
 // two generator chains interleave.
 constexpr int kFhn4MaxThreads = 512;  // three CTAs per SM at <= 42 registers
 
+template <bool Noise = true>
 __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
     k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
                      const float *__restrict__ x_in, float *__restrict__ x_out, int64_t P, float *logw,
@@ -563,6 +578,7 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
                      int32_t *fmax_key, int32_t n_steps, AuxPtrs aux, int32_t noise)
 {
     extern __shared__ unsigned char smem_raw[];
+    (void)noise;  // the template parameter Noise decides
     const int J = mp.J, nn = J * J, quads = nn / 4, pairs = nn / 2, qrow = J / 4;
     float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [2][ppc][quads]
     const int slot = (int)threadIdx.x / quads;
@@ -598,11 +614,14 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
         if (active) buf[q] = make_float4(v[0], v[1], v[2], v[3]);
         __syncthreads();
         if (active) {
-            float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float z[8];
             const uint32_t bk = (uint32_t)k * blocks_per_step + 2u * (uint32_t)q;
-            if (noise) {
+            if (Noise) {
                 normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
                 normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) z[i] = 0.0f;
             }
             const float4 up = buf[qu], dn = buf[qd];
             const float left = has_left ? buf[ql].w : v[0], right = has_right ? buf[qr].x : v[3];
@@ -723,13 +742,25 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
         block_sum_dd<2>(s, shd);
     } else {
         FF f[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-        for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
-            const int64_t p = td.gstart + j;
-            const float w = weight_f32(a.logw[p], mx, degenerate);
-            f[0] = ff_add(f[0], w);
-            f[1] = ff_add(f[1], __fmul_rn(w, w));
-            qs += quant_f32(w, fd.shift);
-            a.B[p] = -1;
+        // every thread holds at most kItems particles of the tile: load them all first
+        float l[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int j = threadIdx.x + r * (int)blockDim.x;
+            l[r] = j < td.len ? a.logw[td.gstart + j] : -INFINITY;
+        }
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int j = threadIdx.x + r * (int)blockDim.x;
+            if (j < td.len) {
+                const float w = weight_f32(l[r], mx, degenerate);
+                f[0] = ff_add(f[0], w);
+                f[1] = ff_add(f[1], __fmul_rn(w, w));
+                const uint64_t qv = quant_f32(w, fd.shift);
+                qs += qv;
+                a.C[td.gstart + j] = qv;  // the scan turns these into the prefix
+                a.B[td.gstart + j] = -1;
+            }
         }
         block_sum_ff<2>(f, s, shd);
     }
@@ -795,8 +826,6 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
             if (!Direct) a.fmax_key[td.m] = kNegInfKey;  // k_weights has consumed it
         }
     }
-    const float mx = Direct ? 0.0f : (float)a.fstats[(int64_t)td.m * kFsCount + kFsMax];
-    const bool degenerate = !Direct && a.fstats[(int64_t)td.m * kFsCount + kFsDegenerate] != 0.0;
     // blocked items: thread j owns tile positions [j * kItems, (j + 1) * kItems)
     const int j0 = threadIdx.x * kItems;
     uint64_t q[kItems];
@@ -807,8 +836,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
         q[r] = 0;
         if (j < td.len) {
             const int64_t p = td.gstart + j;
-            q[r] = Direct ? quant_f64(a.w_direct[p], fd.shift)
-                          : quant_f32(weight_f32(a.logw[p], mx, degenerate), fd.shift);
+            q[r] = Direct ? quant_f64(a.w_direct[p], fd.shift) : a.C[p];  // q from k_weights
         }
         tsum += q[r];
     }
@@ -1296,20 +1324,32 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
     const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
     static bool carveout_set = false;  // prefer shared memory so that several CTAs fit per SM
     if (!carveout_set) {
-        cudaFuncSetAttribute(k_propagate_fhn<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_propagate_fhn<float, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_propagate_fhn4, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_propagate_fhn<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         carveout_set = true;
     }
-    if (nodes == 4)
-        k_propagate_fhn4<<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, weigh ? logw : nullptr,
-                                                     d_obs, stride, c.obs_slot, c.d_t, ppc, weigh ? fmax : nullptr,
-                                                     n_steps, aux, noise);
+    float *lw = weigh ? logw : nullptr;
+    int32_t *fm = weigh ? fmax : nullptr;
+    if (nodes == 4 && noise)
+        k_propagate_fhn4<true><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs, stride,
+                                                           c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
+    else if (nodes == 4)
+        k_propagate_fhn4<false><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+                                                            stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 0);
+    else if (noise)
+        k_propagate_fhn<float, true><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
+                                                                 lw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc,
+                                                                 fm, n_steps, aux, 1);
     else
-        k_propagate_fhn<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
-                                                           weigh ? logw : nullptr, d_obs, stride, c.obs_slot, c.d_t,
-                                                           0, 0, 0, ppc, weigh ? fmax : nullptr, n_steps, aux, noise);
+        k_propagate_fhn<float, false><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo,
+                                                                  c.P, lw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0,
+                                                                  ppc, fm, n_steps, aux, 0);
     return cudaGetLastError();
 }
 
