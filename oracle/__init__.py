@@ -29,6 +29,8 @@ bf_run                 Alg. 1 x M, Def. 1, eq. eqGtN                  LG: conver
 apf_run                auxiliary particle filters (Pitt & Shephard),  LG: converges to the Kalman mean; E G =
                        the filter of Sec. 5.3; remark after Cor. 2    Kalman evidence (unbiased, as Lemma 2);
                                                                       Lorenz: same posterior as bf_run
+sir_run                Alg. 1 with step 2b only when ESS < tau N      tau > 1: bf_run bit for bit; LG: Kalman
+                       (the adaptive form of the resampling step)     mean and unbiased evidence at tau = 0.5
 bf_run_proposal        Alg. 1 step 2a with an importance function     zero network = bf_run bit for bit; p g / q
                        (remark after Alg. 1; Sec. 6 footnote)         weights keep the bootstrap posterior
 mlp (oracle/mlp.py)    the proposal's network                         finite-difference gradients; BF16 rounding
@@ -290,6 +292,25 @@ def apf_run(spec, M: int, N, T: int, obs: np.ndarray, seed: int, est_idx: Option
                       _p(est_idx, ctypes.c_int32), _p(est, ctypes.c_double), _p(logG, ctypes.c_double),
                       _p(ess, ctypes.c_double), _p(ens, ctypes.c_double), ctypes.c_int32(threads))
     return dict(est=est, log_G=logG, ess=ess, ens=ens)
+
+
+def sir_run(spec, M: int, N, T: int, obs: np.ndarray, seed: int, ess_threshold: float,
+            est_idx: Optional[Sequence[int]] = None, obs_per_filter: bool = False, threads: int = 0) -> dict:
+    """M bootstrap filters that resample only when ESS < ess_threshold N (carried weights between
+    resamplings; weighted estimates), and their average (Def. 1)."""
+    md = _Model(spec)
+    N = np.ascontiguousarray(np.broadcast_to(np.asarray(N, dtype=np.int32), (M,)), dtype=np.int32)
+    est_idx = np.ascontiguousarray(range(spec.dx) if est_idx is None else est_idx, dtype=np.int32)
+    ne = len(est_idx)
+    obs = np.ascontiguousarray(obs, dtype=np.float64)
+    est, logG, ess, res, ens = (np.empty((T, M, ne)), np.empty((T, M)), np.empty((T, M)), np.empty((T, M)),
+                                np.empty((T, ne)))
+    lib().orc_sir_run(md.ref, ctypes.c_int32(M), _p(N, ctypes.c_int32), ctypes.c_int32(T), _p(obs, ctypes.c_double),
+                      ctypes.c_int32(1 if obs_per_filter else 0), ctypes.c_uint64(seed), ctypes.c_double(ess_threshold),
+                      ctypes.c_int32(ne), _p(est_idx, ctypes.c_int32), _p(est, ctypes.c_double),
+                      _p(logG, ctypes.c_double), _p(ess, ctypes.c_double), _p(res, ctypes.c_double),
+                      _p(ens, ctypes.c_double), ctypes.c_int32(threads))
+    return dict(est=est, log_G=logG, ess=ess, resampled=res, ens=ens)
 
 
 def bf_run_proposal(spec, theta, M: int, N, T: int, obs: np.ndarray, seed: int, est_idx=None, bf16: bool = True,

@@ -914,3 +914,88 @@ int orc_apf_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, con
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Bootstrap filters with resampling only when the effective sample size      */
+/* falls below ess_threshold N (the standard adaptive form of step 2b; with   */
+/* ess_threshold > 1 every step resamples and the run equals orc_bf_run's     */
+/* systematic one).  Per filter the log-weights are carried between           */
+/* resamplings: logw = lw_c + log g_t(x); log G_t gains log sum exp(logw)    */
+/* - log sum exp(lw_c); the estimate is the mean under the carried weights    */
+/* after the step (uniform after a resampling).                               */
+/* est[T][M][n_est], log_G[T][M], ess[T][M] (before the decision),            */
+/* resampled[T][M] (1 where the filter resampled), ens[T][n_est].             */
+/* ------------------------------------------------------------------------- */
+int orc_sir_run(const orc_model *md, int32_t M, const int32_t *N, int32_t T, const double *obs,
+                int32_t obs_per_filter, uint64_t seed, double ess_threshold, int32_t n_est, const int32_t *est_idx,
+                double *est, double *log_G, double *ess, double *resampled, double *ens, int32_t n_threads)
+{
+    int dx = md->dx;
+    const double log_const = -0.5 * md->dy * log(2.0 * M_PI * md->sigma_obs * md->sigma_obs);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int m = 0; m < M; ++m) {
+        int64_t Nm = N[m];
+        double *x = (double *)malloc(sizeof(double) * Nm * dx);
+        double *xn = (double *)malloc(sizeof(double) * Nm * dx);
+        double *lw = (double *)malloc(sizeof(double) * Nm);
+        double *w = (double *)malloc(sizeof(double) * Nm);
+        int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * Nm);
+        double *z = (double *)malloc(sizeof(double) * dx);
+        double *f = (double *)malloc(sizeof(double) * dx);
+        double lg = 0.0, lse_c = log((double)Nm);
+        for (int64_t i = 0; i < Nm; ++i) {
+            prior_one(md, seed, ORC_STREAM_INIT, (uint32_t)i, (uint32_t)m, x + i * dx);
+            lw[i] = 0.0;
+        }
+        for (int32_t t = 1; t <= T; ++t) {
+            const double *y = obs_per_filter ? obs + ((int64_t)(t - 1) * M + m) * md->dy
+                                             : obs + (int64_t)(t - 1) * md->dy;
+            for (int64_t i = 0; i < Nm; ++i) {
+                propagate_one(md, seed, ORC_STREAM_DYN, (uint32_t)i, (uint32_t)m, t, x + i * dx, z, f);
+                lw[i] += loglik(md, x + i * dx, y);
+            }
+            double nrm[5];
+            orc_normalise(Nm, lw, nrm);
+            lg += nrm[1] - lse_c + log_const;
+            int64_t row = (int64_t)(t - 1) * M + m;
+            int res = nrm[4] < ess_threshold * (double)Nm;
+            if (res) {
+                for (int64_t i = 0; i < Nm; ++i) w[i] = exp(lw[i] - nrm[0]);
+                orc_systematic(Nm, w, orc_resample_u(seed, m, t), anc);
+                for (int64_t i = 0; i < Nm; ++i) memcpy(xn + i * dx, x + (int64_t)anc[i] * dx, sizeof(double) * dx);
+                double *tmp = x; x = xn; xn = tmp;
+                for (int64_t i = 0; i < Nm; ++i) lw[i] = 0.0;
+                lse_c = log((double)Nm);
+            } else {
+                lse_c = nrm[1];
+            }
+            if (log_G) log_G[row] = lg;
+            if (ess) ess[row] = nrm[4];
+            if (resampled) resampled[row] = res;
+            if (est) {
+                double mx = lw[0];
+                for (int64_t i = 1; i < Nm; ++i) if (lw[i] > mx) mx = lw[i];
+                double sw = 0.0;
+                for (int64_t i = 0; i < Nm; ++i) { w[i] = exp(lw[i] - mx); sw += w[i]; }
+                for (int e = 0; e < n_est; ++e) {
+                    double s = 0.0;
+                    for (int64_t i = 0; i < Nm; ++i) s += w[i] * x[i * dx + est_idx[e]];
+                    est[row * n_est + e] = s / sw;
+                }
+            }
+        }
+        free(x); free(xn); free(lw); free(w); free(anc); free(z); free(f);
+    }
+    if (ens && est) {
+        for (int32_t t = 0; t < T; ++t)
+            for (int e = 0; e < n_est; ++e) {
+                double s = 0.0;
+                for (int m = 0; m < M; ++m) s += est[((int64_t)t * M + m) * n_est + e];
+                ens[(int64_t)t * n_est + e] = s / (double)M;
+            }
+    }
+    return 0;
+}

@@ -264,3 +264,37 @@ def test_apf_and_bootstrap_agree_on_lorenz():
     for t in (4, 9, 19):
         se = math.sqrt(a[t].var(ddof=1) / M + b[t].var(ddof=1) / M)
         assert abs(a[t].mean() - b[t].mean()) < 4.5 * se, (t, a[t].mean(), b[t].mean(), se)
+
+
+# ------------------------------------------------------------ resampling only when the ESS is low
+def test_sir_always_resampling_is_the_bootstrap_run():
+    """With a threshold above 1 every step resamples: the adaptive run is the
+    systematic bootstrap run bit for bit (estimates, evidence, ESS)."""
+    spec = W.lorenz63()
+    T = 8
+    _, y = oracle.simulate(spec, T, W.SEED_LORENZ_OBS)
+    a = oracle.sir_run(spec, 6, 200, T, y, seed=3, ess_threshold=2.0)
+    b = oracle.bf_run(spec, 6, 200, T, y, seed=3)
+    assert np.array_equal(a["est"], b["est"]) and np.array_equal(a["log_G"], b["log_G"])
+    assert np.array_equal(a["ess"], b["ess"]) and a["resampled"].min() == 1.0
+
+
+def test_sir_adaptive_converges_to_kalman_and_is_unbiased():
+    spec = W.linear_gaussian()
+    T = 10
+    _, y = oracle.simulate(spec, T, seed=W.SEED_LORENZ_OBS)
+    m, _, _ = oracle.kalman(spec, y)
+    M, N = 64, 1024
+    r = oracle.sir_run(spec, M, N, T, y, seed=8, ess_threshold=0.5)
+    assert 0.0 < r["resampled"].mean() < 1.0, r["resampled"].mean()  # some steps skip, some resample
+    se = r["est"].std(axis=1, ddof=1) / math.sqrt(M)
+    assert np.all(np.abs(r["ens"] - m) < 4.5 * se + 2e-3)
+    spec = W.linear_gaussian(**SCALAR)
+    _, _, ll = oracle.kalman(spec, Y_SCALAR)
+    Mb = 1 << 16
+    for N in (4, 32):
+        rb = oracle.sir_run(spec, Mb, N, 2, Y_SCALAR, seed=400 + N, ess_threshold=0.5)
+        assert 0.0 < rb["resampled"][0].mean() < 1.0
+        for t in range(2):
+            ratio = np.exp(rb["log_G"][t] - ll[t])
+            assert abs(ratio.mean() - 1.0) < 4.5 * ratio.std() / math.sqrt(Mb), (N, t)
