@@ -228,6 +228,19 @@ PF_API pf_status pf_autotune(pf_ctx *ctx, int32_t *h_choice);
  * Errors: PF_ESTATE, PF_EUNSUPPORTED, PF_ENOMEM. */
 PF_API pf_status pf_set_auxiliary(pf_ctx *ctx, int32_t on);
 
+/* Resampling only when it is needed: a filter resamples at step t only if its
+ * effective sample size is below ess_threshold x N_m (0 <= ess_threshold <= 1;
+ * any other value, e.g. -1 or 2, restores resampling at every step, Algorithm 1
+ * as printed and the default).  Between resamplings a filter carries its log-
+ * weights: its step's log-weights are the carried ones plus log g_t; log G_t
+ * gains log sum exp(log-weights) - log sum exp(carried); PF_STAT_MEAN is the
+ * mean under the carried weights (uniform right after a resampling);
+ * PF_STAT_ESS is the ESS the decision was taken on.  pf_set_state makes the
+ * carried weights uniform.  Steps go through pf_step / pf_step_device only;
+ * not combined with the auxiliary filter, the learned proposal or recording.
+ * Synchronises.  Errors: PF_EINVAL (NaN), PF_ESTATE, PF_EUNSUPPORTED, PF_ENOMEM. */
+PF_API pf_status pf_set_resampling(pf_ctx *ctx, double ess_threshold);
+
 /* Sets the launch schedule explicitly (0 in any field: the default):
  * nodes_per_thread 2 or 4 for the lattice kernels (4 needs J % 4 == 0),
  * particles_per_cta >= 1 for the lattice (clamped to what fits in 1024

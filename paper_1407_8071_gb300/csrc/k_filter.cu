@@ -382,7 +382,8 @@ constexpr int kPropThreads = kSubTile / 2;
 // Mode 0: the bootstrap filter.  Mode 1: the auxiliary filter's look-ahead
 // (noise-free Euler prediction mu, nothing stored but la_out = log g(y | mu)
 // and logw = lw_prev + la_out).  Mode 2: its second stage (logw = log g(y | x)
-// - la_src[off + anc]).
+// - la_src[off + anc]).  Mode 3: carried weights (adaptive resampling):
+// logw = lw_prev + log g(y | x).
 template <int D, int Mode>
 __global__ void __launch_bounds__(kPropThreads, 16)
     k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *__restrict__ x_in,
@@ -417,6 +418,8 @@ __global__ void __launch_bounds__(kPropThreads, 16)
             float lr = loglik_small<D, float>(mp, y, xs[r]);
             if (Mode == 1) {
                 aux.la_out[p] = lr;
+                lr = aux.lw_prev[p] + lr;
+            } else if (Mode == 3) {
                 lr = aux.lw_prev[p] + lr;
             } else if (Mode == 2) {
                 lr -= aux.la_src[(st.gstart - st.lstart) + aux.anc[p]];
@@ -785,7 +788,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
 // #{i : t_i < C_k}, and the start markers B[lo_k] = k of every particle with
 // offspring.  The first tile of each filter also writes the filter's log Z,
 // ESS and log G (eq. eqGtN) and its (C_tot, U).
-template <bool Direct>
+template <bool Direct, bool Adaptive = false>
 __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs a)
 {
     __shared__ double shd[kResampleThreads * 2 + 2];
@@ -793,6 +796,33 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = a.filt[td.m];
     const int ti = blockIdx.x - fd.tile_begin;
+    if (Adaptive) {
+        // every tile of the filter forms the same FP64 sums in the same order: the same decision
+        double s[2] = {0.0, 0.0};
+        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) {
+            const double *ts = a.tile_sums + (int64_t)(fd.tile_begin + j) * kTsCount;
+            s[0] += ts[kTsW];
+            s[1] += ts[kTsW2];
+        }
+        block_sum_dd<2>(s, shd);
+        const bool degenerate = a.fstats[(int64_t)td.m * kFsCount + kFsDegenerate] != 0.0;
+        const bool resample = degenerate || s[0] * s[0] / s[1] < a.ess_threshold * (double)fd.N;
+        if (!resample) {  // identity ancestors: a marker at every particle, the tile starts at itself
+            for (int j = threadIdx.x; j < td.len; j += blockDim.x) a.B[td.gstart + j] = td.lstart + j;
+            if (threadIdx.x == 0) a.tile_anc0[blockIdx.x] = td.lstart;
+            if (ti == 0 && threadIdx.x == 0) {
+                double *fs = a.fstats + (int64_t)td.m * kFsCount;
+                const double logZ = fs[kFsMax] + log(s[0]);
+                fs[kFsLogZ] = logZ;
+                fs[kFsEss] = s[0] * s[0] / s[1];
+                fs[kFsLogG] += logZ - fs[kFsLse2] + a.log_const;
+                fs[kFsLse2] = logZ;
+                fs[kFsResampled] = 0.0;
+                a.fmax_key[td.m] = kNegInfKey;
+            }
+            return;
+        }
+    }
     uint64_t q_all = 0, q_before = 0;
     for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) {
         const uint64_t v = a.tile_q[fd.tile_begin + j];
@@ -820,7 +850,13 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
             const double logZ = fs[kFsMax] + log(s[0]);
             fs[kFsLogZ] = logZ;
             fs[kFsEss] = s[0] * s[0] / s[1];
-            if (a.d_t) fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)fd.N) + a.log_const;
+            if (Adaptive) {  // the carried weights' log sum, log N after a resampling
+                fs[kFsLogG] += logZ - fs[kFsLse2] + a.log_const;
+                fs[kFsLse2] = log((double)fd.N);
+                fs[kFsResampled] = 1.0;
+            } else if (a.d_t) {
+                fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)fd.N) + a.log_const;
+            }
             a.fint[(int64_t)td.m * 2] = Ctot;
             a.fint[(int64_t)td.m * 2 + 1] = U;
             if (!Direct) a.fmax_key[td.m] = kNegInfKey;  // k_weights has consumed it
@@ -1049,7 +1085,7 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
 // and for the small models the weighted means of the D variables.  Tile
 // partials in compensated FP32 pairs, FP64 across tiles, combined in tile order
 // by the filter's last tile (completion counter kept at 0 between steps).
-template <int D>
+template <int D, bool Evidence = true>
 __global__ void __launch_bounds__(kResampleThreads)
     k_weight_stats(const TileDesc *tiles, const FilterDesc *filt, const float *__restrict__ lw2,
                    const int32_t *__restrict__ fmax2, const float *__restrict__ x, int64_t P, double *tile_sums,
@@ -1107,10 +1143,12 @@ __global__ void __launch_bounds__(kResampleThreads)
             atomicOr(&err[0], kErrDegenerate);
             atomicCAS(&err[1], -1, td.m);
         }
-        const double lse2 = (double)mx + log(sw);
-        fs[kFsEss] = sw * sw / s[1];
-        fs[kFsLogG] += lse2 - fs[kFsLse2];
-        fs[kFsLse2] = lse2;
+        if (Evidence) {  // the auxiliary filter's second stage
+            const double lse2 = (double)mx + log(sw);
+            fs[kFsEss] = sw * sw / s[1];
+            fs[kFsLogG] += lse2 - fs[kFsLse2];
+            fs[kFsLse2] = lse2;
+        }
         fs[kFsSumW] = sw;
 #pragma unroll
         for (int v = 0; v < D; ++v) est[(int64_t)td.m * D + v] = s[2 + v] / sw;
@@ -1288,6 +1326,7 @@ ResampleArgs ctx_args(const Ctx &c)
     a.err = c.err;
     a.done = c.done;
     a.log_const = -0.5 * c.mp.dy * log(2.0 * M_PI * c.mp.sigma_obs * c.mp.sigma_obs);
+    a.ess_threshold = c.ess_threshold;
     return a;
 }
 
@@ -1381,6 +1420,79 @@ cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)
 {
     k_fill_i32<<<(c.M + 255) / 256, 256, 0, s>>>(c.fmax_key, c.M, kNegInfKey);
     k_refresh_max<<<c.n_tiles, kResampleThreads, 0, s>>>(c.tiles, c.logw, c.fmax_key);
+    return cudaGetLastError();
+}
+
+// Adaptive resampling: the weights carried into the next step (0 where the
+// filter resampled, the step's log-weight where it kept its particles; the
+// particles' order is unchanged then, the gather being the identity), and
+// their per-filter maximum for the weighted estimates.
+__global__ void __launch_bounds__(256) k_carry(const int32_t *__restrict__ pfilt, const double *__restrict__ fstats,
+                                               const float *__restrict__ logw, float *lw_c, int32_t *fmax_c, int64_t P)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int32_t m = pfilt[p];
+    const float l = fstats[(int64_t)m * kFsCount + kFsResampled] != 0.0 ? 0.0f : logw[p];
+    lw_c[p] = l;
+    if (l > -INFINITY && l < INFINITY) atomicMax(&fmax_c[m], float_order_key(l));
+}
+
+template <int D>
+cudaError_t adaptive_small(const Ctx &c, const ResampleArgs &a, const float *d_obs, int32_t stride, float *x,
+                           float *xn, cudaStream_t s)
+{
+    const int th = c.resample_threads;
+    k_propagate_small<D, 3><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, x, x, c.P, c.logw, c.fmax_key,
+                                                              d_obs, stride, c.d_t, AuxPtrs{c.lw2, nullptr, nullptr,
+                                                                                            nullptr});
+    k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
+    k_scan_scatter<false, true><<<c.n_tiles, th, 0, s>>>(a);
+    k_ancestors_small<D><<<c.n_tiles, th, 0, s>>>(a, x, xn, c.P, c.tile_est, c.est);
+    k_carry<<<(unsigned)((c.P + 255) / 256), 256, 0, s>>>(c.pfilt, c.fstats, c.logw, c.lw2, c.fmax2, c.P);
+    k_weight_stats<D, false><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, xn, c.P, c.tile_sums,
+                                                      c.tile_est, c.done, c.fstats, c.est, c.err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t stride, cudaStream_t s)
+{
+    ResampleArgs a = ctx_args(c);
+    a.ess_threshold = c.ess_threshold;
+    const int dx = c.mp.dx, th = c.resample_threads;
+    float *x = c.x[c.cur];
+    float *xn = c.x[c.cur ^ 1];
+    k_fill_i32<<<(c.M + 255) / 256, 256, 0, s>>>(c.fmax2, c.M, kNegInfKey);
+    cudaError_t e = cudaSuccess;
+    if (is_lattice(c.mp.kind)) {
+        const AuxPtrs carry{c.lw2, c.la, nullptr, nullptr};
+        if (c.mp.kind == kFhnPaper)
+            e = launch_fhnp_interval(c, d_obs, stride, x, x, c.mp.K, c.logw, c.fmax_key, carry, 1, s);
+        else
+            e = launch_fhn_interval(c, d_obs, stride, x, x, c.mp.K, true, s, c.logw, c.fmax_key, carry, 1);
+        if (e != cudaSuccess) return e;
+        k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
+        k_scan_scatter<false, true><<<c.n_tiles, th, 0, s>>>(a);
+        k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
+        k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(x),
+                                                   reinterpret_cast<float4 *>(xn), dx / 4);
+        k_carry<<<(unsigned)((c.P + 255) / 256), 256, 0, s>>>(c.pfilt, c.fstats, c.logw, c.lw2, c.fmax2, c.P);
+        k_weight_stats<0, false><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, nullptr, c.P, c.tile_sums,
+                                                          nullptr, c.done, c.fstats, c.est, c.err);
+        dim3 g(c.n_mchunks, (dx + 255) / 256);
+        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, c.lw2, c.fmax2,
+                                      c.fstats);
+    } else {
+        switch (dx) {
+        case 1: e = adaptive_small<1>(c, a, d_obs, stride, x, xn, s); break;
+        case 2: e = adaptive_small<2>(c, a, d_obs, stride, x, xn, s); break;
+        case 3: e = adaptive_small<3>(c, a, d_obs, stride, x, xn, s); break;
+        case 4: e = adaptive_small<4>(c, a, d_obs, stride, x, xn, s); break;
+        default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    k_ensemble<<<dx, ensemble_threads(c.M), 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
     return cudaGetLastError();
 }
 

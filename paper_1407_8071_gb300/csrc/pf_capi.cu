@@ -130,14 +130,22 @@ cudaError_t enqueue_resample(Ctx &c)
 cudaError_t enqueue_step(Ctx &c, int mode)
 {
     if (c.aux) return launch_apf_step(c, c.d_obs, kernel_stride(c, mode), c.stream);
+    if (c.adaptive()) return launch_adaptive_step(c, c.d_obs, kernel_stride(c, mode), c.stream);
     cudaError_t e = enqueue_propagate(c, mode);
     if (e != cudaSuccess) return e;
     return enqueue_resample(c);
 }
 
-// Second-stage weights of the auxiliary filter back to uniform (lw2 = 0, and the
-// running log sum of them = log N_m), e.g. when it is switched on or the state
-// is replaced.
+// Per-particle weight buffers shared by the auxiliary filter and adaptive resampling.
+bool ensure_weight_buffers(Ctx &c)
+{
+    if (c.la) return true;
+    return alloc_n(c, c.la, (size_t)c.P) && alloc_n(c, c.lw2, (size_t)c.P) && alloc_n(c, c.fmax2, (size_t)c.M);
+}
+
+// Second-stage (auxiliary filter) or carried (adaptive resampling) weights back
+// to uniform (lw2 = 0, and the running log sum of them = log N_m), e.g. when
+// the mode is switched on or the state is replaced.
 pf_status reset_aux_weights(Ctx &c)
 {
     std::vector<double> fs((size_t)c.M * kFsCount);
@@ -610,6 +618,7 @@ static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride,
     if (st != PF_OK) return st;
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_propagate called twice without pf_resample");
     if (c.aux) return fail(c, PF_EUNSUPPORTED, "the auxiliary filter steps as a whole: use pf_step");
+    if (c.adaptive()) return fail(c, PF_EUNSUPPORTED, "adaptive resampling steps as a whole: use pf_step");
     cudaSetDevice(c.device);
     cudaError_t e = stage_obs(c, obs, obs_stride, kind);
     if (e == cudaSuccess) e = enqueue_propagate(c, obs_mode(obs_stride));
@@ -722,7 +731,8 @@ pf_status pf_set_proposal(pf_ctx *h, const float *h_theta, int32_t n_params, dou
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_proposal between pf_propagate and pf_resample");
     if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "the learned proposal is for the lattice");
-    if (c.aux && h_theta) return fail(c, PF_EUNSUPPORTED, "the learned proposal is not combined with the auxiliary filter");
+    if ((c.aux || c.adaptive()) && h_theta)
+        return fail(c, PF_EUNSUPPORTED, "the learned proposal is not combined with the auxiliary filter or adaptive resampling");
     if (h_theta && (n_params != PF_MLP_PARAMS || !(ess_frac >= 0.0 && ess_frac <= 1.0)))
         return fail(c, PF_EINVAL, "n_params must be PF_MLP_PARAMS and ess_frac in [0, 1]");
     pf_status st = sync(c, "set_proposal");
@@ -748,7 +758,7 @@ pf_status pf_record_tuples(pf_ctx *h, float *d_X, float *d_R, int64_t capacity, 
     if (!h) return PF_EINVAL;
     Ctx &c = h->c;
     if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the lattice");
-    if (c.aux && d_X) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the bootstrap filter");
+    if ((c.aux || c.adaptive()) && d_X) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the bootstrap filter");
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_record_tuples between pf_propagate and pf_resample");
     pf_status st = sync(c, "record_tuples");
     if (st != PF_OK) return st;
@@ -908,8 +918,9 @@ pf_status pf_set_auxiliary(pf_ctx *h, int32_t on)
     Ctx &c = h->c;
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_auxiliary between pf_propagate and pf_resample");
-    if (on && (c.prop_on || c.rec_X))
-        return fail(c, PF_EUNSUPPORTED, "the auxiliary filter is not combined with the learned proposal or recording");
+    if (on && (c.prop_on || c.rec_X || c.adaptive()))
+        return fail(c, PF_EUNSUPPORTED,
+                    "the auxiliary filter is not combined with the learned proposal, recording or adaptive resampling");
     pf_status st = sync(c, "set_auxiliary");
     if (st != PF_OK) return st;
     drop_graphs(c);
@@ -917,11 +928,28 @@ pf_status pf_set_auxiliary(pf_ctx *h, int32_t on)
         c.aux = false;
         return PF_OK;
     }
-    if (!c.la) {
-        const bool ok = alloc_n(c, c.la, (size_t)c.P) && alloc_n(c, c.lw2, (size_t)c.P) && alloc_n(c, c.fmax2, (size_t)c.M);
-        if (!ok) return fail(c, PF_ENOMEM, "auxiliary filter buffers: device allocation failed");
-    }
+    if (!ensure_weight_buffers(c)) return fail(c, PF_ENOMEM, "auxiliary filter buffers: device allocation failed");
     c.aux = true;
+    return reset_aux_weights(c);
+}
+
+pf_status pf_set_resampling(pf_ctx *h, double ess_threshold)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_resampling between pf_propagate and pf_resample");
+    if (std::isnan(ess_threshold)) return fail(c, PF_EINVAL, "ess_threshold is NaN");
+    const bool adaptive = ess_threshold >= 0.0 && ess_threshold <= 1.0;
+    if (adaptive && (c.aux || c.prop_on || c.rec_X))
+        return fail(c, PF_EUNSUPPORTED,
+                    "adaptive resampling is not combined with the auxiliary filter, the learned proposal or recording");
+    pf_status st = sync(c, "set_resampling");
+    if (st != PF_OK) return st;
+    drop_graphs(c);
+    c.ess_threshold = adaptive ? ess_threshold : -1.0;
+    if (!adaptive) return PF_OK;
+    if (!ensure_weight_buffers(c)) return fail(c, PF_ENOMEM, "adaptive resampling buffers: device allocation failed");
     return reset_aux_weights(c);
 }
 
@@ -1001,7 +1029,7 @@ pf_status pf_set_state(pf_ctx *h, const float *h_x, int32_t t)
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state copy");
     c.t = t;
     c.phase = 0;
-    if (c.aux) return reset_aux_weights(c);
+    if (c.aux || c.adaptive()) return reset_aux_weights(c);
     return PF_OK;
 }
 

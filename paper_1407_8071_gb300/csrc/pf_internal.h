@@ -61,7 +61,8 @@ enum FStat : int {
     kFsLogZ = 0, kFsEss = 1, kFsLogG = 2, kFsMax = 3, kFsDegenerate = 4, kFsFallback = 5,
     kFsLse2 = 6,  // auxiliary filter: log sum of the second-stage weights (log N before the first step)
     kFsSumW = 7,  // auxiliary filter: sum of exp(lw2 - max) behind the weighted means
-    kFsCount = 8
+    kFsResampled = 8,  // adaptive resampling: 1 where the filter resampled this step
+    kFsCount = 10
 };
 // Per-tile FP64 partial sums.
 enum TSum : int { kTsW = 0, kTsW2 = 1, kTsCount = 2 };
@@ -89,6 +90,7 @@ struct ResampleArgs {
     int32_t *tile_anc0;      // [tiles] ancestor of each tile's first output (written by the scan)
     int32_t *err;            // [2]
     double log_const;        // -dy/2 log(2 pi sigma_obs^2), added to log G only
+    double ess_threshold;    // adaptive resampling: resample a filter only when ESS < this x N
     int32_t *done;           // [M] per-filter completion counters, kept at 0 between steps
 };
 
@@ -118,6 +120,8 @@ cudaError_t launch_fhnp_interval(const Ctx &c, const float *d_obs, int32_t strid
                                  cudaStream_t s);
 cudaError_t launch_fhnp_truth_step(const ModelParams &mp, Key key, int32_t record, int32_t t, const double *xi,
                                    double *xo, cudaStream_t s);
+// One step of bootstrap filters that resample only when the ESS is low (k_filter.cu).
+cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t obs_stride, cudaStream_t s);
 // One observation step of the ensemble of auxiliary particle filters (k_filter.cu).
 cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t obs_stride, cudaStream_t s);
 // Learned proposal (k_filter.cu, k_proposal.cu, k_mlp.cu).
@@ -172,6 +176,9 @@ struct Ctx {
     int resample_threads = kResampleThreads;
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
     int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, or 0 (4 where J % 4 == 0)
+    // resampling only when the ESS is low (pf_set_resampling; < 0: every step)
+    double ess_threshold = -1.0;
+    bool adaptive() const { return ess_threshold >= 0.0 && ess_threshold <= 1.0; }
     // auxiliary particle filters (pf_set_auxiliary)
     bool aux = false;
     float *la = nullptr;           // [P] look-ahead log-likelihoods log g(y | mu)

@@ -72,6 +72,7 @@ _SIGS = {
                                                  c_void_p]),
     "pf_set_schedule": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
     "pf_set_auxiliary": (c_int32, [c_void_p, c_int32]),
+    "pf_set_resampling": (c_int32, [c_void_p, c_double]),
     "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
     "pf_record_tuples": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
@@ -380,6 +381,10 @@ class EnsembleFilter:
     def set_auxiliary(self, on: bool = True):
         """Auxiliary particle filters (Pitt & Shephard) instead of bootstrap filters."""
         _check(lib().pf_set_auxiliary(self.h, 1 if on else 0), self.h)
+
+    def set_resampling(self, ess_threshold: float = -1.0):
+        """Resample a filter only when its ESS < ess_threshold N (0..1); other values: every step."""
+        _check(lib().pf_set_resampling(self.h, float(ess_threshold)), self.h)
 
     def set_schedule(self, nodes_per_thread: int = 0, particles_per_cta: int = 0, resample_threads: int = 0):
         """Set the launch schedule explicitly (0: default)."""
