@@ -1431,11 +1431,25 @@ __global__ void __launch_bounds__(256) k_carry(const int32_t *__restrict__ pfilt
                                                const float *__restrict__ logw, float *lw_c, int32_t *fmax_c, int64_t P)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int32_t m = pfilt[p];
-    const float l = fstats[(int64_t)m * kFsCount + kFsResampled] != 0.0 ? 0.0f : logw[p];
-    lw_c[p] = l;
-    if (l > -INFINITY && l < INFINITY) atomicMax(&fmax_c[m], float_order_key(l));
+    const int32_t m = p < P ? pfilt[p] : -1;
+    float l = -INFINITY;
+    if (p < P) {
+        l = fstats[(int64_t)m * kFsCount + kFsResampled] != 0.0 ? 0.0f : logw[p];
+        lw_c[p] = l;
+    }
+    // one atomic per run of equal filters within the warp (a single large filter would
+    // otherwise serialise every particle on one address)
+    const int lane = threadIdx.x & 31;
+    float mx = (l > -INFINITY && l < INFINITY) ? l : -INFINITY;
+    const int32_t m0 = __shfl_sync(0xffffffffu, m, 0);
+    const bool uniform = __all_sync(0xffffffffu, m == m0);
+    if (uniform) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0 && m0 >= 0 && mx > -INFINITY) atomicMax(&fmax_c[m0], float_order_key(mx));
+    } else if (m >= 0 && mx > -INFINITY) {
+        atomicMax(&fmax_c[m], float_order_key(mx));
+    }
 }
 
 template <int D>

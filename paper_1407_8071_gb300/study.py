@@ -35,7 +35,7 @@ def _var_index(spec: W.ModelSpec):
 
 
 def filter_estimates(spec: W.ModelSpec, M: int, N, seed: int, d_y, theta=None, ess_frac: float = 0.1,
-                     want_ess: bool = False, aux: bool = False):
+                     want_ess: bool = False, aux: bool = False, tau: float = -1.0):
     """Per-filter posterior means of the scored statistics at every observation
     time: array (T, M, n_stat); optionally the per-filter ESS (T, M)."""
     idx = _var_index(spec)
@@ -47,6 +47,7 @@ def filter_estimates(spec: W.ModelSpec, M: int, N, seed: int, d_y, theta=None, e
             f.set_proposal(theta, ess_frac)
         if aux:
             f.set_auxiliary(True)
+        f.set_resampling(tau)
         for t in range(T):
             f.step_device(d_y[t])
             if len(idx) == 1:
@@ -69,7 +70,7 @@ def reference_posterior(spec: W.ModelSpec, N_ref: int, seeds, d_y):
 
 
 def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, warmup: int = 3,
-              aux: bool = False) -> float:
+              aux: bool = False, tau: float = -1.0) -> float:
     """Device seconds per observation step of one M-filter context (CUDA events)."""
     import torch
     st = torch.cuda.Stream()
@@ -79,6 +80,7 @@ def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, wa
             f.set_proposal(theta, 0.1)
         if aux:
             f.set_auxiliary(True)
+        f.set_resampling(tau)
         for t in range(warmup):
             f.step_device(d_y[t % d_y.shape[0]])
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -117,14 +119,16 @@ def lorenz_sweep_mse(R: int = 64, T: int = 200, N_ref: int = 1 << 24, ref_seeds=
     if log:
         log(f"reference posterior ({len(ref_seeds)} x {N_ref} particles): {time.perf_counter() - t0:.1f} s")
     rows = []
-    for M, N in W.lorenz_sweep():
-        est, _ = filter_estimates(spec, R * M, N, 1000 + M, d_y)
-        mse, var, bias2, _ = ensemble_mse(est, M, ref, skip=1)
-        dt = step_time(spec, M, N, d_y)
-        rows.append({"M": M, "N": N, "mse": mse, "var": var, "bias2": bias2, "s_per_step": dt,
-                     "s_per_run": dt * T, "time_error_index": dt * T * mse})
-        if log:
-            log(f"M={M:5d} N={N:8d}  MSE {mse:.3e} (var {var:.3e}, bias^2 {bias2:+.2e})  {dt * 1e3:.3f} ms/step")
+    for tau in (-1.0, 0.5):  # resampling at every step (Algorithm 1), and only when ESS < N / 2
+        for M, N in W.lorenz_sweep():
+            est, _ = filter_estimates(spec, R * M, N, 1000 + M, d_y, tau=tau)
+            mse, var, bias2, _ = ensemble_mse(est, M, ref, skip=1)
+            dt = step_time(spec, M, N, d_y, tau=tau)
+            rows.append({"M": M, "N": N, "ess_threshold": tau, "mse": mse, "var": var, "bias2": bias2,
+                         "s_per_step": dt, "s_per_run": dt * T, "time_error_index": dt * T * mse})
+            if log:
+                log(f"tau={tau:+.1f} M={M:5d} N={N:8d}  MSE {mse:.3e} (var {var:.3e}, bias^2 {bias2:+.2e})  "
+                    f"{dt * 1e3:.3f} ms/step")
     return {"workload": "lorenz63 M*N = 2^20 sweep", "R": R, "T": T, "N_ref": N_ref,
             "ref_seeds": len(ref_seeds), "rows": rows}
 
@@ -162,15 +166,16 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
     d_y = torch.from_numpy(np.ascontiguousarray(y)).cuda()
     ref = ensemble_reference(spec, M_ref, N_ref, ref_seeds, d_y)
     out = {}
-    for name, th, m_run, aux in (("plain", None, M, False), ("learned", theta, M, False),
-                                 ("auxiliary", None, M, True), ("centralised", None, 1, False)):
+    for name, th, m_run, aux, tau in (("plain", None, M, False, -1.0), ("learned", theta, M, False, -1.0),
+                                      ("auxiliary", None, M, True, -1.0), ("adaptive", None, M, False, 0.5),
+                                      ("centralised", None, 1, False, -1.0)):
         rows = []
         for N in Ns:
             n_run = N * M // m_run
             est, ess = filter_estimates(spec, R * m_run, n_run, 2000 + N + 7 * m_run, d_y, theta=th, want_ess=True,
-                                        aux=aux)
+                                        aux=aux, tau=tau)
             mse, var, bias2, _ = ensemble_mse(est, m_run, ref, skip=skip)
-            dt = step_time(spec, m_run, n_run, d_y, theta=th, aux=aux)
+            dt = step_time(spec, m_run, n_run, d_y, theta=th, aux=aux, tau=tau)
             rows.append({"M": m_run, "N": n_run, "mse": mse, "var": var, "bias2": bias2, "s_per_step": dt,
                          "s_per_run": dt * T, "mean_ess_frac": float(np.mean(ess[skip:]) / n_run),
                          "time_error_index": dt * T * mse})
@@ -193,6 +198,7 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
             "plain_s_at_target": out["plain"][-1]["s_per_run"],
             "learned_s_at_target": time_at(out["learned"], target),
             "auxiliary_s_at_target": time_at(out["auxiliary"], target),
+            "adaptive_s_at_target": time_at(out["adaptive"], target),
             "centralised_s_at_target": time_at(out["centralised"], target)}
 
 
