@@ -197,6 +197,30 @@ PF_API pf_status pf_resample(pf_ctx *ctx);
  * (no step completed yet). */
 PF_API pf_status pf_estimate(pf_ctx *ctx, const pf_stat *stat, double *out);
 
+/* The number of kernels one pf_step launches: the kernel nodes of the CUDA
+ * graph the latest pf_step captured (a step is replayed from that graph).
+ * Errors: PF_EINVAL, PF_ESTATE (no step captured yet: no pf_step, or a
+ * recording context, whose steps are launched directly). */
+PF_API pf_status pf_step_kernels(pf_ctx *ctx, int32_t *n);
+
+/* The same values without waiting: enqueues their device-to-host copy on the
+ * context's stream into h_out (host memory owned by the caller, pinned for a
+ * truly asynchronous copy; same sizes and layout as pf_estimate), together
+ * with a copy of the device error word, and returns.  h_out holds the values
+ * once pf_estimate_wait has returned; steps enqueued after this call do not
+ * disturb them, so a caller can enqueue step t+1 before reading step t.
+ * Non-MEAN statistics are available per filter only (their M-average is
+ * formed on the host by pf_estimate).  Errors: PF_EINVAL, PF_ESTATE,
+ * PF_EUNSUPPORTED, PF_ECUDA. */
+PF_API pf_status pf_estimate_async(pf_ctx *ctx, const pf_stat *stat, double *h_out);
+
+/* Waits for the latest pf_estimate_async copy only (not for work enqueued
+ * after it), then reports a degenerate filter (PF_ENUMERIC) or an expired
+ * device wait (PF_ETIMEOUT) seen by the step it belongs to, as pf_estimate
+ * does.  Errors: PF_EINVAL, PF_ESTATE (nothing enqueued), PF_ECUDA,
+ * PF_ENUMERIC, PF_ETIMEOUT. */
+PF_API pf_status pf_estimate_wait(pf_ctx *ctx);
+
 /* Picks the launch schedule of this context's hot kernels by timing the
  * candidates on copies of its particles: for the lattice, particles per CTA
  * (one particle per CTA up to as many as fit in 1024 threads); for every model,

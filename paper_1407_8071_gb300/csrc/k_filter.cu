@@ -162,6 +162,25 @@ __device__ uint64_t block_sum_u64(uint64_t v, uint64_t *sh)
     return r;
 }
 
+// Two block sums of uint64 at once (one pair of barriers); `sh` holds 2 kWarps.
+__device__ void block_sum_u64x2(uint64_t &a, uint64_t &b, uint64_t *sh)
+{
+    a = warp_sum_u64(a);
+    b = warp_sum_u64(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) {
+        sh[w] = a;
+        sh[kWarps + w] = b;
+    }
+    __syncthreads();
+    a = b = 0;
+    for (int i = 0; i < nw; ++i) {
+        a += sh[i];
+        b += sh[kWarps + i];
+    }
+}
+
 // Exclusive prefix sum of one uint64 per thread.
 __device__ uint64_t block_exscan_u64(uint64_t v, uint64_t *sh)
 {
@@ -689,6 +708,18 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, 3)
 }
 
 // ------------------------------------------------------------------ resampling chain
+// The filter fields a tile kernel needs, from the tile descriptor alone.
+__device__ __forceinline__ FilterDesc filter_of(const TileDesc &td)
+{
+    FilterDesc fd{};
+    fd.off = td.gstart - td.lstart;
+    fd.N = td.N;
+    fd.tile_begin = td.tile_begin;
+    fd.tile_count = td.tile_count;
+    fd.shift = td.shift;
+    return fd;
+}
+
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t value)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -721,7 +752,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
     __shared__ uint64_t shu[kWarps];
     __shared__ float shf[kWarps];
     const TileDesc td = a.tiles[blockIdx.x];
-    const FilterDesc fd = a.filt[td.m];
+    const FilterDesc fd = filter_of(td);
     float mx = 0.0f;
     bool degenerate = false;
     (void)shf;
@@ -794,7 +825,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
     __shared__ double shd[kResampleThreads * 2 + 2];
     __shared__ uint64_t shu[kWarps * 3];
     const TileDesc td = a.tiles[blockIdx.x];
-    const FilterDesc fd = a.filt[td.m];
+    const FilterDesc fd = filter_of(td);
     const int ti = blockIdx.x - fd.tile_begin;
     if (Adaptive) {
         // every tile of the filter forms the same FP64 sums in the same order: the same decision
@@ -829,8 +860,8 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
         q_all += v;
         if (j < ti) q_before += v;
     }
-    const uint64_t Ctot = block_sum_u64(q_all, shu);
-    const uint64_t Cbefore = block_sum_u64(q_before, shu + kWarps);
+    block_sum_u64x2(q_all, q_before, shu);
+    const uint64_t Ctot = q_all, Cbefore = q_before;
     const int32_t t = a.d_t ? *a.d_t + 1 : 0;
     uint32_t U;
     if (Direct) U = (uint32_t)fmin(floor(a.u_direct[td.m] * 4294967296.0), 4294967295.0);
@@ -938,7 +969,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
     __shared__ double shd[kResampleThreads * D + 2 * D * 32];
     __shared__ int last;
     const TileDesc td = a.tiles[blockIdx.x];
-    const FilterDesc fd = a.filt[td.m];
+    const FilterDesc fd = filter_of(td);
     int32_t anc[kItems];
     tile_ancestors(a, td, fd, anc, shi);
     const int j0 = threadIdx.x * kItems;
@@ -986,12 +1017,156 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
     if (threadIdx.x == 0) a.done[td.m] = 0;
 }
 
+// A whole filter of at most kTile particles per CTA: the resampling step of
+// that filter in one kernel, with the quantised weights, the prefix and the
+// start markers in shared memory instead of global scratch.  The same
+// arithmetic as k_weights -> k_scan_scatter -> k_ancestors_small (or
+// k_ancestors when D = 0): FP32 weights and compensated FP32 sums, the FP64
+// normaliser, the exact q = floor(w 2^shift), the exact prefix C_k and the
+// counts #{i : t_i < C_k} (Algorithm 1 step 2b, systematic form), the
+// ancestor max-scan, then (D > 0) the gather of the SoA state and the
+// per-filter means.  The results are those of the tile chain bit for bit.
+// CTA b handles tile tile0 + b, which must be the filter's only tile.
+template <int D>
+__global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArgs a, int32_t tile0,
+                                                                     const float *__restrict__ x_in,
+                                                                     float *__restrict__ x_out, int64_t P, double *est)
+{
+    __shared__ uint64_t shq[kTile];
+    __shared__ int32_t shB[kTile];
+    __shared__ double shd[(2 * 4 * 32) / 2 + 4];  // block_sum_ff<NV <= 4>
+    __shared__ uint64_t shu[kWarps * 2];
+    __shared__ int shi[kWarps];
+    const int tix = tile0 + blockIdx.x;
+    const TileDesc td = a.tiles[tix];
+    const FilterDesc fd = filter_of(td);
+    const float m0 = float_from_order_key(a.fmax_key[td.m]);
+    const bool degenerate = !(m0 > -INFINITY);
+    const float mx = degenerate ? 0.0f : m0;
+
+    // weights, their sums and the quantised weights (strided: coalesced loads)
+    FF f[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    uint64_t qs = 0;
+    {
+        float l[kItems];
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int j = threadIdx.x + r * (int)blockDim.x;
+            l[r] = j < td.len ? a.logw[td.gstart + j] : -INFINITY;
+        }
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int j = threadIdx.x + r * (int)blockDim.x;
+            if (j < td.len) {
+                const float w = weight_f32(l[r], mx, degenerate);
+                f[0] = ff_add(f[0], w);
+                f[1] = ff_add(f[1], __fmul_rn(w, w));
+                const uint64_t qv = quant_f32(w, fd.shift);
+                qs += qv;
+                shq[j] = qv;
+                shB[j] = -1;
+            }
+        }
+    }
+    double s[2];
+    block_sum_ff<2>(f, s, shd);
+    const uint64_t Ctot = block_sum_u64(qs, shu);  // its barriers also publish shq and shB
+    const int32_t t = a.d_t ? *a.d_t + 1 : 0;
+    const uint32_t U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
+    const Grid g = make_grid(Ctot, U, (int64_t)fd.N);
+    if (threadIdx.x == 0) {  // filter scalars (FP64)
+        double *fs = a.fstats + (int64_t)td.m * kFsCount;
+        fs[kFsMax] = (double)mx;
+        fs[kFsDegenerate] = degenerate ? 1.0 : 0.0;
+        if (degenerate) {
+            atomicOr(&a.err[0], kErrDegenerate);
+            atomicCAS(&a.err[1], -1, td.m);
+        }
+        const double logZ = (double)mx + log(s[0]);
+        fs[kFsLogZ] = logZ;
+        fs[kFsEss] = s[0] * s[0] / s[1];
+        if (a.d_t) fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)fd.N) + a.log_const;
+        a.fint[(int64_t)td.m * 2] = Ctot;
+        a.fint[(int64_t)td.m * 2 + 1] = U;
+        a.fmax_key[td.m] = kNegInfKey;
+    }
+
+    // exact prefix (blocked items), counts and start markers
+    const int j0 = threadIdx.x * kItems;
+    {
+        uint64_t q[kItems];
+        uint64_t tsum = 0;
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            q[r] = j0 + r < td.len ? shq[j0 + r] : 0;
+            tsum += q[r];
+        }
+        uint64_t Cprev = block_exscan_u64(tsum, shu + kWarps);
+        int64_t cnt_prev = count_below(Cprev, g);
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int j = j0 + r;
+            if (j >= td.len) break;
+            const uint64_t Ck = Cprev + q[r];
+            if (q[r] > 0) {
+                const int64_t cnt = count_below(Ck, g);
+                if (cnt > cnt_prev) shB[cnt_prev] = j;
+                cnt_prev = cnt;
+            }
+            Cprev = Ck;
+        }
+    }
+    __syncthreads();
+
+    // ancestors: running max of the markers (output 0 always has one)
+    int b[kItems];
+    int tmax = -1;
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        b[r] = j0 + r < td.len ? shB[j0 + r] : -1;
+        tmax = max(tmax, b[r]);
+    }
+    int run = block_exscan_max_i(tmax, shi);
+    if constexpr (D == 0) {
+        (void)x_in, (void)x_out, (void)P, (void)est;
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            run = max(run, b[r]);
+            if (j0 + r < td.len) a.anc[td.gstart + j0 + r] = run;
+        }
+    } else {
+        constexpr int DD = D;
+        FF fx[DD];
+#pragma unroll
+        for (int v = 0; v < DD; ++v) fx[v] = FF{0.0f, 0.0f};
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            run = max(run, b[r]);
+            const int j = j0 + r;
+            if (j < td.len) {
+                const int64_t p = td.gstart + j;
+                a.anc[p] = run;
+                const int64_t src = fd.off + run;
+#pragma unroll
+                for (int v = 0; v < DD; ++v) {
+                    const float xv = x_in[v * P + src];
+                    x_out[v * P + p] = xv;
+                    fx[v] = ff_add(fx[v], xv);
+                }
+            }
+        }
+        double sx[DD];
+        block_sum_ff<DD>(fx, sx, shd);
+        if (threadIdx.x < DD) est[(int64_t)td.m * DD + threadIdx.x] = sx[threadIdx.x] / (double)fd.N;
+    }
+}
+
 // Ancestors only (lattice models and the stateless entry point).
 __global__ void __launch_bounds__(kResampleThreads) k_ancestors(ResampleArgs a)
 {
     __shared__ int shi[kWarps];
     const TileDesc td = a.tiles[blockIdx.x];
-    const FilterDesc fd = a.filt[td.m];
+    const FilterDesc fd = filter_of(td);
     int32_t anc[kItems];
     tile_ancestors(a, td, fd, anc, shi);
     const int j0 = threadIdx.x * kItems;
@@ -1085,6 +1260,66 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
 // and for the small models the weighted means of the D variables.  Tile
 // partials in compensated FP32 pairs, FP64 across tiles, combined in tile order
 // by the filter's last tile (completion counter kept at 0 between steps).
+// The lattice gather fused with the per-filter means: CTA (chunk of <=
+// kMeanChunk particles of one filter, variable block) copies the ancestors'
+// rows x_out[p] = x_in[off + anc[p]] variable by variable (coalesced over the
+// block's variables) and sums what it copied, in the order and with the
+// arithmetic of k_mean_rows (unweighted), so the estimates are identical and
+// the resampled state is not read a second time.
+__global__ void __launch_bounds__(256) k_gather_mean_rows(const FilterDesc *filt, const TileDesc *__restrict__ chunks,
+                                                          const int32_t *__restrict__ anc,
+                                                          const float *__restrict__ x_in, float *__restrict__ x_out,
+                                                          int dx, double *part, int32_t *cnt, double *est)
+{
+    __shared__ int last;
+    const TileDesc ch = chunks[blockIdx.x];
+    const FilterDesc fd = filt[ch.m];
+    const int v = blockIdx.y * blockDim.x + threadIdx.x;
+    double mine = 0.0;
+    if (v < dx) {
+        const int32_t *a = anc + ch.gstart;
+        float *dst = x_out + ch.gstart * (int64_t)dx + v;
+        const float *src = x_in + fd.off * (int64_t)dx + v;
+        FF acc{0.0f, 0.0f};
+        int i = 0;
+        for (; i + 8 <= ch.len; i += 8) {  // eight rows in flight, then the ordered adds
+            float r[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = src[(int64_t)a[i + k] * dx];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) dst[(int64_t)(i + k) * dx] = r[k];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = ff_add(acc, r[k]);
+        }
+        for (; i < ch.len; ++i) {
+            const float r = src[(int64_t)a[i] * dx];
+            dst[(int64_t)i * dx] = r;
+            acc = ff_add(acc, r);
+        }
+        mine = ff_to_double(acc);
+    }
+    const double denom = (double)fd.N;
+    if (fd.mc_count == 1) {
+        if (v < dx) est[(int64_t)ch.m * dx + v] = mine / denom;
+        return;
+    }
+    if (v < dx) part[(int64_t)blockIdx.x * dx + v] = mine;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *c = cnt + (int64_t)ch.m * gridDim.y + blockIdx.y;
+        last = (atomicAdd(c, 1) == fd.mc_count - 1);
+        if (last) *c = 0;
+    }
+    __syncthreads();
+    if (last && v < dx) {
+        __threadfence();
+        double s = 0.0;
+        for (int k = 0; k < fd.mc_count; ++k) s += __ldcg(&part[(int64_t)(fd.mc_begin + k) * dx + v]);
+        est[(int64_t)ch.m * dx + v] = s / denom;
+    }
+}
+
 template <int D, bool Evidence = true>
 __global__ void __launch_bounds__(kResampleThreads)
     k_weight_stats(const TileDesc *tiles, const FilterDesc *filt, const float *__restrict__ lw2,
@@ -1095,7 +1330,7 @@ __global__ void __launch_bounds__(kResampleThreads)
     __shared__ double shd[kResampleThreads * NV + 2 * NV * 32];
     __shared__ int last;
     const TileDesc td = tiles[blockIdx.x];
-    const FilterDesc fd = filt[td.m];
+    const FilterDesc fd = filter_of(td);
     const float mx = float_from_order_key(fmax2[td.m]);
     FF f[NV];
 #pragma unroll
@@ -1510,6 +1745,45 @@ cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t strid
     return cudaGetLastError();
 }
 
+// Bootstrap resampling of every filter (no adaptive decision): filters of
+// several tiles take the tile chain (weights, scan, ancestors), the tiles of
+// one-tile filters follow theirs and take one fused kernel per filter.
+// Small models: with the gather and the per-filter means.
+// One launch of the fused kernel per size class, with as many threads as the
+// class's largest filter needs (kItems particles each).
+template <int D>
+void resample_whole(const Ctx &c, const ResampleArgs &a, const float *xi, float *xo, cudaStream_t s)
+{
+    for (int k = 0; k < kWholeClasses; ++k) {
+        const int32_t b0 = c.whole_bounds[k], n = c.whole_bounds[k + 1] - b0;
+        if (n) k_resample_whole<D><<<n, 32 << k, 0, s>>>(a, b0, xi, xo, c.P, c.est);
+    }
+}
+
+template <int D>
+void resample_small(const Ctx &c, const ResampleArgs &a, const float *xi, float *xo, int th, cudaStream_t s)
+{
+    const int32_t nm = c.n_multi_tiles;
+    if (nm) {
+        k_weights<false><<<nm, th, 0, s>>>(a);
+        k_scan_scatter<false><<<nm, th, 0, s>>>(a);
+        k_ancestors_small<D><<<nm, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est);
+    }
+    resample_whole<D>(c, a, xi, xo, s);
+}
+
+// The whole bootstrap resampling up to the ancestors (lattice models).
+void resample_ancestors(const Ctx &c, const ResampleArgs &a, int th, cudaStream_t s)
+{
+    const int32_t nm = c.n_multi_tiles;
+    if (nm) {
+        k_weights<false><<<nm, th, 0, s>>>(a);
+        k_scan_scatter<false><<<nm, th, 0, s>>>(a);
+        k_ancestors<<<nm, th, 0, s>>>(a);
+    }
+    resample_whole<0>(c, a, nullptr, nullptr, s);
+}
+
 // One step of the ensemble of auxiliary particle filters: look-ahead weights
 // (noise-free prediction), first-stage systematic resampling and gather, the
 // second-stage propagation and weights, weighted estimates, the M-average.
@@ -1521,9 +1795,7 @@ cudaError_t apf_small(const Ctx &c, const ResampleArgs &a, const float *d_obs, i
     k_propagate_small<D, 1><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, x, nullptr, c.P, c.logw,
                                                               c.fmax_key, d_obs, stride, c.d_t,
                                                               AuxPtrs{c.lw2, c.la, nullptr, nullptr});
-    k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
-    k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
-    k_ancestors_small<D><<<c.n_tiles, th, 0, s>>>(a, x, xn, c.P, c.tile_est, c.est);
+    resample_small<D>(c, a, x, xn, th, s);
     k_propagate_small<D, 2><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xn, xn, c.P, c.lw2, c.fmax2, d_obs,
                                                               stride, c.d_t, AuxPtrs{nullptr, nullptr, c.la, c.anc});
     k_weight_stats<D><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, xn, c.P, c.tile_sums, c.tile_est,
@@ -1547,9 +1819,7 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
             e = launch_fhn_interval(c, d_obs, stride, x, nullptr, c.mp.K, true, s, c.logw, c.fmax_key,
                                     AuxPtrs{c.lw2, c.la, nullptr, nullptr}, 0);
         if (e != cudaSuccess) return e;
-        k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
-        k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
-        k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
+        resample_ancestors(c, a, th, s);
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(x),
                                                    reinterpret_cast<float4 *>(xn), dx / 4);
         if (c.mp.kind == kFhnPaper)
@@ -1582,21 +1852,16 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
 {
     const ResampleArgs a = ctx_args(c);
     const int dx = c.mp.dx, th = c.resample_threads;
-    k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
-    k_scan_scatter<false><<<c.n_tiles, th, 0, s>>>(a);
     if (is_lattice(c.mp.kind)) {
-        k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
-        k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
-                                                   reinterpret_cast<float4 *>(xo), dx / 4);
+        resample_ancestors(c, a, th, s);
         dim3 g(c.n_mchunks, (dx + 255) / 256);
-        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xo, dx, c.mean_part, c.mean_cnt, c.est, nullptr, nullptr,
-                                      nullptr);
+        k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, xi, xo, dx, c.mean_part, c.mean_cnt, c.est);
     } else {
         switch (dx) {
-        case 1: k_ancestors_small<1><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
-        case 2: k_ancestors_small<2><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
-        case 3: k_ancestors_small<3><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
-        case 4: k_ancestors_small<4><<<c.n_tiles, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est); break;
+        case 1: resample_small<1>(c, a, xi, xo, th, s); break;
+        case 2: resample_small<2>(c, a, xi, xo, th, s); break;
+        case 3: resample_small<3>(c, a, xi, xo, th, s); break;
+        case 4: resample_small<4>(c, a, xi, xo, th, s); break;
         default: return cudaErrorInvalidValue;
         }
     }

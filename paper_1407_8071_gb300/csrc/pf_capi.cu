@@ -191,6 +191,23 @@ pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind
             return cuda_fail(c, le, "step launch (capture)");
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "graph capture end");
+        size_t n_nodes = 0;
+        e = cudaGraphGetNodes(g, nullptr, &n_nodes);
+        if (e == cudaSuccess) {
+            std::vector<cudaGraphNode_t> nodes(n_nodes);
+            e = cudaGraphGetNodes(g, nodes.data(), &n_nodes);
+            int32_t k = 0;
+            for (size_t i = 0; e == cudaSuccess && i < n_nodes; ++i) {
+                cudaGraphNodeType ty;
+                e = cudaGraphNodeGetType(nodes[i], &ty);
+                if (ty == cudaGraphNodeTypeKernel) ++k;
+            }
+            c.step_kernels = k;
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(c, e, "graph inspection");
+        }
         e = cudaGraphInstantiate(&c.graph[par], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
@@ -300,30 +317,57 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
 // Tiles of at most kTile particles, never spanning two filters; sub-tiles of
 // at most kSubTile particles inside them.  Per-filter partial maxima come from
 // the sub-tiles (small models) or the tiles (lattice, stateless resampling).
+// With `bounds` (kWholeClasses + 1 entries), the tiles of filters with more
+// than one tile come first (in filter order), then the single tiles of the
+// other filters grouped by size class c (N <= 32 * kItems << c), and
+// bounds[c] .. bounds[c + 1] are class c's tiles (bounds[0]: the count of the
+// former); a filter's tiles are always consecutive.
+int whole_class(int32_t n)
+{
+    int c = 0;
+    while (c + 1 < kWholeClasses && n > (32 * kItems << c)) ++c;
+    return c;
+}
+
 void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std::vector<FilterDesc> &filt,
                 std::vector<int64_t> &off, std::vector<TileDesc> *subs = nullptr,
-                std::vector<TileDesc> *mchunks = nullptr)
+                std::vector<TileDesc> *mchunks = nullptr, int32_t *bounds = nullptr)
 {
     const int32_t M = (int32_t)N.size();
     off.assign(M + 1, 0);
     for (int m = 0; m < M; ++m) off[m + 1] = off[m] + N[m];
     tiles.clear();
-    filt.resize(M);
+    filt.assign(M, FilterDesc{});
+    for (int pass = 0; pass < (bounds ? 1 + kWholeClasses : 1); ++pass) {
+        if (pass > 0) bounds[pass - 1] = (int32_t)tiles.size();
+        for (int m = 0; m < M; ++m) {
+            if (bounds && (pass == 0 ? N[m] <= kTile : (N[m] > kTile || whole_class(N[m]) != pass - 1))) continue;
+            FilterDesc &fd = filt[m];
+            fd.tile_begin = (int32_t)tiles.size();
+            for (int32_t s = 0; s < N[m]; s += kTile) {
+                TileDesc td{};
+                td.m = m;
+                td.lstart = s;
+                td.len = std::min(kTile, N[m] - s);
+                td.gstart = off[m] + s;
+                tiles.push_back(td);
+            }
+            fd.tile_count = (int32_t)tiles.size() - fd.tile_begin;
+        }
+    }
+    if (bounds) bounds[kWholeClasses] = (int32_t)tiles.size();
     for (int m = 0; m < M; ++m) {
-        FilterDesc fd{};
+        FilterDesc &fd = filt[m];
         fd.off = off[m];
         fd.N = N[m];
-        fd.tile_begin = (int32_t)tiles.size();
         fd.shift = 52 - ceil_log2_host(N[m]);
-        for (int32_t s = 0; s < N[m]; s += kTile) {
-            TileDesc td{};
-            td.m = m;
-            td.lstart = s;
-            td.len = std::min(kTile, N[m] - s);
-            td.gstart = off[m] + s;
-            tiles.push_back(td);
+        for (int32_t i = fd.tile_begin; i < fd.tile_begin + fd.tile_count; ++i) {
+            TileDesc &td = tiles[i];
+            td.N = fd.N;
+            td.tile_begin = fd.tile_begin;
+            td.tile_count = fd.tile_count;
+            td.shift = fd.shift;
         }
-        fd.tile_count = (int32_t)tiles.size() - fd.tile_begin;
         if (mchunks) {
             fd.mc_begin = (int32_t)mchunks->size();
             for (int32_t s = 0; s < N[m]; s += kMeanChunk) {
@@ -346,7 +390,6 @@ void make_tiles(const std::vector<int32_t> &N, std::vector<TileDesc> &tiles, std
                 subs->push_back(st);
             }
         }
-        filt[m] = fd;
     }
 }
 
@@ -462,7 +505,8 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     std::vector<TileDesc> tiles, subs, mchunks;
     std::vector<FilterDesc> filt;
     const bool small = !is_lattice(mp.kind);
-    make_tiles(c.N, tiles, filt, c.off, small ? &subs : nullptr, small ? nullptr : &mchunks);
+    make_tiles(c.N, tiles, filt, c.off, small ? &subs : nullptr, small ? nullptr : &mchunks, c.whole_bounds);
+    c.n_multi_tiles = c.whole_bounds[0];
     c.P = c.off[M];
     c.n_tiles = (int32_t)tiles.size();
     c.n_subs = (int32_t)subs.size();
@@ -575,6 +619,8 @@ void pf_destroy(pf_ctx *h)
         if (c.h_stage[k]) cudaFreeHost(c.h_stage[k]);
         if (c.stage_ev[k]) cudaEventDestroy(c.stage_ev[k]);
     }
+    if (c.h_err_async) cudaFreeHost(c.h_err_async);
+    if (c.est_ev) cudaEventDestroy(c.est_ev);
     ctx_free_all(c);
     if (c.own_stream) cudaStreamDestroy(c.own_stream);
     delete h;
@@ -698,6 +744,80 @@ pf_status pf_estimate(pf_ctx *h, const pf_stat *stat, double *out)
         double s = 0.0;
         for (int m = 0; m < M; ++m) s += fs[(size_t)m * kFsCount + slot];
         out[0] = s / M;
+    }
+    return PF_OK;
+}
+
+pf_status pf_step_kernels(pf_ctx *h, int32_t *n)
+{
+    if (!h || !n) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.step_kernels < 0) return fail(c, PF_ESTATE, "no step graph has been captured");
+    *n = c.step_kernels;
+    return PF_OK;
+}
+
+pf_status pf_estimate_async(pf_ctx *h, const pf_stat *stat, double *h_out)
+{
+    if (!h || !stat || !h_out) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal == PF_ECUDA) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (!c.steps_done) return fail(c, PF_ESTATE, "no step has completed");
+    cudaSetDevice(c.device);
+    const int dx = c.mp.dx, M = c.M;
+    cudaError_t e = cudaSuccess;
+    if (!c.est_ev) {
+        e = cudaEventCreateWithFlags(&c.est_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocHost(&c.h_err_async, 2 * sizeof(int32_t));
+        if (e != cudaSuccess) return cuda_fail(c, e, "asynchronous estimate setup");
+    }
+    if (stat->kind == PF_STAT_MEAN) {
+        if (stat->var < -1 || stat->var >= dx) return fail(c, PF_EINVAL, "var out of range");
+        if (stat->per_filter && stat->var < 0)
+            e = cudaMemcpyAsync(h_out, c.est, (size_t)M * dx * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+        else if (stat->per_filter)
+            e = cudaMemcpy2DAsync(h_out, sizeof(double), c.est + stat->var, (size_t)dx * sizeof(double), sizeof(double),
+                                  (size_t)M, cudaMemcpyDeviceToHost, c.stream);
+        else if (stat->var < 0)
+            e = cudaMemcpyAsync(h_out, c.ens, (size_t)dx * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+        else
+            e = cudaMemcpyAsync(h_out, c.ens + stat->var, sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    } else {
+        if (!stat->per_filter) return fail(c, PF_EUNSUPPORTED, "asynchronous statistics other than MEAN are per filter");
+        int slot;
+        switch (stat->kind) {
+        case PF_STAT_LOG_EVIDENCE: slot = kFsLogG; break;
+        case PF_STAT_ESS: slot = kFsEss; break;
+        case PF_STAT_LOG_Z: slot = kFsLogZ; break;
+        case PF_STAT_FALLBACK: slot = kFsFallback; break;
+        default: return fail(c, PF_EINVAL, "unknown statistic");
+        }
+        e = cudaMemcpy2DAsync(h_out, sizeof(double), c.fstats + slot, (size_t)kFsCount * sizeof(double),
+                              sizeof(double), (size_t)M, cudaMemcpyDeviceToHost, c.stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.h_err_async, c.err, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c.est_ev, c.stream);
+    return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "asynchronous estimate copy");
+}
+
+pf_status pf_estimate_wait(pf_ctx *h)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (!c.est_ev) return fail(c, PF_ESTATE, "no asynchronous estimate was enqueued");
+    cudaSetDevice(c.device);
+    const cudaError_t e = cudaEventSynchronize(c.est_ev);
+    if (e != cudaSuccess) return cuda_fail(c, e, "asynchronous estimate wait");
+    const int32_t err0 = c.h_err_async[0], err1 = c.h_err_async[1];
+    if (err0 & kErrDegenerate) {
+        c.fatal = PF_ENUMERIC;
+        return fail(c, PF_ENUMERIC, "filter " + std::to_string(err1) +
+                                        " had no finite positive weight (all log-weights -inf or NaN)");
+    }
+    if (err0 & kErrTimeout) {
+        c.fatal = PF_ETIMEOUT;
+        return fail(c, PF_ETIMEOUT, "a tensor-core wait in the proposal network expired");
     }
     return PF_OK;
 }

@@ -20,15 +20,26 @@ namespace pf {
 constexpr int kTile = 1024;
 constexpr int kResampleThreads = 256;
 constexpr int kItems = kTile / kResampleThreads;  // particles per thread in the tile kernels
+// Size classes of one-tile filters for the fused resampling kernel: class c
+// holds N <= 32 kItems 2^c and runs CTAs of 32 2^c threads.
+constexpr int kWholeClasses = 4;
+static_assert((32 << (kWholeClasses - 1)) == kResampleThreads, "the largest class fills a tile");
 constexpr int kSubTile = 128;                     // propagation block of the thread-per-particle models
 constexpr int kMeanChunk = 256;                   // particles per partial sum of the lattice means
 
+// A tile also carries the fields of its filter that the tile kernels need,
+// so that a CTA reads one descriptor, not a tile and then (dependent) its
+// filter.
 struct TileDesc {
-    int32_t m;       // filter
-    int32_t lstart;  // filter-local index of the tile's first particle
-    int32_t len;     // particles in the tile
+    int32_t m;           // filter
+    int32_t lstart;      // filter-local index of the tile's first particle
+    int32_t len;         // particles in the tile
+    int32_t N;           // the filter's particles
+    int64_t gstart;      // global index of the tile's first particle
+    int32_t tile_begin;  // the filter's first tile
+    int32_t tile_count;  // the filter's tiles
+    int32_t shift;       // the filter's weight quantisation exponent (FilterDesc::shift)
     int32_t pad;
-    int64_t gstart;  // global index of the tile's first particle
 };
 
 struct FilterDesc {
@@ -157,6 +168,8 @@ struct Ctx {
     int32_t M = 0;
     int64_t P = 0;  // total particles
     int32_t n_tiles = 0;
+    int32_t n_multi_tiles = 0;  // tiles of filters with more than one; the one-tile filters' tiles follow
+    int32_t whole_bounds[kWholeClasses + 1] = {};  // one-tile filters of size class c: tiles [b[c], b[c+1])
     std::vector<int32_t> N;
     std::vector<int64_t> off;
 
@@ -198,6 +211,8 @@ struct Ctx {
     float *d_obs = nullptr;       // [M * dy] the current observation on the device
     float *h_stage[2] = {nullptr, nullptr};        // pinned host staging, [M * dy] each
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};  // copy-out of each staging slot done
+    cudaEvent_t est_ev = nullptr;    // the latest asynchronous estimate copy is done
+    int32_t *h_err_async = nullptr;  // pinned copy of the error word taken with it
     bool stage_used[2] = {false, false};
     int stage_slot = 0;
     int32_t *d_t = nullptr;       // completed steps
@@ -228,6 +243,7 @@ struct Ctx {
     int phase = 0;  // 0: ready to propagate; 1: propagated, ready to resample
     bool steps_done = false;
     int32_t graph_mode[2] = {-1, -1};  // obs layout each captured graph was built for
+    int32_t step_kernels = -1;         // kernel nodes of the latest captured step graph
 
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;

@@ -72,6 +72,9 @@ _SIGS = {
                                                  c_void_p]),
     "pf_set_schedule": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
     "pf_set_auxiliary": (c_int32, [c_void_p, c_int32]),
+    "pf_estimate_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "pf_estimate_wait": (c_int32, [c_void_p]),
+    "pf_step_kernels": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_resampling": (c_int32, [c_void_p, c_double]),
     "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
@@ -270,6 +273,16 @@ def use_torch_allocator(enable: bool = True):
 # ---------------------------------------------------------------------------
 # Convenience wrapper
 # ---------------------------------------------------------------------------
+class _PendingEstimate:
+    def __init__(self, f, buf, matrix):
+        self.f, self.buf, self.matrix = f, buf, matrix
+
+    def wait(self):
+        _check(lib().pf_estimate_wait(self.f.h), self.f.h)
+        out = self.buf.numpy().copy()
+        return out.reshape(self.f.M, self.f.spec.dx) if self.matrix else out
+
+
 class EnsembleFilter:
     """M independent bootstrap filters on the GPU (Sec. 3.1) behind the C ABI."""
 
@@ -340,6 +353,26 @@ class EnsembleFilter:
         if per_filter and kind == PF_STAT_MEAN and var < 0:
             return out.reshape(self.M, self.spec.dx)
         return out
+
+    def estimate_async(self, kind: int = PF_STAT_MEAN, var: int = -1, per_filter: bool = False):
+        """Enqueue the copy of a statistic into pinned host memory without waiting
+        (pf_estimate_async); the returned handle's wait() blocks until that copy
+        alone is done (pf_estimate_wait) and gives the values.  Only the latest
+        handle of a filter may be waited on."""
+        import torch
+        n = self.spec.dx if kind == PF_STAT_MEAN and var < 0 else 1
+        if per_filter:
+            n *= self.M
+        buf = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        st = pf_stat(kind, var, 1 if per_filter else 0)
+        _check(lib().pf_estimate_async(self.h, ctypes.byref(st), buf.data_ptr()), self.h)
+        return _PendingEstimate(self, buf, per_filter and kind == PF_STAT_MEAN and var < 0)
+
+    def step_kernels(self) -> int:
+        """Kernels one step launches (kernel nodes of the captured step graph)."""
+        n = c_int32(0)
+        _check(lib().pf_step_kernels(self.h, ctypes.byref(n)), self.h)
+        return n.value
 
     # -- inspection
     @property

@@ -2,7 +2,8 @@
 
 * With the threshold at 1 (the adaptive code path, resampling at every step
   in practice) the particles and ancestors equal the default path's bit for
-  bit, and estimates and evidence agree to FP64 rounding.
+  bit, and estimates and evidence agree to FP64 rounding: the fused one-tile
+  resampling kernel against the tile chain.
 * At threshold 0.5: statistical parity with the FP64 oracle's adaptive filter
   (oracle.sir_run) on Lorenz 63 and the lattice, including the fraction of
   steps that resample; on the linear-Gaussian model the ensemble converges to
@@ -37,7 +38,9 @@ def test_threshold_one_matches_the_default_path(lattice):
     spec = W.fhn_lattice(J=8) if lattice else W.lorenz63()
     _, y = oracle.simulate(spec, 5, W.SEED_FHN_OBS if lattice else W.SEED_LORENZ_OBS)
     y = y.astype(np.float32)
-    N = W.ragged_counts(5, 40, 1500, seed=2)
+    # filters of one tile (<= 1024 particles) and of several: the default path resamples the
+    # former in one fused kernel each, the adaptive path takes the tile chain for every filter
+    N = np.array([1500, 40, 1024, 2049, 300, 7], dtype=np.int32)
     a = _run(spec, len(N), N, y, 3, None, 1)
     b = _run(spec, len(N), N, y, 3, 1.0, 1)
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])

@@ -167,6 +167,48 @@ def test_step_equals_propagate_then_resample_and_device_obs():
         assert np.array_equal(x, outs[0][0]) and np.array_equal(e, outs[0][1])
 
 
+def test_asynchronous_estimates_equal_synchronous():
+    """pf_estimate_async read one step late (step t+1 already enqueued) gives the
+    values pf_estimate gives right after step t, for every statistic it offers."""
+    spec = W.lorenz63()
+    _, y = oracle.simulate(spec, 6, W.SEED_LORENZ_OBS)
+    y32 = y.astype(np.float32)
+    N = W.ragged_counts(9, 16, 600, seed=2)
+    kinds = [(pf.PF_STAT_MEAN, -1, False), (pf.PF_STAT_MEAN, 1, False), (pf.PF_STAT_MEAN, -1, True),
+             (pf.PF_STAT_MEAN, 2, True), (pf.PF_STAT_LOG_EVIDENCE, -1, True), (pf.PF_STAT_ESS, -1, True)]
+    sync_vals = []
+    with pf.EnsembleFilter(spec, len(N), N, 4) as f:
+        for t in range(6):
+            f.step(y32[t])
+            sync_vals.append([f.estimate(k, var=v, per_filter=p) for k, v, p in kinds])
+    with pf.EnsembleFilter(spec, len(N), N, 4) as f:
+        with pytest.raises(pf.PFError) as e:
+            f.estimate_async()
+        assert e.value.status == pf.PF_ESTATE  # no step yet
+        pending = None
+        for t in range(7):
+            if t < 6:
+                f.step(y32[t])
+            if pending is not None:  # step t is enqueued: read step t-1's statistic
+                k = (t - 1) % len(kinds)
+                assert np.array_equal(pending.wait(), sync_vals[t - 1][k]), (t, kinds[k])
+            if t < 6:
+                k, v, p = kinds[t % len(kinds)]
+                pending = f.estimate_async(k, var=v, per_filter=p)
+    with pf.EnsembleFilter(spec, len(N), N, 4) as f:
+        pending = None
+        for t in range(6):
+            f.step(y32[t])
+            if pending is not None:
+                got = pending.wait()
+                assert np.array_equal(got, sync_vals[t - 1][2]), t
+            pending = f.estimate_async(pf.PF_STAT_MEAN, var=-1, per_filter=True)
+        assert np.array_equal(pending.wait(), sync_vals[5][2])
+        with pytest.raises(pf.PFError) as e:
+            f.estimate_async(pf.PF_STAT_ESS)
+        assert e.value.status == pf.PF_EUNSUPPORTED  # the M-average of ESS is formed by pf_estimate
+
+
 def test_per_filter_observation_streams():
     spec = W.lorenz63()
     M, N, T = 4, 256, 3
