@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
                 f[1] = ff_add(f[1], __fmul_rn(w, w));
                 const uint64_t qv = quant_f32(w, fd.shift);
                 qs += qv;
-                a.C[td.gstart + j] = qv;  // the scan turns these into the prefix
+                a.C[td.gstart + j] = qv;  // the scan reads them back
                 a.B[td.gstart + j] = -1;
             }
         }
@@ -896,17 +896,25 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
     // blocked items: thread j owns tile positions [j * kItems, (j + 1) * kItems)
     const int j0 = threadIdx.x * kItems;
     uint64_t q[kItems];
+    if (!Direct && j0 + kItems <= td.len && ((td.gstart + j0) & 1) == 0) {  // q from k_weights, 16-byte loads
+        const ulonglong2 q01 = *reinterpret_cast<const ulonglong2 *>(a.C + td.gstart + j0);
+        const ulonglong2 q23 = *reinterpret_cast<const ulonglong2 *>(a.C + td.gstart + j0 + 2);
+        q[0] = q01.x, q[1] = q01.y, q[2] = q23.x, q[3] = q23.y;
+    } else {
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) {
+            const int j = j0 + r;
+            q[r] = 0;
+            if (j < td.len) {
+                const int64_t p = td.gstart + j;
+                q[r] = Direct ? quant_f64(a.w_direct[p], fd.shift) : a.C[p];
+            }
+        }
+    }
     uint64_t tsum = 0;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const int j = j0 + r;
-        q[r] = 0;
-        if (j < td.len) {
-            const int64_t p = td.gstart + j;
-            q[r] = Direct ? quant_f64(a.w_direct[p], fd.shift) : a.C[p];  // q from k_weights
-        }
-        tsum += q[r];
-    }
+    for (int r = 0; r < kItems; ++r) tsum += q[r];
+    // the prefix C_k stays in registers: nothing after the counts reads it
     uint64_t Cprev = Cbefore + block_exscan_u64(tsum, shu + 2 * kWarps);  // C_{k-1} before my first item
     int64_t cnt_prev = count_below(Cprev, g);
 #pragma unroll
@@ -914,7 +922,6 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
         const int j = j0 + r;
         if (j >= td.len) break;
         const uint64_t Ck = Cprev + q[r];
-        a.C[td.gstart + j] = Ck;
         if (q[r] > 0) {
             const int64_t cnt = count_below(Ck, g);
             if (cnt > cnt_prev) {
@@ -939,19 +946,66 @@ __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const Tile
     (void)fd;
     const int32_t a0 = a.tile_anc0[blockIdx.x];
     const int j0 = threadIdx.x * kItems;
+    static_assert(kItems == 4, "one int4 of markers per thread");
     int b[kItems];
+    if (j0 + kItems <= td.len && ((td.gstart + j0) & 3) == 0) {
+        const int4 v = *reinterpret_cast<const int4 *>(a.B + td.gstart + j0);
+        b[0] = v.x, b[1] = v.y, b[2] = v.z, b[3] = v.w;
+    } else {
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) b[r] = (j0 + r < td.len) ? a.B[td.gstart + j0 + r] : -1;
+    }
     int tmax = -1;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const int j = j0 + r;
-        b[r] = (j < td.len) ? a.B[td.gstart + j] : -1;
-        tmax = max(tmax, b[r]);
-    }
+    for (int r = 0; r < kItems; ++r) tmax = max(tmax, b[r]);
     int run = max(a0, block_exscan_max_i(tmax, shi));
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
         run = max(run, b[r]);
         anc[r] = run;
+    }
+}
+
+// A thread's kItems consecutive outputs p0 .. p0 + kItems - 1 (the first
+// `left` of them exist): their ancestor indices, the gathered SoA state
+// x_out[v][p] = x_in[v][off + anc] and the running compensated sums of what
+// was gathered, item by item.  Whole aligned groups store as int4 / float4.
+template <int D>
+__device__ __forceinline__ void gather_items(int32_t *anc_out, int64_t off, int64_t p0, int left,
+                                             const int32_t (&anc)[kItems], const float *__restrict__ x_in,
+                                             float *__restrict__ x_out, int64_t P, FF (&f)[D])
+{
+    static_assert(kItems == 4, "one int4 / float4 per thread and variable");
+#pragma unroll
+    for (int v = 0; v < D; ++v) f[v] = FF{0.0f, 0.0f};
+    if (left >= kItems && ((p0 | P) & 3) == 0) {
+        *reinterpret_cast<int4 *>(anc_out + p0) = make_int4(anc[0], anc[1], anc[2], anc[3]);
+#pragma unroll
+        for (int v = 0; v < D; ++v) {
+            const float *xi = x_in + v * P + off;
+            float4 g;
+            g.x = xi[anc[0]];
+            g.y = xi[anc[1]];
+            g.z = xi[anc[2]];
+            g.w = xi[anc[3]];
+            *reinterpret_cast<float4 *>(x_out + v * P + p0) = g;
+            f[v] = ff_add(ff_add(ff_add(ff_add(f[v], g.x), g.y), g.z), g.w);
+        }
+        return;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+        if (r < left) {
+            const int64_t p = p0 + r;
+            anc_out[p] = anc[r];
+            const int64_t src = off + anc[r];
+#pragma unroll
+            for (int v = 0; v < D; ++v) {
+                const float xv = x_in[v * P + src];
+                x_out[v * P + p] = xv;
+                f[v] = ff_add(f[v], xv);
+            }
+        }
     }
 }
 
@@ -974,23 +1028,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
     tile_ancestors(a, td, fd, anc, shi);
     const int j0 = threadIdx.x * kItems;
     FF f[D];
-#pragma unroll
-    for (int v = 0; v < D; ++v) f[v] = FF{0.0f, 0.0f};
-#pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-        const int j = j0 + r;
-        if (j < td.len) {
-            const int64_t p = td.gstart + j;
-            a.anc[p] = anc[r];
-            const int64_t src = fd.off + anc[r];
-#pragma unroll
-            for (int v = 0; v < D; ++v) {
-                const float xv = x_in[v * P + src];
-                x_out[v * P + p] = xv;
-                f[v] = ff_add(f[v], xv);
-            }
-        }
-    }
+    gather_items<D>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, f);
     double s[D];
     block_sum_ff<D>(f, s, shd);
     if (fd.tile_count == 1) {  // the tile is the filter
@@ -1074,7 +1112,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
     const int32_t t = a.d_t ? *a.d_t + 1 : 0;
     const uint32_t U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
     const Grid g = make_grid(Ctot, U, (int64_t)fd.N);
-    if (threadIdx.x == 0) {  // filter scalars (FP64)
+    if (threadIdx.x == 0) {  // the FP64 scalars follow in k_whole_finish, a thread per filter
         double *fs = a.fstats + (int64_t)td.m * kFsCount;
         fs[kFsMax] = (double)mx;
         fs[kFsDegenerate] = degenerate ? 1.0 : 0.0;
@@ -1082,10 +1120,8 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
             atomicOr(&a.err[0], kErrDegenerate);
             atomicCAS(&a.err[1], -1, td.m);
         }
-        const double logZ = (double)mx + log(s[0]);
-        fs[kFsLogZ] = logZ;
-        fs[kFsEss] = s[0] * s[0] / s[1];
-        if (a.d_t) fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)fd.N) + a.log_const;
+        fs[kFsS0] = s[0];
+        fs[kFsS1] = s[1];
         a.fint[(int64_t)td.m * 2] = Ctot;
         a.fint[(int64_t)td.m * 2 + 1] = U;
         a.fmax_key[td.m] = kNegInfKey;
@@ -1136,29 +1172,43 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
         }
     } else {
         constexpr int DD = D;
-        FF fx[DD];
-#pragma unroll
-        for (int v = 0; v < DD; ++v) fx[v] = FF{0.0f, 0.0f};
+        int32_t anc[kItems];
 #pragma unroll
         for (int r = 0; r < kItems; ++r) {
             run = max(run, b[r]);
-            const int j = j0 + r;
-            if (j < td.len) {
-                const int64_t p = td.gstart + j;
-                a.anc[p] = run;
-                const int64_t src = fd.off + run;
-#pragma unroll
-                for (int v = 0; v < DD; ++v) {
-                    const float xv = x_in[v * P + src];
-                    x_out[v * P + p] = xv;
-                    fx[v] = ff_add(fx[v], xv);
-                }
-            }
+            anc[r] = run;
         }
+        FF fx[DD];
+        gather_items<DD>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, fx);
         double sx[DD];
         block_sum_ff<DD>(fx, sx, shd);
-        if (threadIdx.x < DD) est[(int64_t)td.m * DD + threadIdx.x] = sx[threadIdx.x] / (double)fd.N;
+        if (threadIdx.x < DD) est[(int64_t)td.m * DD + threadIdx.x] = sx[threadIdx.x];  // divided by N later
     }
+}
+
+// The FP64 scalars of the one-tile filters, a thread per filter: log Z, ESS,
+// log G (eq. eqGtN) and the per-filter means from the sums k_resample_whole
+// left (the expressions of k_scan_scatter and k_ancestors_small, so the
+// results are those of the tile chain).  Thirty-two filters share each FP64
+// instruction here instead of one thread per CTA issuing them alone: FP64 is
+// a narrow pipe on this GPU.
+__global__ void __launch_bounds__(128) k_whole_finish(const TileDesc *__restrict__ tiles, int32_t tile0, int32_t n,
+                                                      int dx, double *fstats, double *est, const int32_t *d_t,
+                                                      double log_const)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TileDesc td = tiles[tile0 + i];
+    double *fs = fstats + (int64_t)td.m * kFsCount;
+    const double s0 = fs[kFsS0], s1 = fs[kFsS1];
+    const double logZ = fs[kFsMax] + log(s0);
+    fs[kFsLogZ] = logZ;
+    fs[kFsEss] = s0 * s0 / s1;
+    if (d_t) {
+        const int32_t t = *d_t + 1;
+        fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)td.N) + log_const;
+    }
+    for (int v = 0; v < dx; ++v) est[(int64_t)td.m * dx + v] /= (double)td.N;
 }
 
 // Ancestors only (lattice models and the stateless entry point).
@@ -1758,6 +1808,8 @@ void resample_whole(const Ctx &c, const ResampleArgs &a, const float *xi, float 
         const int32_t b0 = c.whole_bounds[k], n = c.whole_bounds[k + 1] - b0;
         if (n) k_resample_whole<D><<<n, 32 << k, 0, s>>>(a, b0, xi, xo, c.P, c.est);
     }
+    const int32_t b0 = c.whole_bounds[0], n = c.whole_bounds[kWholeClasses] - b0;
+    if (n) k_whole_finish<<<(n + 127) / 128, 128, 0, s>>>(c.tiles, b0, n, D, c.fstats, c.est, a.d_t, a.log_const);
 }
 
 template <int D>

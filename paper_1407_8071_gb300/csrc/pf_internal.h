@@ -73,7 +73,8 @@ enum FStat : int {
     kFsLse2 = 6,  // auxiliary filter: log sum of the second-stage weights (log N before the first step)
     kFsSumW = 7,  // auxiliary filter: sum of exp(lw2 - max) behind the weighted means
     kFsResampled = 8,  // adaptive resampling: 1 where the filter resampled this step
-    kFsCount = 10
+    kFsS0 = 9, kFsS1 = 10,  // one-tile filters: sum w and sum w^2, finished by a thread per filter
+    kFsCount = 12
 };
 // Per-tile FP64 partial sums.
 enum TSum : int { kTsW = 0, kTsW2 = 1, kTsCount = 2 };
@@ -95,7 +96,7 @@ struct ResampleArgs {
     uint64_t *tile_q;        // [tiles] exact sum of the quantised weights
     double *fstats;          // [M][kFsCount]
     uint64_t *fint;          // [M][2]: C_{N-1} and the resampling uniform U (u = U 2^-32)
-    uint64_t *C;             // [P] inclusive prefix of the quantised weights
+    uint64_t *C;             // [P] the quantised weights q (k_weights -> k_scan_scatter)
     int32_t *B;              // [P] ancestor start markers
     int32_t *anc;            // [P] filter-local ancestors
     int32_t *tile_anc0;      // [tiles] ancestor of each tile's first output (written by the scan)
