@@ -222,14 +222,17 @@ PF_API pf_status pf_estimate_async(pf_ctx *ctx, const pf_stat *stat, double *h_o
 PF_API pf_status pf_estimate_wait(pf_ctx *ctx);
 
 /* Picks the launch schedule of this context's hot kernels by timing the
- * candidates on copies of its particles: for the lattice, particles per CTA
- * (one particle per CTA up to as many as fit in 1024 threads); for every model,
- * threads per resampling tile CTA (64, 128, 256 -- fewer threads and more CTAs
- * for small filters).  The choice is cached per (model, lattice side, K, dx,
- * particle counts) for the process, and reported in h_choice[0..2] (may be
- * NULL): h_choice[0] particles per lattice CTA (0 for the small models, which
- * run one particle per thread), h_choice[1] resampling threads, h_choice[2]
- * lattice nodes per thread (2 or 4; 1 for the small models).  The filter's state, statistics and step counter are unchanged.
+ * candidates on copies of its particles: for the lattice, nodes per thread and
+ * particles per CTA (one particle per CTA up to as many as fit in 1024
+ * threads), and for four nodes per thread whether the kernel is the build for
+ * three or for four CTAs per SM; for every model, threads per resampling tile
+ * CTA (64, 128, 256 -- fewer threads and more CTAs for small filters).  The
+ * choice is cached per (model, lattice side, K, dx, particle counts) for the
+ * process, and reported in h_choice[0..2] (may be NULL): h_choice[0] particles
+ * per lattice CTA (0 for the small models, which run one particle per thread),
+ * h_choice[1] resampling threads, h_choice[2] lattice nodes per thread (2 or 4;
+ * 1 for the small models).  The filter's state, statistics and step counter
+ * are unchanged.
  * Synchronises; needs about one particle buffer of temporary device memory.
  * Errors: PF_ESTATE (between pf_propagate and pf_resample, or recording),
  * PF_ENOMEM, PF_ECUDA. */

@@ -590,10 +590,12 @@ __global__ void __launch_bounds__(1024, 2)
 // bit-identical to the pair kernel's.  One barrier and four shared-memory
 // loads serve four nodes (up/down as float4, left/right as scalars), and the
 // two generator chains interleave.
-constexpr int kFhn4MaxThreads = 512;  // three CTAs per SM at <= 42 registers
+constexpr int kFhn4MaxThreads = 512;
 
-template <bool Noise = true>
-__global__ void __launch_bounds__(kFhn4MaxThreads, 3)
+// MinB: CTAs the compiler must fit per SM (3: at most 42 registers; 4: 32,
+// with a little spilling) -- the autotuner times both.
+template <bool Noise = true, int MinB = 3>
+__global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
     k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
                      const float *__restrict__ x_in, float *__restrict__ x_out, int64_t P, float *logw,
                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
@@ -1652,20 +1654,31 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(k_propagate_fhn<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_propagate_fhn4<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_propagate_fhn4<true, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_propagate_fhn4<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_propagate_fhn4<false, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<true, 4>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<false, 4>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         carveout_set = true;
     }
     float *lw = weigh ? logw : nullptr;
     int32_t *fm = weigh ? fmax : nullptr;
-    if (nodes == 4 && noise)
-        k_propagate_fhn4<true><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs, stride,
-                                                           c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
+    const bool four = c.fhn_quad_ctas == 4;
+    if (nodes == 4 && noise && four)
+        k_propagate_fhn4<true, 4><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+                                                              stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
+    else if (nodes == 4 && noise)
+        k_propagate_fhn4<true, 3><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+                                                              stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
+    else if (nodes == 4 && four)
+        k_propagate_fhn4<false, 4><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+                                                               stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 0);
     else if (nodes == 4)
-        k_propagate_fhn4<false><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
-                                                            stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 0);
+        k_propagate_fhn4<false, 3><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+                                                               stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 0);
     else if (noise)
         k_propagate_fhn<float, true><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,
                                                                  lw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc,

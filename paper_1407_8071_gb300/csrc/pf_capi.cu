@@ -411,7 +411,7 @@ static std::mutex g_tune_mu;
 // keyed by model kind, lattice side, K, dx, total particles, filters and a
 // hash (FNV-1a) of the particle counts, so ragged batches of the same total
 // are told apart
-static std::map<std::tuple<int, int, int, int, int64_t, int32_t, uint64_t>, std::tuple<int, int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int64_t, int32_t, uint64_t>, std::tuple<int, int, int, int>> g_tune_cache;
 
 static uint64_t counts_hash(const std::vector<int32_t> &N)
 {
@@ -932,6 +932,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
             c.fhn_ppc = std::get<0>(it->second);
             c.resample_threads = std::get<1>(it->second);
             c.fhn_nodes = std::get<2>(it->second);
+            c.fhn_quad_ctas = std::get<3>(it->second);
             cached = true;
         }
     }
@@ -965,7 +966,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         std::vector<float> zeros(M * c.mp.dy, 0.0f);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c.d_obs, zeros.data(), zeros.size() * 4, cudaMemcpyHostToDevice, c.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
-        int best_ppc = c.fhn_ppc, best_rt = c.resample_threads, best_nodes = c.fhn_nodes;
+        int best_ppc = c.fhn_ppc, best_rt = c.resample_threads, best_nodes = c.fhn_nodes, best_qc = c.fhn_quad_ctas;
         auto trial_step = [&] {
             cudaMemcpyAsync(scratch, c.x[c.cur], xb, cudaMemcpyDeviceToDevice, c.stream);
             launch_propagate(c, c.d_obs, 0, scratch, scratch, c.stream);
@@ -977,15 +978,18 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
                 const int per = c.mp.J * c.mp.J / nodes, cap = nodes == 4 ? 512 : 1024;
                 int maxp = 1;
                 while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
-                for (int ppc = 1; ppc <= maxp; ++ppc) {
-                    c.fhn_nodes = nodes;
-                    c.fhn_ppc = ppc;
-                    const float ms = time_ms(c, 3, trial_step);
-                    if (ms < best) { best = ms; best_ppc = ppc; best_nodes = nodes; }
-                }
+                for (int ppc = 1; ppc <= maxp; ++ppc)
+                    for (int qc = 3; qc <= (nodes == 4 ? 4 : 3); ++qc) {
+                        c.fhn_nodes = nodes;
+                        c.fhn_ppc = ppc;
+                        c.fhn_quad_ctas = qc;
+                        const float ms = time_ms(c, 3, trial_step);
+                        if (ms < best) { best = ms; best_ppc = ppc; best_nodes = nodes; best_qc = qc; }
+                    }
             }
             c.fhn_ppc = best_ppc;
             c.fhn_nodes = best_nodes;
+            c.fhn_quad_ctas = best_qc;
         }
         if (e == cudaSuccess) {  // threads per resampling tile CTA
             int max_len = 1;
@@ -1020,7 +1024,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = std::make_tuple(c.fhn_ppc, c.resample_threads, c.fhn_nodes);
+        g_tune_cache[key] = std::make_tuple(c.fhn_ppc, c.resample_threads, c.fhn_nodes, c.fhn_quad_ctas);
     }
     drop_graphs(c);
     if (h_choice) {

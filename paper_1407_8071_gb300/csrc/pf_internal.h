@@ -190,6 +190,7 @@ struct Ctx {
     int resample_threads = kResampleThreads;
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
     int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, or 0 (4 where J % 4 == 0)
+    int fhn_quad_ctas = 3;         // four-node kernel: CTAs per SM it is compiled for (3 or 4; autotuned)
     // resampling only when the ESS is low (pf_set_resampling; < 0: every step)
     double ess_threshold = -1.0;
     bool adaptive() const { return ess_threshold >= 0.0 && ess_threshold <= 1.0; }

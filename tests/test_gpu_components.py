@@ -122,6 +122,55 @@ def test_lorenz_full_size_sampled():
     assert_state_close(xg[sample], xo)
 
 
+def test_lorenz_sweep_one_context_sampled():
+    """The timed launch configuration: the seven M*N = 2^20 rows of the sweep as one context of
+    5461 filters (N from 2^20 down to 256; the tile chain for filters of several tiles, the fused
+    kernel for the others).  Sampled particles of the propagation against the oracle one by one;
+    for one filter of every size, the resampling against the oracle's systematic resampling of
+    the GPU's log-weights, the gather, the per-filter means and the normaliser."""
+    spec = W.lorenz63()
+    N = np.concatenate([np.full(M, n, dtype=np.int32) for M, n in W.lorenz_sweep()])
+    off = np.concatenate([[0], np.cumsum(N)])
+    seed = 2025
+    y = oracle.simulate(spec, 1, W.SEED_LORENZ_OBS)[1][0].astype(np.float32)
+    with pf.EnsembleFilter(spec, len(N), N, seed) as f:
+        x0 = f.get_state()
+        f.propagate(y)
+        xg = f.get_state()
+        lg = f.get_logw()
+        f.resample()
+        anc = f.get_ancestors()
+        x1 = f.get_state()
+        logZ = f.estimate(pf.PF_STAT_LOG_Z, per_filter=True)
+        est = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)
+        ens = f.estimate(pf.PF_STAT_MEAN, var=-1)
+    rng = np.random.default_rng(5)
+    sample = rng.choice(int(off[-1]), size=2000, replace=False)
+    fid = (np.searchsorted(off, sample, side="right") - 1).astype(np.int32)
+    pid = (sample - off[fid]).astype(np.int32)
+    xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid, fid, 1, seed)
+    assert_state_close(xg[sample], xo)
+    lo = oracle.loglik(spec, xg[sample].astype(np.float64), y.astype(np.float64))
+    assert np.max(np.abs(lg[sample] - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+    first = np.concatenate([[0], np.cumsum([M for M, _ in W.lorenz_sweep()])[:-1]])
+    for m in list(first) + [len(N) - 1]:  # the first filter of each row and the very last one
+        a, b = off[m], off[m + 1]
+        l = lg[a:b].astype(np.float64)
+        nrm = oracle.normalise(l)
+        assert logZ[m] == pytest.approx(nrm["logZ"], rel=1e-6)
+        w = np.exp(l - nrm["max"])
+        exp = oracle.systematic(w, oracle.resample_u(seed, int(m), 1))
+        got = anc[a:b]
+        assert np.all(np.diff(got) >= 0) and got.min() >= 0 and got.max() < b - a
+        # FP32 exp moves a systematic boundary only when a grid point falls within ~1e-7 of a C_k
+        assert np.sum(got != exp) <= max(2, (b - a) // 1000), (m, b - a)
+        src = xg[a + got]
+        assert np.array_equal(x1[a:b], src)
+        ref = src.astype(np.float64).mean(axis=0)
+        assert np.all(np.abs(est[m] - ref) <= 1e-6 * np.abs(src).astype(np.float64).mean(axis=0) + 1e-12)
+    assert np.allclose(ens, est.mean(axis=0), rtol=1e-12, atol=1e-12)
+
+
 # ------------------------------------------------------------------ lattice
 def fhn_spec(J, **kw):
     return W.fhn_lattice(J=J, **kw)
