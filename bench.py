@@ -77,8 +77,8 @@ FHN_LOOKAHEAD_OPS_PER_NODE_STEP = 17
 # counter 2, two updates 2 -> 51.5 (look-ahead without the generator: 17).
 FHNP_OPS_PER_NODE_STEP = 51.5
 # With one Euler step per observation the auxiliary step on the paper's lattice
-# moves each particle's state six times (see the roofline below).
-FHNP_STATE_PASSES = 6
+# moves each particle's state four times (see the roofline below).
+FHNP_STATE_PASSES = 4
 
 
 def env_int(name, default):
@@ -577,12 +577,12 @@ def main():
                     "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
                     "ops_per_particle_step": LORENZ_OPS_PER_PARTICLE_STEP, "avg_launch_s": t_prop}
     elif wl.spec.kind == W.FHN_PAPER:
-        # one Euler step per observation: the step streams the state six times (look-ahead read,
-        # gather read + write, second-stage read + write, weighted means read), so HBM bounds it
+        # one Euler step per observation: the step streams the state four times (look-ahead read,
+        # second-stage read of the ancestors' rows + write, weighted means read), so HBM bounds it
         hbm = float(peaks["hbm_gbs"])
         per_launch_bytes = (wl.particles / nf) * wl.spec.dx * 4 * FHNP_STATE_PASSES
         achieved = per_launch_bytes / t_prop / 1e9
-        roofline = {"bound": "hbm", "kernel": "auxiliary step (look-ahead, resampling + gather, second stage, means)",
+        roofline = {"bound": "hbm", "kernel": "auxiliary step (look-ahead, resampling, second stage from the ancestors' rows, means)",
                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                     "peak_source": f"{peak_src} copy bandwidth", "bytes_per_particle_step": wl.spec.dx * 4 *
                     FHNP_STATE_PASSES, "avg_launch_s": t_prop}

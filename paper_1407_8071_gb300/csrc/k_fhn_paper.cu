@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(1024, 1)
             c0 = (uint32_t)fixed_c0;
             c2 = (uint32_t)fixed_c2;
         }
-        const Real *xi = x_in + p * (int64_t)mp.dx;
+        const int64_t row_in = aux.gather ? filt[pfilt[p]].off + aux.gather[p] : p;
+        const Real *xi = x_in + row_in * (int64_t)mp.dx;
         u0 = xi[n0];
         u1 = xi[n0 + 1];
         v0 = xi[nn + n0];

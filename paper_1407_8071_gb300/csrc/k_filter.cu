@@ -491,7 +491,8 @@ __global__ void __launch_bounds__(1024, 2)
             c0 = (uint32_t)fixed_c0;
             c2 = (uint32_t)fixed_c2;
         }
-        const Real *xi = x_in + p * (int64_t)mp.dx;
+        const int64_t row_in = aux.gather ? filt[pfilt[p]].off + aux.gather[p] : p;
+        const Real *xi = x_in + row_in * (int64_t)mp.dx;
         v0 = xi[n0];
         v1 = xi[n0 + 1];
         w0 = xi[nn + n0];
@@ -619,8 +620,9 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
         const int32_t m = pfilt[p];
         c0 = (uint32_t)(p - filt[m].off);
         c2 = (uint32_t)m;
-        const float4 a = *reinterpret_cast<const float4 *>(x_in + p * (int64_t)mp.dx + n0);
-        const float4 b = *reinterpret_cast<const float4 *>(x_in + p * (int64_t)mp.dx + nn + n0);
+        const int64_t row_in = aux.gather ? filt[m].off + aux.gather[p] : p;
+        const float4 a = *reinterpret_cast<const float4 *>(x_in + row_in * (int64_t)mp.dx + n0);
+        const float4 b = *reinterpret_cast<const float4 *>(x_in + row_in * (int64_t)mp.dx + nn + n0);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
         w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
     }
@@ -1885,14 +1887,13 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
                                     AuxPtrs{c.lw2, c.la, nullptr, nullptr}, 0);
         if (e != cudaSuccess) return e;
         resample_ancestors(c, a, th, s);
-        k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(x),
-                                                   reinterpret_cast<float4 *>(xn), dx / 4);
+        // the second stage starts from the ancestors' rows of x: no separate gather pass
         if (c.mp.kind == kFhnPaper)
-            e = launch_fhnp_interval(c, d_obs, stride, xn, xn, c.mp.K, c.lw2, c.fmax2,
-                                     AuxPtrs{nullptr, nullptr, c.la, c.anc}, 1, s);
+            e = launch_fhnp_interval(c, d_obs, stride, x, xn, c.mp.K, c.lw2, c.fmax2,
+                                     AuxPtrs{nullptr, nullptr, c.la, c.anc, c.anc}, 1, s);
         else
-            e = launch_fhn_interval(c, d_obs, stride, xn, xn, c.mp.K, true, s, c.lw2, c.fmax2,
-                                    AuxPtrs{nullptr, nullptr, c.la, c.anc}, 1);
+            e = launch_fhn_interval(c, d_obs, stride, x, xn, c.mp.K, true, s, c.lw2, c.fmax2,
+                                    AuxPtrs{nullptr, nullptr, c.la, c.anc, c.anc}, 1);
         if (e != cudaSuccess) return e;
         k_weight_stats<0><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, nullptr, c.P, c.tile_sums, nullptr,
                                                    c.done, c.fstats, c.est, c.err);

@@ -115,6 +115,8 @@ struct AuxPtrs {
     float *la_out;
     const float *la_src;
     const int32_t *anc;
+    const int32_t *gather;  // lattice kernels: particle p starts from row off_m + gather[p] of x_in (the
+                            // resampling's gather folded into the propagation's first load)
 };
 
 struct Ctx;
