@@ -592,11 +592,12 @@ def main():
         ops_node = base_ops + (FHN_LOOKAHEAD_OPS_PER_NODE_STEP if wl.aux else 0)
         per_launch_ops = (wl.particles / nf) * wl.spec.K * wl.spec.J * wl.spec.J * ops_node
         achieved = per_launch_ops / t_prop / 1e12
-        kern = ("k_propagate_fhn<float>" if wl.theta is None else "proposal propagate (5 kernels)") if not wl.aux \
+        lattice_kernel = "k_propagate_fhn4" if wl.choice and wl.choice[2] == 4 else "k_propagate_fhn<float>"
+        kern = (lattice_kernel if wl.theta is None else "proposal propagate (5 kernels)") if not wl.aux \
             else "auxiliary step (look-ahead + second-stage propagate + resampling)"
         roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                     "frac": achieved / alu_peak,
-                    "traffic": recorded_traffic("k_propagate_fhn<float>") if wl.theta is None else None,
+                    "traffic": recorded_traffic(lattice_kernel) if wl.theta is None and not wl.aux else None,
                     "peak_source": f"152 SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz ({peak_src} max clock)",
                     "ops_per_node_step": FHN_OPS_PER_NODE_STEP, "avg_launch_s": t_prop}
 
