@@ -1196,7 +1196,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
 // results are those of the tile chain).  Thirty-two filters share each FP64
 // instruction here instead of one thread per CTA issuing them alone: FP64 is
 // a narrow pipe on this GPU.
-__global__ void __launch_bounds__(128) k_whole_finish(const TileDesc *__restrict__ tiles, int32_t tile0, int32_t n,
+__global__ void __launch_bounds__(32) k_whole_finish(const TileDesc *__restrict__ tiles, int32_t tile0, int32_t n,
                                                       int dx, double *fstats, double *est, const int32_t *d_t,
                                                       double log_const)
 {
@@ -1824,7 +1824,8 @@ void resample_whole(const Ctx &c, const ResampleArgs &a, const float *xi, float 
         if (n) k_resample_whole<D><<<n, 32 << k, 0, s>>>(a, b0, xi, xo, c.P, c.est);
     }
     const int32_t b0 = c.whole_bounds[0], n = c.whole_bounds[kWholeClasses] - b0;
-    if (n) k_whole_finish<<<(n + 127) / 128, 128, 0, s>>>(c.tiles, b0, n, D, c.fstats, c.est, a.d_t, a.log_const);
+    // one warp per CTA: the FP64 work spreads over every SM's FP64 units
+    if (n) k_whole_finish<<<(n + 31) / 32, 32, 0, s>>>(c.tiles, b0, n, D, c.fstats, c.est, a.d_t, a.log_const);
 }
 
 template <int D>
