@@ -114,6 +114,66 @@ def test_context_resampling_and_normaliser(N):
     assert mismatched <= max(2, M * N // 1000)
 
 
+def test_context_size_classes_in_one_context():
+    """Filters on both sides of every boundary of the fused kernel's size classes (128, 256, 512
+    threads x 4 particles) and of the tile (1024) in one context: each filter's resampling
+    against the oracle, the gather, the per-filter means and the normaliser."""
+    spec = W.lorenz63()
+    N = np.array([1, 2, 127, 128, 129, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2048, 3000],
+                 dtype=np.int32)
+    M, seed = len(N), 77
+    off = np.concatenate([[0], np.cumsum(N)])
+    rng = np.random.default_rng(11)
+    logw = rng.normal(-20.0, 3.0, size=int(off[-1])).astype(np.float32)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.propagate(np.zeros(spec.dy, dtype=np.float32))
+        xbar = f.get_state()
+        f.set_logw(logw)
+        f.resample()
+        anc = f.get_ancestors()
+        x = f.get_state()
+        logZ = f.estimate(pf.PF_STAT_LOG_Z, per_filter=True)
+        ess = f.estimate(pf.PF_STAT_ESS, per_filter=True)
+        est = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)
+    mismatched = 0
+    for m in range(M):
+        a, b = off[m], off[m + 1]
+        l = logw[a:b].astype(np.float64)
+        nrm = oracle.normalise(l)
+        assert logZ[m] == pytest.approx(nrm["logZ"], rel=1e-6)
+        assert ess[m] == pytest.approx(nrm["ess"], rel=1e-5)
+        got = anc[a:b]
+        exp = oracle.systematic(np.exp(l - nrm["max"]), oracle.resample_u(seed, m, 1))
+        mismatched += int(np.sum(got != exp))
+        assert np.all(np.diff(got) >= 0) and got.min() >= 0 and got.max() < b - a
+        src = xbar[a + got]
+        assert np.array_equal(x[a:b], src)
+        ref = src.astype(np.float64).mean(axis=0)
+        assert np.all(np.abs(est[m] - ref) <= 1e-6 * np.abs(src).astype(np.float64).mean(axis=0) + 1e-12)
+    assert mismatched <= max(2, int(off[-1]) // 1000)
+
+
+def test_step_kernel_counts():
+    """pf_step_kernels: the kernels of the captured step graph for each resampling layout."""
+    spec = W.lorenz63()
+    y = np.zeros(spec.dy, dtype=np.float32)
+    # small model: propagate + the tile chain (weights, scan, ancestors) + ensemble
+    for N, want in (([4096, 2048], 5),
+                    # propagate + one fused launch per size class present + finish + ensemble
+                    ([256, 300, 1024], 1 + 3 + 1 + 1),
+                    # both: propagate, chain (3), fused classes (1), finish, ensemble
+                    ([2048, 100], 1 + 3 + 1 + 1 + 1)):
+        with pf.EnsembleFilter(spec, len(N), N, 1) as f:
+            with pytest.raises(pf.PFError):
+                f.step_kernels()  # nothing captured yet
+            f.step(y)
+            assert f.step_kernels() == want, (N, f.step_kernels())
+    lat = W.fhn_lattice(J=8)
+    with pf.EnsembleFilter(lat, 2, 64, 1) as f:  # propagate, fused, finish, gather + means, ensemble
+        f.step(np.zeros(lat.dy, dtype=np.float32))
+        assert f.step_kernels() == 5
+
+
 def test_context_gather_is_exact_and_estimate_within_fp32_partials():
     spec = W.lorenz63()
     M, N, seed = 3, 2000, 5
