@@ -176,7 +176,7 @@ def fhn_spec(J, **kw):
     return W.fhn_lattice(J=J, **kw)
 
 
-@pytest.mark.parametrize("J,M,N", [(2, 2, 5), (2, 3, 17), (8, 3, 40), (20, 2, 9), (40, 1, 3)])
+@pytest.mark.parametrize("J,M,N", [(2, 2, 5), (2, 3, 17), (4, 3, 11), (8, 3, 40), (20, 2, 9), (40, 1, 3)])
 def test_fhn_prior_and_propagate_match_oracle(J, M, N):
     spec = fhn_spec(J)
     seed = 99
