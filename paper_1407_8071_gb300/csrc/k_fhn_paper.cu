@@ -110,9 +110,9 @@ __global__ void __launch_bounds__(1024, 1)
     const Real dt = par_dt<Real>(mp), sq = par_sq<Real>(mp), coup = par<Real>(mp, 7);
     const Real b0 = par<Real>(mp, 4), b1 = par<Real>(mp, 5), b2 = par<Real>(mp, 6);
     const Real Ff = par<Real>(mp, 8), Fpsi = par<Real>(mp, 15), l0 = par<Real>(mp, 16);
-    const int64_t period = (int64_t)mp.p[9], width = (int64_t)mp.p[10];
-    const int fcols = (int)mp.p[11];
-    const uint32_t eps_thr = (uint32_t)mp.p[14];
+    const int64_t period = mp.ip[9], width = mp.ip[10];
+    const int fcols = (int)mp.ip[11];
+    const uint32_t eps_thr = (uint32_t)mp.ip[14];
     const int64_t n_base = (int64_t)(t - 1) * mp.K;  // (n - 1) of sub-step k is n_base + k
     const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
     const bool has_up = row > 0, has_dn = row < J - 1, has_left = col > 0, has_right = col + 2 < J;

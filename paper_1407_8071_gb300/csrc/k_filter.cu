@@ -501,8 +501,8 @@ __global__ void __launch_bounds__(1024, 2)
     const Real dt = par_dt<Real>(mp);
     const Real sq = par_sq<Real>(mp);
     const Real amp = par<Real>(mp, 6);
-    const int64_t stim_steps = (int64_t)mp.p[7];
-    const int blk = (int)mp.p[8];
+    const int64_t stim_steps = mp.ip[7];
+    const int blk = (int)mp.ip[8];
     const bool stim_node0 = row < blk && col < blk, stim_node1 = row < blk && col + 1 < blk;
     const int64_t n_base = (int64_t)(t - 1) * mp.K;  // (n - 1) of sub-step k is n_base + k
     const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
@@ -627,8 +627,8 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
         w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
     }
     const float dt = mp.fdt, sq = mp.fsq, amp = mp.fp[6];
-    const int64_t stim_steps = (int64_t)mp.p[7];
-    const int blk = (int)mp.p[8];
+    const int64_t stim_steps = mp.ip[7];
+    const int blk = (int)mp.ip[8];
     const int64_t n_base = (int64_t)(t - 1) * mp.K;
     const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
     const int qu = row > 0 ? q - qrow : q, qd = row < J - 1 ? q + qrow : q;

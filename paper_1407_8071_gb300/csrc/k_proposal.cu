@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(1024, 2) k_last_step_fhn(ModelParams mp, Key k
         float lap[2];
         pair_laplacian<float>(v[0], v[1], up.x, up.y, dn.x, dn.y, left, right, lap[0], lap[1]);
         const int64_t n_base = (int64_t)(t - 1) * mp.K;
-        const bool on = (n_base + k) < (int64_t)mp.p[7];
-        const int blk = (int)mp.p[8];
+        const bool on = (n_base + k) < mp.ip[7];
+        const int blk = (int)mp.ip[8];
         float z[4];
         normals4<float>(key, c0, t, c2, kStreamDyn, (uint32_t)k * (uint32_t)(mp.dx / 4) + (uint32_t)q, z);
         const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);

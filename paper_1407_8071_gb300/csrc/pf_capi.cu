@@ -305,7 +305,10 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
     for (int j = 0; j < obs->dy && j < kMaxObsSmall; ++j) mp.obs_small[j] = obs->idx[j];
     if (!is_lattice(model->kind))
         for (int v = 0; v < model->dx; ++v) mp.x0_small[v] = noise->x0_mean[v];
-    for (int i = 0; i < 24; ++i) mp.fp[i] = (float)mp.p[i];
+    for (int i = 0; i < 24; ++i) {
+        mp.fp[i] = (float)mp.p[i];
+        mp.ip[i] = (std::isfinite(mp.p[i]) && std::fabs(mp.p[i]) < 9.0e18) ? (int64_t)mp.p[i] : 0;
+    }
     mp.fdt = (float)dt;
     mp.dsq = noise->sigma_dyn * std::sqrt(dt);
     mp.fsq = (float)mp.dsq;

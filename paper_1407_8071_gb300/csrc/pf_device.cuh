@@ -157,8 +157,10 @@ struct ModelParams {
     int32_t dy;
     int32_t obs_small[kMaxObsSmall];  // observation indices when dy <= kMaxObsSmall
     double x0_small[kMaxLgDim];       // prior mean for the small models
-    // FP32 copies made once on the host (FP64 is a narrow pipe on this GPU):
+    // FP32 and integer copies made once on the host (FP64 is a narrow pipe on this
+    // GPU, and converting a double to an integer runs on it):
     float fp[24];      // p
+    int64_t ip[24];    // p truncated toward zero (the integer-valued parameters: step counts, sizes)
     float fdt;         // dt
     float fsq;         // sigma_dyn * sqrt(dt)
     float fhalf_prec;  // -1 / (2 sigma_obs^2)
