@@ -185,6 +185,148 @@ __global__ void __launch_bounds__(1024, 2) k_last_step_fhn(ModelParams mp, Key k
     }
 }
 
+// The same last sub-step with four nodes per thread (lattice sides divisible
+// by 4), the layout of k_propagate_fhn4: float4 loads and stores of a quad's v
+// and w, one shared-memory exchange, the two pairs' normals, the per-node
+// arithmetic of k_last_step_fhn in the same order, and the per-pair partial sums
+// reduced per particle in the pair kernel's order -- so the results are the
+// pair kernel's bit for bit, with four CTAs or three per SM instead of two.
+constexpr int kLast4MaxThreads = 512;
+
+template <int MinB>
+__global__ void __launch_bounds__(kLast4MaxThreads, MinB)
+    k_last_step_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt, float *x, int64_t P,
+                     const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
+                     const float *mlp_out, float *xboot, float *mp_obs, float *logw, float *logw_boot)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int J = mp.J, nn = J * J, quads = nn / 4, pairs = nn / 2, qrow = J / 4, dy = mp.dy;
+    float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [ppc][quads]
+    const int slot = (int)threadIdx.x / quads;
+    const int s = min(slot, ppc);
+    const int q = threadIdx.x - min(slot, ppc - 1) * quads;
+    const int64_t p = (int64_t)blockIdx.x * ppc + s;
+    const bool active = (s < ppc) && (p < P);
+    const uint32_t t = (uint32_t)(*d_t + 1);
+    const int k = mp.K - 1;
+    uint32_t c0 = 0, c2 = 0;
+    float v[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
+    const int n0 = 4 * q, row = n0 / J, col = n0 - row * J;
+    int32_t m = 0;
+    if (active) {
+        m = pfilt[p];
+        c0 = (uint32_t)(p - filt[m].off);
+        c2 = (uint32_t)m;
+        const float4 a = *reinterpret_cast<const float4 *>(x + p * (int64_t)mp.dx + n0);
+        const float4 b = *reinterpret_cast<const float4 *>(x + p * (int64_t)mp.dx + nn + n0);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
+        sv[s * quads + q] = a;
+    }
+    __syncthreads();
+    float part_prop[2] = {0.f, 0.f}, part_boot[2] = {0.f, 0.f}, lw[2] = {0.f, 0.f};
+    if (active) {
+        const float dt = mp.fdt, h = mp.fsq;
+        const float4 *buf = sv + s * quads;
+        const int qu = row > 0 ? q - qrow : q, qd = row < J - 1 ? q + qrow : q;
+        const bool has_left = col > 0, has_right = col + 4 < J;
+        const float4 up = buf[qu], dn = buf[qd];
+        const float left = has_left ? buf[q - 1].w : v[0], right = has_right ? buf[q + 1].x : v[3];
+        float lap[4];
+        pair_laplacian<float>(v[0], v[1], up.x, up.y, dn.x, dn.y, left, v[2], lap[0], lap[1]);
+        pair_laplacian<float>(v[2], v[3], up.z, up.w, dn.z, dn.w, v[1], right, lap[2], lap[3]);
+        const int64_t n_base = (int64_t)(t - 1) * mp.K;
+        const bool on = (n_base + k) < mp.ip[7];
+        const int blk = (int)mp.ip[8];
+        float z[8];
+        const uint32_t bk = (uint32_t)k * (uint32_t)(mp.dx / 4) + 2u * (uint32_t)q;
+        normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
+        normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+        const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
+        const float inv_h = 1.0f / h;
+        float nvs[4], nws[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int node = n0 + e, hp = e >> 1;
+            const bool stim = on && row < blk && col + e < blk;
+            const float I = stim ? par<float>(mp, 6) : 0.0f;
+            const float fv = fhn_drift_v<float>(mp, v[e], w[e], lap[e], I), fw = fhn_drift_w<float>(mp, v[e], w[e]);
+            const float mv = __fmaf_rn(dt, fv, v[e]), mw = __fmaf_rn(dt, fw, w[e]);
+            const float zv = z[2 * e], zw = z[2 * e + 1];
+            const float bv = __fmaf_rn(h, zv, mv), bw = __fmaf_rn(h, zw, mw);  // = em_update
+            float nv = bv, nw = bw;
+            const int j = obs_slot[node];
+            if (j >= 0) {
+                float o[4] = {0.f, 0.f, 0.f, 0.f};
+                if (mlp_out) {
+                    const float4 oo = reinterpret_cast<const float4 *>(mlp_out)[p * dy + j];
+                    o[0] = oo.x; o[1] = oo.y; o[2] = oo.z; o[3] = oo.w;
+                }
+                const float mc[2] = {mv, mw}, zc[2] = {zv, zw};
+                float xn[2];
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const float os = fminf(fmaxf(o[2 + cc], -mlp::kClamp), mlp::kClamp);
+                    const float mu = __fmaf_rn(h, o[cc], mc[cc]);
+                    const float es = __expf(os);
+                    const float sd = h * es;
+                    xn[cc] = __fmaf_rn(sd, zc[cc], mu);
+                    const float t1 = (xn[cc] - mc[cc]) * inv_h, t2 = (xn[cc] - mu) * (inv_h / es);
+                    lw[hp] += os + 0.5f * (t2 * t2 - t1 * t1);
+                }
+                nv = xn[0];
+                nw = xn[1];
+                const int64_t oj = (p * dy + j) * 2;
+                xboot[oj] = bv;
+                xboot[oj + 1] = bw;
+                mp_obs[oj] = mv;
+                mp_obs[oj + 1] = mw;
+                const float ep = y[j] - nv, eb = y[j] - bv;
+                part_prop[hp] += ep * ep;
+                part_boot[hp] += eb * eb;
+            }
+            nvs[e] = nv;
+            nws[e] = nw;
+        }
+        float *xo = x + p * (int64_t)mp.dx;
+        *reinterpret_cast<float4 *>(xo + n0) = make_float4(nvs[0], nvs[1], nvs[2], nvs[3]);
+        *reinterpret_cast<float4 *>(xo + nn + n0) = make_float4(nws[0], nws[1], nws[2], nws[3]);
+    }
+    // per-pair partials, then per particle in the pair kernel's order
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(smem_raw);  // [3][ppc][pairs]
+    const int np = ppc * pairs;
+    if (active) {
+#pragma unroll
+        for (int hp = 0; hp < 2; ++hp) {
+            red[s * pairs + 2 * q + hp] = part_prop[hp];
+            red[np + s * pairs + 2 * q + hp] = part_boot[hp];
+            red[2 * np + s * pairs + 2 * q + hp] = lw[hp];
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int sl = warp; sl < ppc; sl += nwarps) {
+        const int64_t pp = (int64_t)blockIdx.x * ppc + sl;
+        float a = 0.0f, b = 0.0f, c = 0.0f;
+        for (int i = lane; i < pairs; i += 32) {
+            a += red[sl * pairs + i];
+            b += red[np + sl * pairs + i];
+            c += red[2 * np + sl * pairs + i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0 && pp < P) {
+            logw[pp] = mp.fhalf_prec * a + c;
+            logw_boot[pp] = mp.fhalf_prec * b;
+        }
+    }
+}
+
 // Per filter: the ESS of the proposal weights; below ess_frac N the step takes
 // the transition's candidates and weights instead (the bootstrap fallback).
 // Also sets the filter's maximum log-weight for the resampling chain.
@@ -336,9 +478,28 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
         if (e != cudaSuccess) return e;
         mo = c.mlp_out;
     }
-    const size_t smem_last = std::max((size_t)ppc * pairs * sizeof(float2), (size_t)3 * threads * sizeof(float));
-    k_last_step_fhn<<<grid, threads, smem_last, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride, c.obs_slot,
-                                                     c.d_t, ppc, mo, c.xboot, c.mp_obs, c.logw, c.logw_boot);
+    if (c.fhn_nodes != 2 && c.mp.J % 4 == 0) {  // four nodes per thread, as the sub-steps
+        const int quads = c.mp.J * c.mp.J / 4;
+        int n4 = 1;
+        while ((n4 + 1) * quads <= kLast4MaxThreads && n4 < 8) ++n4;
+        if (c.fhn_ppc > 0 && c.fhn_ppc < n4) n4 = c.fhn_ppc;
+        const int threads4 = (n4 * quads + 31) / 32 * 32;
+        const unsigned grid4 = (unsigned)((c.P + n4 - 1) / n4);
+        const size_t smem4 = (size_t)3 * n4 * pairs * sizeof(float);  // >= the v-planes (n4 * J * J floats)
+        if (c.fhn_quad_ctas == 4)
+            k_last_step_fhn4<4><<<grid4, threads4, smem4, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
+                                                               c.obs_slot, c.d_t, n4, mo, c.xboot, c.mp_obs, c.logw,
+                                                               c.logw_boot);
+        else
+            k_last_step_fhn4<3><<<grid4, threads4, smem4, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
+                                                               c.obs_slot, c.d_t, n4, mo, c.xboot, c.mp_obs, c.logw,
+                                                               c.logw_boot);
+    } else {
+        const size_t smem_last = std::max((size_t)ppc * pairs * sizeof(float2), (size_t)3 * threads * sizeof(float));
+        k_last_step_fhn<<<grid, threads, smem_last, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
+                                                         c.obs_slot, c.d_t, ppc, mo, c.xboot, c.mp_obs, c.logw,
+                                                         c.logw_boot);
+    }
     k_proposal_select<<<c.M, 256, 0, s>>>(c.filt, c.mp, c.prop_ess_frac, c.prop_on ? 1 : 0, c.logw, c.logw_boot, x,
                                           c.xboot, c.obs_idx, c.fmax_key, c.fstats);
     const int64_t rows = c.P * c.mp.dy;

@@ -64,11 +64,12 @@ def test_autotune_preserves_the_filter(spec_name):
     assert np.allclose(za, zb, rtol=1e-12, atol=1e-12)
 
 
-@pytest.mark.parametrize("J", [8, 20, 6])
-def test_lattice_schedules_give_identical_filters(J):
+@pytest.mark.parametrize("J,proposal", [(8, False), (20, False), (6, False), (8, True), (20, True)])
+def test_lattice_schedules_give_identical_filters(J, proposal):
     """Two or four nodes per thread and any number of particles per CTA: the
     same particles, log-weights and ancestors bit for bit (the four-node
-    kernel keeps the pair kernel's arithmetic and reduction order)."""
+    kernels keep the pair kernels' arithmetic and reduction order), with the
+    bootstrap transition and with the learned proposal's last sub-step."""
     spec = W.fhn_lattice(J=J)
     T = 3
     _, y = oracle.simulate(spec, T, W.SEED_FHN_OBS)
@@ -79,6 +80,8 @@ def test_lattice_schedules_give_identical_filters(J):
     for nodes, ppc, rt in scheds:
         with pf.EnsembleFilter(spec, len(N), N, 23) as f:
             f.set_schedule(nodes, ppc, rt)
+            if proposal:
+                f.set_proposal(_theta(), 0.1)
             for t in range(T):
                 f.step(y[t])
             outs.append((f.get_state(), f.get_logw(), f.get_ancestors(),
