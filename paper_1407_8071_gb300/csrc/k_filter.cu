@@ -2,11 +2,13 @@
 // filters (arXiv:1407.8071, Algorithm 1 run M times, Definition 1 average).
 //
 // One observation step is
-//   propagate+weight  (Alg. 1 step 2a)      k_propagate_small / k_propagate_fhn (+ per-filter max log-weight)
-//   weights           (FP64 sums, eq. eqGtN) k_weights
-//   prefix + scatter  (step 2b, systematic)  k_scan_scatter
-//   ancestors+gather  (step 2b)              k_ancestors_small (+ per-filter means) / k_ancestors + k_gather_rows
-//   estimates         (Def. 1)               (fused above) / k_mean_rows; then k_ensemble
+//   propagate+weight  (Alg. 1 step 2a)      k_propagate_small / k_propagate_fhn(4) (+ per-filter max log-weight)
+//   resampling        (step 2b, systematic; FP64 sums, eq. eqGtN)
+//     filters of several tiles:  k_weights -> k_scan_scatter -> k_ancestors_small (gather, per-filter
+//                                means) / k_ancestors
+//     filters of one tile:       k_resample_whole (one launch per size class) -> k_whole_finish
+//   lattice gather + estimates   k_gather_mean_rows (Def. 1 per filter)
+//   M-average         (Def. 1)               k_ensemble
 // Particles of all filters are contiguous; tiles of <= kTile particles never
 // span two filters, so per-filter reductions read only that filter's tiles
 // and no kernel waits on another block.

@@ -2,10 +2,10 @@
 // recording of training tuples.
 //
 // With a network set, a step of the lattice filter is
-//   k_propagate_fhn       K - 1 ordinary sub-steps (Alg. 1 step 2a, transition)
-//   k_build_rows          network inputs at the observed nodes (BF16)
-//   network forward       tensor cores (k_mlp.cu)
-//   k_last_step_fhn       last sub-step: proposal at the observed nodes, the
+//   k_propagate_fhn(4)    K - 1 ordinary sub-steps (Alg. 1 step 2a, transition)
+//   network forward       tensor cores, input rows gathered from the state
+//                         (k_proposal_tc.cu; k_build_rows when recording tuples)
+//   k_last_step_fhn(4)    last sub-step: proposal at the observed nodes, the
 //                         transition elsewhere; weight g p / q, and the weight
 //                         the transition alone would have given
 //   k_proposal_select     per filter: ESS of the proposal weights; below
