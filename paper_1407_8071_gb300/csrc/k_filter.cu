@@ -309,6 +309,18 @@ __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
 // #{i in [0, N) : t_i < x}: the t_i increase with i, so this is the first i
 // with grid_point(i) >= x N 2^32.  A float estimate is corrected by a short
 // walk on the exact comparison, with bisection as the fallback.
+// The bisection fallback, out of line: it almost never runs, and inlining it
+// at every call site only crowds the instruction cache.
+__device__ __noinline__ int64_t count_bisect(const U128 X, const Grid g)
+{
+    int64_t lo = 0, hi = g.N;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ge128(grid_point((uint64_t)mid, g.U, g.Ctot), X)) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
 __device__ int64_t count_below(uint64_t x, const Grid &g)
 {
     if (x == 0) return 0;
@@ -317,25 +329,20 @@ __device__ int64_t count_below(uint64_t x, const Grid &g)
     const float est = ceilf(__fmaf_rn(xf, g.est_scale, -g.u));
     int64_t i = est <= 0.0f ? 0 : (est >= g.Nf ? g.N : (int64_t)__float2int_rz(est));
     bool settled = false;
+#pragma unroll 1
     for (int it = 0; it < 4; ++it) {
         if (i > 0 && ge128(grid_point((uint64_t)(i - 1), g.U, g.Ctot), X)) --i;
         else { settled = true; break; }
     }
     if (settled) {
         settled = false;
+#pragma unroll 1
         for (int it = 0; it < 4; ++it) {
             if (i < g.N && !ge128(grid_point((uint64_t)i, g.U, g.Ctot), X)) ++i;
             else { settled = true; break; }
         }
     }
-    if (!settled) {
-        int64_t lo = 0, hi = g.N;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (ge128(grid_point((uint64_t)mid, g.U, g.Ctot), X)) hi = mid; else lo = mid + 1;
-        }
-        i = lo;
-    }
+    if (!settled) i = count_bisect(X, g);
     return i;
 }
 
