@@ -64,8 +64,12 @@ __device__ int block_exclusive_scan(int v, int *warp_tot)
 
 }  // namespace
 
-template <typename Real>
-__global__ void __launch_bounds__(1024, 1)
+// MaxT / MinB: the filters' build for lattices whose particle fits 512 threads
+// (J <= 32) is <512, 3> -- at most 40 registers, three CTAs per SM: with one
+// Euler step per observation the kernel streams the state and needs the warps
+// to hide its loads; larger lattices and the FP64 truth record use <1024, 1>.
+template <typename Real, int MaxT = 1024, int MinB = 1>
+__global__ void __launch_bounds__(MaxT, MinB)
     k_propagate_fhnp(ModelParams mp, Key key, uint32_t stream, uint32_t stim_stream, const int32_t *pfilt,
                      const FilterDesc *filt, const Real *__restrict__ x_in, Real *__restrict__ x_out, int64_t P,
                      float *logw, const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t,
@@ -99,13 +103,14 @@ __global__ void __launch_bounds__(1024, 1)
             c2 = (uint32_t)fixed_c2;
         }
         const int64_t row_in = aux.gather ? filt[pfilt[p]].off + aux.gather[p] : p;
-        const Real *xi = x_in + row_in * (int64_t)mp.dx;
-        u0 = xi[n0];
-        u1 = xi[n0 + 1];
-        v0 = xi[nn + n0];
-        v1 = xi[nn + n0 + 1];
-        s0 = xi[2 * nn + n0];
-        s1 = xi[2 * nn + n0 + 1];
+        const Pair *xi = reinterpret_cast<const Pair *>(x_in + row_in * (int64_t)mp.dx + n0);  // n0, nn even
+        const Pair a = xi[0], b = xi[nn / 2], c = xi[nn];
+        u0 = a.x;
+        u1 = a.y;
+        v0 = b.x;
+        v1 = b.y;
+        s0 = c.x;
+        s1 = c.y;
     }
     const Real dt = par_dt<Real>(mp), sq = par_sq<Real>(mp), coup = par<Real>(mp, 7);
     const Real b0 = par<Real>(mp, 4), b1 = par<Real>(mp, 5), b2 = par<Real>(mp, 6);
@@ -114,6 +119,9 @@ __global__ void __launch_bounds__(1024, 1)
     const int fcols = (int)mp.ip[11];
     const uint32_t eps_thr = (uint32_t)mp.ip[14];
     const int64_t n_base = (int64_t)(t - 1) * mp.K;  // (n - 1) of sub-step k is n_base + k
+    // (n_base + k) mod period, advanced per sub-step; 32-bit division when both fit
+    int64_t phase = (n_base < 0x7FFFFFFF && period < 0x7FFFFFFF)
+                        ? (int64_t)((uint32_t)n_base % (uint32_t)period) : n_base % period;
     const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
     const bool has_up = row > 0, has_dn = row < J - 1, has_left = col > 0, has_right = col + 2 < J;
     const int qu = has_up ? q - half : q, qd = has_dn ? q + half : q;
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(1024, 1)
             nb0 = nb0 + (has_left ? lf.y : (Real)0) + u1;
             Real nb1 = (has_up ? up.y : (Real)0) + (has_dn ? dn.y : (Real)0);
             nb1 = nb1 + u0 + (has_right ? rt.x : (Real)0);
-            const bool on = ((n_base + k) % period) < width;
+            const bool on = phase < width;
             const Real F0 = (on && col < fcols) ? Ff : (Real)0, F1 = (on && col + 1 < fcols) ? Ff : (Real)0;
             const Real P0 = s0 < l0 ? Fpsi : (Real)0, P1 = s1 < l0 ? Fpsi : (Real)0;
             const Real fu0 = fhnp_p3<Real>(mp, u0) - v0 + coup * nb0 + F0 + P0;
@@ -208,15 +216,17 @@ __global__ void __launch_bounds__(1024, 1)
             v0 = em_update(v0, fv0, (Real)0, dt, sq);
             v1 = em_update(v1, fv1, (Real)0, dt, sq);
         }
+        if (++phase == period) phase = 0;
     }
     if (active && x_out) {
-        Real *xo = x_out + p * (int64_t)mp.dx;
-        xo[n0] = u0;
-        xo[n0 + 1] = u1;
-        xo[nn + n0] = v0;
-        xo[nn + n0 + 1] = v1;
-        xo[2 * nn + n0] = s0;
-        xo[2 * nn + n0 + 1] = s1;
+        Pair *xo = reinterpret_cast<Pair *>(x_out + p * (int64_t)mp.dx + n0);
+        Pair a, b, c;
+        a.x = u0, a.y = u1;
+        b.x = v0, b.y = v1;
+        c.x = s0, c.y = s1;
+        xo[0] = a;
+        xo[nn / 2] = b;
+        xo[nn] = c;
     }
     if (!logw) return;
     // log-likelihood over the observed U nodes, per particle, fixed order (as the RM kernel)
@@ -259,16 +269,24 @@ cudaError_t launch_fhnp_interval(const Ctx &c, const float *d_obs, int32_t strid
                                  cudaStream_t s)
 {
     const int pairs = c.mp.J * c.mp.J / 2;
+    const bool small = pairs <= 512;  // a particle fits the 512-thread build
+    const int cap = small ? 512 : 1024;
     int n = 1;
-    while ((n + 1) * pairs <= 1024 && n < kMaxSlots) ++n;
+    while ((n + 1) * pairs <= cap && n < kMaxSlots) ++n;
     if (c.fhn_ppc > 0 && c.fhn_ppc < n) n = c.fhn_ppc;
     const int ppc = n, threads = (ppc * pairs + 31) / 32 * 32;
     const size_t planes = 2 * (size_t)ppc * c.mp.J * c.mp.J * sizeof(float), red = (size_t)threads * sizeof(float);
     const size_t smem = planes > red ? planes : red;
     const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
-    k_propagate_fhnp<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, kStreamMisc, c.pfilt, c.filt, xi, xo,
-                                                        c.P, logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0, ppc,
-                                                        fmax, n_steps, aux, noise);
+    if (small)
+        k_propagate_fhnp<float, 512, 3><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, kStreamMisc, c.pfilt,
+                                                                    c.filt, xi, xo, c.P, logw, d_obs, stride,
+                                                                    c.obs_slot, c.d_t, 0, 0, 0, ppc, fmax, n_steps,
+                                                                    aux, noise);
+    else
+        k_propagate_fhnp<float><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, kStreamMisc, c.pfilt, c.filt, xi,
+                                                            xo, c.P, logw, d_obs, stride, c.obs_slot, c.d_t, 0, 0, 0,
+                                                            ppc, fmax, n_steps, aux, noise);
     return cudaGetLastError();
 }
 

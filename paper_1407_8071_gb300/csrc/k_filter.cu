@@ -1383,6 +1383,98 @@ __global__ void __launch_bounds__(256) k_gather_mean_rows(const FilterDesc *filt
     }
 }
 
+// k_mean_rows with four consecutive variables per thread (dx % 4 == 0, rows
+// 16-byte aligned): float4 loads, four times the bytes in flight per
+// instruction; each variable's compensated sum runs over the chunk's particles
+// in the same order, so the estimates are k_mean_rows' own.
+__global__ void __launch_bounds__(256) k_mean_rows4(const FilterDesc *filt, const TileDesc *__restrict__ chunks,
+                                                    const float *__restrict__ x, int dx, double *part, int32_t *cnt,
+                                                    double *est, const float *__restrict__ lw2,
+                                                    const int32_t *__restrict__ fmax2, const double *fstats)
+{
+    __shared__ int last;
+    const TileDesc ch = chunks[blockIdx.x];
+    const FilterDesc fd = filt[ch.m];
+    const int v4 = blockIdx.y * blockDim.x + threadIdx.x, dx4 = dx >> 2;
+    const float mx = lw2 ? float_from_order_key(fmax2[ch.m]) : 0.0f;
+    const double denom = lw2 ? fstats[(int64_t)ch.m * kFsCount + kFsSumW] : (double)fd.N;
+    double mine[4] = {0.0, 0.0, 0.0, 0.0};
+    if (v4 < dx4) {
+        const float4 *base = reinterpret_cast<const float4 *>(x + ch.gstart * (int64_t)dx) + v4;
+        FF acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+        int i = 0;
+        for (; i + 8 <= ch.len; i += 8) {  // eight rows in flight, then the ordered adds
+            float4 r[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = base[(int64_t)(i + k) * dx4];
+            if (lw2) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const float wk = aux_weight(lw2[ch.gstart + i + k], mx);
+                    r[k].x *= wk, r[k].y *= wk, r[k].z *= wk, r[k].w *= wk;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[0] = ff_add(acc[0], r[k].x);
+                acc[1] = ff_add(acc[1], r[k].y);
+                acc[2] = ff_add(acc[2], r[k].z);
+                acc[3] = ff_add(acc[3], r[k].w);
+            }
+        }
+        for (; i < ch.len; ++i) {
+            float4 r = base[(int64_t)i * dx4];
+            const float wk = lw2 ? aux_weight(lw2[ch.gstart + i], mx) : 1.0f;
+            acc[0] = ff_add(acc[0], r.x * wk);
+            acc[1] = ff_add(acc[1], r.y * wk);
+            acc[2] = ff_add(acc[2], r.z * wk);
+            acc[3] = ff_add(acc[3], r.w * wk);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) mine[e] = ff_to_double(acc[e]);
+    }
+    if (fd.mc_count == 1) {  // the whole filter in this chunk (uniform over the CTA)
+        if (v4 < dx4)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) est[(int64_t)ch.m * dx + 4 * v4 + e] = mine[e] / denom;
+        return;
+    }
+    if (v4 < dx4)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) part[(int64_t)blockIdx.x * dx + 4 * v4 + e] = mine[e];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *c = cnt + (int64_t)ch.m * gridDim.y + blockIdx.y;
+        last = (atomicAdd(c, 1) == fd.mc_count - 1);
+        if (last) *c = 0;  // every other chunk of this filter and block has counted
+    }
+    __syncthreads();
+    if (last && v4 < dx4) {
+        __threadfence();
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            double sum = 0.0;
+            for (int k = 0; k < fd.mc_count; ++k) sum += __ldcg(&part[(int64_t)(fd.mc_begin + k) * dx + 4 * v4 + e]);
+            est[(int64_t)ch.m * dx + 4 * v4 + e] = sum / denom;
+        }
+    }
+}
+
+// The (weighted) per-filter means of the lattice particles xn.
+void launch_mean_rows(const Ctx &c, const float *xn, const float *lw2, const int32_t *fmax2, const double *fstats,
+                      cudaStream_t s)
+{
+    const int dx = c.mp.dx;
+    if (dx % 4 == 0) {
+        dim3 g(c.n_mchunks, (dx / 4 + 255) / 256);
+        k_mean_rows4<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
+    } else {
+        dim3 g(c.n_mchunks, (dx + 255) / 256);
+        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
+    }
+}
+
 template <int D, bool Evidence = true>
 __global__ void __launch_bounds__(kResampleThreads)
     k_weight_stats(const TileDesc *tiles, const FilterDesc *filt, const float *__restrict__ lw2,
@@ -1802,9 +1894,7 @@ cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t strid
         k_carry<<<(unsigned)((c.P + 255) / 256), 256, 0, s>>>(c.pfilt, c.fstats, c.logw, c.lw2, c.fmax2, c.P);
         k_weight_stats<0, false><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, nullptr, c.P, c.tile_sums,
                                                           nullptr, c.done, c.fstats, c.est, c.err);
-        dim3 g(c.n_mchunks, (dx + 255) / 256);
-        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, c.lw2, c.fmax2,
-                                      c.fstats);
+        launch_mean_rows(c, xn, c.lw2, c.fmax2, c.fstats, s);
     } else {
         switch (dx) {
         case 1: e = adaptive_small<1>(c, a, d_obs, stride, x, xn, s); break;
@@ -1907,9 +1997,7 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
         if (e != cudaSuccess) return e;
         k_weight_stats<0><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, nullptr, c.P, c.tile_sums, nullptr,
                                                    c.done, c.fstats, c.est, c.err);
-        dim3 g(c.n_mchunks, (dx + 255) / 256);
-        k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, c.lw2, c.fmax2,
-                                      c.fstats);
+        launch_mean_rows(c, xn, c.lw2, c.fmax2, c.fstats, s);
     } else {
         switch (dx) {
         case 1: e = apf_small<1>(c, a, d_obs, stride, x, xn, s); break;
