@@ -87,39 +87,44 @@ __device__ __forceinline__ FF ff_add(FF a, FF b)
 
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
 
-// Sums of NV compensated pairs over the block in a fixed order (xor tree in
-// each warp, then warps in order); every thread receives the FP64 results.
-// `sh` holds 2 * NV * (blockDim.x / 32) floats + NV doubles.
+// Sums of NV compensated pairs over the block in a fixed order; every thread
+// receives the FP64 results.  Every thread leaves its pairs in shared memory;
+// warp j (j < NV, strided over the block's warps) then adds column j -- each
+// lane the values lane, lane + 32, ... in order, then an xor tree over the
+// lanes -- so the shuffle tree runs once per sum instead of once per warp.
+// `sf` holds 2 NV blockDim.x floats, `sd` NV doubles.
 template <int NV>
-__device__ void block_sum_ff(FF (&v)[NV], double (&out)[NV], void *shm)
+__device__ void block_sum_ff(FF (&v)[NV], double (&out)[NV], float *sf, double *sd)
 {
-    const int nw = blockDim.x >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    float *sf = reinterpret_cast<float *>(shm);
-    double *sd = reinterpret_cast<double *>(sf + 2 * NV * 32);
+    const int n = blockDim.x, nw = n >> 5, w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();  // the scratch may still be read by a previous use
 #pragma unroll
-    for (int j = 0; j < NV; ++j)
+    for (int j = 0; j < NV; ++j) {
+        sf[(2 * j) * n + threadIdx.x] = v[j].hi;
+        sf[(2 * j + 1) * n + threadIdx.x] = v[j].lo;
+    }
+    __syncthreads();
+    for (int j = w; j < NV; j += nw) {
+        FF acc{0.0f, 0.0f};
+        for (int i = l; i < n; i += 32) acc = ff_add(acc, FF{sf[(2 * j) * n + i], sf[(2 * j + 1) * n + i]});
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            FF other{__shfl_xor_sync(0xffffffffu, v[j].hi, o), __shfl_xor_sync(0xffffffffu, v[j].lo, o)};
-            v[j] = ff_add(v[j], other);
+            const FF other{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+            acc = ff_add(acc, other);
         }
-    __syncthreads();
-    if (l == 0)
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            sf[2 * (j * 32 + w)] = v[j].hi;
-            sf[2 * (j * 32 + w) + 1] = v[j].lo;
-        }
-    __syncthreads();
-    if (threadIdx.x < NV) {
-        const int j = threadIdx.x;
-        FF acc{0.0f, 0.0f};
-        for (int i = 0; i < nw; ++i) acc = ff_add(acc, FF{sf[2 * (j * 32 + i)], sf[2 * (j * 32 + i) + 1]});
-        sd[j] = ff_to_double(acc);
+        if (l == 0) sd[j] = ff_to_double(acc);
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < NV; ++j) out[j] = sd[j];
+}
+
+// The same with one scratch area `shm` of 2 NV blockDim.x floats followed by NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum_ff(FF (&v)[NV], double (&out)[NV], void *shm)
+{
+    float *sf = reinterpret_cast<float *>(shm);
+    block_sum_ff<NV>(v, out, sf, reinterpret_cast<double *>(sf + 2 * NV * blockDim.x));
 }
 
 // FP64 sums over the block of NV per-thread values, in a fixed order
@@ -1085,7 +1090,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
 {
     __shared__ uint64_t shq[kTile];
     __shared__ int32_t shB[kTile];
-    __shared__ double shd[(2 * 4 * 32) / 2 + 4];  // block_sum_ff<NV <= 4>
+    __shared__ double shd[4];  // block_sum_ff results; its scratch is shB, then shq
     __shared__ uint64_t shu[kWarps * 2];
     __shared__ int shi[kWarps];
     const int tix = tile0 + blockIdx.x;
@@ -1115,12 +1120,13 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
                 const uint64_t qv = quant_f32(w, fd.shift);
                 qs += qv;
                 shq[j] = qv;
-                shB[j] = -1;
             }
         }
     }
     double s[2];
-    block_sum_ff<2>(f, s, shd);
+    static_assert(2 * 2 * kResampleThreads * sizeof(float) <= sizeof(shB), "scratch of the weight sums");
+    block_sum_ff<2>(f, s, reinterpret_cast<float *>(shB), shd);
+    for (int j = threadIdx.x; j < td.len; j += blockDim.x) shB[j] = -1;
     const uint64_t Ctot = block_sum_u64(qs, shu);  // its barriers also publish shq and shB
     const int32_t t = a.d_t ? *a.d_t + 1 : 0;
     const uint32_t U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
@@ -1194,7 +1200,8 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
         FF fx[DD];
         gather_items<DD>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, fx);
         double sx[DD];
-        block_sum_ff<DD>(fx, sx, shd);
+        static_assert(2 * DD * kResampleThreads * sizeof(float) <= sizeof(shq), "scratch of the state sums");
+        block_sum_ff<DD>(fx, sx, reinterpret_cast<float *>(shq), shd);  // q is no longer needed
         if (threadIdx.x < DD) est[(int64_t)td.m * DD + threadIdx.x] = sx[threadIdx.x];  // divided by N later
     }
 }
