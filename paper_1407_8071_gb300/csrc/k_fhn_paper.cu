@@ -71,7 +71,7 @@ __device__ int block_exclusive_scan(int v, int *warp_tot)
 template <typename Real, int MaxT = 1024, int MinB = 1>
 __global__ void __launch_bounds__(MaxT, MinB)
     k_propagate_fhnp(ModelParams mp, Key key, uint32_t stream, uint32_t stim_stream, const int32_t *pfilt,
-                     const FilterDesc *filt, const Real *__restrict__ x_in, Real *__restrict__ x_out, int64_t P,
+                     const FilterDesc *filt, const Real *x_in, Real *x_out, int64_t P,
                      float *logw, const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t,
                      int32_t fixed_c0, int32_t fixed_c2, int32_t t_direct, int32_t ppc, int32_t *fmax_key,
                      int32_t n_steps, AuxPtrs aux, int32_t noise)

@@ -410,6 +410,9 @@ __global__ void __launch_bounds__(256) k_init_fhn(ModelParams mp, Key key, const
 // then the FP32 log-likelihood; the sub-tile's maximum of it joins the
 // filter's maximum by one atomicMax (the first pass of the log-sum-exp).  A
 // thread past the sub-tile's end repeats its last particle and stores nothing.
+// x_in and x_out may be one buffer (the step propagates in place): a thread
+// reads its particles before it writes them, and no other thread touches them;
+// the same holds for the lattice kernels below, per particle row.
 constexpr int kPropThreads = kSubTile / 2;
 
 // Mode 0: the bootstrap filter.  Mode 1: the auxiliary filter's look-ahead
@@ -419,8 +422,8 @@ constexpr int kPropThreads = kSubTile / 2;
 // logw = lw_prev + log g(y | x).
 template <int D, int Mode>
 __global__ void __launch_bounds__(kPropThreads, 16)
-    k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *__restrict__ x_in,
-                      float *__restrict__ x_out, int64_t P, float *logw, int32_t *fmax_key, const float *obs,
+    k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *x_in,
+                      float *x_out, int64_t P, float *logw, int32_t *fmax_key, const float *obs,
                       int32_t obs_stride, const int32_t *d_t, AuxPtrs aux)
 {
     __shared__ float sh[kPropThreads / 32];
@@ -476,7 +479,7 @@ __global__ void __launch_bounds__(kPropThreads, 16)
 template <typename Real, bool Noise = true>
 __global__ void __launch_bounds__(1024, 2)
     k_propagate_fhn(ModelParams mp, Key key, uint32_t stream, const int32_t *pfilt, const FilterDesc *filt,
-                    const Real *__restrict__ x_in, Real *__restrict__ x_out, int64_t P, float *logw, const float *obs,
+                    const Real *x_in, Real *x_out, int64_t P, float *logw, const float *obs,
                     int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t fixed_c0,
                     int32_t fixed_c2, int32_t t_direct, int32_t ppc, int32_t *fmax_key, int32_t n_steps,
                     AuxPtrs aux, int32_t noise)
@@ -612,7 +615,7 @@ constexpr int kFhn4MaxThreads = 512;
 template <bool Noise = true, int MinB = 3>
 __global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
     k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
-                     const float *__restrict__ x_in, float *__restrict__ x_out, int64_t P, float *logw,
+                     const float *x_in, float *x_out, int64_t P, float *logw,
                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
                      int32_t *fmax_key, int32_t n_steps, AuxPtrs aux, int32_t noise)
 {
@@ -1804,7 +1807,6 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
                              cudaStream_t s)
 {
     if (is_lattice(c.mp.kind)) {
-        int ppc;
         if (c.mp.kind == kFhnPaper)
             return launch_fhnp_interval(c, d_obs, stride, xi, xo, c.mp.K, c.logw, c.fmax_key, AuxPtrs{}, 1, s);
         return launch_fhn_interval(c, d_obs, stride, xi, xo, c.mp.K, true, s);
