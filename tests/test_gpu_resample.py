@@ -56,6 +56,44 @@ def test_systematic_bit_exact_one_big_filter():
     run_stateless([(1 << 20) - 3], lambda i: "sparse", seed=8)
 
 
+def test_systematic_bit_exact_at_the_maximum_size():
+    """N_m = 2^24, the largest particle count the ABI accepts (q below 2^28 each), next to N = 1."""
+    run_stateless([1 << 24, 1], lambda i: "lognormal", seed=9)
+
+
+def test_context_at_the_maximum_size():
+    """One Lorenz filter of 2^24 particles in a context with a small one: resampling against the
+    oracle, gather, normaliser; one particle more is refused."""
+    spec = W.lorenz63()
+    N = np.array([1 << 24, 300], dtype=np.int32)
+    off = np.concatenate([[0], np.cumsum(N)])
+    seed = 31
+    rng = np.random.default_rng(4)
+    logw = rng.normal(-10.0, 2.0, size=int(off[-1])).astype(np.float32)
+    with pf.EnsembleFilter(spec, 2, N, seed) as f:
+        f.propagate(np.zeros(spec.dy, dtype=np.float32))
+        xbar = f.get_state()
+        f.set_logw(logw)
+        f.resample()
+        anc = f.get_ancestors()
+        x = f.get_state()
+        logZ = f.estimate(pf.PF_STAT_LOG_Z, per_filter=True)
+    for m in range(2):
+        a, b = off[m], off[m + 1]
+        l = logw[a:b].astype(np.float64)
+        nrm = oracle.normalise(l)
+        assert logZ[m] == pytest.approx(nrm["logZ"], rel=1e-6)
+        exp = oracle.systematic(np.exp(l - nrm["max"]), oracle.resample_u(seed, m, 1))
+        got = anc[a:b]
+        assert np.sum(got != exp) <= max(2, (b - a) // 1000)
+        assert np.all(np.diff(got) >= 0) and got.min() >= 0 and got.max() < b - a
+        sample = np.random.default_rng(m).choice(b - a, size=min(b - a, 4096), replace=False)
+        assert np.array_equal(x[a + sample], xbar[a + got[sample]])
+    with pytest.raises(pf.PFError) as e:
+        pf.EnsembleFilter(spec, 1, (1 << 24) + 1, 1)
+    assert e.value.status == pf.PF_EINVAL
+
+
 def test_systematic_golden_worked_examples():
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "systematic_worked.txt")
