@@ -63,7 +63,11 @@ def test_systematic_bit_exact_at_the_maximum_size():
 
 def test_context_at_the_maximum_size():
     """One Lorenz filter of 2^24 particles in a context with a small one: resampling against the
-    oracle, gather, normaliser; one particle more is refused."""
+    oracle, gather, normaliser; one particle more is refused.  The context's weights are FP32
+    exp(l - max) against the oracle's FP64 exp: their roundings add up along the 2^24-term prefix,
+    so more grid points change sides than at 2^20 (0.11 % of the ancestors here); the exact
+    arithmetic itself is pinned bit for bit at this size by the stateless test above, and here the
+    offspring counts must stay within one of floor / ceil of N times the FP64 weights."""
     spec = W.lorenz63()
     N = np.array([1 << 24, 300], dtype=np.int32)
     off = np.concatenate([[0], np.cumsum(N)])
@@ -85,8 +89,12 @@ def test_context_at_the_maximum_size():
         assert logZ[m] == pytest.approx(nrm["logZ"], rel=1e-6)
         exp = oracle.systematic(np.exp(l - nrm["max"]), oracle.resample_u(seed, m, 1))
         got = anc[a:b]
-        assert np.sum(got != exp) <= max(2, (b - a) // 1000)
+        assert np.sum(got != exp) <= max(2, (b - a) // 200)
         assert np.all(np.diff(got) >= 0) and got.min() >= 0 and got.max() < b - a
+        w = np.exp(l - nrm["max"])
+        o = np.bincount(got, minlength=b - a)
+        nw = (b - a) * w / w.sum()
+        assert np.all(o >= np.floor(nw) - 1) and np.all(o <= np.ceil(nw) + 1)
         sample = np.random.default_rng(m).choice(b - a, size=min(b - a, 4096), replace=False)
         assert np.array_equal(x[a + sample], xbar[a + got[sample]])
     with pytest.raises(pf.PFError) as e:
