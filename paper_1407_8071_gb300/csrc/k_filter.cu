@@ -286,6 +286,7 @@ struct Grid {
     float est_scale;  // N 2^est_shift / Ctot
     float u;        // U 2^-32
     float Nf;       // N (<= 2^24, exact)
+    float Cf;       // Ctot in FP32 (relative error <= 2^-23)
 };
 
 // A 64-bit unsigned value as FP32 from its two 32-bit halves: 64-bit integer
@@ -308,6 +309,7 @@ __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
     g.Nf = __int2float_rn((int32_t)N);
     g.est_scale = g.Nf * __int_as_float((127 + g.est_shift) << 23) / u64_to_f32(Ctot ? Ctot : 1);
     g.u = __uint2float_rn(U) * 0x1p-32f;
+    g.Cf = u64_to_f32(Ctot);
     return g;
 }
 
@@ -329,10 +331,21 @@ __device__ __noinline__ int64_t count_bisect(const U128 X, const Grid g)
 __device__ int64_t count_below(uint64_t x, const Grid &g)
 {
     if (x == 0) return 0;
-    const U128 X = scaled_C(x, (uint64_t)g.N);
     const float xf = __uint2float_rn((uint32_t)(x >> g.est_shift));
     const float est = ceilf(__fmaf_rn(xf, g.est_scale, -g.u));
     int64_t i = est <= 0.0f ? 0 : (est >= g.Nf ? g.N : (int64_t)__float2int_rz(est));
+    // FP32 certificate: the count is i when (i - 1 + u) Ctot < x N <= (i + u) Ctot.  Each side
+    // evaluated in FP32 (u64_to_f32 of x and Ctot, one rounding per operation) is within 3e-7 of
+    // its value relative to itself; a gap of 4e-6 x N on both sides decides the comparisons
+    // exactly, and anything closer takes the exact 128-bit path below.
+    {
+        const float xn = u64_to_f32(x) * g.Nf, tol = 4.0e-6f * xn;
+        const float fi = (float)(int32_t)i;
+        const bool lo_ok = i == 0 || (fi - 1.0f + g.u) * g.Cf < xn - tol;
+        const bool hi_ok = i == g.N || (fi + g.u) * g.Cf > xn + tol;
+        if (lo_ok && hi_ok) return i;
+    }
+    const U128 X = scaled_C(x, (uint64_t)g.N);
     bool settled = false;
 #pragma unroll 1
     for (int it = 0; it < 4; ++it) {
