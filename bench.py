@@ -48,7 +48,7 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 # Algorithmic ALU operations per Lorenz particle-step (one Euler-Maruyama
-# sub-step of one particle); the derivation is in the design doc:
+# sub-step of one particle), counting the minimal work of each published step:
 #   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs) = 40,
 #                  0.75 calls per sub-step (3 blocks per 4 sub-steps)       -> 30
 #   Box-Muller pair: 4 (uniforms) + 8 (log) + 2 (sqrt) + 12 (sincospi)
