@@ -1949,28 +1949,52 @@ void resample_whole(const Ctx &c, const ResampleArgs &a, const float *xi, float 
     if (n) k_whole_finish<<<(n + 31) / 32, 32, 0, s>>>(c.tiles, b0, n, D, c.fstats, c.est, a.d_t, a.log_const);
 }
 
+// The two groups of filters share no data (every buffer is split by filter,
+// tile or particle, and the error word takes atomics), so when both are present
+// the fused one-tile kernels run on the side stream next to the tile chain:
+// fork from s, join back into s before anything reads every filter.
+cudaStream_t fork_side(const Ctx &c, cudaStream_t s)
+{
+    const bool both = c.n_multi_tiles > 0 && c.whole_bounds[kWholeClasses] > c.whole_bounds[0];
+    if (!both) return s;
+    cudaEventRecord(c.fork_ev, s);
+    cudaStreamWaitEvent(c.side_stream, c.fork_ev, 0);
+    return c.side_stream;
+}
+
+void join_side(const Ctx &c, cudaStream_t side, cudaStream_t s)
+{
+    if (side == s) return;
+    cudaEventRecord(c.join_ev, side);
+    cudaStreamWaitEvent(s, c.join_ev, 0);
+}
+
 template <int D>
 void resample_small(const Ctx &c, const ResampleArgs &a, const float *xi, float *xo, int th, cudaStream_t s)
 {
     const int32_t nm = c.n_multi_tiles;
+    const cudaStream_t side = fork_side(c, s);
+    resample_whole<D>(c, a, xi, xo, side);
     if (nm) {
         k_weights<false><<<nm, th, 0, s>>>(a);
         k_scan_scatter<false><<<nm, th, 0, s>>>(a);
         k_ancestors_small<D><<<nm, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est);
     }
-    resample_whole<D>(c, a, xi, xo, s);
+    join_side(c, side, s);
 }
 
 // The whole bootstrap resampling up to the ancestors (lattice models).
 void resample_ancestors(const Ctx &c, const ResampleArgs &a, int th, cudaStream_t s)
 {
     const int32_t nm = c.n_multi_tiles;
+    const cudaStream_t side = fork_side(c, s);
+    resample_whole<0>(c, a, nullptr, nullptr, side);
     if (nm) {
         k_weights<false><<<nm, th, 0, s>>>(a);
         k_scan_scatter<false><<<nm, th, 0, s>>>(a);
         k_ancestors<<<nm, th, 0, s>>>(a);
     }
-    resample_whole<0>(c, a, nullptr, nullptr, s);
+    join_side(c, side, s);
 }
 
 // One step of the ensemble of auxiliary particle filters: look-ahead weights

@@ -463,6 +463,17 @@ pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn free_fn, void *user)
     return PF_OK;
 }
 
+// The context's own streams and fork / join events (null handles are skipped).
+static void destroy_streams(Ctx &c)
+{
+    if (c.fork_ev) cudaEventDestroy(c.fork_ev);
+    if (c.join_ev) cudaEventDestroy(c.join_ev);
+    if (c.side_stream) cudaStreamDestroy(c.side_stream);
+    if (c.own_stream) cudaStreamDestroy(c.own_stream);
+    c.fork_ev = c.join_ev = nullptr;
+    c.side_stream = c.own_stream = nullptr;
+}
+
 pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double dt, const pf_obs_op *obs,
                     const pf_noise *noise, pf_ctx **out)
 {
@@ -498,8 +509,12 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
         c.alloc_user = g_alloc_user;
     }
     cudaError_t e = cudaStreamCreateWithFlags(&c.own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         g_create_error = std::string("stream create: ") + cudaGetErrorString(e);
+        destroy_streams(c);
         delete h;
         return PF_ECUDA;
     }
@@ -543,7 +558,7 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     if (!ok) {
         g_create_error = "device allocation failed";
         ctx_free_all(c);
-        cudaStreamDestroy(c.own_stream);
+        destroy_streams(c);
         delete h;
         return PF_ENOMEM;
     }
@@ -558,7 +573,7 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
             if (c.stage_ev[k]) cudaEventDestroy(c.stage_ev[k]);
         }
         ctx_free_all(c);
-        cudaStreamDestroy(c.own_stream);
+        destroy_streams(c);
         delete h;
         return PF_ENOMEM;
     }
@@ -602,7 +617,7 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
             cudaEventDestroy(c.stage_ev[k]);
         }
         ctx_free_all(c);
-        cudaStreamDestroy(c.own_stream);
+        destroy_streams(c);
         delete h;
         return PF_ECUDA;
     }
@@ -625,7 +640,7 @@ void pf_destroy(pf_ctx *h)
     if (c.h_err_async) cudaFreeHost(c.h_err_async);
     if (c.est_ev) cudaEventDestroy(c.est_ev);
     ctx_free_all(c);
-    if (c.own_stream) cudaStreamDestroy(c.own_stream);
+    destroy_streams(c);
     delete h;
 }
 

@@ -251,6 +251,12 @@ struct Ctx {
 
     cudaStream_t stream = nullptr;
     cudaStream_t own_stream = nullptr;
+    // A second stream for work of a step that is independent of the main chain
+    // (the fused resampling of one-tile filters next to the tile chain of the
+    // others): forked from and joined back into `stream` with the two events,
+    // so a captured step graph holds both branches.
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
 
     pf_alloc_fn alloc = nullptr;
