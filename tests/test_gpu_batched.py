@@ -137,3 +137,30 @@ def test_ragged_batch_with_learned_proposal_matches_the_oracle():
         a, b = eg[t], ro["est"][t, :, 0]
         se = math.sqrt(a.var(ddof=1) / M + b.var(ddof=1) / M)
         assert abs(a.mean() - b.mean()) <= 4.5 * se, (t, a.mean(), b.mean(), se)
+
+
+def test_user_stream_and_graph_branches_give_the_same_filter():
+    """A context on a caller stream (pf_set_stream) with filters of one tile and of several (the
+    step graph forks the fused one-tile resampling onto the context's second stream and joins it
+    back): the same particles, ancestors and estimates as on the context's own stream, step by
+    step, through graph replays and asynchronous estimate reads."""
+    spec = W.lorenz63()
+    _, y = oracle.simulate(spec, 6, W.SEED_LORENZ_OBS)
+    y = y.astype(np.float32)
+    N = np.array([3000, 700, 1024, 64, 5000, 1], dtype=np.int32)
+    outs = []
+    for use_stream in (False, True):
+        st = torch.cuda.Stream() if use_stream else None
+        with pf.EnsembleFilter(spec, len(N), N, 12) as f:
+            if st is not None:
+                f.set_stream(st.cuda_stream)
+            ens = []
+            for t in range(6):
+                f.step(y[t])
+                ens.append(f.estimate_async(pf.PF_STAT_MEAN, var=-1).wait())
+            outs.append((f.get_state(), f.get_ancestors(), np.array(ens),
+                         f.estimate(pf.PF_STAT_LOG_EVIDENCE, per_filter=True)))
+    a, b = outs
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+
