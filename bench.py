@@ -137,11 +137,18 @@ class ClockSampler:
 
 
 def source_digest():
+    """Digest of the CUDA sources with comments and blank lines removed, so that
+    the recorded DRAM traffic stays attached to the code it was measured on."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_8071_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update(("\n".join(lines) + "\n").encode())
     return h.hexdigest()[:16]
 
 

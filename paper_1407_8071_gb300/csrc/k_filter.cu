@@ -776,9 +776,9 @@ __global__ void __launch_bounds__(kResampleThreads) k_refresh_max(const TileDesc
     if (threadIdx.x == 0 && mx > -INFINITY) atomicMax(&fmax_key[td.m], float_order_key(mx));
 }
 
-// Pass 2: the filter maximum, then per tile sum w and sum w^2 (FP32 per
-// thread, FP64 across threads) and the exact sum of q = floor(w 2^shift);
-// clears the ancestor markers.
+// Pass 2: the filter maximum, then per tile sum w and sum w^2 (compensated
+// FP32 pairs, FP64 per tile) and the exact sum of q = floor(w 2^shift); stores
+// each q for the scan and clears the ancestor markers.
 template <bool Direct>
 __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
 {
