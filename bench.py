@@ -599,7 +599,9 @@ def main():
         ops_node = base_ops + (FHN_LOOKAHEAD_OPS_PER_NODE_STEP if wl.aux else 0)
         per_launch_ops = (wl.particles / nf) * wl.spec.K * wl.spec.J * wl.spec.J * ops_node
         achieved = per_launch_ops / t_prop / 1e12
-        lattice_kernel = "k_propagate_fhn4" if wl.choice and wl.choice[2] == 4 else "k_propagate_fhn<float>"
+        # the four- and eight-node builds (template G = 1, 2; either CTAs-per-SM build)
+        lattice_kernel = {4: "k_propagate_fhn4<1,*,1>", 8: "k_propagate_fhn4<1,*,2>"}.get(
+            wl.choice[2] if wl.choice else 0, "k_propagate_fhn<float>")
         kern = (lattice_kernel if wl.theta is None else "proposal propagate (5 kernels)") if not wl.aux \
             else "auxiliary step (look-ahead + second-stage propagate + resampling)"
         roofline = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",

@@ -269,7 +269,8 @@ PF_API pf_status pf_set_auxiliary(pf_ctx *ctx, int32_t on);
 PF_API pf_status pf_set_resampling(pf_ctx *ctx, double ess_threshold);
 
 /* Sets the launch schedule explicitly (0 in any field: the default):
- * nodes_per_thread 2 or 4 for the lattice kernels (4 needs J % 4 == 0),
+ * nodes_per_thread 2, 4 or 8 for the lattice kernels (4 and 8 on the
+ * Rogers-McCulloch lattice only, with J divisible by them),
  * particles_per_cta >= 1 for the lattice (clamped to what fits in 1024
  * threads), resample_threads 64, 128 or 256 (at least a quarter of the
  * largest tile, min(N_m, 1024)).  Results do not depend on the schedule

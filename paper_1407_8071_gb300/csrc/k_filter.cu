@@ -624,69 +624,95 @@ __global__ void __launch_bounds__(1024, 2)
 constexpr int kFhn4MaxThreads = 512;
 
 // MinB: CTAs the compiler must fit per SM (3: at most 42 registers; 4: 32,
-// with a little spilling) -- the autotuner times both.
-template <bool Noise = true, int MinB = 3>
+// with a little spilling) -- the autotuner times both.  G float4 groups per
+// thread: G = 1 the four-node kernel, G = 2 eight consecutive nodes of a row
+// (sides divisible by 8), the same per-pair arithmetic, Philox blocks and
+// reduction order in both, so every width gives the pair kernel's bits.  The
+// G groups of a thread sit side by side in shared memory: with G = 2 lanes
+// read float4s 32 bytes apart (two-way bank conflicts), yet the conflict-free
+// [G][units] order measured slower for its runtime-stride addressing.
+template <bool Noise = true, int MinB = 3, int G = 1>
 __global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
     k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
                      const float *x_in, float *x_out, int64_t P, float *logw,
                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
                      int32_t *fmax_key, int32_t n_steps, AuxPtrs aux, int32_t noise)
 {
+    constexpr int NV = 4 * G;  // nodes per thread
     extern __shared__ unsigned char smem_raw[];
     (void)noise;  // the template parameter Noise decides
-    const int J = mp.J, nn = J * J, quads = nn / 4, pairs = nn / 2, qrow = J / 4;
-    float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [2][ppc][quads]
-    const int slot = (int)threadIdx.x / quads;
+    const int J = mp.J, nn = J * J, units = nn / NV, pairs = nn / 2, urow = J / NV;
+    float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [2][ppc][units][G]
+    const int slot = (int)threadIdx.x / units;
     const int s = min(slot, ppc);                   // s == ppc: padding thread
-    const int q = threadIdx.x - min(slot, ppc - 1) * quads;
+    const int q = threadIdx.x - min(slot, ppc - 1) * units;
     const int64_t p = (int64_t)blockIdx.x * ppc + s;
     const bool active = (s < ppc) && (p < P);
     const uint32_t t = (uint32_t)(*d_t + 1);
 
     uint32_t c0 = 0, c2 = 0;
-    float v[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
-    const int n0 = 4 * q, row = n0 / J, col = n0 - row * J;
+    float v[NV], w[NV];
+#pragma unroll
+    for (int e = 0; e < NV; ++e) v[e] = w[e] = 0.0f;
+    const int n0 = NV * q, row = n0 / J, col = n0 - row * J;
     if (active) {
         const int32_t m = pfilt[p];
         c0 = (uint32_t)(p - filt[m].off);
         c2 = (uint32_t)m;
         const int64_t row_in = aux.gather ? filt[m].off + aux.gather[p] : p;
-        const float4 a = *reinterpret_cast<const float4 *>(x_in + row_in * (int64_t)mp.dx + n0);
-        const float4 b = *reinterpret_cast<const float4 *>(x_in + row_in * (int64_t)mp.dx + nn + n0);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float4 a = *reinterpret_cast<const float4 *>(x_in + row_in * (int64_t)mp.dx + n0 + 4 * g);
+            const float4 b = *reinterpret_cast<const float4 *>(x_in + row_in * (int64_t)mp.dx + nn + n0 + 4 * g);
+            v[4 * g] = a.x; v[4 * g + 1] = a.y; v[4 * g + 2] = a.z; v[4 * g + 3] = a.w;
+            w[4 * g] = b.x; w[4 * g + 1] = b.y; w[4 * g + 2] = b.z; w[4 * g + 3] = b.w;
+        }
     }
     const float dt = mp.fdt, sq = mp.fsq, amp = mp.fp[6];
     const int64_t stim_steps = mp.ip[7];
     const int blk = (int)mp.ip[8];
     const int64_t n_base = (int64_t)(t - 1) * mp.K;
     const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
-    const int qu = row > 0 ? q - qrow : q, qd = row < J - 1 ? q + qrow : q;
-    const bool has_left = col > 0, has_right = col + 4 < J;
+    const int qu = row > 0 ? q - urow : q, qd = row < J - 1 ? q + urow : q;
+    const bool has_left = col > 0, has_right = col + NV < J;
     const int ql = has_left ? q - 1 : q, qr = has_right ? q + 1 : q;
 
     for (int k = 0; k < n_steps; ++k) {
-        float4 *buf = sv + ((k & 1) * ppc + (active ? s : 0)) * quads;
-        if (active) buf[q] = make_float4(v[0], v[1], v[2], v[3]);
+        float4 *buf = sv + ((k & 1) * ppc + (active ? s : 0)) * units * G;
+        if (active)
+#pragma unroll
+            for (int g = 0; g < G; ++g) buf[q * G + g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
         __syncthreads();
         if (active) {
-            float z[8];
-            const uint32_t bk = (uint32_t)k * blocks_per_step + 2u * (uint32_t)q;
+            float z[2 * NV];
+            const uint32_t bk = (uint32_t)k * blocks_per_step + (uint32_t)(NV / 2) * (uint32_t)q;  // pair n0 / 2
             if (Noise) {
-                normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
-                normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+#pragma unroll
+                for (int h = 0; h < NV / 2; ++h) normals4<float>(key, c0, t, c2, kStreamDyn, bk + h, z + 4 * h);
             } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) z[i] = 0.0f;
+                for (int i = 0; i < 2 * NV; ++i) z[i] = 0.0f;
             }
-            const float4 up = buf[qu], dn = buf[qd];
-            const float left = has_left ? buf[ql].w : v[0], right = has_right ? buf[qr].x : v[3];
-            float l[4];
-            pair_laplacian<float>(v[0], v[1], up.x, up.y, dn.x, dn.y, left, v[2], l[0], l[1]);
-            pair_laplacian<float>(v[2], v[3], up.z, up.w, dn.z, dn.w, v[1], right, l[2], l[3]);
+            float4 up[G], dn[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                up[g] = buf[qu * G + g];
+                dn[g] = buf[qd * G + g];
+            }
+            const float left = has_left ? buf[ql * G + G - 1].w : v[0];
+            const float right = has_right ? buf[qr * G].x : v[NV - 1];
+            float l[NV];
+#pragma unroll
+            for (int h = 0; h < NV / 2; ++h) {  // pair h: nodes 2h, 2h + 1
+                const float4 &u4 = up[h >> 1], &d4 = dn[h >> 1];
+                const float ua = (h & 1) ? u4.z : u4.x, ub = (h & 1) ? u4.w : u4.y;
+                const float da = (h & 1) ? d4.z : d4.x, db = (h & 1) ? d4.w : d4.y;
+                const float lf = h == 0 ? left : v[2 * h - 1], rt = h == NV / 2 - 1 ? right : v[2 * h + 2];
+                pair_laplacian<float>(v[2 * h], v[2 * h + 1], ua, ub, da, db, lf, rt, l[2 * h], l[2 * h + 1]);
+            }
             const bool on = (n_base + k) < stim_steps;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < NV; ++e) {
                 const float I = (on && row < blk && col + e < blk) ? amp : 0.0f;
                 const float fv = fhn_drift_v<float>(mp, v[e], w[e], l[e], I), fw = fhn_drift_w<float>(mp, v[e], w[e]);
                 v[e] = em_update(v[e], fv, z[2 * e], dt, sq);
@@ -695,17 +721,24 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
         }
     }
     if (active && x_out) {
-        *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + n0) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + nn + n0) = make_float4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + n0 + 4 * g) =
+                make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            *reinterpret_cast<float4 *>(x_out + p * (int64_t)mp.dx + nn + n0 + 4 * g) =
+                make_float4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+        }
     }
     if (!logw) return;
     // per pair, as the pair kernel forms it, then its fixed-order sum over pairs
-    float part[2] = {0.0f, 0.0f};
+    float part[NV / 2];
+#pragma unroll
+    for (int h = 0; h < NV / 2; ++h) part[h] = 0.0f;
     if (active) {
         const int32_t m = pfilt[p];
         const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < NV; ++e) {
             const int j = obs_slot[n0 + e];
             if (j >= 0) {
                 const float d = y[j] - v[e];
@@ -715,10 +748,9 @@ __global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
     }
     __syncthreads();
     float *red = reinterpret_cast<float *>(smem_raw);  // [ppc][pairs]
-    if (active) {
-        red[s * pairs + 2 * q] = part[0];
-        red[s * pairs + 2 * q + 1] = part[1];
-    }
+    if (active)
+#pragma unroll
+        for (int h = 0; h < NV / 2; ++h) red[s * pairs + (NV / 2) * q + h] = part[h];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int sl = warp; sl < ppc; sl += nwarps) {
@@ -1676,7 +1708,7 @@ namespace {
 // (2 or 4) nodes per thread.
 int fhn_threads(const ModelParams &mp, int *ppc, int want = 0, int nodes = 2)
 {
-    const int per = mp.J * mp.J / nodes, cap = nodes == 4 ? kFhn4MaxThreads : 1024;
+    const int per = mp.J * mp.J / nodes, cap = nodes >= 4 ? kFhn4MaxThreads : 1024;
     int n = 1;
     while ((n + 1) * per <= cap && n < 8) ++n;
     if (want > 0 && want < n) n = want;
@@ -1686,7 +1718,11 @@ int fhn_threads(const ModelParams &mp, int *ppc, int want = 0, int nodes = 2)
 
 // Nodes per thread of the lattice kernels: 4 where the side allows it, unless
 // the schedule asks for 2.
-int fhn_nodes(const Ctx &c) { return (c.fhn_nodes == 2 || c.mp.J % 4 != 0) ? 2 : 4; }
+int fhn_nodes(const Ctx &c)
+{
+    if (c.fhn_nodes == 8 && c.mp.J % 8 == 0) return 8;
+    return (c.fhn_nodes == 2 || c.mp.J % 4 != 0) ? 2 : 4;
+}
 
 size_t fhn_smem(const ModelParams &mp, int threads, int ppc, size_t real_bytes)
 {
@@ -1780,6 +1816,14 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(k_propagate_fhn<float, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<true, 2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<false, 2, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<true, 3, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_propagate_fhn4<false, 3, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(k_propagate_fhn4<true, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(k_propagate_fhn4<false, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1793,7 +1837,25 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
     float *lw = weigh ? logw : nullptr;
     int32_t *fm = weigh ? fmax : nullptr;
     const bool four = c.fhn_quad_ctas == 4;
-    if (nodes == 4 && noise && four)
+    if (nodes == 8) {  // eight nodes per thread: built for two or three CTAs per SM
+        const bool three = c.fhn_quad_ctas >= 3;
+        if (noise && three)
+            k_propagate_fhn4<true, 3, 2><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw,
+                                                                     d_obs, stride, c.obs_slot, c.d_t, ppc, fm, n_steps,
+                                                                     aux, 1);
+        else if (noise)
+            k_propagate_fhn4<true, 2, 2><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw,
+                                                                     d_obs, stride, c.obs_slot, c.d_t, ppc, fm, n_steps,
+                                                                     aux, 1);
+        else if (three)
+            k_propagate_fhn4<false, 3, 2><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw,
+                                                                      d_obs, stride, c.obs_slot, c.d_t, ppc, fm,
+                                                                      n_steps, aux, 0);
+        else
+            k_propagate_fhn4<false, 2, 2><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw,
+                                                                      d_obs, stride, c.obs_slot, c.d_t, ppc, fm,
+                                                                      n_steps, aux, 0);
+    } else if (nodes == 4 && noise && four)
         k_propagate_fhn4<true, 4><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
                                                               stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
     else if (nodes == 4 && noise)

@@ -100,7 +100,7 @@ def test_apf_lattice_schedules_and_graph_replay_identical():
     y = y.astype(np.float32)
     N = W.ragged_counts(5, 30, 400, seed=6)
     outs = []
-    for sched in ((2, 1, 0), (4, 0, 0), (4, 2, 128)):
+    for sched in ((2, 1, 0), (4, 0, 0), (4, 2, 128), (8, 0, 0)):
         with pf.EnsembleFilter(spec, len(N), N, 8) as f:
             f.set_auxiliary(True)
             f.set_schedule(*sched)

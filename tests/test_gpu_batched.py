@@ -66,7 +66,7 @@ def test_autotune_preserves_the_filter(spec_name):
 
 @pytest.mark.parametrize("J,proposal", [(8, False), (20, False), (6, False), (8, True), (20, True)])
 def test_lattice_schedules_give_identical_filters(J, proposal):
-    """Two or four nodes per thread and any number of particles per CTA: the
+    """Two, four or eight nodes per thread and any number of particles per CTA: the
     same particles, log-weights and ancestors bit for bit (the four-node
     kernels keep the pair kernels' arithmetic and reduction order), with the
     bootstrap transition and with the learned proposal's last sub-step."""
@@ -75,7 +75,8 @@ def test_lattice_schedules_give_identical_filters(J, proposal):
     _, y = oracle.simulate(spec, T, W.SEED_FHN_OBS)
     y = y.astype(np.float32)
     N = W.ragged_counts(4, 30, 300, seed=J)
-    scheds = [(2, 1, 0), (2, 0, 0), (0, 0, 0)] + ([(4, 1, 0), (4, 0, 128)] if J % 4 == 0 else [])
+    scheds = [(2, 1, 0), (2, 0, 0), (0, 0, 0)] + ([(4, 1, 0), (4, 0, 128)] if J % 4 == 0 else []) \
+        + ([(8, 1, 0), (8, 0, 0)] if J % 8 == 0 else [])
     outs = []
     for nodes, ppc, rt in scheds:
         with pf.EnsembleFilter(spec, len(N), N, 23) as f:
@@ -92,6 +93,9 @@ def test_lattice_schedules_give_identical_filters(J, proposal):
     if J % 4 != 0:
         with pf.EnsembleFilter(spec, 1, 10, 1) as f, pytest.raises(pf.PFError):
             f.set_schedule(4, 0, 0)
+    if J % 8 != 0:
+        with pf.EnsembleFilter(spec, 1, 10, 1) as f, pytest.raises(pf.PFError):
+            f.set_schedule(8, 0, 0)
 
 
 @pytest.mark.parametrize("proposal", [False, True])
