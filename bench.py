@@ -136,13 +136,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def source_digest():
-    """Digest of the CUDA sources with comments and blank lines removed, so that
-    the recorded DRAM traffic stays attached to the code it was measured on."""
+def source_digest(unit: str = "k_filter.cu"):
+    """Digest of the CUDA translation unit `unit` and every header beside it,
+    with comments and blank lines removed, so that the recorded DRAM traffic
+    stays attached to the code it was measured on."""
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_8071_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
+        if not (f == unit or f.endswith((".h", ".cuh"))):
+            continue
         with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -153,8 +156,9 @@ def source_digest():
 
 
 def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel sources have not changed since it was taken (else None)."""
+    """DRAM bytes per launch of `kernel` (a kernel of k_filter.cu) from the
+    committed ncu summary, if its sources have not changed since it was taken
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None

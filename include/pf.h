@@ -224,14 +224,15 @@ PF_API pf_status pf_estimate_wait(pf_ctx *ctx);
 /* Picks the launch schedule of this context's hot kernels by timing the
  * candidates on copies of its particles: for the lattice, nodes per thread and
  * particles per CTA (one particle per CTA up to as many as fit in 1024
- * threads), and for four nodes per thread whether the kernel is the build for
- * three or for four CTAs per SM; for every model, threads per resampling tile
+ * threads), and for four (eight) nodes per thread whether the kernel is the
+ * build for three or four (two or three) CTAs per SM; for every model, threads
+ * per resampling tile
  * CTA (64, 128, 256 -- fewer threads and more CTAs for small filters).  The
  * choice is cached per (model, lattice side, K, dx, particle counts) for the
  * process, and reported in h_choice[0..2] (may be NULL): h_choice[0] particles
  * per lattice CTA (0 for the small models, which run one particle per thread),
- * h_choice[1] resampling threads, h_choice[2] lattice nodes per thread (2 or 4;
- * 1 for the small models).  The filter's state, statistics and step counter
+ * h_choice[1] resampling threads, h_choice[2] lattice nodes per thread (2, 4
+ * or 8; 1 for the small models).  The filter's state, statistics and step counter
  * are unchanged.
  * Synchronises; needs about one particle buffer of temporary device memory.
  * Errors: PF_ESTATE (between pf_propagate and pf_resample, or recording),
@@ -269,8 +270,8 @@ PF_API pf_status pf_set_auxiliary(pf_ctx *ctx, int32_t on);
 PF_API pf_status pf_set_resampling(pf_ctx *ctx, double ess_threshold);
 
 /* Sets the launch schedule explicitly (0 in any field: the default):
- * nodes_per_thread 2, 4 or 8 for the lattice kernels (4 and 8 on the
- * Rogers-McCulloch lattice only, with J divisible by them),
+ * nodes_per_thread 2, 4 or 8 for the lattice kernels (4 and 8 where J
+ * is divisible by them),
  * particles_per_cta >= 1 for the lattice (clamped to what fits in 1024
  * threads), resample_threads 64, 128 or 256 (at least a quarter of the
  * largest tile, min(N_m, 1024)).  Results do not depend on the schedule

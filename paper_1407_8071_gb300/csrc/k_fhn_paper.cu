@@ -263,11 +263,263 @@ __global__ void __launch_bounds__(MaxT, MinB)
     }
 }
 
+// The same interval in FP32 with 4G consecutive nodes of a row per thread
+// (lattice sides divisible by 4G): thread (slot s, unit q) carries nodes
+// 4Gq..4Gq+4G-1, i.e. the pairs 2Gq..2Gq+2G-1 of k_propagate_fhnp, with their
+// Philox blocks, the same per-node arithmetic in the same order, the same
+// stimulus selection (row-major rank over the region) and the same
+// per-particle sum over pair partials, so its results are the pair kernel's
+// bits.  With one Euler step per observation a thread's fixed cost (indices,
+// parameters, the filter lookup, the barriers) is spread over 4G nodes
+// instead of two.  MinB: CTAs per SM the compiler must fit.
+template <int MinB, int G>
+__global__ void __launch_bounds__(512, MinB)
+    k_propagate_fhnp4(ModelParams mp, Key key, uint32_t stream, uint32_t stim_stream, const int32_t *pfilt,
+                      const FilterDesc *filt, const float *x_in, float *x_out, int64_t P, float *logw,
+                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
+                      int32_t *fmax_key, int32_t n_steps, AuxPtrs aux, int32_t noise)
+{
+    constexpr int NV = 4 * G;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int sh_ev[2][kMaxSlots], sh_cnt[2][kMaxSlots], sh_target[2][kMaxSlots], sh_base[kMaxSlots];
+    __shared__ uint32_t sh_r1[2][kMaxSlots];
+    __shared__ int warp_tot[32];
+    const int J = mp.J, nn = J * J, units = nn / NV, pairs = nn / 2, urow = J / NV;
+    float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [2][ppc][units][G]
+    const int slot = (int)threadIdx.x / units;
+    const int s = min(slot, ppc);  // s == ppc: padding thread
+    const int q = threadIdx.x - min(slot, ppc - 1) * units;
+    const int64_t p = (int64_t)blockIdx.x * ppc + s;
+    const bool active = (s < ppc) && (p < P);
+    const uint32_t t = (uint32_t)(*d_t + 1);
+
+    uint32_t c0 = 0, c2 = 0;
+    float u[NV], v[NV], sc[NV];
+#pragma unroll
+    for (int e = 0; e < NV; ++e) u[e] = v[e] = sc[e] = 0.0f;
+    const int n0 = NV * q, row = n0 / J, col = n0 - row * J;
+    if (active) {
+        const int32_t m = pfilt[p];
+        c0 = (uint32_t)(p - filt[m].off);
+        c2 = (uint32_t)m;
+        const int64_t row_in = aux.gather ? filt[m].off + aux.gather[p] : p;
+        const float *xi = x_in + row_in * (int64_t)mp.dx + n0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float4 a = *reinterpret_cast<const float4 *>(xi + 4 * g);
+            const float4 b = *reinterpret_cast<const float4 *>(xi + nn + 4 * g);
+            const float4 c = *reinterpret_cast<const float4 *>(xi + 2 * nn + 4 * g);
+            u[4 * g] = a.x; u[4 * g + 1] = a.y; u[4 * g + 2] = a.z; u[4 * g + 3] = a.w;
+            v[4 * g] = b.x; v[4 * g + 1] = b.y; v[4 * g + 2] = b.z; v[4 * g + 3] = b.w;
+            sc[4 * g] = c.x; sc[4 * g + 1] = c.y; sc[4 * g + 2] = c.z; sc[4 * g + 3] = c.w;
+        }
+    }
+    const float dt = par_dt<float>(mp), sq = par_sq<float>(mp), coup = par<float>(mp, 7);
+    const float b0 = par<float>(mp, 4), b1 = par<float>(mp, 5), b2 = par<float>(mp, 6);
+    const float Ff = par<float>(mp, 8), Fpsi = par<float>(mp, 15), l0 = par<float>(mp, 16);
+    const int64_t period = mp.ip[9], width = mp.ip[10];
+    const int fcols = (int)mp.ip[11];
+    const uint32_t eps_thr = (uint32_t)mp.ip[14];
+    const int64_t n_base = (int64_t)(t - 1) * mp.K;
+    int64_t phase = (n_base < 0x7FFFFFFF && period < 0x7FFFFFFF)
+                        ? (int64_t)((uint32_t)n_base % (uint32_t)period) : n_base % period;
+    const uint32_t blocks_per_step = (uint32_t)(mp.dx / 4);
+    const bool has_up = row > 0, has_dn = row < J - 1, has_left = col > 0, has_right = col + NV < J;
+    const int qu = has_up ? q - urow : q, qd = has_dn ? q + urow : q;
+    const int ql = has_left ? q - 1 : q, qr = has_right ? q + 1 : q;
+
+    for (int k = 0; k < n_steps; ++k) {
+        const int par_k = k & 1;
+        float4 *buf = sv + (par_k * ppc + (active ? s : 0)) * units * G;
+        if (active) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) buf[q * G + g] = make_float4(u[4 * g], u[4 * g + 1], u[4 * g + 2], u[4 * g + 3]);
+            if (q == 0) {  // the slot's stimulus numbers
+                int ev = 0;
+                uint32_t r1 = 0;
+                if (noise) {
+                    const uint4 r = philox4x32_10(make_uint4(c0, t, c2, (stim_stream << 24) | (uint32_t)k), key);
+                    ev = (r.x >> 8) < eps_thr;
+                    r1 = r.y;
+                }
+                sh_ev[par_k][s] = ev;
+                sh_r1[par_k][s] = r1;
+                sh_cnt[par_k][s] = 0;
+                sh_target[par_k][s] = -1;
+            }
+        }
+        __syncthreads();
+        int any = 0;
+        for (int i = 0; i < ppc; ++i) any |= sh_ev[par_k][i];
+        // (1/D) times the sum over the existing von Neumann neighbours (Sec. 5.2's sets),
+        // formed at once so that the neighbour values die here
+        float nb[NV];
+        if (active) {
+            const float left = has_left ? buf[ql * G + G - 1].w : 0.0f, right = has_right ? buf[qr * G].x : 0.0f;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const float4 up = buf[qu * G + g], dn = buf[qd * G + g];
+                const float uu[4] = {up.x, up.y, up.z, up.w}, dd[4] = {dn.x, dn.y, dn.z, dn.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int e = 4 * g + i;
+                    float a = (has_up ? uu[i] : 0.0f) + (has_dn ? dd[i] : 0.0f);
+                    a = a + (e > 0 ? u[e - 1] : left);
+                    nb[e] = a + (e < NV - 1 ? u[e + 1] : right);
+                }
+            }
+        }
+        uint32_t hit = 0;  // bit e: node e restarts its stimulus counter
+        if (any) {         // uniform over the CTA (rare): the neighbours again from shared memory
+            uint32_t f = 0;
+            if (active && sh_ev[par_k][s]) {
+                const float *bf = reinterpret_cast<const float *>(buf);
+                const float left = has_left ? bf[ql * NV + NV - 1] : u[0];
+                const float right = has_right ? bf[qr * NV] : u[NV - 1];
+                for (int e = 0; e < NV; ++e) {
+                    const bool in = in_band<float>(mp, u[e]) ||
+                                    (e > 0 ? in_band<float>(mp, u[e - 1]) : (has_left && in_band<float>(mp, left))) ||
+                                    (e < NV - 1 ? in_band<float>(mp, u[e + 1])
+                                                : (has_right && in_band<float>(mp, right))) ||
+                                    (has_up && in_band<float>(mp, bf[qu * NV + e])) ||
+                                    (has_dn && in_band<float>(mp, bf[qd * NV + e]));
+                    f |= (uint32_t)in << e;
+                }
+            }
+            const int c = __popc(f);
+            if (c) atomicAdd(&sh_cnt[par_k][s], c);
+            const int excl = block_exclusive_scan(c, warp_tot);
+            if (active && q == 0) sh_base[s] = excl;
+            __syncthreads();
+            if (active && sh_ev[par_k][s] && c) {
+                const int cnt = sh_cnt[par_k][s];
+                const int rank = (int)(((uint64_t)(sh_r1[par_k][s] >> 8) * (uint64_t)cnt) >> 24);
+                const int local = excl - sh_base[s];
+                if (rank >= local && rank < local + c) {
+                    uint32_t rest = f;  // the (rank - local)-th set node, in row-major order
+                    for (int i = local; i < rank; ++i) rest &= rest - 1;
+                    sh_target[par_k][s] = n0 + __ffs(rest) - 1;
+                }
+            }
+            __syncthreads();
+            if (active) {
+                const int tg = sh_target[par_k][s];
+                if (tg >= 0) {
+                    const int ti = tg / J, tj = tg - (tg / J) * J;
+                    for (int e = 0; e < NV; ++e) {
+                        const int ce = col + e;
+                        const bool h = (row == ti && (ce == tj || ce == tj - 1 || ce == tj + 1)) ||
+                                       (ce == tj && (row == ti - 1 || row == ti + 1));
+                        hit |= (uint32_t)h << e;
+                    }
+                }
+            }
+        }
+        if (active) {
+            const bool on = phase < width;
+#pragma unroll
+            for (int h = 0; h < NV / 2; ++h) {  // pair h: nodes 2h, 2h + 1 and their Philox block
+                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                if (noise)
+                    normals4<float>(key, c0, t, c2, stream,
+                                    (uint32_t)k * blocks_per_step + (uint32_t)(NV / 2) * (uint32_t)q + (uint32_t)h, z);
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int e = 2 * h + i;
+                    sc[e] = ((hit >> e) & 1) ? 0.0f : (sc[e] + 1.0f < l0 ? sc[e] + 1.0f : l0);
+                    const float F = (on && col + e < fcols) ? Ff : 0.0f, Ps = sc[e] < l0 ? Fpsi : 0.0f;
+                    const float fu = fhnp_p3<float>(mp, u[e]) - v[e] + coup * nb[e] + F + Ps;
+                    const float fv = b0 * u[e] + b1 * v[e] + b2;
+                    u[e] = em_update(u[e], fu, z[2 * i], dt, sq);
+                    v[e] = em_update(v[e], fv, 0.0f, dt, sq);
+                }
+            }
+        }
+        if (++phase == period) phase = 0;
+    }
+    if (active && x_out) {
+        float *xo = x_out + p * (int64_t)mp.dx + n0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            *reinterpret_cast<float4 *>(xo + 4 * g) = make_float4(u[4 * g], u[4 * g + 1], u[4 * g + 2], u[4 * g + 3]);
+            *reinterpret_cast<float4 *>(xo + nn + 4 * g) =
+                make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            *reinterpret_cast<float4 *>(xo + 2 * nn + 4 * g) =
+                make_float4(sc[4 * g], sc[4 * g + 1], sc[4 * g + 2], sc[4 * g + 3]);
+        }
+    }
+    if (!logw) return;
+    float part[NV / 2];
+#pragma unroll
+    for (int h = 0; h < NV / 2; ++h) part[h] = 0.0f;
+    if (active) {
+        const float *y = obs + (obs_stride ? (int64_t)pfilt[p] * obs_stride : 0);
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            const int j = obs_slot[n0 + e];
+            if (j >= 0) {
+                const float d = y[j] - u[e];
+                part[e >> 1] += d * d;
+            }
+        }
+    }
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(smem_raw);  // [ppc][pairs], the pair kernel's order
+    if (active)
+#pragma unroll
+        for (int h = 0; h < NV / 2; ++h) red[s * pairs + (NV / 2) * q + h] = part[h];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int sl = warp; sl < ppc; sl += nwarps) {
+        const int64_t pp = (int64_t)blockIdx.x * ppc + sl;
+        float acc = 0.0f;
+        for (int i = lane; i < pairs; i += 32) acc += red[sl * pairs + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && pp < P) {
+            float l = mp.fhalf_prec * acc;
+            if (aux.la_out) {
+                aux.la_out[pp] = l;
+                l = aux.lw_prev[pp] + l;
+            } else if (aux.la_src) {
+                l -= aux.la_src[filt[pfilt[pp]].off + aux.anc[pp]];
+            }
+            logw[pp] = l;
+            if (l > -INFINITY && l < INFINITY) atomicMax(&fmax_key[pfilt[pp]], float_order_key(l));
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 cudaError_t launch_fhnp_interval(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                                  int32_t n_steps, float *logw, int32_t *fmax, AuxPtrs aux, int32_t noise,
                                  cudaStream_t s)
 {
+    const int nodes = (c.fhn_nodes == 4 || c.fhn_nodes == 8) && c.mp.J % c.fhn_nodes == 0 ? c.fhn_nodes : 2;
+    if (nodes > 2) {  // 4 or 8 nodes per thread
+        const int units = c.mp.J * c.mp.J / nodes;
+        int n = 1;
+        while ((n + 1) * units <= 512 && n < kMaxSlots) ++n;
+        if (c.fhn_ppc > 0 && c.fhn_ppc < n) n = c.fhn_ppc;
+        const int ppc = n, threads = (ppc * units + 31) / 32 * 32;
+        const size_t planes = 2 * (size_t)ppc * c.mp.J * c.mp.J * sizeof(float);
+        const size_t smem = planes > (size_t)threads * sizeof(float) ? planes : (size_t)threads * sizeof(float);
+        const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
+        const bool more = c.fhn_quad_ctas >= (nodes == 4 ? 4 : 3);  // the build for more CTAs per SM
+#define PF_FHNP4_ARGS                                                                                             \
+    c.mp, c.key, kStreamDyn, kStreamMisc, c.pfilt, c.filt, xi, xo, c.P, logw, d_obs, stride, c.obs_slot, c.d_t, ppc, \
+        fmax, n_steps, aux, noise
+        if (nodes == 4 && more)
+            k_propagate_fhnp4<4, 1><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+        else if (nodes == 4)
+            k_propagate_fhnp4<3, 1><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+        else if (more)
+            k_propagate_fhnp4<3, 2><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+        else
+            k_propagate_fhnp4<2, 2><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+#undef PF_FHNP4_ARGS
+        return cudaGetLastError();
+    }
     const int pairs = c.mp.J * c.mp.J / 2;
     const bool small = pairs <= 512;  // a particle fits the 512-thread build
     const int cap = small ? 512 : 1024;

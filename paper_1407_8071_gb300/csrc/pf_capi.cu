@@ -992,7 +992,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         if (e == cudaSuccess && is_lattice(c.mp.kind)) {  // nodes per thread, particles per CTA
             float best = 1e30f;
             for (int nodes = 2; nodes <= 8; nodes *= 2) {
-                if (nodes > 2 && (c.mp.J % nodes != 0 || c.mp.kind == PF_MODEL_FHN_PAPER)) continue;
+                if (nodes > 2 && c.mp.J % nodes != 0) continue;
                 const int per = c.mp.J * c.mp.J / nodes, cap = nodes >= 4 ? 512 : 1024;
                 int maxp = 1;
                 while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
@@ -1049,7 +1049,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         h_choice[0] = c.fhn_ppc;
         h_choice[1] = c.resample_threads;
         h_choice[2] = c.mp.kind == PF_MODEL_FHN_LATTICE ? (c.fhn_nodes ? c.fhn_nodes : (c.mp.J % 4 ? 2 : 4))
-                      : (c.mp.kind == PF_MODEL_FHN_PAPER ? 2 : 1);
+                      : (c.mp.kind == PF_MODEL_FHN_PAPER ? (c.fhn_nodes ? c.fhn_nodes : 2) : 1);
     }
     return PF_OK;
 }
@@ -1103,11 +1103,9 @@ pf_status pf_set_schedule(pf_ctx *h, int32_t nodes_per_thread, int32_t particles
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_schedule between pf_propagate and pf_resample");
     const bool lattice = is_lattice(c.mp.kind);
     if (nodes_per_thread != 0 &&
-        !(lattice && (nodes_per_thread == 2 || ((nodes_per_thread == 4 || nodes_per_thread == 8) &&
-                                                c.mp.J % nodes_per_thread == 0 &&
-                                                c.mp.kind == PF_MODEL_FHN_LATTICE))))
-        return fail(c, PF_EINVAL,
-                    "nodes_per_thread: 0, 2, 4 or 8 (4 and 8: Rogers-McCulloch lattice, J divisible by them)");
+        !(lattice && (nodes_per_thread == 2 ||
+                      ((nodes_per_thread == 4 || nodes_per_thread == 8) && c.mp.J % nodes_per_thread == 0))))
+        return fail(c, PF_EINVAL, "nodes_per_thread: 0, 2, 4 or 8 (4 and 8: J divisible by them)");
     if (particles_per_cta < 0 || (particles_per_cta > 0 && !lattice))
         return fail(c, PF_EINVAL, "particles_per_cta: 0, or >= 1 for the lattice");
     int max_len = 1;

@@ -45,12 +45,17 @@ def _states(spec, n, seed, band_frac=0.1):
     return x.astype(np.float32)
 
 
+@pytest.mark.parametrize("nodes", [2, 4, 8])
 @pytest.mark.parametrize("J,M,N,eps", [(8, 3, 40, 0.0), (8, 2, 50, 1.0 - 2.0 ** -30), (32, 1, 3, 0.5), (6, 2, 7, 0.3)])
-def test_paper_lattice_prior_and_interval_match_oracle(J, M, N, eps):
+def test_paper_lattice_prior_and_interval_match_oracle(J, M, N, eps, nodes):
+    """Every kernel width: the pair kernel and the 4- and 8-node builds."""
+    if J % nodes:
+        pytest.skip("the side is not divisible by the nodes per thread")
     spec = W.fhn_paper(J=J, zones=4 if J >= 8 else 1, eps=eps)
     seed = 77
     nn = J * J
     with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.set_schedule(nodes, 0, 0)
         pid, fid = _ids(N, M)
         x_init = f.get_state()
         xo0 = oracle.prior(spec, pid, fid, seed)
@@ -102,3 +107,30 @@ def test_paper_lattice_filters_match_oracle(aux):
         a, b = est[t], eo[t]
         se = math.sqrt(a.var(ddof=1) / M + b.var(ddof=1) / M)
         assert abs(a.mean() - b.mean()) <= 4.5 * se + 1e-9, (t, a.mean(), b.mean(), se)
+
+
+@pytest.mark.parametrize("J,eps,aux", [(8, 0.3, False), (8, 0.3, True), (32, 0.05, True), (16, 1e-3, False)])
+def test_paper_lattice_schedules_give_identical_filters(J, eps, aux):
+    """Two, four or eight nodes per thread and any particles per CTA: the same
+    particles (stimulus counters included), log-weights and ancestors bit for
+    bit: every width keeps the pair kernel's per-node arithmetic, Philox
+    blocks, row-major stimulus choice and per-pair reduction order."""
+    spec = W.fhn_paper(J=J, zones=4, eps=eps, K=3)
+    T = 4
+    _, y = oracle.simulate(spec, T, W.SEED_FHN_OBS)
+    y = y.astype(np.float32)
+    N = W.ragged_counts(4, 20, 200, seed=J)
+    scheds = [(2, 1, 0), (2, 0, 0), (4, 1, 0), (4, 0, 0)] + ([(8, 1, 0), (8, 0, 0)] if J % 8 == 0 else [])
+    outs = []
+    for sched in scheds:
+        with pf.EnsembleFilter(spec, len(N), N, 5) as f:
+            if aux:
+                f.set_auxiliary(True)
+            f.set_schedule(*sched)
+            for t in range(T):
+                f.step(y[t])
+            outs.append((f.get_state(), f.get_logw(), f.get_ancestors(),
+                         f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)))
+    for x, l, a, e in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(l, outs[0][1]) and np.array_equal(a, outs[0][2])
+        assert np.allclose(e, outs[0][3], rtol=1e-12, atol=1e-15)
