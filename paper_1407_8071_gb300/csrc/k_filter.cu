@@ -1458,19 +1458,19 @@ __global__ void __launch_bounds__(256) k_mean_rows4(const FilterDesc *filt, cons
         const float4 *base = reinterpret_cast<const float4 *>(x + ch.gstart * (int64_t)dx) + v4;
         FF acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
         int i = 0;
-        for (; i + 8 <= ch.len; i += 8) {  // eight rows in flight, then the ordered adds
-            float4 r[8];
+        for (; i + 16 <= ch.len; i += 16) {  // sixteen rows in flight, then the ordered adds
+            float4 r[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) r[k] = base[(int64_t)(i + k) * dx4];
+            for (int k = 0; k < 16; ++k) r[k] = base[(int64_t)(i + k) * dx4];
             if (lw2) {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < 16; ++k) {
                     const float wk = aux_weight(lw2[ch.gstart + i + k], mx);
                     r[k].x *= wk, r[k].y *= wk, r[k].z *= wk, r[k].w *= wk;
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 16; ++k) {
                 acc[0] = ff_add(acc[0], r[k].x);
                 acc[1] = ff_add(acc[1], r[k].y);
                 acc[2] = ff_add(acc[2], r[k].z);
@@ -1522,8 +1522,9 @@ void launch_mean_rows(const Ctx &c, const float *xn, const float *lw2, const int
 {
     const int dx = c.mp.dx;
     if (dx % 4 == 0) {
-        dim3 g(c.n_mchunks, (dx / 4 + 255) / 256);
-        k_mean_rows4<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
+        // 128 threads of four variables: more CTAs in flight (the counters hold ceil(dx / 256) per filter)
+        dim3 g(c.n_mchunks, (dx / 4 + 127) / 128);
+        k_mean_rows4<<<g, 128, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
     } else {
         dim3 g(c.n_mchunks, (dx + 255) / 256);
         k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
