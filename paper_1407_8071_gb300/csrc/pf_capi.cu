@@ -11,8 +11,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pf.h"
 #include "pf_internal.h"
+
+namespace {
+// A named NVTX range over one API call (a no-op unless a profiler attaches),
+// so that traces show each step, propagation, resampling and estimate.
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
+}  // namespace
 
 using namespace pf;
 
@@ -664,12 +677,14 @@ pf_status pf_set_stream(pf_ctx *h, void *stream)
 
 pf_status pf_step(pf_ctx *h, const float *h_obs, int32_t obs_stride)
 {
+    Trace trace("pf_step");
     if (!h) return PF_EINVAL;
     return run_step(h->c, h_obs, obs_stride, cudaMemcpyHostToDevice);
 }
 
 pf_status pf_step_device(pf_ctx *h, const float *d_obs, int32_t obs_stride)
 {
+    Trace trace("pf_step_device");
     if (!h) return PF_EINVAL;
     return run_step(h->c, d_obs, obs_stride, cudaMemcpyDeviceToDevice);
 }
@@ -693,16 +708,19 @@ static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride,
 
 pf_status pf_propagate(pf_ctx *h, const float *h_obs, int32_t obs_stride)
 {
+    Trace trace("pf_propagate");
     return propagate_impl(h, h_obs, obs_stride, cudaMemcpyHostToDevice);
 }
 
 pf_status pf_propagate_device(pf_ctx *h, const float *d_obs, int32_t obs_stride)
 {
+    Trace trace("pf_propagate_device");
     return propagate_impl(h, d_obs, obs_stride, cudaMemcpyDeviceToDevice);
 }
 
 pf_status pf_resample(pf_ctx *h)
 {
+    Trace trace("pf_resample");
     if (!h) return PF_EINVAL;
     Ctx &c = h->c;
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
@@ -719,6 +737,7 @@ pf_status pf_resample(pf_ctx *h)
 
 pf_status pf_estimate(pf_ctx *h, const pf_stat *stat, double *out)
 {
+    Trace trace("pf_estimate");
     if (!h || !stat || !out) return PF_EINVAL;
     Ctx &c = h->c;
     if (c.fatal == PF_ECUDA) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
@@ -777,6 +796,7 @@ pf_status pf_step_kernels(pf_ctx *h, int32_t *n)
 
 pf_status pf_estimate_async(pf_ctx *h, const pf_stat *stat, double *h_out)
 {
+    Trace trace("pf_estimate_async");
     if (!h || !stat || !h_out) return PF_EINVAL;
     Ctx &c = h->c;
     if (c.fatal == PF_ECUDA) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
@@ -821,6 +841,7 @@ pf_status pf_estimate_async(pf_ctx *h, const pf_stat *stat, double *h_out)
 
 pf_status pf_estimate_wait(pf_ctx *h)
 {
+    Trace trace("pf_estimate_wait");
     if (!h) return PF_EINVAL;
     Ctx &c = h->c;
     if (!c.est_ev) return fail(c, PF_ESTATE, "no asynchronous estimate was enqueued");
@@ -934,6 +955,7 @@ pf_status pf_recorded_tuples(const pf_ctx *h, int64_t *count)
 
 pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
 {
+    Trace trace("pf_autotune");
     if (!h) return PF_EINVAL;
     Ctx &c = h->c;
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
@@ -1131,6 +1153,7 @@ pf_status pf_get_time(const pf_ctx *h, int32_t *t)
 
 pf_status pf_get_state(pf_ctx *h, float *h_x)
 {
+    Trace trace("pf_get_state");
     if (!h || !h_x) return PF_EINVAL;
     Ctx &c = h->c;
     pf_status st = sync(c, "get_state");
@@ -1152,6 +1175,7 @@ pf_status pf_get_state(pf_ctx *h, float *h_x)
 
 pf_status pf_set_state(pf_ctx *h, const float *h_x, int32_t t)
 {
+    Trace trace("pf_set_state");
     if (!h || !h_x || t < 0) return PF_EINVAL;
     Ctx &c = h->c;
     pf_status st = sync(c, "set_state");
