@@ -134,3 +134,30 @@ def test_paper_lattice_schedules_give_identical_filters(J, eps, aux):
     for x, l, a, e in outs[1:]:
         assert np.array_equal(x, outs[0][0]) and np.array_equal(l, outs[0][1]) and np.array_equal(a, outs[0][2])
         assert np.allclose(e, outs[0][3], rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 0.3])
+def test_paper_lattice_full_size_sampled(eps):
+    """The 32 x 32 paper lattice at M = 10, N = 5000 (the bench's workload) in the
+    schedule the autotuner picks for that shape, one interval from states with
+    nodes in the stimulus band: sampled particles against the oracle one by one
+    (U and V within 1e-5, the stimulus counters exactly, the log-weights)."""
+    spec = W.fhn_paper(J=32, eps=eps)
+    M, N, seed = 10, 5000, 41
+    nn = 32 * 32
+    x0 = _states(spec, M * N, seed=5)
+    y = np.random.default_rng(5).normal(-1.0, 0.5, spec.dy).astype(np.float32)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.autotune()
+        f.set_state(x0, 3)
+        f.propagate(y)
+        xg = f.get_state()
+        lg = f.get_logw()
+    rng = np.random.default_rng(2)
+    sample = np.sort(rng.choice(M * N, size=40, replace=False))
+    pid, fid = (sample % N).astype(np.int32), (sample // N).astype(np.int32)
+    xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid, fid, 4, seed)
+    assert np.array_equal(xg[sample, 2 * nn:], xo[:, 2 * nn:].astype(np.float32)), "stimulus counters differ"
+    _close(xg[sample, :2 * nn], xo[:, :2 * nn])
+    lo = oracle.loglik(spec, xg[sample].astype(np.float64), y.astype(np.float64))
+    assert np.max(np.abs(lg[sample] - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
