@@ -271,8 +271,10 @@ __global__ void __launch_bounds__(MaxT, MinB)
 // per-particle sum over pair partials, so its results are the pair kernel's
 // bits.  With one Euler step per observation a thread's fixed cost (indices,
 // parameters, the filter lookup, the barriers) is spread over 4G nodes
-// instead of two.  MinB: CTAs per SM the compiler must fit.
-template <int MinB, int G>
+// instead of two.  MinB: CTAs per SM the compiler must fit.  JT: the lattice
+// side fixed at compile time (0: mp.J), so that the index divisions of a
+// one-sub-step launch become shifts.
+template <int MinB, int G, int JT = 0>
 __global__ void __launch_bounds__(512, MinB)
     k_propagate_fhnp4(ModelParams mp, Key key, uint32_t stream, uint32_t stim_stream, const int32_t *pfilt,
                       const FilterDesc *filt, const float *x_in, float *x_out, int64_t P, float *logw,
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(512, MinB)
     __shared__ int sh_ev[2][kMaxSlots], sh_cnt[2][kMaxSlots], sh_target[2][kMaxSlots], sh_base[kMaxSlots];
     __shared__ uint32_t sh_r1[2][kMaxSlots];
     __shared__ int warp_tot[32];
-    const int J = mp.J, nn = J * J, units = nn / NV, pairs = nn / 2, urow = J / NV;
+    const int J = JT ? JT : mp.J, nn = J * J, units = nn / NV, pairs = nn / 2, urow = J / NV;
     float4 *sv = reinterpret_cast<float4 *>(smem_raw);  // [2][ppc][units][G]
     const int slot = (int)threadIdx.x / units;
     const int s = min(slot, ppc);  // s == ppc: padding thread
@@ -509,7 +511,16 @@ cudaError_t launch_fhnp_interval(const Ctx &c, const float *d_obs, int32_t strid
 #define PF_FHNP4_ARGS                                                                                             \
     c.mp, c.key, kStreamDyn, kStreamMisc, c.pfilt, c.filt, xi, xo, c.P, logw, d_obs, stride, c.obs_slot, c.d_t, ppc, \
         fmax, n_steps, aux, noise
-        if (nodes == 4 && more)
+        if (c.mp.J == 32) {  // the paper's side (Sec. 5.2): compile-time indexing
+            if (nodes == 4 && more)
+                k_propagate_fhnp4<4, 1, 32><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+            else if (nodes == 4)
+                k_propagate_fhnp4<3, 1, 32><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+            else if (more)
+                k_propagate_fhnp4<3, 2, 32><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+            else
+                k_propagate_fhnp4<2, 2, 32><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
+        } else if (nodes == 4 && more)
             k_propagate_fhnp4<4, 1><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
         else if (nodes == 4)
             k_propagate_fhnp4<3, 1><<<grid, threads, smem, s>>>(PF_FHNP4_ARGS);
