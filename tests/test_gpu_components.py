@@ -53,6 +53,18 @@ def test_philox_bit_exact():
         assert np.array_equal(got, oracle.philox(ctr, *key))
 
 
+def test_philox_known_answers_on_the_device():
+    """The device generator reproduces the published Philox4x32-10 known-answer vectors."""
+    from test_oracle_rng import philox_kat
+
+    for c, k, o in philox_kat():
+        d_ctr = torch.from_numpy(c[None, :].view(np.int32).copy()).cuda()
+        d_out = torch.empty_like(d_ctr)
+        pf.pf_rng_philox(d_ctr, int(k[0]), int(k[1]), d_out)
+        torch.cuda.synchronize()
+        assert np.array_equal(d_out.cpu().numpy().view(np.uint32)[0], o), (c, k)
+
+
 def test_normals_match_oracle():
     ctr = W.random_counters(1 << 20, seed=2)  # 4M normals: u1 within 2^-20 of 1 is sampled
     seed = 0x0123456789ABCDEF
