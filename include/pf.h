@@ -416,22 +416,24 @@ PF_API pf_status pf_record_tuples(pf_ctx *ctx, float *d_X, float *d_R, int64_t c
 PF_API pf_status pf_recorded_tuples(const pf_ctx *ctx, int64_t *count);
 
 /* Systematic resampling that allocates nothing.  Some callers cannot call
- * cudaMalloc when they resample -- code running while its stream is captured
- * into a CUDA graph, host frameworks that own every device allocation, loops
- * with a fixed memory budget -- and cannot hand over scratch either.  This
- * variant of pf_systematic_resample takes the same arguments minus the
- * scratch, and uses a device array built into the library instead (about
- * 3.3 MB, held by every GPU that loads the library until the process exits).
+ * cudaMalloc when they resample -- host frameworks that own every device
+ * allocation, real-time loops with a fixed memory budget, where an allocation
+ * could fail or stall -- and cannot hand over scratch either.  This variant of
+ * pf_systematic_resample takes the same arguments minus the scratch, and uses
+ * a device array built into the library instead (about 3.3 MB, held by every
+ * GPU that loads the library until the process exits).
  * The paper has no counterpart; it is a convenience of this library.
  * Limits: M <= PF_NOALLOC_MAX_FILTERS and sum N_m <= PF_NOALLOC_MAX_PARTICLES,
  * else PF_EINVAL (message in pf_last_error(NULL)).
- * The first call on a device looks the array's address up on that device
- * (make that device current; make the first call before any stream capture).
- * Every call on a device shares the one array: calls whose work overlaps on the
- * GPU (other streams, other host threads) race and must be serialised by the
- * caller.  The call calls no cudaMalloc, cudaFree or allocating routine; like
- * pf_systematic_resample it synchronises `stream` once to upload its plan.
- * Results are identical to pf_systematic_resample's.
+ * Each call looks the array's address up on the current device, which must be
+ * the device of `stream` and of the pointers.  The first call on a device also
+ * loads the array there; make that first call before any stream capture.
+ * Every call on a device shares the one array, which keeps the previous call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The call calls no
+ * cudaMalloc, cudaFree or allocating routine; like pf_systematic_resample it
+ * synchronises `stream` once to upload its plan.  Results are identical to
+ * pf_systematic_resample's.
  * Errors: PF_EINVAL, PF_ECUDA. */
 #define PF_NOALLOC_MAX_FILTERS 1024
 #define PF_NOALLOC_MAX_PARTICLES 262144

@@ -1,13 +1,12 @@
 // pf_noalloc.cu -- systematic resampling without any allocation.
 //
 // Some callers cannot allocate device memory at the moment they need to
-// resample: code that runs while a stream is being captured into a CUDA
-// graph, applications whose host framework owns every device allocation and
-// forbids others, and real-time loops with a fixed memory budget.  For them
+// resample: applications whose host framework owns every device allocation
+// and forbids others, and real-time loops with a fixed memory budget, where
+// an allocation could fail or stall.  For them
 // pf_systematic_resample_noalloc takes its scratch from one file-scope device
 // array instead of from the caller or from cudaMalloc.
 #include <cstdint>
-#include <mutex>
 
 #include "pf.h"
 #include "pf_internal.h"
@@ -32,27 +31,17 @@ constexpr size_t kScratchBytes =
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device.  In host
-// code the array's name is only a host-side stand-in, so the address must come
-// from cudaGetSymbolAddress with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};
-
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress with that device current.  It is looked up on every
+// call (cheap once the module is loaded, and it allocates nothing), so the
+// address stays right across devices and after a cudaDeviceReset.
 cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -1,9 +1,9 @@
 """Systematic resampling through the entry point that allocates nothing.
 
 pf_systematic_resample_noalloc serves callers that can neither allocate device
-memory nor hand over scratch when they resample (code running under stream
-capture, host frameworks that own every allocation, fixed-budget loops); it
-uses a device array built into the library.  Its ancestors must equal those of
+memory nor hand over scratch when they resample (host frameworks that own every
+allocation, real-time loops with a fixed memory budget); it uses a device array
+built into the library.  Its ancestors must equal those of
 pf_systematic_resample (whose scratch the caller allocates) exactly -- this is
 index work -- on two calls in a row, since every call reuses the same array.
 This file is collected last so that a failure here leaves every other test run.
@@ -25,10 +25,10 @@ def _inputs(N, seed):
     return torch.from_numpy(w).cuda(), torch.from_numpy(u).cuda()
 
 
-def _with_caller_scratch(N, d_w, d_u):
+def _with_caller_scratch(N, d_w, d_u, stream=None):
     d_anc = torch.empty(d_w.numel(), dtype=torch.int32, device="cuda")
     d_scr = torch.empty(pf.pf_systematic_scratch_bytes(len(N), d_w.numel()), dtype=torch.uint8, device="cuda")
-    pf.pf_systematic_resample(N, d_w, d_u, d_anc, d_scr)
+    pf.pf_systematic_resample(N, d_w, d_u, d_anc, d_scr, stream=stream)
     torch.cuda.synchronize()
     return d_anc.cpu().numpy()
 
@@ -45,6 +45,19 @@ def test_noalloc_matches_allocating_entry_point_twice():
         torch.cuda.synchronize()
         got = d_anc.cpu().numpy()
         assert np.array_equal(got, _with_caller_scratch(N, d_w, d_u)), k
+
+
+def test_noalloc_on_a_stream_of_the_callers():
+    """Callers normally pass a stream of their own, not the legacy default stream."""
+    N = W.ragged_counts(24, 64, 4096)
+    d_w, d_u = _inputs(N, seed=300)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        d_anc = torch.full((d_w.numel(),), -7, dtype=torch.int32, device="cuda")
+        pf.pf_systematic_resample_noalloc(N, d_w, d_u, d_anc, stream=s.cuda_stream)
+        s.synchronize()
+        assert np.array_equal(d_anc.cpu().numpy(), _with_caller_scratch(N, d_w, d_u, stream=s.cuda_stream))
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
