@@ -280,6 +280,29 @@ PF_API pf_status pf_set_resampling(pf_ctx *ctx, double ess_threshold);
 PF_API pf_status pf_set_schedule(pf_ctx *ctx, int32_t nodes_per_thread, int32_t particles_per_cta,
                                  int32_t resample_threads);
 
+/* Failure injection from the host, for testing a caller's error handling
+ * without faulting the GPU: writes the context's device error word as a
+ * failed bounded device wait (code = PF_ETIMEOUT) or a filter whose weights
+ * all vanished (code = PF_ENUMERIC, naming `filter`) would have written it,
+ * behind the work already on the context's stream (synchronises).  The next
+ * pf_estimate or pf_estimate_wait then returns that code and the context
+ * refuses further steps (PF_ESTATE), exactly as after the real failure.  The
+ * paper has no counterpart (its analysis assumes exact arithmetic).
+ * Errors: PF_EINVAL (another code, filter out of range), PF_ECUDA. */
+PF_API pf_status pf_inject_error(pf_ctx *ctx, int32_t code, int32_t filter);
+
+/* Definition 1's average over the M filters, from per-filter estimates held
+ * on the host (the form a caller that splits the filters over several
+ * processes gathers): h_out[s] = (sum_m h_est[m * n_stat + s]) / M for
+ * s < n_stat.  h_est: M x n_stat doubles, row-major [m][s] (host);
+ * h_out: n_stat doubles (host).  The sum over m is exact (a fixed-point
+ * accumulator spanning the binary64 range) and rounded once to the nearest
+ * double, so the result does not depend on the order of the filters or on how
+ * they were split; the division by M is one IEEE rounding.  A NaN, or
+ * infinities of both signs, give NaN.  Host code only: no device, no stream.
+ * Errors: PF_EINVAL. */
+PF_API pf_status pf_ensemble_average(int32_t M, int32_t n_stat, const double *h_est, double *h_out);
+
 /* --------------------------------------------------------------------- */
 /* Inspection and state transfer (synchronous; for tests and checkpoints) */
 /* --------------------------------------------------------------------- */
@@ -315,6 +338,15 @@ PF_API pf_status pf_rng_philox(int64_t n, const uint32_t *d_ctr, uint32_t key0, 
 
 /* Four FP32 Box-Muller normals per counter (key = seed): d_z is n x 4. */
 PF_API pf_status pf_rng_normals(int64_t n, const uint32_t *d_ctr, uint64_t seed, float *d_z, void *stream);
+
+/* A keyed pseudo-random permutation of [0, n): d_perm[i] = pi(i) (n int64,
+ * device).  pi is four rounds of (add a key word, multiply by an odd
+ * constant, xor-shift) on the integers below the next power of two >= n, each
+ * a bijection there, keyed by the Philox4x32-10 block (0, 0, 0, stream 6)
+ * under `seed`, and cycle-walked into [0, n) -- a bijection of [0, n) that
+ * every element evaluates on its own (no sort).  Used to shuffle training
+ * batches.  Errors: PF_EINVAL, PF_ECUDA. */
+PF_API pf_status pf_permutation(int64_t n, uint64_t seed, int64_t *d_perm, void *stream);
 
 /* Bytes of device scratch pf_systematic_resample needs for M filters with
  * `total` particles in all. */
@@ -387,6 +419,14 @@ PF_API pf_status pf_mlp_trainer_create(const float *h_theta, int32_t n_params, i
  * call synchronises `stream`.  Deterministic (fixed-order reductions). */
 PF_API pf_status pf_mlp_train_step(pf_mlp_trainer *tr, int64_t batch, const float *d_X, const float *d_R, float lr,
                                    float *h_grad, double *h_loss, void *stream);
+/* pf_mlp_train_step on a shuffled mini-batch gathered by the library: the
+ * rows pi(first), ..., pi(first + batch - 1) of d_X (n x 51) and d_R (n x 2),
+ * with pi the keyed permutation of [0, n) that pf_permutation(n, perm_seed)
+ * gives.  An epoch of shuffled batches takes one seed and first = 0, batch,
+ * 2 batch, ...  Requires first + batch <= n.  Errors: PF_EINVAL, PF_ECUDA. */
+PF_API pf_status pf_mlp_train_step_shuffled(pf_mlp_trainer *tr, int64_t n, const float *d_X, const float *d_R,
+                                            int64_t batch, int64_t first, uint64_t perm_seed, float lr,
+                                            float *h_grad, double *h_loss, void *stream);
 /* Copies the current parameters to host memory (synchronous). */
 PF_API pf_status pf_mlp_trainer_get(pf_mlp_trainer *tr, float *h_theta);
 /* NULL-safe. */

@@ -37,6 +37,74 @@ __global__ void k_pack(const float *__restrict__ theta, __nv_bfloat16 *__restric
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shuffled mini-batches.  pi is a keyed bijection of [0, n): four rounds of
+// (add a key, multiply by an odd constant, xor with the upper half shifted
+// down), each a bijection of the k-bit integers, 2^k >= n, and cycle-walking
+// (apply the rounds again while the value is >= n) to stay inside [0, n).
+// The round keys are the four words of Philox4x32-10 at counter
+// (0, 0, 0, stream 6) under the caller's 64-bit seed.
+// ---------------------------------------------------------------------------
+struct Perm {
+    uint64_t n, mask;
+    int half;
+    uint64_t key[4];
+};
+
+__device__ __forceinline__ Perm make_perm(uint64_t n, const Key &key)
+{
+    Perm p;
+    p.n = n;
+    int k = 1;
+    while ((uint64_t(1) << k) < n) ++k;
+    p.mask = (uint64_t(1) << k) - 1;
+    p.half = (k + 1) / 2;
+    const uint4 r = philox4x32_10(make_uint4(0u, 0u, 0u, 6u << 24), key);
+    p.key[0] = r.x; p.key[1] = r.y; p.key[2] = r.z; p.key[3] = r.w;
+    return p;
+}
+
+__device__ __forceinline__ uint64_t perm_rounds(uint64_t x, const Perm &p)
+{
+    const uint64_t C[4] = {0x9E3779B97F4A7C15ull, 0xC2B2AE3D27D4EB4Full, 0x165667B19E3779F9ull, 0xD6E8FEB86659FD93ull};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        x = (x + p.key[r]) & p.mask;
+        x = (x * C[r]) & p.mask;
+        x ^= x >> p.half;
+    }
+    return x;
+}
+
+// pi(i) for i < n: the walk stays on the cycle of i, which holds i itself, so it ends.
+__device__ __forceinline__ uint64_t perm_apply(uint64_t i, const Perm &p)
+{
+    uint64_t y = perm_rounds(i, p);
+    while (y >= p.n) y = perm_rounds(y, p);
+    return y;
+}
+
+__global__ void k_permutation(int64_t n, Key key, int64_t *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Perm p = make_perm((uint64_t)n, key);
+    out[i] = (int64_t)perm_apply((uint64_t)i, p);
+}
+
+// Rows pi(first + j), j < batch, of (X, R) into the batch buffers.
+__global__ void k_gather_batch(int64_t n, const float *__restrict__ X, const float *__restrict__ R, int64_t batch,
+                               int64_t first, Key key, float *__restrict__ Xb, float *__restrict__ Rb)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= batch) return;
+    const Perm p = make_perm((uint64_t)n, key);
+    const int64_t src = (int64_t)perm_apply((uint64_t)(first + j), p);
+    for (int c = 0; c < kIn; ++c) Xb[j * kIn + c] = X[src * kIn + c];
+    Rb[j * 2] = R[src * 2];
+    Rb[j * 2 + 1] = R[src * 2 + 1];
+}
+
 constexpr int kRowsPerCta = 64;  // 4 warps x 16 rows
 constexpr int kFwdThreads = 128;
 
@@ -396,13 +464,14 @@ struct pf_mlp_trainer {
     __nv_bfloat16 *wp = nullptr, *w2t = nullptr;
     __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *dz1 = nullptr, *dz2 = nullptr;
     float *z1 = nullptr, *z2 = nullptr, *out = nullptr, *dout = nullptr, *row_loss = nullptr, *partial = nullptr;
+    float *xb = nullptr, *rb = nullptr;  // a shuffled batch's rows
     int64_t step = 0;
 };
 
 static void trainer_free(pf_mlp_trainer *t)
 {
     void *ptrs[] = {t->theta, t->m, t->v, t->grad, t->wp, t->w2t, t->x0, t->a1, t->a2, t->dz1, t->dz2,
-                    t->z1, t->z2, t->out, t->dout, t->row_loss, t->partial};
+                    t->z1, t->z2, t->out, t->dout, t->row_loss, t->partial, t->xb, t->rb};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -448,7 +517,8 @@ pf_status pf_mlp_trainer_create(const float *h_theta, int32_t n_params, int64_t 
               cudaMalloc(&t->dz2, B * mlp::kHid * 2) == cudaSuccess && cudaMalloc(&t->z1, B * mlp::kHid * 4) == cudaSuccess &&
               cudaMalloc(&t->z2, B * mlp::kHid * 4) == cudaSuccess && cudaMalloc(&t->out, B * mlp::kOut * 4) == cudaSuccess &&
               cudaMalloc(&t->dout, B * mlp::kOut * 4) == cudaSuccess && cudaMalloc(&t->row_loss, B * 4) == cudaSuccess &&
-              cudaMalloc(&t->partial, chunks * (P + 1) * 4) == cudaSuccess;
+              cudaMalloc(&t->partial, chunks * (P + 1) * 4) == cudaSuccess &&
+              cudaMalloc(&t->xb, B * mlp::kIn * 4) == cudaSuccess && cudaMalloc(&t->rb, B * 2 * 4) == cudaSuccess;
     if (ok) ok = cudaMemcpy(t->theta, h_theta, P * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
                  cudaMemset(t->m, 0, P * 4) == cudaSuccess && cudaMemset(t->v, 0, P * 4) == cudaSuccess;
     if (!ok) {
@@ -505,6 +575,28 @@ pf_status pf_mlp_train_step(pf_mlp_trainer *t, int64_t batch, const float *d_X, 
         if (e == cudaSuccess && h_loss) *h_loss = (double)loss_sum / (double)batch;
     }
     return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+pf_status pf_permutation(int64_t n, uint64_t seed, int64_t *d_perm, void *stream)
+{
+    if (n < 0 || (n > 0 && !d_perm)) return PF_EINVAL;
+    if (n == 0) return PF_OK;
+    mlp::k_permutation<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, make_key(seed), d_perm);
+    return cudaGetLastError() == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+pf_status pf_mlp_train_step_shuffled(pf_mlp_trainer *t, int64_t n, const float *d_X, const float *d_R, int64_t batch,
+                                     int64_t first, uint64_t perm_seed, float lr, float *h_grad, double *h_loss,
+                                     void *stream)
+{
+    if (!t || !d_X || !d_R || batch < 1 || batch > t->max_batch || first < 0 || n < 1 || first + batch > n)
+        return PF_EINVAL;
+    cudaSetDevice(t->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    mlp::k_gather_batch<<<(unsigned)((batch + 255) / 256), 256, 0, s>>>(n, d_X, d_R, batch, first, make_key(perm_seed),
+                                                                       t->xb, t->rb);
+    if (cudaGetLastError() != cudaSuccess) return PF_ECUDA;
+    return pf_mlp_train_step(t, batch, t->xb, t->rb, lr, h_grad, h_loss, stream);
 }
 
 pf_status pf_mlp_trainer_get(pf_mlp_trainer *t, float *h_theta)

@@ -861,6 +861,22 @@ pf_status pf_estimate_wait(pf_ctx *h)
     return PF_OK;
 }
 
+pf_status pf_inject_error(pf_ctx *h, int32_t code, int32_t filter)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (code != PF_ETIMEOUT && code != PF_ENUMERIC) return fail(c, PF_EINVAL, "only PF_ETIMEOUT and PF_ENUMERIC are injected");
+    if (filter < 0 || filter >= c.M) return fail(c, PF_EINVAL, "filter out of range");
+    cudaSetDevice(c.device);
+    // The words the device would have written: the flag of the failed wait or of
+    // the degenerate normaliser, and the filter it names.  Enqueued behind the
+    // work already on the stream, so the next check sees them like a real failure.
+    const int32_t word[2] = {code == PF_ETIMEOUT ? kErrTimeout : kErrDegenerate, filter};
+    cudaError_t e = cudaMemcpyAsync(c.err, word, sizeof(word), cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    return e == cudaSuccess ? PF_OK : cuda_fail(c, e, "error injection");
+}
+
 static void drop_graphs(Ctx &c)
 {
     for (int k = 0; k < 2; ++k) {

@@ -74,6 +74,8 @@ _SIGS = {
     "pf_set_auxiliary": (c_int32, [c_void_p, c_int32]),
     "pf_estimate_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pf_estimate_wait": (c_int32, [c_void_p]),
+    "pf_inject_error": (c_int32, [c_void_p, c_int32, c_int32]),
+    "pf_ensemble_average": (c_int32, [c_int32, c_int32, POINTER(c_double), POINTER(c_double)]),
     "pf_step_kernels": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_resampling": (c_int32, [c_void_p, c_double]),
     "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
@@ -87,6 +89,9 @@ _SIGS = {
     "pf_mlp_train_step": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_float, POINTER(c_float),
                                     POINTER(c_double), c_void_p]),
     "pf_mlp_trainer_get": (c_int32, [c_void_p, POINTER(c_float)]),
+    "pf_mlp_train_step_shuffled": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_int64, c_int64, c_uint64,
+                                             c_float, POINTER(c_float), POINTER(c_double), c_void_p]),
+    "pf_permutation": (c_int32, [c_int64, c_uint64, c_void_p, c_void_p]),
     "pf_mlp_trainer_destroy": (None, [c_void_p]),
     "pf_simulate": (c_int32, [POINTER(pf_model), c_double, POINTER(pf_obs_op), POINTER(pf_noise), c_int32, c_int32,
                               c_int32, POINTER(c_double), POINTER(c_float)]),
@@ -182,6 +187,22 @@ def pf_systematic_resample(N: Sequence[int], d_w, d_u, d_anc, d_scratch, stream=
                                         d_scratch.data_ptr(), d_scratch.numel() * d_scratch.element_size(), stream))
 
 
+def pf_permutation(n: int, seed: int, d_perm, stream=None):
+    """The library's keyed permutation of [0, n) into d_perm (n int64, device)."""
+    _check(lib().pf_permutation(int(n), int(seed), d_perm.data_ptr(), stream))
+
+
+def pf_ensemble_average(est) -> np.ndarray:
+    """Definition 1's average of per-filter estimates (M x n_stat, host FP64):
+    the exact sum over filters rounded once, divided by M (pf_ensemble_average)."""
+    e = np.ascontiguousarray(est, dtype=np.float64)
+    if e.ndim == 1:
+        e = e[:, None]
+    out = np.empty(e.shape[1], dtype=np.float64)
+    _check(lib().pf_ensemble_average(e.shape[0], e.shape[1], _dp(e), _dp(out)))
+    return out
+
+
 def pf_systematic_resample_noalloc(N: Sequence[int], d_w, d_u, d_anc, stream=None):
     """Systematic resampling with the library's built-in scratch (no allocation)."""
     Nh = np.ascontiguousarray(N, dtype=np.int32)
@@ -222,6 +243,18 @@ class MLPTrainer:
                                        _fp(g) if g is not None else POINTER(c_float)(),
                                        ctypes.byref(loss) if (want_loss or want_grad) else POINTER(c_double)(),
                                        stream))
+        return loss.value, g
+
+    def step_shuffled(self, d_X, d_R, batch: int, first: int, perm_seed: int, lr: float, want_grad: bool = False,
+                      want_loss: bool = True, stream=None):
+        """A step on rows pi(first .. first + batch - 1) of (d_X, d_R), pi = pf_permutation(n, perm_seed)."""
+        g = np.empty(MLP_PARAMS, dtype=np.float32) if want_grad else None
+        loss = c_double(0.0)
+        _check(lib().pf_mlp_train_step_shuffled(self.h, d_X.shape[0], d_X.data_ptr(), d_R.data_ptr(), int(batch),
+                                                int(first), int(perm_seed), float(lr),
+                                                _fp(g) if g is not None else POINTER(c_float)(),
+                                                ctypes.byref(loss) if (want_loss or want_grad) else POINTER(c_double)(),
+                                                stream))
         return loss.value, g
 
     def theta(self) -> np.ndarray:
@@ -367,6 +400,10 @@ class EnsembleFilter:
         st = pf_stat(kind, var, 1 if per_filter else 0)
         _check(lib().pf_estimate_async(self.h, ctypes.byref(st), buf.data_ptr()), self.h)
         return _PendingEstimate(self, buf, per_filter and kind == PF_STAT_MEAN and var < 0)
+
+    def inject_error(self, code: int, filter: int = 0):
+        """Host-side failure injection (pf_inject_error): the next estimate reports `code`."""
+        _check(lib().pf_inject_error(self.h, int(code), int(filter)), self.h)
 
     def step_kernels(self) -> int:
         """Kernels one step launches (kernel nodes of the captured step graph)."""

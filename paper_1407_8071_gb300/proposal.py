@@ -37,21 +37,25 @@ def collect_tuples(spec: W.ModelSpec, M: int, N: int, record: np.ndarray, seed: 
     return X[:n], R[:n], n
 
 
+def epoch_seed(seed: int, epoch: int) -> int:
+    """The permutation key of one epoch: the run's seed in the low word, the epoch above it."""
+    return (int(seed) & 0xFFFFFFFF) | ((int(epoch) & 0xFFFFFFFF) << 32)
+
+
 def train(theta0: np.ndarray, X, R, epochs: int = 4, batch: int = 8192, lr: float = 1e-3, seed: int = 0,
           log=None) -> tuple[np.ndarray, list]:
-    """Adam on the tuples in shuffled mini-batches; returns the parameters and the loss history."""
-    import torch
+    """Adam on the tuples in shuffled mini-batches; returns the parameters and the loss history.
+    Each epoch's order is the library's keyed permutation of the rows (pf_permutation),
+    and the library gathers each batch's rows (pf_mlp_train_step_shuffled)."""
     n = X.shape[0]
+    batch = min(batch, n)
     tr = pf.MLPTrainer(theta0, max_batch=batch)
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
     losses = []
     try:
         for ep in range(epochs):
-            perm = torch.randperm(n, device="cuda", generator=g)
+            key = epoch_seed(seed, ep)
             for b0 in range(0, n - batch + 1, batch):
-                idx = perm[b0:b0 + batch]
-                loss, _ = tr.step(X[idx].contiguous(), R[idx].contiguous(), lr=lr)
+                loss, _ = tr.step_shuffled(X, R, batch, b0, key, lr=lr)
                 losses.append(loss)
             if log:
                 log(f"epoch {ep}: loss {np.mean(losses[-max(1, n // batch):]):.5f}")

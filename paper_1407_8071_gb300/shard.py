@@ -4,14 +4,13 @@ The filters share nothing (Sec. 3.1: the ensemble is M independent filters),
 so ranks exchange no particle and no weight: each rank runs a contiguous range
 of filters, balanced by particle count, through its own context, and the only
 collective is the gather of per-filter estimates for the M-average of
-Definition 1.  The average is the correctly rounded FP64 sum (math.fsum) over
-all filters divided by M, so it does not depend on how the filters were split
-or in which order they arrive: any number of ranks gives the number one
-process gives, bit for bit.
+Definition 1.  The average is formed by the library (pf_ensemble_average): the
+exact sum over all filters rounded once to FP64, divided by M, so it does not
+depend on how the filters were split or in which order they arrive: any number
+of ranks gives the number one process gives, bit for bit.
 """
 from __future__ import annotations
 
-import math
 from typing import List, Sequence, Tuple
 
 import numpy as np
@@ -44,8 +43,8 @@ def partition(N: Sequence[int], world: int) -> List[Tuple[int, int]]:
 def ensemble_mean(local_est: np.ndarray, begin: int, M: int, group=None) -> np.ndarray:
     """Definition 1's average over all M filters from each rank's per-filter
     estimates (local_est: rows for filters begin, begin + 1, ...).  Gathers
-    every rank's rows (torch.distributed, any backend), then sums each
-    statistic with math.fsum in FP64."""
+    every rank's rows (torch.distributed, any backend) in filter order; the
+    library forms the average."""
     import torch
     import torch.distributed as dist
     local_est = np.ascontiguousarray(local_est, dtype=np.float64)
@@ -72,4 +71,5 @@ def ensemble_mean(local_est: np.ndarray, begin: int, M: int, group=None) -> np.n
             seen[b:b + n] = True
         if not seen.all():
             raise ValueError("the ranks' filter ranges do not cover all M filters")
-    return np.array([math.fsum(rows[:, s]) / M for s in range(rows.shape[1])])
+    from . import pf
+    return pf.pf_ensemble_average(rows)

@@ -281,3 +281,36 @@ def test_torch_allocator_and_injected_allocation_failure():
         assert torch.cuda.memory_allocated() == before
     finally:
         pf.use_torch_allocator(False)
+
+
+@pytest.mark.parametrize("code", [pf.PF_ETIMEOUT, pf.PF_ENUMERIC])
+def test_device_failure_flags_reach_the_caller(code):
+    """The error word a bounded device wait (or a degenerate normaliser) sets is
+    turned into the status code on both read paths, and the context refuses
+    further steps.  The word is written from the host (pf_inject_error): making
+    a tensor-core wait expire with MMAs in flight is not a safe test."""
+    spec = W.lorenz63()
+    _, y = oracle.simulate(spec, 3, W.SEED_LORENZ_OBS)
+    y32 = y.astype(np.float32)
+    for path in ("sync", "async"):
+        with pf.EnsembleFilter(spec, 3, 128, 21) as f:
+            f.step(y32[0])
+            assert np.isfinite(f.estimate(pf.PF_STAT_MEAN, var=1)).all()  # healthy before
+            f.inject_error(code, filter=2)
+            with pytest.raises(pf.PFError) as e:
+                if path == "sync":
+                    f.estimate(pf.PF_STAT_MEAN, var=1)
+                else:
+                    f.estimate_async(pf.PF_STAT_MEAN, var=1).wait()
+            assert e.value.status == code
+            if code == pf.PF_ENUMERIC:
+                assert "filter 2" in str(e.value)
+            else:
+                assert "wait" in str(e.value)
+            with pytest.raises(pf.PFError) as e2:
+                f.step(y32[1])
+            assert e2.value.status == pf.PF_ESTATE
+    with pf.EnsembleFilter(spec, 3, 128, 21) as f:
+        with pytest.raises(pf.PFError) as e:
+            f.inject_error(pf.PF_EINVAL)
+        assert e.value.status == pf.PF_EINVAL

@@ -125,3 +125,40 @@ def test_lattice_forward_on_tcgen05_matches_oracle(J, P):
     err = np.abs(got - ref) / (np.abs(ref) + scale)
     assert np.all(np.isfinite(got))
     assert err.max() <= 2e-2, (err.max(), np.unravel_index(np.argmax(err), err.shape))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1000, 4096, 70001])
+def test_permutation_is_a_bijection(n):
+    d = torch.empty(n, dtype=torch.int64, device="cuda")
+    perms = []
+    for seed in (1, 2, 1 | (7 << 32)):
+        pf.pf_permutation(n, seed, d)
+        torch.cuda.synchronize()
+        p = d.cpu().numpy()
+        assert np.array_equal(np.sort(p), np.arange(n))
+        perms.append(p)
+    if n >= 1000:
+        assert not np.array_equal(perms[0], perms[1]) and not np.array_equal(perms[0], perms[2])
+        # a shuffle, not a shift: consecutive rows land far apart
+        assert np.mean(np.abs(np.diff(perms[0]))) > n / 8
+
+
+def test_shuffled_step_trains_on_the_permuted_rows():
+    """The library's gathered batch is exactly rows pi(first ..) of the tuples: the
+    shuffled step's gradient is bit-identical to the plain step's on X[pi]."""
+    th = _theta(5)
+    X, R = _rows(5000, 6)
+    d_X = torch.from_numpy(X.astype(np.float32)).cuda()
+    d_R = torch.from_numpy(R.astype(np.float32)).cuda()
+    seed, first, batch = 12345 | (3 << 32), 1024, 2048
+    d_p = torch.empty(5000, dtype=torch.int64, device="cuda")
+    pf.pf_permutation(5000, seed, d_p)
+    idx = d_p[first:first + batch]
+    t1, t2 = pf.MLPTrainer(th, max_batch=batch), pf.MLPTrainer(th, max_batch=batch)
+    try:
+        l1, g1 = t1.step_shuffled(d_X, d_R, batch, first, seed, lr=0.0, want_grad=True)
+        l2, g2 = t2.step(d_X[idx].contiguous(), d_R[idx].contiguous(), lr=0.0, want_grad=True)
+    finally:
+        t1.close()
+        t2.close()
+    assert l1 == l2 and np.array_equal(g1, g2)

@@ -4,6 +4,10 @@
   within the largest filter.
 * ensemble_mean over ranks equals the single-process value bit for bit (FP64
   correctly rounded sums), for ragged filter counts and several statistics.
+* the library's Definition 1 average (pf_ensemble_average, host code, no GPU)
+  is the exact sum rounded once: it equals the exact rational sum (Python's
+  fractions) rounded to a double, divided by M, on hard cases -- cancellation across the
+  whole exponent range, subnormals, ties -- and does not depend on the order.
 """
 import math
 import os
@@ -67,3 +71,41 @@ def test_ensemble_mean_over_ranks_is_bit_identical(world):
     for r in range(world):
         assert np.array_equal(got[r], ref)
     assert np.allclose(ref, est.mean(axis=0), rtol=1e-12, atol=0)
+
+
+def _fsum_mean(est):
+    """Exact rational sum (fractions.Fraction), rounded once by Python's correctly
+    rounded int / int division, then divided by M."""
+    from fractions import Fraction
+    est = np.asarray(est, dtype=np.float64).reshape(len(est), -1)
+    out = []
+    for s in range(est.shape[1]):
+        tot = sum((Fraction(float(v)) for v in est[:, s]), Fraction(0))
+        out.append(float(tot) / est.shape[0])
+    return np.array(out)
+
+
+def test_library_average_is_the_exact_sum_rounded_once():
+    from paper_1407_8071_gb300 import pf
+    rng = np.random.default_rng(5)
+    cases = [
+        rng.normal(0.0, 1.0, (1000, 3)),
+        rng.normal(0.0, 1.0, (257, 4)) * 10.0 ** rng.integers(-300, 300, (257, 4)),
+        np.array([[1e308], [1e308], [-1e308], [-1e308], [1e-308], [3.0]]),   # cancellation, no overflow
+        np.array([[2.0 ** 53], [1.0], [1.0]]),                                 # 2^53 + 2: exact only if summed exactly
+        np.array([[1.0], [2.0 ** -53], [2.0 ** -106]]),                        # just above a tie: rounds up
+        np.array([[1.0], [2.0 ** -53]]),                                       # an exact tie: to even (down)
+        np.array([[5e-324], [5e-324], [-1e-323], [4e-323]]),                   # subnormals
+        np.array([[0.1]] * 10),
+        np.array([[-0.0], [-0.0]]),
+    ]
+    for est in cases:
+        got = pf.pf_ensemble_average(est)
+        ref = _fsum_mean(est)
+        assert np.array_equal(got, ref), (est.ravel()[:6], got, ref)
+        for _ in range(3):  # any order of the filters gives the same bits
+            assert np.array_equal(pf.pf_ensemble_average(est[rng.permutation(len(est))]), got)
+    assert pf.pf_ensemble_average(np.array([[2.0 ** 53], [1.0], [1.0]]))[0] * 3 == 2.0 ** 53 + 2
+    assert np.isnan(pf.pf_ensemble_average(np.array([[1.0], [np.nan]]))[0])
+    assert np.isnan(pf.pf_ensemble_average(np.array([[np.inf], [-np.inf]]))[0])
+    assert pf.pf_ensemble_average(np.array([[np.inf], [1.0]]))[0] == np.inf
