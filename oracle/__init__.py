@@ -267,6 +267,29 @@ def mlp_forward_c(theta: np.ndarray, rows: np.ndarray, bf16: bool = True) -> np.
     return out
 
 
+def propagate_proposal(spec, theta, x: np.ndarray, pid, fid, t: int, seed: int, y: np.ndarray, bf16: bool = True):
+    """One interval of the learned-proposal filter for each particle row of x (lattice):
+    returns (proposed x, the transition's candidates xb, sum of log p - log q per row,
+    network outputs o [n, dy, 4], normals and transition means zm [n, dy, 4], network
+    inputs rows [n, dy, 51])."""
+    md = _Model(spec)
+    x = np.array(x, dtype=np.float64, order="C", copy=True).reshape(-1, spec.dx)
+    n = len(x)
+    pid = np.ascontiguousarray(pid, dtype=np.int32)
+    fid = np.ascontiguousarray(fid, dtype=np.int32)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float32)
+    pr = _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, 0.0)
+    xb, lw = np.empty_like(x), np.empty(n)
+    o, zm, rows = np.empty((n, spec.dy, 4)), np.empty((n, spec.dy, 4)), np.empty((n, spec.dy, 51))
+    lib().orc_propagate_proposal(md.ref, ctypes.byref(pr), ctypes.c_int64(n), _p(pid, ctypes.c_int32),
+                                 _p(fid, ctypes.c_int32), ctypes.c_int32(t), ctypes.c_uint64(seed),
+                                 _p(y, ctypes.c_double), _p(x, ctypes.c_double), _p(xb, ctypes.c_double),
+                                 _p(lw, ctypes.c_double), _p(o, ctypes.c_double), _p(zm, ctypes.c_double),
+                                 _p(rows, ctypes.c_double))
+    return x, xb, lw, o, zm, rows
+
+
 def patch_row_c(spec, x: np.ndarray, node: int, y: float) -> np.ndarray:
     md = _Model(spec)
     x = np.ascontiguousarray(x, dtype=np.float64)

@@ -108,9 +108,14 @@ def nll(out: np.ndarray, R: np.ndarray) -> np.ndarray:
     return np.sum((R - mu) ** 2 / (2.0 * np.exp(2.0 * s)) + s, axis=1)
 
 
-def loss_and_grad(theta: np.ndarray, X: np.ndarray, R: np.ndarray, bf16_emulation: bool = False):
-    """Mean NLL over the rows and its gradient with respect to theta (hand-written backprop)."""
+def loss_and_grad(theta: np.ndarray, X: np.ndarray, R: np.ndarray, bf16_emulation: bool = False,
+                  bf16_backward: bool = False):
+    """Mean NLL over the rows and its gradient with respect to theta (hand-written backprop).
+    bf16_backward also rounds the two hidden-layer pre-activation gradients d_z2 and d_z1 to
+    bfloat16 where they are formed (the precision in which a BF16 training step stores them
+    between its passes)."""
     out, c = forward(theta, X, bf16_emulation)
+    rb = bf16 if bf16_backward else (lambda a: a)
     B = len(X)
     loss = float(np.mean(nll(out, R)))
     mu, s_raw = out[:, :2], out[:, 2:]
@@ -124,11 +129,11 @@ def loss_and_grad(theta: np.ndarray, X: np.ndarray, R: np.ndarray, bf16_emulatio
     g["W3"] = d_out.T @ c["a2"]
     g["b3"] = d_out.sum(0)
     d_a2 = d_out @ c["W3"]
-    d_z2 = d_a2 * gelu_grad(c["z2"])
+    d_z2 = rb(d_a2 * gelu_grad(c["z2"]))
     g["W2"] = d_z2.T @ c["a1"]
     g["b2"] = d_z2.sum(0)
     d_a1 = d_z2 @ c["W2"]
-    d_z1 = d_a1 * gelu_grad(c["z1"])
+    d_z1 = rb(d_a1 * gelu_grad(c["z1"]))
     g["W1"] = d_z1.T @ c["x0"]
     g["b1"] = d_z1.sum(0)
     return loss, pack(g)

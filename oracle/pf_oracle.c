@@ -441,10 +441,13 @@ void orc_patch_row(const orc_model *md, const double *x, int32_t node, double y,
 
 /* K - 1 ordinary sub-steps, then the last one with the proposal at the
  * observed nodes.  On return x holds the proposed state, xb (dx) the state
- * the transition alone would have produced, and *lw = sum (log p - log q). */
+ * the transition alone would have produced, and *lw = sum (log p - log q).
+ * o_rec (dy x 4) and zm_rec (dy x 4: the normals and the transition means of
+ * (v, w)) receive the network outputs and what they act on, and row_rec
+ * (dy x 51) the network inputs, when not NULL. */
 static void propagate_proposal(const orc_model *md, const orc_proposal *pr, uint64_t seed, uint32_t c0,
                                uint32_t c2, int32_t t, const double *y, double *x, double *xb, double *lw,
-                               double *z, double *f)
+                               double *z, double *f, double *o_rec, double *zm_rec, double *row_rec)
 {
     nstream ns;
     ns_init(&ns, seed, c0, (uint32_t)t, c2, ORC_STREAM_DYN);
@@ -464,10 +467,16 @@ static void propagate_proposal(const orc_model *md, const orc_proposal *pr, uint
     for (int j = 0; j < md->dy; ++j) {
         const int nd = md->obs_idx[j];
         orc_patch_row(md, x, nd, y[j], row);
+        if (row_rec) memcpy(row_rec + MLP_IN * j, row, sizeof(row));
         orc_mlp_forward(pr, 1, row, o);
+        if (o_rec) memcpy(o_rec + 4 * j, o, sizeof(o));
         for (int c = 0; c < 2; ++c) {
             const int var = c * nn + nd;
             const double m = x[var] + md->dt * f[var];
+            if (zm_rec) {
+                zm_rec[4 * j + c] = z[var];
+                zm_rec[4 * j + 2 + c] = m;
+            }
             const double oc = o[2 + c] < -MLP_CLAMP ? -MLP_CLAMP : (o[2 + c] > MLP_CLAMP ? MLP_CLAMP : o[2 + c]);
             const double mu = m + h * o[c], sd = h * exp(oc);
             const double xv = mu + sd * z[var];
@@ -507,6 +516,27 @@ void orc_propagate(const orc_model *md, int64_t n, const int32_t *pid, const int
 
 /* One Euler-Maruyama step with explicit normals (z: n x dx), for the
  * closed-form single-step pins. */
+/* One observation interval of the learned-proposal filter for each particle
+ * row of x (lattice): K - 1 transition sub-steps, then the last one drawn from
+ * the proposal at the observed nodes (see propagate_proposal).  x (n x dx) is
+ * replaced by the proposed states; xb (n x dx) receives the transition's
+ * candidates, lw (n) the sum over observed nodes of log p - log q; o (n x dy x 4),
+ * zm (n x dy x 4) and rows (n x dy x 51), when not NULL, the network outputs,
+ * the (normals, transition means) and the network inputs at the observed nodes. */
+void orc_propagate_proposal(const orc_model *md, const orc_proposal *pr, int64_t n, const int32_t *pid,
+                            const int32_t *fid, int32_t t, uint64_t seed, const double *y, double *x, double *xb,
+                            double *lw, double *o, double *zm, double *rows)
+{
+    double *z = (double *)malloc(sizeof(double) * md->dx);
+    double *f = (double *)malloc(sizeof(double) * md->dx);
+    for (int64_t q = 0; q < n; ++q)
+        propagate_proposal(md, pr, seed, (uint32_t)pid[q], (uint32_t)fid[q], t, y, x + q * md->dx, xb + q * md->dx,
+                           lw + q, z, f, o ? o + q * md->dy * 4 : NULL, zm ? zm + q * md->dy * 4 : NULL,
+                           rows ? rows + q * md->dy * MLP_IN : NULL);
+    free(z);
+    free(f);
+}
+
 void orc_em_step(const orc_model *md, int64_t n, int64_t step, double *x, const double *z)
 {
     double *f = (double *)malloc(sizeof(double) * md->dx);
@@ -745,7 +775,7 @@ int orc_bf_run_proposal(const orc_model *md, const orc_proposal *pr, int32_t M, 
                 for (int64_t i = 0; i < Nm; ++i) {
                     double lw;
                     propagate_proposal(md, pr, seed, (uint32_t)i, (uint32_t)m, t, y, x + i * dx, xb + i * dx, &lw, z,
-                                       f);
+                                       f, NULL, NULL, NULL);
                     l[i] = loglik(md, x + i * dx, y) + lw;
                     lb[i] = loglik(md, xb + i * dx, y);
                 }

@@ -250,3 +250,49 @@ def test_simulate_matches_oracle_lattice():
     xo, yo = oracle.simulate(spec, T, seed)
     assert np.max(np.abs(xg - xo)) <= 1e-10
     assert np.max(np.abs(yg - yo.astype(np.float32)) / (np.abs(yo) + 1.0)) <= 1e-6
+
+
+@pytest.mark.parametrize("N", [64, 1024])
+def test_fhn_full_size_one_step(N):
+    """One complete step of the 40 x 40 lattice (K = 20) from identical states:
+    propagated states and log-weights against the oracle, the per-filter log Z,
+    the ancestors against the oracle's systematic resampling of the GPU's own
+    log-weights (an FP32 exp moves a boundary only where a grid point lies
+    within ~1e-7 of a prefix value), the gather fused with the per-filter means
+    bit for bit, and the means within 1e-6."""
+    spec = fhn_spec(40)
+    M, seed = 2, 57
+    _, y = oracle.simulate(spec, 1, W.SEED_FHN_OBS)
+    y32 = y[0].astype(np.float32)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        x0 = f.get_state()
+        f.propagate(y32)
+        xg = f.get_state()
+        lg = f.get_logw()
+        f.resample()
+        anc = f.get_ancestors()
+        x1 = f.get_state()
+        logZ = f.estimate(pf.PF_STAT_LOG_Z, per_filter=True)
+        est = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)
+        ens = f.estimate(pf.PF_STAT_MEAN, var=-1)
+    rng = np.random.default_rng(8)
+    sample = np.arange(M * N) if N <= 64 else np.sort(rng.choice(M * N, size=96, replace=False))
+    pid, fid = (sample % N).astype(np.int32), (sample // N).astype(np.int32)
+    xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid, fid, 1, seed)
+    assert_state_close(xg[sample], xo)
+    lo = oracle.loglik(spec, xg.astype(np.float64), y32.astype(np.float64))
+    assert np.max(np.abs(lg - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+    for m in range(M):
+        a, b = m * N, (m + 1) * N
+        l = lg[a:b].astype(np.float64)
+        nrm = oracle.normalise(l)
+        assert logZ[m] == pytest.approx(nrm["logZ"], rel=1e-6)
+        exp = oracle.systematic(np.exp(l - nrm["max"]), oracle.resample_u(seed, m, 1))
+        got = anc[a:b]
+        assert np.all(np.diff(got) >= 0) and got.min() >= 0 and got.max() < N
+        assert np.sum(got != exp) <= max(2, N // 1000), (m, np.sum(got != exp))
+        src = xg[a + got]
+        assert np.array_equal(x1[a:b], src)
+        ref = src.astype(np.float64).mean(axis=0)
+        assert np.all(np.abs(est[m] - ref) <= 1e-6 * np.abs(src).astype(np.float64).mean(axis=0) + 1e-12)
+    assert np.allclose(ens, est.mean(axis=0), rtol=1e-12, atol=1e-12)

@@ -314,3 +314,16 @@ def test_device_failure_flags_reach_the_caller(code):
         with pytest.raises(pf.PFError) as e:
             f.inject_error(pf.PF_EINVAL)
         assert e.value.status == pf.PF_EINVAL
+
+
+def test_fhn_20x20_statistical_parity_with_oracle():
+    """The ragged batch's lattice size (20 x 20, 800 variables) over ten observations."""
+    spec = W.fhn_lattice(J=20, K=20)
+    T = 10
+    _, y = oracle.simulate(spec, T, W.SEED_FHN_OBS)
+    y32 = y.astype(np.float32)
+    M, N = 64, 64
+    node = 21  # a v-variable inside the stimulated corner block
+    eg = run_gpu(spec, M, N, y32, seed=23, var=node)
+    eo = oracle.bf_run(spec, M, N, T, y32.astype(np.float64), seed=24, est_idx=[node])["est"][:, :, 0]
+    z_parity(eg, eo, [0, 4, 9])

@@ -1,16 +1,26 @@
 """The learned proposal's network on the GPU against the FP64 oracle (oracle/mlp.py).
 
 Tolerances (BF16 operands and activations on both sides; the GPU accumulates
-in FP32 and stores backward intermediates in BF16, the oracle works in FP64):
-* forward: |o_gpu - o| <= 2e-2 (|o| + rms(o)),
-* gradient: cosine >= 0.999 and ||g_gpu - g|| <= 5e-2 ||g|| overall and per
-  parameter block; loss within 1e-3 relative,
+in FP32, the oracle works in FP64; tests/_mlp_bounds.py derives the bounds):
+* forward: every output within the interval bound that propagates the FP32
+  accumulation error gamma_K = (K + 2) 2^-23 of each dot product and a
+  possible one-step BF16 rounding flip of every activation close enough to a
+  rounding boundary; and at most 2 % of the rows beyond the bound of the last
+  layer's accumulation alone, gamma_128 (sum |W3| |a2| + |b3|) -- a row leaves
+  it only when one of its 256 hidden activations rounds to the other BF16
+  neighbour on the two sides, which the FP32 accumulation error (about
+  2^-24 sqrt(K) of a dot product) makes rare (0.5 % of rows measured);
+* gradient, with the oracle also storing the backward intermediates d_z2 and
+  d_z1 in BF16 as the GPU does: relative error <= 1e-4 overall and 1e-3 per
+  parameter block (FP32 accumulation over the batch, and the rare flips:
+  each moves one row's term by 2^-8 of itself); loss within 1e-6 relative;
 * Adam's first step: theta moves by lr sign(g) wherever |g| is not tiny,
 * training steps are bit-for-bit repeatable.
 """
 import numpy as np
 import pytest
 
+import _mlp_bounds
 from oracle import mlp
 from paper_1407_8071_gb300 import pf
 
@@ -33,6 +43,13 @@ def _rows(n, seed):
     return X.astype(np.float32).astype(np.float64), R.astype(np.float32).astype(np.float64)
 
 
+def check_forward(got, ref, bound, S3):
+    err = np.abs(got - ref)
+    assert np.all(err <= bound + 1e-12), (np.max(err / bound), np.unravel_index(np.argmax(err / bound), err.shape))
+    beyond = np.any(err > _mlp_bounds.gamma(128) * S3 + 1e-12, axis=1)
+    assert beyond.sum() <= 0.02 * len(beyond) + 2, beyond.mean()
+
+
 @pytest.mark.parametrize("n", [1, 17, 64, 1000, 70001])
 def test_forward_matches_oracle(n):
     th = _theta(1)
@@ -43,8 +60,7 @@ def test_forward_matches_oracle(n):
     torch.cuda.synchronize()
     got = d_out.cpu().numpy().astype(np.float64)
     ref, _ = mlp.forward(th, X, bf16_emulation=True)
-    scale = np.sqrt(np.mean(ref ** 2, axis=0, keepdims=True))
-    assert np.all(np.abs(got - ref) <= 2e-2 * (np.abs(ref) + scale)), np.max(np.abs(got - ref) / (np.abs(ref) + scale))
+    check_forward(got, ref, _mlp_bounds.forward_bound(th, X), _mlp_bounds.hidden_sizes(th, X))
 
 
 def _blocks():
@@ -60,14 +76,12 @@ def test_gradient_matches_oracle(B):
     loss, g = tr.step(torch.from_numpy(X.astype(np.float32)).cuda(), torch.from_numpy(R.astype(np.float32)).cuda(),
                       lr=0.0, want_grad=True)
     tr.close()
-    lo, go = mlp.loss_and_grad(th, X, R, bf16_emulation=True)
-    assert loss == pytest.approx(lo, rel=1e-3)
+    lo, go = mlp.loss_and_grad(th, X, R, bf16_emulation=True, bf16_backward=True)
+    assert loss == pytest.approx(lo, rel=1e-6)
     g = g.astype(np.float64)
-    cos = g @ go / (np.linalg.norm(g) * np.linalg.norm(go))
-    assert cos >= 0.999, cos
-    assert np.linalg.norm(g - go) <= 5e-2 * np.linalg.norm(go)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
     for name, a, b in _blocks():
-        assert np.linalg.norm(g[a:b] - go[a:b]) <= 5e-2 * np.linalg.norm(go[a:b]) + 1e-7, name
+        assert np.linalg.norm(g[a:b] - go[a:b]) <= 1e-3 * np.linalg.norm(go[a:b]) + 1e-9, name
 
 
 def test_adam_first_step_and_determinism():
@@ -106,8 +120,8 @@ def test_lattice_forward_on_tcgen05_matches_oracle(J, P):
     """The filter's fused form: input rows gathered from lattice states on the
     device, the network on tcgen05 with TMEM accumulators (a ragged last tile
     of 128 rows), against the FP64 oracle's rows (oracle/mlp.patch_rows) and
-    BF16-emulating forward; tolerance as for the forward above (the GELU's erf
-    approximation, |error| <= 1.5e-7, is far below the BF16 rounding)."""
+    BF16-emulating forward; tolerance as for the forward above (the bound
+    allows the GELU's erf approximation, |error| <= 1.5e-7)."""
     from paper_1407_8071_gb300 import workloads as W
     th = _theta(9)
     nodes = W.fhn_obs_nodes(J, 4 if J > 2 else 1)
@@ -121,10 +135,8 @@ def test_lattice_forward_on_tcgen05_matches_oracle(J, P):
     got = d_out.cpu().numpy().astype(np.float64)
     rows = np.concatenate([mlp.patch_rows(x[p].astype(np.float64), J, nodes, y.astype(np.float64)) for p in range(P)])
     ref, _ = mlp.forward(th, rows, bf16_emulation=True)
-    scale = np.sqrt(np.mean(ref ** 2, axis=0, keepdims=True))
-    err = np.abs(got - ref) / (np.abs(ref) + scale)
     assert np.all(np.isfinite(got))
-    assert err.max() <= 2e-2, (err.max(), np.unravel_index(np.argmax(err), err.shape))
+    check_forward(got, ref, _mlp_bounds.forward_bound(th, rows), _mlp_bounds.hidden_sizes(th, rows))
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 1000, 4096, 70001])

@@ -8,6 +8,10 @@
 * A non-trivial proposal keeps the posterior: GPU ensemble means agree with the
   FP64 oracle's proposal filter over many independent filters (both use the
   transition's normals and BF16 network weights).
+* Element-wise parity of one proposal interval from identical states
+  (oracle.propagate_proposal): with exact network outputs (W3 = 0) to FP32
+  rounding; with a non-trivial network within the bounds derived from the
+  network-output bound (tests/_mlp_bounds.py).
 * Recorded tuples: the standardised residuals of the transition's own step
   are the normals it drew (mean 0, variance 1), inputs end with y.
 * Training on recorded tuples lowers the held-out loss, and the trained
@@ -19,6 +23,7 @@ import numpy as np
 import pytest
 
 import oracle
+import _mlp_bounds
 from oracle import mlp
 from paper_1407_8071_gb300 import pf, proposal, workloads as W
 
@@ -136,30 +141,143 @@ def test_trained_network_gains_where_the_transition_noise_sits_in_the_last_sub_s
     (K = 1) all the transition noise is in the step the network controls, and
     an observation sharper than that noise makes the bootstrap weights uneven.
     The trained proposal moves the observed nodes toward y: the mean ESS
-    rises, and the posterior means agree with the bootstrap filter's."""
+    rises, and the posterior means agree with the bootstrap filter's.  The
+    posterior comparison runs with many particles per filter (N = 2048): each
+    filter's estimate carries a bias of order 1/N (Theorem 1) that differs
+    between the two proposals, and at small N it is not small against the
+    standard error of a mean over many filters."""
     spec = W.fhn_lattice(J=8, K=1, sigma=0.05, sigma_obs=0.02)
     T = 24
     _, y_train = oracle.simulate(spec, T, W.SEED_FHN_OBS, record=1)
     _, y_eval = oracle.simulate(spec, T, W.SEED_FHN_OBS, record=2)
     X, R, n = proposal.collect_tuples(spec, 64, 256, y_train.astype(np.float32), seed=6, capacity=400_000, stride=2)
     theta, _ = proposal.train(proposal.initial_theta(12), X, R, epochs=4, batch=4096, lr=2e-3)
-    M, N, skip, node = 256, 128, 4, 0
-    ess, est = {}, {}
-    for name, th in (("bootstrap", None), ("learned", theta)):
-        with pf.EnsembleFilter(spec, M, N, 61) as f:
-            if th is not None:
-                f.set_proposal(th, 0.1)
-            e, m = [], []
-            for t in range(T):
-                f.step(y_eval[t].astype(np.float32))
-                e.append(f.estimate(pf.PF_STAT_ESS, per_filter=True))
-                m.append(f.estimate(pf.PF_STAT_MEAN, var=node, per_filter=True))
-        ess[name], est[name] = np.array(e)[skip:], np.array(m)[skip:]
+    skip, node = 4, 0
+
+    def run(M, N, seed):
+        ess, est = {}, {}
+        for name, th in (("bootstrap", None), ("learned", theta)):
+            with pf.EnsembleFilter(spec, M, N, seed) as f:
+                if th is not None:
+                    f.set_proposal(th, 0.1)
+                e, m = [], []
+                for t in range(T):
+                    f.step(y_eval[t].astype(np.float32))
+                    e.append(f.estimate(pf.PF_STAT_ESS, per_filter=True))
+                    m.append(f.estimate(pf.PF_STAT_MEAN, var=node, per_filter=True))
+            ess[name], est[name] = np.array(e)[skip:], np.array(m)[skip:]
+        return ess, est
+
+    M, N = 256, 128
+    ess, _ = run(M, N, 61)
     gain = ess["learned"].mean() / ess["bootstrap"].mean()
     print(f"mean ESS/N bootstrap {ess['bootstrap'].mean() / N:.3f}, learned {ess['learned'].mean() / N:.3f}, "
           f"gain {gain:.2f}")
     assert gain > 1.15, gain
+    M, N = 48, 2048
+    _, est = run(M, N, 62)
     for t in range(0, T - skip, 5):
         a, b = est["bootstrap"][t], est["learned"][t]
         se = math.sqrt(a.var() / M + b.var() / M)
         assert abs(a.mean() - b.mean()) < 4.5 * se, (t, a.mean(), b.mean(), se)
+
+
+def _one_proposal_interval(J, K, theta, M, N, seed=77):
+    """From identical FP32 states, one observation interval with the proposal on
+    (no fallback): the GPU's proposed states and log-weights, and the oracle's
+    proposal step from the same states."""
+    spec = W.fhn_lattice(J=J, K=K)
+    _, y = oracle.simulate(spec, 3, W.SEED_FHN_OBS)
+    y32 = y.astype(np.float32)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.step(y32[0])
+        x0 = f.get_state()
+        f.set_proposal(theta, 0.0)
+        f.propagate(y32[1])
+        xg = f.get_state().astype(np.float64)
+        lg = f.get_logw().astype(np.float64)
+    pid, fid = np.tile(np.arange(N), M), np.repeat(np.arange(M), N)
+    y1 = y32[1].astype(np.float64)
+    xo, xb, lw, o, zm, rows = oracle.propagate_proposal(spec, theta, x0.astype(np.float64), pid, fid, 2, seed, y1)
+    lo = oracle.loglik(spec, xo, y1) + lw
+    return spec, x0, xg, lg, xo, lo, o, zm, rows, y1
+
+
+def _observed_mask(spec):
+    nn = spec.J * spec.J
+    obs = np.zeros(spec.dx, dtype=bool)
+    obs[np.asarray(spec.obs_idx)] = True
+    obs[nn + np.asarray(spec.obs_idx)] = True
+    return obs
+
+
+def _rel(xg, xo):
+    rms = np.sqrt(np.mean(xo ** 2, axis=0, keepdims=True))
+    return np.abs(xg - xo) / np.maximum(np.abs(xo), rms)
+
+
+@pytest.mark.parametrize("J,K,N", [(8, 20, 64), (8, 1, 64), (40, 20, 16)])
+def test_proposal_step_with_exact_network_outputs(J, K, N):
+    """A network whose outputs are its output biases (W3 = 0): both sides then
+    have the same o exactly, and the proposal step -- residual mean and scale,
+    the draw with the transition's normal, log g + sum (log p - log q) -- differs
+    only by FP32 rounding: states within 1e-5 relative everywhere, log-weights
+    within the FP32 accumulation bound of their terms."""
+    th = mlp.unpack(mlp.init_params(1, out_scale=0.0))
+    th["b3"] = np.array([0.35, -0.25, 0.4, -0.3])
+    theta = mlp.pack(th).astype(np.float32).astype(np.float64)
+    spec, x0, xg, lg, xo, lo, o, zm, rows, y1 = _one_proposal_interval(J, K, theta, 2, N)
+    assert np.all(o == th["b3"].astype(np.float32).astype(np.float64))
+    assert np.max(_rel(xg, xo)) <= 1e-5
+    # the proposal moved every observed component away from the transition's candidate
+    xb = oracle.propagate(spec, x0.astype(np.float64), np.tile(np.arange(N), 2), np.repeat(np.arange(2), N), 2, 77)
+    assert np.min(np.abs(xo - xb)[:, _observed_mask(spec)]) > 0
+    # log-weights: the oracle's log g at the GPU's states plus its own sum of
+    # log p - log q; they differ by the FP32 accumulation of the 3 dy terms and
+    # the rounding of r = (x' - m) / h if the GPU forms it from x' and m
+    h = spec.sigma_dyn * np.sqrt(spec.dt)
+    s_ = np.clip(o[..., 2:], -3.0, 3.0)
+    r = o[..., :2] + np.exp(s_) * zm[..., :2]
+    q = s_ + zm[..., :2] ** 2 / 2.0 - r ** 2 / 2.0
+    lw = q.sum(axis=(1, 2))
+    lgx = oracle.loglik(spec, xg, y1)
+    nn, nodes = spec.J * spec.J, np.asarray(spec.obs_idx)
+    xp = np.stack([xg[:, nodes], xg[:, nn + nodes]], axis=2)
+    canc = 2.0 ** -22 * (np.abs(zm[..., 2:]) + np.abs(xp)) / h
+    tol = (_mlp_bounds.gamma(3 * spec.dy) * (np.abs(lgx) + np.abs(q).sum(axis=(1, 2)))
+           + (np.abs(r) * canc + canc ** 2).sum(axis=(1, 2)) + 1e-6)
+    assert np.all(np.abs(lg - (lgx + lw)) <= tol), np.max(np.abs(lg - (lgx + lw)) / tol)
+    # and the oracle's own weights agree with that reconstruction of them
+    assert np.allclose(lo, oracle.loglik(spec, xo, y1) + lw, rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("J,K,N", [(8, 20, 64), (8, 1, 64), (40, 20, 16)])
+def test_proposal_step_matches_oracle_elementwise(J, K, N):
+    """A non-trivial network (non-zero W3 and b3): unobserved components within
+    1e-5 relative; observed ones within the bound the network-output bound
+    implies (tests/_mlp_bounds.step_bounds), and at most 2 % of them beyond the
+    bound without rounding flips; log-weights within their derived bound."""
+    p = mlp.unpack(mlp.init_params(5, out_scale=0.3))
+    rng = np.random.default_rng(105)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(0.0, 0.1, p[k].shape)
+    theta = mlp.pack(p).astype(np.float32).astype(np.float64)
+    spec, x0, xg, lg, xo, lo, o, zm, rows, y1 = _one_proposal_interval(J, K, theta, 2, N)
+    assert np.abs(o[..., :2]).max() > 0.05 and np.abs(o[..., 2:]).max() > 0.05
+    obs = _observed_mask(spec)
+    assert np.max(_rel(xg, xo)[:, ~obs]) <= 1e-5
+    # network inputs: the states after K - 1 sub-steps, known to 1e-5 of their size on the GPU
+    if K > 1:
+        rms_v = np.sqrt(np.mean(rows[..., :25] ** 2))
+        rms_w = np.sqrt(np.mean(rows[..., 25:50] ** 2))
+        x_tol = np.concatenate([1e-5 * np.maximum(np.abs(rows[..., :25]), rms_v),
+                                1e-5 * np.maximum(np.abs(rows[..., 25:50]), rms_w),
+                                np.zeros(rows.shape[:2] + (1,))], axis=2).reshape(-1, 51)
+    else:
+        x_tol = 0.0
+    dx, dx_nf, dl = _mlp_bounds.step_bounds(spec, theta, o, zm, rows, xo, y1, x_tol)
+    nn, nodes = spec.J * spec.J, np.asarray(spec.obs_idx)
+    d = np.stack([np.abs(xg - xo)[:, nodes], np.abs(xg - xo)[:, nn + nodes]], axis=2)
+    assert np.all(d <= dx + 1e-12), np.max(d / dx)
+    assert np.mean(d > dx_nf + 1e-12) <= 0.02, np.mean(d > dx_nf)
+    assert np.all(np.abs(lg - lo) <= dl + 1e-9), np.max(np.abs(lg - lo) / dl)
