@@ -517,61 +517,36 @@ def run_study(args):
     return 0
 
 
-# ---------------------------------------------------------------------------
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="lorenz-sweep", choices=list(WORKLOAD_TEXT))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--study", choices=["mse"], default=None,
-                    help="accuracy study instead of the throughput bench (one JSON line)")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.study:
-        return run_study(args)
-
+def measure(name, steps, warmup, rank, world, barrier, cpu_seconds):
+    """One workload: W untimed steps, K timed steps (device-resident inputs), the
+    same K through host buffers, the dominant kernel timed live, the oracle
+    timed on a bounded sample (cpu_seconds > 0, rank 0, N = 1).  Returns the
+    workload's JSON object."""
     import torch
     import torch.distributed as dist
-    from paper_1407_8071_gb300 import pf
-
-    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
-    torch.cuda.set_device(local)
-    barrier = None
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        barrier = dist.barrier
-    pf.lib()
-
-    wl = Workload(args.workload, seed_base=1000 * rank + 1)
-    for _ in range(args.warmup):
+    wl = Workload(name, seed_base=1000 * rank + 1)
+    for _ in range(warmup):
         wl.step_device()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    elapsed = time_region(torch, wl, wl.step_device, args.steps, barrier)
+    elapsed = time_region(torch, wl, wl.step_device, steps, barrier)
     clocks = sampler.stop()
     if world > 1:
         t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
-    value = world * wl.particle_steps_per_step * args.steps / elapsed
+    value = world * wl.particle_steps_per_step * steps / elapsed
 
     # end to end through the public API with host buffers
     for _ in range(2):
         wl.step_host()
-    e2e_elapsed = time_region(torch, wl, wl.step_host, args.steps, barrier)
+    e2e_elapsed = time_region(torch, wl, wl.step_host, steps, barrier)
     if world > 1:
         t = torch.tensor([e2e_elapsed], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_elapsed = float(t.item())
-    e2e_value = world * wl.particle_steps_per_step * args.steps / e2e_elapsed
+    e2e_value = world * wl.particle_steps_per_step * steps / e2e_elapsed
     nf = len(wl.filters)
 
     # the dominant kernel, timed live per launch
@@ -615,11 +590,11 @@ def main():
                     "ops_per_node_step": FHN_OPS_PER_NODE_STEP, "avg_launch_s": t_prop}
 
     line = {
-        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": elapsed / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {
-            "workload": WORKLOAD_TEXT[args.workload],
+            "workload": WORKLOAD_TEXT[name],
             "rows": ([{"M": M, "N": N} for M, N in wl.rows] if wl.N_list is None else
                      [{"M": len(wl.N_list), "N_min": int(wl.N_list.min()), "N_max": int(wl.N_list.max()),
                        "N_total": int(wl.N_list.sum())}]),
@@ -629,25 +604,106 @@ def main():
                                                          "nodes_per_thread": wl.choice[2]},
             "precision": "FP32 state and propagation; FP64 normaliser, prefix sum and M-average",
             "l2": ("working set of the seven configurations (~340 MB: state 2 x 88 MB, prefix 59 MB, ...) exceeds "
-                   "the 129 MB L2") if args.workload.startswith("lorenz-sweep")
+                   "the 129 MB L2") if name.startswith("lorenz-sweep")
             else f"state {wl.particles * wl.spec.dx * 4 / 1e6:.0f} MB per buffer, larger than L2",
         },
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "particle-steps/s", "h2d_bytes_per_step": wl.obs_bytes(),
                 "d2h_bytes_per_step": nf * 8},
-        "gpu_launches": args.steps * wl.launches_per_step(),
+        "gpu_launches": steps * wl.launches_per_step(),
         "roofline": roofline,
         "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res},
         "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src) if t_res > 0 else None,
     }
     theta = wl.theta
     if wl.name == "ragged":
-        line["separate_contexts"] = separate_contexts(torch, wl, max(1, args.steps // 4))
+        line["separate_contexts"] = separate_contexts(torch, wl, max(1, steps // 4))
     wl.close()
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, desc = oracle_sample(args.workload, args.cpu_seconds, theta)
+    if rank == 0 and world == 1 and cpu_seconds > 0:
+        v, cores, desc = oracle_sample(name, cpu_seconds, theta)
         line["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": desc}
+    return line
+
+
+# The other workloads of the default run: (timed steps, oracle seconds).  Each
+# is a separate context, measured the way the headline is.
+EXTRA_WORKLOADS = {"fhn": (20, 3.0), "fhn-learned": (20, 3.0), "ragged": (12, 3.0), "fhn-paper": (100, 3.0)}
+
+
+def extra_workloads(rank, world, barrier, args):
+    out = {}
+    for name, (steps, cpu_s) in EXTRA_WORKLOADS.items():
+        out[name] = measure(name, steps, 3, rank, world, barrier, 0.0 if args.no_cpu_baseline else cpu_s)
+    return out
+
+
+def time_to_mse_block():
+    """A short seeded study on the 40 x 40 lattice at M = 32 (the learned-proposal
+    workload): MSE of the averaged v-estimates against a large-ensemble reference
+    for the plain, learned-proposal and auxiliary ensembles at N = 256, 512, 1024,
+    and the wall time each needs to reach the plain ensemble's MSE at N = 1024
+    (log-log interpolation between the runs that bracket it)."""
+    from paper_1407_8071_gb300 import pf, proposal, study
+    t0 = time.perf_counter()
+    spec = W.fhn_lattice()
+    train_record = pf.pf_simulate(spec, 20, W.SEED_FHN_OBS, record=1)[1]  # not the scored record
+    theta = proposal.trained_theta(spec, train_record, seed=77)
+    r = study.lattice_time_to_mse(theta, Ns=(256, 512, 1024), R=4, T=30, M_ref=512, N_ref=1024, ref_seeds=(951,),
+                                  skip=5, methods=("plain", "learned", "auxiliary"))
+    plain = r["plain_s_at_target"]
+    return {
+        "workload": "fhn 40x40 lattice, M=32 ensembles of N in {256, 512, 1024}; R=4 ensembles per point, T=30 "
+                    "observations (the first 5 not scored), reference: 512 x 1024 bootstrap ensemble",
+        "target_mse": r["target_mse"], "plain_s": plain,
+        "learned_s": r["learned_s_at_target"], "auxiliary_s": r["auxiliary_s_at_target"],
+        "learned_vs_plain": (r["learned_s_at_target"] / plain) if r["learned_s_at_target"] else None,
+        "auxiliary_vs_plain": (r["auxiliary_s_at_target"] / plain) if r["auxiliary_s_at_target"] else None,
+        "rows": {k: [{kk: row[kk] for kk in ("N", "mse", "s_per_run", "mean_ess_frac")} for row in v]
+                 for k, v in r["rows"].items()},
+        "wall_s": time.perf_counter() - t0,
+    }
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="lorenz-sweep", choices=list(WORKLOAD_TEXT))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the headline workload only (no other workloads, no time-to-MSE study)")
+    ap.add_argument("--study", choices=["mse"], default=None,
+                    help="accuracy study instead of the throughput bench (one JSON line)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.study:
+        return run_study(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1407_8071_gb300 import pf
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    barrier = None
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        barrier = dist.barrier
+    pf.lib()
+
+    line = measure(args.workload, args.steps, args.warmup, rank, world, barrier,
+                   0.0 if args.no_cpu_baseline else args.cpu_seconds)
+    if args.workload == "lorenz-sweep" and world == 1 and not args.no_extras:
+        line["workloads"] = extra_workloads(rank, world, barrier, args)
+        line["time_to_mse"] = time_to_mse_block()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -147,8 +147,11 @@ def ensemble_reference(spec: W.ModelSpec, M: int, N: int, seeds, d_y):
     return acc / len(seeds)
 
 
+ALL_METHODS = ("plain", "learned", "auxiliary", "adaptive", "centralised")
+
+
 def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8, T: int = 40, M_ref: int = 1024,
-                        N_ref: int = 1024, ref_seeds=(951, 952), skip: int = 5, log=None):
+                        N_ref: int = 1024, ref_seeds=(951, 952), skip: int = 5, log=None, methods=ALL_METHODS):
     """Plain bootstrap vs learned proposal on the 40 x 40 lattice: MSE of the
     averaged v-estimates (every node) against a reference posterior, wall time
     per run, and the wall time the learned form needs to reach the plain
@@ -169,6 +172,8 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
     for name, th, m_run, aux, tau in (("plain", None, M, False, -1.0), ("learned", theta, M, False, -1.0),
                                       ("auxiliary", None, M, True, -1.0), ("adaptive", None, M, False, 0.5),
                                       ("centralised", None, 1, False, -1.0)):
+        if name not in methods:
+            continue
         rows = []
         for N in Ns:
             n_run = N * M // m_run
@@ -196,10 +201,7 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
     return {"workload": "fhn 40x40, M=32", "R": R, "T": T, "M_ref": M_ref, "N_ref": N_ref,
             "ref_seeds": len(ref_seeds), "skip": skip, "rows": out, "target_mse": target,
             "plain_s_at_target": out["plain"][-1]["s_per_run"],
-            "learned_s_at_target": time_at(out["learned"], target),
-            "auxiliary_s_at_target": time_at(out["auxiliary"], target),
-            "adaptive_s_at_target": time_at(out["adaptive"], target),
-            "centralised_s_at_target": time_at(out["centralised"], target)}
+            **{f"{k}_s_at_target": time_at(out[k], target) for k in out if k != "plain"}}
 
 
 def paper_lattice_mse(Ns=(100, 500, 1000, 2000, 5000), M: int = 10, records=(0, 1, 2, 3), T: int = 200,
