@@ -505,6 +505,17 @@ def run_study(args):
     pf.lib()
     log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
     t0 = time.perf_counter()
+    if args.study == "time-error":
+        # Sec. 3.4's time-error index (wall time x MSE) of every split of the Lorenz 2^20 budget, and of
+        # the ragged batch in one context against 256 separate contexts
+        lor = study.lorenz_sweep_mse(log=log)
+        spec = W.fhn_lattice(J=W.RAGGED["J"])
+        train_record = pf.pf_simulate(spec, 20, W.SEED_RAGGED, record=1 << 20)[1]
+        theta = proposal.trained_theta(spec, train_record, seed=77)
+        rag = study.ragged_time_error(theta, log=log)
+        print(json.dumps({"study": "time-error", "data": "synthetic", "lorenz_sweep": lor, "ragged": rag,
+                          "wall_s": time.perf_counter() - t0}))
+        return 0
     lor = study.lorenz_sweep_mse(log=log)
     spec = W.fhn_lattice()
     train_record = pf.pf_simulate(spec, 20, W.SEED_FHN_OBS, record=1)[1]  # not the scored record
@@ -677,7 +688,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="the headline workload only (no other workloads, no time-to-MSE study)")
-    ap.add_argument("--study", choices=["mse"], default=None,
+    ap.add_argument("--study", choices=["mse", "time-error"], default=None,
                     help="accuracy study instead of the throughput bench (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

@@ -273,8 +273,9 @@ PF_API pf_status pf_set_resampling(pf_ctx *ctx, double ess_threshold);
  * nodes_per_thread 2, 4 or 8 for the lattice kernels (4 and 8 where J
  * is divisible by them),
  * particles_per_cta >= 1 for the lattice (clamped to what fits in 1024
- * threads), resample_threads 64, 128 or 256 (at least a quarter of the
- * largest tile, min(N_m, 1024)).  Results do not depend on the schedule
+ * threads), resample_threads 64, 128 or 256 (at least an eighth of the
+ * largest tile, min(N_m, 1024): a tile CTA takes 4 particles per thread, or 8
+ * where 4 do not cover the tile).  Results do not depend on the schedule
  * (particles and ancestors bit for bit; FP64 estimates to summation order).
  * Synchronises.  Errors: PF_EINVAL, PF_ESTATE. */
 PF_API pf_status pf_set_schedule(pf_ctx *ctx, int32_t nodes_per_thread, int32_t particles_per_cta,

@@ -809,19 +809,20 @@ __global__ void __launch_bounds__(kResampleThreads) k_refresh_max(const TileDesc
 }
 
 // Pass 2: the filter maximum, then per tile sum w and sum w^2 (compensated
-// FP32 pairs, FP64 per tile) and the exact sum of q = floor(w 2^shift); stores
-// each q for the scan and clears the ancestor markers.
-template <bool Direct>
+// FP32 pairs, FP64 per tile) and the exact sum of q = floor(w 2^shift);
+// stores each q for the scan and clears the ancestor markers.  (Recomputing q
+// in the scan instead, and clearing the markers in the ancestor kernel, was
+// measured slower: 175 against 136 us for the Lorenz sweep's resampling.)
+// Each thread holds IT particles of the tile (strided: coalesced loads).
+template <bool Direct, int IT>
 __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
 {
     __shared__ double shd[kResampleThreads * 2 + 2];
     __shared__ uint64_t shu[kWarps];
-    __shared__ float shf[kWarps];
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = filter_of(td);
     float mx = 0.0f;
     bool degenerate = false;
-    (void)shf;
     if (!Direct) {
         const float m = float_from_order_key(a.fmax_key[td.m]);
         degenerate = !(m > -INFINITY);
@@ -842,15 +843,14 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
         block_sum_dd<2>(s, shd);
     } else {
         FF f[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-        // every thread holds at most kItems particles of the tile: load them all first
-        float l[kItems];
+        float l[IT];
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             const int j = threadIdx.x + r * (int)blockDim.x;
             l[r] = j < td.len ? a.logw[td.gstart + j] : -INFINITY;
         }
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             const int j = threadIdx.x + r * (int)blockDim.x;
             if (j < td.len) {
                 const float w = weight_f32(l[r], mx, degenerate);
@@ -881,11 +881,13 @@ __global__ void __launch_bounds__(kResampleThreads) k_weights(ResampleArgs a)
     }
 }
 
-// Pass 3: the exact prefix C of q (tile offset + block scan), the counts
+// Pass 3: the exact prefix C of the quantised weights q (tile offset + block
+// scan), the counts
 // #{i : t_i < C_k}, and the start markers B[lo_k] = k of every particle with
 // offspring.  The first tile of each filter also writes the filter's log Z,
-// ESS and log G (eq. eqGtN) and its (C_tot, U).
-template <bool Direct, bool Adaptive = false>
+// ESS and log G (eq. eqGtN) and its (C_tot, U).  Each thread holds IT
+// consecutive particles of the tile.
+template <bool Direct, bool Adaptive, int IT>
 __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs a)
 {
     __shared__ double shd[kResampleThreads * 2 + 2];
@@ -920,6 +922,12 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
             return;
         }
     }
+    __shared__ uint32_t shU;
+    const int32_t t = a.d_t ? *a.d_t + 1 : 0;
+    if (threadIdx.x == 0) {  // the filter's uniform, once per CTA (published by the barriers below)
+        if (Direct) shU = (uint32_t)fmin(floor(a.u_direct[td.m] * 4294967296.0), 4294967295.0);
+        else shU = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
+    }
     uint64_t q_all = 0, q_before = 0;
     for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x) {
         const uint64_t v = a.tile_q[fd.tile_begin + j];
@@ -928,10 +936,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
     }
     block_sum_u64x2(q_all, q_before, shu);
     const uint64_t Ctot = q_all, Cbefore = q_before;
-    const int32_t t = a.d_t ? *a.d_t + 1 : 0;
-    uint32_t U;
-    if (Direct) U = (uint32_t)fmin(floor(a.u_direct[td.m] * 4294967296.0), 4294967295.0);
-    else U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
+    const uint32_t U = shU;
     const Grid g = make_grid(Ctot, U, (int64_t)fd.N);
 
     if (ti == 0) {  // filter scalars (FP64)
@@ -956,35 +961,35 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
             }
             a.fint[(int64_t)td.m * 2] = Ctot;
             a.fint[(int64_t)td.m * 2 + 1] = U;
-            if (!Direct) a.fmax_key[td.m] = kNegInfKey;  // k_weights has consumed it
         }
     }
-    // blocked items: thread j owns tile positions [j * kItems, (j + 1) * kItems)
-    const int j0 = threadIdx.x * kItems;
-    uint64_t q[kItems];
-    if (!Direct && j0 + kItems <= td.len && ((td.gstart + j0) & 1) == 0) {  // q from k_weights, 16-byte loads
-        const ulonglong2 q01 = *reinterpret_cast<const ulonglong2 *>(a.C + td.gstart + j0);
-        const ulonglong2 q23 = *reinterpret_cast<const ulonglong2 *>(a.C + td.gstart + j0 + 2);
-        q[0] = q01.x, q[1] = q01.y, q[2] = q23.x, q[3] = q23.y;
+    // blocked items: thread j owns tile positions [j IT, (j + 1) IT)
+    const int j0 = threadIdx.x * IT;
+    uint64_t q[IT];
+    if (Direct) {
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            const int j = j0 + r;
+            q[r] = j < td.len ? quant_f64(a.w_direct[td.gstart + j], fd.shift) : 0;
+        }
+    } else if (j0 + IT <= td.len && ((td.gstart + j0) & 1) == 0) {  // q from k_weights, 16-byte loads
+#pragma unroll
+        for (int r = 0; r < IT; r += 2) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(a.C + td.gstart + j0 + r);
+            q[r] = v.x, q[r + 1] = v.y;
+        }
     } else {
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
-            const int j = j0 + r;
-            q[r] = 0;
-            if (j < td.len) {
-                const int64_t p = td.gstart + j;
-                q[r] = Direct ? quant_f64(a.w_direct[p], fd.shift) : a.C[p];
-            }
-        }
+        for (int r = 0; r < IT; ++r) q[r] = j0 + r < td.len ? a.C[td.gstart + j0 + r] : 0;
     }
     uint64_t tsum = 0;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) tsum += q[r];
+    for (int r = 0; r < IT; ++r) tsum += q[r];
     // the prefix C_k stays in registers: nothing after the counts reads it
     uint64_t Cprev = Cbefore + block_exscan_u64(tsum, shu + 2 * kWarps);  // C_{k-1} before my first item
     int64_t cnt_prev = count_below(Cprev, g);
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < IT; ++r) {
         const int j = j0 + r;
         if (j >= td.len) break;
         const uint64_t Ck = Cprev + q[r];
@@ -1006,61 +1011,72 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
 // a_i = max(first ancestor of the tile, max of the markers B[i0..i]); the
 // first ancestor comes from the scan (the particle whose offspring range
 // holds the tile's first output).
-__device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const TileDesc &td, const FilterDesc &fd,
-                                               int32_t (&anc)[kItems], int *shi)
+template <int IT>
+__device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const TileDesc &td, int32_t (&anc)[IT], int *shi)
 {
-    (void)fd;
+    static_assert(IT % 4 == 0, "whole int4 groups of markers per thread");
     const int32_t a0 = a.tile_anc0[blockIdx.x];
-    const int j0 = threadIdx.x * kItems;
-    static_assert(kItems == 4, "one int4 of markers per thread");
-    int b[kItems];
-    if (j0 + kItems <= td.len && ((td.gstart + j0) & 3) == 0) {
-        const int4 v = *reinterpret_cast<const int4 *>(a.B + td.gstart + j0);
-        b[0] = v.x, b[1] = v.y, b[2] = v.z, b[3] = v.w;
+    const int j0 = threadIdx.x * IT;
+    int b[IT];
+    const int32_t *B = a.B + td.gstart + j0;
+    if (j0 + IT <= td.len && ((td.gstart + j0) & 3) == 0) {
+#pragma unroll
+        for (int r = 0; r < IT; r += 4) {
+            const int4 v = *reinterpret_cast<const int4 *>(B + r);
+            b[r] = v.x, b[r + 1] = v.y, b[r + 2] = v.z, b[r + 3] = v.w;
+        }
     } else {
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) b[r] = (j0 + r < td.len) ? a.B[td.gstart + j0 + r] : -1;
+        for (int r = 0; r < IT; ++r) {
+            b[r] = -1;
+            if (j0 + r < td.len) b[r] = B[r];
+        }
     }
     int tmax = -1;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) tmax = max(tmax, b[r]);
+    for (int r = 0; r < IT; ++r) tmax = max(tmax, b[r]);
     int run = max(a0, block_exscan_max_i(tmax, shi));
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < IT; ++r) {
         run = max(run, b[r]);
         anc[r] = run;
     }
 }
 
-// A thread's kItems consecutive outputs p0 .. p0 + kItems - 1 (the first
-// `left` of them exist): their ancestor indices, the gathered SoA state
+// A thread's IT consecutive outputs p0 .. p0 + IT - 1 (the first `left` of
+// them exist): their ancestor indices, the gathered SoA state
 // x_out[v][p] = x_in[v][off + anc] and the running compensated sums of what
 // was gathered, item by item.  Whole aligned groups store as int4 / float4.
-template <int D>
+template <int D, int IT>
 __device__ __forceinline__ void gather_items(int32_t *anc_out, int64_t off, int64_t p0, int left,
-                                             const int32_t (&anc)[kItems], const float *__restrict__ x_in,
+                                             const int32_t (&anc)[IT], const float *__restrict__ x_in,
                                              float *__restrict__ x_out, int64_t P, FF (&f)[D])
 {
-    static_assert(kItems == 4, "one int4 / float4 per thread and variable");
+    static_assert(IT % 4 == 0, "whole int4 / float4 groups per thread and variable");
 #pragma unroll
     for (int v = 0; v < D; ++v) f[v] = FF{0.0f, 0.0f};
-    if (left >= kItems && ((p0 | P) & 3) == 0) {
-        *reinterpret_cast<int4 *>(anc_out + p0) = make_int4(anc[0], anc[1], anc[2], anc[3]);
+    if (left >= IT && ((p0 | P) & 3) == 0) {
+#pragma unroll
+        for (int r = 0; r < IT; r += 4)
+            *reinterpret_cast<int4 *>(anc_out + p0 + r) = make_int4(anc[r], anc[r + 1], anc[r + 2], anc[r + 3]);
 #pragma unroll
         for (int v = 0; v < D; ++v) {
             const float *xi = x_in + v * P + off;
-            float4 g;
-            g.x = xi[anc[0]];
-            g.y = xi[anc[1]];
-            g.z = xi[anc[2]];
-            g.w = xi[anc[3]];
-            *reinterpret_cast<float4 *>(x_out + v * P + p0) = g;
-            f[v] = ff_add(ff_add(ff_add(ff_add(f[v], g.x), g.y), g.z), g.w);
+#pragma unroll
+            for (int r = 0; r < IT; r += 4) {
+                float4 g;
+                g.x = xi[anc[r]];
+                g.y = xi[anc[r + 1]];
+                g.z = xi[anc[r + 2]];
+                g.w = xi[anc[r + 3]];
+                *reinterpret_cast<float4 *>(x_out + v * P + p0 + r) = g;
+                f[v] = ff_add(ff_add(ff_add(ff_add(f[v], g.x), g.y), g.z), g.w);
+            }
         }
         return;
     }
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < IT; ++r) {
         if (r < left) {
             const int64_t p = p0 + r;
             anc_out[p] = anc[r];
@@ -1075,50 +1091,63 @@ __device__ __forceinline__ void gather_items(int32_t *anc_out, int64_t off, int6
     }
 }
 
-// Small models: ancestors, gather of the SoA state and per-tile sums of every
-// variable of the resampled particles (compensated FP32 pairs, FP64 per tile).
-// The last tile of a filter to finish (atomic completion counter after a
-// memory fence; nothing waits) turns the filter's tile sums into est[m], the
-// per-filter estimates of Definition 1, in a fixed order.
-template <int D>
+// Ancestors, and for the small models (D > 0) the gather of the SoA state
+// and per-tile sums of every variable of the resampled particles (compensated
+// FP32 pairs, FP64 per tile).  The last tile
+// of a filter to finish (atomic completion counter after a memory fence;
+// nothing waits) turns the filter's tile sums into est[m], the per-filter
+// estimates of Definition 1, in a fixed order.  The filter's first tile
+// resets its maximum log-weight key for the next step (every tile of the scan
+// has read it by now).
+template <int D, int IT, bool ResetMax>
 __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleArgs a, const float *__restrict__ x_in,
                                                                       float *__restrict__ x_out, int64_t P,
                                                                       double *tile_est, double *est)
 {
+    constexpr int DS = D > 0 ? D : 1;
     __shared__ int shi[kWarps];
-    __shared__ double shd[kResampleThreads * D + 2 * D * 32];
+    __shared__ double shd[kResampleThreads * DS + 2 * DS * 32];
     __shared__ int last;
     const TileDesc td = a.tiles[blockIdx.x];
     const FilterDesc fd = filter_of(td);
-    int32_t anc[kItems];
-    tile_ancestors(a, td, fd, anc, shi);
-    const int j0 = threadIdx.x * kItems;
-    FF f[D];
-    gather_items<D>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, f);
-    double s[D];
-    block_sum_ff<D>(f, s, shd);
-    if (fd.tile_count == 1) {  // the tile is the filter
-        if (threadIdx.x < D) est[(int64_t)td.m * D + threadIdx.x] = s[threadIdx.x] / (double)fd.N;
+    if (ResetMax && td.lstart == 0 && threadIdx.x == 0) a.fmax_key[td.m] = kNegInfKey;
+    int32_t anc[IT];
+    tile_ancestors<IT>(a, td, anc, shi);
+    const int j0 = threadIdx.x * IT;
+    if constexpr (D == 0) {
+        (void)x_in, (void)x_out, (void)P, (void)tile_est, (void)est, (void)fd;
+#pragma unroll
+        for (int r = 0; r < IT; ++r)
+            if (j0 + r < td.len) a.anc[td.gstart + j0 + r] = anc[r];
         return;
+    } else {
+        FF f[D];
+        gather_items<D, IT>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, f);
+        double s[D];
+        block_sum_ff<D>(f, s, shd);
+        if (fd.tile_count == 1) {  // the tile is the filter
+            if (threadIdx.x < D) est[(int64_t)td.m * D + threadIdx.x] = s[threadIdx.x] / (double)fd.N;
+            return;
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int v = 0; v < D; ++v) tile_est[(int64_t)blockIdx.x * D + v] = s[v];
+            __threadfence();
+            last = (atomicAdd(&a.done[td.m], 1) == fd.tile_count - 1);
+        }
+        __syncthreads();
+        if (!last) return;
+        // the filter's estimate: tiles strided over the threads, then a fixed tree
+        double part[D];
+#pragma unroll
+        for (int v = 0; v < D; ++v) part[v] = 0.0;
+        for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x)
+#pragma unroll
+            for (int v = 0; v < D; ++v) part[v] += __ldcg(&tile_est[(int64_t)(fd.tile_begin + j) * D + v]);
+        block_sum_dd<D>(part, shd);
+        if (threadIdx.x < D) est[(int64_t)td.m * D + threadIdx.x] = part[threadIdx.x] / (double)fd.N;
+        if (threadIdx.x == 0) a.done[td.m] = 0;
     }
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int v = 0; v < D; ++v) tile_est[(int64_t)blockIdx.x * D + v] = s[v];
-        __threadfence();
-        last = (atomicAdd(&a.done[td.m], 1) == fd.tile_count - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    // the filter's estimate: tiles strided over the threads, then a fixed tree
-    double part[D];
-#pragma unroll
-    for (int v = 0; v < D; ++v) part[v] = 0.0;
-    for (int j = threadIdx.x; j < fd.tile_count; j += blockDim.x)
-#pragma unroll
-        for (int v = 0; v < D; ++v) part[v] += __ldcg(&tile_est[(int64_t)(fd.tile_begin + j) * D + v]);
-    block_sum_dd<D>(part, shd);
-    if (threadIdx.x < D) est[(int64_t)td.m * D + threadIdx.x] = part[threadIdx.x] / (double)fd.N;
-    if (threadIdx.x == 0) a.done[td.m] = 0;
 }
 
 // A whole filter of at most kTile particles per CTA: the resampling step of
@@ -1131,8 +1160,8 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
 // ancestor max-scan, then (D > 0) the gather of the SoA state and the
 // per-filter means.  The results are those of the tile chain bit for bit.
 // CTA b handles tile tile0 + b, which must be the filter's only tile.
-template <int D>
-__global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArgs a, int32_t tile0,
+template <int D, int IT>
+__global__ void __launch_bounds__(kTile / IT) k_resample_whole(ResampleArgs a, int32_t tile0,
                                                                      const float *__restrict__ x_in,
                                                                      float *__restrict__ x_out, int64_t P, double *est)
 {
@@ -1152,14 +1181,14 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
     FF f[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     uint64_t qs = 0;
     {
-        float l[kItems];
+        float l[IT];
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             const int j = threadIdx.x + r * (int)blockDim.x;
             l[r] = j < td.len ? a.logw[td.gstart + j] : -INFINITY;
         }
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             const int j = threadIdx.x + r * (int)blockDim.x;
             if (j < td.len) {
                 const float w = weight_f32(l[r], mx, degenerate);
@@ -1195,19 +1224,19 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
     }
 
     // exact prefix (blocked items), counts and start markers
-    const int j0 = threadIdx.x * kItems;
+    const int j0 = threadIdx.x * IT;
     {
-        uint64_t q[kItems];
+        uint64_t q[IT];
         uint64_t tsum = 0;
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             q[r] = j0 + r < td.len ? shq[j0 + r] : 0;
             tsum += q[r];
         }
         uint64_t Cprev = block_exscan_u64(tsum, shu + kWarps);
         int64_t cnt_prev = count_below(Cprev, g);
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             const int j = j0 + r;
             if (j >= td.len) break;
             const uint64_t Ck = Cprev + q[r];
@@ -1222,10 +1251,10 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
     __syncthreads();
 
     // ancestors: running max of the markers (output 0 always has one)
-    int b[kItems];
+    int b[IT];
     int tmax = -1;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < IT; ++r) {
         b[r] = j0 + r < td.len ? shB[j0 + r] : -1;
         tmax = max(tmax, b[r]);
     }
@@ -1233,24 +1262,192 @@ __global__ void __launch_bounds__(kResampleThreads) k_resample_whole(ResampleArg
     if constexpr (D == 0) {
         (void)x_in, (void)x_out, (void)P, (void)est;
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             run = max(run, b[r]);
             if (j0 + r < td.len) a.anc[td.gstart + j0 + r] = run;
         }
     } else {
         constexpr int DD = D;
-        int32_t anc[kItems];
+        int32_t anc[IT];
 #pragma unroll
-        for (int r = 0; r < kItems; ++r) {
+        for (int r = 0; r < IT; ++r) {
             run = max(run, b[r]);
             anc[r] = run;
         }
         FF fx[DD];
-        gather_items<DD>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, fx);
+        gather_items<DD, IT>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, fx);
         double sx[DD];
         static_assert(2 * DD * kResampleThreads * sizeof(float) <= sizeof(shq), "scratch of the state sums");
         block_sum_ff<DD>(fx, sx, reinterpret_cast<float *>(shq), shd);  // q is no longer needed
         if (threadIdx.x < DD) est[(int64_t)td.m * DD + threadIdx.x] = sx[threadIdx.x];  // divided by N later
+    }
+}
+
+// Warp-level forms of the block primitives above (every lane gets the result).
+__device__ __forceinline__ FF warp_sum_ff(FF v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_add(v, FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_exscan_u64(uint64_t v, int lane)
+{
+    uint64_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t n = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += n;
+    }
+    return inc - v;
+}
+
+__device__ __forceinline__ int warp_exscan_max_i(int v, int lane)
+{
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc = max(inc, n);
+    }
+    const int ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    return lane == 0 ? -1 : ex;
+}
+
+// Filters of at most 32 kWarpItems particles: one warp per filter, kWarpFilters
+// filters per CTA, every reduction and scan in warp shuffles (no block
+// barrier).  The same arithmetic as k_resample_whole: FP32 weights, the
+// compensated sums (a lane's items in order, then an xor tree), the exact
+// q = floor(w 2^shift), prefix C_k and counts, the ancestor max-scan, the
+// gather and the sums of the gathered state; the FP64 scalars follow in
+// k_whole_finish.  Warp w of CTA b takes one-tile filter tile0 + 4 b + w.
+constexpr int kWarpItems = 8;
+constexpr int kWarpFilters = 4;
+constexpr int kWarpFilterMax = 32 * kWarpItems;
+
+template <int D>
+__global__ void __launch_bounds__(32 * kWarpFilters) k_resample_warp(ResampleArgs a, int32_t tile0, int32_t n,
+                                                                     const float *__restrict__ x_in,
+                                                                     float *__restrict__ x_out, int64_t P, double *est)
+{
+    constexpr int IT = kWarpItems;
+    __shared__ uint64_t shq_all[kWarpFilters][kWarpFilterMax];
+    __shared__ int32_t shB_all[kWarpFilters][kWarpFilterMax];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int fi = blockIdx.x * kWarpFilters + w;
+    if (fi >= n) return;  // the whole warp leaves together
+    uint64_t *shq = shq_all[w];
+    int32_t *shB = shB_all[w];
+    const TileDesc td = a.tiles[tile0 + fi];
+    const FilterDesc fd = filter_of(td);
+    const float m0 = float_from_order_key(a.fmax_key[td.m]);
+    const bool degenerate = !(m0 > -INFINITY);
+    const float mx = degenerate ? 0.0f : m0;
+
+    // weights, their sums and the quantised weights (strided: coalesced loads)
+    FF f0{0.0f, 0.0f}, f1{0.0f, 0.0f};
+    uint64_t qs = 0;
+    {
+        float l[IT];
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            const int j = lane + 32 * r;
+            l[r] = j < td.len ? a.logw[td.gstart + j] : -INFINITY;
+        }
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            const int j = lane + 32 * r;
+            shB[j] = -1;
+            if (j < td.len) {
+                const float wt = weight_f32(l[r], mx, degenerate);
+                f0 = ff_add(f0, wt);
+                f1 = ff_add(f1, __fmul_rn(wt, wt));
+                const uint64_t qv = quant_f32(wt, fd.shift);
+                qs += qv;
+                shq[j] = qv;
+            }
+        }
+    }
+    f0 = warp_sum_ff(f0);
+    f1 = warp_sum_ff(f1);
+    const uint64_t Ctot = warp_sum_u64(qs);
+    const int32_t t = a.d_t ? *a.d_t + 1 : 0;
+    const uint32_t U = philox4x32_10(make_uint4(0u, (uint32_t)t, (uint32_t)td.m, kStreamResample << 24), a.key).x;
+    const Grid g = make_grid(Ctot, U, (int64_t)fd.N);
+    if (lane == 0) {
+        double *fs = a.fstats + (int64_t)td.m * kFsCount;
+        fs[kFsMax] = (double)mx;
+        fs[kFsDegenerate] = degenerate ? 1.0 : 0.0;
+        if (degenerate) {
+            atomicOr(&a.err[0], kErrDegenerate);
+            atomicCAS(&a.err[1], -1, td.m);
+        }
+        fs[kFsS0] = ff_to_double(f0);
+        fs[kFsS1] = ff_to_double(f1);
+        a.fint[(int64_t)td.m * 2] = Ctot;
+        a.fint[(int64_t)td.m * 2 + 1] = U;
+        a.fmax_key[td.m] = kNegInfKey;
+    }
+    __syncwarp();
+
+    // exact prefix (blocked items), counts and start markers
+    const int j0 = lane * IT;
+    {
+        uint64_t q[IT];
+        uint64_t tsum = 0;
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            q[r] = j0 + r < td.len ? shq[j0 + r] : 0;
+            tsum += q[r];
+        }
+        uint64_t Cprev = warp_exscan_u64(tsum, lane);
+        int64_t cnt_prev = count_below(Cprev, g);
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            const int j = j0 + r;
+            if (j >= td.len) break;
+            const uint64_t Ck = Cprev + q[r];
+            if (q[r] > 0) {
+                const int64_t cnt = count_below(Ck, g);
+                if (cnt > cnt_prev) shB[cnt_prev] = j;
+                cnt_prev = cnt;
+            }
+            Cprev = Ck;
+        }
+    }
+    __syncwarp();
+
+    // ancestors: running max of the markers (output 0 always has one)
+    int b[IT];
+    int tmax = -1;
+#pragma unroll
+    for (int r = 0; r < IT; ++r) {
+        b[r] = j0 + r < td.len ? shB[j0 + r] : -1;
+        tmax = max(tmax, b[r]);
+    }
+    int run = warp_exscan_max_i(tmax, lane);
+    if constexpr (D == 0) {
+        (void)x_in, (void)x_out, (void)P, (void)est;
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            run = max(run, b[r]);
+            if (j0 + r < td.len) a.anc[td.gstart + j0 + r] = run;
+        }
+    } else {
+        int32_t anc[IT];
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            run = max(run, b[r]);
+            anc[r] = run;
+        }
+        FF fx[D];
+        gather_items<D, IT>(a.anc, fd.off, td.gstart + j0, td.len - j0, anc, x_in, x_out, P, fx);
+#pragma unroll
+        for (int v = 0; v < D; ++v) {
+            const FF sv = warp_sum_ff(fx[v]);
+            if (lane == 0) est[(int64_t)td.m * D + v] = ff_to_double(sv);  // divided by N later
+        }
     }
 }
 
@@ -1277,20 +1474,6 @@ __global__ void __launch_bounds__(32) k_whole_finish(const TileDesc *__restrict_
         fs[kFsLogG] = (t == 1 ? 0.0 : fs[kFsLogG]) + logZ - log((double)td.N) + log_const;
     }
     for (int v = 0; v < dx; ++v) est[(int64_t)td.m * dx + v] /= (double)td.N;
-}
-
-// Ancestors only (lattice models and the stateless entry point).
-__global__ void __launch_bounds__(kResampleThreads) k_ancestors(ResampleArgs a)
-{
-    __shared__ int shi[kWarps];
-    const TileDesc td = a.tiles[blockIdx.x];
-    const FilterDesc fd = filter_of(td);
-    int32_t anc[kItems];
-    tile_ancestors(a, td, fd, anc, shi);
-    const int j0 = threadIdx.x * kItems;
-#pragma unroll
-    for (int r = 0; r < kItems; ++r)
-        if (j0 + r < td.len) a.anc[td.gstart + j0 + r] = anc[r];
 }
 
 // Lattice gather: whole particle rows x_out[p] = x_in[off + anc[p]] (float4).
@@ -1909,6 +2092,27 @@ cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The tile chain over the first n tiles: weights -> scan -> ancestors (with the
+// gather and the per-filter means for the small models, D > 0).  Each CTA of
+// c.resample_threads threads covers one tile with 4 particles per thread, or 8
+// where 4 per thread do not cover the longest tile.
+template <int D, bool Adaptive, int IT>
+void tile_chain_it(const Ctx &c, const ResampleArgs &a, int32_t n, const float *xi, float *xo, cudaStream_t s)
+{
+    const int th = c.resample_threads;
+    k_weights<false, IT><<<n, th, 0, s>>>(a);
+    k_scan_scatter<false, Adaptive, IT><<<n, th, 0, s>>>(a);
+    k_ancestors_small<D, IT, true><<<n, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est);
+}
+
+template <int D, bool Adaptive>
+void tile_chain(const Ctx &c, const ResampleArgs &a, int32_t n, const float *xi, float *xo, cudaStream_t s)
+{
+    if (n <= 0) return;
+    if (c.resample_threads * kItems >= c.max_tile_len) tile_chain_it<D, Adaptive, kItems>(c, a, n, xi, xo, s);
+    else tile_chain_it<D, Adaptive, 2 * kItems>(c, a, n, xi, xo, s);
+}
+
 // Adaptive resampling: the weights carried into the next step (0 where the
 // filter resampled, the step's log-weight where it kept its particles; the
 // particles' order is unchanged then, the gather being the identity), and
@@ -1946,9 +2150,7 @@ cudaError_t adaptive_small(const Ctx &c, const ResampleArgs &a, const float *d_o
     k_propagate_small<D, 3><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, x, x, c.P, c.logw, c.fmax_key,
                                                               d_obs, stride, c.d_t, AuxPtrs{c.lw2, nullptr, nullptr,
                                                                                             nullptr});
-    k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
-    k_scan_scatter<false, true><<<c.n_tiles, th, 0, s>>>(a);
-    k_ancestors_small<D><<<c.n_tiles, th, 0, s>>>(a, x, xn, c.P, c.tile_est, c.est);
+    tile_chain<D, true>(c, a, c.n_tiles, x, xn, s);
     k_carry<<<(unsigned)((c.P + 255) / 256), 256, 0, s>>>(c.pfilt, c.fstats, c.logw, c.lw2, c.fmax2, c.P);
     k_weight_stats<D, false><<<c.n_tiles, th, 0, s>>>(c.tiles, c.filt, c.lw2, c.fmax2, xn, c.P, c.tile_sums,
                                                       c.tile_est, c.done, c.fstats, c.est, c.err);
@@ -1971,9 +2173,7 @@ cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t strid
         else
             e = launch_fhn_interval(c, d_obs, stride, x, x, c.mp.K, true, s, c.logw, c.fmax_key, carry, 1);
         if (e != cudaSuccess) return e;
-        k_weights<false><<<c.n_tiles, th, 0, s>>>(a);
-        k_scan_scatter<false, true><<<c.n_tiles, th, 0, s>>>(a);
-        k_ancestors<<<c.n_tiles, th, 0, s>>>(a);
+        tile_chain<0, true>(c, a, c.n_tiles, nullptr, nullptr, s);
         k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(x),
                                                    reinterpret_cast<float4 *>(xn), dx / 4);
         k_carry<<<(unsigned)((c.P + 255) / 256), 256, 0, s>>>(c.pfilt, c.fstats, c.logw, c.lw2, c.fmax2, c.P);
@@ -2003,9 +2203,14 @@ cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t strid
 template <int D>
 void resample_whole(const Ctx &c, const ResampleArgs &a, const float *xi, float *xo, cudaStream_t s)
 {
-    for (int k = 0; k < kWholeClasses; ++k) {
+    {  // class 0: a warp per filter
+        const int32_t b0 = c.whole_bounds[0], n = c.whole_bounds[1] - b0;
+        if (n) k_resample_warp<D><<<(n + kWarpFilters - 1) / kWarpFilters, 32 * kWarpFilters, 0, s>>>(a, b0, n, xi, xo,
+                                                                                                      c.P, c.est);
+    }
+    for (int k = 1; k < kWholeClasses; ++k) {  // class k: a CTA of 32 2^k threads, kWholeItems particles each
         const int32_t b0 = c.whole_bounds[k], n = c.whole_bounds[k + 1] - b0;
-        if (n) k_resample_whole<D><<<n, 32 << k, 0, s>>>(a, b0, xi, xo, c.P, c.est);
+        if (n) k_resample_whole<D, kWholeItems><<<n, 32 << k, 0, s>>>(a, b0, xi, xo, c.P, c.est);
     }
     const int32_t b0 = c.whole_bounds[0], n = c.whole_bounds[kWholeClasses] - b0;
     // one warp per CTA: the FP64 work spreads over every SM's FP64 units
@@ -2039,9 +2244,7 @@ void resample_small(const Ctx &c, const ResampleArgs &a, const float *xi, float 
     const cudaStream_t side = fork_side(c, s);
     resample_whole<D>(c, a, xi, xo, side);
     if (nm) {
-        k_weights<false><<<nm, th, 0, s>>>(a);
-        k_scan_scatter<false><<<nm, th, 0, s>>>(a);
-        k_ancestors_small<D><<<nm, th, 0, s>>>(a, xi, xo, c.P, c.tile_est, c.est);
+        tile_chain<D, false>(c, a, nm, xi, xo, s);
     }
     join_side(c, side, s);
 }
@@ -2053,9 +2256,7 @@ void resample_ancestors(const Ctx &c, const ResampleArgs &a, int th, cudaStream_
     const cudaStream_t side = fork_side(c, s);
     resample_whole<0>(c, a, nullptr, nullptr, side);
     if (nm) {
-        k_weights<false><<<nm, th, 0, s>>>(a);
-        k_scan_scatter<false><<<nm, th, 0, s>>>(a);
-        k_ancestors<<<nm, th, 0, s>>>(a);
+        tile_chain<0, false>(c, a, nm, nullptr, nullptr, s);
     }
     join_side(c, side, s);
 }
@@ -2145,9 +2346,9 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
 cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s)
 {
     (void)M;
-    k_weights<true><<<n_tiles, kResampleThreads, 0, s>>>(a);
-    k_scan_scatter<true><<<n_tiles, kResampleThreads, 0, s>>>(a);
-    k_ancestors<<<n_tiles, kResampleThreads, 0, s>>>(a);
+    k_weights<true, kItems><<<n_tiles, kResampleThreads, 0, s>>>(a);
+    k_scan_scatter<true, false, kItems><<<n_tiles, kResampleThreads, 0, s>>>(a);
+    k_ancestors_small<0, kItems, false><<<n_tiles, kResampleThreads, 0, s>>>(a, nullptr, nullptr, 0, nullptr, nullptr);
     return cudaGetLastError();
 }
 

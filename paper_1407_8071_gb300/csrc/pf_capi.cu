@@ -335,13 +335,13 @@ bool fill_params(const pf_model *model, double dt, const pf_obs_op *obs, const p
 // the sub-tiles (small models) or the tiles (lattice, stateless resampling).
 // With `bounds` (kWholeClasses + 1 entries), the tiles of filters with more
 // than one tile come first (in filter order), then the single tiles of the
-// other filters grouped by size class c (N <= 32 * kItems << c), and
+// other filters grouped by size class c (N <= 32 * kWholeItems << c), and
 // bounds[c] .. bounds[c + 1] are class c's tiles (bounds[0]: the count of the
 // former); a filter's tiles are always consecutive.
 int whole_class(int32_t n)
 {
     int c = 0;
-    while (c + 1 < kWholeClasses && n > (32 * kItems << c)) ++c;
+    while (c + 1 < kWholeClasses && n > (32 * kWholeItems << c)) ++c;
     return c;
 }
 
@@ -545,9 +545,12 @@ pf_status pf_create(const pf_model *model, int32_t M, const int32_t *N, double d
     {
         int max_len = 1;
         for (const TileDesc &td : tiles) max_len = std::max(max_len, td.len);
-        int th = 64;  // threads per tile CTA: enough for kItems particles each, whole warps, 64..256
-        while (th < kResampleThreads && th * kItems < max_len) th *= 2;
+        // threads per tile CTA: whole warps, 64..256, enough for 8 particles each (the tile
+        // kernels take 4 per thread where that covers the longest tile)
+        int th = 64;
+        while (th < kResampleThreads && th * 2 * kItems < max_len) th *= 2;
         c.resample_threads = th;
+        c.max_tile_len = max_len;
     }
     const int dx = mp.dx;
     const int64_t P = c.P;
@@ -1052,7 +1055,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
             for (int32_t n : c.N) max_len = std::max(max_len, std::min(n, kTile));
             std::vector<int> cands;
             for (int th = 64; th <= kResampleThreads; th *= 2)
-                if (th * kItems >= max_len) cands.push_back(th);
+                if (th * 2 * kItems >= max_len) cands.push_back(th);
             float best = 1e30f;
             for (int th : cands) {
                 c.resample_threads = th;
@@ -1149,8 +1152,8 @@ pf_status pf_set_schedule(pf_ctx *h, int32_t nodes_per_thread, int32_t particles
     int max_len = 1;
     for (int32_t n : c.N) max_len = std::max(max_len, std::min(n, kTile));
     if (resample_threads != 0 && !((resample_threads == 64 || resample_threads == 128 || resample_threads == 256) &&
-                                   resample_threads * kItems >= max_len))
-        return fail(c, PF_EINVAL, "resample_threads: 0, or 64/128/256 with 4 threads' worth covering a tile");
+                                   resample_threads * 2 * kItems >= max_len))
+        return fail(c, PF_EINVAL, "resample_threads: 0, or 64/128/256 with 8 particles per thread covering a tile");
     pf_status st = sync(c, "set_schedule");
     if (st != PF_OK) return st;
     c.fhn_nodes = nodes_per_thread;

@@ -20,10 +20,12 @@ namespace pf {
 constexpr int kTile = 1024;
 constexpr int kResampleThreads = 256;
 constexpr int kItems = kTile / kResampleThreads;  // particles per thread in the tile kernels
-// Size classes of one-tile filters for the fused resampling kernel: class c
-// holds N <= 32 kItems 2^c and runs CTAs of 32 2^c threads.
-constexpr int kWholeClasses = 4;
-static_assert((32 << (kWholeClasses - 1)) == kResampleThreads, "the largest class fills a tile");
+// Size classes of one-tile filters for the fused resampling kernels: class c
+// holds N <= 32 kWholeItems 2^c; class 0 runs a warp per filter, class c > 0
+// CTAs of 32 2^c threads, kWholeItems particles per thread.
+constexpr int kWholeItems = 8;
+constexpr int kWholeClasses = 3;
+static_assert((32 * kWholeItems << (kWholeClasses - 1)) == kTile, "the largest class fills a tile");
 constexpr int kSubTile = 128;                     // propagation block of the thread-per-particle models
 constexpr int kMeanChunk = 256;                   // particles per partial sum of the lattice means
 
@@ -190,6 +192,7 @@ struct Ctx {
     float *logw = nullptr;
     int32_t *fmax_key = nullptr;  // [M]
     int resample_threads = kResampleThreads;
+    int max_tile_len = kTile;  // the longest tile: with 4 particles per thread it needs max_tile_len / 4 threads
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
     int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, or 0 (4 where J % 4 == 0)
     int fhn_quad_ctas = 3;         // four-node kernel: CTAs per SM it is compiled for (3 or 4; autotuned)

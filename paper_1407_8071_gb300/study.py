@@ -235,3 +235,110 @@ def paper_lattice_mse(Ns=(100, 500, 1000, 2000, 5000), M: int = 10, records=(0, 
                     f"{dt * 1e3:.3f} ms/step")
     return {"workload": "paper's 32x32 lattice, auxiliary filters", "M": M, "records": len(records), "T": T,
             "skip": skip, "rows": rows}
+
+
+def _ragged_records(spec: W.ModelSpec, n_filters: int, T: int):
+    """One synthetic record per filter of the ragged batch: truth (T+1, M, dx) and y (T, M, dy)."""
+    xs, ys = [], []
+    for m in range(n_filters):
+        x, y = pf.pf_simulate(spec, T, W.SEED_RAGGED, record=m)
+        xs.append(x)
+        ys.append(y)
+    return np.stack(xs, axis=1), np.stack(ys, axis=1)
+
+
+def ragged_time_error(theta, T: int = 20, R: int = 2, M_ref: int = 8, N_ref: int = 2048, skip: int = 4, log=None):
+    """The ragged batch (256 lattices of 20 x 20, N log-uniform in [64, 4096], a
+    record per filter, learned proposal on) run as one context and as 256
+    separate contexts: the MSE of each filter's v-estimates against its own
+    record's reference posterior (an ensemble of M_ref x N_ref bootstrap
+    filters per record, Def. 1), the wall time per run, and the time-error
+    index of Sec. 3.4 (wall time x MSE) of both forms."""
+    import torch
+    spec = W.fhn_lattice(J=W.RAGGED["J"])
+    counts = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
+    nf = len(counts)
+    idx = _var_index(spec)
+    _, y = _ragged_records(spec, nf, T)
+    d_y = torch.from_numpy(np.ascontiguousarray(y)).cuda()  # (T, nf, dy)
+    # reference: M_ref filters per record, filter r nf + m observing record m
+    d_y_ref = torch.from_numpy(np.ascontiguousarray(np.tile(y, (1, M_ref, 1)))).cuda()
+    ref = np.zeros((T, nf, len(idx)))
+    with pf.EnsembleFilter(spec, M_ref * nf, N_ref, 777) as f:
+        for t in range(T):
+            f.step_device(d_y_ref[t], per_filter=True)
+            e = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)[:, idx]
+            ref[t] = e.reshape(M_ref, nf, len(idx)).mean(axis=0)
+    if log:
+        log(f"ragged reference: {M_ref} x {N_ref} particles per record")
+
+    def batched(seed):
+        out = np.empty((T, nf, len(idx)))
+        with pf.EnsembleFilter(spec, nf, counts, seed) as f:
+            f.set_proposal(theta, 0.1)
+            for t in range(T):
+                f.step_device(d_y[t], per_filter=True)
+                out[t] = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)[:, idx]
+        return out
+
+    def separate(seed):
+        out = np.empty((T, nf, len(idx)))
+        ctxs = [pf.EnsembleFilter(spec, 1, int(n), seed + m) for m, n in enumerate(counts)]
+        try:
+            for f in ctxs:
+                f.set_proposal(theta, 0.1)
+            for t in range(T):
+                for m, f in enumerate(ctxs):
+                    f.step_device(d_y[t, m])
+                for m, f in enumerate(ctxs):
+                    out[t, m] = f.estimate(pf.PF_STAT_MEAN, var=-1)[idx]
+        finally:
+            for f in ctxs:
+                f.close()
+        return out
+
+    def contexts(form, st):
+        """The batch as one context (form "batched") or 256 (form "separate") on stream st."""
+        if form == "batched":
+            ctxs = [pf.EnsembleFilter(spec, nf, counts, 99)]
+        else:
+            ctxs = [pf.EnsembleFilter(spec, 1, int(n), 7000 + m) for m, n in enumerate(counts)]
+        for f in ctxs:
+            f.set_stream(st.cuda_stream)
+            f.set_proposal(theta, 0.1)
+        return ctxs
+
+    def step_all(form, ctxs, t):
+        if form == "batched":
+            ctxs[0].step_device(d_y[t % T], per_filter=True)
+        else:
+            for m, f in enumerate(ctxs):
+                f.step_device(d_y[t % T, m])
+
+    def seconds_per_step(form, steps=10):
+        st = torch.cuda.Stream()
+        ctxs = contexts(form, st)
+        try:
+            for t in range(3):
+                step_all(form, ctxs, t)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            for t in range(steps):
+                step_all(form, ctxs, 3 + t)
+            b.record(st)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / 1e3 / steps
+        finally:
+            for f in ctxs:
+                f.close()
+
+    rows = {}
+    for name, run in (("batched", batched), ("separate", separate)):
+        mse = float(np.mean([np.mean((run(5000 + 311 * r)[skip:] - ref[skip:]) ** 2) for r in range(R)]))
+        dt = seconds_per_step(name)
+        rows[name] = {"mse": mse, "s_per_step": dt, "s_per_run": dt * T, "time_error_index": dt * T * mse}
+        if log:
+            log(f"ragged {name:9s} MSE {mse:.3e}  {dt * 1e3:.2f} ms/step")
+    return {"workload": "256 fhn 20x20 lattices, N log-uniform in [64, 4096], a record per filter, learned proposal",
+            "T": T, "R": R, "skip": skip, "M_ref": M_ref, "N_ref": N_ref, "N_total": int(counts.sum()), "rows": rows}
