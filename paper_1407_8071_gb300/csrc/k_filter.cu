@@ -260,33 +260,11 @@ struct U128 {
 
 __device__ __forceinline__ U128 mul64(uint64_t a, uint64_t b) { return U128{__umul64hi(a, b), a * b}; }
 
-__device__ __forceinline__ bool ge128(const U128 &a, const U128 &b)
-{
-    return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo);
-}
-
-// x N 2^32 as 128 bits (x < 2^53, N <= 2^24).
-__device__ __forceinline__ U128 scaled_C(uint64_t x, uint64_t N)
-{
-    const U128 p = mul64(x, N);
-    return U128{(p.hi << 32) | (p.lo >> 32), p.lo << 32};
-}
-
-// (i 2^32 + U) Ctot: the systematic grid point t_i = (i + U 2^-32) Ctot / N, times N 2^32.
-__device__ __forceinline__ U128 grid_point(uint64_t i, uint32_t U, uint64_t Ctot)
-{
-    return mul64((i << 32) | U, Ctot);
-}
-
 struct Grid {
     uint64_t Ctot;  // C_{N-1}
     uint32_t U;     // u = U 2^-32
     int64_t N;
-    int est_shift;  // the estimate uses x >> est_shift (< 2^24, exact in FP32)
-    float est_scale;  // N 2^est_shift / Ctot
-    float u;        // U 2^-32
-    float Nf;       // N (<= 2^24, exact)
-    float Cf;       // Ctot in FP32 (relative error <= 2^-23)
+    float ratio;    // N / Ctot in FP32: only the starting point of the exact division below
 };
 
 // A 64-bit unsigned value as FP32 from its two 32-bit halves: 64-bit integer
@@ -299,69 +277,39 @@ __device__ __forceinline__ float u64_to_f32(uint64_t v)
 __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
 {
     Grid g;
-    g.Ctot = Ctot;
+    g.Ctot = Ctot ? Ctot : 1;
     g.U = U;
     g.N = N;
-    const int bits = 64 - __clzll((long long)(Ctot | 1));
-    g.est_shift = bits > 24 ? bits - 24 : 0;
-    // only a starting point for the exact walk: FP32 is enough (and FP64 division would
-    // cost every thread of the scan a slow FP64 sequence)
-    g.Nf = __int2float_rn((int32_t)N);
-    g.est_scale = g.Nf * __int_as_float((127 + g.est_shift) << 23) / u64_to_f32(Ctot ? Ctot : 1);
-    g.u = __uint2float_rn(U) * 0x1p-32f;
-    g.Cf = u64_to_f32(Ctot);
+    g.ratio = __int2float_rn((int32_t)N) / u64_to_f32(g.Ctot);
     return g;
 }
 
-// #{i in [0, N) : t_i < x}: the t_i increase with i, so this is the first i
-// with grid_point(i) >= x N 2^32.  A float estimate is corrected by a short
-// walk on the exact comparison, with bisection as the fallback.
-// The bisection fallback, out of line: it almost never runs, and inlining it
-// at every call site only crowds the instruction cache.
-__device__ __noinline__ int64_t count_bisect(const U128 X, const Grid g)
+// #{i in [0, N) : t_i < x}, t_i = (i + U 2^-32) Ctot / N, in exact integer
+// arithmetic (x <= Ctot < 2^53, N <= 2^24).  With x N = Q Ctot + R,
+// 0 <= R < Ctot, the grid points below x are i = 0 .. Q - 1, and i = Q when
+// R / Ctot > U 2^-32, i.e. R 2^32 > U Ctot (128-bit products); so the count is
+// Q + [R 2^32 > U Ctot], at most N.  Q starts from an FP32 estimate (relative
+// error about 3e-7, so within a few units of Q for N <= 2^24) and is corrected
+// exactly: R = x N - Q Ctot is formed modulo 2^64, which is exact while
+// |R| < 2^63 (here |R| < 8 Ctot), and moved into [0, Ctot) by whole steps.
+__device__ __forceinline__ int64_t count_below(uint64_t x, const Grid &g)
 {
-    int64_t lo = 0, hi = g.N;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (ge128(grid_point((uint64_t)mid, g.U, g.Ctot), X)) hi = mid; else lo = mid + 1;
+    const float qf = fminf(floorf(u64_to_f32(x) * g.ratio), (float)g.N);
+    int64_t Q = qf > 0.0f ? (int64_t)__float2int_rz(qf) : 0;
+    const int64_t C = (int64_t)g.Ctot;
+    int64_t R = (int64_t)(x * (uint64_t)g.N - (uint64_t)Q * g.Ctot);
+    while (R < 0) {
+        --Q;
+        R += C;
     }
-    return lo;
-}
-
-__device__ int64_t count_below(uint64_t x, const Grid &g)
-{
-    if (x == 0) return 0;
-    const float xf = __uint2float_rn((uint32_t)(x >> g.est_shift));
-    const float est = ceilf(__fmaf_rn(xf, g.est_scale, -g.u));
-    int64_t i = est <= 0.0f ? 0 : (est >= g.Nf ? g.N : (int64_t)__float2int_rz(est));
-    // FP32 certificate: the count is i when (i - 1 + u) Ctot < x N <= (i + u) Ctot.  Each side
-    // evaluated in FP32 (u64_to_f32 of x and Ctot, one rounding per operation) is within 3e-7 of
-    // its value relative to itself; a gap of 4e-6 x N on both sides decides the comparisons
-    // exactly, and anything closer takes the exact 128-bit path below.
-    {
-        const float xn = u64_to_f32(x) * g.Nf, tol = 4.0e-6f * xn;
-        const float fi = (float)(int32_t)i;
-        const bool lo_ok = i == 0 || (fi - 1.0f + g.u) * g.Cf < xn - tol;
-        const bool hi_ok = i == g.N || (fi + g.u) * g.Cf > xn + tol;
-        if (lo_ok && hi_ok) return i;
+    while (R >= C) {
+        ++Q;
+        R -= C;
     }
-    const U128 X = scaled_C(x, (uint64_t)g.N);
-    bool settled = false;
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-        if (i > 0 && ge128(grid_point((uint64_t)(i - 1), g.U, g.Ctot), X)) --i;
-        else { settled = true; break; }
-    }
-    if (settled) {
-        settled = false;
-#pragma unroll 1
-        for (int it = 0; it < 4; ++it) {
-            if (i < g.N && !ge128(grid_point((uint64_t)i, g.U, g.Ctot), X)) ++i;
-            else { settled = true; break; }
-        }
-    }
-    if (!settled) i = count_bisect(X, g);
-    return i;
+    const U128 rhs = mul64((uint64_t)g.U, g.Ctot);
+    const uint64_t lhi = (uint64_t)R >> 32, llo = (uint64_t)R << 32;
+    Q += (lhi > rhs.hi || (lhi == rhs.hi && llo > rhs.lo)) ? 1 : 0;
+    return Q < g.N ? Q : g.N;
 }
 
 // Unnormalised FP32 weight exp(l - max) from the FP32 log-weight; non-finite
