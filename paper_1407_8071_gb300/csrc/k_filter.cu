@@ -1109,7 +1109,7 @@ __global__ void __launch_bounds__(kResampleThreads) k_ancestors_small(ResampleAr
 // per-filter means.  The results are those of the tile chain bit for bit.
 // CTA b handles tile tile0 + b, which must be the filter's only tile.
 template <int D, int IT>
-__global__ void __launch_bounds__(kTile / IT) k_resample_whole(ResampleArgs a, int32_t tile0,
+__global__ void __launch_bounds__(kTile / IT, 8) k_resample_whole(ResampleArgs a, int32_t tile0,
                                                                      const float *__restrict__ x_in,
                                                                      float *__restrict__ x_out, int64_t P, double *est)
 {
@@ -1275,7 +1275,7 @@ constexpr int kWarpFilters = 4;
 constexpr int kWarpFilterMax = 32 * kWarpItems;
 
 template <int D>
-__global__ void __launch_bounds__(32 * kWarpFilters) k_resample_warp(ResampleArgs a, int32_t tile0, int32_t n,
+__global__ void __launch_bounds__(32 * kWarpFilters, 8) k_resample_warp(ResampleArgs a, int32_t tile0, int32_t n,
                                                                      const float *__restrict__ x_in,
                                                                      float *__restrict__ x_out, int64_t P, double *est)
 {
@@ -1514,7 +1514,10 @@ __global__ void __launch_bounds__(256) k_mean_rows(const FilterDesc *filt, const
 // rows x_out[p] = x_in[off + anc[p]] variable by variable (coalesced over the
 // block's variables) and sums what it copied, in the order and with the
 // arithmetic of k_mean_rows (unweighted), so the estimates are identical and
-// the resampled state is not read a second time.
+// the resampled state is not read a second time.  With x_out null the rows
+// are only summed: the gather itself is left to the next propagation, which
+// loads each particle's ancestor row directly (the same values, so the same
+// estimates).
 __global__ void __launch_bounds__(256) k_gather_mean_rows(const FilterDesc *filt, const TileDesc *__restrict__ chunks,
                                                           const int32_t *__restrict__ anc,
                                                           const float *__restrict__ x_in, float *__restrict__ x_out,
@@ -1527,22 +1530,25 @@ __global__ void __launch_bounds__(256) k_gather_mean_rows(const FilterDesc *filt
     double mine = 0.0;
     if (v < dx) {
         const int32_t *a = anc + ch.gstart;
-        float *dst = x_out + ch.gstart * (int64_t)dx + v;
+        float *dst = x_out ? x_out + ch.gstart * (int64_t)dx + v : nullptr;
         const float *src = x_in + fd.off * (int64_t)dx + v;
         FF acc{0.0f, 0.0f};
         int i = 0;
+        const bool store = x_out != nullptr;
         for (; i + 8 <= ch.len; i += 8) {  // eight rows in flight, then the ordered adds
             float r[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) r[k] = src[(int64_t)a[i + k] * dx];
+            if (store) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) dst[(int64_t)(i + k) * dx] = r[k];
+                for (int k = 0; k < 8; ++k) dst[(int64_t)(i + k) * dx] = r[k];
+            }
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc = ff_add(acc, r[k]);
         }
         for (; i < ch.len; ++i) {
             const float r = src[(int64_t)a[i] * dx];
-            dst[(int64_t)i * dx] = r;
+            if (store) dst[(int64_t)i * dx] = r;
             acc = ff_add(acc, r);
         }
         mine = ff_to_double(acc);
@@ -2267,6 +2273,39 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
         if (e != cudaSuccess) return e;
     }
     k_ensemble<<<dx, ensemble_threads(c.M), 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
+    return cudaGetLastError();
+}
+
+// Bootstrap lattice filters with the resampling's gather folded into the next
+// propagation: x_in holds the previous step's weighted particles and `gather`
+// (null on a first step) their ancestors, so particle p starts from row
+// off_m + gather[p] of x_in; the result goes to x_out (never in place: rows
+// of x_in are read by several particles).
+cudaError_t launch_propagate_fold(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
+                                  const int32_t *gather, cudaStream_t s)
+{
+    const AuxPtrs g{nullptr, nullptr, nullptr, nullptr, gather};
+    if (c.mp.kind == kFhnPaper) return launch_fhnp_interval(c, d_obs, stride, xi, xo, c.mp.K, c.logw, c.fmax_key, g, 1, s);
+    return launch_fhn_interval(c, d_obs, stride, xi, xo, c.mp.K, true, s, c.logw, c.fmax_key, g, 1);
+}
+
+// ... and its resampling: the ancestors and the per-filter means of the
+// ancestors' rows of x (read, not copied), then the M-average.
+cudaError_t launch_resample_fold(const Ctx &c, const float *x, cudaStream_t s)
+{
+    const ResampleArgs a = ctx_args(c);
+    resample_ancestors(c, a, c.resample_threads, s);
+    dim3 g(c.n_mchunks, (c.mp.dx + 255) / 256);
+    k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, x, nullptr, c.mp.dx, c.mean_part, c.mean_cnt, c.est);
+    k_ensemble<<<c.mp.dx, ensemble_threads(c.M), 0, s>>>(c.est, c.mp.dx, c.M, c.ens, c.d_t);
+    return cudaGetLastError();
+}
+
+// The resampled lattice particles as a state of their own: x_out[p] = x_in[off_m + anc[p]].
+cudaError_t launch_materialise(const Ctx &c, const float *xi, float *xo, cudaStream_t s)
+{
+    k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
+                                               reinterpret_cast<float4 *>(xo), c.mp.dx / 4);
     return cudaGetLastError();
 }
 

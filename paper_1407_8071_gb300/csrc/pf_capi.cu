@@ -123,15 +123,23 @@ cudaError_t stage_obs(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind k
 
 int32_t kernel_stride(const Ctx &c, int mode) { return mode == 0 ? 0 : c.mp.dy; }
 
-cudaError_t enqueue_propagate(Ctx &c, int mode)
+// Folded steps (Ctx::fold_gather) propagate x[cur] -> x[cur ^ 1], from the
+// ancestors' rows when the previous step left its gather pending, and resample
+// x[cur ^ 1] without copying it; other steps propagate x[cur] in place and
+// gather into x[cur ^ 1].  Either way the step's particles end in x[cur ^ 1].
+cudaError_t enqueue_propagate(Ctx &c, int mode, bool fold = false)
 {
     if (c.split_path()) return launch_propagate_split(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.stream);
+    if (fold)
+        return launch_propagate_fold(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[c.cur ^ 1],
+                                     c.gather_pending ? c.anc : nullptr, c.stream);
     return launch_propagate(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[c.cur], c.stream);
 }
 
-cudaError_t enqueue_resample(Ctx &c)
+cudaError_t enqueue_resample(Ctx &c, bool fold = false)
 {
     const int nxt = c.cur ^ 1;
+    if (fold) return launch_resample_fold(c, c.x[nxt], c.stream);
     cudaError_t e = launch_resample(c, c.x[c.cur], c.x[nxt], c.stream);
     if (e == cudaSuccess && c.rec_X && c.rec_count < c.rec_cap) {
         e = launch_gather_tuples(c, c.x[nxt], c.stream);
@@ -144,9 +152,23 @@ cudaError_t enqueue_step(Ctx &c, int mode)
 {
     if (c.aux) return launch_apf_step(c, c.d_obs, kernel_stride(c, mode), c.stream);
     if (c.adaptive()) return launch_adaptive_step(c, c.d_obs, kernel_stride(c, mode), c.stream);
-    cudaError_t e = enqueue_propagate(c, mode);
+    const bool fold = c.fold_gather();
+    cudaError_t e = enqueue_propagate(c, mode, fold);
     if (e != cudaSuccess) return e;
-    return enqueue_resample(c);
+    return enqueue_resample(c, fold);
+}
+
+// Writes the resampled particles of a folded step out as a state of their own
+// (x[cur ^ 1] = the ancestors' rows of x[cur]) for every reader other than the
+// next folded propagation.
+cudaError_t materialise(Ctx &c)
+{
+    if (!c.gather_pending) return cudaSuccess;
+    const cudaError_t e = launch_materialise(c, c.x[c.cur], c.x[c.cur ^ 1], c.stream);
+    if (e != cudaSuccess) return e;
+    c.cur ^= 1;
+    c.gather_pending = false;
+    return cudaSuccess;
 }
 
 // Per-particle weight buffers shared by the auxiliary filter and adaptive resampling.
@@ -181,15 +203,20 @@ pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind
     if (e != cudaSuccess) return cuda_fail(c, e, "observation copy");
     const int mode = obs_mode(stride);
     const int par = c.cur;
+    const bool fold = c.fold_gather();
+    // a captured step depends on the observation layout and on whether the gather is folded
+    // and pending from the previous step
+    const int32_t key = mode | (fold ? 2 : 0) | (fold && c.gather_pending ? 4 : 0);
     if (c.rec_X) {  // recording steps carry a moving output offset: launched directly
         e = enqueue_step(c, mode);
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        c.gather_pending = false;
         c.cur ^= 1;
         c.t += 1;
         c.steps_done = true;
         return PF_OK;
     }
-    if (!c.graph[par] || c.graph_mode[par] != mode) {
+    if (!c.graph[par] || c.graph_mode[par] != key) {
         if (c.graph[par]) {
             cudaGraphExecDestroy(c.graph[par]);
             c.graph[par] = nullptr;
@@ -224,13 +251,14 @@ pf_status run_step(Ctx &c, const float *obs, int32_t stride, cudaMemcpyKind kind
         e = cudaGraphInstantiate(&c.graph[par], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-        c.graph_mode[par] = mode;
+        c.graph_mode[par] = key;
     }
     e = cudaGraphLaunch(c.graph[par], c.stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
     c.cur ^= 1;
     c.t += 1;
     c.steps_done = true;
+    c.gather_pending = fold;
     return PF_OK;
 }
 
@@ -240,6 +268,15 @@ pf_status sync(Ctx &c, const char *where)
     const cudaError_t e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return cuda_fail(c, e, where);
     return PF_OK;
+}
+
+// sync, after writing out a pending folded gather (for readers and mode switches)
+pf_status sync_materialised(Ctx &c, const char *where)
+{
+    cudaSetDevice(c.device);
+    const cudaError_t e = materialise(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return sync(c, where);
 }
 
 pf_status check_device_flags(Ctx &c)
@@ -702,7 +739,8 @@ static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride,
     if (c.aux) return fail(c, PF_EUNSUPPORTED, "the auxiliary filter steps as a whole: use pf_step");
     if (c.adaptive()) return fail(c, PF_EUNSUPPORTED, "adaptive resampling steps as a whole: use pf_step");
     cudaSetDevice(c.device);
-    cudaError_t e = stage_obs(c, obs, obs_stride, kind);
+    cudaError_t e = materialise(c);  // the two halves take the unfolded path
+    if (e == cudaSuccess) e = stage_obs(c, obs, obs_stride, kind);
     if (e == cudaSuccess) e = enqueue_propagate(c, obs_mode(obs_stride));
     if (e != cudaSuccess) return cuda_fail(c, e, "propagate");
     c.phase = 1;
@@ -913,7 +951,7 @@ pf_status pf_set_proposal(pf_ctx *h, const float *h_theta, int32_t n_params, dou
         return fail(c, PF_EUNSUPPORTED, "the learned proposal is not combined with the auxiliary filter or adaptive resampling");
     if (h_theta && (n_params != PF_MLP_PARAMS || !(ess_frac >= 0.0 && ess_frac <= 1.0)))
         return fail(c, PF_EINVAL, "n_params must be PF_MLP_PARAMS and ess_frac in [0, 1]");
-    pf_status st = sync(c, "set_proposal");
+    pf_status st = sync_materialised(c, "set_proposal");
     if (st != PF_OK) return st;
     drop_graphs(c);
     if (!h_theta) {
@@ -938,7 +976,7 @@ pf_status pf_record_tuples(pf_ctx *h, float *d_X, float *d_R, int64_t capacity, 
     if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the lattice");
     if ((c.aux || c.adaptive()) && d_X) return fail(c, PF_EUNSUPPORTED, "tuple recording is for the bootstrap filter");
     if (c.phase != 0) return fail(c, PF_ESTATE, "pf_record_tuples between pf_propagate and pf_resample");
-    pf_status st = sync(c, "record_tuples");
+    pf_status st = sync_materialised(c, "record_tuples");
     if (st != PF_OK) return st;
     drop_graphs(c);
     if (!d_X) {
@@ -979,7 +1017,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
     Ctx &c = h->c;
     if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
     if (c.phase != 0 || c.rec_X) return fail(c, PF_ESTATE, "pf_autotune needs a context between steps, not recording");
-    pf_status st = sync(c, "autotune");
+    pf_status st = sync_materialised(c, "autotune");
     if (st != PF_OK) return st;
     const auto key = std::make_tuple((int)c.mp.kind, (int)c.mp.J, (int)c.mp.K, (int)c.mp.dx, (int64_t)c.P, c.M,
                                      counts_hash(c.N));
@@ -1104,7 +1142,7 @@ pf_status pf_set_auxiliary(pf_ctx *h, int32_t on)
     if (on && (c.prop_on || c.rec_X || c.adaptive()))
         return fail(c, PF_EUNSUPPORTED,
                     "the auxiliary filter is not combined with the learned proposal, recording or adaptive resampling");
-    pf_status st = sync(c, "set_auxiliary");
+    pf_status st = sync_materialised(c, "set_auxiliary");
     if (st != PF_OK) return st;
     drop_graphs(c);
     if (!on) {
@@ -1127,7 +1165,7 @@ pf_status pf_set_resampling(pf_ctx *h, double ess_threshold)
     if (adaptive && (c.aux || c.prop_on || c.rec_X))
         return fail(c, PF_EUNSUPPORTED,
                     "adaptive resampling is not combined with the auxiliary filter, the learned proposal or recording");
-    pf_status st = sync(c, "set_resampling");
+    pf_status st = sync_materialised(c, "set_resampling");
     if (st != PF_OK) return st;
     drop_graphs(c);
     c.ess_threshold = adaptive ? ess_threshold : -1.0;
@@ -1175,7 +1213,7 @@ pf_status pf_get_state(pf_ctx *h, float *h_x)
     Trace trace("pf_get_state");
     if (!h || !h_x) return PF_EINVAL;
     Ctx &c = h->c;
-    pf_status st = sync(c, "get_state");
+    pf_status st = sync_materialised(c, "get_state");
     if (st != PF_OK) return st;
     const int dx = c.mp.dx;
     const size_t n = (size_t)c.P * dx;
@@ -1214,6 +1252,7 @@ pf_status pf_set_state(pf_ctx *h, const float *h_x, int32_t t)
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state copy");
     c.t = t;
     c.phase = 0;
+    c.gather_pending = false;  // the state is the one given
     if (c.aux || c.adaptive()) return reset_aux_weights(c);
     return PF_OK;
 }

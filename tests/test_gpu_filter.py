@@ -327,3 +327,32 @@ def test_fhn_20x20_statistical_parity_with_oracle():
     eg = run_gpu(spec, M, N, y32, seed=23, var=node)
     eo = oracle.bf_run(spec, M, N, T, y32.astype(np.float64), seed=24, est_idx=[node])["est"][:, :, 0]
     z_parity(eg, eo, [0, 4, 9])
+
+
+@pytest.mark.parametrize("paper", [False, True])
+def test_folded_gather_equals_the_copied_state(paper):
+    """Bootstrap lattice steps fold the resampling's gather into the next
+    propagation (which loads each particle's ancestor row itself); the two
+    halves pf_propagate / pf_resample copy the resampled rows instead, and a
+    read of the state in between writes a pending gather out.  All three give
+    the same particles and estimates bit for bit, on ragged filters of one and
+    of several tiles."""
+    spec = W.fhn_paper(J=8, zones=4) if paper else W.fhn_lattice(J=8)
+    _, y = oracle.simulate(spec, 4, W.SEED_FHN_OBS)
+    y32 = y.astype(np.float32)
+    N = np.array([1500, 40, 700], dtype=np.int32)
+    outs = []
+    for mode in ("step", "phases", "step+read"):
+        with pf.EnsembleFilter(spec, len(N), N, 13) as f:
+            for t in range(4):
+                if mode == "phases":
+                    f.propagate(y32[t])
+                    f.resample()
+                else:
+                    f.step(y32[t])
+                    if mode == "step+read" and t % 2 == 0:
+                        f.get_state()
+            outs.append((f.get_state(), f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True),
+                         f.get_ancestors()))
+    for x, e, a in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(e, outs[0][1]) and np.array_equal(a, outs[0][2])
