@@ -57,10 +57,12 @@ FP32_LANES_PER_SM = 128
 LORENZ_OPS_PER_PARTICLE_STEP = 86.5
 # Algorithmic HBM bytes of a resampling step per particle: its log-weight read
 # and its ancestor index written, plus, per state variable, the gather (one
-# read, one write; the per-filter means are taken from the gathered values).
+# read, one write; the per-filter means are taken from the gathered values) --
+# or, where the gather is folded into the next propagation, the read alone.
 # The prefix and the markers of the tile chain are implementation traffic.
 RESAMPLE_BYTES_PER_PARTICLE = 4 + 4
 RESAMPLE_BYTES_PER_VARIABLE = 4 + 4
+RESAMPLE_BYTES_PER_VARIABLE_FOLDED = 4
 
 # Algorithmic ALU operations per lattice node-step (one Euler-Maruyama
 # sub-step of one node, both planes): Philox4x32-10 40 per 4 normals -> 20,
@@ -351,9 +353,10 @@ def time_region(torch, wl, fn, K, barrier=None):
 
 
 def phase_times(torch, wl, reps=5):
-    """Average device time of the propagate+weight kernel and of the resampling
-    chain, per launch, with CUDA events on the filters' stream (the auxiliary
-    filter steps as one unit: its whole step is the first figure)."""
+    """Average device time of the propagate+weight half and of the resampling
+    half of a step, per launch, as the step runs them (pf_step_timed: CUDA
+    events between the halves on the filters' stream; the auxiliary filter
+    steps as one unit, so its whole step is the first figure)."""
     prop, res = [], []
     if wl.aux:
         for f, st in zip(wl.filters, wl.streams):
@@ -366,18 +369,11 @@ def phase_times(torch, wl, reps=5):
                 prop.append(e0.elapsed_time(e1) / 1e3)
                 wl.t += 1
         return float(np.mean(prop)), 0.0, prop
-    for f, st in zip(wl.filters, wl.streams):
+    for f in wl.filters:
         for _ in range(reps):
-            row = wl.y_dev[wl.t % wl.T]
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(st)
-            f.propagate_device(row, per_filter=wl.per_filter_obs)
-            e1.record(st)
-            f.resample()
-            e2.record(st)
-            torch.cuda.synchronize()
-            prop.append(e0.elapsed_time(e1) / 1e3)
-            res.append(e1.elapsed_time(e2) / 1e3)
+            a, b = f.step_timed(wl.y_dev[wl.t % wl.T], per_filter=wl.per_filter_obs)
+            prop.append(a / 1e3)
+            res.append(b / 1e3)
             wl.t += 1
     return float(np.mean(prop)), float(np.mean(res)), prop
 
@@ -385,12 +381,15 @@ def phase_times(torch, wl, reps=5):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------
-def resample_roofline(wl, t_res, peaks, peak_src):
+def resample_roofline(wl, t_res, peaks, peak_src, folded):
     """HBM roofline of the resampling chain (normaliser, systematic resampling,
-    gather, per-filter means), per context step, on algorithmic bytes."""
+    gather, per-filter means), per context step, on algorithmic bytes: with
+    the gather folded into the next propagation only the ancestors' values are
+    read (for the means), else they are also written as the new state."""
     nf = len(wl.filters)
     per_ctx = wl.particles / nf
-    bytes_ = per_ctx * (RESAMPLE_BYTES_PER_PARTICLE + wl.spec.dx * RESAMPLE_BYTES_PER_VARIABLE)
+    per_var = RESAMPLE_BYTES_PER_VARIABLE_FOLDED if folded else RESAMPLE_BYTES_PER_VARIABLE
+    bytes_ = per_ctx * (RESAMPLE_BYTES_PER_PARTICLE + wl.spec.dx * per_var)
     hbm = float(peaks["hbm_gbs"])
     achieved = bytes_ / t_res / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -562,6 +561,9 @@ def measure(name, steps, warmup, rank, world, barrier, cpu_seconds):
 
     # the dominant kernel, timed live per launch
     t_prop, t_res, _ = phase_times(torch, wl)
+    # bootstrap steps fold the resampling's gather into the next propagation: the resampling then reads
+    # the ancestors' values for the means and writes no copy of the state
+    folded = not wl.aux and wl.theta is None
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if wl.spec.kind == W.LORENZ63:
@@ -623,8 +625,8 @@ def measure(name, steps, warmup, rank, world, barrier, cpu_seconds):
                 "d2h_bytes_per_step": nf * 8},
         "gpu_launches": steps * wl.launches_per_step(),
         "roofline": roofline,
-        "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res},
-        "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src) if t_res > 0 else None,
+        "phases_s": {"propagate_weight": t_prop, "resample_chain": t_res, "gather_folded": folded},
+        "resample_roofline": resample_roofline(wl, t_res, peaks, peak_src, folded) if t_res > 0 else None,
     }
     theta = wl.theta
     if wl.name == "ragged":

@@ -180,6 +180,15 @@ PF_API pf_status pf_step(pf_ctx *ctx, const float *h_obs, int32_t obs_stride);
  * as h_obs); d_obs must stay valid until the step completes on the stream. */
 PF_API pf_status pf_step_device(pf_ctx *ctx, const float *d_obs, int32_t obs_stride);
 
+/* pf_step_device launched without its CUDA graph, with CUDA events around
+ * its two halves as a step runs them: h_ms[0] receives the device time of
+ * the propagation and weighting (Alg. 1 step 2a), h_ms[1] that of the
+ * resampling with the estimates (step 2b, Definition 1).  For measuring the
+ * step; the filter advances exactly as with pf_step_device.  Synchronises.
+ * Bootstrap filters only.  Errors: PF_EINVAL, PF_ESTATE, PF_EUNSUPPORTED,
+ * PF_ECUDA. */
+PF_API pf_status pf_step_timed(pf_ctx *ctx, const float *d_obs, int32_t obs_stride, float *h_ms);
+
 /* The two halves of pf_step, for callers that inspect the weighted particles
  * between them: pf_propagate is step 2a (propagate + log-weights);
  * pf_resample is the normalisation, step 2b and the estimates.  A pf_step is

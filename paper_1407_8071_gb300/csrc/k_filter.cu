@@ -398,9 +398,10 @@ __global__ void __launch_bounds__(kPropThreads, 16)
     for (int r = 0; r < 2; ++r) {
         j[r] = min((int)threadIdx.x + r * kPropThreads, st.len - 1);
         c0[r] = (uint32_t)(st.lstart + j[r]);
-        const int64_t p = st.gstart + j[r];
+        // with a folded gather the particle starts from its ancestor's variables
+        const int64_t src = aux.gather ? (st.gstart - st.lstart) + aux.gather[st.gstart + j[r]] : st.gstart + j[r];
 #pragma unroll
-        for (int v = 0; v < D; ++v) xs[r][v] = x_in[v * P + p];
+        for (int v = 0; v < D; ++v) xs[r][v] = x_in[v * P + src];
     }
     propagate_small_n<D, 2, float, Mode != 1>(mp, key, kStreamDyn, c0, t, (uint32_t)st.m, xs);
     float l = -INFINITY;
@@ -993,8 +994,9 @@ __device__ __forceinline__ void tile_ancestors(const ResampleArgs &a, const Tile
 
 // A thread's IT consecutive outputs p0 .. p0 + IT - 1 (the first `left` of
 // them exist): their ancestor indices, the gathered SoA state
-// x_out[v][p] = x_in[v][off + anc] and the running compensated sums of what
-// was gathered, item by item.  Whole aligned groups store as int4 / float4.
+// x_out[v][p] = x_in[v][off + anc] (not stored when x_out is null: the gather
+// is folded into the next propagation) and the running compensated sums of
+// what was gathered, item by item.  Whole aligned groups store as int4 / float4.
 template <int D, int IT>
 __device__ __forceinline__ void gather_items(int32_t *anc_out, int64_t off, int64_t p0, int left,
                                              const int32_t (&anc)[IT], const float *__restrict__ x_in,
@@ -1003,6 +1005,17 @@ __device__ __forceinline__ void gather_items(int32_t *anc_out, int64_t off, int6
     static_assert(IT % 4 == 0, "whole int4 / float4 groups per thread and variable");
 #pragma unroll
     for (int v = 0; v < D; ++v) f[v] = FF{0.0f, 0.0f};
+    if (!x_out) {  // a folded gather: only the sums of the ancestors' variables
+#pragma unroll
+        for (int r = 0; r < IT; ++r) {
+            if (r < left) {
+                anc_out[p0 + r] = anc[r];
+#pragma unroll
+                for (int v = 0; v < D; ++v) f[v] = ff_add(f[v], x_in[v * P + off + anc[r]]);
+            }
+        }
+        return;
+    }
     if (left >= IT && ((p0 | P) & 3) == 0) {
 #pragma unroll
         for (int r = 0; r < IT; r += 4)
@@ -2276,36 +2289,82 @@ cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t stride, cu
     return cudaGetLastError();
 }
 
-// Bootstrap lattice filters with the resampling's gather folded into the next
+// Small models: the resampled SoA state written out from the ancestors,
+// x_out[v][p] = x_in[v][off_m + anc[p]], a CTA per tile.
+template <int D>
+__global__ void __launch_bounds__(256) k_gather_small(const TileDesc *__restrict__ tiles, const int32_t *__restrict__ anc,
+                                                      const float *__restrict__ x_in, float *__restrict__ x_out,
+                                                      int64_t P)
+{
+    const TileDesc td = tiles[blockIdx.x];
+    const int64_t off = td.gstart - td.lstart;
+    for (int j = threadIdx.x; j < td.len; j += blockDim.x) {
+        const int64_t p = td.gstart + j, src = off + anc[p];
+#pragma unroll
+        for (int v = 0; v < D; ++v) x_out[v * P + p] = x_in[v * P + src];
+    }
+}
+
+// Bootstrap filters with the resampling's gather folded into the next
 // propagation: x_in holds the previous step's weighted particles and `gather`
-// (null on a first step) their ancestors, so particle p starts from row
-// off_m + gather[p] of x_in; the result goes to x_out (never in place: rows
-// of x_in are read by several particles).
+// (null on a first step) their ancestors, so particle p starts from particle
+// off_m + gather[p] of x_in; the result goes to x_out (never in place: a
+// particle of x_in is read by all its offspring).
 cudaError_t launch_propagate_fold(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
                                   const int32_t *gather, cudaStream_t s)
 {
     const AuxPtrs g{nullptr, nullptr, nullptr, nullptr, gather};
     if (c.mp.kind == kFhnPaper) return launch_fhnp_interval(c, d_obs, stride, xi, xo, c.mp.K, c.logw, c.fmax_key, g, 1, s);
-    return launch_fhn_interval(c, d_obs, stride, xi, xo, c.mp.K, true, s, c.logw, c.fmax_key, g, 1);
-}
-
-// ... and its resampling: the ancestors and the per-filter means of the
-// ancestors' rows of x (read, not copied), then the M-average.
-cudaError_t launch_resample_fold(const Ctx &c, const float *x, cudaStream_t s)
-{
-    const ResampleArgs a = ctx_args(c);
-    resample_ancestors(c, a, c.resample_threads, s);
-    dim3 g(c.n_mchunks, (c.mp.dx + 255) / 256);
-    k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, x, nullptr, c.mp.dx, c.mean_part, c.mean_cnt, c.est);
-    k_ensemble<<<c.mp.dx, ensemble_threads(c.M), 0, s>>>(c.est, c.mp.dx, c.M, c.ens, c.d_t);
+    if (is_lattice(c.mp.kind)) return launch_fhn_interval(c, d_obs, stride, xi, xo, c.mp.K, true, s, c.logw, c.fmax_key, g, 1);
+    switch (c.mp.dx) {
+    case 1: k_propagate_small<1, 0><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs, stride, c.d_t, g); break;
+    case 2: k_propagate_small<2, 0><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs, stride, c.d_t, g); break;
+    case 3: k_propagate_small<3, 0><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs, stride, c.d_t, g); break;
+    case 4: k_propagate_small<4, 0><<<c.n_subs, kPropThreads, 0, s>>>(c.mp, c.key, c.subs, xi, xo, c.P, c.logw, c.fmax_key, d_obs, stride, c.d_t, g); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-// The resampled lattice particles as a state of their own: x_out[p] = x_in[off_m + anc[p]].
+// ... and its resampling: the ancestors and the per-filter means of the
+// ancestors' values (read, not copied), then the M-average.
+cudaError_t launch_resample_fold(const Ctx &c, const float *x, cudaStream_t s)
+{
+    const ResampleArgs a = ctx_args(c);
+    const int dx = c.mp.dx, th = c.resample_threads;
+    if (is_lattice(c.mp.kind)) {
+        resample_ancestors(c, a, th, s);
+        dim3 g(c.n_mchunks, (dx + 255) / 256);
+        k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, x, nullptr, dx, c.mean_part, c.mean_cnt, c.est);
+    } else {
+        switch (dx) {
+        case 1: resample_small<1>(c, a, x, nullptr, th, s); break;
+        case 2: resample_small<2>(c, a, x, nullptr, th, s); break;
+        case 3: resample_small<3>(c, a, x, nullptr, th, s); break;
+        case 4: resample_small<4>(c, a, x, nullptr, th, s); break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    k_ensemble<<<dx, ensemble_threads(c.M), 0, s>>>(c.est, dx, c.M, c.ens, c.d_t);
+    return cudaGetLastError();
+}
+
+// The resampled particles as a state of their own: the ancestors' rows
+// (lattice) or variables (small models) of x_in.
 cudaError_t launch_materialise(const Ctx &c, const float *xi, float *xo, cudaStream_t s)
 {
-    k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
-                                               reinterpret_cast<float4 *>(xo), c.mp.dx / 4);
+    if (is_lattice(c.mp.kind)) {
+        k_gather_rows<<<(unsigned)c.P, 256, 0, s>>>(c.anc, c.pfilt, c.filt, reinterpret_cast<const float4 *>(xi),
+                                                   reinterpret_cast<float4 *>(xo), c.mp.dx / 4);
+        return cudaGetLastError();
+    }
+    switch (c.mp.dx) {
+    case 1: k_gather_small<1><<<c.n_tiles, 256, 0, s>>>(c.tiles, c.anc, xi, xo, c.P); break;
+    case 2: k_gather_small<2><<<c.n_tiles, 256, 0, s>>>(c.tiles, c.anc, xi, xo, c.P); break;
+    case 3: k_gather_small<3><<<c.n_tiles, 256, 0, s>>>(c.tiles, c.anc, xi, xo, c.P); break;
+    case 4: k_gather_small<4><<<c.n_tiles, 256, 0, s>>>(c.tiles, c.anc, xi, xo, c.P); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

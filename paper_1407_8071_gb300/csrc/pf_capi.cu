@@ -729,6 +729,40 @@ pf_status pf_step_device(pf_ctx *h, const float *d_obs, int32_t obs_stride)
     return run_step(h->c, d_obs, obs_stride, cudaMemcpyDeviceToDevice);
 }
 
+pf_status pf_step_timed(pf_ctx *h, const float *d_obs, int32_t obs_stride, float *h_ms)
+{
+    Trace trace("pf_step_timed");
+    if (!h || !h_ms) return PF_EINVAL;
+    Ctx &c = h->c;
+    pf_status st = validate_step(c, d_obs, obs_stride);
+    if (st != PF_OK) return st;
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_step_timed between pf_propagate and pf_resample");
+    if (c.aux || c.adaptive() || c.rec_X) return fail(c, PF_EUNSUPPORTED, "timed steps are for the bootstrap filter");
+    cudaSetDevice(c.device);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    const int mode = obs_mode(obs_stride);
+    const bool fold = c.fold_gather();
+    if (e == cudaSuccess) e = stage_obs(c, d_obs, obs_stride, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], c.stream);
+    if (e == cudaSuccess) e = enqueue_propagate(c, mode, fold);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c.stream);
+    if (e == cudaSuccess) e = enqueue_resample(c, fold);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], c.stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&h_ms[0], ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&h_ms[1], ev[1], ev[2]);
+    for (int i = 0; i < 3; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "timed step");
+    c.cur ^= 1;
+    c.t += 1;
+    c.steps_done = true;
+    c.gather_pending = fold;
+    return PF_OK;
+}
+
 static pf_status propagate_impl(pf_ctx *h, const float *obs, int32_t obs_stride, cudaMemcpyKind kind)
 {
     if (!h) return PF_EINVAL;

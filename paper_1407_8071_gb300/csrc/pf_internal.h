@@ -128,10 +128,10 @@ cudaError_t launch_init(const Ctx &c, cudaStream_t s);
 cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t obs_stride, const float *x_in, float *x_out,
                              cudaStream_t s);
 cudaError_t launch_resample(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s);
-// Bootstrap lattice steps with the resampling's gather folded into the next
-// propagation (Ctx::fold_gather): the propagation from the ancestors' rows
-// (gather null: from row p), the resampling without the copy, and the copy
-// itself for readers of the resampled state.
+// Bootstrap steps with the resampling's gather folded into the next
+// propagation (Ctx::fold_gather): the propagation from the ancestors
+// (gather null: from particle p), the resampling without the copy, and the
+// copy itself for readers of the resampled state.
 cudaError_t launch_propagate_fold(const Ctx &c, const float *d_obs, int32_t obs_stride, const float *x_in,
                                   float *x_out, const int32_t *gather, cudaStream_t s);
 cudaError_t launch_resample_fold(const Ctx &c, const float *x, cudaStream_t s);
@@ -252,11 +252,11 @@ struct Ctx {
     int32_t rec_stride = 1;
     int64_t *rec_sel_off = nullptr;   // [M] kept particles before each filter
     bool split_path() const { return prop_on || rec_X != nullptr; }
-    // Bootstrap lattice filters fold the resampling's gather into the next
+    // Bootstrap filters fold the resampling's gather into the next
     // propagation (Alg. 1 step 2b's copy is never written): after such a step
-    // the resampled particles are rows off_m + anc[p] of x[cur]
+    // the resampled particles are particles off_m + anc[p] of x[cur]
     // (gather_pending), and every other reader first materialises them.
-    bool fold_gather() const { return is_lattice(mp.kind) && !aux && !adaptive() && !split_path(); }
+    bool fold_gather() const { return !aux && !adaptive() && !split_path(); }
     bool gather_pending = false;
 
     int cur = 0;  // x[cur] holds the current particles

@@ -75,6 +75,7 @@ _SIGS = {
     "pf_estimate_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "pf_estimate_wait": (c_int32, [c_void_p]),
     "pf_inject_error": (c_int32, [c_void_p, c_int32, c_int32]),
+    "pf_step_timed": (c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_float)]),
     "pf_ensemble_average": (c_int32, [c_int32, c_int32, POINTER(c_double), POINTER(c_double)]),
     "pf_step_kernels": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_resampling": (c_int32, [c_void_p, c_double]),
@@ -363,6 +364,12 @@ class EnsembleFilter:
 
     def step_device(self, d_y, per_filter: bool = False):
         _check(lib().pf_step_device(self.h, d_y.data_ptr(), self.spec.dy if per_filter else 0), self.h)
+
+    def step_timed(self, d_y, per_filter: bool = False):
+        """A step without its graph, timed by halves: (propagation ms, resampling ms)."""
+        ms = (c_float * 2)()
+        _check(lib().pf_step_timed(self.h, d_y.data_ptr(), self.spec.dy if per_filter else 0, ms), self.h)
+        return float(ms[0]), float(ms[1])
 
     def propagate(self, y, per_filter: bool = False):
         y = self._obs(y)

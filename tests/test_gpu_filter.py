@@ -329,16 +329,17 @@ def test_fhn_20x20_statistical_parity_with_oracle():
     z_parity(eg, eo, [0, 4, 9])
 
 
-@pytest.mark.parametrize("paper", [False, True])
-def test_folded_gather_equals_the_copied_state(paper):
-    """Bootstrap lattice steps fold the resampling's gather into the next
-    propagation (which loads each particle's ancestor row itself); the two
-    halves pf_propagate / pf_resample copy the resampled rows instead, and a
+@pytest.mark.parametrize("model", ["lorenz63", "fhn", "fhn_paper"])
+def test_folded_gather_equals_the_copied_state(model):
+    """Bootstrap steps fold the resampling's gather into the next propagation
+    (which loads each particle's ancestor itself); the two halves
+    pf_propagate / pf_resample copy the resampled particles instead, and a
     read of the state in between writes a pending gather out.  All three give
     the same particles and estimates bit for bit, on ragged filters of one and
     of several tiles."""
-    spec = W.fhn_paper(J=8, zones=4) if paper else W.fhn_lattice(J=8)
-    _, y = oracle.simulate(spec, 4, W.SEED_FHN_OBS)
+    spec = {"lorenz63": W.lorenz63, "fhn": lambda: W.fhn_lattice(J=8),
+            "fhn_paper": lambda: W.fhn_paper(J=8, zones=4)}[model]()
+    _, y = oracle.simulate(spec, 4, W.SEED_LORENZ_OBS if model == "lorenz63" else W.SEED_FHN_OBS)
     y32 = y.astype(np.float32)
     N = np.array([1500, 40, 700], dtype=np.int32)
     outs = []
@@ -356,3 +357,22 @@ def test_folded_gather_equals_the_copied_state(paper):
                          f.get_ancestors()))
     for x, e, a in outs[1:]:
         assert np.array_equal(x, outs[0][0]) and np.array_equal(e, outs[0][1]) and np.array_equal(a, outs[0][2])
+
+
+def test_timed_step_is_a_step():
+    """pf_step_timed advances the filter exactly as pf_step_device does and
+    reports two positive device times (propagation, resampling)."""
+    spec = W.lorenz63()
+    _, y = oracle.simulate(spec, 3, W.SEED_LORENZ_OBS)
+    d_y = torch.from_numpy(y.astype(np.float32)).cuda()
+    outs = []
+    for timed in (False, True):
+        with pf.EnsembleFilter(spec, 3, np.array([1500, 40, 700], dtype=np.int32), 4) as f:
+            for t in range(3):
+                if timed:
+                    a, b = f.step_timed(d_y[t])
+                    assert a > 0 and b > 0
+                else:
+                    f.step_device(d_y[t])
+            outs.append((f.get_state(), f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
