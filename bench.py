@@ -652,11 +652,17 @@ def extra_workloads(rank, world, barrier, args):
 
 
 def time_to_mse_block():
-    """A short seeded study on the 40 x 40 lattice at M = 32 (the learned-proposal
-    workload): MSE of the averaged v-estimates against a large-ensemble reference
-    for the plain, learned-proposal and auxiliary ensembles at N = 256, 512, 1024,
-    and the wall time each needs to reach the plain ensemble's MSE at N = 1024
-    (log-log interpolation between the runs that bracket it)."""
+    """Short seeded studies of the wall time to reach a fixed MSE.
+
+    config4: the 40 x 40 lattice at M = 32: MSE of the averaged v-estimates against
+    a large-ensemble reference for the plain, learned-proposal and auxiliary
+    ensembles at N = 256, 512, 1024, and the wall time each needs to reach the
+    plain ensemble's MSE at N = 1024 (log-log interpolation between the runs that
+    bracket it).
+    config5: the ragged batch of 256 20 x 20 lattices: the learned proposal in one
+    batched context (particle counts scaled by 0.5, 1, 2) against the bootstrap
+    filters as 256 separate contexts, and the wall time the batched learned form
+    needs to reach the separate bootstrap filters' MSE."""
     from paper_1407_8071_gb300 import pf, proposal, study
     t0 = time.perf_counter()
     spec = W.fhn_lattice()
@@ -665,7 +671,7 @@ def time_to_mse_block():
     r = study.lattice_time_to_mse(theta, Ns=(256, 512, 1024), R=4, T=30, M_ref=512, N_ref=1024, ref_seeds=(951,),
                                   skip=5, methods=("plain", "learned", "auxiliary"))
     plain = r["plain_s_at_target"]
-    return {
+    c4 = {
         "workload": "fhn 40x40 lattice, M=32 ensembles of N in {256, 512, 1024}; R=4 ensembles per point, T=30 "
                     "observations (the first 5 not scored), reference: 512 x 1024 bootstrap ensemble",
         "target_mse": r["target_mse"], "plain_s": plain,
@@ -674,8 +680,17 @@ def time_to_mse_block():
         "auxiliary_vs_plain": (r["auxiliary_s_at_target"] / plain) if r["auxiliary_s_at_target"] else None,
         "rows": {k: [{kk: row[kk] for kk in ("N", "mse", "s_per_run", "mean_ess_frac")} for row in v]
                  for k, v in r["rows"].items()},
-        "wall_s": time.perf_counter() - t0,
     }
+    rspec = W.fhn_lattice(J=W.RAGGED["J"])
+    rtheta = proposal.trained_theta(rspec, pf.pf_simulate(rspec, 20, W.SEED_RAGGED, record=1 << 20)[1], seed=77)
+    rg = study.ragged_time_error(rtheta, T=12, R=1, M_ref=4, N_ref=2048, skip=3)
+    c5 = {"workload": rg["workload"] + "; T=12 (the first 3 not scored), R=1, reference 4 x 2048 per record",
+          "target_mse": rg["target_mse"], "plain_separate_s": rg["plain_separate_s"],
+          "learned_batched_s": rg["learned_batched_s_at_target"],
+          "learned_batched_vs_plain_separate": rg["learned_batched_vs_plain_separate"],
+          "rows": [{k: row[k] for k in ("form", "proposal", "scale", "N_total", "mse", "s_per_run")}
+                   for row in rg["rows"]]}
+    return {"config4": c4, "config5": c5, "wall_s": time.perf_counter() - t0}
 
 
 # ---------------------------------------------------------------------------

@@ -247,13 +247,27 @@ def _ragged_records(spec: W.ModelSpec, n_filters: int, T: int):
     return np.stack(xs, axis=1), np.stack(ys, axis=1)
 
 
-def ragged_time_error(theta, T: int = 20, R: int = 2, M_ref: int = 8, N_ref: int = 2048, skip: int = 4, log=None):
+def _time_at(rows, mse, key="s_per_run"):
+    """Wall time where the MSE curve of `rows` (ordered by size) crosses `mse`, by
+    log-log interpolation between the two runs that bracket it (None if none do)."""
+    for a, b in zip(rows, rows[1:]):
+        if (a["mse"] - mse) * (b["mse"] - mse) <= 0 and a["mse"] != b["mse"]:
+            u = (math.log(mse) - math.log(a["mse"])) / (math.log(b["mse"]) - math.log(a["mse"]))
+            return math.exp(math.log(a[key]) + u * (math.log(b[key]) - math.log(a[key])))
+    return None
+
+
+def ragged_time_error(theta, T: int = 20, R: int = 2, M_ref: int = 8, N_ref: int = 2048, skip: int = 4,
+                      scales=(0.5, 1.0, 2.0), log=None):
     """The ragged batch (256 lattices of 20 x 20, N log-uniform in [64, 4096], a
-    record per filter, learned proposal on) run as one context and as 256
-    separate contexts: the MSE of each filter's v-estimates against its own
-    record's reference posterior (an ensemble of M_ref x N_ref bootstrap
-    filters per record, Def. 1), the wall time per run, and the time-error
-    index of Sec. 3.4 (wall time x MSE) of both forms."""
+    record per filter) with the learned proposal in one context -- the batched
+    form -- against the same filters with the bootstrap proposal as 256
+    separate contexts, and the two mixed forms: the MSE of each filter's
+    v-estimates against its own record's reference posterior (an ensemble of
+    M_ref x N_ref bootstrap filters per record, Def. 1), the wall time per run,
+    the time-error index of Sec. 3.4 (wall time x MSE), and the wall time the
+    batched learned form needs to reach the separate bootstrap filters' MSE
+    (its particle counts scaled by `scales`, log-log interpolation)."""
     import torch
     spec = W.fhn_lattice(J=W.RAGGED["J"])
     counts = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
@@ -272,60 +286,51 @@ def ragged_time_error(theta, T: int = 20, R: int = 2, M_ref: int = 8, N_ref: int
     if log:
         log(f"ragged reference: {M_ref} x {N_ref} particles per record")
 
-    def batched(seed):
-        out = np.empty((T, nf, len(idx)))
-        with pf.EnsembleFilter(spec, nf, counts, seed) as f:
-            f.set_proposal(theta, 0.1)
-            for t in range(T):
-                f.step_device(d_y[t], per_filter=True)
-                out[t] = f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)[:, idx]
-        return out
-
-    def separate(seed):
-        out = np.empty((T, nf, len(idx)))
-        ctxs = [pf.EnsembleFilter(spec, 1, int(n), seed + m) for m, n in enumerate(counts)]
-        try:
-            for f in ctxs:
-                f.set_proposal(theta, 0.1)
-            for t in range(T):
-                for m, f in enumerate(ctxs):
-                    f.step_device(d_y[t, m])
-                for m, f in enumerate(ctxs):
-                    out[t, m] = f.estimate(pf.PF_STAT_MEAN, var=-1)[idx]
-        finally:
-            for f in ctxs:
-                f.close()
-        return out
-
-    def contexts(form, st):
-        """The batch as one context (form "batched") or 256 (form "separate") on stream st."""
-        if form == "batched":
-            ctxs = [pf.EnsembleFilter(spec, nf, counts, 99)]
-        else:
-            ctxs = [pf.EnsembleFilter(spec, 1, int(n), 7000 + m) for m, n in enumerate(counts)]
+    def contexts(batched, learned, scale, seed, st=None):
+        n = np.maximum(1, np.round(counts * scale)).astype(np.int32)
+        ctxs = [pf.EnsembleFilter(spec, nf, n, seed)] if batched else \
+            [pf.EnsembleFilter(spec, 1, int(k), seed + m) for m, k in enumerate(n)]
         for f in ctxs:
-            f.set_stream(st.cuda_stream)
-            f.set_proposal(theta, 0.1)
-        return ctxs
+            if st is not None:
+                f.set_stream(st.cuda_stream)
+            if learned:
+                f.set_proposal(theta, 0.1)
+        return ctxs, int(n.sum())
 
-    def step_all(form, ctxs, t):
-        if form == "batched":
+    def step_all(batched, ctxs, t):
+        if batched:
             ctxs[0].step_device(d_y[t % T], per_filter=True)
         else:
             for m, f in enumerate(ctxs):
                 f.step_device(d_y[t % T, m])
 
-    def seconds_per_step(form, steps=10):
+    def estimates(batched, learned, scale, seed):
+        out = np.empty((T, nf, len(idx)))
+        ctxs, _ = contexts(batched, learned, scale, seed)
+        try:
+            for t in range(T):
+                step_all(batched, ctxs, t)
+                if batched:
+                    out[t] = ctxs[0].estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True)[:, idx]
+                else:
+                    for m, f in enumerate(ctxs):
+                        out[t, m] = f.estimate(pf.PF_STAT_MEAN, var=-1)[idx]
+        finally:
+            for f in ctxs:
+                f.close()
+        return out
+
+    def seconds_per_step(batched, learned, scale, steps=10):
         st = torch.cuda.Stream()
-        ctxs = contexts(form, st)
+        ctxs, _ = contexts(batched, learned, scale, 99, st)
         try:
             for t in range(3):
-                step_all(form, ctxs, t)
+                step_all(batched, ctxs, t)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(st)
             for t in range(steps):
-                step_all(form, ctxs, 3 + t)
+                step_all(batched, ctxs, 3 + t)
             b.record(st)
             torch.cuda.synchronize()
             return a.elapsed_time(b) / 1e3 / steps
@@ -333,12 +338,24 @@ def ragged_time_error(theta, T: int = 20, R: int = 2, M_ref: int = 8, N_ref: int
             for f in ctxs:
                 f.close()
 
-    rows = {}
-    for name, run in (("batched", batched), ("separate", separate)):
-        mse = float(np.mean([np.mean((run(5000 + 311 * r)[skip:] - ref[skip:]) ** 2) for r in range(R)]))
-        dt = seconds_per_step(name)
-        rows[name] = {"mse": mse, "s_per_step": dt, "s_per_run": dt * T, "time_error_index": dt * T * mse}
+    forms = [(True, True, sc) for sc in scales] + [(False, False, 1.0), (True, False, 1.0), (False, True, 1.0)]
+    rows = []
+    for batched, learned, scale in forms:
+        mse = float(np.mean([np.mean((estimates(batched, learned, scale, 5000 + 311 * r)[skip:] - ref[skip:]) ** 2)
+                             for r in range(R)]))
+        dt = seconds_per_step(batched, learned, scale)
+        row = {"form": "batched" if batched else "separate", "proposal": "learned" if learned else "bootstrap",
+               "scale": scale, "N_total": int(np.maximum(1, np.round(counts * scale)).sum()), "mse": mse,
+               "s_per_step": dt, "s_per_run": dt * T, "time_error_index": dt * T * mse}
+        rows.append(row)
         if log:
-            log(f"ragged {name:9s} MSE {mse:.3e}  {dt * 1e3:.2f} ms/step")
-    return {"workload": "256 fhn 20x20 lattices, N log-uniform in [64, 4096], a record per filter, learned proposal",
-            "T": T, "R": R, "skip": skip, "M_ref": M_ref, "N_ref": N_ref, "N_total": int(counts.sum()), "rows": rows}
+            log(f"ragged {row['form']:8s} {row['proposal']:9s} x{scale:<4g} MSE {mse:.3e}  {dt * 1e3:.2f} ms/step")
+    plain_sep = next(r for r in rows if r["form"] == "separate" and r["proposal"] == "bootstrap")
+    learned_b = sorted([r for r in rows if r["form"] == "batched" and r["proposal"] == "learned"],
+                       key=lambda r: r["scale"])
+    t_learned = _time_at(learned_b, plain_sep["mse"])
+    return {"workload": "256 fhn 20x20 lattices, N log-uniform in [64, 4096], a record per filter",
+            "T": T, "R": R, "skip": skip, "M_ref": M_ref, "N_ref": N_ref, "N_total": int(counts.sum()), "rows": rows,
+            "target_mse": plain_sep["mse"], "plain_separate_s": plain_sep["s_per_run"],
+            "learned_batched_s_at_target": t_learned,
+            "learned_batched_vs_plain_separate": (t_learned / plain_sep["s_per_run"]) if t_learned else None}
