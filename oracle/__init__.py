@@ -253,7 +253,8 @@ def bf_run(spec, M: int, N, T: int, obs: np.ndarray, seed: int, resampler: str =
 
 
 class _OrcProposal(ctypes.Structure):
-    _fields_ = [("theta", ctypes.POINTER(ctypes.c_float)), ("bf16", ctypes.c_int32), ("ess_frac", ctypes.c_double)]
+    _fields_ = [("theta", ctypes.POINTER(ctypes.c_float)), ("bf16", ctypes.c_int32), ("ess_frac", ctypes.c_double),
+                ("span", ctypes.c_int32)]
 
 
 def mlp_forward_c(theta: np.ndarray, rows: np.ndarray, bf16: bool = True) -> np.ndarray:
@@ -261,15 +262,17 @@ def mlp_forward_c(theta: np.ndarray, rows: np.ndarray, bf16: bool = True) -> np.
     th = np.ascontiguousarray(theta, dtype=np.float32)
     rows = np.ascontiguousarray(rows, dtype=np.float64).reshape(-1, 51)
     out = np.empty((len(rows), 4))
-    pr = _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, 0.1)
+    pr = _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, 0.1, 1)
     lib().orc_mlp_forward(ctypes.byref(pr), ctypes.c_int64(len(rows)), _p(rows, ctypes.c_double),
                           _p(out, ctypes.c_double))
     return out
 
 
-def propagate_proposal(spec, theta, x: np.ndarray, pid, fid, t: int, seed: int, y: np.ndarray, bf16: bool = True):
-    """One interval of the learned-proposal filter for each particle row of x (lattice):
-    returns (proposed x, the transition's candidates xb, sum of log p - log q per row,
+def propagate_proposal(spec, theta, x: np.ndarray, pid, fid, t: int, seed: int, y: np.ndarray, bf16: bool = True,
+                       span: int = 1):
+    """One interval of the learned-proposal filter for each particle row of x (lattice), the proposal
+    acting on the last `span` sub-steps: returns (proposed x, the transition's candidates xb from the
+    state before the last sub-step, sum of log p - log q per row,
     network outputs o [n, dy, 4], normals and transition means zm [n, dy, 4], network
     inputs rows [n, dy, 51])."""
     md = _Model(spec)
@@ -279,7 +282,7 @@ def propagate_proposal(spec, theta, x: np.ndarray, pid, fid, t: int, seed: int, 
     fid = np.ascontiguousarray(fid, dtype=np.int32)
     y = np.ascontiguousarray(y, dtype=np.float64)
     th = np.ascontiguousarray(theta, dtype=np.float32)
-    pr = _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, 0.0)
+    pr = _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, 0.0, int(span))
     xb, lw = np.empty_like(x), np.empty(n)
     o, zm, rows = np.empty((n, spec.dy, 4)), np.empty((n, spec.dy, 4)), np.empty((n, spec.dy, 51))
     lib().orc_propagate_proposal(md.ref, ctypes.byref(pr), ctypes.c_int64(n), _p(pid, ctypes.c_int32),
@@ -337,8 +340,9 @@ def sir_run(spec, M: int, N, T: int, obs: np.ndarray, seed: int, ess_threshold: 
 
 
 def bf_run_proposal(spec, theta, M: int, N, T: int, obs: np.ndarray, seed: int, est_idx=None, bf16: bool = True,
-                    ess_frac: float = 0.1, obs_per_filter: bool = False, threads: int = 0) -> dict:
-    """M filters with the learned proposal (lattice); theta None = bootstrap."""
+                    ess_frac: float = 0.1, obs_per_filter: bool = False, threads: int = 0, span: int = 1) -> dict:
+    """M filters with the learned proposal (lattice) acting on the last `span` sub-steps of each
+    interval (the fallback to the transition only for span 1); theta None = bootstrap."""
     md = _Model(spec)
     N = np.ascontiguousarray(np.broadcast_to(np.asarray(N, dtype=np.int32), (M,)), dtype=np.int32)
     est_idx = np.ascontiguousarray(range(spec.dx) if est_idx is None else est_idx, dtype=np.int32)
@@ -347,7 +351,7 @@ def bf_run_proposal(spec, theta, M: int, N, T: int, obs: np.ndarray, seed: int, 
     post, logG, ess = np.empty((T, M, ne)), np.empty((T, M)), np.empty((T, M))
     ens, fb = np.empty((T, ne)), np.empty((T, M))
     th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
-    pr = None if th is None else _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, ess_frac)
+    pr = None if th is None else _OrcProposal(_p(th, ctypes.c_float), 1 if bf16 else 0, ess_frac, int(span))
     nullp = ctypes.POINTER(ctypes.c_double)()
     lib().orc_bf_run_proposal(md.ref, ctypes.byref(pr) if pr is not None else None, ctypes.c_int32(M),
                               _p(N, ctypes.c_int32), ctypes.c_int32(T), _p(obs, ctypes.c_double),

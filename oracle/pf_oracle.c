@@ -383,6 +383,7 @@ typedef struct {
     const float *theta; /* W1 (128x51), b1, W2 (128x128), b2, W3 (4x128), b3 */
     int32_t bf16;       /* round weights and layer inputs to bfloat16          */
     double ess_frac;    /* fall back to the transition when ESS < ess_frac N    */
+    int32_t span;       /* the proposal acts on the last `span` sub-steps (1..K) */
 } orc_proposal;
 
 static double bf16r(double x)
@@ -439,58 +440,71 @@ void orc_patch_row(const orc_model *md, const double *x, int32_t node, double y,
     row[50] = y;
 }
 
-/* K - 1 ordinary sub-steps, then the last one with the proposal at the
- * observed nodes.  On return x holds the proposed state, xb (dx) the state
- * the transition alone would have produced, and *lw = sum (log p - log q).
+/* K - L ordinary sub-steps (L = pr->span, 1..K), then the network once, on
+ * the state reached and y, and the last L sub-steps with the proposal at the
+ * observed nodes: at each of them the node's (v, w) is drawn from
+ * N(m + h o_mu, (h e^s)^2) with the sub-step's own normal, m the transition
+ * mean and s = clip(o_s, -3, 3), the same outputs o for all L sub-steps; the
+ * other nodes take the transition.  On return x holds the proposed state,
+ * *lw = sum over the L sub-steps and observed nodes of (log p - log q), and
+ * xb (dx) the state the transition alone would have produced from the state
+ * before the last sub-step (the fallback's candidate; meaningful for L = 1).
  * o_rec (dy x 4) and zm_rec (dy x 4: the normals and the transition means of
- * (v, w)) receive the network outputs and what they act on, and row_rec
- * (dy x 51) the network inputs, when not NULL. */
+ * (v, w) at the last sub-step) receive the network outputs and what they act
+ * on, and row_rec (dy x 51) the network inputs, when not NULL. */
 static void propagate_proposal(const orc_model *md, const orc_proposal *pr, uint64_t seed, uint32_t c0,
                                uint32_t c2, int32_t t, const double *y, double *x, double *xb, double *lw,
                                double *z, double *f, double *o_rec, double *zm_rec, double *row_rec)
 {
     nstream ns;
     ns_init(&ns, seed, c0, (uint32_t)t, c2, ORC_STREAM_DYN);
-    const int K = md->K, dx = md->dx, nn = md->J * md->J;
-    for (int k = 0; k < K - 1; ++k) {
+    const int K = md->K, dx = md->dx, nn = md->J * md->J, dy = md->dy;
+    const int L = pr->span < 1 ? 1 : (pr->span > K ? K : pr->span);
+    for (int k = 0; k < K - L; ++k) {
         for (int v = 0; v < dx; ++v) z[v] = ns_get(&ns, (int64_t)k * dx + noise_slot(md, v));
         em_step(md, (int64_t)(t - 1) * K + k + 1, x, z, f);
     }
-    const int k = K - 1;
-    for (int v = 0; v < dx; ++v) z[v] = ns_get(&ns, (int64_t)k * dx + noise_slot(md, v));
-    drift(md, (int64_t)(t - 1) * K + k + 1, x, f);
-    const double h = md->sigma_dyn * sqrt(md->dt);
-    double row[MLP_IN], o[MLP_OUT];
-    *lw = 0.0;
-    /* observed nodes first, from the pre-step state */
-    double *prop = (double *)malloc(sizeof(double) * 2 * md->dy);
-    for (int j = 0; j < md->dy; ++j) {
-        const int nd = md->obs_idx[j];
-        orc_patch_row(md, x, nd, y[j], row);
+    /* the network, once, on the state before the proposed sub-steps */
+    double row[MLP_IN];
+    double *o = (double *)malloc(sizeof(double) * MLP_OUT * dy);
+    for (int j = 0; j < dy; ++j) {
+        orc_patch_row(md, x, md->obs_idx[j], y[j], row);
         if (row_rec) memcpy(row_rec + MLP_IN * j, row, sizeof(row));
-        orc_mlp_forward(pr, 1, row, o);
-        if (o_rec) memcpy(o_rec + 4 * j, o, sizeof(o));
-        for (int c = 0; c < 2; ++c) {
-            const int var = c * nn + nd;
-            const double m = x[var] + md->dt * f[var];
-            if (zm_rec) {
-                zm_rec[4 * j + c] = z[var];
-                zm_rec[4 * j + 2 + c] = m;
+        orc_mlp_forward(pr, 1, row, o + MLP_OUT * j);
+    }
+    if (o_rec) memcpy(o_rec, o, sizeof(double) * MLP_OUT * dy);
+    const double h = md->sigma_dyn * sqrt(md->dt);
+    double *prop = (double *)malloc(sizeof(double) * 2 * dy);
+    *lw = 0.0;
+    for (int k = K - L; k < K; ++k) {
+        for (int v = 0; v < dx; ++v) z[v] = ns_get(&ns, (int64_t)k * dx + noise_slot(md, v));
+        drift(md, (int64_t)(t - 1) * K + k + 1, x, f);
+        for (int j = 0; j < dy; ++j) {
+            const int nd = md->obs_idx[j];
+            for (int c = 0; c < 2; ++c) {
+                const int var = c * nn + nd;
+                const double m = x[var] + md->dt * f[var];
+                const double oo = o[MLP_OUT * j + 2 + c];
+                const double oc = oo < -MLP_CLAMP ? -MLP_CLAMP : (oo > MLP_CLAMP ? MLP_CLAMP : oo);
+                const double mu = m + h * o[MLP_OUT * j + c], sd = h * exp(oc);
+                const double xv = mu + sd * z[var];
+                prop[2 * j + c] = xv;
+                if (k == K - 1 && zm_rec) {
+                    zm_rec[4 * j + c] = z[var];
+                    zm_rec[4 * j + 2 + c] = m;
+                }
+                *lw += (-(xv - m) * (xv - m) / (2.0 * h * h) - log(h)) - (-(xv - mu) * (xv - mu) / (2.0 * sd * sd) - log(sd));
             }
-            const double oc = o[2 + c] < -MLP_CLAMP ? -MLP_CLAMP : (o[2 + c] > MLP_CLAMP ? MLP_CLAMP : o[2 + c]);
-            const double mu = m + h * o[c], sd = h * exp(oc);
-            const double xv = mu + sd * z[var];
-            prop[2 * j + c] = xv;
-            *lw += (-(xv - m) * (xv - m) / (2.0 * h * h) - log(h)) - (-(xv - mu) * (xv - mu) / (2.0 * sd * sd) - log(sd));
         }
+        for (int v = 0; v < dx; ++v) {
+            x[v] = x[v] + md->dt * f[v] + h * z[v];
+            if (k == K - 1) xb[v] = x[v];
+        }
+        for (int j = 0; j < dy; ++j)
+            for (int c = 0; c < 2; ++c) x[c * nn + md->obs_idx[j]] = prop[2 * j + c];
     }
-    for (int v = 0; v < dx; ++v) {
-        x[v] = x[v] + md->dt * f[v] + h * z[v];
-        xb[v] = x[v];
-    }
-    for (int j = 0; j < md->dy; ++j)
-        for (int c = 0; c < 2; ++c) x[c * nn + md->obs_idx[j]] = prop[2 * j + c];
     free(prop);
+    free(o);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -781,7 +795,9 @@ int orc_bf_run_proposal(const orc_model *md, const orc_proposal *pr, int32_t M, 
                 }
                 double np_[5];
                 orc_normalise(Nm, l, np_);
-                if (np_[4] < pr->ess_frac * (double)Nm) { /* the bootstrap proposal instead */
+                /* the bootstrap proposal instead; only a proposal on the last sub-step has the
+                   transition's candidate from the same state to fall back to */
+                if (pr->span <= 1 && np_[4] < pr->ess_frac * (double)Nm) {
                     used_fallback = 1;
                     memcpy(x, xb, sizeof(double) * Nm * dx);
                     memcpy(l, lb, sizeof(double) * Nm);

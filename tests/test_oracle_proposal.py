@@ -96,3 +96,37 @@ def test_bad_proposal_falls_back_to_the_transition(record):
     rb = oracle.bf_run(SPEC, M, N, T, record, seed=21, est_idx=[9])
     assert rp["fallback"].min() == 1.0
     assert np.array_equal(rp["est"], rb["est"])
+
+
+def test_zero_output_proposal_over_the_whole_interval_is_the_bootstrap_filter(record):
+    """The proposal acting on every sub-step of the interval (span K): with a zero
+    output layer each sub-step draws the transition's own value and log p - log q
+    is zero, so the filter is the bootstrap filter bit for bit."""
+    r0 = oracle.bf_run(SPEC, 6, 48, T, record, seed=3, est_idx=[9, 70])
+    r1 = oracle.bf_run_proposal(SPEC, mlp.init_params(7, out_scale=0.0), 6, 48, T, record, seed=3, est_idx=[9, 70],
+                                span=SPEC.K)
+    assert np.array_equal(r0["est"], r1["est"]) and np.array_equal(r0["log_G"], r1["log_G"])
+
+
+@pytest.mark.parametrize("span", [2, 20])
+def test_proposal_over_several_sub_steps_keeps_the_posterior(record, span):
+    """With the proposal on the last `span` sub-steps, the weights carry the product
+    over those sub-steps of p / q, and the ensemble mean agrees with the bootstrap
+    ensemble's (no fallback: only a last-sub-step proposal has one)."""
+    M, N = 600, 96
+    node = 9
+    rb = oracle.bf_run(SPEC, M, N, T, record, seed=31, est_idx=[node])
+    rp = oracle.bf_run_proposal(SPEC, _moderate_proposal(1), M, N, T, record, seed=32, est_idx=[node], ess_frac=0.5,
+                                span=span)
+    assert rp["fallback"].sum() == 0  # the threshold is ignored beyond the last sub-step
+    for t in range(T):
+        a, b = rb["est"][t, :, 0], rp["est"][t, :, 0]
+        se = math.sqrt(a.var() / M + b.var() / M)
+        assert abs(a.mean() - b.mean()) < 4.5 * se, (t, a.mean(), b.mean(), se)
+
+
+def test_span_one_is_the_last_sub_step_reading(record):
+    theta = _moderate_proposal(2)
+    a = oracle.bf_run_proposal(SPEC, theta, 4, 40, T, record, seed=5, est_idx=[9], ess_frac=0.0)
+    b = oracle.bf_run_proposal(SPEC, theta, 4, 40, T, record, seed=5, est_idx=[9], ess_frac=0.0, span=1)
+    assert np.array_equal(a["est"], b["est"]) and np.array_equal(a["log_G"], b["log_G"])
