@@ -655,8 +655,9 @@ def time_to_mse_block():
     """Short seeded studies of the wall time to reach a fixed MSE.
 
     config4: the 40 x 40 lattice at M = 32: MSE of the averaged v-estimates against
-    a large-ensemble reference for the plain, learned-proposal and auxiliary
-    ensembles at N = 256, 512, 1024, and the wall time each needs to reach the
+    a large-ensemble reference for the plain, learned-proposal (on the last
+    sub-step, and on every sub-step of the interval) and auxiliary ensembles at
+    N = 256, 512, 1024, and the wall time each needs to reach the
     plain ensemble's MSE at N = 1024 (log-log interpolation between the runs that
     bracket it).
     config5: the ragged batch of 256 20 x 20 lattices: the learned proposal in one
@@ -668,14 +669,16 @@ def time_to_mse_block():
     spec = W.fhn_lattice()
     train_record = pf.pf_simulate(spec, 20, W.SEED_FHN_OBS, record=1)[1]  # not the scored record
     theta = proposal.trained_theta(spec, train_record, seed=77)
+    theta_interval = proposal.trained_theta(spec, train_record, seed=78, span=spec.K)
     r = study.lattice_time_to_mse(theta, Ns=(256, 512, 1024), R=4, T=30, M_ref=512, N_ref=1024, ref_seeds=(951,),
-                                  skip=5, methods=("plain", "learned", "auxiliary"))
+                                  skip=5, methods=("plain", "learned", "auxiliary"), theta_interval=theta_interval)
     plain = r["plain_s_at_target"]
     c4 = {
         "workload": "fhn 40x40 lattice, M=32 ensembles of N in {256, 512, 1024}; R=4 ensembles per point, T=30 "
                     "observations (the first 5 not scored), reference: 512 x 1024 bootstrap ensemble",
         "target_mse": r["target_mse"], "plain_s": plain,
         "learned_s": r["learned_s_at_target"], "auxiliary_s": r["auxiliary_s_at_target"],
+        "learned_interval_s": r["learned_interval_s_at_target"],
         "learned_vs_plain": (r["learned_s_at_target"] / plain) if r["learned_s_at_target"] else None,
         "auxiliary_vs_plain": (r["auxiliary_s_at_target"] / plain) if r["auxiliary_s_at_target"] else None,
         "rows": {k: [{kk: row[kk] for kk in ("N", "mse", "s_per_run", "mean_ess_frac")} for row in v]

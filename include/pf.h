@@ -452,6 +452,20 @@ PF_API void pf_mlp_trainer_destroy(pf_mlp_trainer *tr);
  * PF_EUNSUPPORTED (not a lattice), PF_ENOMEM, PF_ESTATE. */
 PF_API pf_status pf_set_proposal(pf_ctx *ctx, const float *h_theta, int32_t n_params, double ess_frac);
 
+/* How much of each observation interval the learned proposal acts on: the
+ * last `span` Euler-Maruyama sub-steps (1 <= span <= steps_per_obs; default 1,
+ * the last sub-step).  The network is evaluated once per interval, on the
+ * state before the first of them and y; at each of them the observed nodes
+ * draw from N(m + h o_mu, (h e^{clip(o_s)})^2) with that sub-step's normal and
+ * transition mean m, and the weights carry g times the product over the span
+ * of p / q.  Only a span of one has a fallback to the transition (its
+ * candidate comes from the same state); for longer spans ess_frac is
+ * ignored.  Tuple recording builds its network inputs from the state before
+ * the span, with the residual of the last sub-step as the target.  Spans
+ * above one need J divisible by 4.  Synchronises.  Errors: PF_EINVAL,
+ * PF_EUNSUPPORTED, PF_ESTATE. */
+PF_API pf_status pf_set_proposal_span(pf_ctx *ctx, int32_t span);
+
 /* Records training tuples for the proposal network during the following
  * steps (lattice contexts): for every resampled particle whose filter-local
  * index is a multiple of `stride` and every observed node, the 51 network

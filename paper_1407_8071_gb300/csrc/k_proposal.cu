@@ -193,11 +193,20 @@ __global__ void __launch_bounds__(1024, 2) k_last_step_fhn(ModelParams mp, Key k
 // pair kernel's bit for bit, with four CTAs or three per SM instead of two.
 constexpr int kLast4MaxThreads = 512;
 
+// Sub-step k_sub of the proposal's span (the last `span` sub-steps of the
+// interval, sharing one network evaluation): the transition at unobserved
+// nodes, the proposal at observed ones.  The span's sums of log p - log q are
+// carried in lw_acc from its first sub-step (first) to its last (last), which
+// adds log g and writes the step's log-weights; a span of one sub-step is the
+// last-sub-step reading (first = last = 1), the only one whose transition
+// candidates (xboot, logw_boot) serve a fallback.
+
 template <int MinB>
 __global__ void __launch_bounds__(kLast4MaxThreads, MinB)
     k_last_step_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt, float *x, int64_t P,
                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
-                     const float *mlp_out, float *xboot, float *mp_obs, float *logw, float *logw_boot)
+                     const float *mlp_out, float *xboot, float *mp_obs, float *logw, float *logw_boot,
+                     int32_t k_sub, int32_t first, int32_t last, float *lw_acc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int J = mp.J, nn = J * J, quads = nn / 4, pairs = nn / 2, qrow = J / 4, dy = mp.dy;
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(kLast4MaxThreads, MinB)
     const int64_t p = (int64_t)blockIdx.x * ppc + s;
     const bool active = (s < ppc) && (p < P);
     const uint32_t t = (uint32_t)(*d_t + 1);
-    const int k = mp.K - 1;
+    const int k = k_sub;
     uint32_t c0 = 0, c2 = 0;
     float v[4] = {0.f, 0.f, 0.f, 0.f}, w[4] = {0.f, 0.f, 0.f, 0.f};
     const int n0 = 4 * q, row = n0 / J, col = n0 - row * J;
@@ -321,8 +330,14 @@ __global__ void __launch_bounds__(kLast4MaxThreads, MinB)
             c += __shfl_xor_sync(0xffffffffu, c, o);
         }
         if (lane == 0 && pp < P) {
-            logw[pp] = mp.fhalf_prec * a + c;
-            logw_boot[pp] = mp.fhalf_prec * b;
+            // the sub-step's sum of log p - log q joins those of the span's earlier sub-steps
+            const float cs = first ? c : lw_acc[pp] + c;
+            if (last) {
+                logw[pp] = mp.fhalf_prec * a + cs;
+                logw_boot[pp] = mp.fhalf_prec * b;
+            } else {
+                lw_acc[pp] = cs;
+            }
         }
     }
 }
@@ -461,9 +476,11 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
     const int ppc = n;
     const int threads = (ppc * pairs + 31) / 32 * 32;
     const unsigned grid = (unsigned)((c.P + ppc - 1) / ppc);
-    // K - 1 ordinary sub-steps (no weights yet)
-    if (c.mp.K > 1) {
-        cudaError_t e = launch_fhn_substeps(c, d_obs, stride, x, c.mp.K - 1, s);
+    // K - L ordinary sub-steps (no weights yet), L = the proposal's span; recording builds its
+    // network inputs at the same place (without a network the span's sub-steps are the transition's)
+    const int L = c.prop_span;
+    if (c.mp.K > L) {
+        cudaError_t e = launch_fhn_substeps(c, d_obs, stride, x, c.mp.K - L, s);
         if (e != cudaSuccess) return e;
     }
     const float *mo = nullptr;
@@ -478,7 +495,7 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
         if (e != cudaSuccess) return e;
         mo = c.mlp_out;
     }
-    if (c.fhn_nodes != 2 && c.mp.J % 4 == 0) {  // four nodes per thread, as the sub-steps
+    if ((c.fhn_nodes != 2 || L > 1) && c.mp.J % 4 == 0) {  // four nodes per thread, as the sub-steps
         const int quads = c.mp.J * c.mp.J / 4;
         int n4 = 1;
         while ((n4 + 1) * quads <= kLast4MaxThreads && n4 < 8) ++n4;
@@ -486,21 +503,26 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
         const int threads4 = (n4 * quads + 31) / 32 * 32;
         const unsigned grid4 = (unsigned)((c.P + n4 - 1) / n4);
         const size_t smem4 = (size_t)3 * n4 * pairs * sizeof(float);  // >= the v-planes (n4 * J * J floats)
-        if (c.fhn_quad_ctas == 4)
-            k_last_step_fhn4<4><<<grid4, threads4, smem4, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
-                                                               c.obs_slot, c.d_t, n4, mo, c.xboot, c.mp_obs, c.logw,
-                                                               c.logw_boot);
-        else
-            k_last_step_fhn4<3><<<grid4, threads4, smem4, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
-                                                               c.obs_slot, c.d_t, n4, mo, c.xboot, c.mp_obs, c.logw,
-                                                               c.logw_boot);
+        for (int k = c.mp.K - L; k < c.mp.K; ++k) {
+            const int32_t first = k == c.mp.K - L, last = k == c.mp.K - 1;
+            if (c.fhn_quad_ctas == 4)
+                k_last_step_fhn4<4><<<grid4, threads4, smem4, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
+                                                                   c.obs_slot, c.d_t, n4, mo, c.xboot, c.mp_obs,
+                                                                   c.logw, c.logw_boot, k, first, last, c.lw_acc);
+            else
+                k_last_step_fhn4<3><<<grid4, threads4, smem4, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
+                                                                   c.obs_slot, c.d_t, n4, mo, c.xboot, c.mp_obs,
+                                                                   c.logw, c.logw_boot, k, first, last, c.lw_acc);
+        }
     } else {
         const size_t smem_last = std::max((size_t)ppc * pairs * sizeof(float2), (size_t)3 * threads * sizeof(float));
         k_last_step_fhn<<<grid, threads, smem_last, s>>>(c.mp, c.key, c.pfilt, c.filt, x, c.P, d_obs, stride,
                                                          c.obs_slot, c.d_t, ppc, mo, c.xboot, c.mp_obs, c.logw,
                                                          c.logw_boot);
     }
-    k_proposal_select<<<c.M, 256, 0, s>>>(c.filt, c.mp, c.prop_ess_frac, c.prop_on ? 1 : 0, c.logw, c.logw_boot, x,
+    // a fallback needs the transition's candidates from the same state: only for a span of one
+    const float ess_frac = L == 1 ? c.prop_ess_frac : 0.0f;
+    k_proposal_select<<<c.M, 256, 0, s>>>(c.filt, c.mp, ess_frac, c.prop_on ? 1 : 0, c.logw, c.logw_boot, x,
                                           c.xboot, c.obs_idx, c.fmax_key, c.fstats);
     const int64_t rows = c.P * c.mp.dy;
     k_proposal_fixup<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(c.pfilt, c.mp, c.P, c.fstats, x, c.xboot,

@@ -970,6 +970,7 @@ static pf_status ensure_proposal_buffers(Ctx &c)
                     alloc_n(c, c.wpack, (size_t)(128 * 64 + 128 * 128 + 8 * 128) + 128 * 128) &&
                     alloc_n(c, c.rows, R * 64) && alloc_n(c, c.mlp_out, R * 4) && alloc_n(c, c.xboot, R * 2) &&
                     alloc_n(c, c.mp_obs, R * 2) && alloc_n(c, c.logw_boot, (size_t)c.P) &&
+                    alloc_n(c, c.lw_acc, (size_t)c.P) &&
                     alloc_n(c, c.rec_sel_off, (size_t)c.M);
     return ok ? PF_OK : fail(c, PF_ENOMEM, "proposal buffers: device allocation failed");
 }
@@ -1000,6 +1001,22 @@ pf_status pf_set_proposal(pf_ctx *h, const float *h_theta, int32_t n_params, dou
     if (e != cudaSuccess) return cuda_fail(c, e, "set_proposal");
     c.prop_on = true;
     c.prop_ess_frac = (float)ess_frac;
+    return PF_OK;
+}
+
+pf_status pf_set_proposal_span(pf_ctx *h, int32_t span)
+{
+    if (!h) return PF_EINVAL;
+    Ctx &c = h->c;
+    if (c.fatal) return fail(c, PF_ESTATE, "context is in an error state: " + c.last_error);
+    if (c.phase != 0) return fail(c, PF_ESTATE, "pf_set_proposal_span between pf_propagate and pf_resample");
+    if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "the learned proposal is for the lattice");
+    if (span < 1 || span > c.mp.K) return fail(c, PF_EINVAL, "span must be in [1, steps_per_obs]");
+    if (span > 1 && c.mp.J % 4 != 0) return fail(c, PF_EUNSUPPORTED, "a span above one needs J divisible by 4");
+    pf_status st = sync(c, "set_proposal_span");
+    if (st != PF_OK) return st;
+    drop_graphs(c);
+    c.prop_span = span;
     return PF_OK;
 }
 

@@ -247,6 +247,8 @@ struct Ctx {
     float *xboot = nullptr;           // [P][dy][2] the transition's candidates at the observed nodes
     float *mp_obs = nullptr;          // [P][dy][2] transition means at the observed nodes
     float *logw_boot = nullptr;       // [P]
+    float *lw_acc = nullptr;          // [P] log p - log q of the span's earlier sub-steps
+    int32_t prop_span = 1;            // the proposal acts on the last prop_span sub-steps (pf_set_proposal_span)
     float *rec_X = nullptr, *rec_R = nullptr;  // caller's tuple buffers (recording armed when non-null)
     int64_t rec_cap = 0, rec_count = 0, rec_sel_total = 0;
     int32_t rec_stride = 1;

@@ -81,6 +81,7 @@ _SIGS = {
     "pf_set_resampling": (c_int32, [c_void_p, c_double]),
     "pf_autotune": (c_int32, [c_void_p, POINTER(c_int32)]),
     "pf_set_proposal": (c_int32, [c_void_p, POINTER(c_float), c_int32, c_double]),
+    "pf_set_proposal_span": (c_int32, [c_void_p, c_int32]),
     "pf_record_tuples": (c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32]),
     "pf_recorded_tuples": (c_int32, [c_void_p, POINTER(c_int64)]),
     "pf_proposal_forward": (c_int32, [c_int32, c_int64, c_void_p, c_int32, POINTER(c_int32), c_void_p, c_void_p,
@@ -474,6 +475,10 @@ class EnsembleFilter:
             return
         th = np.ascontiguousarray(theta, dtype=np.float32)
         _check(lib().pf_set_proposal(self.h, _fp(th), th.size, float(ess_frac)), self.h)
+
+    def set_proposal_span(self, span: int = 1):
+        """The learned proposal acts on the last `span` sub-steps of each interval (1: the last one)."""
+        _check(lib().pf_set_proposal_span(self.h, int(span)), self.h)
 
     def record_tuples(self, d_X, d_R, stride: int = 1):
         """Record (inputs, standardised residual) training tuples into device tensors (None stops)."""

@@ -19,14 +19,17 @@ from . import workloads as W
 
 
 def collect_tuples(spec: W.ModelSpec, M: int, N: int, record: np.ndarray, seed: int, capacity: int,
-                   stride: int = 1, steps: int | None = None):
+                   stride: int = 1, steps: int | None = None, span: int = 1):
     """Runs the bootstrap filter over the record and returns (X, R) device tensors
-    (capacity x 51 and capacity x 2) holding the first `count` tuples, and count."""
+    (capacity x 51 and capacity x 2) holding the first `count` tuples, and count.
+    The network inputs are taken before the last `span` sub-steps of each
+    interval (where a proposal of that span evaluates its network)."""
     import torch
     X = torch.empty((capacity, 51), dtype=torch.float32, device="cuda")
     R = torch.empty((capacity, 2), dtype=torch.float32, device="cuda")
     steps = len(record) if steps is None else steps
     with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.set_proposal_span(span)
         f.record_tuples(X, R, stride=stride)
         for t in range(steps):
             f.step(record[t])
@@ -89,8 +92,9 @@ def initial_theta(seed: int) -> np.ndarray:
 
 
 def trained_theta(spec: W.ModelSpec, record: np.ndarray, seed: int, tuples: int = 300_000, epochs: int = 2,
-                  M: int = 16, N: int = 256, stride: int = 4) -> np.ndarray:
-    """Collect tuples with the plain filter on `record`, then train from initial_theta."""
-    X, R, n = collect_tuples(spec, M, N, record, seed=seed, capacity=tuples, stride=stride)
+                  M: int = 16, N: int = 256, stride: int = 4, span: int = 1) -> np.ndarray:
+    """Collect tuples with the plain filter on `record`, then train from initial_theta
+    (for a proposal acting on the last `span` sub-steps of each interval)."""
+    X, R, n = collect_tuples(spec, M, N, record, seed=seed, capacity=tuples, stride=stride, span=span)
     theta, _ = train(initial_theta(seed), X, R, epochs=epochs, batch=8192, lr=1e-3)
     return theta

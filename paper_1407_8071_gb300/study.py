@@ -35,7 +35,7 @@ def _var_index(spec: W.ModelSpec):
 
 
 def filter_estimates(spec: W.ModelSpec, M: int, N, seed: int, d_y, theta=None, ess_frac: float = 0.1,
-                     want_ess: bool = False, aux: bool = False, tau: float = -1.0):
+                     want_ess: bool = False, aux: bool = False, tau: float = -1.0, span: int = 1):
     """Per-filter posterior means of the scored statistics at every observation
     time: array (T, M, n_stat); optionally the per-filter ESS (T, M)."""
     idx = _var_index(spec)
@@ -45,6 +45,7 @@ def filter_estimates(spec: W.ModelSpec, M: int, N, seed: int, d_y, theta=None, e
     with pf.EnsembleFilter(spec, M, N, seed) as f:
         if theta is not None:
             f.set_proposal(theta, ess_frac)
+            f.set_proposal_span(span)
         if aux:
             f.set_auxiliary(True)
         f.set_resampling(tau)
@@ -70,7 +71,7 @@ def reference_posterior(spec: W.ModelSpec, N_ref: int, seeds, d_y):
 
 
 def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, warmup: int = 3,
-              aux: bool = False, tau: float = -1.0) -> float:
+              aux: bool = False, tau: float = -1.0, span: int = 1) -> float:
     """Device seconds per observation step of one M-filter context (CUDA events)."""
     import torch
     st = torch.cuda.Stream()
@@ -78,6 +79,7 @@ def step_time(spec: W.ModelSpec, M: int, N, d_y, theta=None, steps: int = 20, wa
         f.set_stream(st.cuda_stream)
         if theta is not None:
             f.set_proposal(theta, 0.1)
+            f.set_proposal_span(span)
         if aux:
             f.set_auxiliary(True)
         f.set_resampling(tau)
@@ -151,7 +153,8 @@ ALL_METHODS = ("plain", "learned", "auxiliary", "adaptive", "centralised")
 
 
 def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8, T: int = 40, M_ref: int = 1024,
-                        N_ref: int = 1024, ref_seeds=(951, 952), skip: int = 5, log=None, methods=ALL_METHODS):
+                        N_ref: int = 1024, ref_seeds=(951, 952), skip: int = 5, log=None, methods=ALL_METHODS,
+                        theta_interval=None):
     """Plain bootstrap vs learned proposal on the 40 x 40 lattice: MSE of the
     averaged v-estimates (every node) against a reference posterior, wall time
     per run, and the wall time the learned form needs to reach the plain
@@ -169,18 +172,21 @@ def lattice_time_to_mse(theta, Ns=(128, 256, 512, 1024), M: int = 32, R: int = 8
     d_y = torch.from_numpy(np.ascontiguousarray(y)).cuda()
     ref = ensemble_reference(spec, M_ref, N_ref, ref_seeds, d_y)
     out = {}
-    for name, th, m_run, aux, tau in (("plain", None, M, False, -1.0), ("learned", theta, M, False, -1.0),
-                                      ("auxiliary", None, M, True, -1.0), ("adaptive", None, M, False, 0.5),
-                                      ("centralised", None, 1, False, -1.0)):
-        if name not in methods:
+    runs = [("plain", None, M, False, -1.0, 1), ("learned", theta, M, False, -1.0, 1),
+            ("auxiliary", None, M, True, -1.0, 1), ("adaptive", None, M, False, 0.5, 1),
+            ("centralised", None, 1, False, -1.0, 1)]
+    if theta_interval is not None:  # the proposal over the whole interval (every sub-step)
+        runs.insert(2, ("learned_interval", theta_interval, M, False, -1.0, spec.K))
+    for name, th, m_run, aux, tau, span in runs:
+        if name not in methods and not (name == "learned_interval" and theta_interval is not None):
             continue
         rows = []
         for N in Ns:
             n_run = N * M // m_run
             est, ess = filter_estimates(spec, R * m_run, n_run, 2000 + N + 7 * m_run, d_y, theta=th, want_ess=True,
-                                        aux=aux, tau=tau)
+                                        aux=aux, tau=tau, span=span)
             mse, var, bias2, _ = ensemble_mse(est, m_run, ref, skip=skip)
-            dt = step_time(spec, m_run, n_run, d_y, theta=th, aux=aux, tau=tau)
+            dt = step_time(spec, m_run, n_run, d_y, theta=th, aux=aux, tau=tau, span=span)
             rows.append({"M": m_run, "N": n_run, "mse": mse, "var": var, "bias2": bias2, "s_per_step": dt,
                          "s_per_run": dt * T, "mean_ess_frac": float(np.mean(ess[skip:]) / n_run),
                          "time_error_index": dt * T * mse})

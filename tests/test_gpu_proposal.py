@@ -182,10 +182,10 @@ def test_trained_network_gains_where_the_transition_noise_sits_in_the_last_sub_s
         assert abs(a.mean() - b.mean()) < 4.5 * se, (t, a.mean(), b.mean(), se)
 
 
-def _one_proposal_interval(J, K, theta, M, N, seed=77):
+def _one_proposal_interval(J, K, theta, M, N, seed=77, span=1):
     """From identical FP32 states, one observation interval with the proposal on
-    (no fallback): the GPU's proposed states and log-weights, and the oracle's
-    proposal step from the same states."""
+    its last `span` sub-steps (no fallback): the GPU's proposed states and
+    log-weights, and the oracle's proposal step from the same states."""
     spec = W.fhn_lattice(J=J, K=K)
     _, y = oracle.simulate(spec, 3, W.SEED_FHN_OBS)
     y32 = y.astype(np.float32)
@@ -193,12 +193,14 @@ def _one_proposal_interval(J, K, theta, M, N, seed=77):
         f.step(y32[0])
         x0 = f.get_state()
         f.set_proposal(theta, 0.0)
+        f.set_proposal_span(span)
         f.propagate(y32[1])
         xg = f.get_state().astype(np.float64)
         lg = f.get_logw().astype(np.float64)
     pid, fid = np.tile(np.arange(N), M), np.repeat(np.arange(M), N)
     y1 = y32[1].astype(np.float64)
-    xo, xb, lw, o, zm, rows = oracle.propagate_proposal(spec, theta, x0.astype(np.float64), pid, fid, 2, seed, y1)
+    xo, xb, lw, o, zm, rows = oracle.propagate_proposal(spec, theta, x0.astype(np.float64), pid, fid, 2, seed, y1,
+                                                        span=span)
     lo = oracle.loglik(spec, xo, y1) + lw
     return spec, x0, xg, lg, xo, lo, o, zm, rows, y1
 
@@ -281,3 +283,64 @@ def test_proposal_step_matches_oracle_elementwise(J, K, N):
     assert np.all(d <= dx + 1e-12), np.max(d / dx)
     assert np.mean(d > dx_nf + 1e-12) <= 0.02, np.mean(d > dx_nf)
     assert np.all(np.abs(lg - lo) <= dl + 1e-9), np.max(np.abs(lg - lo) / dl)
+
+
+def test_zero_network_over_the_whole_interval_is_the_bootstrap_filter(record):
+    M, N, seed = 3, 70, 5
+    e0, _, x0 = _run(SPEC, M, N, seed, record)
+    with pf.EnsembleFilter(SPEC, M, N, seed) as f:
+        f.set_proposal(mlp.init_params(1, out_scale=0.0), 0.1)
+        f.set_proposal_span(SPEC.K)
+        est = []
+        for t in range(len(record)):
+            f.step(record[t])
+            est.append(f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True))
+        x1 = f.get_state()
+    assert np.array_equal(e0, np.array(est)) and np.array_equal(x0, x1)
+
+
+@pytest.mark.parametrize("span", [2, 20])
+def test_proposal_over_several_sub_steps_with_exact_network_outputs(span):
+    """The proposal on the last `span` sub-steps with outputs known exactly on both
+    sides (W3 = 0): states within 1e-5 relative, log-weights within the FP32
+    accumulation bound of their terms over the span's sub-steps."""
+    th = mlp.unpack(mlp.init_params(1, out_scale=0.0))
+    th["b3"] = np.array([0.35, -0.25, 0.4, -0.3])
+    theta = mlp.pack(th).astype(np.float32).astype(np.float64)
+    spec, x0, xg, lg, xo, lo, o, zm, rows, y1 = _one_proposal_interval(8, 20, theta, 2, 64, span=span)
+    assert np.max(_rel(xg, xo)) <= 1e-5
+    lgx = oracle.loglik(spec, xo, y1)
+    lw = lo - lgx  # the oracle's sum over the span of log p - log q
+    # Bound: FP32 accumulation of the dy log g terms and of the 2 dy span terms s + z^2/2 - r^2/2, plus,
+    # per term, the rounding of r = (x' - m) / h formed from FP32 x' and m: |dr| <= 2^-22 (|m| + |x'|) / h,
+    # moving the term by at most (|r| + |dr|) |dr|, with |r| <= |o_mu| + e^s |z| and |z| <= 6.
+    h = spec.sigma_dyn * np.sqrt(spec.dt)
+    n_terms = 2 * spec.dy * span
+    dr = 2.0 ** -22 * 2.0 * np.max(np.abs(xo)) / h
+    r_max = np.max(np.abs(th["b3"][:2]) + np.exp(np.clip(th["b3"][2:], -3, 3)) * 6.0)
+    q_max = 3.0 + 18.0 + r_max ** 2 / 2.0
+    tol = (_mlp_bounds.gamma(spec.dy + n_terms) * (np.abs(lgx) + n_terms * q_max)
+           + n_terms * (r_max + dr) * dr + 1e-5 * (np.abs(lgx) + 1.0))
+    assert np.all(np.abs(lg - lo) <= tol), np.max(np.abs(lg - lo) / tol)
+    # the bound is far below what a wrong term would move: dropping z^2/2 alone shifts by ~ n_terms / 2
+    assert np.max(tol) < 0.05 * n_terms
+
+
+def test_proposal_over_the_whole_interval_matches_the_oracle_statistically(record):
+    theta = _moderate_proposal()
+    T = 4
+    y = record[:T]
+    M, N, node = 1000, 48, 9
+    with pf.EnsembleFilter(SPEC, M, N, 31) as f:
+        f.set_proposal(theta, 0.0)
+        f.set_proposal_span(SPEC.K)
+        eg = []
+        for t in range(T):
+            f.step(y[t])
+            eg.append(f.estimate(pf.PF_STAT_MEAN, var=node, per_filter=True))
+    ro = oracle.bf_run_proposal(SPEC, theta, M, N, T, y.astype(np.float64), seed=32, est_idx=[node], ess_frac=0.0,
+                                span=SPEC.K)
+    for t in range(T):
+        a, b = eg[t], ro["est"][t, :, 0]
+        se = math.sqrt(a.var() / M + b.var() / M)
+        assert abs(a.mean() - b.mean()) < 4.5 * se, (t, a.mean(), b.mean(), se)
