@@ -265,6 +265,7 @@ struct Grid {
     uint32_t U;     // u = U 2^-32
     int64_t N;
     float ratio;    // N / Ctot in FP32: only the starting point of the exact division below
+    U128 UC;        // U Ctot
 };
 
 // A 64-bit unsigned value as FP32 from its two 32-bit halves: 64-bit integer
@@ -281,6 +282,7 @@ __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
     g.U = U;
     g.N = N;
     g.ratio = __int2float_rn((int32_t)N) / u64_to_f32(g.Ctot);
+    g.UC = mul64((uint64_t)U, g.Ctot);
     return g;
 }
 
@@ -292,7 +294,13 @@ __device__ __forceinline__ Grid make_grid(uint64_t Ctot, uint32_t U, int64_t N)
 // error about 3e-7, so within a few units of Q for N <= 2^24) and is corrected
 // exactly: R = x N - Q Ctot is formed modulo 2^64, which is exact while
 // |R| < 2^63 (here |R| < 8 Ctot), and moved into [0, Ctot) by whole steps.
-__device__ __forceinline__ int64_t count_below(uint64_t x, const Grid &g)
+// The division x N = Q Ctot + R of a prefix value, kept as the prefix grows.
+struct Counter {
+    int64_t Q;
+    uint64_t R;  // 0 <= R < Ctot
+};
+
+__device__ __forceinline__ Counter counter_at(uint64_t x, const Grid &g)
 {
     const float qf = fminf(floorf(u64_to_f32(x) * g.ratio), (float)g.N);
     int64_t Q = qf > 0.0f ? (int64_t)__float2int_rz(qf) : 0;
@@ -306,10 +314,32 @@ __device__ __forceinline__ int64_t count_below(uint64_t x, const Grid &g)
         ++Q;
         R -= C;
     }
-    const U128 rhs = mul64((uint64_t)g.U, g.Ctot);
-    const uint64_t lhi = (uint64_t)R >> 32, llo = (uint64_t)R << 32;
-    Q += (lhi > rhs.hi || (lhi == rhs.hi && llo > rhs.lo)) ? 1 : 0;
-    return Q < g.N ? Q : g.N;
+    return Counter{Q, (uint64_t)R};
+}
+
+// #{i : t_i < x} from x's division: Q + [R 2^32 > U Ctot], at most N.
+__device__ __forceinline__ int64_t counter_value(const Counter &c, const Grid &g)
+{
+    const uint64_t lhi = c.R >> 32, llo = c.R << 32;
+    const int64_t n = c.Q + ((lhi > g.UC.hi || (lhi == g.UC.hi && llo > g.UC.lo)) ? 1 : 0);
+    return n < g.N ? n : g.N;
+}
+
+// The prefix grew by q to x: R grows by q N (< 2^53, since q <= 2^(52 - L) and
+// N <= 2^L), which moves Q by its expected offspring count -- whole steps while
+// that is small, the division afresh otherwise.
+__device__ __forceinline__ void counter_add(Counter &c, uint64_t q, uint64_t x, const Grid &g)
+{
+    uint64_t R = c.R + q * (uint64_t)g.N;
+    if (R < 8 * g.Ctot) {
+        while (R >= g.Ctot) {
+            R -= g.Ctot;
+            ++c.Q;
+        }
+        c.R = R;
+    } else {
+        c = counter_at(x, g);
+    }
 }
 
 // Unnormalised FP32 weight exp(l - max) from the FP32 log-weight; non-finite
@@ -936,14 +966,16 @@ __global__ void __launch_bounds__(kResampleThreads) k_scan_scatter(ResampleArgs 
     for (int r = 0; r < IT; ++r) tsum += q[r];
     // the prefix C_k stays in registers: nothing after the counts reads it
     uint64_t Cprev = Cbefore + block_exscan_u64(tsum, shu + 2 * kWarps);  // C_{k-1} before my first item
-    int64_t cnt_prev = count_below(Cprev, g);
+    Counter cn = counter_at(Cprev, g);
+    int64_t cnt_prev = counter_value(cn, g);
 #pragma unroll
     for (int r = 0; r < IT; ++r) {
         const int j = j0 + r;
         if (j >= td.len) break;
         const uint64_t Ck = Cprev + q[r];
         if (q[r] > 0) {
-            const int64_t cnt = count_below(Ck, g);
+            counter_add(cn, q[r], Ck, g);
+            const int64_t cnt = counter_value(cn, g);
             if (cnt > cnt_prev) {
                 a.B[fd.off + cnt_prev] = td.lstart + j;
                 // the outputs [cnt_prev, cnt) descend from this particle: it is the first
@@ -1195,14 +1227,16 @@ __global__ void __launch_bounds__(kTile / IT, 8) k_resample_whole(ResampleArgs a
             tsum += q[r];
         }
         uint64_t Cprev = block_exscan_u64(tsum, shu + kWarps);
-        int64_t cnt_prev = count_below(Cprev, g);
+        Counter cn = counter_at(Cprev, g);
+        int64_t cnt_prev = counter_value(cn, g);
 #pragma unroll
         for (int r = 0; r < IT; ++r) {
             const int j = j0 + r;
             if (j >= td.len) break;
             const uint64_t Ck = Cprev + q[r];
             if (q[r] > 0) {
-                const int64_t cnt = count_below(Ck, g);
+                counter_add(cn, q[r], Ck, g);
+                const int64_t cnt = counter_value(cn, g);
                 if (cnt > cnt_prev) shB[cnt_prev] = j;
                 cnt_prev = cnt;
             }
@@ -1363,14 +1397,16 @@ __global__ void __launch_bounds__(32 * kWarpFilters, 8) k_resample_warp(Resample
             tsum += q[r];
         }
         uint64_t Cprev = warp_exscan_u64(tsum, lane);
-        int64_t cnt_prev = count_below(Cprev, g);
+        Counter cn = counter_at(Cprev, g);
+        int64_t cnt_prev = counter_value(cn, g);
 #pragma unroll
         for (int r = 0; r < IT; ++r) {
             const int j = j0 + r;
             if (j >= td.len) break;
             const uint64_t Ck = Cprev + q[r];
             if (q[r] > 0) {
-                const int64_t cnt = count_below(Ck, g);
+                counter_add(cn, q[r], Ck, g);
+                const int64_t cnt = counter_value(cn, g);
                 if (cnt > cnt_prev) shB[cnt_prev] = j;
                 cnt_prev = cnt;
             }
