@@ -34,6 +34,7 @@
 #include "mlp_device.cuh"
 #include "pf.h"
 #include "pf_internal.h"
+#include "tc_device.cuh"
 
 namespace pf {
 namespace tc {
@@ -53,131 +54,52 @@ constexpr uint32_t kSmemBytes = kOffTmem + 8;
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
 static_assert(kSmemBytes <= 110 * 1024, "two CTAs per SM");
 
-// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
-// 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-// Shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
-// (K-direction) byte offset >> 4 (16-29), stride (8-row group) byte offset
-// >> 4 (32-45), descriptor version 1 (bits 46-47), base offset 0, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
-
-__device__ __forceinline__ uint32_t cm_off(int r, int kgroup, int kdim)
-{
-    return (uint32_t)((r >> 3) * (kdim * 16) + kgroup * 128 + (r & 7) * 16);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for one completion of the barrier's phase `parity`.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
-{
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 2000000000ull) return false;
-    return true;
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(taddr));
-}
-
 // Bias + GELU on 32 accumulator columns [c0, c0 + 32) of row r, stored as BF16
-// into the 128-wide A operand at `h`.
-__device__ __forceinline__ void gelu_store(const uint32_t (&v)[32], const float *bias, int c0, int r, unsigned char *h)
+// into the 128-wide A operand at `h`; with zs / as (training) also the
+// pre-activations (FP32) and the BF16 activations of the row to global memory.
+__device__ __forceinline__ void gelu_store(const uint32_t (&v)[32], const float *bias, int c0, int r, unsigned char *h,
+                                           float *zs = nullptr, __nv_bfloat16 *as = nullptr)
 {
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         uint32_t w[4];
+        float z[8];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int c = g * 8 + 2 * i;
-            w[i] = mlp::pack_bf16(mlp::gelu_fast(__uint_as_float(v[c]) + bias[c0 + c]),
-                                  mlp::gelu_fast(__uint_as_float(v[c + 1]) + bias[c0 + c + 1]));
+            z[2 * i] = __uint_as_float(v[c]) + bias[c0 + c];
+            z[2 * i + 1] = __uint_as_float(v[c + 1]) + bias[c0 + c + 1];
+            w[i] = mlp::pack_bf16(mlp::gelu_fast(z[2 * i]), mlp::gelu_fast(z[2 * i + 1]));
         }
         *reinterpret_cast<uint4 *>(h + cm_off(r, (c0 >> 3) + g, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+        if (zs) {
+            *reinterpret_cast<float4 *>(zs + c0 + g * 8) = make_float4(z[0], z[1], z[2], z[3]);
+            *reinterpret_cast<float4 *>(zs + c0 + g * 8 + 4) = make_float4(z[4], z[5], z[6], z[7]);
+            *reinterpret_cast<uint4 *>(as + c0 + g * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
     }
 }
 
+// Rows from an FP32 matrix (training, and the stateless forward) and, when x0 and
+// z1 are given, the activations the backward pass needs.
+struct TrainIO {
+    const float *X;        // [R][51] input rows (null: rows from lattice states)
+    int64_t R;
+    __nv_bfloat16 *x0;     // [R][64] the BF16 input rows (zero-padded)
+    float *z1, *z2;        // [R][128] pre-activations
+    __nv_bfloat16 *a1, *a2;  // [R][128] BF16 activations
+};
+
+template <bool Train>
 __global__ void __launch_bounds__(kThreads, 1)
     k_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const float *__restrict__ x, int64_t P,
                           const int32_t *__restrict__ pfilt, const int32_t *__restrict__ obs_idx,
                           const float *__restrict__ obs, int32_t obs_stride, const __nv_bfloat16 *__restrict__ wp,
-                          const float *__restrict__ theta, float *__restrict__ out, int32_t *err)
+                          const float *__restrict__ theta, float *__restrict__ out, int32_t *err, TrainIO io)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t R = P * dy;
+    const int64_t R = Train ? io.R : P * dy;
     const int64_t n_tiles = (R + kRows - 1) / kRows;
     float *bias = reinterpret_cast<float *>(smem + kOffBias);
     const uint32_t bar = smem_u32(smem + kOffBar);
@@ -235,7 +157,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t w[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) w[i] = 0u;
-            if (g < R) {
+            if (Train && g < R) {  // an FP32 row of 51 inputs, zero-padded to 64
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = 32 * half + 2 * q;
+                    w[q] = mlp::pack_bf16(c < mlp::kIn ? io.X[g * mlp::kIn + c] : 0.0f,
+                                          c + 1 < mlp::kIn ? io.X[g * mlp::kIn + c + 1] : 0.0f);
+                }
+                if (io.x0)
+#pragma unroll
+                    for (int kg = 0; kg < 4; ++kg)
+                        reinterpret_cast<uint4 *>(io.x0 + g * mlp::kInPad + 32 * half)[kg] =
+                            make_uint4(w[4 * kg], w[4 * kg + 1], w[4 * kg + 2], w[4 * kg + 3]);
+            } else if (!Train && g < R) {
                 const int64_t p = g / dy;
                 const int j = (int)(g - p * dy);
                 const int nd = obs_idx[j], ri = nd / J, ci = nd - ri * J;
@@ -283,12 +217,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         phase ^= 1u;
         if (__syncthreads_or(!ok)) { expired = true; break; }
         tc_fence_after();
+        const int64_t grow = tile * kRows + row;
+        const bool save = Train && io.z1 && grow < R;
 #pragma unroll 1
         for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
             uint32_t v[32];
             tmem_ld32(lane_base + c0, v);
             tc_wait_ld();
-            gelu_store(v, bias, c0, row, smem + kOffH);
+            gelu_store(v, bias, c0, row, smem + kOffH, save ? io.z1 + grow * mlp::kHid : nullptr,
+                       save ? io.a1 + grow * mlp::kHid : nullptr);
         }
         fence_proxy_async();
         tc_fence_before();
@@ -311,7 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t v[32];
             tmem_ld32(lane_base + 128 + c0, v);
             tc_wait_ld();
-            gelu_store(v, bias + 128, c0, row, smem + kOffH);
+            gelu_store(v, bias + 128, c0, row, smem + kOffH, save ? io.z2 + grow * mlp::kHid : nullptr,
+                       save ? io.a2 + grow * mlp::kHid : nullptr);
         }
         fence_proxy_async();
         tc_fence_before();
@@ -350,6 +288,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// The forward kernels' shared-memory size, set once per process.
+cudaError_t forward_attrs()
+{
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(k_proposal_forward_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kSmemBytes);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_proposal_forward_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kSmemBytes);
+    });
+    return attr_err;
+}
+
 int sm_count()
 {
     static int cached[64] = {0};
@@ -373,17 +326,30 @@ cudaError_t launch_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const 
 {
     const int64_t R = P * dy;
     if (R <= 0) return cudaSuccess;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(tc::k_proposal_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)tc::kSmemBytes);
-    });
+    const cudaError_t attr_err = tc::forward_attrs();
     if (attr_err != cudaSuccess) return attr_err;
     const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
     const int64_t grid = std::min<int64_t>(n_tiles, 2 * (int64_t)tc::sm_count());
-    tc::k_proposal_forward_tc<<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
-        J, dx, dy, x, P, pfilt, obs_idx, obs, obs_stride, wp, theta, out, err);
+    tc::k_proposal_forward_tc<false><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
+        J, dx, dy, x, P, pfilt, obs_idx, obs, obs_stride, wp, theta, out, err, tc::TrainIO{});
+    return cudaGetLastError();
+}
+
+// The forward on FP32 input rows X [R][51] -> outputs [R][4] (training, and the
+// stateless forward), with the BF16 inputs, the pre-activations and the BF16
+// activations saved for the backward pass when x0 and z1 are given -- the same
+// tensor-core kernel as the filter's forward.
+cudaError_t launch_train_forward_tc(const float *X, int64_t R, const __nv_bfloat16 *wp, const float *theta, float *out,
+                                    __nv_bfloat16 *x0, float *z1, __nv_bfloat16 *a1, float *z2, __nv_bfloat16 *a2,
+                                    int32_t *err, cudaStream_t s)
+{
+    if (R <= 0) return cudaSuccess;
+    const cudaError_t e = tc::forward_attrs();
+    if (e != cudaSuccess) return e;
+    const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
+    const int64_t grid = std::min<int64_t>(n_tiles, 2 * (int64_t)tc::sm_count());
+    tc::k_proposal_forward_tc<true><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
+        2, 8, 1, nullptr, 0, nullptr, nullptr, nullptr, 0, wp, theta, out, err, tc::TrainIO{X, R, x0, z1, z2, a1, a2});
     return cudaGetLastError();
 }
 

@@ -161,8 +161,16 @@ cudaError_t launch_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const 
                                        const int32_t *pfilt, const int32_t *obs_idx, const float *obs,
                                        int32_t obs_stride, const __nv_bfloat16 *wp, const float *theta, float *out,
                                        int32_t *err, cudaStream_t s);
-cudaError_t launch_mlp_forward_bf16(const __nv_bfloat16 *rows, int64_t R, const __nv_bfloat16 *wp, const float *theta,
-                                    float *out, cudaStream_t s);
+cudaError_t launch_train_forward_tc(const float *X, int64_t R, const __nv_bfloat16 *wp, const float *theta, float *out,
+                                    __nv_bfloat16 *x0, float *z1, __nv_bfloat16 *a1, float *z2, __nv_bfloat16 *a2,
+                                    int32_t *err, cudaStream_t s);
+// The training step's backward GEMMs on the tensor cores (k_mlp_tc.cu).
+cudaError_t launch_hidden_grad_tc(int64_t B, const __nv_bfloat16 *dz2, const __nv_bfloat16 *w2t, const float *z1,
+                                  __nv_bfloat16 *dz1, int32_t *err, cudaStream_t s);
+cudaError_t launch_weight_grad_tc(int64_t B, const __nv_bfloat16 *x0s, const __nv_bfloat16 *a1s,
+                                  const __nv_bfloat16 *a2s, const __nv_bfloat16 *dz1, const __nv_bfloat16 *dz2,
+                                  const float *dout, const float *row_loss, float *partial, int32_t *err,
+                                  cudaStream_t s);
 cudaError_t launch_systematic(int32_t M, int32_t n_tiles, const ResampleArgs &a, cudaStream_t s);
 cudaError_t launch_rng_philox(int64_t n, const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
                               cudaStream_t s);
