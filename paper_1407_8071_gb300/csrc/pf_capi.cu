@@ -1145,18 +1145,27 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
             std::vector<int> cands;
             for (int th = 64; th <= kResampleThreads; th *= 2)
                 if (th * 2 * kItems >= max_len) cands.push_back(th);
+            // the form the steps take (folded: the means read from the
+            // propagated rows, nothing copied), two interleaved rounds, the
+            // better median of five per candidate
+            const bool fold = c.fold_gather();
+            std::vector<float> best_ms(cands.size(), 1e30f);
+            for (int round = 0; round < 2; ++round)
+                for (size_t i = 0; i < cands.size(); ++i) {
+                    c.resample_threads = cands[i];
+                    trial_step();
+                    // each resampling consumes the per-filter maxima the propagation
+                    // left (and resets them), so every trial recomputes them first
+                    const float ms = time_ms(c, 5, [&] {
+                        launch_refresh_max(c, c.stream);
+                        if (fold) launch_resample_fold(c, scratch, c.stream);
+                        else launch_resample(c, scratch, dest, c.stream);
+                    });
+                    best_ms[i] = std::min(best_ms[i], ms);
+                }
             float best = 1e30f;
-            for (int th : cands) {
-                c.resample_threads = th;
-                trial_step();
-                // each resampling consumes the per-filter maxima the propagation
-                // left (and resets them), so every trial recomputes them first
-                const float ms = time_ms(c, 3, [&] {
-                    launch_refresh_max(c, c.stream);
-                    launch_resample(c, scratch, dest, c.stream);
-                });
-                if (ms < best) { best = ms; best_rt = th; }
-            }
+            for (size_t i = 0; i < cands.size(); ++i)
+                if (best_ms[i] < best) { best = best_ms[i]; best_rt = cands[i]; }
             c.resample_threads = best_rt;
         }
         o = 0;
