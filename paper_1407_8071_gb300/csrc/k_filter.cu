@@ -7,7 +7,7 @@
 //     filters of several tiles:  k_weights -> k_scan_scatter -> k_ancestors_small (gather, per-filter
 //                                means) / k_ancestors
 //     filters of one tile:       k_resample_whole (one launch per size class) -> k_whole_finish
-//   lattice gather + estimates   k_gather_mean_rows (Def. 1 per filter)
+//   lattice gather + estimates   k_gather_mean_rows(4) (Def. 1 per filter)
 //   M-average         (Def. 1)               k_ensemble
 // Particles of all filters are contiguous; tiles of <= kTile particles never
 // span two filters, so per-filter reductions read only that filter's tiles
@@ -1624,6 +1624,84 @@ __global__ void __launch_bounds__(256) k_gather_mean_rows(const FilterDesc *filt
     }
 }
 
+// k_gather_mean_rows with four consecutive variables per thread (dx % 4 ==
+// 0, rows 16-byte aligned): float4 loads of the ancestors' rows (eight rows
+// in flight, 128 bytes per thread), each variable's compensated sum over the
+// chunk's outputs in the same order, so the copies and the estimates are
+// k_gather_mean_rows' own.
+__global__ void __launch_bounds__(256, 4) k_gather_mean_rows4(const FilterDesc *filt, const TileDesc *__restrict__ chunks,
+                                                           const int32_t *__restrict__ anc,
+                                                           const float *__restrict__ x_in, float *__restrict__ x_out,
+                                                           int dx, double *part, int32_t *cnt, double *est)
+{
+    __shared__ int last;
+    const TileDesc ch = chunks[blockIdx.x];
+    const FilterDesc fd = filt[ch.m];
+    const int v4 = blockIdx.y * blockDim.x + threadIdx.x, dx4 = dx >> 2;
+    double mine[4] = {0.0, 0.0, 0.0, 0.0};
+    if (v4 < dx4) {
+        const int32_t *a = anc + ch.gstart;
+        const float4 *src = reinterpret_cast<const float4 *>(x_in + fd.off * (int64_t)dx) + v4;
+        float4 *dst = x_out ? reinterpret_cast<float4 *>(x_out + ch.gstart * (int64_t)dx) + v4 : nullptr;
+        FF acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+        int i = 0;
+        for (; i + 8 <= ch.len; i += 8) {
+            float4 r[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) r[k] = src[(int64_t)a[i + k] * dx4];
+            if (dst) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) dst[(int64_t)(i + k) * dx4] = r[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc[0] = ff_add(acc[0], r[k].x);
+                acc[1] = ff_add(acc[1], r[k].y);
+                acc[2] = ff_add(acc[2], r[k].z);
+                acc[3] = ff_add(acc[3], r[k].w);
+            }
+        }
+        for (; i < ch.len; ++i) {
+            const float4 r = src[(int64_t)a[i] * dx4];
+            if (dst) dst[(int64_t)i * dx4] = r;
+            acc[0] = ff_add(acc[0], r.x);
+            acc[1] = ff_add(acc[1], r.y);
+            acc[2] = ff_add(acc[2], r.z);
+            acc[3] = ff_add(acc[3], r.w);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) mine[e] = ff_to_double(acc[e]);
+    }
+    const double denom = (double)fd.N;
+    if (fd.mc_count == 1) {
+        if (v4 < dx4)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) est[(int64_t)ch.m * dx + 4 * v4 + e] = mine[e] / denom;
+        return;
+    }
+    if (v4 < dx4)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) part[(int64_t)blockIdx.x * dx + 4 * v4 + e] = mine[e];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t *c = cnt + (int64_t)ch.m * gridDim.y + blockIdx.y;
+        last = (atomicAdd(c, 1) == fd.mc_count - 1);
+        if (last) *c = 0;
+    }
+    __syncthreads();
+    if (last && v4 < dx4) {
+        __threadfence();
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int v = 4 * v4 + e;
+            double sum = 0.0;
+            for (int k = 0; k < fd.mc_count; ++k) sum += __ldcg(&part[(int64_t)(fd.mc_begin + k) * dx + v]);
+            est[(int64_t)ch.m * dx + v] = sum / denom;
+        }
+    }
+}
+
 // k_mean_rows with four consecutive variables per thread (dx % 4 == 0, rows
 // 16-byte aligned): float4 loads, four times the bytes in flight per
 // instruction; each variable's compensated sum runs over the chunk's particles
@@ -1702,15 +1780,44 @@ __global__ void __launch_bounds__(256) k_mean_rows4(const FilterDesc *filt, cons
     }
 }
 
+// Threads per CTA of the four-variable row kernels: the warp multiple in
+// [128, 256] that wastes the fewest threads on the last column block (the
+// smallest on a tie: more CTAs in flight).  At least 64 threads keep the
+// column blocks within the ceil(dx / 256) completion counters per filter.
+static int rows4_threads(int dx4)
+{
+    int best = 128;
+    for (int th = 128; th <= 256; th += 32)
+        if ((dx4 + th - 1) / th * th < (dx4 + best - 1) / best * best) best = th;
+    return best;
+}
+
+// The ancestors' rows of x_in: their per-filter means, and the copy into x_out
+// unless it is null (the gather folded into the next propagation).
+static void launch_gather_means(const Ctx &c, const float *x_in, float *x_out, cudaStream_t s)
+{
+    const int dx = c.mp.dx;
+    if (dx % 4 == 0) {
+        const int th = rows4_threads(dx / 4);
+        dim3 g(c.n_mchunks, (dx / 4 + th - 1) / th);
+        k_gather_mean_rows4<<<g, th, 0, s>>>(c.filt, c.mchunks, c.anc, x_in, x_out, dx, c.mean_part, c.mean_cnt,
+                                             c.est);
+    } else {
+        dim3 g(c.n_mchunks, (dx + 255) / 256);
+        k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, x_in, x_out, dx, c.mean_part, c.mean_cnt,
+                                            c.est);
+    }
+}
+
 // The (weighted) per-filter means of the lattice particles xn.
 void launch_mean_rows(const Ctx &c, const float *xn, const float *lw2, const int32_t *fmax2, const double *fstats,
                       cudaStream_t s)
 {
     const int dx = c.mp.dx;
     if (dx % 4 == 0) {
-        // 128 threads of four variables: more CTAs in flight (the counters hold ceil(dx / 256) per filter)
-        dim3 g(c.n_mchunks, (dx / 4 + 127) / 128);
-        k_mean_rows4<<<g, 128, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
+        const int th = rows4_threads(dx / 4);
+        dim3 g(c.n_mchunks, (dx / 4 + th - 1) / th);
+        k_mean_rows4<<<g, th, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
     } else {
         dim3 g(c.n_mchunks, (dx + 255) / 256);
         k_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, xn, dx, c.mean_part, c.mean_cnt, c.est, lw2, fmax2, fstats);
@@ -2370,8 +2477,7 @@ cudaError_t launch_resample_fold(const Ctx &c, const float *x, cudaStream_t s)
     const int dx = c.mp.dx, th = c.resample_threads;
     if (is_lattice(c.mp.kind)) {
         resample_ancestors(c, a, th, s);
-        dim3 g(c.n_mchunks, (dx + 255) / 256);
-        k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, x, nullptr, dx, c.mean_part, c.mean_cnt, c.est);
+        launch_gather_means(c, x, nullptr, s);
     } else {
         switch (dx) {
         case 1: resample_small<1>(c, a, x, nullptr, th, s); break;
@@ -2410,8 +2516,7 @@ cudaError_t launch_resample(const Ctx &c, const float *xi, float *xo, cudaStream
     const int dx = c.mp.dx, th = c.resample_threads;
     if (is_lattice(c.mp.kind)) {
         resample_ancestors(c, a, th, s);
-        dim3 g(c.n_mchunks, (dx + 255) / 256);
-        k_gather_mean_rows<<<g, 256, 0, s>>>(c.filt, c.mchunks, c.anc, xi, xo, dx, c.mean_part, c.mean_cnt, c.est);
+        launch_gather_means(c, xi, xo, s);
     } else {
         switch (dx) {
         case 1: resample_small<1>(c, a, xi, xo, th, s); break;
