@@ -1894,18 +1894,25 @@ __global__ void __launch_bounds__(kResampleThreads)
     }
 }
 
-// Definition 1: ens[v] = (1/M) sum_m est[m][v] in FP64, one CTA per variable,
-// strided partial sums then a fixed-order tree (deterministic); advances the
-// step counter.
+// Definition 1: ens[v] = (1/M) sum_m est[m][v] in FP64, one CTA per variable:
+// each thread adds its filters m = t, t + T, ... in order, each warp folds
+// its lanes by an xor tree and the first warp folds the warps' sums the same
+// way (a fixed order: deterministic, and ten dependent FP64 adds after the
+// strided ones instead of a 32-long chain); advances the step counter.
 __global__ void __launch_bounds__(1024) k_ensemble(const double *est, int dx, int32_t M, double *ens, int32_t *d_t)
 {
-    __shared__ double sh[1024 + 1];
-    const int v = blockIdx.x;
-    double s[1] = {0.0};
-    for (int m = threadIdx.x; m < M; m += blockDim.x) s[0] += est[(int64_t)m * dx + v];
-    block_sum_dd<1>(s, sh);
+    __shared__ double sh[32];
+    const int v = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double s = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) s += est[(int64_t)m * dx + v];
+    s = warp_sum_d(s);
+    if (nw > 1) {
+        if (lane == 0) sh[w] = s;
+        __syncthreads();
+        if (w == 0) s = warp_sum_d(lane < nw ? sh[lane] : 0.0);
+    }
     if (threadIdx.x == 0) {
-        ens[v] = s[0] / (double)M;
+        ens[v] = s / (double)M;
         if (v == 0 && d_t) *d_t += 1;
     }
 }
