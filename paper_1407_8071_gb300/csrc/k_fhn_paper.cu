@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(MaxT, MinB)
 // side fixed at compile time (0: mp.J), so that the index divisions of a
 // one-sub-step launch become shifts.
 template <int MinB, int G, int JT = 0>
-__global__ void __launch_bounds__(512, MinB)
+__global__ void __launch_bounds__(kFhnp4MaxThreads, MinB)
     k_propagate_fhnp4(ModelParams mp, Key key, uint32_t stream, uint32_t stim_stream, const int32_t *pfilt,
                       const FilterDesc *filt, const float *x_in, float *x_out, int64_t P, float *logw,
                       const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
@@ -501,7 +501,7 @@ cudaError_t launch_fhnp_interval(const Ctx &c, const float *d_obs, int32_t strid
     if (nodes > 2) {  // 4 or 8 nodes per thread
         const int units = c.mp.J * c.mp.J / nodes;
         int n = 1;
-        while ((n + 1) * units <= 512 && n < kMaxSlots) ++n;
+        while ((n + 1) * units <= kFhnp4MaxThreads && n < kMaxSlots) ++n;
         if (c.fhn_ppc > 0 && c.fhn_ppc < n) n = c.fhn_ppc;
         const int ppc = n, threads = (ppc * units + 31) / 32 * 32;
         const size_t planes = 2 * (size_t)ppc * c.mp.J * c.mp.J * sizeof(float);

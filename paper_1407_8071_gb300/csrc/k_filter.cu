@@ -599,10 +599,10 @@ __global__ void __launch_bounds__(1024, 2)
 // calls) and the same per-particle reduction over pairs, so its results are
 // bit-identical to the pair kernel's.  One barrier and four shared-memory
 // loads serve four nodes (up/down as float4, left/right as scalars), and the
-// two generator chains interleave.
-constexpr int kFhn4MaxThreads = 512;
-
-// MinB: CTAs the compiler must fit per SM (3: at most 42 registers; 4: 32,
+// two generator chains interleave.  At most fhn4_max_threads(4 G) threads per
+// CTA.
+//
+// MinB: CTAs the compiler must fit per SM (3: at most 48 registers; 4: 32,
 // with a little spilling) -- the autotuner times both.  G float4 groups per
 // thread: G = 1 the four-node kernel, G = 2 eight consecutive nodes of a row
 // (sides divisible by 8), the same per-pair arithmetic, Philox blocks and
@@ -611,7 +611,7 @@ constexpr int kFhn4MaxThreads = 512;
 // read float4s 32 bytes apart (two-way bank conflicts), yet the conflict-free
 // [G][units] order measured slower for its runtime-stride addressing.
 template <bool Noise = true, int MinB = 3, int G = 1>
-__global__ void __launch_bounds__(kFhn4MaxThreads, MinB)
+__global__ void __launch_bounds__(fhn4_max_threads(4 * G), MinB)
     k_propagate_fhn4(ModelParams mp, Key key, const int32_t *pfilt, const FilterDesc *filt,
                      const float *x_in, float *x_out, int64_t P, float *logw,
                      const float *obs, int32_t obs_stride, const int32_t *obs_slot, const int32_t *d_t, int32_t ppc,
@@ -2005,24 +2005,16 @@ namespace {
 // whole warps (the extra threads hold no particle).  want = 0 picks as many
 // particles as fit in 1024 threads (at most 8).
 // Threads of a lattice CTA carrying up to `want` particles (0: as many as fit
-// in 1024 threads -- 512 for the four-node kernel --, at most 8) with `nodes`
-// (2 or 4) nodes per thread.
+// in 1024 threads -- fhn4_max_threads(nodes) for the four- and eight-node
+// kernels --, at most 8) with `nodes` (2, 4 or 8) nodes per thread.
 int fhn_threads(const ModelParams &mp, int *ppc, int want = 0, int nodes = 2)
 {
-    const int per = mp.J * mp.J / nodes, cap = nodes >= 4 ? kFhn4MaxThreads : 1024;
+    const int per = mp.J * mp.J / nodes, cap = nodes >= 4 ? fhn4_max_threads(nodes) : 1024;
     int n = 1;
     while ((n + 1) * per <= cap && n < 8) ++n;
     if (want > 0 && want < n) n = want;
     *ppc = n;
     return (n * per + 31) / 32 * 32;
-}
-
-// Nodes per thread of the lattice kernels: 4 where the side allows it, unless
-// the schedule asks for 2.
-int fhn_nodes(const Ctx &c)
-{
-    if (c.fhn_nodes == 8 && c.mp.J % 8 == 0) return 8;
-    return (c.fhn_nodes == 2 || c.mp.J % 4 != 0) ? 2 : 4;
 }
 
 size_t fhn_smem(const ModelParams &mp, int threads, int ppc, size_t real_bytes)

@@ -1122,8 +1122,9 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
         if (e == cudaSuccess && is_lattice(c.mp.kind)) {  // nodes per thread, particles per CTA
             float best = 1e30f;
             for (int nodes = 2; nodes <= 8; nodes *= 2) {
-                if (nodes > 2 && c.mp.J % nodes != 0) continue;
-                const int per = c.mp.J * c.mp.J / nodes, cap = nodes >= 4 ? 512 : 1024;
+                const int cap4 = c.mp.kind == kFhnPaper ? kFhnp4MaxThreads : fhn4_max_threads(nodes);
+                if (nodes > 2 && (c.mp.J % nodes != 0 || c.mp.J * c.mp.J / nodes > cap4)) continue;
+                const int per = c.mp.J * c.mp.J / nodes, cap = nodes >= 4 ? cap4 : 1024;
                 int maxp = 1;
                 while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
                 for (int ppc = 1; ppc <= maxp; ++ppc)
@@ -1187,7 +1188,7 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
     if (h_choice) {
         h_choice[0] = c.fhn_ppc;
         h_choice[1] = c.resample_threads;
-        h_choice[2] = c.mp.kind == PF_MODEL_FHN_LATTICE ? (c.fhn_nodes ? c.fhn_nodes : (c.mp.J % 4 ? 2 : 4))
+        h_choice[2] = c.mp.kind == PF_MODEL_FHN_LATTICE ? fhn_nodes(c)
                       : (c.mp.kind == PF_MODEL_FHN_PAPER ? (c.fhn_nodes ? c.fhn_nodes : 2) : 1);
     }
     return PF_OK;
@@ -1243,8 +1244,11 @@ pf_status pf_set_schedule(pf_ctx *h, int32_t nodes_per_thread, int32_t particles
     const bool lattice = is_lattice(c.mp.kind);
     if (nodes_per_thread != 0 &&
         !(lattice && (nodes_per_thread == 2 ||
-                      ((nodes_per_thread == 4 || nodes_per_thread == 8) && c.mp.J % nodes_per_thread == 0))))
-        return fail(c, PF_EINVAL, "nodes_per_thread: 0, 2, 4 or 8 (4 and 8: J divisible by them)");
+                      ((nodes_per_thread == 4 || nodes_per_thread == 8) &&
+                       (c.mp.kind == kFhnPaper ? c.mp.J % nodes_per_thread == 0
+                                               : fhn_nodes_fit(c.mp.J, nodes_per_thread))))))
+        return fail(c, PF_EINVAL, "nodes_per_thread: 0, 2, 4 or 8 (4 and 8: J divisible by them and J^2 / nodes "
+                                  "threads within the kernel's bound)");
     if (particles_per_cta < 0 || (particles_per_cta > 0 && !lattice))
         return fail(c, PF_EINVAL, "particles_per_cta: 0, or >= 1 for the lattice");
     int max_len = 1;

@@ -27,6 +27,15 @@ constexpr int kWholeItems = 8;
 constexpr int kWholeClasses = 3;
 static_assert((32 * kWholeItems << (kWholeClasses - 1)) == kTile, "the largest class fills a tile");
 constexpr int kSubTile = 128;                     // propagation block of the thread-per-particle models
+// Threads per CTA of the four- and eight-node lattice kernels at most (their
+// launch bounds): 512 with four nodes per thread; 416 with eight, so that the
+// eight-node build for three CTAs per SM gets 48 registers instead of 40 and
+// stops spilling in its loop (400 threads carry two 40x40 particles).  A
+// particle's J^2 / nodes threads must fit.
+constexpr int fhn4_max_threads(int nodes) { return nodes == 8 ? 416 : 512; }
+inline bool fhn_nodes_fit(int J, int nodes) { return J % nodes == 0 && J * J / nodes <= fhn4_max_threads(nodes); }
+// The same bound of the paper lattice's four- and eight-node kernels.
+constexpr int kFhnp4MaxThreads = 512;
 constexpr int kMeanChunk = 256;                   // particles per partial sum of the lattice means
 
 // A tile also carries the fields of its filter that the tile kernels need,
@@ -210,7 +219,7 @@ struct Ctx {
     int resample_threads = kResampleThreads;
     int max_tile_len = kTile;  // the longest tile: with 4 particles per thread it needs max_tile_len / 4 threads
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
-    int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, or 0 (4 where J % 4 == 0)
+    int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, 8, or 0 (4 where fhn_nodes_fit)
     int fhn_quad_ctas = 3;         // four-node kernel: CTAs per SM it is compiled for (3 or 4; autotuned)
     // resampling only when the ESS is low (pf_set_resampling; < 0: every step)
     double ess_threshold = -1.0;
@@ -297,5 +306,13 @@ struct Ctx {
 
     size_t dyn_obs() const { return (size_t)mp.dy; }
 };
+// Nodes per thread the lattice kernels of context c run with: 4 where the side
+// allows it, unless the schedule asks for 2 or 8.
+inline int fhn_nodes(const Ctx &c)
+{
+    if (c.fhn_nodes == 8 && fhn_nodes_fit(c.mp.J, 8)) return 8;
+    return (c.fhn_nodes == 2 || !fhn_nodes_fit(c.mp.J, 4)) ? 2 : 4;
+}
+
 
 }  // namespace pf
