@@ -410,9 +410,11 @@ constexpr int kPropThreads = kSubTile / 2;
 // (noise-free Euler prediction mu, nothing stored but la_out = log g(y | mu)
 // and logw = lw_prev + la_out).  Mode 2: its second stage (logw = log g(y | x)
 // - la_src[off + anc]).  Mode 3: carried weights (adaptive resampling):
-// logw = lw_prev + log g(y | x).
+// logw = lw_prev + log g(y | x).  At least ten CTAs per SM: the compiler
+// keeps the two chains in 79 registers (12 CTAs, 24 warps per SM); held to 64
+// registers for 16 CTAs, the Lorenz interval ran 2 % slower.
 template <int D, int Mode>
-__global__ void __launch_bounds__(kPropThreads, 16)
+__global__ void __launch_bounds__(kPropThreads, 10)
     k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *x_in,
                       float *x_out, int64_t P, float *logw, int32_t *fmax_key, const float *obs,
                       int32_t obs_stride, const int32_t *d_t, AuxPtrs aux)
