@@ -604,8 +604,9 @@ __global__ void __launch_bounds__(1024, 2)
 // two generator chains interleave.  At most fhn4_max_threads(4 G) threads per
 // CTA.
 //
-// MinB: CTAs the compiler must fit per SM (3: at most 48 registers; 4: 32,
-// with a little spilling) -- the autotuner times both.  G float4 groups per
+// MinB: CTAs the compiler must fit per SM -- four nodes per thread: 2 (63
+// registers) or 4 (32, with a little spilling); eight: 2 or 3 (48 registers
+// within the 416-thread bound) -- the autotuner times both of each.  G float4 groups per
 // thread: G = 1 the four-node kernel, G = 2 eight consecutive nodes of a row
 // (sides divisible by 8), the same per-pair arithmetic, Philox blocks and
 // reduction order in both, so every width gives the pair kernel's bits.  The
@@ -2119,9 +2120,9 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(k_propagate_fhn4<false, 3, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_propagate_fhn4<true, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_propagate_fhn4<true, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(k_propagate_fhn4<false, 3>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_propagate_fhn4<false, 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
         cudaFuncSetAttribute(k_propagate_fhn4<true, 4>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
@@ -2154,13 +2155,13 @@ cudaError_t launch_fhn_interval(const Ctx &c, const float *d_obs, int32_t stride
         k_propagate_fhn4<true, 4><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
                                                               stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
     else if (nodes == 4 && noise)
-        k_propagate_fhn4<true, 3><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+        k_propagate_fhn4<true, 2><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
                                                               stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 1);
     else if (nodes == 4 && four)
         k_propagate_fhn4<false, 4><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
                                                                stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 0);
     else if (nodes == 4)
-        k_propagate_fhn4<false, 3><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
+        k_propagate_fhn4<false, 2><<<grid, threads, smem, s>>>(c.mp, c.key, c.pfilt, c.filt, xi, xo, c.P, lw, d_obs,
                                                                stride, c.obs_slot, c.d_t, ppc, fm, n_steps, aux, 0);
     else if (noise)
         k_propagate_fhn<float, true><<<grid, threads, smem, s>>>(c.mp, c.key, kStreamDyn, c.pfilt, c.filt, xi, xo, c.P,

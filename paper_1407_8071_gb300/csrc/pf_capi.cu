@@ -1127,8 +1127,11 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
                 const int per = c.mp.J * c.mp.J / nodes, cap = nodes >= 4 ? cap4 : 1024;
                 int maxp = 1;
                 while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
+                // the builds' CTAs per SM: four nodes 2 or 4, eight 2 or 3 (two nodes: one build)
+                const int qcs[2] = {nodes == 2 ? 3 : 2, nodes == 4 ? 4 : 3};
                 for (int ppc = 1; ppc <= maxp; ++ppc)
-                    for (int qc = nodes == 8 ? 2 : 3; qc <= (nodes == 4 ? 4 : 3); ++qc) {
+                    for (int qc : qcs) {
+                        if (nodes == 2 && qc != qcs[0]) continue;
                         c.fhn_nodes = nodes;
                         c.fhn_ppc = ppc;
                         c.fhn_quad_ctas = qc;

@@ -220,7 +220,7 @@ struct Ctx {
     int max_tile_len = kTile;  // the longest tile: with 4 particles per thread it needs max_tile_len / 4 threads
     int fhn_ppc = 0;               // lattice particles per CTA (0: as many as fit in 1024 threads, at most 8)
     int fhn_nodes = 0;             // lattice nodes per thread: 2, 4, 8, or 0 (4 where fhn_nodes_fit)
-    int fhn_quad_ctas = 3;         // four-node kernel: CTAs per SM it is compiled for (3 or 4; autotuned)
+    int fhn_quad_ctas = 3;         // CTAs per SM the lattice build is compiled for (four nodes: 4, else 2; eight: 3, else 2; autotuned)
     // resampling only when the ESS is low (pf_set_resampling; < 0: every step)
     double ess_threshold = -1.0;
     bool adaptive() const { return ess_threshold >= 0.0 && ess_threshold <= 1.0; }
