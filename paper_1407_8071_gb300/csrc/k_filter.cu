@@ -435,7 +435,14 @@ __global__ void __launch_bounds__(kPropThreads, 10)
 #pragma unroll
         for (int v = 0; v < D; ++v) xs[r][v] = x_in[v * P + src];
     }
-    propagate_small_n<D, 2, float, Mode != 1>(mp, key, kStreamDyn, c0, t, (uint32_t)st.m, xs);
+    {
+        float2 x2[D];
+#pragma unroll
+        for (int v = 0; v < D; ++v) x2[v] = make_float2(xs[0][v], xs[1][v]);
+        propagate_small_x2<D, Mode != 1>(mp, key, kStreamDyn, c0[0], c0[1], t, (uint32_t)st.m, x2);
+#pragma unroll
+        for (int v = 0; v < D; ++v) xs[0][v] = x2[v].x, xs[1][v] = x2[v].y;
+    }
     float l = -INFINITY;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {

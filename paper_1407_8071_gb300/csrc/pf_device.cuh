@@ -92,30 +92,75 @@ __device__ __forceinline__ float rcp_approx(float x)
 // |s| <= 3 - 2 sqrt(2) = 0.1716 (Abramowitz & Stegun 4.1.27); the first
 // omitted term, 2 s^9 / 9, is below 3e-8 of ln f.  f - 1 is exact (Sterbenz),
 // so s keeps its relative accuracy as f -> 1.  -2 ln u1 = -2 (k - 24) ln 2 - 2 ln f.
-__device__ __forceinline__ float neg2_ln_u24(uint32_t n)
+// Every rounding is spelled out (no contraction left to the compiler), so the
+// two-lane form below gives the same bits lane by lane.
+constexpr float kM2Ln2 = -1.38629436111989061883f;  // -2 ln 2
+constexpr float kTwoPi = 6.28318530717958647692f;
+
+__device__ __forceinline__ uint32_t ln_reduce(uint32_t n, uint32_t &k)
 {
     const uint32_t bits = __float_as_uint(__uint2float_rn(n));
-    const uint32_t k = (bits - 0x3F3504F3u) >> 23;  // 0x3F3504F3: binary32 sqrt(1/2)
-    const float f = __uint_as_float(bits - (k << 23));
-    const float s = (f - 1.0f) * rcp_approx(f + 1.0f);
-    const float s2 = s * s;
-    float c = -4.0f / 7.0f;  // -2 x the series' coefficients 2 / (2j + 1)
-    c = fmaf(c, s2, -4.0f / 5.0f);
-    c = fmaf(c, s2, -4.0f / 3.0f);
-    const float m2lnf = fmaf(s * s2, c, -4.0f * s);
-    return fmaf((float)((int32_t)k - 24), -1.38629436111989061883f, m2lnf);  // -2 ln 2
+    k = (bits - 0x3F3504F3u) >> 23;  // 0x3F3504F3: binary32 sqrt(1/2)
+    return bits - (k << 23);
+}
+
+__device__ __forceinline__ float neg2_ln_u24(uint32_t n)
+{
+    uint32_t k;
+    const float f = __uint_as_float(ln_reduce(n, k));
+    const float s = __fmul_rn(__fadd_rn(f, -1.0f), rcp_approx(__fadd_rn(f, 1.0f)));
+    const float s2 = __fmul_rn(s, s);
+    float c = __fmaf_rn(-4.0f / 7.0f, s2, -4.0f / 5.0f);  // -2 x the series' coefficients 2 / (2j + 1)
+    c = __fmaf_rn(c, s2, -4.0f / 3.0f);
+    const float m2lnf = __fmaf_rn(__fmul_rn(s, s2), c, __fmul_rn(-4.0f, s));
+    return __fmaf_rn((float)((int32_t)k - 24), kM2Ln2, m2lnf);
 }
 
 template <>
 __device__ __forceinline__ void box_muller<float>(uint32_t a, uint32_t b, float &z0, float &z1)
 {
     const float v = neg2_ln_u24((a >> 8) + 1u);
-    const float h = __uint2float_rn(b >> 8) * 0x1p-24f - 0.5f;
-    const float R = v > 0.0f ? v * rsqrtf(v) : 0.0f;
+    const float h = __fmaf_rn(__uint2float_rn(b >> 8), 0x1p-24f, -0.5f);
+    const float R = v > 0.0f ? __fmul_rn(v, rsqrtf(v)) : 0.0f;
     float s, c;
-    __sincosf(6.28318530717958647692f * h, &s, &c);
-    z0 = -R * c;
-    z1 = -R * s;
+    __sincosf(__fmul_rn(kTwoPi, h), &s, &c);
+    z0 = __fmul_rn(-R, c);
+    z1 = __fmul_rn(-R, s);
+}
+
+// Two lanes at once on the packed FP32 pipes (fma/mul/add.rn.f32x2: each
+// lane rounds as the scalar instruction does): lane i is neg2_ln_u24(n_i) and
+// box_muller<float>(a_i, b_i) bit for bit, for half the FP32 instructions.
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ float2 neg2_ln_u24_x2(uint32_t n0, uint32_t n1)
+{
+    uint32_t k0, k1;
+    const uint32_t r0 = ln_reduce(n0, k0), r1 = ln_reduce(n1, k1);
+    const float2 f = make_float2(__uint_as_float(r0), __uint_as_float(r1));
+    const float2 fp = __fadd2_rn(f, f2s(1.0f));
+    const float2 s = __fmul2_rn(__fadd2_rn(f, f2s(-1.0f)), make_float2(rcp_approx(fp.x), rcp_approx(fp.y)));
+    const float2 s2 = __fmul2_rn(s, s);
+    float2 c = __ffma2_rn(f2s(-4.0f / 7.0f), s2, f2s(-4.0f / 5.0f));
+    c = __ffma2_rn(c, s2, f2s(-4.0f / 3.0f));
+    const float2 m2lnf = __ffma2_rn(__fmul2_rn(s, s2), c, __fmul2_rn(f2s(-4.0f), s));
+    return __ffma2_rn(make_float2((float)((int32_t)k0 - 24), (float)((int32_t)k1 - 24)), f2s(kM2Ln2), m2lnf);
+}
+
+__device__ __forceinline__ void box_muller_x2(uint32_t a0, uint32_t b0, uint32_t a1, uint32_t b1, float2 &z0,
+                                              float2 &z1)
+{
+    const float2 v = neg2_ln_u24_x2((a0 >> 8) + 1u, (a1 >> 8) + 1u);
+    const float2 h = __ffma2_rn(make_float2(__uint2float_rn(b0 >> 8), __uint2float_rn(b1 >> 8)), f2s(0x1p-24f),
+                                f2s(-0.5f));
+    const float2 rv = __fmul2_rn(v, make_float2(rsqrtf(v.x), rsqrtf(v.y)));
+    const float2 nR = make_float2(v.x > 0.0f ? -rv.x : -0.0f, v.y > 0.0f ? -rv.y : -0.0f);
+    const float2 ang = __fmul2_rn(f2s(kTwoPi), h);
+    float s0, c0, s1, c1;
+    __sincosf(ang.x, &s0, &c0);
+    __sincosf(ang.y, &s1, &c1);
+    z0 = __fmul2_rn(nR, make_float2(c0, c1));
+    z1 = __fmul2_rn(nR, make_float2(s0, s1));
 }
 
 template <>
@@ -138,6 +183,18 @@ __device__ __forceinline__ void normals4(const Key &key, uint32_t c0, uint32_t c
     const uint4 r = philox4x32_10(make_uint4(c0, c1, c2, (stream << 24) | block), key);
     box_muller<Real>(r.x, r.y, z[0], z[1]);
     box_muller<Real>(r.z, r.w, z[2], z[3]);
+}
+
+// normals4<float> of two counters (c0a and c0b, the other words shared) in the
+// two lanes of z: lane 0 is the first counter's normal, lane 1 the second's.
+__device__ __forceinline__ void normals4_x2(const Key &key, uint32_t c0a, uint32_t c0b, uint32_t c1, uint32_t c2,
+                                            uint32_t stream, uint32_t block, float2 z[4])
+{
+    const uint32_t w = (stream << 24) | block;
+    const uint4 ra = philox4x32_10(make_uint4(c0a, c1, c2, w), key);
+    const uint4 rb = philox4x32_10(make_uint4(c0b, c1, c2, w), key);
+    box_muller_x2(ra.x, ra.y, rb.x, rb.y, z[0], z[1]);
+    box_muller_x2(ra.z, ra.w, rb.z, rb.w, z[2], z[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -264,6 +321,60 @@ __device__ __forceinline__ void propagate_small_n(const ModelParams &mp, const K
                     SmallModel<D, Real>::drift(mp, x[r], f);
 #pragma unroll
                     for (int v = 0; v < D; ++v) x[r][v] = x[r][v] + dt * f[v] + sq * z[r][s * D + v];
+                }
+            }
+        }
+    }
+}
+
+// The same interval for two particles of a thread at once (counter words c0a
+// and c0b), their states in the two lanes of x: the normals from
+// normals4_x2, the drift and the Euler-Maruyama update on the packed FP32
+// pipes with every rounding spelled out -- Lorenz 63 as s (x2 - x1),
+// x1 (r - x3) - x2, x1 x2 - b x3; the linear-Gaussian drift as the dot product
+// sum_j A_ij x_j in order j = 0, 1, ..; the update (x + dt f) + sq z, two
+// fused multiply-adds.  Both particles of a thread take the same instructions.
+template <int D, bool Noise = true>
+__device__ __forceinline__ void propagate_small_x2(const ModelParams &mp, const Key &key, uint32_t stream,
+                                                   uint32_t c0a, uint32_t c0b, uint32_t t, uint32_t c2, float2 x[D])
+{
+    using NP = NoisePacking<D>;
+    const float2 DT = f2s(mp.fdt), NDT = f2s(-mp.fdt), SQ = f2s(mp.fsq), M1 = f2s(-1.0f);
+    const bool lorenz = mp.kind == kLorenz63;
+    const int K = mp.K;
+    uint32_t block = 0;
+    for (int k0 = 0; k0 < K; k0 += NP::steps) {
+        float2 z[4 * NP::blocks];
+#pragma unroll
+        for (int b = 0; b < NP::blocks; ++b) {
+            if (Noise) {
+                normals4_x2(key, c0a, c0b, t, c2, stream, block + b, z + 4 * b);
+            } else {  // the noise-free Euler prediction (auxiliary filter's look-ahead)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) z[4 * b + i] = f2s(0.0f);
+            }
+        }
+        block += NP::blocks;
+#pragma unroll
+        for (int s = 0; s < NP::steps; ++s) {
+            if (k0 + s < K) {
+                if (D == 3 && lorenz) {
+                    const float2 f0 = __fmul2_rn(f2s(mp.fp[0]), __ffma2_rn(x[0], M1, x[1]));
+                    const float2 f1 = __ffma2_rn(x[1], M1, __fmul2_rn(x[0], __ffma2_rn(x[2], M1, f2s(mp.fp[1]))));
+                    const float2 fz = __ffma2_rn(f2s(-mp.fp[2]), x[2], __fmul2_rn(x[0], x[1]));
+                    x[0] = __ffma2_rn(SQ, z[s * D], __ffma2_rn(DT, f0, x[0]));
+                    x[1] = __ffma2_rn(SQ, z[s * D + 1], __ffma2_rn(DT, f1, x[1]));
+                    x[2] = __ffma2_rn(SQ, z[s * D + 2], __ffma2_rn(DT, fz, x[2]));
+                } else {  // dx' = -A x dt + sq dW
+                    float2 ax[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        ax[i] = __fmul2_rn(f2s(mp.fp[i * D]), x[0]);
+#pragma unroll
+                        for (int j = 1; j < D; ++j) ax[i] = __ffma2_rn(f2s(mp.fp[i * D + j]), x[j], ax[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < D; ++i) x[i] = __ffma2_rn(SQ, z[s * D + i], __ffma2_rn(NDT, ax[i], x[i]));
                 }
             }
         }
