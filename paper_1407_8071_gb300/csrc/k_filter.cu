@@ -539,24 +539,35 @@ __global__ void __launch_bounds__(1024, 2)
         }
         __syncthreads();
         if (active) {
-            Real z[4];
-            if (Noise) {
-                normals4<Real>(key, c0, t, c2, stream, (uint32_t)k * blocks_per_step + (uint32_t)q, z);
-            } else {
-                z[0] = z[1] = z[2] = z[3] = (Real)0;
-            }
             const Pair up = buf[qu], dn = buf[qd], lf = buf[ql], rt = buf[qr];
             const Real left = has_left ? lf.y : v0, right = has_right ? rt.x : v1;
-            Real l0, l1;
-            pair_laplacian<Real>(v0, v1, up.x, up.y, dn.x, dn.y, left, right, l0, l1);
             const bool on = (n_base + k) < stim_steps;
             const Real I0 = (on && stim_node0) ? amp : (Real)0, I1 = (on && stim_node1) ? amp : (Real)0;
-            const Real fv0 = fhn_drift_v<Real>(mp, v0, w0, l0, I0), fv1 = fhn_drift_v<Real>(mp, v1, w1, l1, I1);
-            const Real fw0 = fhn_drift_w<Real>(mp, v0, w0), fw1 = fhn_drift_w<Real>(mp, v1, w1);
-            v0 = em_update(v0, fv0, z[0], dt, sq);
-            w0 = em_update(w0, fw0, z[1], dt, sq);
-            v1 = em_update(v1, fv1, z[2], dt, sq);
-            w1 = em_update(w1, fw1, z[3], dt, sq);
+            const uint32_t bk = (uint32_t)k * blocks_per_step + (uint32_t)q;
+            if constexpr (std::is_same<Real, float>::value) {  // both nodes on the packed FP32 pipes
+                float2 zv = f2s(0.0f), zw = f2s(0.0f);
+                if (Noise) pair_normals_x2(key, c0, t, c2, stream, bk, zv, zw);
+                const float2 vv = make_float2(v0, v1), ww = make_float2(w0, w1);
+                const float2 lap = pair_laplacian_x2(vv, make_float2(up.x, up.y), make_float2(dn.x, dn.y), left, right);
+                const float2 fv = fhn_drift_v_x2(mp, vv, ww, lap, make_float2(I0, I1)), fw = fhn_drift_w_x2(mp, vv, ww);
+                const float2 vn = em_update_x2(vv, fv, zv, dt, sq), wn = em_update_x2(ww, fw, zw, dt, sq);
+                v0 = vn.x, v1 = vn.y, w0 = wn.x, w1 = wn.y;
+            } else {
+                Real z[4];
+                if (Noise) {
+                    normals4<Real>(key, c0, t, c2, stream, bk, z);
+                } else {
+                    z[0] = z[1] = z[2] = z[3] = (Real)0;
+                }
+                Real l0, l1;
+                pair_laplacian<Real>(v0, v1, up.x, up.y, dn.x, dn.y, left, right, l0, l1);
+                const Real fv0 = fhn_drift_v<Real>(mp, v0, w0, l0, I0), fv1 = fhn_drift_v<Real>(mp, v1, w1, l1, I1);
+                const Real fw0 = fhn_drift_w<Real>(mp, v0, w0), fw1 = fhn_drift_w<Real>(mp, v1, w1);
+                v0 = em_update(v0, fv0, z[0], dt, sq);
+                w0 = em_update(w0, fw0, z[1], dt, sq);
+                v1 = em_update(v1, fv1, z[2], dt, sq);
+                w1 = em_update(w1, fw1, z[3], dt, sq);
+            }
         }
     }
     if (active && x_out) {
@@ -673,14 +684,14 @@ __global__ void __launch_bounds__(fhn4_max_threads(4 * G), MinB)
             for (int g = 0; g < G; ++g) buf[q * G + g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
         __syncthreads();
         if (active) {
-            float z[2 * NV];
+            float2 zv[NV / 2], zw[NV / 2];  // pair h: the (v, w) noise of its two nodes
             const uint32_t bk = (uint32_t)k * blocks_per_step + (uint32_t)(NV / 2) * (uint32_t)q;  // pair n0 / 2
             if (Noise) {
 #pragma unroll
-                for (int h = 0; h < NV / 2; ++h) normals4<float>(key, c0, t, c2, kStreamDyn, bk + h, z + 4 * h);
+                for (int h = 0; h < NV / 2; ++h) pair_normals_x2(key, c0, t, c2, kStreamDyn, bk + h, zv[h], zw[h]);
             } else {
 #pragma unroll
-                for (int i = 0; i < 2 * NV; ++i) z[i] = 0.0f;
+                for (int h = 0; h < NV / 2; ++h) zv[h] = zw[h] = f2s(0.0f);
             }
             float4 up[G], dn[G];
 #pragma unroll
@@ -690,22 +701,25 @@ __global__ void __launch_bounds__(fhn4_max_threads(4 * G), MinB)
             }
             const float left = has_left ? buf[ql * G + G - 1].w : v[0];
             const float right = has_right ? buf[qr * G].x : v[NV - 1];
-            float l[NV];
+            float2 l[NV / 2];  // every pair's Laplacian from the values before this sub-step
 #pragma unroll
             for (int h = 0; h < NV / 2; ++h) {  // pair h: nodes 2h, 2h + 1
                 const float4 &u4 = up[h >> 1], &d4 = dn[h >> 1];
-                const float ua = (h & 1) ? u4.z : u4.x, ub = (h & 1) ? u4.w : u4.y;
-                const float da = (h & 1) ? d4.z : d4.x, db = (h & 1) ? d4.w : d4.y;
+                const float2 u2 = (h & 1) ? make_float2(u4.z, u4.w) : make_float2(u4.x, u4.y);
+                const float2 d2 = (h & 1) ? make_float2(d4.z, d4.w) : make_float2(d4.x, d4.y);
                 const float lf = h == 0 ? left : v[2 * h - 1], rt = h == NV / 2 - 1 ? right : v[2 * h + 2];
-                pair_laplacian<float>(v[2 * h], v[2 * h + 1], ua, ub, da, db, lf, rt, l[2 * h], l[2 * h + 1]);
+                l[h] = pair_laplacian_x2(make_float2(v[2 * h], v[2 * h + 1]), u2, d2, lf, rt);
             }
             const bool on = (n_base + k) < stim_steps;
 #pragma unroll
-            for (int e = 0; e < NV; ++e) {
-                const float I = (on && row < blk && col + e < blk) ? amp : 0.0f;
-                const float fv = fhn_drift_v<float>(mp, v[e], w[e], l[e], I), fw = fhn_drift_w<float>(mp, v[e], w[e]);
-                v[e] = em_update(v[e], fv, z[2 * e], dt, sq);
-                w[e] = em_update(w[e], fw, z[2 * e + 1], dt, sq);
+            for (int h = 0; h < NV / 2; ++h) {
+                const float2 I = make_float2((on && row < blk && col + 2 * h < blk) ? amp : 0.0f,
+                                             (on && row < blk && col + 2 * h + 1 < blk) ? amp : 0.0f);
+                const float2 vv = make_float2(v[2 * h], v[2 * h + 1]), ww = make_float2(w[2 * h], w[2 * h + 1]);
+                const float2 fv = fhn_drift_v_x2(mp, vv, ww, l[h], I), fw = fhn_drift_w_x2(mp, vv, ww);
+                const float2 vn = em_update_x2(vv, fv, zv[h], dt, sq), wn = em_update_x2(ww, fw, zw[h], dt, sq);
+                v[2 * h] = vn.x, v[2 * h + 1] = vn.y;
+                w[2 * h] = wn.x, w[2 * h + 1] = wn.y;
             }
         }
     }
