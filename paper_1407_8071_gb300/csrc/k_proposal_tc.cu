@@ -65,11 +65,14 @@ __device__ __forceinline__ void gelu_store(const uint32_t (&v)[32], const float 
         uint32_t w[4];
         float z[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 4; ++i) {  // two columns at once on the packed FP32 pipes
             const int c = g * 8 + 2 * i;
-            z[2 * i] = __uint_as_float(v[c]) + bias[c0 + c];
-            z[2 * i + 1] = __uint_as_float(v[c + 1]) + bias[c0 + c + 1];
-            w[i] = mlp::pack_bf16(mlp::gelu_fast(z[2 * i]), mlp::gelu_fast(z[2 * i + 1]));
+            const float2 zz = __fadd2_rn(make_float2(__uint_as_float(v[c]), __uint_as_float(v[c + 1])),
+                                         make_float2(bias[c0 + c], bias[c0 + c + 1]));
+            z[2 * i] = zz.x;
+            z[2 * i + 1] = zz.y;
+            const float2 gg = mlp::gelu_fast_x2(zz);
+            w[i] = mlp::pack_bf16(gg.x, gg.y);
         }
         *reinterpret_cast<uint4 *>(h + cm_off(r, (c0 >> 3) + g, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
         if (zs) {
