@@ -411,8 +411,9 @@ constexpr int kPropThreads = kSubTile / 2;
 // and logw = lw_prev + la_out).  Mode 2: its second stage (logw = log g(y | x)
 // - la_src[off + anc]).  Mode 3: carried weights (adaptive resampling):
 // logw = lw_prev + log g(y | x).  At least ten CTAs per SM: the compiler
-// keeps the two chains in 79 registers (12 CTAs, 24 warps per SM); held to 64
-// registers for 16 CTAs, the Lorenz interval ran 2 % slower.
+// keeps the two packed chains in 88 registers (11 CTAs, 22 warps per SM);
+// held to 64 registers for 16 CTAs the Lorenz interval ran 2 % slower, and to
+// 72 or 79 for 14 or 12 CTAs 1 % slower.
 template <int D, int Mode>
 __global__ void __launch_bounds__(kPropThreads, 10)
     k_propagate_small(ModelParams mp, Key key, const TileDesc *__restrict__ subs, const float *x_in,
