@@ -241,28 +241,38 @@ __global__ void __launch_bounds__(kLast4MaxThreads, MinB)
         const bool has_left = col > 0, has_right = col + 4 < J;
         const float4 up = buf[qu], dn = buf[qd];
         const float left = has_left ? buf[q - 1].w : v[0], right = has_right ? buf[q + 1].x : v[3];
-        float lap[4];
-        pair_laplacian<float>(v[0], v[1], up.x, up.y, dn.x, dn.y, left, v[2], lap[0], lap[1]);
-        pair_laplacian<float>(v[2], v[3], up.z, up.w, dn.z, dn.w, v[1], right, lap[2], lap[3]);
+        // the transition of both node pairs on the packed FP32 pipes (the scalar helpers' bits)
+        const float2 lap2[2] = {
+            pair_laplacian_x2(make_float2(v[0], v[1]), make_float2(up.x, up.y), make_float2(dn.x, dn.y), left, v[2]),
+            pair_laplacian_x2(make_float2(v[2], v[3]), make_float2(up.z, up.w), make_float2(dn.z, dn.w), v[1], right)};
         const int64_t n_base = (int64_t)(t - 1) * mp.K;
         const bool on = (n_base + k) < mp.ip[7];
         const int blk = (int)mp.ip[8];
-        float z[8];
         const uint32_t bk = (uint32_t)k * (uint32_t)(mp.dx / 4) + 2u * (uint32_t)q;
-        normals4<float>(key, c0, t, c2, kStreamDyn, bk, z);
-        normals4<float>(key, c0, t, c2, kStreamDyn, bk + 1u, z + 4);
+        float2 zv2[2], zw2[2], mv2[2], mw2[2], bv2[2], bw2[2];
+#pragma unroll
+        for (int hp = 0; hp < 2; ++hp) {
+            pair_normals_x2(key, c0, t, c2, kStreamDyn, bk + (uint32_t)hp, zv2[hp], zw2[hp]);
+            const float amp = par<float>(mp, 6);
+            const float2 I = make_float2((on && row < blk && col + 2 * hp < blk) ? amp : 0.0f,
+                                         (on && row < blk && col + 2 * hp + 1 < blk) ? amp : 0.0f);
+            const float2 vv = make_float2(v[2 * hp], v[2 * hp + 1]), ww = make_float2(w[2 * hp], w[2 * hp + 1]);
+            const float2 fv = fhn_drift_v_x2(mp, vv, ww, lap2[hp], I), fw = fhn_drift_w_x2(mp, vv, ww);
+            mv2[hp] = __ffma2_rn(f2s(dt), fv, vv);
+            mw2[hp] = __ffma2_rn(f2s(dt), fw, ww);
+            bv2[hp] = __ffma2_rn(f2s(h), zv2[hp], mv2[hp]);  // = em_update
+            bw2[hp] = __ffma2_rn(f2s(h), zw2[hp], mw2[hp]);
+        }
         const float *y = obs + (obs_stride ? (int64_t)m * obs_stride : 0);
         const float inv_h = 1.0f / h;
         float nvs[4], nws[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int node = n0 + e, hp = e >> 1;
-            const bool stim = on && row < blk && col + e < blk;
-            const float I = stim ? par<float>(mp, 6) : 0.0f;
-            const float fv = fhn_drift_v<float>(mp, v[e], w[e], lap[e], I), fw = fhn_drift_w<float>(mp, v[e], w[e]);
-            const float mv = __fmaf_rn(dt, fv, v[e]), mw = __fmaf_rn(dt, fw, w[e]);
-            const float zv = z[2 * e], zw = z[2 * e + 1];
-            const float bv = __fmaf_rn(h, zv, mv), bw = __fmaf_rn(h, zw, mw);  // = em_update
+            const bool hi = e & 1;
+            const float mv = hi ? mv2[hp].y : mv2[hp].x, mw = hi ? mw2[hp].y : mw2[hp].x;
+            const float zv = hi ? zv2[hp].y : zv2[hp].x, zw = hi ? zw2[hp].y : zw2[hp].x;
+            const float bv = hi ? bv2[hp].y : bv2[hp].x, bw = hi ? bw2[hp].y : bw2[hp].x;
             float nv = bv, nw = bw;
             const int j = obs_slot[node];
             if (j >= 0) {
