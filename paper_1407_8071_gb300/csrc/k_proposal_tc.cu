@@ -40,19 +40,41 @@ namespace pf {
 namespace tc {
 
 constexpr int kRows = 128;
-constexpr int kThreads = 256;
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kOffW1 = 0;                            // 128 x 64
-constexpr uint32_t kOffW2 = kOffW1 + 128 * 64 * 2;        // 128 x 128
-constexpr uint32_t kOffW3 = kOffW2 + 128 * 128 * 2;       // 16 x 128
-constexpr uint32_t kOffA = kOffW3 + 16 * 128 * 2;         // 128 x 64
-constexpr uint32_t kOffH = kOffA + 128 * 64 * 2;          // 128 x 128
-constexpr uint32_t kOffBias = kOffH + 128 * 128 * 2;      // b1[128], b2[128], b3[4]
-constexpr uint32_t kOffBar = kOffBias + (128 + 128 + 4) * 4;
-constexpr uint32_t kOffTmem = kOffBar + 8;
+constexpr int kSlots = 4;                     // tiles in flight per CTA, one warpgroup each
+constexpr int kThreads = 128 * kSlots;        // a thread per row of its slot's tile
+constexpr uint32_t kTmemCols = 128 * kSlots;  // 128 accumulator columns per slot: all 512 of the SM
+constexpr uint32_t kOffW1 = 0;                          // 128 x 64
+constexpr uint32_t kOffW2 = kOffW1 + 128 * 64 * 2;      // 128 x 128
+constexpr uint32_t kOffW3 = kOffW2 + 128 * 128 * 2;     // 16 x 128
+constexpr uint32_t kOffBuf = kOffW3 + 16 * 128 * 2;     // per slot: A (128 x 64), then H (128 x 128) over it
+constexpr uint32_t kBufBytes = 128 * 128 * 2;
+constexpr uint32_t kOffBias = kOffBuf + kSlots * kBufBytes;  // b1[128], b2[128], b3[4]
+constexpr uint32_t kOffBar = kOffBias + (128 + 128 + 4) * 4; // an mbarrier per slot
+constexpr uint32_t kOffTmem = kOffBar + 8 * kSlots;
 constexpr uint32_t kSmemBytes = kOffTmem + 8;
 static_assert(kOffBar % 8 == 0, "mbarrier alignment");
-static_assert(kSmemBytes <= 110 * 1024, "two CTAs per SM");
+static_assert(kOffBuf % 1024 == 0, "operand alignment");
+static_assert(kSmemBytes <= 227 * 1024, "one CTA per SM");
+
+// A slot's warpgroup synchronises on named barrier 1 + slot (barrier 0 is the
+// CTA's); the OR form returns whether any of its threads passed `pred`.
+__device__ __forceinline__ void slot_sync(int slot)
+{
+    asm volatile("bar.sync %0, 128;" ::"r"(1 + slot) : "memory");
+}
+__device__ __forceinline__ bool slot_any(int slot, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(1 + slot)
+        : "memory");
+    return r != 0;
+}
 
 // Bias + GELU on 32 accumulator columns [c0, c0 + 32) of row r, stored as BF16
 // into the 128-wide A operand at `h`; with zs / as (training) also the
@@ -101,14 +123,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                           const float *__restrict__ theta, float *__restrict__ out, int32_t *err, TrainIO io)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, slot = tid >> 7, row = tid & (kRows - 1);
     const int64_t R = Train ? io.R : P * dy;
     const int64_t n_tiles = (R + kRows - 1) / kRows;
     float *bias = reinterpret_cast<float *>(smem + kOffBias);
-    const uint32_t bar = smem_u32(smem + kOffBar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffTmem);
 
-    // weights (core-matrix layout) and biases, once per CTA
+    // weights (core-matrix layout) and biases, once per CTA for its four slots
     const uint4 *w1g = reinterpret_cast<const uint4 *>(wp);
     const uint4 *w2g = reinterpret_cast<const uint4 *>(wp + mlp::kPackW1);
     const uint4 *w3g = reinterpret_cast<const uint4 *>(wp + mlp::kPackW1 + mlp::kPackW2);
@@ -130,10 +151,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         bias[128 + i] = theta[mlp::kOffB2 + i];
     }
     if (tid < 4) bias[256 + tid] = theta[mlp::kOffB3 + tid];
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (tid < kSlots) mbar_init(smem_u32(smem + kOffBar + 8 * tid), 1);
+    if (tid == 0) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols)
@@ -145,18 +164,25 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    const int row = tid & (kRows - 1), half = tid >> 7;
+    // the slot's accumulator columns; warp w reaches TMEM lanes 32 (w % 4) .. + 31 (its rows)
+    const uint32_t dcol = tmem + 128u * (uint32_t)slot;
+    const uint32_t lane_base = dcol + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t bar = smem_u32(smem + kOffBar + 8 * slot);
+    unsigned char *buf = smem + kOffBuf + (uint32_t)slot * kBufBytes;
 
-    const uint32_t sbase = smem_u32(smem);
+    const uint32_t sbase = smem_u32(smem), sbuf = sbase + kOffBuf + (uint32_t)slot * kBufBytes;
     const uint32_t id128 = idesc_bf16(128, 128), id16 = idesc_bf16(128, 16);
     uint32_t phase = 0;
     bool expired = false;
     const int nn = J * J;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        // ---- input rows -> A (half 0: columns 0..31, half 1: columns 32..63)
-        {
-            const int64_t g = tile * kRows + row;
+    for (int64_t tile = (int64_t)blockIdx.x * kSlots + slot; tile < n_tiles; tile += (int64_t)gridDim.x * kSlots) {
+        const int64_t g = tile * kRows + row;
+        // ---- the input row -> A (columns 0..31, then 32..63)
+        const int64_t p = (!Train && g < R) ? g / dy : 0;
+        const int j = (!Train && g < R) ? (int)(g - p * dy) : 0;
+        const int nd = (!Train && g < R) ? obs_idx[j] : 0, ri = nd / J, ci = nd - ri * J;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
             uint32_t w[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) w[i] = 0u;
@@ -173,9 +199,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         reinterpret_cast<uint4 *>(io.x0 + g * mlp::kInPad + 32 * half)[kg] =
                             make_uint4(w[4 * kg], w[4 * kg + 1], w[4 * kg + 2], w[4 * kg + 3]);
             } else if (!Train && g < R) {
-                const int64_t p = g / dy;
-                const int j = (int)(g - p * dy);
-                const int nd = obs_idx[j], ri = nd / J, ci = nd - ri * J;
                 const float *xp = x + p * (int64_t)dx;
                 float vals[32];
                 if (half == 0) {  // v patch (25) and w patch elements 0..6
@@ -201,89 +224,85 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
 #pragma unroll
             for (int kg = 0; kg < 4; ++kg)
-                *reinterpret_cast<uint4 *>(smem + kOffA + cm_off(row, 4 * half + kg, 64)) =
+                *reinterpret_cast<uint4 *>(buf + cm_off(row, 4 * half + kg, 64)) =
                     make_uint4(w[4 * kg], w[4 * kg + 1], w[4 * kg + 2], w[4 * kg + 3]);
         }
         fence_proxy_async();
         tc_fence_before();
-        __syncthreads();
+        slot_sync(slot);
         // ---- layer 1
-        if (tid == 0) {
+        if (row == 0) {
             tc_fence_after();
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                umma(tmem, sdesc(sbase + kOffA + 256 * k, 128, 1024), sdesc(sbase + kOffW1 + 256 * k, 128, 1024),
-                     id128, k > 0);
+                umma(dcol, sdesc(sbuf + 256 * k, 128, 1024), sdesc(sbase + kOffW1 + 256 * k, 128, 1024), id128, k > 0);
             umma_commit(bar);
         }
         bool ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) { expired = true; break; }
+        if (slot_any(slot, !ok)) { expired = true; break; }
         tc_fence_after();
-        const int64_t grow = tile * kRows + row;
-        const bool save = Train && io.z1 && grow < R;
+        const bool save = Train && io.z1 && g < R;
 #pragma unroll 1
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+        for (int c0 = 0; c0 < 128; c0 += 32) {  // H over A: layer 1's MMAs have read it
             uint32_t v[32];
             tmem_ld32(lane_base + c0, v);
             tc_wait_ld();
-            gelu_store(v, bias, c0, row, smem + kOffH, save ? io.z1 + grow * mlp::kHid : nullptr,
-                       save ? io.a1 + grow * mlp::kHid : nullptr);
+            gelu_store(v, bias, c0, row, buf, save ? io.z1 + g * mlp::kHid : nullptr,
+                       save ? io.a1 + g * mlp::kHid : nullptr);
         }
         fence_proxy_async();
         tc_fence_before();
-        __syncthreads();
-        // ---- layer 2
-        if (tid == 0) {
+        slot_sync(slot);
+        // ---- layer 2 (into the same columns: every thread has read layer 1's)
+        if (row == 0) {
             tc_fence_after();
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                umma(tmem + 128, sdesc(sbase + kOffH + 256 * k, 128, 2048), sdesc(sbase + kOffW2 + 256 * k, 128, 2048),
-                     id128, k > 0);
+                umma(dcol, sdesc(sbuf + 256 * k, 128, 2048), sdesc(sbase + kOffW2 + 256 * k, 128, 2048), id128, k > 0);
             umma_commit(bar);
         }
         ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) { expired = true; break; }
+        if (slot_any(slot, !ok)) { expired = true; break; }
         tc_fence_after();
 #pragma unroll 1
-        for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 32) {
+        for (int c0 = 0; c0 < 128; c0 += 32) {  // H again: layer 2's MMAs have read it
             uint32_t v[32];
-            tmem_ld32(lane_base + 128 + c0, v);
+            tmem_ld32(lane_base + c0, v);
             tc_wait_ld();
-            gelu_store(v, bias + 128, c0, row, smem + kOffH, save ? io.z2 + grow * mlp::kHid : nullptr,
-                       save ? io.a2 + grow * mlp::kHid : nullptr);
+            gelu_store(v, bias + 128, c0, row, buf, save ? io.z2 + g * mlp::kHid : nullptr,
+                       save ? io.a2 + g * mlp::kHid : nullptr);
         }
         fence_proxy_async();
         tc_fence_before();
-        __syncthreads();
+        slot_sync(slot);
         // ---- layer 3 (N = 16; rows 4..15 of W3 are zero)
-        if (tid == 0) {
+        if (row == 0) {
             tc_fence_after();
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-                umma(tmem, sdesc(sbase + kOffH + 256 * k, 128, 2048), sdesc(sbase + kOffW3 + 256 * k, 128, 2048), id16,
-                     k > 0);
+                umma(dcol, sdesc(sbuf + 256 * k, 128, 2048), sdesc(sbase + kOffW3 + 256 * k, 128, 2048), id16, k > 0);
             umma_commit(bar);
         }
         ok = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
-        if (__syncthreads_or(!ok)) { expired = true; break; }
+        if (slot_any(slot, !ok)) { expired = true; break; }
         tc_fence_after();
-        if (half == 0) {
+        {
             uint32_t v[4];
             tmem_ld4(lane_base, v);
             tc_wait_ld();
-            const int64_t g = tile * kRows + row;
             if (g < R)
                 reinterpret_cast<float4 *>(out)[g] =
                     make_float4(__uint_as_float(v[0]) + bias[256], __uint_as_float(v[1]) + bias[257],
                                 __uint_as_float(v[2]) + bias[258], __uint_as_float(v[3]) + bias[259]);
         }
         tc_fence_before();
+        slot_sync(slot);  // every row's output read before the next tile's layer 1 overwrites the columns
     }
-    // a wait that expired: report it (every thread left the loop together)
-    if (expired && tid == 0 && err) atomicOr(&err[0], kErrTimeout);
+    // a wait that expired: report it (the slot's threads left its loop together)
+    if (expired && row == 0 && err) atomicOr(&err[0], kErrTimeout);
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
@@ -332,7 +351,7 @@ cudaError_t launch_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const 
     const cudaError_t attr_err = tc::forward_attrs();
     if (attr_err != cudaSuccess) return attr_err;
     const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
-    const int64_t grid = std::min<int64_t>(n_tiles, 2 * (int64_t)tc::sm_count());
+    const int64_t grid = std::min<int64_t>((n_tiles + tc::kSlots - 1) / tc::kSlots, (int64_t)tc::sm_count());
     tc::k_proposal_forward_tc<false><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
         J, dx, dy, x, P, pfilt, obs_idx, obs, obs_stride, wp, theta, out, err, tc::TrainIO{});
     return cudaGetLastError();
@@ -350,7 +369,7 @@ cudaError_t launch_train_forward_tc(const float *X, int64_t R, const __nv_bfloat
     const cudaError_t e = tc::forward_attrs();
     if (e != cudaSuccess) return e;
     const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
-    const int64_t grid = std::min<int64_t>(n_tiles, 2 * (int64_t)tc::sm_count());
+    const int64_t grid = std::min<int64_t>((n_tiles + tc::kSlots - 1) / tc::kSlots, (int64_t)tc::sm_count());
     tc::k_proposal_forward_tc<true><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
         2, 8, 1, nullptr, 0, nullptr, nullptr, nullptr, 0, wp, theta, out, err, tc::TrainIO{X, R, x0, z1, z2, a1, a2});
     return cudaGetLastError();
