@@ -2,28 +2,31 @@
 // fifth-generation tensor cores, fused with the construction of its input
 // rows from the lattice state.
 //
-// One CTA of 256 threads (two warpgroups), persistent over tiles of 128
-// network rows (one row per (particle, observed node)); two CTAs per SM
-// (shared memory bounds it).  Thread t works on row t % 128, half t / 128.
-// Per tile:
-//   rows     every thread gathers its half of its row (columns 0..31: the v
-//            patch and the first w values; 32..63: the rest of the w patch and
-//            y; 5x5 patches mirrored at the edges) from the particle's state,
-//            rounds it to BF16 and stores it as the A operand in shared memory;
-//   layer 1  one thread issues 4 tcgen05.mma (M 128, N 128, K 16) into tensor
-//            memory (TMEM columns 0..127), commit -> mbarrier;
-//   GELU     every thread loads its half of its row of the accumulator
-//            (tcgen05.ld; warp w reaches TMEM lanes 32 (w % 4) .. + 31), adds
-//            the bias, applies GELU and stores BF16 as the next A operand;
-//   layer 2  8 MMAs into TMEM columns 128..255, GELU again;
+// One CTA of 512 threads per SM, persistent over tiles of 128 network rows
+// (one row per (particle, observed node)), with four independent slots: each
+// warpgroup of 128 threads carries its own tile through the three layers,
+// with its own 128 TMEM columns (the four slots take all 512), its own 32 KB
+// operand buffer and mbarrier, and named barrier 1 + slot, so a slot's
+// epilogue runs while the others' MMAs do; the weights are staged once for
+// all four.  Thread t works on row t % 128 of slot t / 128.  Per tile:
+//   rows     every thread gathers its row (columns 0..31: the v patch and the
+//            first w values; 32..63: the rest of the w patch and y; 5x5
+//            patches mirrored at the edges) from the particle's state, rounds
+//            it to BF16 and stores it as the A operand in the slot's buffer;
+//   layer 1  the slot's first thread issues 4 tcgen05.mma (M 128, N 128,
+//            K 16) into the slot's TMEM columns, commit -> mbarrier;
+//   GELU     every thread loads its row of the accumulator (tcgen05.ld; warp
+//            w reaches TMEM lanes 32 (w % 4) .. + 31), adds the bias, applies
+//            GELU and stores BF16 as the next A operand over the first;
+//   layer 2  8 MMAs into the same columns (every row of layer 1's read), GELU;
 //   layer 3  8 MMAs with N 16 (W3 zero-padded from 4 to 16 rows) into
-//            columns 0..15; the first warpgroup writes the 4 outputs + bias.
+//            columns 0..15; every thread writes its row's 4 outputs + bias.
 // Operands are K-major without swizzle: element (r, k) of a tile with K
 // columns sits at (r / 8) (K / 8) 128 + (k / 8) 128 + (r % 8) 16 + (k % 8) 2
 // bytes (8 x 16-byte core matrices; K-direction stride 128 B, row-group
-// stride K * 16 B).  The weights are staged once per CTA.  Every wait on the
-// tensor cores is bounded (2 s by the global timer); on expiry the kernel
-// flags kErrTimeout in the context's error word, stops, and frees its TMEM.
+// stride K * 16 B).  Every wait on the tensor cores is bounded (2 s by the
+// global timer); on expiry the slot flags kErrTimeout in the context's error
+// word and stops, and the CTA frees its TMEM once every slot has stopped.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
