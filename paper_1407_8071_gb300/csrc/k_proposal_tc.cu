@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     bool expired = false;
     const int nn = J * J;
-    for (int64_t tile = (int64_t)blockIdx.x * kSlots + slot; tile < n_tiles; tile += (int64_t)gridDim.x * kSlots) {
+    // slot-major: with fewer tiles than SMs each CTA's first slot takes one, spread over the SMs
+    for (int64_t tile = (int64_t)slot * gridDim.x + blockIdx.x; tile < n_tiles; tile += (int64_t)gridDim.x * kSlots) {
         const int64_t g = tile * kRows + row;
         // ---- the input row -> A (columns 0..31, then 32..63)
         const int64_t p = (!Train && g < R) ? g / dy : 0;
@@ -354,7 +355,7 @@ cudaError_t launch_proposal_forward_tc(int32_t J, int32_t dx, int32_t dy, const 
     const cudaError_t attr_err = tc::forward_attrs();
     if (attr_err != cudaSuccess) return attr_err;
     const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
-    const int64_t grid = std::min<int64_t>((n_tiles + tc::kSlots - 1) / tc::kSlots, (int64_t)tc::sm_count());
+    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)tc::sm_count());
     tc::k_proposal_forward_tc<false><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
         J, dx, dy, x, P, pfilt, obs_idx, obs, obs_stride, wp, theta, out, err, tc::TrainIO{});
     return cudaGetLastError();
@@ -372,7 +373,7 @@ cudaError_t launch_train_forward_tc(const float *X, int64_t R, const __nv_bfloat
     const cudaError_t e = tc::forward_attrs();
     if (e != cudaSuccess) return e;
     const int64_t n_tiles = (R + tc::kRows - 1) / tc::kRows;
-    const int64_t grid = std::min<int64_t>((n_tiles + tc::kSlots - 1) / tc::kSlots, (int64_t)tc::sm_count());
+    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)tc::sm_count());
     tc::k_proposal_forward_tc<true><<<(unsigned)grid, tc::kThreads, tc::kSmemBytes, s>>>(
         2, 8, 1, nullptr, 0, nullptr, nullptr, nullptr, 0, wp, theta, out, err, tc::TrainIO{X, R, x0, z1, z2, a1, a2});
     return cudaGetLastError();
