@@ -1128,10 +1128,10 @@ pf_status pf_autotune(pf_ctx *h, int32_t *h_choice)
                 int maxp = 1;
                 while ((maxp + 1) * per <= cap && maxp < 8) ++maxp;
                 // the builds' CTAs per SM: four nodes 2 or 4, eight 2 or 3 (two nodes: one build)
-                const int qcs[2] = {nodes == 2 ? 3 : 2, nodes == 4 ? 4 : 3};
+                const int qcs[2] = {nodes == 2 ? 3 : 2, nodes == 4 ? 4 : 3}, n_qc = nodes == 2 ? 1 : 2;
                 for (int ppc = 1; ppc <= maxp; ++ppc)
-                    for (int qc : qcs) {
-                        if (nodes == 2 && qc != qcs[0]) continue;
+                    for (int iq = 0; iq < n_qc; ++iq) {
+                        const int qc = qcs[iq];
                         c.fhn_nodes = nodes;
                         c.fhn_ppc = ppc;
                         c.fhn_quad_ctas = qc;
