@@ -77,6 +77,31 @@ def test_normals_match_oracle():
     assert err.max() <= 1e-5, err.max()
 
 
+def test_propagation_noise_is_the_stateless_normals_bit_for_bit():
+    """The small-model propagation draws its normals two particles per packed FP32 instruction;
+    pf_rng_normals draws them one at a time. With zero drift, unit noise scale (sigma sqrt(dt) = 1),
+    one sub-step and a zero state, a propagated particle is exactly the normal it drew
+    (fma(1, z, 0) = z), so the two generators must agree bit for bit at the propagation's counters
+    (particle, t = 1, filter, dynamics stream << 24 | block 0), on ragged filters whose threads
+    carry two particles each (and repeat the last one past a sub-tile's end)."""
+    spec = W.linear_gaussian(K=1, dt=1.0, sigma=1.0, A=[[0.0]], obs_idx=[0])
+    N = np.array([257, 64, 1000, 3], dtype=np.int32)
+    seed = 0x5EED0F00D
+    with pf.EnsembleFilter(spec, len(N), N, seed) as f:
+        f.set_state(np.zeros(int(N.sum()), dtype=np.float32), 0)
+        f.propagate(np.zeros(1, dtype=np.float32))
+        x = f.get_state().reshape(-1)
+    fid = np.repeat(np.arange(len(N)), N).astype(np.uint32)
+    pid = np.concatenate([np.arange(n) for n in N]).astype(np.uint32)
+    ctr = np.stack([pid, np.ones_like(pid), fid, np.full_like(pid, 3 << 24)], axis=1).astype(np.uint32)
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_z = torch.empty((len(ctr), 4), dtype=torch.float32, device="cuda")
+    pf.pf_rng_normals(d_ctr, seed, d_z)
+    torch.cuda.synchronize()
+    z = d_z.cpu().numpy()[:, 0]
+    assert np.array_equal(x.view(np.uint32), z.view(np.uint32))
+
+
 # ------------------------------------------------------------------ prior and propagation
 SMALL_SPECS = {
     "lorenz63": lambda: W.lorenz63(),

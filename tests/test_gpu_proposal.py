@@ -65,6 +65,20 @@ def test_zero_network_and_recording_are_the_bootstrap_filter(record):
     assert np.array_equal(e0, e2) and np.array_equal(x0, x2)
 
 
+def test_zero_network_on_a_side_the_four_node_kernels_skip():
+    """J = 6: the bootstrap filter's sub-steps run in the two-node kernel, whose node pair takes the
+    packed FP32 pipes, while the learned path's last sub-step runs in the two-node proposal kernel
+    with the scalar helpers and scalar Box-Muller. A zero network must still reproduce the bootstrap
+    filter bit for bit: the scalar and the packed forms round alike."""
+    spec = W.fhn_lattice(J=6)
+    _, y = oracle.simulate(spec, 4, W.SEED_FHN_OBS)
+    y = y.astype(np.float32)
+    e0, _, x0 = _run(spec, 3, 50, 5, y)
+    e1, fb, x1 = _run(spec, 3, 50, 5, y, theta=mlp.init_params(1, out_scale=0.0))
+    assert np.array_equal(e0, e1) and np.array_equal(x0, x1)
+    assert fb.sum() == 0
+
+
 def test_bad_proposal_falls_back_to_the_transition(record):
     th = mlp.unpack(mlp.init_params(3, out_scale=0.0))
     th["b3"] = np.array([40.0, 40.0, -3.0, -3.0])
