@@ -256,6 +256,29 @@ def test_fhn_full_size_sampled():
     assert np.max(np.abs(lg[sample] - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
 
 
+def test_ragged_full_size_sampled():
+    """The ragged batch at full size -- 256 filters of the 20 x 20 lattice, N log-uniform in
+    [64, 4096], 250,979 particles in one context -- in the layout and the autotuned schedule the
+    bench runs it in: one bootstrap interval from the prior, sampled particles against the oracle."""
+    spec = fhn_spec(W.RAGGED["J"])
+    N = W.ragged_counts(W.RAGGED["n_filters"], W.RAGGED["n_lo"], W.RAGGED["n_hi"])
+    M, seed = len(N), 41
+    _, y = oracle.simulate(spec, 1, W.SEED_FHN_OBS)
+    with pf.EnsembleFilter(spec, M, N, seed) as f:
+        f.autotune()
+        x0 = f.get_state()
+        f.propagate(y[0].astype(np.float32))
+        xg = f.get_state()
+        lg = f.get_logw()
+    pid, fid = ids(N, M)
+    rng = np.random.default_rng(4)
+    sample = rng.choice(int(N.sum()), size=32, replace=False)
+    xo = oracle.propagate(spec, x0[sample].astype(np.float64), pid[sample], fid[sample], 1, seed)
+    assert_state_close(xg[sample], xo)
+    lo = oracle.loglik(spec, xg[sample].astype(np.float64), y[0].astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(lg[sample] - lo) / np.maximum(np.abs(lo), 1.0)) <= 1e-5
+
+
 # ------------------------------------------------------------------ record simulator
 @pytest.mark.parametrize("name", ["lorenz63", "lg3"])
 def test_simulate_matches_oracle_small(name):
