@@ -491,7 +491,7 @@ PF_API pf_status pf_recorded_tuples(const pf_ctx *ctx, int64_t *count);
  * else PF_EINVAL (message in pf_last_error(NULL)).
  * Each call looks the array's address up on the current device, which must be
  * the device of `stream` and of the pointers.  The first call on a device also
- * loads the array there; make that first call before any stream capture.
+ * loads the array there.
  * Every call on a device shares the one array, which keeps the previous call's
  * contents: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The call calls no
