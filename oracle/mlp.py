@@ -11,8 +11,9 @@ Sec. 6 footnote; Remark after Cor. 2 for the auxiliary filter).
 
 Network: 51 inputs (the 5x5 patch of v, the 5x5 patch of w around the node,
 row-major with zero-flux mirroring at the lattice edge, and y at the node)
--> 128 -> 128 -> 4 (o_mu_v, o_mu_w, o_s_v, o_s_w), exact GELU
-g(x) = x Phi(x) between layers.  Parameters are one flat FP32 vector:
+-> 128 -> 128 -> 4 (o_mu_v, o_mu_w, o_s_v, o_s_w), GELU in its tanh form
+(Hendrycks & Gimpel 2016) g(x) = x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) / 2
+between layers, written here as that definition in FP64.  Parameters are one flat FP32 vector:
 W1 (128 x 51), b1 (128), W2 (128 x 128), b2 (128), W3 (4 x 128), b3 (4).
 
 Loss: Gaussian negative log-likelihood of the standardised residual
@@ -76,14 +77,19 @@ def bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
+GELU_K0 = math.sqrt(2.0 / math.pi)
+GELU_K1 = 0.044715
+
+
 def gelu(x):
-    from scipy.special import erf
-    return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
+    """x (1 + tanh(u)) / 2, u = k0 (x + k1 x^3): the tanh form of x Phi(x)."""
+    return 0.5 * x * (1.0 + np.tanh(GELU_K0 * (x + GELU_K1 * x ** 3)))
 
 
 def gelu_grad(x):
-    from scipy.special import erf
-    return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    """d/dx of gelu: (1 + t) / 2 + x (1 - t^2) u' / 2, t = tanh(u), u' = k0 (1 + 3 k1 x^2)."""
+    t = np.tanh(GELU_K0 * (x + GELU_K1 * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * GELU_K0 * (1.0 + 3.0 * GELU_K1 * x * x)
 
 
 def forward(theta: np.ndarray, X: np.ndarray, bf16_emulation: bool = False):

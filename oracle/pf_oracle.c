@@ -397,7 +397,9 @@ static double bf16r(double x)
     return (double)f;
 }
 
-static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+/* GELU in its tanh form (Hendrycks & Gimpel 2016), the network's activation:
+ * x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))) / 2. */
+static double gelu(double x) { return 0.5 * x * (1.0 + tanh(sqrt(2.0 / M_PI) * (x + 0.044715 * x * x * x))); }
 
 void orc_mlp_forward(const orc_proposal *pr, int64_t rows, const double *in, double *out)
 {

@@ -96,7 +96,7 @@ __device__ __forceinline__ void gelu_store(const uint32_t (&v)[32], const float 
                                          make_float2(bias[c0 + c], bias[c0 + c + 1]));
             z[2 * i] = zz.x;
             z[2 * i + 1] = zz.y;
-            const float2 gg = mlp::gelu_fast_x2(zz);
+            const float2 gg = mlp::gelu_x2(zz);
             w[i] = mlp::pack_bf16(gg.x, gg.y);
         }
         *reinterpret_cast<uint4 *>(h + cm_off(r, (c0 >> 3) + g, 128)) = make_uint4(w[0], w[1], w[2], w[3]);

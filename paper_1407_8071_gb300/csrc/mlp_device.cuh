@@ -1,7 +1,8 @@
 // mlp_device.cuh -- the learned proposal's network on the tensor cores.
 //
 // 51 inputs (5x5 patches of v and w around an observed lattice node, and y at
-// the node) -> 128 -> 128 -> 4 (o_mu_v, o_mu_w, o_s_v, o_s_w), exact GELU.
+// the node) -> 128 -> 128 -> 4 (o_mu_v, o_mu_w, o_s_v, o_s_w), GELU in its
+// tanh form.
 // Operands are bfloat16, accumulation FP32 on the tensor cores (tcgen05): the
 // inputs are padded to 64 columns and the 4 outputs to 8 (16 in the MMA).
 // Parameter vector (FP32 master, the oracle's layout): W1 (128 x 51), b1 (128),
@@ -26,16 +27,21 @@ constexpr float kClamp = 3.0f;
 constexpr int kPackW1 = kHid * kInPad, kPackW2 = kHid * kHid, kPackW3 = kOutPad * kHid;
 constexpr int kPackTotal = kPackW1 + kPackW2 + kPackW3;
 
-// GELU of the tensor-core kernels: x Phi(x) with Phi(x) = (1 + erf(x / sqrt 2)) / 2
-// and erf from Abramowitz & Stegun 7.1.26 (Hastings' rational form,
-// |error| <= 1.5e-7): 1 - erf(u) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-u^2},
-// t = 1 / (1 + p u), u = |x| / sqrt 2; Phi(x) = 1 - tail / 2 for x >= 0 and
-// tail / 2 below.  Far below the BF16 rounding of the activations it feeds.
-// Every rounding is spelled out, so that the two-lane form below gives the
-// same bits lane by lane.
-constexpr float kInvSqrt2 = 0.70710678118654752f, kLog2e = 1.44269504088896341f, kAsP = 0.3275911f;
-constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f, kAs4 = -1.453152027f,
-                kAs5 = 1.061405429f;
+// GELU in its tanh form (Hendrycks & Gimpel 2016),
+//   g(x) = x (1 + tanh(u)) / 2,  u = k0 (x + k1 x^3),  k0 = sqrt(2/pi), k1 = 0.044715,
+// which equals x / (1 + e^{-2u}) = x / (1 + 2^a) with a = x (c0 + c1 x^2),
+// c0 = -2 k0 log2(e), c1 = c0 k1: one exp2 and one reciprocal on the MUFU
+// unit and five FP32 operations, each of which rounds to nearest.  With exp2
+// and the reciprocal within 2^-21 and 2^-22 of their results, the value is
+// within 3.6e-7 (|x| + |g(x)|) of g(x): the argument's three roundings enter
+// through r (1 - r) |a| ln 2 <= 0.23 (r = 1 / (1 + 2^a)), exp2's error through
+// r (1 - r) <= 1/4, the reciprocal's and the two last roundings through r.
+// Saturation is exact: 2^a overflows to +inf for large negative x (r = 0,
+// g = -0) and flushes to 0 for large positive x (r = 1, g = x).
+constexpr float kGeluC0 = -2.30220818519592285f;  // -2 sqrt(2/pi) log2(e)
+constexpr float kGeluC1 = -0.102943241596221924f;  // kGeluC0 * 0.044715
+constexpr float kGelu2K0 = 1.59576912160573081f;   // 2 sqrt(2/pi)
+constexpr float kGelu3K1 = 0.134145f;              // 3 * 0.044715
 
 __device__ __forceinline__ float rcp_apx(float x)
 {
@@ -50,43 +56,24 @@ __device__ __forceinline__ float ex2_apx(float x)
     return r;
 }
 
-__device__ __forceinline__ float gelu_fast(float x)
+// g of two values at once on the packed FP32 pipes (each lane rounds as the
+// scalar instruction would).
+__device__ __forceinline__ float2 gelu_x2(float2 x)
 {
-    const float u = __fmul_rn(fabsf(x), kInvSqrt2);
-    const float t = rcp_apx(__fmaf_rn(kAsP, u, 1.0f));
-    float q = __fmaf_rn(t, kAs5, kAs4);
-    q = __fmaf_rn(t, q, kAs3);
-    q = __fmaf_rn(t, q, kAs2);
-    q = __fmaf_rn(t, q, kAs1);
-    q = __fmul_rn(q, t);
-    const float e = ex2_apx(__fmul_rn(__fmul_rn(u, u), -kLog2e));
-    const float tail = __fmul_rn(q, e);  // 1 - erf(|x| / sqrt 2) = 2 Phi(-|x|), without cancellation
-    return __fmul_rn(__fmul_rn(0.5f, x), x >= 0.0f ? __fmaf_rn(tail, -1.0f, 2.0f) : tail);
+    const float2 p = __ffma2_rn(__fmul2_rn(x, x), make_float2(kGeluC1, kGeluC1), make_float2(kGeluC0, kGeluC0));
+    const float2 a = __fmul2_rn(x, p);
+    const float2 d = __fadd2_rn(make_float2(ex2_apx(a.x), ex2_apx(a.y)), make_float2(1.0f, 1.0f));
+    return __fmul2_rn(x, make_float2(rcp_apx(d.x), rcp_apx(d.y)));
 }
 
-// gelu_fast of two values at once on the packed FP32 pipes (lane by lane the
-// same bits, about two thirds of the instructions).
-__device__ __forceinline__ float2 gelu_fast_x2(float2 x)
-{
-    const float2 c = make_float2(kInvSqrt2, kInvSqrt2);
-    const float2 u = __fmul2_rn(make_float2(fabsf(x.x), fabsf(x.y)), c);
-    const float2 d = __ffma2_rn(make_float2(kAsP, kAsP), u, make_float2(1.0f, 1.0f));
-    const float2 t = make_float2(rcp_apx(d.x), rcp_apx(d.y));
-    float2 q = __ffma2_rn(t, make_float2(kAs5, kAs5), make_float2(kAs4, kAs4));
-    q = __ffma2_rn(t, q, make_float2(kAs3, kAs3));
-    q = __ffma2_rn(t, q, make_float2(kAs2, kAs2));
-    q = __ffma2_rn(t, q, make_float2(kAs1, kAs1));
-    q = __fmul2_rn(q, t);
-    const float2 a = __fmul2_rn(__fmul2_rn(u, u), make_float2(-kLog2e, -kLog2e));
-    const float2 tail = __fmul2_rn(q, make_float2(ex2_apx(a.x), ex2_apx(a.y)));
-    const float2 two = __ffma2_rn(tail, make_float2(-1.0f, -1.0f), make_float2(2.0f, 2.0f));
-    const float2 sel = make_float2(x.x >= 0.0f ? two.x : tail.x, x.y >= 0.0f ? two.y : tail.y);
-    return __fmul2_rn(__fmul2_rn(make_float2(0.5f, 0.5f), x), sel);
-}
-
+// g'(x) = r + x r (1 - r) 2 k0 (1 + 3 k1 x^2), r = 1 / (1 + e^{-2u}) (the
+// training kernels' GELU derivative; r (1 - r) is written so that it is 0,
+// not NaN, where 2^a saturates).
 __device__ __forceinline__ float gelu_grad(float x)
 {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+    const float x2 = x * x;
+    const float r = rcp_apx(1.0f + ex2_apx(x * fmaf(kGeluC1, x2, kGeluC0)));
+    return r + x * r * (1.0f - r) * (kGelu2K0 * fmaf(kGelu3K1, x2, 1.0f));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)

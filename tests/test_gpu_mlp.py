@@ -124,7 +124,7 @@ def test_lattice_forward_on_tcgen05_matches_oracle(J, P):
     device, the network on tcgen05 with TMEM accumulators (a ragged last tile
     of 128 rows), against the FP64 oracle's rows (oracle/mlp.patch_rows) and
     BF16-emulating forward; tolerance as for the forward above (the bound
-    allows the GELU's erf approximation, |error| <= 1.5e-7)."""
+    allows the FP32 GELU's own error, 4e-7 (|z| + |g(z)|))."""
     from paper_1407_8071_gb300 import workloads as W
     th = _theta(9)
     nodes = W.fhn_obs_nodes(J, 4 if J > 2 else 1)

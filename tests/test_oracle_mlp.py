@@ -2,8 +2,11 @@
 
 * The hand-written backpropagation equals central finite differences of the
   loss (FP64, no BF16 rounding), parameter by parameter on a sample.
-* GELU: g(0) = 0, g(x) -> x for large x, g(-x) = g(x) - x; its derivative
-  matches finite differences.
+* GELU (tanh form): g(0) = 0, g(x) -> x for large x, g(-x) = g(x) - x; its
+  derivative matches finite differences; g'(0) = 1/2 and g''(0) = sqrt(2/pi),
+  as for x Phi(x); the x^4 coefficient of its Taylor series,
+  k0 (k1 - k0^2 / 3) / 2, pins k1; and it stays within 5e-4 of x Phi(x)
+  (scipy's erf) on [-12, 12] (the form's known accuracy, about 4.7e-4).
 * bf16 rounding: exact values stay, ties go to even, the relative error is
   at most 2^-8 (7 stored fraction bits: half an ulp).
 * The NLL of a standard-normal residual with zero output equals
@@ -51,6 +54,21 @@ def test_gelu_closed_forms():
     assert mlp.gelu(np.array([30.0]))[0] == 30.0
     h = 1e-6
     assert np.allclose(mlp.gelu_grad(x), (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h), atol=1e-8)
+
+
+def test_gelu_tanh_form_against_x_phi():
+    from scipy.special import erf
+    k0 = math.sqrt(2.0 / math.pi)
+    assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
+    h = 1e-5  # g''(0) = 2 phi(0) = sqrt(2/pi), the same as x Phi(x)'s
+    d2 = (mlp.gelu_grad(np.array([h]))[0] - mlp.gelu_grad(np.array([-h]))[0]) / (2 * h)
+    assert d2 == pytest.approx(k0, rel=1e-9)
+    # series g = x/2 + k0 x^2/2 + k0 (k1 - k0^2/3) x^4 / 2 + O(x^6) with k1 = 0.044715
+    x = 3e-3
+    c4 = (mlp.gelu(np.array([x]))[0] - x / 2 - k0 * x * x / 2) / x ** 4
+    assert c4 == pytest.approx(0.5 * k0 * (0.044715 - k0 ** 2 / 3), rel=1e-5)
+    z = np.linspace(-12.0, 12.0, 240001)
+    assert np.max(np.abs(mlp.gelu(z) - 0.5 * z * (1.0 + erf(z / math.sqrt(2.0))))) <= 5e-4
 
 
 def test_bf16_rounding():
