@@ -138,22 +138,31 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def source_digest(unit: str = "k_filter.cu"):
-    """Digest of the CUDA translation unit `unit` and every header beside it,
-    with comments and blank lines removed, so that the recorded DRAM traffic
-    stays attached to the code it was measured on."""
+def source_digest(unit: str = "k_filter.cu", root: str = None):
+    """Digest of the CUDA translation unit `unit` and every local header it
+    includes (directly or through another header), with comments and blank
+    lines removed, so that a recorded measurement stays attached to the code
+    it was taken on."""
     import re
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1407_8071_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if not (f == unit or f.endswith((".h", ".cuh"))):
+    root = root or ROOT
+    dirs = [os.path.join(root, "paper_1407_8071_gb300", "csrc"), os.path.join(root, "include")]
+    found, todo = {}, [unit]
+    while todo:
+        name = todo.pop()
+        if name in found:
             continue
-        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+        path = next((os.path.join(d, name) for d in dirs if os.path.exists(os.path.join(d, name))), None)
+        if path is None:
+            continue
+        with open(path, encoding="utf-8") as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         text = re.sub(r"//[^\n]*", "", text)
-        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
-        h.update(("\n".join(lines) + "\n").encode())
+        found[name] = "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip()) + "\n"
+        todo.extend(re.findall(r'#include\s+"([^"]+)"', text))
+    h = hashlib.sha256()
+    for name in sorted(found):
+        h.update(name.encode() + b"\n" + found[name].encode())
     return h.hexdigest()[:16]
 
 
