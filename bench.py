@@ -570,9 +570,10 @@ def measure(name, steps, warmup, rank, world, barrier, cpu_seconds):
 
     # the dominant kernel, timed live per launch
     t_prop, t_res, _ = phase_times(torch, wl)
-    # bootstrap steps fold the resampling's gather into the next propagation: the resampling then reads
-    # the ancestors' values for the means and writes no copy of the state
-    folded = not wl.aux and wl.theta is None
+    # bootstrap steps, and learned-proposal steps whose proposal acts on the last sub-step only (the
+    # bench's), fold the resampling's gather into the next propagation: the resampling then reads the
+    # ancestors' values for the means and writes no copy of the state
+    folded = not wl.aux
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if wl.spec.kind == W.LORENZ63:

@@ -2213,10 +2213,11 @@ cudaError_t launch_propagate(const Ctx &c, const float *d_obs, int32_t stride, c
     }
 }
 
-cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, float *x, int32_t n_steps,
-                                cudaStream_t s)
+cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
+                                const int32_t *gather, int32_t n_steps, cudaStream_t s)
 {
-    return launch_fhn_interval(c, d_obs, stride, x, x, n_steps, false, s);
+    const AuxPtrs g{nullptr, nullptr, nullptr, nullptr, gather};
+    return launch_fhn_interval(c, d_obs, stride, xi, xo, n_steps, false, s, nullptr, nullptr, g, 1);
 }
 
 cudaError_t launch_refresh_max(const Ctx &c, cudaStream_t s)

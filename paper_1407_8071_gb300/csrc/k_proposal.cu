@@ -477,7 +477,8 @@ __global__ void k_gather_tuples(ModelParams mp, const FilterDesc *filt, const in
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t stride, float *x, cudaStream_t s)
+cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *x,
+                                   const int32_t *gather, cudaStream_t s)
 {
     const int pairs = c.mp.J * c.mp.J / 2;
     int n = 1;
@@ -490,8 +491,10 @@ cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t str
     // network inputs at the same place (without a network the span's sub-steps are the transition's)
     const int L = c.prop_span;
     if (c.mp.K > L) {
-        cudaError_t e = launch_fhn_substeps(c, d_obs, stride, x, c.mp.K - L, s);
+        cudaError_t e = launch_fhn_substeps(c, d_obs, stride, xi, x, gather, c.mp.K - L, s);
         if (e != cudaSuccess) return e;
+    } else if (xi != x || gather) {
+        return cudaErrorInvalidValue;  // a span of the whole interval steps in place
     }
     const float *mo = nullptr;
     if (c.rec_X) {  // the recorded tuples need the rows themselves

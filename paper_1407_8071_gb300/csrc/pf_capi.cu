@@ -129,7 +129,9 @@ int32_t kernel_stride(const Ctx &c, int mode) { return mode == 0 ? 0 : c.mp.dy; 
 // gather into x[cur ^ 1].  Either way the step's particles end in x[cur ^ 1].
 cudaError_t enqueue_propagate(Ctx &c, int mode, bool fold = false)
 {
-    if (c.split_path()) return launch_propagate_split(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.stream);
+    if (c.split_path())
+        return launch_propagate_split(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[fold ? c.cur ^ 1 : c.cur],
+                                      fold && c.gather_pending ? c.anc : nullptr, c.stream);
     if (fold)
         return launch_propagate_fold(c, c.d_obs, kernel_stride(c, mode), c.x[c.cur], c.x[c.cur ^ 1],
                                      c.gather_pending ? c.anc : nullptr, c.stream);
@@ -1013,7 +1015,7 @@ pf_status pf_set_proposal_span(pf_ctx *h, int32_t span)
     if (c.mp.kind != PF_MODEL_FHN_LATTICE) return fail(c, PF_EUNSUPPORTED, "the learned proposal is for the lattice");
     if (span < 1 || span > c.mp.K) return fail(c, PF_EINVAL, "span must be in [1, steps_per_obs]");
     if (span > 1 && c.mp.J % 4 != 0) return fail(c, PF_EUNSUPPORTED, "a span above one needs J divisible by 4");
-    pf_status st = sync(c, "set_proposal_span");
+    pf_status st = sync_materialised(c, "set_proposal_span");
     if (st != PF_OK) return st;
     drop_graphs(c);
     c.prop_span = span;

@@ -158,9 +158,14 @@ cudaError_t launch_adaptive_step(const Ctx &c, const float *d_obs, int32_t obs_s
 // One observation step of the ensemble of auxiliary particle filters (k_filter.cu).
 cudaError_t launch_apf_step(const Ctx &c, const float *d_obs, int32_t obs_stride, cudaStream_t s);
 // Learned proposal (k_filter.cu, k_proposal.cu, k_mlp.cu).
-cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, float *x, int32_t n_steps,
-                                cudaStream_t s);
-cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t stride, float *x, cudaStream_t s);
+// n_steps ordinary sub-steps xi -> xo (xi == xo: in place), from the rows of
+// the ancestors gather[p] when gather is non-null (a folded gather).
+cudaError_t launch_fhn_substeps(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *xo,
+                                const int32_t *gather, int32_t n_steps, cudaStream_t s);
+// The learned-proposal step's propagation into x: its ordinary sub-steps from
+// xi (through gather when non-null), then the proposal's span in place in x.
+cudaError_t launch_propagate_split(const Ctx &c, const float *d_obs, int32_t stride, const float *xi, float *x,
+                                   const int32_t *gather, cudaStream_t s);
 cudaError_t launch_gather_tuples(const Ctx &c, const float *x_new, cudaStream_t s);
 cudaError_t launch_mlp_pack(const float *theta, __nv_bfloat16 *wp, __nv_bfloat16 *w2t, cudaStream_t s);
 // Network forward on the tcgen05 tensor cores fused with its input rows
@@ -271,11 +276,13 @@ struct Ctx {
     int32_t rec_stride = 1;
     int64_t *rec_sel_off = nullptr;   // [M] kept particles before each filter
     bool split_path() const { return prop_on || rec_X != nullptr; }
-    // Bootstrap filters fold the resampling's gather into the next
+    // Bootstrap filters, and the learned proposal when its span leaves
+    // ordinary sub-steps before it, fold the resampling's gather into the next
     // propagation (Alg. 1 step 2b's copy is never written): after such a step
     // the resampled particles are particles off_m + anc[p] of x[cur]
     // (gather_pending), and every other reader first materialises them.
-    bool fold_gather() const { return !aux && !adaptive() && !split_path(); }
+    // Recording steps keep the copy (their tuples read the ancestors' rows).
+    bool fold_gather() const { return !aux && !adaptive() && !rec_X && (!prop_on || mp.K > prop_span); }
     bool gather_pending = false;
 
     int cur = 0;  // x[cur] holds the current particles

@@ -89,6 +89,36 @@ def test_bad_proposal_falls_back_to_the_transition(record):
     assert np.array_equal(e0, e1) and np.array_equal(x0, x1)
 
 
+@pytest.mark.parametrize("span", [1, 4, SPEC.K])
+def test_folded_gather_with_the_learned_proposal(record, span):
+    """Learned-proposal steps fold the resampling's gather into the next step's
+    ordinary sub-steps (which load each particle's ancestor row themselves) when
+    the proposal's span leaves some; the halves pf_propagate / pf_resample copy
+    the resampled rows instead, and a read in between writes a pending gather out.
+    All three give the same particles, estimates and ancestors bit for bit (a span
+    of the whole interval takes the copy in every form)."""
+    theta = _moderate_proposal()
+    N = np.array([300, 40, 150], dtype=np.int32)
+    outs = []
+    for mode in ("step", "phases", "step+read"):
+        with pf.EnsembleFilter(SPEC, len(N), N, 21) as f:
+            f.set_proposal(theta, 0.1)
+            f.set_proposal_span(span)
+            for t in range(4):
+                if mode == "phases":
+                    f.propagate(record[t])
+                    f.resample()
+                else:
+                    f.step(record[t])
+                    if mode == "step+read" and t % 2 == 0:
+                        f.get_state()
+            outs.append((f.get_state(), f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True),
+                         f.get_ancestors(), f.estimate(pf.PF_STAT_FALLBACK, per_filter=True)))
+    for x, e, a, fb in outs[1:]:
+        assert np.array_equal(x, outs[0][0]) and np.array_equal(e, outs[0][1])
+        assert np.array_equal(a, outs[0][2]) and np.array_equal(fb, outs[0][3])
+
+
 def _moderate_proposal():
     th = mlp.unpack(mlp.init_params(1, out_scale=0.0))
     th["b3"] = np.array([0.15, -0.1, 0.1, 0.05])
