@@ -491,7 +491,8 @@ PF_API pf_status pf_recorded_tuples(const pf_ctx *ctx, int64_t *count);
  * else PF_EINVAL (message in pf_last_error(NULL)).
  * Each call looks the array's address up on the current device, which must be
  * the device of `stream` and of the pointers.  The first call on a device also
- * loads the array there.
+ * loads the array there (the library's device code is loaded on first use), so
+ * that first call should come before any stream capture.
  * Every call on a device shares the one array, which keeps the previous call's
  * contents: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The call calls no
