@@ -119,6 +119,35 @@ def test_folded_gather_with_the_learned_proposal(record, span):
         assert np.array_equal(a, outs[0][2]) and np.array_equal(fb, outs[0][3])
 
 
+def test_span_and_recording_changes_between_folded_steps(record):
+    """Changing the proposal's span or arming tuple recording between steps switches a
+    context between the folded and the copying form while a gather may be pending;
+    the results must equal those of the same schedule taken as copying halves."""
+    theta = _moderate_proposal()
+    N = np.array([260, 33, 128], dtype=np.int32)
+    X = torch.empty((20000, 51), dtype=torch.float32, device="cuda")
+    R = torch.empty((20000, 2), dtype=torch.float32, device="cuda")
+    schedule = [(1, False), (SPEC.K, False), (1, False), (1, True), (1, False), (4, False)]
+    outs = []
+    for halves in (False, True):
+        with pf.EnsembleFilter(SPEC, len(N), N, 33) as f:
+            f.set_proposal(theta, 0.1)
+            for t, (span, rec) in enumerate(schedule):
+                f.set_proposal_span(span)
+                if rec:
+                    f.record_tuples(X, R)
+                if halves:
+                    f.propagate(record[t])
+                    f.resample()
+                else:
+                    f.step(record[t])
+                if rec:
+                    f.record_tuples(None, None)
+            outs.append((f.get_state(), f.estimate(pf.PF_STAT_MEAN, var=-1, per_filter=True), f.get_ancestors()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+
+
 def _moderate_proposal():
     th = mlp.unpack(mlp.init_params(1, out_scale=0.0))
     th["b3"] = np.array([0.15, -0.1, 0.1, 0.05])
