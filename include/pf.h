@@ -505,6 +505,20 @@ PF_API pf_status pf_recorded_tuples(const pf_ctx *ctx, int64_t *count);
 PF_API pf_status pf_systematic_resample_noalloc(int32_t M, const int32_t *h_N, const double *d_w, const double *d_u,
                                                 int32_t *d_anc, void *stream);
 
+/* Self-test of the failure detection of bounded device waits.  Every wait of
+ * this library's kernels on another agent (the tensor cores' completion
+ * barriers) is bounded by the GPU's global timer; a wait that runs out sets
+ * the error word the host turns into PF_ETIMEOUT instead of hanging the GPU.
+ * This call runs one such wait, with a 20 ms limit, on a barrier of its own:
+ * arrive != 0 completes the barrier first (the wait succeeds: PF_OK); arrive
+ * == 0 leaves it incomplete, so nothing can end the wait but its limit
+ * (PF_ETIMEOUT, message in pf_last_error(NULL)).  Either way no work is in
+ * flight when the wait gives up, the kernel returns, and the device and every
+ * context stay usable.  stream: a CUDA stream of the current device, or NULL.
+ * Synchronises the stream.  Errors: PF_ECUDA.  The paper has no counterpart;
+ * it checks this library's own error path. */
+PF_API pf_status pf_probe_bounded_wait(int32_t arrive, void *stream);
+
 /* --------------------------------------------------------------------- */
 /* Synthetic records                                                      */
 /* --------------------------------------------------------------------- */

@@ -64,12 +64,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait for one completion of the barrier's phase `parity`.
+// Bounded wait for one completion of the barrier's phase `parity`: false once
+// LimitNs nanoseconds of the global timer have passed without it (2 s for the
+// kernels; the self-test in pf_probe.cu takes a short limit).
+template <uint64_t LimitNs = 2000000000ull>
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
 {
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > LimitNs) return false;
     return true;
 }
 

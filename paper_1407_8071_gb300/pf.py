@@ -70,6 +70,7 @@ _SIGS = {
                                          c_size_t, c_void_p]),
     "pf_systematic_resample_noalloc": (c_int32, [c_int32, POINTER(c_int32), c_void_p, c_void_p, c_void_p,
                                                  c_void_p]),
+    "pf_probe_bounded_wait": (c_int32, [c_int32, c_void_p]),
     "pf_set_schedule": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
     "pf_set_auxiliary": (c_int32, [c_void_p, c_int32]),
     "pf_estimate_async": (c_int32, [c_void_p, c_void_p, c_void_p]),
@@ -210,6 +211,13 @@ def pf_systematic_resample_noalloc(N: Sequence[int], d_w, d_u, d_anc, stream=Non
     Nh = np.ascontiguousarray(N, dtype=np.int32)
     _check(lib().pf_systematic_resample_noalloc(len(Nh), _ip(Nh), d_w.data_ptr(), d_u.data_ptr(), d_anc.data_ptr(),
                                                 stream))
+
+
+def pf_probe_bounded_wait(arrive: bool, stream=None) -> int:
+    """One bounded device wait on a barrier of the library's own (20 ms limit):
+    the status it returns, PF_OK when the barrier was completed first,
+    PF_ETIMEOUT when nothing completed it and the wait gave up."""
+    return int(lib().pf_probe_bounded_wait(1 if arrive else 0, stream))
 
 
 MLP_PARAMS = 23684
