@@ -83,12 +83,12 @@ GELU_K1 = 0.044715
 
 def gelu(x):
     """x (1 + tanh(u)) / 2, u = k0 (x + k1 x^3): the tanh form of x Phi(x)."""
-    return 0.5 * x * (1.0 + np.tanh(GELU_K0 * (x + GELU_K1 * x ** 3)))
+    return 0.5 * x * (1.0 + np.tanh(GELU_K0 * (x + GELU_K1 * x * x * x)))
 
 
 def gelu_grad(x):
     """d/dx of gelu: (1 + t) / 2 + x (1 - t^2) u' / 2, t = tanh(u), u' = k0 (1 + 3 k1 x^2)."""
-    t = np.tanh(GELU_K0 * (x + GELU_K1 * x ** 3))
+    t = np.tanh(GELU_K0 * (x + GELU_K1 * x * x * x))
     return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * GELU_K0 * (1.0 + 3.0 * GELU_K1 * x * x)
 
 
